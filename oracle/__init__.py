@@ -1,0 +1,319 @@
+"""FP64 CPU oracle for SSIM / MS-SSIM (arXiv 2101.06354).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The CUDA library never calls it and shares no code with it.
+
+The window statistics, SSIM terms, integral images, downsampling and the
+gradient are plain C (``ssim_oracle.c``); this module marshals numpy arrays
+into it and writes the multi-scale, colour and temporal combinations out in
+numpy, each function citing the passage of the paper it follows.
+
+Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
+(closed forms, invariants, library routines on small inputs, finite
+differences); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from .build import build_oracle
+
+_lib = None
+
+#: MS-SSIM scale exponents used by the paper's MS-SSIM implementations
+#: (Introduction: five dyadic scales combined by exponential weighting).  The
+#: paper does not print them; these are the values of the original MS-SSIM.
+MSSSIM_EXPONENTS = (0.0448, 0.2856, 0.3001, 0.2363, 0.1333)
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build_oracle())
+        L, I = ctypes.c_long, ctypes.c_int
+        D = ctypes.c_double
+        lib.oracle_gaussian_window.argtypes = [I, D, _dp]
+        lib.oracle_box_window.argtypes = [I, _dp]
+        lib.oracle_window_stats.argtypes = [_dp, _dp, L, L, _dp, I, I, _dp, _dp, _dp, _dp, _dp]
+        lib.oracle_ssim_terms.argtypes = [_dp, _dp, _dp, _dp, _dp, L, D, D, _dp, _dp, _dp]
+        lib.oracle_mean.argtypes = [_dp, L]
+        lib.oracle_mean.restype = D
+        lib.oracle_box_sums_direct.argtypes = [_u8p, _u8p, L, L, L, I, I, _i64p]
+        lib.oracle_box_sums_integral.argtypes = [_u8p, _u8p, L, L, L, I, I, _i64p]
+        lib.oracle_box_ssim_from_sums.argtypes = [_i64p, L, I, D, D, _dp, _dp]
+        lib.oracle_downsample2x2.argtypes = [_dp, L, L, _dp]
+        lib.oracle_ssim_grad.argtypes = [_dp, _dp, L, L, _dp, I, I, D, D, I, _dp]
+        lib.oracle_num_threads.restype = I
+        _lib = lib
+    return _lib
+
+
+def _ptr(a, t=_dp):
+    return a.ctypes.data_as(t)
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _check(rc):
+    if rc != 0:
+        raise ValueError("oracle rejected its arguments (rc=%d)" % rc)
+
+
+def num_threads() -> int:
+    """Threads the oracle's OpenMP split uses."""
+    return int(_load().oracle_num_threads())
+
+
+def out_shape(h: int, w: int, k: int, stride: int):
+    """Valid, strided map size (Section "Effect of stride"): floor((n-k)/s)+1."""
+    return ((h - k) // stride + 1, (w - k) // stride + 1)
+
+
+def constants(K1: float = 0.01, K2: float = 0.03, L: float = 255.0):
+    """C1 = (K1 L)^2, C2 = (K2 L)^2 (Background section)."""
+    return (K1 * L) ** 2, (K2 * L) ** 2
+
+
+def gaussian_window(k: int = 11, sigma: float = 1.5) -> np.ndarray:
+    """k x k Gaussian weights summing to one (Background section)."""
+    w = np.empty((k, k), np.float64)
+    _check(_load().oracle_gaussian_window(k, sigma, _ptr(w)))
+    return w
+
+
+def box_window(k: int) -> np.ndarray:
+    """k x k rectangular weights 1/k^2."""
+    w = np.empty((k, k), np.float64)
+    _check(_load().oracle_box_window(k, _ptr(w)))
+    return w
+
+
+def window(kind: str, k: int, sigma: float = 1.5) -> np.ndarray:
+    if kind == "gaussian":
+        return gaussian_window(k, sigma)
+    if kind == "box":
+        return box_window(k)
+    raise ValueError(kind)
+
+
+def gaussian_k_for_sigma(sigma: float) -> int:
+    """Window width for a Gaussian of scale sigma.
+
+    Section "Effect of window size" truncates at about 7 sigma and forces an
+    odd width; this helper takes 2*floor(3.5 sigma)+1 (11 at sigma = 1.5,
+    the same as MATLAB's 2*ceil(3 sigma)+1 there).
+    """
+    return 2 * int(math.floor(3.5 * sigma)) + 1
+
+
+def rect_k_equivalent(sigma: float, rule: str = "variance") -> int:
+    """Rectangular window size 2K+1 matched to a Gaussian (Section "Effect of
+    window size"): same variance K = ceil(sigma sqrt 3); same 3 dB bandwidth
+    K = ceil(1.602 sigma)."""
+    if rule == "variance":
+        K = math.ceil(sigma * math.sqrt(3.0))
+    elif rule == "bandwidth":
+        K = math.ceil(1.602 * sigma)
+    else:
+        raise ValueError(rule)
+    return 2 * K + 1
+
+
+def window_stats(x, y, w, stride: int = 1):
+    """Eqs. local_means .. local_corr at every valid strided position."""
+    x, y, w = _f64(x), _f64(y), _f64(w)
+    H, W = x.shape
+    k = w.shape[0]
+    if y.shape != x.shape or w.shape != (k, k) or H < k or W < k or stride < 1:
+        raise ValueError("bad shapes")
+    oh, ow = out_shape(H, W, k, stride)
+    maps = [np.empty((oh, ow), np.float64) for _ in range(5)]
+    _check(_load().oracle_window_stats(_ptr(x), _ptr(y), H, W, _ptr(w), k, stride,
+                                       *[_ptr(m) for m in maps]))
+    return dict(zip(("mu1", "mu2", "var1", "var2", "cov"), maps))
+
+
+def ssim_terms(st, C1: float, C2: float):
+    """Eq. lum_term and the C3 = C2/2 contrast-structure term; returns l, cs, Q."""
+    n = st["mu1"].size
+    l, cs, q = (np.empty(st["mu1"].shape, np.float64) for _ in range(3))
+    _check(_load().oracle_ssim_terms(*[_ptr(st[k]) for k in ("mu1", "mu2", "var1", "var2", "cov")],
+                                     n, C1, C2, _ptr(l), _ptr(cs), _ptr(q)))
+    return l, cs, q
+
+
+def mean(v) -> float:
+    """Mean pooling over the map elements that exist (Background section)."""
+    v = _f64(v).ravel()
+    return float(_load().oracle_mean(_ptr(v), v.size))
+
+
+def ssim(x, y, window_kind: str = "gaussian", k: int = 11, sigma: float = 1.5,
+         K1: float = 0.01, K2: float = 0.03, L: float = 255.0, stride: int = 1):
+    """SSIM map and MSSIM of one pair, valid borders.
+
+    Returns ``(mssim, maps)`` with maps = {"q", "cs", "l", and the statistics}.
+    """
+    C1, C2 = constants(K1, K2, L)
+    st = window_stats(x, y, window(window_kind, k, sigma), stride)
+    l, cs, q = ssim_terms(st, C1, C2)
+    maps = dict(st, l=l, cs=cs, q=q)
+    return mean(q), maps
+
+
+def box_sums(x, y, k: int, stride: int = 1, method: str = "integral"):
+    """Exact int64 window sums (S1_1, S1_2, S2_1, S2_2, S12) of a uint8 pair,
+    shape (OH, OW, 5).  method="integral" follows the paper's summed-area-table
+    algorithm (Eqs. integral_image_start .. integral_image_end);
+    method="direct" sums each window."""
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    y = np.ascontiguousarray(y, dtype=np.uint8)
+    H, W = x.shape
+    if y.shape != x.shape or H < k or W < k or stride < 1 or k < 1:
+        raise ValueError("bad shapes")
+    oh, ow = out_shape(H, W, k, stride)
+    out = np.empty((oh, ow, 5), np.int64)
+    fn = {"integral": _load().oracle_box_sums_integral,
+          "direct": _load().oracle_box_sums_direct}[method]
+    _check(fn(_ptr(x, _u8p), _ptr(y, _u8p), H, W, W, k, stride, _ptr(out, _i64p)))
+    return out
+
+
+def box_ssim(x, y, k: int = 8, stride: int = 4, K1: float = 0.01, K2: float = 0.03,
+             L: float = 255.0):
+    """Rectangular-window SSIM of a uint8 pair through integral images
+    (Eqs. mean_from_sum .. corr_from_sum).  Returns (mssim, q_map, cs_map, sums)."""
+    C1, C2 = constants(K1, K2, L)
+    sums = box_sums(x, y, k, stride, "integral")
+    n = sums.shape[0] * sums.shape[1]
+    q = np.empty(sums.shape[:2], np.float64)
+    cs = np.empty(sums.shape[:2], np.float64)
+    _check(_load().oracle_box_ssim_from_sums(_ptr(sums, _i64p), n, k, C1, C2, _ptr(q), _ptr(cs)))
+    return mean(q), q, cs, sums
+
+
+def downsample2x2(img) -> np.ndarray:
+    """2x2 average pooling, floor size (Daala / Scikit-Video / Tensorflow MS-SSIM)."""
+    img = _f64(img)
+    H, W = img.shape
+    out = np.empty((H // 2, W // 2), np.float64)
+    _check(_load().oracle_downsample2x2(_ptr(img), H, W, _ptr(out)))
+    return out
+
+
+def msssim(x, y, scales: int = 5, exponents=MSSSIM_EXPONENTS, combine: str = "product",
+           window_kind: str = "gaussian", k: int = 11, sigma: float = 1.5,
+           K1: float = 0.01, K2: float = 0.03, L: float = 255.0):
+    """MS-SSIM (Introduction; Section "Salient Features ...").
+
+    Scale 1 is the input; scale j+1 is the 2x2 average of scale j.  The
+    contrast-structure term is pooled at every scale and the luminance term
+    only at the coarsest: m_j = mean cs_j for j < S and m_S = mean Q_S.
+    combine="product": prod_j m_j^beta_j.  combine="sum" (Scikit-Video):
+    sum_j (beta_j / sum beta) m_j, a convex combination.
+    Returns (score, per_scale) with per_scale[j] = (mean cs_j, mean Q_j).
+    """
+    exps = np.asarray(exponents[:scales], np.float64)
+    if len(exps) != scales:
+        raise ValueError("need one exponent per scale")
+    C1, C2 = constants(K1, K2, L)
+    w = window(window_kind, k, sigma)
+    a, b = _f64(x), _f64(y)
+    per = []
+    for j in range(scales):
+        st = window_stats(a, b, w, 1)
+        _, cs, q = ssim_terms(st, C1, C2)
+        per.append((mean(cs), mean(q)))
+        if j + 1 < scales:
+            a, b = downsample2x2(a), downsample2x2(b)
+    m = np.array([per[j][0] for j in range(scales - 1)] + [per[-1][1]])
+    if combine == "product":
+        with np.errstate(invalid="ignore"):
+            score = float(np.prod(np.power(m, exps)))
+    elif combine == "sum":
+        score = float(np.sum(exps / exps.sum() * m))
+    else:
+        raise ValueError(combine)
+    return score, per
+
+
+def ssim_grad(x, y, window_kind: str = "gaussian", k: int = 11, sigma: float = 1.5,
+              K1: float = 0.01, K2: float = 0.03, L: float = 255.0, stride: int = 1,
+              which: str = "q") -> np.ndarray:
+    """d(mean Q)/dy (which="q") or d(mean cs)/dy (which="cs"); chain rule of
+    the Background-section definition (see ssim_oracle.c)."""
+    C1, C2 = constants(K1, K2, L)
+    x, y = _f64(x), _f64(y)
+    w = window(window_kind, k, sigma)
+    g = np.empty_like(y)
+    H, W = y.shape
+    _check(_load().oracle_ssim_grad(_ptr(x), _ptr(y), H, W, _ptr(w), k, stride, C1, C2,
+                                    {"q": 0, "cs": 1}[which], _ptr(g)))
+    return g
+
+
+def msssim_grad(x, y, scales: int = 5, exponents=MSSSIM_EXPONENTS, combine: str = "product",
+                window_kind: str = "gaussian", k: int = 11, sigma: float = 1.5,
+                K1: float = 0.01, K2: float = 0.03, L: float = 255.0):
+    """d(MS-SSIM)/dy by the chain rule through the scale combination and the
+    2x2 average pooling (its adjoint spreads a quarter of each coarse gradient
+    to the four pixels it averaged)."""
+    score, per = msssim(x, y, scales, exponents, combine, window_kind, k, sigma, K1, K2, L)
+    exps = np.asarray(exponents[:scales], np.float64)
+    m = np.array([per[j][0] for j in range(scales - 1)] + [per[-1][1]])
+    if combine == "product":
+        dscore_dm = score * exps / m
+    else:
+        dscore_dm = exps / exps.sum()
+    xs, ys = [_f64(x)], [_f64(y)]
+    for _ in range(scales - 1):
+        xs.append(downsample2x2(xs[-1]))
+        ys.append(downsample2x2(ys[-1]))
+    g = None
+    for j in reversed(range(scales)):
+        gj = dscore_dm[j] * ssim_grad(xs[j], ys[j], window_kind, k, sigma, K1, K2, L, 1,
+                                      "q" if j == scales - 1 else "cs")
+        if g is not None:
+            up = np.zeros_like(gj)
+            h2, w2 = g.shape
+            up[: 2 * h2, : 2 * w2] = 0.25 * np.repeat(np.repeat(g, 2, 0), 2, 1)
+            gj = gj + up
+        g = gj
+    return score, g
+
+
+def colour_score(s_y: float, s_u: float, s_v: float, weights=(6.0, 1.0, 1.0)) -> float:
+    """Channel-weighted colour SSIM (Section "Channel-wise SSIM"):
+    F = (f_Y + alpha f_Cb + beta f_Cr) / (1 + alpha + beta); weights are
+    (w_Y, w_U, w_V) = (1, alpha, beta) up to scale, e.g. 6:1:1 or 0.8/0.1/0.1."""
+    wy, wu, wv = (float(t) for t in weights)
+    return (wy * s_y + wu * s_u + wv * s_v) / (wy + wu + wv)
+
+
+def temporal_pool(frame_scores, percentile: float = 10.0):
+    """Temporal pooling of frame scores (Section "Spatio-temporal Aggregation
+    of Quality Scores"): the temporal mean, the p-th percentile by linear
+    interpolation between order statistics (position h = p/100 (n-1) in the
+    sorted list), and the percentile-pooled mean with r_t = 1 taken over the
+    frames whose score is at or below that percentile (Section "Percentile
+    Pooling")."""
+    v = np.sort(_f64(frame_scores).ravel())
+    n = v.size
+    mean_ = float(v.sum() / n)
+    h = percentile / 100.0 * (n - 1)
+    lo = int(math.floor(h))
+    hi = min(lo + 1, n - 1)
+    pct = float(v[lo] + (h - lo) * (v[hi] - v[lo]))
+    low = v[v <= pct]
+    return mean_, pct, float(low.sum() / low.size)
