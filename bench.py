@@ -1,0 +1,279 @@
+"""Benchmark: 1080p MS-SSIM throughput (Mpx-pairs/s) on GB300.
+
+Workload (one "step"): MS-SSIM of 64 uint8 luma pairs of 1920x1080 (smooth
+noise references, block-quantised + noisy distortions), 5 scales, 11x11
+Gaussian sigma = 1.5, 2x2 average pyramid, exponents 0.0448/0.2856/0.3001/
+0.2363/0.1333, all through the C ABI (gbssim_msssim).  Inputs (265 MB) are
+larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbssim|reference]
+
+N > 1 runs under torchrun, one rank per GPU, each rank on its own 64 pairs
+(weak scaling, no data-path collective); rank 0 prints one JSON line.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_PAIRS, H, W = 64, 1080, 1920
+PX_PER_PAIR = H * W
+METRIC = "1080p MS-SSIM Mpx-pairs/s (% HBM roofline); SSIM-loss fwd+bwd Mpx/s"
+UNIT = "Mpx-pairs/s"
+WORKLOAD = "msssim_1080p_u8_x64"
+CONFIG = {"workload": WORKLOAD, "pairs_per_gpu": N_PAIRS, "height": H, "width": W, "dtype_in": "u8",
+          "scales": 5, "window": "gaussian11_sigma1.5", "l2": "inputs (265 MB) larger than L2, no flush"}
+# FP32 non-tensor peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz max SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# algorithmic FLOP per SSIM output: 5 moments x 2 separable passes x 11 taps x 2 + 3 products + ~17 formula
+FLOP_PER_OUTPUT = 240
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling in the background during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [t.strip() for t in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on a bounded sample (a few 1080p pairs per step)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2101_06354_gb300 import synth
+
+    sample = 4
+    x, y = synth.luma_pairs_u8(sample, H, W)
+    xs, ys = x.numpy(), y.numpy()
+    step = lambda: [oracle.msssim(xs[i], ys[i]) for i in range(sample)]
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t
+    value = sample * PX_PER_PAIR * args.steps / dt / 1e6
+    cores = oracle.num_threads()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(CONFIG, sample_pairs_per_step=sample), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d of the 64 1080p pairs per step, FP64 direct-sum oracle" % sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def cpu_baseline():
+    """Oracle throughput on a bounded sample (16 pairs), for the JSON line."""
+    import oracle
+    from paper_2101_06354_gb300 import synth
+
+    sample = 16
+    x, y = synth.luma_pairs_u8(sample, H, W)
+    xs, ys = x.numpy(), y.numpy()
+    t = time.perf_counter()
+    for i in range(sample):
+        oracle.msssim(xs[i], ys[i])
+    dt = time.perf_counter() - t
+    return {"value": sample * PX_PER_PAIR / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": "%d of the 64 1080p pairs, MS-SSIM, FP64 direct-sum oracle (%.1f s)"
+                                        % (sample, dt)}
+
+
+def run_gbssim(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2101_06354_gb300 import build
+
+    build.build()
+    from paper_2101_06354_gb300 import gbssim, synth
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    # rank r processes its own 64 pairs (seeds offset by rank)
+    x, y = synth.luma_pairs_u8(N_PAIRS, H, W, seed_ref=10 + 1000 * rank, seed_dist=100000 + 1000 * rank,
+                               device=dev)
+    px = gbssim.plane(x)
+    p = gbssim.make_params(exponents=gbssim.MSSSIM_EXPONENTS)
+    wsp = gbssim.workspace(px, p, gbssim.OP_MSSSIM, dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return gbssim.msssim(x, y, ws=wsp)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    def timed(fn, k):
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if ws > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = t.item()
+        return ms
+
+    with ClockSampler(local) as clk:
+        ms = timed(step, args.steps)
+    clocks = clk.summary()
+    value = ws * N_PAIRS * PX_PER_PAIR * args.steps / (ms / 1e3) / 1e6
+    ms_step = ms / args.steps
+    score = step()
+
+    # dominant kernel alone: the scale-0 11x11 Gaussian level kernel (same
+    # kernel, same 64 pairs, without the pyramid side output), CUDA events on
+    # the launching stream.
+    wss = gbssim.workspace(px, p, gbssim.OP_SSIM, dev)
+    ms_k = timed(lambda: gbssim.ssim(x, y, ws=wss), args.steps) / args.steps
+    outputs = N_PAIRS * (H - 10) * (W - 10)
+    achieved = FLOP_PER_OUTPUT * outputs / (ms_k / 1e3) / 1e12
+    hbm_peak, hbm_src = _peaks()
+    in_bytes = 2 * N_PAIRS * PX_PER_PAIR
+    hbm_frac = in_bytes / (ms_step / 1e3) / 1e9 / hbm_peak
+
+    # end to end: pinned host inputs, H2D copies + device->host score inside the timed region
+    xh = x.cpu().pin_memory()
+    yh = y.cpu().pin_memory()
+    for _ in range(2):
+        gbssim.msssim(xh, yh, ws=wsp)
+    ms_e2e = timed(lambda: gbssim.msssim(xh, yh, ws=wsp), max(2, args.steps // 2)) / max(2, args.steps // 2)
+    e2e = {"value": ws * N_PAIRS * PX_PER_PAIR / (ms_e2e / 1e3) / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": 8 * N_PAIRS}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(CONFIG, parallelism="dp%d" % ws if ws > 1 else "single"),
+                "gpu_launches": 6 * args.steps,
+                "e2e": e2e,
+                "hbm_frac": hbm_frac,
+                "roofline": {"bound": "alu", "kernel": "gauss11_kernel<uint8_t> (scale 0)",
+                             "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                             "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+                             "kernel_ms": ms_k, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src},
+                "clocks": clocks,
+                "score_mean": float(score.double().mean().item())}
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbssim", choices=["gbssim", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gbssim(args)
+
+
+if __name__ == "__main__":
+    main()

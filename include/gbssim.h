@@ -1,0 +1,177 @@
+/*
+ * gbssim.h -- C ABI of libgbssim.so, a GB300-native (sm_103a) implementation of
+ * the SSIM / MS-SSIM hot path of "A Hitchhiker's Guide to Structural
+ * Similarity" (arXiv 2101.06354).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers named *_out, `data`, `map`, `workspace`, `grad_y` are DEVICE
+ *    pointers owned by the caller.  Descriptor/parameter structs are HOST
+ *    memory read during the call only.  The library allocates nothing per call
+ *    (gbssim_batch_plan is the one exception and says so).
+ *  - Every function is asynchronous on `stream` (a cudaStream_t; NULL = the
+ *    legacy default stream): it validates its arguments on the host, enqueues
+ *    kernels and returns; results appear in device memory when the stream
+ *    reaches them.  Nothing synchronises.
+ *  - Return value: GBSSIM_OK (0) or a negative gbssim_status.  Argument errors
+ *    are detected before anything is enqueued, so a failed call has no effect.
+ *    GBSSIM_ERR_CUDA reports a launch error returned by the CUDA runtime.
+ *  - Images are "valid"-bordered: a k x k window W_ij spans rows i..i+k-1 and
+ *    columns j..j+k-1 (Background section) and is evaluated at i, j in
+ *    {0, s, 2s, ...} with i <= H-k, j <= W-k (Section "Effect of stride"), so
+ *    the quality map is OH x OW with OH = (H-k)/s + 1, OW = (W-k)/s + 1.
+ *  - Pooled scores are doubles, combined in a fixed order (deterministic:
+ *    identical inputs give bit-identical scores).
+ */
+#ifndef GBSSIM_H
+#define GBSSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBSSIM_VERSION 1
+#define GBSSIM_MAX_SCALES 8
+#define GBSSIM_MAX_K 63
+
+typedef enum gbssim_status {
+    GBSSIM_OK = 0,
+    GBSSIM_ERR_INVALID_ARG = -1,  /* null pointer, bad enum, stride < 1, ... */
+    GBSSIM_ERR_TOO_SMALL = -2,    /* an image (or pyramid level) is smaller than k */
+    GBSSIM_ERR_UNSUPPORTED = -3,  /* valid combination this build does not implement */
+    GBSSIM_ERR_CUDA = -4,         /* the CUDA runtime reported an error */
+    GBSSIM_ERR_DOMAIN = -5,       /* MS-SSIM product with a non-positive pooled term */
+    GBSSIM_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up */
+    GBSSIM_ERR_WORKSPACE = -7     /* workspace missing or smaller than required */
+} gbssim_status;
+
+typedef enum gbssim_dtype {
+    GBSSIM_U8 = 0,   /* 8-bit luminance, nominal range [0, 255] */
+    GBSSIM_F16 = 1,
+    GBSSIM_BF16 = 2,
+    GBSSIM_F32 = 3
+} gbssim_dtype;
+
+typedef enum gbssim_window {
+    GBSSIM_WIN_GAUSSIAN = 0,  /* w(m,n) = g(m) g(n), g(t) ~ exp(-(t-c)^2 / 2 sigma^2), sum 1 */
+    GBSSIM_WIN_BOX = 1        /* w(m,n) = 1/k^2 (integral-image path for uint8) */
+} gbssim_window;
+
+typedef enum gbssim_combine {
+    GBSSIM_COMBINE_PRODUCT = 0,  /* MS = prod_j m_j^beta_j */
+    GBSSIM_COMBINE_SUM = 1       /* MS = sum_j (beta_j / sum beta) m_j  (Scikit-Video "Sum") */
+} gbssim_combine;
+
+/* A batch of `count` equally sized images in device memory.  Image b, row r,
+ * column c is at element  b*image_stride + r*row_stride + c  of `data`
+ * (strides in ELEMENTS, not bytes). */
+typedef struct gbssim_plane {
+    const void *data;
+    int32_t dtype;          /* gbssim_dtype */
+    int32_t count;          /* >= 1 */
+    int64_t height;         /* H (rows) */
+    int64_t width;          /* W (columns) */
+    int64_t row_stride;     /* >= width */
+    int64_t image_stride;   /* >= height*row_stride when count > 1 */
+} gbssim_plane;
+
+/* The problem's knobs as the paper states them.  Fill with
+ * gbssim_params_default() and override fields. */
+typedef struct gbssim_params {
+    int32_t window;   /* gbssim_window */
+    int32_t k;        /* window size, 1..GBSSIM_MAX_K (Background: k x k window) */
+    double sigma;     /* Gaussian scale (recommended 1.5 with k = 11); ignored for box */
+    double K1, K2;    /* C1 = (K1 L)^2, C2 = (K2 L)^2  (Background section) */
+    double L;         /* dynamic range, 255 for 8-bit */
+    int32_t stride;   /* distance between evaluated windows, >= 1 (Section "Effect of stride") */
+    int32_t scales;   /* MS-SSIM scales, 1..GBSSIM_MAX_SCALES (5 in MS-SSIM) */
+    double exponents[GBSSIM_MAX_SCALES];  /* beta_j per scale, finest first */
+    int32_t combine;  /* gbssim_combine */
+    int32_t flags;    /* reserved, must be 0 */
+} gbssim_params;
+
+/* Operation codes for gbssim_workspace_size. */
+typedef enum gbssim_op {
+    GBSSIM_OP_SSIM = 0,
+    GBSSIM_OP_MSSSIM = 1,
+    GBSSIM_OP_BACKWARD = 2,
+    GBSSIM_OP_BACKWARD_MS = 3,
+    GBSSIM_OP_POOL = 4
+} gbssim_op;
+
+/* Pooling kinds for gbssim_ssim_pool. */
+typedef enum gbssim_pool_kind {
+    GBSSIM_POOL_MEAN = 0   /* mean of the map (Background section, MSSIM) */
+} gbssim_pool_kind;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *gbssim_status_string(int status);
+
+/* GBSSIM_VERSION of the loaded library. */
+int gbssim_version(void);
+
+/* Recommended defaults (Background section): Gaussian window k = 11,
+ * sigma = 1.5, K1 = 0.01, K2 = 0.03, L = 255, stride 1; 5 MS-SSIM scales with
+ * exponents 0.0448, 0.2856, 0.3001, 0.2363, 0.1333, product combination. */
+void gbssim_params_default(gbssim_params *p);
+
+/* Bytes of device workspace that `op` needs for planes shaped like `x` with
+ * parameters `p` (written to *bytes).  The workspace is scratch owned by the
+ * caller; it may be reused across calls that do not overlap on the GPU. */
+int gbssim_workspace_size(const gbssim_plane *x, const gbssim_params *p, int op, size_t *bytes);
+
+/* SSIM index map and mean-pooled score (MSSIM) of each of the x.count pairs.
+ * Eqs. local_means..local_corr (window statistics), lum_term and the
+ * C3 = C2/2 contrast-structure term (Q = l * cs), mean pooling (Background
+ * section); box windows on uint8 use the integral-image formulation
+ * (Eqs. integral_image_start..corr_from_sum) with exact integer sums.
+ *   x, y       : reference and distorted batches, identical shape and dtype.
+ *   map_out    : nullable; receives Q as float, image b at
+ *                map_out + b*map_image_stride, rows map_ld floats apart
+ *                (map_ld >= OW, map_image_stride >= OH*map_ld).
+ *   mean_out   : nullable; receives x.count doubles (MSSIM per pair).
+ *   workspace  : device scratch of at least gbssim_workspace_size(GBSSIM_OP_SSIM).
+ */
+int gbssim_ssim_map(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
+                    float *map_out, int64_t map_ld, int64_t map_image_stride, double *mean_out,
+                    void *workspace, size_t workspace_bytes, void *stream);
+
+/* Pool `count` float maps (h x w, rows `ld` floats apart, images
+ * `image_stride` floats apart) into one double each.  kind = GBSSIM_POOL_MEAN
+ * is the Background section's mean pooling; `args` is unused for it (may be
+ * NULL).  Needs gbssim_workspace_size(GBSSIM_OP_POOL) bytes of workspace
+ * computed for a plane of the map's shape. */
+int gbssim_ssim_pool(const float *map, int64_t h, int64_t w, int64_t ld, int32_t count,
+                     int64_t image_stride, int32_t kind, const double *args, double *out,
+                     void *workspace, size_t workspace_bytes, void *stream);
+
+/* MS-SSIM of each pair (Introduction; Section "Salient Features of SSIM and
+ * MS-SSIM Implementations"): scale 1 is the input, scale j+1 the 2x2 average
+ * of scale j (floor size); the contrast-structure term is mean-pooled at every
+ * scale and the luminance term only at the coarsest, m_j = mean cs_j (j < S),
+ * m_S = mean Q_S; score = prod m_j^beta_j (or the normalised sum).
+ *   score_out     : x.count doubles.  A product with a non-positive m_j under a
+ *                   non-integer exponent yields NaN for that pair (the call
+ *                   still returns GBSSIM_OK; the value is checked on device).
+ *   per_scale_out : nullable; x.count * scales * 2 doubles, (mean cs_j, mean Q_j)
+ *                   for each scale j, finest first.
+ * Every pyramid level must be at least k x k (else GBSSIM_ERR_TOO_SMALL). */
+int gbssim_msssim(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
+                  double *score_out, double *per_scale_out, void *workspace,
+                  size_t workspace_bytes, void *stream);
+
+/* Exact integer window sums of a uint8 pair, the quantities the paper's
+ * integral images produce (Eqs. integral_image_start..integral_image_end):
+ * for every window position, 5 int64 values S1_x, S1_y, S2_x, S2_y, S_xy in
+ * row-major map order, image b at sums_out + 5*b*OH*OW.  k <= GBSSIM_MAX_K. */
+int gbssim_window_sums(const gbssim_plane *x, const gbssim_plane *y, int32_t k, int32_t stride,
+                       int64_t *sums_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBSSIM_H */

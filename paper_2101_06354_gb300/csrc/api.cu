@@ -1,0 +1,390 @@
+// api.cu -- the extern "C" boundary of libgbssim.so (declared in
+// include/gbssim.h): argument validation, workspace layout and kernel
+// dispatch.  No function here allocates device memory or synchronises.
+#include <math.h>
+#include <string.h>
+
+#include "common.cuh"
+
+using namespace gbssim;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+const double kDefaultExps[5] = {0.0448, 0.2856, 0.3001, 0.2363, 0.1333};
+
+int check_plane(const gbssim_plane *p) {
+    if (!p || !p->data) return GBSSIM_ERR_INVALID_ARG;
+    if (p->dtype < GBSSIM_U8 || p->dtype > GBSSIM_F32) return GBSSIM_ERR_INVALID_ARG;
+    if (p->count < 1 || p->height < 1 || p->width < 1) return GBSSIM_ERR_INVALID_ARG;
+    if (p->row_stride < p->width) return GBSSIM_ERR_INVALID_ARG;
+    if (p->count > 1 && p->image_stride < p->height * p->row_stride) return GBSSIM_ERR_INVALID_ARG;
+    if (p->count > 65535) return GBSSIM_ERR_UNSUPPORTED;
+    return GBSSIM_OK;
+}
+
+int check_pair(const gbssim_plane *x, const gbssim_plane *y) {
+    int rc = check_plane(x);
+    if (rc) return rc;
+    rc = check_plane(y);
+    if (rc) return rc;
+    if (x->dtype != y->dtype || x->count != y->count || x->height != y->height ||
+        x->width != y->width || x->row_stride != y->row_stride ||
+        (x->count > 1 && x->image_stride != y->image_stride))
+        return GBSSIM_ERR_INVALID_ARG;
+    return GBSSIM_OK;
+}
+
+int check_params(const gbssim_params *p) {
+    if (!p) return GBSSIM_ERR_INVALID_ARG;
+    if (p->window != GBSSIM_WIN_GAUSSIAN && p->window != GBSSIM_WIN_BOX) return GBSSIM_ERR_INVALID_ARG;
+    if (p->k < 1 || p->k > GBSSIM_MAX_K) return GBSSIM_ERR_INVALID_ARG;
+    if (p->window == GBSSIM_WIN_GAUSSIAN && !(p->sigma > 0.0 && isfinite(p->sigma)))
+        return GBSSIM_ERR_INVALID_ARG;
+    if (!(isfinite(p->K1) && isfinite(p->K2) && p->K1 >= 0.0 && p->K2 >= 0.0)) return GBSSIM_ERR_INVALID_ARG;
+    if (!(p->L > 0.0 && isfinite(p->L))) return GBSSIM_ERR_INVALID_ARG;
+    if (p->stride < 1) return GBSSIM_ERR_INVALID_ARG;
+    if (p->scales < 1 || p->scales > GBSSIM_MAX_SCALES) return GBSSIM_ERR_INVALID_ARG;
+    for (int j = 0; j < p->scales; ++j)
+        if (!isfinite(p->exponents[j])) return GBSSIM_ERR_INVALID_ARG;
+    if (p->combine != GBSSIM_COMBINE_PRODUCT && p->combine != GBSSIM_COMBINE_SUM) return GBSSIM_ERR_INVALID_ARG;
+    if (p->flags != 0) return GBSSIM_ERR_INVALID_ARG;
+    return GBSSIM_OK;
+}
+
+void make_taps(const gbssim_params *p, float *g) {
+    const int k = p->k;
+    if (p->window == GBSSIM_WIN_BOX) {
+        for (int t = 0; t < k; ++t) g[t] = (float)(1.0 / k);
+        return;
+    }
+    double v[GBSSIM_MAX_K], z = 0.0, c = 0.5 * (k - 1);
+    for (int t = 0; t < k; ++t) {
+        v[t] = exp(-((t - c) * (t - c)) / (2.0 * p->sigma * p->sigma));
+        z += v[t];
+    }
+    for (int t = 0; t < k; ++t) g[t] = (float)(v[t] / z);
+}
+
+SsimConst make_const(const gbssim_params *p) {
+    const double c1 = (p->K1 * p->L) * (p->K1 * p->L), c2 = (p->K2 * p->L) * (p->K2 * p->L);
+    return SsimConst{(float)c1, (float)c2};
+}
+
+ImgDesc desc_of(const gbssim_plane *p) {
+    return ImgDesc{p->data, p->height, p->width, p->row_stride,
+                   p->count > 1 ? p->image_stride : p->height * p->row_stride};
+}
+
+enum Path { PATH_GAUSS11, PATH_GENERIC, PATH_BOX_U8 };
+
+Path pick_path(int dtype, const gbssim_params *p) {
+    if (p->window == GBSSIM_WIN_BOX && dtype == GBSSIM_U8) return PATH_BOX_U8;
+    if (p->k == 11 && p->stride == 1) return PATH_GAUSS11;
+    return PATH_GENERIC;
+}
+
+int pick_seg_rows(int64_t H, int64_t W, int count) {
+    int strips, segs;
+    int seg = 256;
+    while (seg > 32) {
+        gauss11_items(H, W, seg, &strips, &segs);
+        if ((int64_t)strips * segs * count >= 4 * 456) break;
+        seg -= 32;
+    }
+    return seg;
+}
+
+// Items (CTAs producing one partial each) per image for one level.
+int level_items(Path path, int64_t H, int64_t W, int count, const gbssim_params *p, int *seg_rows) {
+    const int64_t OH = out_dim(H, p->k, p->stride), OW = out_dim(W, p->k, p->stride);
+    switch (path) {
+    case PATH_GAUSS11: {
+        int strips, segs;
+        *seg_rows = pick_seg_rows(H, W, count);
+        return gauss11_items(H, W, *seg_rows, &strips, &segs);
+    }
+    case PATH_BOX_U8: return box_items_ks(OH, OW, p->k, p->stride);
+    default: return generic_items(OH, OW);
+    }
+}
+
+struct Level {
+    int64_t H, W;
+    Path path;
+    int items, seg_rows;
+    size_t part_off, plane_off;  // plane_off: x then y planes of this level (j >= 1)
+};
+
+struct MsPlan {
+    Level lv[GBSSIM_MAX_SCALES];
+    size_t bytes;
+};
+
+int plan_levels(const gbssim_plane *x, const gbssim_params *p, int scales, MsPlan *P) {
+    size_t off = 0;
+    int64_t H = x->height, W = x->width;
+    for (int j = 0; j < scales; ++j) {
+        if (H < p->k || W < p->k) return GBSSIM_ERR_TOO_SMALL;
+        Level &L = P->lv[j];
+        L.H = H;
+        L.W = W;
+        const int dtype = j == 0 ? x->dtype : GBSSIM_F32;
+        L.path = pick_path(dtype, p);
+        L.seg_rows = 0;
+        L.items = level_items(L.path, H, W, x->count, p, &L.seg_rows);
+        L.part_off = off;
+        off = align_up(off + sizeof(double2) * (size_t)L.items * x->count);
+        if (j > 0) {
+            L.plane_off = off;
+            off = align_up(off + 2 * sizeof(float) * (size_t)H * W * x->count);
+        } else {
+            L.plane_off = 0;
+        }
+        H >>= 1;
+        W >>= 1;
+    }
+    P->bytes = off;
+    return GBSSIM_OK;
+}
+
+// Launch one SSIM level: `in_x/in_y` describe the level's images (dtype),
+// partials/map as given; ds_x/ds_y (nullable) receive the next level.
+cudaError_t run_level(const Level &L, const ImgDesc &dx, const ImgDesc &dy, int dtype, int count,
+                      const gbssim_params *p, float *map, int64_t map_ld, int64_t map_is,
+                      double2 *partials, float *ds_x, float *ds_y, cudaStream_t st) {
+    const SsimConst cc = make_const(p);
+    cudaError_t e = cudaSuccess;
+    bool fused_ds = false;
+    if (L.path == PATH_GAUSS11) {
+        GaussLaunch G;
+        G.x = dx;
+        G.y = dy;
+        G.dtype = dtype;
+        G.count = count;
+        G.map = map;
+        G.map_ld = map_ld;
+        G.map_is = map_is;
+        G.ds_x = ds_x;
+        G.ds_y = ds_y;
+        G.partials = partials;
+        make_taps(p, G.taps.g);
+        G.c = cc;
+        G.seg_rows = L.seg_rows;
+        e = launch_gauss11(G, st);
+        fused_ds = true;
+    } else if (L.path == PATH_BOX_U8) {
+        BoxLaunch B;
+        B.x = dx;
+        B.y = dy;
+        B.count = count;
+        B.k = p->k;
+        B.stride = p->stride;
+        B.map = map;
+        B.map_ld = map_ld;
+        B.map_is = map_is;
+        B.partials = partials;
+        B.sums_out = nullptr;
+        const double k4 = pow((double)p->k, 4.0);
+        const double c1 = (p->K1 * p->L) * (p->K1 * p->L), c2 = (p->K2 * p->L) * (p->K2 * p->L);
+        B.C1k4 = (float)(c1 * k4);
+        B.C2k4 = (float)(c2 * k4);
+        e = launch_box_u8(B, st);
+    } else {
+        GenericLaunch G;
+        G.x = dx;
+        G.y = dy;
+        G.dtype = dtype;
+        G.count = count;
+        G.k = p->k;
+        G.stride = p->stride;
+        G.map = map;
+        G.map_ld = map_ld;
+        G.map_is = map_is;
+        G.partials = partials;
+        memset(G.taps.g, 0, sizeof G.taps.g);
+        make_taps(p, G.taps.g);
+        G.c = cc;
+        e = launch_generic(G, st);
+    }
+    if (e != cudaSuccess) return e;
+    if (ds_x && !fused_ds) {
+        e = launch_downsample(dx, dtype, count, ds_x, st);
+        if (e != cudaSuccess) return e;
+        e = launch_downsample(dy, dtype, count, ds_y, st);
+    }
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gbssim_status_string(int status) {
+    switch (status) {
+    case GBSSIM_OK: return "ok";
+    case GBSSIM_ERR_INVALID_ARG: return "invalid argument";
+    case GBSSIM_ERR_TOO_SMALL: return "image (or pyramid level) smaller than the window";
+    case GBSSIM_ERR_UNSUPPORTED: return "unsupported combination";
+    case GBSSIM_ERR_CUDA: return "CUDA runtime error";
+    case GBSSIM_ERR_DOMAIN: return "non-positive pooled term under a fractional exponent";
+    case GBSSIM_ERR_TIMEOUT: return "bounded device wait timed out";
+    case GBSSIM_ERR_WORKSPACE: return "workspace missing or too small";
+    }
+    return "unknown status";
+}
+
+int gbssim_version(void) { return GBSSIM_VERSION; }
+
+void gbssim_params_default(gbssim_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->window = GBSSIM_WIN_GAUSSIAN;
+    p->k = 11;
+    p->sigma = 1.5;
+    p->K1 = 0.01;
+    p->K2 = 0.03;
+    p->L = 255.0;
+    p->stride = 1;
+    p->scales = 5;
+    for (int j = 0; j < 5; ++j) p->exponents[j] = kDefaultExps[j];
+    p->combine = GBSSIM_COMBINE_PRODUCT;
+    p->flags = 0;
+}
+
+int gbssim_workspace_size(const gbssim_plane *x, const gbssim_params *p, int op, size_t *bytes) {
+    if (!bytes) return GBSSIM_ERR_INVALID_ARG;
+    int rc = check_plane(x);
+    if (rc) return rc;
+    if (op == GBSSIM_OP_POOL) {
+        *bytes = align_up(sizeof(double2) * (size_t)pool_items(x->height, x->width) * x->count);
+        return GBSSIM_OK;
+    }
+    rc = check_params(p);
+    if (rc) return rc;
+    MsPlan P;
+    if (op == GBSSIM_OP_SSIM) {
+        rc = plan_levels(x, p, 1, &P);
+    } else if (op == GBSSIM_OP_MSSSIM) {
+        rc = plan_levels(x, p, p->scales, &P);
+    } else {
+        return GBSSIM_ERR_INVALID_ARG;
+    }
+    if (rc) return rc;
+    *bytes = P.bytes;
+    return GBSSIM_OK;
+}
+
+int gbssim_ssim_map(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
+                    float *map_out, int64_t map_ld, int64_t map_image_stride, double *mean_out,
+                    void *workspace, size_t workspace_bytes, void *stream) {
+    int rc = check_pair(x, y);
+    if (rc) return rc;
+    rc = check_params(p);
+    if (rc) return rc;
+    MsPlan P;
+    rc = plan_levels(x, p, 1, &P);
+    if (rc) return rc;
+    const int64_t OH = out_dim(x->height, p->k, p->stride), OW = out_dim(x->width, p->k, p->stride);
+    if (map_out && (map_ld < OW || (x->count > 1 && map_image_stride < OH * map_ld)))
+        return GBSSIM_ERR_INVALID_ARG;
+    if (!map_out && !mean_out) return GBSSIM_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < P.bytes) return GBSSIM_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    double2 *part = (double2 *)((char *)workspace + P.lv[0].part_off);
+    cudaError_t e = run_level(P.lv[0], desc_of(x), desc_of(y), x->dtype, x->count, p, map_out, map_ld,
+                              map_image_stride, part, nullptr, nullptr, st);
+    if (e != cudaSuccess) return GBSSIM_ERR_CUDA;
+    if (mean_out) {
+        e = launch_finalize_ssim(part, x->count, P.lv[0].items, 1.0 / ((double)OH * (double)OW), mean_out, st);
+        if (e != cudaSuccess) return GBSSIM_ERR_CUDA;
+    }
+    return GBSSIM_OK;
+}
+
+int gbssim_ssim_pool(const float *map, int64_t h, int64_t w, int64_t ld, int32_t count,
+                     int64_t image_stride, int32_t kind, const double *args, double *out,
+                     void *workspace, size_t workspace_bytes, void *stream) {
+    (void)args;
+    if (!map || !out || h < 1 || w < 1 || ld < w || count < 1 || count > 65535) return GBSSIM_ERR_INVALID_ARG;
+    if (count > 1 && image_stride < h * ld) return GBSSIM_ERR_INVALID_ARG;
+    if (kind != GBSSIM_POOL_MEAN) return GBSSIM_ERR_UNSUPPORTED;
+    const size_t need = align_up(sizeof(double2) * (size_t)pool_items(h, w) * count);
+    if (!workspace || workspace_bytes < need) return GBSSIM_ERR_WORKSPACE;
+    cudaError_t e = launch_pool_mean(map, h, w, ld, count, count > 1 ? image_stride : h * ld,
+                                     (double2 *)workspace, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
+}
+
+int gbssim_msssim(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
+                  double *score_out, double *per_scale_out, void *workspace,
+                  size_t workspace_bytes, void *stream) {
+    int rc = check_pair(x, y);
+    if (rc) return rc;
+    rc = check_params(p);
+    if (rc) return rc;
+    if (!score_out) return GBSSIM_ERR_INVALID_ARG;
+    const int S = p->scales;
+    MsPlan P;
+    rc = plan_levels(x, p, S, &P);
+    if (rc) return rc;
+    if (!workspace || workspace_bytes < P.bytes) return GBSSIM_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)workspace;
+    const int n = x->count;
+    ImgDesc dx = desc_of(x), dy = desc_of(y);
+    int dtype = x->dtype;
+    MsFinalize F;
+    memset(&F, 0, sizeof F);
+    for (int j = 0; j < S; ++j) {
+        const Level &L = P.lv[j];
+        float *ds_x = nullptr, *ds_y = nullptr;
+        if (j + 1 < S) {
+            const Level &N = P.lv[j + 1];
+            ds_x = (float *)(ws + N.plane_off);
+            ds_y = ds_x + (size_t)N.H * N.W * n;
+        }
+        double2 *part = (double2 *)(ws + L.part_off);
+        cudaError_t e = run_level(L, dx, dy, dtype, n, p, nullptr, 0, 0, part, ds_x, ds_y, st);
+        if (e != cudaSuccess) return GBSSIM_ERR_CUDA;
+        const int64_t OH = out_dim(L.H, p->k, p->stride), OW = out_dim(L.W, p->k, p->stride);
+        F.lv[j].partials = part;
+        F.lv[j].items_per_image = L.items;
+        F.lv[j].inv_n = 1.0 / ((double)OH * (double)OW);
+        F.exps[j] = p->exponents[j];
+        if (j + 1 < S) {
+            const Level &N = P.lv[j + 1];
+            dx = ImgDesc{ds_x, N.H, N.W, N.W, N.H * N.W};
+            dy = ImgDesc{ds_y, N.H, N.W, N.W, N.H * N.W};
+            dtype = GBSSIM_F32;
+        }
+    }
+    F.scales = S;
+    F.count = n;
+    F.combine = p->combine;
+    F.score_out = score_out;
+    F.per_scale_out = per_scale_out;
+    return launch_finalize_msssim(F, st) == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
+}
+
+int gbssim_window_sums(const gbssim_plane *x, const gbssim_plane *y, int32_t k, int32_t stride,
+                       int64_t *sums_out, void *stream) {
+    int rc = check_pair(x, y);
+    if (rc) return rc;
+    if (x->dtype != GBSSIM_U8) return GBSSIM_ERR_UNSUPPORTED;
+    if (!sums_out || k < 1 || k > GBSSIM_MAX_K || stride < 1) return GBSSIM_ERR_INVALID_ARG;
+    if (x->height < k || x->width < k) return GBSSIM_ERR_TOO_SMALL;
+    BoxLaunch B;
+    memset(&B, 0, sizeof B);
+    B.x = desc_of(x);
+    B.y = desc_of(y);
+    B.count = x->count;
+    B.k = k;
+    B.stride = stride;
+    B.sums_out = sums_out;
+    return launch_box_u8(B, (cudaStream_t)stream) == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,266 @@
+// k_box.cu -- rectangular-window SSIM for 8-bit images with exact integer
+// window sums (Section "Performance-Efficiency Tradeoffs" of arXiv 2101.06354,
+// Eqs. integral_image_start .. corr_from_sum).
+//
+// The five local sums S1_x, S1_y, S2_x, S2_y, S_xy of every k x k window are
+// formed exactly in integers.  Multiplying the statistics of
+// Eqs. mean_from_sum .. corr_from_sum through by k^4 gives integer numerators,
+//   l  = (2 S1x S1y + C1 k^4) / (S1x^2 + S1y^2 + C1 k^4)
+//   cs = (2 (k^2 Sxy - S1x S1y) + C2 k^4) / ((k^2 S2x - S1x^2) + (k^2 S2y - S1y^2) + C2 k^4),
+// whose integer parts are exact in int64 and are rounded to fp32 once each,
+// so Q carries only a few fp32 roundings.
+//
+// Two tile schemes:
+//  * block path (stride s a multiple of 4 and k a multiple of s): sums over
+//    the non-overlapping s x s blocks, four pixels per dp4a instruction,
+//    then each window adds (k/s)^2 block sums.  Every input byte is read
+//    once from HBM; this is the HBM-bound configuration (8 x 8 at stride 4).
+//  * integral-image path (any k <= 63, any stride): five summed-area tables
+//    of a <= 64 x 64 input tile in shared memory (int32, zero first row and
+//    column) and the paper's four-corner formula per window.
+#include "common.cuh"
+
+namespace gbssim {
+namespace {
+
+constexpr int NT = 256;
+
+struct BoxOut {
+    int64_t s1x, s1y, s2x, s2y, sxy;
+};
+
+__device__ __forceinline__ void box_formula(const BoxOut &v, int k, float C1k4, float C2k4, float &q,
+                                            float &cs) {
+    const int64_t kk = (int64_t)k * k;
+    const int64_t P = 2 * v.s1x * v.s1y;
+    const int64_t Q1 = v.s1x * v.s1x + v.s1y * v.s1y;
+    const int64_t Nxy = kk * v.sxy - v.s1x * v.s1y;
+    const int64_t T2 = (kk * v.s2x - v.s1x * v.s1x) + (kk * v.s2y - v.s1y * v.s1y);
+    const float A1 = __ll2float_rn(P) + C1k4, B1 = __ll2float_rn(Q1) + C1k4;
+    const float A2 = fmaf(2.f, __ll2float_rn(Nxy), C2k4), B2 = __ll2float_rn(T2) + C2k4;
+    cs = __fdividef(A2, B2);
+    q = __fdividef(A1, B1) * cs;
+}
+
+// ------------------------------------------------------------------ block path
+
+constexpr int BW = 32, BH = 16;  // blocks per CTA tile
+
+__global__ void __launch_bounds__(NT) box_block_kernel(const BoxLaunch L, int tiles_x, int tiles_y,
+                                                       int aligned4) {
+    __shared__ unsigned Bs[5][BH][BW + 1];
+    __shared__ double red[2 * NT / 32];
+    const int s = L.stride, m = L.k / L.stride, wps = s >> 2;
+    const int tow = BW - m + 1, toh = BH - m + 1;
+    const int img = blockIdx.z;
+    const int64_t H = L.x.H, W = L.x.W, rs = L.x.row_stride;
+    const int64_t OH = out_dim(H, L.k, s), OW = out_dim(W, L.k, s);
+    const int64_t a0 = (int64_t)blockIdx.y * toh, b0 = (int64_t)blockIdx.x * tow;
+    const uint8_t *xb = static_cast<const uint8_t *>(L.x.data) + img * L.x.image_stride;
+    const uint8_t *yb = static_cast<const uint8_t *>(L.y.data) + img * L.y.image_stride;
+
+    for (int t = threadIdx.x; t < BW * BH; t += NT) {
+        const int bi = t / BW, bj = t - bi * BW;
+        const int64_t r0 = (a0 + bi) * s, c0 = (b0 + bj) * s;
+        unsigned sx = 0, sy = 0, sxx = 0, syy = 0, sxy = 0;
+        if (r0 + s <= H && c0 + s <= W) {  // partial blocks feed no valid window
+            for (int r = 0; r < s; ++r) {
+                const uint8_t *px = xb + (r0 + r) * rs + c0, *py = yb + (r0 + r) * rs + c0;
+                for (int w = 0; w < wps; ++w) {
+                    unsigned wx, wy;
+                    if (aligned4) {
+                        wx = __ldg(reinterpret_cast<const unsigned *>(px) + w);
+                        wy = __ldg(reinterpret_cast<const unsigned *>(py) + w);
+                    } else {
+                        wx = wy = 0;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            wx |= (unsigned)__ldg(px + 4 * w + u) << (8 * u);
+                            wy |= (unsigned)__ldg(py + 4 * w + u) << (8 * u);
+                        }
+                    }
+                    sx = __dp4a(wx, 0x01010101u, sx);
+                    sy = __dp4a(wy, 0x01010101u, sy);
+                    sxx = __dp4a(wx, wx, sxx);
+                    syy = __dp4a(wy, wy, syy);
+                    sxy = __dp4a(wx, wy, sxy);
+                }
+            }
+        }
+        Bs[0][bi][bj] = sx;
+        Bs[1][bi][bj] = sy;
+        Bs[2][bi][bj] = sxx;
+        Bs[3][bi][bj] = syy;
+        Bs[4][bi][bj] = sxy;
+    }
+    __syncthreads();
+
+    float accQ = 0.f, accCS = 0.f;
+    for (int t = threadIdx.x; t < tow * toh; t += NT) {
+        const int oi = t / tow, oj = t - oi * tow;
+        const int64_t a = a0 + oi, b = b0 + oj;
+        if (a >= OH || b >= OW) continue;
+        int64_t acc[5] = {0, 0, 0, 0, 0};
+        for (int u = 0; u < m; ++u)
+            for (int v = 0; v < m; ++v)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) acc[q] += Bs[q][oi + u][oj + v];
+        BoxOut o{acc[0], acc[1], acc[2], acc[3], acc[4]};
+        if (L.sums_out) {
+            int64_t *dst = L.sums_out + 5 * (img * OH * OW + a * OW + b);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) dst[q] = acc[q];
+            continue;
+        }
+        float q, cs;
+        box_formula(o, L.k, L.C1k4, L.C2k4, q, cs);
+        accQ += q;
+        accCS += cs;
+        if (L.map) L.map[img * L.map_is + a * L.map_ld + b] = q;
+    }
+    if (L.partials) {
+        double da = accQ, db = accCS;
+        block_sum2(da, db, red);
+        if (threadIdx.x == 0)
+            L.partials[((int64_t)img * tiles_y + blockIdx.y) * tiles_x + blockIdx.x] = make_double2(da, db);
+    }
+}
+
+// ------------------------------------------------------------------ integral-image path
+
+constexpr int RMAX = 64;             // input tile rows / columns (max)
+constexpr int SP = RMAX + 1;         // SAT pitch (first row/column are zero)
+
+struct SatSmem {
+    int sat[5][SP][SP + 1];
+    double red[2 * NT / 32];
+};
+
+__host__ __device__ inline int sat_tile_outputs(int k, int s) {
+    return k > RMAX ? 0 : (RMAX - k) / s + 1;
+}
+
+__global__ void __launch_bounds__(NT) box_sat_kernel(const BoxLaunch L, int tiles_x, int tiles_y) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SatSmem &S = *reinterpret_cast<SatSmem *>(smem_raw);
+    const int k = L.k, s = L.stride;
+    const int to = sat_tile_outputs(k, s);
+    const int img = blockIdx.z;
+    const int64_t H = L.x.H, W = L.x.W, rs = L.x.row_stride;
+    const int64_t OH = out_dim(H, k, s), OW = out_dim(W, k, s);
+    const int64_t a0 = (int64_t)blockIdx.y * to, b0 = (int64_t)blockIdx.x * to;
+    const int64_t r0 = a0 * s, c0 = b0 * s;
+    const int R = (int)min((int64_t)(to - 1) * s + k, H - r0);
+    const int C = (int)min((int64_t)(to - 1) * s + k, W - c0);
+    const uint8_t *xb = static_cast<const uint8_t *>(L.x.data) + img * L.x.image_stride;
+    const uint8_t *yb = static_cast<const uint8_t *>(L.y.data) + img * L.y.image_stride;
+
+    // products at [r+1][c+1]; zero first row and column
+    for (int t = threadIdx.x; t < (R + 1) * (C + 1); t += NT) {
+        const int r = t / (C + 1), c = t - r * (C + 1);
+        int v[5] = {0, 0, 0, 0, 0};
+        if (r > 0 && c > 0) {
+            const int p = __ldg(xb + (r0 + r - 1) * rs + c0 + c - 1);
+            const int q = __ldg(yb + (r0 + r - 1) * rs + c0 + c - 1);
+            v[0] = p; v[1] = q; v[2] = p * p; v[3] = q * q; v[4] = p * q;
+        }
+#pragma unroll
+        for (int u = 0; u < 5; ++u) S.sat[u][r][c] = v[u];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 5 * R; t += NT) {  // row prefix sums
+        const int u = t / R, r = 1 + t - u * R;
+        int acc = 0;
+        for (int c = 1; c <= C; ++c) S.sat[u][r][c] = (acc += S.sat[u][r][c]);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 5 * C; t += NT) {  // column prefix sums
+        const int u = t / C, c = 1 + t - u * C;
+        int acc = 0;
+        for (int r = 1; r <= R; ++r) S.sat[u][r][c] = (acc += S.sat[u][r][c]);
+    }
+    __syncthreads();
+
+    float accQ = 0.f, accCS = 0.f;
+    for (int t = threadIdx.x; t < to * to; t += NT) {
+        const int oi = t / to, oj = t - oi * to;
+        const int64_t a = a0 + oi, b = b0 + oj;
+        if (a >= OH || b >= OW) continue;
+        // 1-based top-left (i, j) = (oi*s + 1, oj*s + 1) inside the tile:
+        // S = I(i+k-1, j+k-1) + I(i-1, j-1) - I(i+k-1, j-1) - I(i-1, j+k-1)
+        const int i = oi * s + 1, j = oj * s + 1;
+        int64_t acc[5];
+#pragma unroll
+        for (int u = 0; u < 5; ++u)
+            acc[u] = (int64_t)S.sat[u][i + k - 1][j + k - 1] + S.sat[u][i - 1][j - 1] -
+                     S.sat[u][i + k - 1][j - 1] - S.sat[u][i - 1][j + k - 1];
+        if (L.sums_out) {
+            int64_t *dst = L.sums_out + 5 * (img * OH * OW + a * OW + b);
+#pragma unroll
+            for (int u = 0; u < 5; ++u) dst[u] = acc[u];
+            continue;
+        }
+        BoxOut o{acc[0], acc[1], acc[2], acc[3], acc[4]};
+        float q, cs;
+        box_formula(o, k, L.C1k4, L.C2k4, q, cs);
+        accQ += q;
+        accCS += cs;
+        if (L.map) L.map[img * L.map_is + a * L.map_ld + b] = q;
+    }
+    if (L.partials) {
+        double da = accQ, db = accCS;
+        block_sum2(da, db, S.red);
+        if (threadIdx.x == 0)
+            L.partials[((int64_t)img * tiles_y + blockIdx.y) * tiles_x + blockIdx.x] = make_double2(da, db);
+    }
+}
+
+bool use_block_path(int k, int s) { return s % 4 == 0 && k % s == 0 && k <= 16; }
+
+void box_tiles(int64_t OH, int64_t OW, int k, int s, int *tx, int *ty) {
+    if (use_block_path(k, s)) {
+        const int m = k / s;
+        const int tow = BW - m + 1, toh = BH - m + 1;
+        *tx = (int)((OW + tow - 1) / tow);
+        *ty = (int)((OH + toh - 1) / toh);
+    } else {
+        const int to = sat_tile_outputs(k, s);
+        *tx = (int)((OW + to - 1) / to);
+        *ty = (int)((OH + to - 1) / to);
+    }
+}
+
+}  // namespace
+
+int box_items_ks(int64_t OH, int64_t OW, int k, int s) {
+    int tx, ty;
+    box_tiles(OH, OW, k, s, &tx, &ty);
+    return tx * ty;
+}
+
+cudaError_t launch_box_u8(const BoxLaunch &L, cudaStream_t st) {
+    const int64_t OH = out_dim(L.x.H, L.k, L.stride), OW = out_dim(L.x.W, L.k, L.stride);
+    int tx, ty;
+    box_tiles(OH, OW, L.k, L.stride, &tx, &ty);
+    dim3 grid(tx, ty, L.count);
+    if (use_block_path(L.k, L.stride)) {
+        const uintptr_t bx = (uintptr_t)L.x.data, by = (uintptr_t)L.y.data;
+        const int aligned4 = (bx % 4 == 0) && (by % 4 == 0) && (L.x.row_stride % 4 == 0) &&
+                             (L.y.row_stride % 4 == 0) && (L.x.image_stride % 4 == 0) &&
+                             (L.y.image_stride % 4 == 0);
+        box_block_kernel<<<grid, NT, 0, st>>>(L, tx, ty, aligned4);
+    } else {
+        static bool attr_set = false;
+        const size_t smem = sizeof(SatSmem);
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(box_sat_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        box_sat_kernel<<<grid, NT, smem, st>>>(L, tx, ty);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gbssim

@@ -1,0 +1,148 @@
+// k_pool.cu -- pooling, pyramid and finalisation kernels.
+//
+//  * finalize_ssim / finalize_msssim: one CTA per image adds the per-item
+//    partial sums of the SSIM kernels in a fixed order in fp64, so scores are
+//    bit-reproducible, then forms MSSIM (mean pooling, Background section) or
+//    MS-SSIM (product prod_j m_j^beta_j, or the normalised sum, with
+//    m_j = mean cs_j below the coarsest scale and mean Q at the coarsest).
+//  * downsample: dyadic 2x2 average pooling with floor size (the MS-SSIM
+//    implementations of Daala, Scikit-Video and Tensorflow) for the paths
+//    that do not fuse it into the level kernel.
+//  * pool_mean: mean of a stored float map (gbssim_ssim_pool).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace gbssim {
+namespace {
+
+constexpr int NT = 256;
+
+__global__ void __launch_bounds__(NT) finalize_ssim_kernel(const double2 *partials, int items,
+                                                           double inv_n, double *mean_out) {
+    __shared__ double red[2 * NT / 32];
+    const double2 *p = partials + (int64_t)blockIdx.x * items;
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < items; i += NT) {
+        a += p[i].x;
+        b += p[i].y;
+    }
+    block_sum2(a, b, red);
+    if (threadIdx.x == 0) mean_out[blockIdx.x] = a * inv_n;
+}
+
+__global__ void __launch_bounds__(NT) finalize_msssim_kernel(const MsFinalize F) {
+    __shared__ double red[2 * NT / 32];
+    __shared__ double mq[GBSSIM_MAX_SCALES], mcs[GBSSIM_MAX_SCALES];
+    const int img = blockIdx.x;
+    for (int j = 0; j < F.scales; ++j) {
+        const MsLevelInfo &lv = F.lv[j];
+        const double2 *p = lv.partials + (int64_t)img * lv.items_per_image;
+        double a = 0.0, b = 0.0;
+        for (int i = threadIdx.x; i < lv.items_per_image; i += NT) {
+            a += p[i].x;
+            b += p[i].y;
+        }
+        block_sum2(a, b, red);
+        if (threadIdx.x == 0) {
+            mq[j] = a * lv.inv_n;
+            mcs[j] = b * lv.inv_n;
+        }
+    }
+    if (threadIdx.x == 0) {
+        const int S = F.scales;
+        double score;
+        if (F.combine == GBSSIM_COMBINE_SUM) {
+            double wsum = 0.0, acc = 0.0;
+            for (int j = 0; j < S; ++j) wsum += F.exps[j];
+            for (int j = 0; j < S; ++j) acc += F.exps[j] / wsum * (j == S - 1 ? mq[j] : mcs[j]);
+            score = acc;
+        } else {
+            double acc = 1.0;
+            for (int j = 0; j < S; ++j) acc *= pow(j == S - 1 ? mq[j] : mcs[j], F.exps[j]);
+            score = acc;  // pow of a negative base with a non-integer exponent is NaN
+        }
+        F.score_out[img] = score;
+        if (F.per_scale_out)
+            for (int j = 0; j < S; ++j) {
+                F.per_scale_out[((int64_t)img * S + j) * 2] = mcs[j];
+                F.per_scale_out[((int64_t)img * S + j) * 2 + 1] = mq[j];
+            }
+    }
+}
+
+template <typename T>
+__global__ void downsample_kernel(ImgDesc in, float *out) {
+    const int64_t Hh = in.H >> 1, Wh = in.W >> 1;
+    const int img = blockIdx.z;
+    const int64_t C = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t R = blockIdx.y;
+    if (C >= Wh) return;
+    const T *b = static_cast<const T *>(in.data) + img * in.image_stride + 2 * R * in.row_stride + 2 * C;
+    const float s = (load_f32<T>(b) + load_f32<T>(b + 1)) +
+                    (load_f32<T>(b + in.row_stride) + load_f32<T>(b + in.row_stride + 1));
+    out[img * Hh * Wh + R * Wh + C] = 0.25f * s;
+}
+
+constexpr int PT = 64;  // rows per pool item
+
+__global__ void __launch_bounds__(NT) pool_mean_kernel(const float *map, int64_t h, int64_t w,
+                                                       int64_t ld, int64_t is, int items,
+                                                       double2 *partials) {
+    __shared__ double red[2 * NT / 32];
+    const int img = blockIdx.y;
+    const int64_t r0 = (int64_t)blockIdx.x * PT;
+    const float *m = map + img * is;
+    double a = 0.0;
+    for (int64_t r = r0; r < min(r0 + PT, h); ++r) {
+        float acc = 0.f;
+        for (int64_t c = threadIdx.x; c < w; c += NT) acc += m[r * ld + c];
+        a += acc;
+    }
+    double b = 0.0;
+    block_sum2(a, b, red);
+    if (threadIdx.x == 0) partials[(int64_t)img * items + blockIdx.x] = make_double2(a, 0.0);
+}
+
+}  // namespace
+
+cudaError_t launch_finalize_ssim(const double2 *partials, int count, int items_per_image,
+                                 double inv_n, double *mean_out, cudaStream_t st) {
+    finalize_ssim_kernel<<<count, NT, 0, st>>>(partials, items_per_image, inv_n, mean_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_msssim(const MsFinalize &F, cudaStream_t st) {
+    finalize_msssim_kernel<<<F.count, NT, 0, st>>>(F);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_downsample(const ImgDesc &in, int dtype, int count, float *out,
+                              cudaStream_t st) {
+    const int64_t Hh = in.H >> 1, Wh = in.W >> 1;
+    if (Hh == 0 || Wh == 0) return cudaSuccess;
+    dim3 grid((unsigned)((Wh + 127) / 128), (unsigned)Hh, count);
+    switch (dtype) {
+    case GBSSIM_U8: downsample_kernel<uint8_t><<<grid, 128, 0, st>>>(in, out); break;
+    case GBSSIM_F16: downsample_kernel<__half><<<grid, 128, 0, st>>>(in, out); break;
+    case GBSSIM_BF16: downsample_kernel<__nv_bfloat16><<<grid, 128, 0, st>>>(in, out); break;
+    case GBSSIM_F32: downsample_kernel<float><<<grid, 128, 0, st>>>(in, out); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int pool_items(int64_t h, int64_t w) { return (int)((h + PT - 1) / PT); }
+
+cudaError_t launch_pool_mean(const float *map, int64_t h, int64_t w, int64_t ld, int count,
+                             int64_t image_stride, double2 *partials, double *out,
+                             cudaStream_t st) {
+    const int items = pool_items(h, w);
+    dim3 grid(items, count);
+    pool_mean_kernel<<<grid, NT, 0, st>>>(map, h, w, ld, image_stride, items, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_finalize_ssim(partials, count, items, 1.0 / ((double)h * (double)w), out, st);
+}
+
+}  // namespace gbssim

@@ -1,0 +1,235 @@
+"""ctypes binding of libgbssim.so (include/gbssim.h).
+
+Argument marshalling only: every step of SSIM / MS-SSIM runs in the library's
+CUDA kernels.  PyTorch supplies device memory (inputs, outputs and the
+workspace the C ABI asks for) and the current CUDA stream.  Importing this
+module raises ImportError when the library has not been built, so no code path
+can silently fall back to a CPU implementation.
+
+Two layers:
+  * ``lib`` with the raw C entry points (``lib.gbssim_ssim_map`` ...) and the
+    ctypes structs ``Plane`` / ``Params`` mirroring the header;
+  * tensor-level helpers with the same names minus the prefix: ``ssim``,
+    ``msssim``, ``window_sums``, ``ssim_pool``.  They accept CUDA tensors, or
+    CPU tensors (copied to the current CUDA device first, results copied
+    back) shaped (H, W), (N, H, W) or (B, C, H, W).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbssim.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libgbssim.so is not built; run `python -c 'import __graft_entry__ as g; g.build()'` "
+                      "(or paper_2101_06354_gb300/build.py) first")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+MAX_SCALES = 8
+MAX_K = 63
+MSSSIM_EXPONENTS = (0.0448, 0.2856, 0.3001, 0.2363, 0.1333)
+
+OK, ERR_INVALID_ARG, ERR_TOO_SMALL, ERR_UNSUPPORTED, ERR_CUDA, ERR_DOMAIN, ERR_TIMEOUT, ERR_WORKSPACE = \
+    0, -1, -2, -3, -4, -5, -6, -7
+U8, F16, BF16, F32 = 0, 1, 2, 3
+WIN_GAUSSIAN, WIN_BOX = 0, 1
+COMBINE_PRODUCT, COMBINE_SUM = 0, 1
+OP_SSIM, OP_MSSSIM, OP_BACKWARD, OP_BACKWARD_MS, OP_POOL = 0, 1, 2, 3, 4
+POOL_MEAN = 0
+
+
+class Plane(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("count", ctypes.c_int32),
+                ("height", ctypes.c_int64), ("width", ctypes.c_int64),
+                ("row_stride", ctypes.c_int64), ("image_stride", ctypes.c_int64)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("window", ctypes.c_int32), ("k", ctypes.c_int32), ("sigma", ctypes.c_double),
+                ("K1", ctypes.c_double), ("K2", ctypes.c_double), ("L", ctypes.c_double),
+                ("stride", ctypes.c_int32), ("scales", ctypes.c_int32),
+                ("exponents", ctypes.c_double * MAX_SCALES), ("combine", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+_P = ctypes.POINTER
+_vp, _i32, _i64, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+_SIGS = {
+    "gbssim_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "gbssim_version": ([], ctypes.c_int),
+    "gbssim_params_default": ([_P(Params)], None),
+    "gbssim_workspace_size": ([_P(Plane), _P(Params), ctypes.c_int, _P(_sz)], ctypes.c_int),
+    "gbssim_ssim_map": ([_P(Plane), _P(Plane), _P(Params), _vp, _i64, _i64, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "gbssim_ssim_pool": ([_vp, _i64, _i64, _i64, _i32, _i64, _i32, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "gbssim_msssim": ([_P(Plane), _P(Plane), _P(Params), _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "gbssim_window_sums": ([_P(Plane), _P(Plane), _i32, _i32, _vp, _vp], ctypes.c_int),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+class GbssimError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s failed: %s (%d)" % (where, status_string(status), status))
+
+
+def status_string(status: int) -> str:
+    return lib.gbssim_status_string(int(status)).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise GbssimError(rc, where)
+
+
+_DTYPES = {torch.uint8: U8, torch.float16: F16, torch.bfloat16: BF16, torch.float32: F32}
+
+
+def make_params(window: str = "gaussian", k: int = 11, sigma: float = 1.5, K1: float = 0.01,
+                K2: float = 0.03, L: float = 255.0, stride: int = 1, scales: int = 5,
+                exponents=None, combine: str = "product") -> Params:
+    p = Params()
+    lib.gbssim_params_default(ctypes.byref(p))
+    p.window = {"gaussian": WIN_GAUSSIAN, "box": WIN_BOX}[window]
+    p.k, p.sigma, p.K1, p.K2, p.L, p.stride, p.scales = int(k), float(sigma), float(K1), float(K2), \
+        float(L), int(stride), int(scales)
+    if exponents is not None:
+        if len(exponents) < scales:
+            raise ValueError("need one exponent per scale")
+        for j in range(MAX_SCALES):
+            p.exponents[j] = float(exponents[j]) if j < len(exponents) else 0.0
+    p.combine = {"product": COMBINE_PRODUCT, "sum": COMBINE_SUM}[combine]
+    return p
+
+
+def _as_batch(t: torch.Tensor) -> torch.Tensor:
+    """View (H, W), (N, H, W) or (B, C, H, W) as (N, H, W) with unit column stride."""
+    if t.dim() == 2:
+        t = t.unsqueeze(0)
+    elif t.dim() == 4:
+        t = t.reshape(-1, t.shape[-2], t.shape[-1])
+    elif t.dim() != 3:
+        raise ValueError("expected a 2-, 3- or 4-D tensor")
+    if t.stride(-1) != 1 or (t.shape[0] > 1 and t.stride(0) < t.shape[1] * t.stride(1)):
+        t = t.contiguous()
+    return t
+
+
+def plane(t: torch.Tensor) -> Plane:
+    """Describe an (N, H, W) CUDA tensor (unit column stride) for the C ABI."""
+    if t.dtype not in _DTYPES:
+        raise TypeError("unsupported dtype %s" % t.dtype)
+    n, h, w = t.shape
+    return Plane(t.data_ptr(), _DTYPES[t.dtype], n, h, w, t.stride(1), t.stride(0) if n > 1 else h * t.stride(1))
+
+
+def _stream(dev) -> int:
+    return torch.cuda.current_stream(dev).cuda_stream
+
+
+def _prepare(x, y):
+    host = x.device.type == "cpu"
+    dev = torch.device("cuda", torch.cuda.current_device()) if host else x.device
+    if host:
+        x = x.to(dev, non_blocking=True)
+        y = y.to(dev, non_blocking=True)
+    if y.device != x.device or y.dtype != x.dtype or y.shape != x.shape:
+        raise ValueError("x and y must share device, dtype and shape")
+    xb, yb = _as_batch(x), _as_batch(y)
+    if xb.stride() != yb.stride():
+        xb, yb = xb.contiguous(), yb.contiguous()
+    return host, dev, xb, yb
+
+
+def workspace(px: Plane, p: Params, op: int, dev) -> torch.Tensor:
+    n = ctypes.c_size_t()
+    _check(lib.gbssim_workspace_size(ctypes.byref(px), ctypes.byref(p), op, ctypes.byref(n)),
+           "gbssim_workspace_size")
+    return torch.empty(max(int(n.value), 1), dtype=torch.uint8, device=dev)
+
+
+def out_shape(h: int, w: int, k: int, stride: int):
+    return ((h - k) // stride + 1, (w - k) // stride + 1)
+
+
+def ssim(x: torch.Tensor, y: torch.Tensor, return_map: bool = False, ws: torch.Tensor = None, **kw):
+    """MSSIM of each pair (float64 tensor of length N), optionally with the
+    float Q map (N, OH, OW).  Keyword arguments as ``make_params``."""
+    host, dev, xb, yb = _prepare(x, y)
+    p = make_params(**kw)
+    px, py = plane(xb), plane(yb)
+    n = xb.shape[0]
+    if ws is None:
+        ws = workspace(px, p, OP_SSIM, dev)
+    mean = torch.empty(n, dtype=torch.float64, device=dev)
+    mp = None
+    if return_map:
+        oh, ow = out_shape(xb.shape[1], xb.shape[2], p.k, p.stride)
+        mp = torch.empty((n, oh, ow), dtype=torch.float32, device=dev)
+    _check(lib.gbssim_ssim_map(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p),
+                               mp.data_ptr() if mp is not None else None,
+                               mp.stride(1) if mp is not None else 0,
+                               mp.stride(0) if mp is not None else 0,
+                               mean.data_ptr(), ws.data_ptr(), ws.numel(), _stream(dev)),
+           "gbssim_ssim_map")
+    if host:
+        mean = mean.cpu()
+        mp = mp.cpu() if mp is not None else None
+    return (mean, mp) if return_map else mean
+
+
+def msssim(x: torch.Tensor, y: torch.Tensor, per_scale: bool = False, ws: torch.Tensor = None, **kw):
+    """MS-SSIM of each pair (float64 tensor of length N); with per_scale=True
+    also the (N, scales, 2) tensor of (mean cs_j, mean Q_j)."""
+    host, dev, xb, yb = _prepare(x, y)
+    kw.setdefault("exponents", MSSSIM_EXPONENTS[: kw.get("scales", 5)])
+    p = make_params(**kw)
+    px, py = plane(xb), plane(yb)
+    n = xb.shape[0]
+    if ws is None:
+        ws = workspace(px, p, OP_MSSSIM, dev)
+    score = torch.empty(n, dtype=torch.float64, device=dev)
+    per = torch.empty((n, p.scales, 2), dtype=torch.float64, device=dev) if per_scale else None
+    _check(lib.gbssim_msssim(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p), score.data_ptr(),
+                             per.data_ptr() if per is not None else None, ws.data_ptr(), ws.numel(),
+                             _stream(dev)), "gbssim_msssim")
+    if host:
+        score = score.cpu()
+        per = per.cpu() if per is not None else None
+    return (score, per) if per_scale else score
+
+
+def window_sums(x: torch.Tensor, y: torch.Tensor, k: int, stride: int = 1) -> torch.Tensor:
+    """Exact int64 window sums (N, OH, OW, 5) of a uint8 pair batch."""
+    host, dev, xb, yb = _prepare(x, y)
+    n, h, w = xb.shape
+    oh, ow = out_shape(h, w, k, stride)
+    out = torch.empty((n, max(oh, 0), max(ow, 0), 5), dtype=torch.int64, device=dev)
+    px, py = plane(xb), plane(yb)
+    _check(lib.gbssim_window_sums(ctypes.byref(px), ctypes.byref(py), int(k), int(stride),
+                                  out.data_ptr(), _stream(dev)), "gbssim_window_sums")
+    return out.cpu() if host else out
+
+
+def ssim_pool(qmap: torch.Tensor, kind: str = "mean") -> torch.Tensor:
+    """Pool float maps (H, W) or (N, H, W) into one double each."""
+    m = qmap if qmap.dim() == 3 else qmap.unsqueeze(0)
+    if m.dtype != torch.float32 or m.stride(-1) != 1:
+        raise TypeError("expected float32 maps with unit column stride")
+    n, h, w = m.shape
+    dev = m.device
+    px = Plane(m.data_ptr(), F32, n, h, w, m.stride(1), m.stride(0) if n > 1 else h * m.stride(1))
+    ws = workspace(px, Params(), OP_POOL, dev)
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    _check(lib.gbssim_ssim_pool(m.data_ptr(), h, w, m.stride(1), n, px.image_stride,
+                                {"mean": POOL_MEAN}[kind], None, out.data_ptr(), ws.data_ptr(),
+                                ws.numel(), _stream(dev)), "gbssim_ssim_pool")
+    return out

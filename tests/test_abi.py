@@ -1,0 +1,140 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+The library must load, export every function declared in include/gbssim.h,
+and reject bad arguments on the host before anything reaches the GPU (these
+calls return before any CUDA runtime call, so they run on a CPU-only host).
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def g():
+    from paper_2101_06354_gb300 import build
+
+    build.build()
+    from paper_2101_06354_gb300 import gbssim
+
+    return gbssim
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(gbssim_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(g):
+    names = declared_functions()
+    assert "gbssim_ssim_map" in names and "gbssim_msssim" in names
+    for n in names:
+        assert hasattr(g.lib, n), n
+
+
+def test_status_strings_and_version(g):
+    assert g.lib.gbssim_version() == 1
+    for s in range(-7, 1):
+        assert g.status_string(s)
+    assert g.status_string(-99) == "unknown status"
+
+
+def test_defaults_follow_recommended_parameters(g):
+    p = g.Params()
+    g.lib.gbssim_params_default(ctypes.byref(p))
+    assert (p.window, p.k, p.sigma, p.K1, p.K2, p.L, p.stride, p.scales) == (0, 11, 1.5, 0.01, 0.03, 255.0, 1, 5)
+    assert list(p.exponents)[:5] == [0.0448, 0.2856, 0.3001, 0.2363, 0.1333]
+
+
+def _plane(g, h=64, w=80, n=1, dtype=0, ptr=0x1000, rs=None, is_=None):
+    rs = w if rs is None else rs
+    return g.Plane(ptr, dtype, n, h, w, rs, h * rs if is_ is None else is_)
+
+
+def _ws(g, x, p, op):
+    n = ctypes.c_size_t()
+    rc = g.lib.gbssim_workspace_size(ctypes.byref(x), ctypes.byref(p), op, ctypes.byref(n))
+    return rc, n.value
+
+
+def test_workspace_sizes(g):
+    p = g.make_params()
+    rc, n1 = _ws(g, _plane(g, 1080, 1920), p, g.OP_SSIM)
+    assert rc == 0 and n1 > 0 and n1 % 256 == 0
+    rc, n64 = _ws(g, _plane(g, 1080, 1920, 64), p, g.OP_SSIM)
+    # one fp64 (sum Q, sum cs) pair per work item and image
+    assert rc == 0 and n64 > n1 and n64 >= 64 * 16 * 30
+    rc, m = _ws(g, _plane(g, 1080, 1920, 2), p, g.OP_MSSSIM)
+    # pyramid levels 2..5 of two pairs, x and y, fp32
+    pyr = sum((1080 >> j) * (1920 >> j) for j in range(1, 5)) * 2 * 2 * 4
+    assert rc == 0 and m >= pyr
+    assert _ws(g, _plane(g, 100, 100), p, g.OP_MSSSIM)[0] == g.ERR_TOO_SMALL  # 100 -> 50 -> 25 -> 12 -> 6 < 11
+    assert _ws(g, _plane(g, 100, 100), g.make_params(scales=3), g.OP_MSSSIM)[0] == 0
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("k", 0, -1), ("k", 64, -1), ("stride", 0, -1), ("scales", 0, -1), ("scales", 9, -1),
+    ("window", 7, -1), ("sigma", 0.0, -1), ("L", -1.0, -1), ("combine", 3, -1), ("flags", 1, -1),
+])
+def test_bad_params_rejected(g, field, value, status):
+    p = g.make_params()
+    setattr(p, field, value)
+    x = _plane(g)
+    mean = ctypes.c_void_p(0x2000)
+    rc = g.lib.gbssim_ssim_map(ctypes.byref(x), ctypes.byref(x), ctypes.byref(p), None, 0, 0, mean,
+                               ctypes.c_void_p(0x3000), 1 << 20, None)
+    assert rc == status
+
+
+def test_bad_planes_rejected(g):
+    p = g.make_params()
+    ok = _plane(g)
+    call = lambda a, b, ws=1 << 20: g.lib.gbssim_ssim_map(ctypes.byref(a), ctypes.byref(b), ctypes.byref(p),
+                                                          None, 0, 0, ctypes.c_void_p(0x2000),
+                                                          ctypes.c_void_p(0x3000), ws, None)
+    assert call(_plane(g, ptr=0), ok) == g.ERR_INVALID_ARG          # null data
+    assert call(ok, _plane(g, w=81)) == g.ERR_INVALID_ARG           # shape mismatch
+    assert call(ok, _plane(g, dtype=3)) == g.ERR_INVALID_ARG        # dtype mismatch
+    assert call(_plane(g, dtype=9), _plane(g, dtype=9)) == g.ERR_INVALID_ARG
+    assert call(_plane(g, rs=10), _plane(g, rs=10)) == g.ERR_INVALID_ARG  # row stride < width
+    assert call(_plane(g, h=10), _plane(g, h=10)) == g.ERR_TOO_SMALL  # k = 11 > H
+    assert call(ok, ok, ws=16) == g.ERR_WORKSPACE
+    x2 = _plane(g, n=2, is_=10)
+    assert call(x2, x2) == g.ERR_INVALID_ARG                       # overlapping images
+    # neither a map nor a mean requested
+    assert g.lib.gbssim_ssim_map(ctypes.byref(ok), ctypes.byref(ok), ctypes.byref(p), None, 0, 0, None,
+                                 ctypes.c_void_p(0x3000), 1 << 20, None) == g.ERR_INVALID_ARG
+
+
+def test_msssim_and_window_sums_validation(g):
+    p = g.make_params()
+    x = _plane(g, 150, 150)
+    ws = ctypes.c_void_p(0x3000)
+    assert g.lib.gbssim_msssim(ctypes.byref(x), ctypes.byref(x), ctypes.byref(p), ctypes.c_void_p(0x10), None,
+                               ws, 1 << 30, None) == g.ERR_TOO_SMALL   # 150 -> 9 at scale 5
+    assert g.lib.gbssim_msssim(ctypes.byref(x), ctypes.byref(x), ctypes.byref(p), None, None,
+                               ws, 1 << 30, None) == g.ERR_INVALID_ARG
+    xf = _plane(g, dtype=3)
+    assert g.lib.gbssim_window_sums(ctypes.byref(xf), ctypes.byref(xf), 8, 4, ctypes.c_void_p(0x10), None) \
+        == g.ERR_UNSUPPORTED
+    xu = _plane(g)
+    assert g.lib.gbssim_window_sums(ctypes.byref(xu), ctypes.byref(xu), 0, 4, ctypes.c_void_p(0x10), None) \
+        == g.ERR_INVALID_ARG
+    assert g.lib.gbssim_window_sums(ctypes.byref(xu), ctypes.byref(xu), 65, 1, ctypes.c_void_p(0x10), None) \
+        == g.ERR_INVALID_ARG
+
+
+def test_pool_validation(g):
+    m = ctypes.c_void_p(0x1000)
+    assert g.lib.gbssim_ssim_pool(m, 10, 10, 5, 1, 0, 0, None, ctypes.c_void_p(0x10), ctypes.c_void_p(0x20),
+                                  1 << 20, None) == g.ERR_INVALID_ARG  # ld < w
+    assert g.lib.gbssim_ssim_pool(m, 10, 10, 10, 1, 0, 42, None, ctypes.c_void_p(0x10), ctypes.c_void_p(0x20),
+                                  1 << 20, None) == g.ERR_UNSUPPORTED
