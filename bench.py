@@ -64,7 +64,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -180,9 +180,10 @@ def run_gbssim(args):
         if ws > 1:
             dist.barrier()
 
-    # rank r processes its own 64 pairs (seeds offset by rank)
-    x, y = synth.luma_pairs_u8(N_PAIRS, H, W, seed_ref=10 + 1000 * rank, seed_dist=100000 + 1000 * rank,
-                               device=dev)
+    # rank r processes its own 64 pairs (seeds offset by rank); generated on
+    # the host so that no input-synthesis kernel runs on the GPU
+    x, y = synth.luma_pairs_u8(N_PAIRS, H, W, seed_ref=10 + 1000 * rank, seed_dist=100000 + 1000 * rank)
+    x, y = x.to(dev), y.to(dev)
     px = gbssim.plane(x)
     p = gbssim.make_params(exponents=gbssim.MSSSIM_EXPONENTS)
     wsp = gbssim.workspace(px, p, gbssim.OP_MSSSIM, dev)
@@ -264,7 +265,7 @@ def run_gbssim(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbssim", choices=["gbssim", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -105,6 +105,7 @@ struct GaussLaunch {
     Taps<11> taps;
     SsimConst c;
     int seg_rows;       // output rows per work item (multiple of 16)
+    bool vec;           // x/y rows aligned for 4-element vector loads (set by the launcher)
 };
 int gauss11_items(int64_t H, int64_t W, int seg_rows, int *strips, int *segs);
 cudaError_t launch_gauss11(const GaussLaunch &L, cudaStream_t st);

@@ -50,17 +50,23 @@ constexpr int FIRST = CH + HALO;  // input rows staged for the first chunk
 constexpr int IW = TW + HALO;     // input columns per strip (74)
 constexpr int IWP = 80;           // staged row pitch in floats
 constexpr int NT = 256;
-constexpr int PF = (2 * CH * IW + NT - 1) / NT;  // prefetched elements per thread (10)
+constexpr int QUADS = (IW + 3) / 4;             // 4-column staging units per row (19)
+constexpr int PFQ = (2 * CH * QUADS + NT - 1) / NT;  // prefetched quads per thread (3)
+// The vertical pass of a thread reads ring rows base..base+13 with base a
+// multiple of 4 below RING; rows 0..DUP-1 are also stored at RING..RING+DUP-1
+// so those reads never wrap.
+constexpr int DUP = 10;
+constexpr int RROWS = RING + DUP;
 
 struct __align__(16) Smem {
     float in_x[FIRST][IWP];
     float in_y[FIRST][IWP];
-    float mu_x[RING][TW];
-    float mu_y[RING][TW];
-    float v_x[RING][TW];
-    float v_y[RING][TW];
-    float c_xy[RING][TW];
-    double red[2 * NT / 32];
+    float mu_x[RROWS][TW];
+    float mu_y[RROWS][TW];
+    float v_x[RROWS][TW];
+    float v_y[RROWS][TW];
+    float c_xy[RROWS][TW];
+    float red[2 * NT / 32];
 };
 
 struct Geo {
@@ -70,55 +76,111 @@ struct Geo {
     int64_t o0, oend;  // output rows [o0, oend)
     int64_t own_r1;    // owned input rows [o0, own_r1) (downsample)
     int64_t own_c1;    // owned input columns [j0, own_c1)
+    bool vec;          // rows and strip start aligned for 4-element vector loads
 };
 
+// Four consecutive elements (columns c..c+3 of one row) as floats; zero
+// outside the image.  `vec`: the row start and c are aligned for one vector
+// load of four elements.
+__device__ __forceinline__ float u8f(unsigned w, int k) {
+    // byte k of w placed in the mantissa of 2^23, minus 2^23: exact for 0..255
+    return __int_as_float(__byte_perm(w, 0x4B000000u, 0x7540u + k)) - 8388608.0f;
+}
 template <typename T>
-__device__ __forceinline__ float fetch(const Geo &g, int which, int64_t r, int64_t c) {
-    if (r >= g.H || c >= g.W) return 0.f;
-    const T *p = static_cast<const T *>(which ? g.yb : g.xb);
-    return load_f32<T>(p + r * g.rs + c);
+__device__ __forceinline__ float4 load_quad(const T *row, int64_t c, int64_t W, bool vec);
+template <>
+__device__ __forceinline__ float4 load_quad<uint8_t>(const uint8_t *row, int64_t c, int64_t W, bool vec) {
+    if (vec && c + 4 <= W) {
+        const unsigned w = __ldg(reinterpret_cast<const unsigned *>(row + c));
+        return make_float4(u8f(w, 0), u8f(w, 1), u8f(w, 2), u8f(w, 3));
+    }
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = c + k < W ? (float)__ldg(row + c + k) : 0.f;
+    return make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ float4 load_quad<float>(const float *row, int64_t c, int64_t W, bool vec) {
+    if (vec && c + 4 <= W) return __ldg(reinterpret_cast<const float4 *>(row + c));
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = c + k < W ? __ldg(row + c + k) : 0.f;
+    return make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ float4 load_quad<__half>(const __half *row, int64_t c, int64_t W, bool vec) {
+    if (vec && c + 4 <= W) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2 *>(row + c));
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = c + k < W ? load_f32<__half>(row + c + k) : 0.f;
+    return make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ float4 load_quad<__nv_bfloat16>(const __nv_bfloat16 *row, int64_t c, int64_t W,
+                                                           bool vec) {
+    if (vec && c + 4 <= W) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2 *>(row + c));
+        return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                           __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+    }
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = c + k < W ? load_f32<__nv_bfloat16>(row + c + k) : 0.f;
+    return make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// Staging unit t (of 2*nr*QUADS): image (x or y), row within the block, quad.
+template <typename T>
+__device__ __forceinline__ float4 fetch_unit(const Geo &g, int t, int nr, int64_t r0, int &which, int &r,
+                                             int &u) {
+    which = t >= nr * QUADS;
+    const int rem = t - which * nr * QUADS;
+    r = rem / QUADS;
+    u = rem - r * QUADS;
+    const int64_t row = r0 + r;
+    if (row >= g.H) return make_float4(0.f, 0.f, 0.f, 0.f);
+    const T *base = static_cast<const T *>(which ? g.yb : g.xb) + row * g.rs;
+    return load_quad<T>(base, g.j0 + 4 * u, g.W, g.vec);
+}
+
+__device__ __forceinline__ void put_unit(Smem &S, int which, int r, int u, float4 v) {
+    *reinterpret_cast<float4 *>(&(which ? S.in_y : S.in_x)[r][4 * u]) = v;
 }
 
 // Stage `nr` input rows starting at absolute row r0 into in_x/in_y rows 0..nr-1.
 template <typename T>
 __device__ __forceinline__ void stage_direct(Smem &S, const Geo &g, int64_t r0, int nr) {
-    const int per = nr * IW;
-    for (int e = threadIdx.x; e < 2 * per; e += NT) {
-        const int which = e >= per;
-        const int rem = e - which * per;
-        const int r = rem / IW, c = rem - r * IW;
-        const float v = fetch<T>(g, which, r0 + r, g.j0 + c);
-        (which ? S.in_y : S.in_x)[r][c] = v;
+    for (int t = threadIdx.x; t < 2 * nr * QUADS; t += NT) {
+        int which, r, u;
+        const float4 v = fetch_unit<T>(g, t, nr, r0, which, r, u);
+        put_unit(S, which, r, u, v);
     }
 }
 
 template <typename T>
-__device__ __forceinline__ void prefetch(float (&pf)[PF], const Geo &g, int64_t r0) {
-    constexpr int per = CH * IW;
+__device__ __forceinline__ void prefetch(float4 (&pf)[PFQ], const Geo &g, int64_t r0) {
 #pragma unroll
-    for (int i = 0; i < PF; ++i) {
-        const int e = threadIdx.x + i * NT;
-        float v = 0.f;
-        if (e < 2 * per) {
-            const int which = e >= per;
-            const int rem = e - which * per;
-            const int r = rem / IW, c = rem - r * IW;
-            v = fetch<T>(g, which, r0 + r, g.j0 + c);
-        }
-        pf[i] = v;
+    for (int i = 0; i < PFQ; ++i) {
+        const int t = threadIdx.x + i * NT;
+        int which, r, u;
+        pf[i] = t < 2 * CH * QUADS ? fetch_unit<T>(g, t, CH, r0, which, r, u) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
-__device__ __forceinline__ void store_prefetch(Smem &S, const float (&pf)[PF]) {
-    constexpr int per = CH * IW;
+__device__ __forceinline__ void store_prefetch(Smem &S, const float4 (&pf)[PFQ]) {
 #pragma unroll
-    for (int i = 0; i < PF; ++i) {
-        const int e = threadIdx.x + i * NT;
-        if (e < 2 * per) {
-            const int which = e >= per;
-            const int rem = e - which * per;
-            const int r = rem / IW, c = rem - r * IW;
-            (which ? S.in_y : S.in_x)[r][c] = pf[i];
+    for (int i = 0; i < PFQ; ++i) {
+        const int t = threadIdx.x + i * NT;
+        if (t < 2 * CH * QUADS) {
+            const int which = t >= CH * QUADS;
+            const int rem = t - which * CH * QUADS;
+            const int r = rem / QUADS;
+            put_unit(S, which, r, rem - r * QUADS, pf[i]);
         }
     }
 }
@@ -204,6 +266,13 @@ __device__ __forceinline__ void horizontal(Smem &S, int nr, int rel0, const Taps
         *reinterpret_cast<float4 *>(&S.v_x[slot][g4]) = o_vx;
         *reinterpret_cast<float4 *>(&S.v_y[slot][g4]) = o_vy;
         *reinterpret_cast<float4 *>(&S.c_xy[slot][g4]) = o_c;
+        if (slot < DUP) {
+            *reinterpret_cast<float4 *>(&S.mu_x[slot + RING][g4]) = o_mx;
+            *reinterpret_cast<float4 *>(&S.mu_y[slot + RING][g4]) = o_my;
+            *reinterpret_cast<float4 *>(&S.v_x[slot + RING][g4]) = o_vx;
+            *reinterpret_cast<float4 *>(&S.v_y[slot + RING][g4]) = o_vy;
+            *reinterpret_cast<float4 *>(&S.c_xy[slot + RING][g4]) = o_c;
+        }
     }
 }
 
@@ -211,17 +280,17 @@ __device__ __forceinline__ void horizontal(Smem &S, int nr, int rel0, const Taps
 // (relative to the segment); each thread does 4 rows of one column.
 __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, const Taps<K> &t,
                                          const SsimConst &cc, float *map, int64_t map_ld,
-                                         float &accQ, float &accCS) {
+                                         float &sumQ, float &sumCS) {
     const int col = threadIdx.x & (TW - 1);
     const int base = rel0 + 4 * (threadIdx.x >> 6);
-    const int sb = (base + 7) & (RING - 1);
-    const float bx = S.mu_x[sb][col], by = S.mu_y[sb][col];
+    const int b0 = base & (RING - 1);  // multiple of 4; b0 + 13 < RROWS
+    const float bx = S.mu_x[b0 + 7][col], by = S.mu_y[b0 + 7][col];
     float mx[4], my[4], sxx[4], syy[4], sxy[4];
 #pragma unroll
     for (int o = 0; o < 4; ++o) mx[o] = my[o] = sxx[o] = syy[o] = sxy[o] = 0.f;
 #pragma unroll
     for (int i = 0; i < 14; ++i) {
-        const int s = (base + i) & (RING - 1);
+        const int s = b0 + i;
         const float ex = S.mu_x[s][col] - bx, ey = S.mu_y[s][col] - by;
         const float qxx = fmaf(ex, ex, S.v_x[s][col]);
         const float qyy = fmaf(ey, ey, S.v_y[s][col]);
@@ -240,6 +309,8 @@ __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, 
         }
     }
     const int64_t c_abs = g.j0 + col;
+    sumQ = 0.f;
+    sumCS = 0.f;
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
         const int64_t row = g.o0 + base + o;
@@ -252,11 +323,45 @@ __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, 
         const float l = __fdividef(A1, B1), cs = __fdividef(A2, B2);
         const float q = l * cs;
         if (row < g.oend && c_abs < g.OW) {
-            accQ += q;
-            accCS += cs;
+            sumQ += q;
+            sumCS += cs;
             if (map) map[row * map_ld + c_abs] = q;
         }
     }
+}
+
+// Compensated (Kahan) fp32 running sum.
+struct KSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+// Sum (a, b) over the CTA: fp32 pairwise tree inside each warp, fp64 across
+// warps; the result is valid in thread 0.
+__device__ __forceinline__ void block_sum2f(float a, float b, float *red, double &ra, double &rb) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) {
+        red[2 * warp] = a;
+        red[2 * warp + 1] = b;
+    }
+    __syncthreads();
+    ra = rb = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NT / 32; ++w) {
+            ra += (double)red[2 * w];
+            rb += (double)red[2 * w + 1];
+        }
 }
 
 template <typename T>
@@ -279,13 +384,14 @@ __global__ void __launch_bounds__(NT, 3) gauss11_kernel(const GaussLaunch L, int
     g.own_r1 = (seg == segs - 1) ? g.H : g.o0 + L.seg_rows;
     g.own_c1 = (strip == strips - 1) ? g.W : g.j0 + TW;
     const int nchunks = (int)((g.oend - g.o0 + CH - 1) / CH);
+    g.vec = L.vec;
     float *map = L.map ? L.map + img * L.map_is : nullptr;
     const int64_t dsn = (g.H >> 1) * (g.W >> 1);
     float *dsx = L.ds_x ? L.ds_x + img * dsn : nullptr;
     float *dsy = L.ds_y ? L.ds_y + img * dsn : nullptr;
 
-    float accQ = 0.f, accCS = 0.f;
-    float pf[PF];
+    KSum accQ, accCS;
+    float4 pf[PFQ];
 
     stage_direct<T>(S, g, g.o0, FIRST);
     __syncthreads();
@@ -296,7 +402,10 @@ __global__ void __launch_bounds__(NT, 3) gauss11_kernel(const GaussLaunch L, int
         const int64_t next_r0 = g.o0 + FIRST + (int64_t)CH * c;
         if (more) prefetch<T>(pf, g, next_r0);
         __syncthreads();  // ring rows of chunk c complete; staging free
-        vertical(S, g, CH * c, L.taps, L.c, map, L.map_ld, accQ, accCS);
+        float cq, ccs;
+        vertical(S, g, CH * c, L.taps, L.c, map, L.map_ld, cq, ccs);
+        accQ.add(cq);
+        accCS.add(ccs);
         if (more) store_prefetch(S, pf);
         __syncthreads();  // staging complete; ring rows of chunk c consumed
         if (more) {
@@ -304,8 +413,8 @@ __global__ void __launch_bounds__(NT, 3) gauss11_kernel(const GaussLaunch L, int
             horizontal(S, CH, FIRST + CH * c, L.taps);
         }
     }
-    double a = accQ, b = accCS;
-    block_sum2(a, b, S.red);
+    double a, b;
+    block_sum2f(accQ.s - accQ.c, accCS.s - accCS.c, S.red, a, b);
     if (threadIdx.x == 0)
         L.partials[((int64_t)img * segs + seg) * strips + strip] = make_double2(a, b);
 }
@@ -398,8 +507,12 @@ cudaError_t launch_gauss11_t(const GaussLaunch &L, cudaStream_t st) {
     }
     int strips, segs;
     gauss11_items(L.x.H, L.x.W, L.seg_rows, &strips, &segs);
+    GaussLaunch A = L;
+    const uintptr_t vbytes = 4 * sizeof(T);  // one 4-element vector
+    A.vec = ((uintptr_t)L.x.data % vbytes == 0) && ((uintptr_t)L.y.data % vbytes == 0) &&
+            (L.x.row_stride % 4 == 0) && (L.x.image_stride % 4 == 0) && (L.y.image_stride % 4 == 0);
     dim3 grid(strips, segs, L.count);
-    gauss11_kernel<T><<<grid, NT, smem, st>>>(L, strips, segs);
+    gauss11_kernel<T><<<grid, NT, smem, st>>>(A, strips, segs);
     return cudaGetLastError();
 }
 
