@@ -162,27 +162,107 @@ __device__ __forceinline__ void stage_direct(Smem &S, const Geo &g, int64_t r0, 
     }
 }
 
+// Raw (unconverted) four-element load for the register prefetch: the
+// conversion to float happens only when the data is stored to shared memory,
+// so the load latency overlaps the barrier and the vertical pass.  `packed`:
+// one vector load (element bits packed as in memory); otherwise component k
+// holds element k's bits.  Zero outside the image.
 template <typename T>
-__device__ __forceinline__ void prefetch(float4 (&pf)[PFQ], const Geo &g, int64_t r0) {
-#pragma unroll
-    for (int i = 0; i < PFQ; ++i) {
-        const int t = threadIdx.x + i * NT;
-        int which, r, u;
-        pf[i] = t < 2 * CH * QUADS ? fetch_unit<T>(g, t, CH, r0, which, r, u) : make_float4(0.f, 0.f, 0.f, 0.f);
+__device__ __forceinline__ uint4 load_raw(const T *p, int ncols, bool packed) {
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
+    if (packed) {
+        if (sizeof(T) == 1) r.x = __ldg(reinterpret_cast<const unsigned *>(p));
+        else if (sizeof(T) == 2) {
+            const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+            r.x = v.x;
+            r.y = v.y;
+        } else r = __ldg(reinterpret_cast<const uint4 *>(p));
+        return r;
     }
+    unsigned v[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (k < ncols) {
+            if (sizeof(T) == 1) v[k] = __ldg(reinterpret_cast<const unsigned char *>(p) + k);
+            else if (sizeof(T) == 2) v[k] = __ldg(reinterpret_cast<const unsigned short *>(p) + k);
+            else v[k] = __ldg(reinterpret_cast<const unsigned *>(p) + k);
+        }
+    return make_uint4(v[0], v[1], v[2], v[3]);
 }
 
-__device__ __forceinline__ void store_prefetch(Smem &S, const float4 (&pf)[PFQ]) {
+template <typename T>
+__device__ __forceinline__ float elem_f32(unsigned bits);
+template <>
+__device__ __forceinline__ float elem_f32<uint8_t>(unsigned b) { return u8f(b, 0); }
+template <>
+__device__ __forceinline__ float elem_f32<__half>(unsigned b) {
+    return __half2float(__ushort_as_half((unsigned short)b));
+}
+template <>
+__device__ __forceinline__ float elem_f32<__nv_bfloat16>(unsigned b) { return __uint_as_float(b << 16); }
+template <>
+__device__ __forceinline__ float elem_f32<float>(unsigned b) { return __uint_as_float(b); }
+
+template <typename T>
+__device__ __forceinline__ float4 convert_raw(uint4 r, bool packed) {
+    if (!packed || sizeof(T) == 4)
+        return make_float4(elem_f32<T>(r.x), elem_f32<T>(r.y), elem_f32<T>(r.z), elem_f32<T>(r.w));
+    if (sizeof(T) == 1) return make_float4(u8f(r.x, 0), u8f(r.x, 1), u8f(r.x, 2), u8f(r.x, 3));
+    return make_float4(elem_f32<T>(r.x & 0xffffu), elem_f32<T>(r.x >> 16), elem_f32<T>(r.y & 0xffffu),
+                       elem_f32<T>(r.y >> 16));
+}
+
+// Per-thread staging units of a 16-row chunk, fixed for the whole CTA.
+struct Units {
+    unsigned dst[PFQ];       // byte offset of the shared-memory destination
+    const char *src[PFQ];    // global address of the unit in chunk row 0
+    int r[PFQ];              // row within the chunk (-1: no unit)
+    int ncols[PFQ];          // columns inside the image (0..4)
+    bool packed[PFQ];
+};
+
+template <typename T>
+__device__ __forceinline__ void make_units(Units &U, Smem &S, const Geo &g) {
 #pragma unroll
     for (int i = 0; i < PFQ; ++i) {
         const int t = threadIdx.x + i * NT;
+        U.r[i] = -1;
+        U.ncols[i] = 0;
+        U.packed[i] = false;
+        U.dst[i] = 0;
+        U.src[i] = nullptr;
         if (t < 2 * CH * QUADS) {
             const int which = t >= CH * QUADS;
             const int rem = t - which * CH * QUADS;
-            const int r = rem / QUADS;
-            put_unit(S, which, r, rem - r * QUADS, pf[i]);
+            const int r = rem / QUADS, q = rem - r * QUADS;
+            const int64_t c = g.j0 + 4 * q;
+            U.r[i] = r;
+            U.ncols[i] = (int)max((int64_t)0, min((int64_t)4, g.W - c));
+            U.packed[i] = g.vec && U.ncols[i] == 4;
+            U.dst[i] = (unsigned)(reinterpret_cast<const char *>(&(which ? S.in_y : S.in_x)[r][4 * q]) -
+                                  reinterpret_cast<const char *>(&S));
+            U.src[i] = reinterpret_cast<const char *>(static_cast<const T *>(which ? g.yb : g.xb) + r * g.rs + c);
         }
     }
+}
+
+template <typename T>
+__device__ __forceinline__ void prefetch(uint4 (&pf)[PFQ], const Units &U, const Geo &g, int64_t r0) {
+    const int64_t off = r0 * g.rs * (int64_t)sizeof(T);
+#pragma unroll
+    for (int i = 0; i < PFQ; ++i) {
+        pf[i] = make_uint4(0u, 0u, 0u, 0u);
+        if (U.r[i] >= 0 && r0 + U.r[i] < g.H && U.ncols[i] > 0)
+            pf[i] = load_raw<T>(reinterpret_cast<const T *>(U.src[i] + off), U.ncols[i], U.packed[i]);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_prefetch(Smem &S, const uint4 (&pf)[PFQ], const Units &U) {
+#pragma unroll
+    for (int i = 0; i < PFQ; ++i)
+        if (U.r[i] >= 0)
+            *reinterpret_cast<float4 *>(reinterpret_cast<char *>(&S) + U.dst[i]) = convert_raw<T>(pf[i], U.packed[i]);
 }
 
 // 2x2 average of the owned part of the staged rows (absolute rows r0..r0+nr-1).
@@ -279,7 +359,7 @@ __device__ __forceinline__ void horizontal(Smem &S, int nr, int rel0, const Taps
 // Vertical pass + SSIM formula for the 16 output rows starting at rel0
 // (relative to the segment); each thread does 4 rows of one column.
 __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, const Taps<K> &t,
-                                         const SsimConst &cc, float *map, int64_t map_ld,
+                                         const SsimConst &cc, float *map, int64_t map_ld, bool col_ok,
                                          float &sumQ, float &sumCS) {
     const int col = threadIdx.x & (TW - 1);
     const int base = rel0 + 4 * (threadIdx.x >> 6);
@@ -308,12 +388,12 @@ __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, 
             }
         }
     }
-    const int64_t c_abs = g.j0 + col;
+    const int rows_left = col_ok ? (int)(g.oend - g.o0) - base : 0;
+    float *mrow = map ? map + (g.o0 + base) * map_ld + g.j0 + col : nullptr;
     sumQ = 0.f;
     sumCS = 0.f;
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
-        const int64_t row = g.o0 + base + o;
         const float ux = mx[o] + bx, uy = my[o] + by;
         const float vx = fmaf(-mx[o], mx[o], sxx[o]);
         const float vy = fmaf(-my[o], my[o], syy[o]);
@@ -322,10 +402,10 @@ __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, 
         const float A2 = fmaf(2.f, cv, cc.C2), B2 = (vx + vy) + cc.C2;
         const float l = __fdividef(A1, B1), cs = __fdividef(A2, B2);
         const float q = l * cs;
-        if (row < g.oend && c_abs < g.OW) {
+        if (o < rows_left) {
             sumQ += q;
             sumCS += cs;
-            if (map) map[row * map_ld + c_abs] = q;
+            if (mrow) mrow[o * map_ld] = q;
         }
     }
 }
@@ -391,7 +471,10 @@ __global__ void __launch_bounds__(NT, 3) gauss11_kernel(const GaussLaunch L, int
     float *dsy = L.ds_y ? L.ds_y + img * dsn : nullptr;
 
     KSum accQ, accCS;
-    float4 pf[PFQ];
+    uint4 pf[PFQ];
+    Units U;
+    make_units<T>(U, S, g);
+    const bool col_ok = g.j0 + (threadIdx.x & (TW - 1)) < g.OW;
 
     stage_direct<T>(S, g, g.o0, FIRST);
     __syncthreads();
@@ -400,13 +483,13 @@ __global__ void __launch_bounds__(NT, 3) gauss11_kernel(const GaussLaunch L, int
     for (int c = 0; c < nchunks; ++c) {
         const bool more = c + 1 < nchunks;
         const int64_t next_r0 = g.o0 + FIRST + (int64_t)CH * c;
-        if (more) prefetch<T>(pf, g, next_r0);
+        if (more) prefetch<T>(pf, U, g, next_r0);
         __syncthreads();  // ring rows of chunk c complete; staging free
         float cq, ccs;
-        vertical(S, g, CH * c, L.taps, L.c, map, L.map_ld, cq, ccs);
+        vertical(S, g, CH * c, L.taps, L.c, map, L.map_ld, col_ok, cq, ccs);
         accQ.add(cq);
         accCS.add(ccs);
-        if (more) store_prefetch(S, pf);
+        if (more) store_prefetch<T>(S, pf, U);
         __syncthreads();  // staging complete; ring rows of chunk c consumed
         if (more) {
             if (dsx) downsample_rows(S, g, next_r0, CH, dsx, dsy);

@@ -31,42 +31,47 @@ __global__ void __launch_bounds__(NT) finalize_ssim_kernel(const double2 *partia
     if (threadIdx.x == 0) mean_out[blockIdx.x] = a * inv_n;
 }
 
-__global__ void __launch_bounds__(NT) finalize_msssim_kernel(const MsFinalize F) {
-    __shared__ double red[2 * NT / 32];
-    __shared__ double mq[GBSSIM_MAX_SCALES], mcs[GBSSIM_MAX_SCALES];
-    const int img = blockIdx.x;
-    for (int j = 0; j < F.scales; ++j) {
+// One warp per scale: warp j adds level j's partials (fp64, fixed lane
+// order), lane 0 forms the scale's factor, thread 0 combines the factors.
+__global__ void __launch_bounds__(32 * GBSSIM_MAX_SCALES) finalize_msssim_kernel(const MsFinalize F) {
+    __shared__ double term[GBSSIM_MAX_SCALES], mq[GBSSIM_MAX_SCALES], mcs[GBSSIM_MAX_SCALES];
+    const int img = blockIdx.x, j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S = F.scales;
+    if (j < S) {
         const MsLevelInfo &lv = F.lv[j];
         const double2 *p = lv.partials + (int64_t)img * lv.items_per_image;
         double a = 0.0, b = 0.0;
-        for (int i = threadIdx.x; i < lv.items_per_image; i += NT) {
+        for (int i = lane; i < lv.items_per_image; i += 32) {
             a += p[i].x;
             b += p[i].y;
         }
-        block_sum2(a, b, red);
-        if (threadIdx.x == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) {
             mq[j] = a * lv.inv_n;
             mcs[j] = b * lv.inv_n;
+            const double m = j == S - 1 ? mq[j] : mcs[j];
+            if (F.combine == GBSSIM_COMBINE_SUM) {
+                double wsum = 0.0;
+                for (int t = 0; t < S; ++t) wsum += F.exps[t];
+                term[j] = F.exps[j] / wsum * m;
+            } else {
+                term[j] = pow(m, F.exps[j]);  // NaN for m < 0 under a non-integer exponent
+            }
         }
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        const int S = F.scales;
-        double score;
-        if (F.combine == GBSSIM_COMBINE_SUM) {
-            double wsum = 0.0, acc = 0.0;
-            for (int j = 0; j < S; ++j) wsum += F.exps[j];
-            for (int j = 0; j < S; ++j) acc += F.exps[j] / wsum * (j == S - 1 ? mq[j] : mcs[j]);
-            score = acc;
-        } else {
-            double acc = 1.0;
-            for (int j = 0; j < S; ++j) acc *= pow(j == S - 1 ? mq[j] : mcs[j], F.exps[j]);
-            score = acc;  // pow of a negative base with a non-integer exponent is NaN
-        }
+        double score = F.combine == GBSSIM_COMBINE_SUM ? 0.0 : 1.0;
+        for (int t = 0; t < S; ++t) score = F.combine == GBSSIM_COMBINE_SUM ? score + term[t] : score * term[t];
         F.score_out[img] = score;
         if (F.per_scale_out)
-            for (int j = 0; j < S; ++j) {
-                F.per_scale_out[((int64_t)img * S + j) * 2] = mcs[j];
-                F.per_scale_out[((int64_t)img * S + j) * 2 + 1] = mq[j];
+            for (int t = 0; t < S; ++t) {
+                F.per_scale_out[((int64_t)img * S + t) * 2] = mcs[t];
+                F.per_scale_out[((int64_t)img * S + t) * 2 + 1] = mq[t];
             }
     }
 }
@@ -113,7 +118,7 @@ cudaError_t launch_finalize_ssim(const double2 *partials, int count, int items_p
 }
 
 cudaError_t launch_finalize_msssim(const MsFinalize &F, cudaStream_t st) {
-    finalize_msssim_kernel<<<F.count, NT, 0, st>>>(F);
+    finalize_msssim_kernel<<<F.count, 32 * F.scales, 0, st>>>(F);
     return cudaGetLastError();
 }
 
