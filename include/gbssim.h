@@ -36,6 +36,7 @@ extern "C" {
 #define GBSSIM_VERSION 1
 #define GBSSIM_MAX_SCALES 8
 #define GBSSIM_MAX_K 63
+#define GBSSIM_STATIC_SCRATCH_BYTES (1 << 20)
 
 typedef enum gbssim_status {
     GBSSIM_OK = 0,
@@ -45,7 +46,8 @@ typedef enum gbssim_status {
     GBSSIM_ERR_CUDA = -4,         /* the CUDA runtime reported an error */
     GBSSIM_ERR_DOMAIN = -5,       /* MS-SSIM product with a non-positive pooled term */
     GBSSIM_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up */
-    GBSSIM_ERR_WORKSPACE = -7     /* workspace missing or smaller than required */
+    GBSSIM_ERR_WORKSPACE = -7,    /* workspace missing or smaller than required */
+    GBSSIM_ERR_TOO_LARGE = -8     /* problem needs more than the static scratch holds */
 } gbssim_status;
 
 typedef enum gbssim_dtype {
@@ -162,6 +164,28 @@ int gbssim_ssim_pool(const float *map, int64_t h, int64_t w, int64_t ld, int32_t
 int gbssim_msssim(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
                   double *score_out, double *per_scale_out, void *workspace,
                   size_t workspace_bytes, void *stream);
+
+/* gbssim_ssim_map without a workspace argument, for callers that cannot
+ * allocate device memory: a plugin inside a host application that owns the
+ * GPU allocator and gives it only input and output buffers, or a real-time
+ * pipeline that forbids cudaMalloc after start-up because it can block and
+ * synchronise the device.  (The paper has no counterpart; this is a calling
+ * convention of this library.)
+ *   Same arguments, results and errors as gbssim_ssim_map, minus the
+ *   workspace.  Scratch comes from a static device array of
+ *   GBSSIM_STATIC_SCRATCH_BYTES (1 MiB) that every GPU loading the library
+ *   holds until exit; a problem whose gbssim_workspace_size(GBSSIM_OP_SSIM)
+ *   exceeds it is rejected with GBSSIM_ERR_TOO_LARGE before any work is
+ *   enqueued (about 430 pairs of 1920x1080 fit in one call).
+ *   The call allocates nothing.  Its first call on a device (with that
+ *   device current) looks up the array's device address once; make that
+ *   first call before any stream capture.  All calls share the array and it
+ *   keeps the last call's contents (nothing needs clearing: each call writes
+ *   every slot it reads), so calls whose GPU work overlaps race: serialise
+ *   them. */
+int gbssim_ssim_map_static(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
+                           float *map_out, int64_t map_ld, int64_t map_image_stride,
+                           double *mean_out, void *stream);
 
 /* Exact integer window sums of a uint8 pair, the quantities the paper's
  * integral images produce (Eqs. integral_image_start..integral_image_end):

@@ -232,6 +232,7 @@ const char *gbssim_status_string(int status) {
     case GBSSIM_ERR_DOMAIN: return "non-positive pooled term under a fractional exponent";
     case GBSSIM_ERR_TIMEOUT: return "bounded device wait timed out";
     case GBSSIM_ERR_WORKSPACE: return "workspace missing or too small";
+    case GBSSIM_ERR_TOO_LARGE: return "problem exceeds the static scratch of gbssim_ssim_map_static";
     }
     return "unknown status";
 }

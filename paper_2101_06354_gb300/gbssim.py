@@ -36,6 +36,8 @@ MSSSIM_EXPONENTS = (0.0448, 0.2856, 0.3001, 0.2363, 0.1333)
 
 OK, ERR_INVALID_ARG, ERR_TOO_SMALL, ERR_UNSUPPORTED, ERR_CUDA, ERR_DOMAIN, ERR_TIMEOUT, ERR_WORKSPACE = \
     0, -1, -2, -3, -4, -5, -6, -7
+ERR_TOO_LARGE = -8
+STATIC_SCRATCH_BYTES = 1 << 20
 U8, F16, BF16, F32 = 0, 1, 2, 3
 WIN_GAUSSIAN, WIN_BOX = 0, 1
 COMBINE_PRODUCT, COMBINE_SUM = 0, 1
@@ -68,6 +70,7 @@ _SIGS = {
     "gbssim_ssim_pool": ([_vp, _i64, _i64, _i64, _i32, _i64, _i32, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
     "gbssim_msssim": ([_P(Plane), _P(Plane), _P(Params), _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
     "gbssim_window_sums": ([_P(Plane), _P(Plane), _i32, _i32, _vp, _vp], ctypes.c_int),
+    "gbssim_ssim_map_static": ([_P(Plane), _P(Plane), _P(Params), _vp, _i64, _i64, _vp, _vp], ctypes.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -180,6 +183,32 @@ def ssim(x: torch.Tensor, y: torch.Tensor, return_map: bool = False, ws: torch.T
                                mp.stride(0) if mp is not None else 0,
                                mean.data_ptr(), ws.data_ptr(), ws.numel(), _stream(dev)),
            "gbssim_ssim_map")
+    if host:
+        mean = mean.cpu()
+        mp = mp.cpu() if mp is not None else None
+    return (mean, mp) if return_map else mean
+
+
+def ssim_static(x: torch.Tensor, y: torch.Tensor, return_map: bool = False, **kw):
+    """As ``ssim`` but through gbssim_ssim_map_static, which needs no
+    workspace: its scratch is a static device array inside the library, for
+    callers that cannot allocate device memory.  Calls whose GPU work overlaps
+    race on that array."""
+    host, dev, xb, yb = _prepare(x, y)
+    p = make_params(**kw)
+    px, py = plane(xb), plane(yb)
+    n = xb.shape[0]
+    mean = torch.empty(n, dtype=torch.float64, device=dev)
+    mp = None
+    if return_map:
+        oh, ow = out_shape(xb.shape[1], xb.shape[2], p.k, p.stride)
+        mp = torch.empty((n, oh, ow), dtype=torch.float32, device=dev)
+    _check(lib.gbssim_ssim_map_static(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p),
+                                      mp.data_ptr() if mp is not None else None,
+                                      mp.stride(1) if mp is not None else 0,
+                                      mp.stride(0) if mp is not None else 0,
+                                      mean.data_ptr(), _stream(dev)),
+           "gbssim_ssim_map_static")
     if host:
         mean = mean.cpu()
         mp = mp.cpu() if mp is not None else None
