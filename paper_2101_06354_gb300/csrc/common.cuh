@@ -55,6 +55,12 @@ struct Taps {
 struct TapsDyn {
     float g[GBSSIM_MAX_K];
 };
+// Taps duplicated as (w, w) pairs, the operand form of the packed f32x2
+// instructions, so the pair comes straight from the parameter bank.
+template <int K>
+struct Taps2 {
+    float2 g2[K];
+};
 
 // SSIM constants of one launch.
 struct SsimConst {
@@ -103,6 +109,7 @@ struct GaussLaunch {
     float *ds_x, *ds_y; // nullable: downsampled outputs ((H/2) x (W/2), dense)
     double2 *partials;  // items: count * strips * segments
     Taps<11> taps;
+    Taps2<11> taps2;    // filled by the launcher from `taps`
     SsimConst c;
     int seg_rows;       // output rows per work item (multiple of 16)
     bool vec;           // x/y rows aligned for 4-element vector loads (set by the launcher)

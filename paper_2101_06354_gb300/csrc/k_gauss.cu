@@ -48,26 +48,29 @@ constexpr int CH = 16;            // output rows per chunk
 constexpr int RING = 32;          // ring rows (>= CH + HALO, power of two)
 constexpr int FIRST = CH + HALO;  // input rows staged for the first chunk
 constexpr int IW = TW + HALO;     // input columns per strip (74)
-constexpr int IWP = 80;           // staged row pitch in floats
+constexpr int QUADS = (IW + 3) / 4;                 // 4-column staging units per row (19)
+constexpr int IWP = 4 * QUADS;                      // staged row pitch in (x, y) pairs (76)
 constexpr int NT = 256;
-constexpr int QUADS = (IW + 3) / 4;             // 4-column staging units per row (19)
-constexpr int PFQ = (2 * CH * QUADS + NT - 1) / NT;  // prefetched quads per thread (3)
+constexpr int PFQ = (CH * QUADS + NT - 1) / NT;     // prefetched units per thread (2)
 // The vertical pass of a thread reads ring rows base..base+13 with base a
 // multiple of 4 below RING; rows 0..DUP-1 are also stored at RING..RING+DUP-1
 // so those reads never wrap.
 constexpr int DUP = 10;
 constexpr int RROWS = RING + DUP;
 
+// x and y travel together as float2 pairs so that every moment of the pair
+// is one packed f32x2 instruction (FFMA2 / FADD2 / FMUL2 on sm_100+).
 struct __align__(16) Smem {
-    float in_x[FIRST][IWP];
-    float in_y[FIRST][IWP];
-    float mu_x[RROWS][TW];
-    float mu_y[RROWS][TW];
-    float v_x[RROWS][TW];
-    float v_y[RROWS][TW];
-    float c_xy[RROWS][TW];
+    float2 in[FIRST][IWP];   // staged input rows, (x, y) per column
+    float2 mu[RROWS][TW];    // row-window means (mu_x, mu_y)
+    float2 v[RROWS][TW];     // row-window variances (v_x, v_y)
+    float c[RROWS][TW];      // row-window covariances
     float red[2 * NT / 32];
 };
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 struct Geo {
     const void *xb, *yb;
@@ -79,94 +82,16 @@ struct Geo {
     bool vec;          // rows and strip start aligned for 4-element vector loads
 };
 
-// Four consecutive elements (columns c..c+3 of one row) as floats; zero
-// outside the image.  `vec`: the row start and c are aligned for one vector
-// load of four elements.
+// byte k of w placed in the mantissa of 2^23, minus 2^23: exact for 0..255
 __device__ __forceinline__ float u8f(unsigned w, int k) {
-    // byte k of w placed in the mantissa of 2^23, minus 2^23: exact for 0..255
     return __int_as_float(__byte_perm(w, 0x4B000000u, 0x7540u + k)) - 8388608.0f;
 }
-template <typename T>
-__device__ __forceinline__ float4 load_quad(const T *row, int64_t c, int64_t W, bool vec);
-template <>
-__device__ __forceinline__ float4 load_quad<uint8_t>(const uint8_t *row, int64_t c, int64_t W, bool vec) {
-    if (vec && c + 4 <= W) {
-        const unsigned w = __ldg(reinterpret_cast<const unsigned *>(row + c));
-        return make_float4(u8f(w, 0), u8f(w, 1), u8f(w, 2), u8f(w, 3));
-    }
-    float v[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = c + k < W ? (float)__ldg(row + c + k) : 0.f;
-    return make_float4(v[0], v[1], v[2], v[3]);
-}
-template <>
-__device__ __forceinline__ float4 load_quad<float>(const float *row, int64_t c, int64_t W, bool vec) {
-    if (vec && c + 4 <= W) return __ldg(reinterpret_cast<const float4 *>(row + c));
-    float v[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = c + k < W ? __ldg(row + c + k) : 0.f;
-    return make_float4(v[0], v[1], v[2], v[3]);
-}
-template <>
-__device__ __forceinline__ float4 load_quad<__half>(const __half *row, int64_t c, int64_t W, bool vec) {
-    if (vec && c + 4 <= W) {
-        const uint2 u = __ldg(reinterpret_cast<const uint2 *>(row + c));
-        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
-        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
-        return make_float4(a.x, a.y, b.x, b.y);
-    }
-    float v[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = c + k < W ? load_f32<__half>(row + c + k) : 0.f;
-    return make_float4(v[0], v[1], v[2], v[3]);
-}
-template <>
-__device__ __forceinline__ float4 load_quad<__nv_bfloat16>(const __nv_bfloat16 *row, int64_t c, int64_t W,
-                                                           bool vec) {
-    if (vec && c + 4 <= W) {
-        const uint2 u = __ldg(reinterpret_cast<const uint2 *>(row + c));
-        return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
-                           __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
-    }
-    float v[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = c + k < W ? load_f32<__nv_bfloat16>(row + c + k) : 0.f;
-    return make_float4(v[0], v[1], v[2], v[3]);
-}
 
-// Staging unit t (of 2*nr*QUADS): image (x or y), row within the block, quad.
-template <typename T>
-__device__ __forceinline__ float4 fetch_unit(const Geo &g, int t, int nr, int64_t r0, int &which, int &r,
-                                             int &u) {
-    which = t >= nr * QUADS;
-    const int rem = t - which * nr * QUADS;
-    r = rem / QUADS;
-    u = rem - r * QUADS;
-    const int64_t row = r0 + r;
-    if (row >= g.H) return make_float4(0.f, 0.f, 0.f, 0.f);
-    const T *base = static_cast<const T *>(which ? g.yb : g.xb) + row * g.rs;
-    return load_quad<T>(base, g.j0 + 4 * u, g.W, g.vec);
-}
-
-__device__ __forceinline__ void put_unit(Smem &S, int which, int r, int u, float4 v) {
-    *reinterpret_cast<float4 *>(&(which ? S.in_y : S.in_x)[r][4 * u]) = v;
-}
-
-// Stage `nr` input rows starting at absolute row r0 into in_x/in_y rows 0..nr-1.
-template <typename T>
-__device__ __forceinline__ void stage_direct(Smem &S, const Geo &g, int64_t r0, int nr) {
-    for (int t = threadIdx.x; t < 2 * nr * QUADS; t += NT) {
-        int which, r, u;
-        const float4 v = fetch_unit<T>(g, t, nr, r0, which, r, u);
-        put_unit(S, which, r, u, v);
-    }
-}
-
-// Raw (unconverted) four-element load for the register prefetch: the
-// conversion to float happens only when the data is stored to shared memory,
-// so the load latency overlaps the barrier and the vertical pass.  `packed`:
-// one vector load (element bits packed as in memory); otherwise component k
-// holds element k's bits.  Zero outside the image.
+// Raw (unconverted) load of four consecutive elements.  `packed`: one
+// vector load, element bits as in memory; otherwise component k holds
+// element k's bits (only the first `ncols` are read).  Keeping the data raw
+// lets the register prefetch defer the conversion until after the barrier,
+// so the load latency overlaps the vertical pass.
 template <typename T>
 __device__ __forceinline__ uint4 load_raw(const T *p, int ncols, bool packed) {
     uint4 r = make_uint4(0u, 0u, 0u, 0u);
@@ -212,146 +137,166 @@ __device__ __forceinline__ float4 convert_raw(uint4 r, bool packed) {
                        elem_f32<T>(r.y >> 16));
 }
 
+// Store one staged unit: columns 4q..4q+3 of x and y, interleaved.
+__device__ __forceinline__ void put_unit(Smem &S, int r, int q, float4 a, float4 b) {
+    float4 *d = reinterpret_cast<float4 *>(&S.in[r][4 * q]);
+    d[0] = make_float4(a.x, b.x, a.y, b.y);
+    d[1] = make_float4(a.z, b.z, a.w, b.w);
+}
+
+// Stage `nr` input rows starting at absolute row r0 into in rows 0..nr-1
+// (used once per segment, for the first FIRST rows).
+template <typename T>
+__device__ __forceinline__ void stage_direct(Smem &S, const Geo &g, int64_t r0, int nr) {
+    for (int t = threadIdx.x; t < nr * QUADS; t += NT) {
+        const int r = t / QUADS, q = t - r * QUADS;
+        const int64_t row = r0 + r, c = g.j0 + 4 * q;
+        const int ncols = (int)max((int64_t)0, min((int64_t)4, g.W - c));
+        const bool packed = g.vec && ncols == 4;
+        uint4 rx = make_uint4(0u, 0u, 0u, 0u), ry = rx;
+        if (row < g.H && ncols > 0) {
+            rx = load_raw<T>(static_cast<const T *>(g.xb) + row * g.rs + c, ncols, packed);
+            ry = load_raw<T>(static_cast<const T *>(g.yb) + row * g.rs + c, ncols, packed);
+        }
+        put_unit(S, r, q, convert_raw<T>(rx, packed), convert_raw<T>(ry, packed));
+    }
+}
+
 // Per-thread staging units of a 16-row chunk, fixed for the whole CTA.
 struct Units {
-    unsigned dst[PFQ];       // byte offset of the shared-memory destination
-    const char *src[PFQ];    // global address of the unit in chunk row 0
-    int r[PFQ];              // row within the chunk (-1: no unit)
-    int ncols[PFQ];          // columns inside the image (0..4)
+    int64_t off[PFQ];  // element offset of the unit in chunk row 0 (from the image start)
+    int r[PFQ];        // row within the chunk (-1: no unit)
+    int q[PFQ];        // quad
+    int ncols[PFQ];    // columns inside the image (0..4)
     bool packed[PFQ];
 };
 
-template <typename T>
-__device__ __forceinline__ void make_units(Units &U, Smem &S, const Geo &g) {
+__device__ __forceinline__ void make_units(Units &U, const Geo &g) {
 #pragma unroll
     for (int i = 0; i < PFQ; ++i) {
         const int t = threadIdx.x + i * NT;
         U.r[i] = -1;
+        U.q[i] = 0;
         U.ncols[i] = 0;
         U.packed[i] = false;
-        U.dst[i] = 0;
-        U.src[i] = nullptr;
-        if (t < 2 * CH * QUADS) {
-            const int which = t >= CH * QUADS;
-            const int rem = t - which * CH * QUADS;
-            const int r = rem / QUADS, q = rem - r * QUADS;
+        U.off[i] = 0;
+        if (t < CH * QUADS) {
+            const int r = t / QUADS, q = t - r * QUADS;
             const int64_t c = g.j0 + 4 * q;
             U.r[i] = r;
+            U.q[i] = q;
             U.ncols[i] = (int)max((int64_t)0, min((int64_t)4, g.W - c));
             U.packed[i] = g.vec && U.ncols[i] == 4;
-            U.dst[i] = (unsigned)(reinterpret_cast<const char *>(&(which ? S.in_y : S.in_x)[r][4 * q]) -
-                                  reinterpret_cast<const char *>(&S));
-            U.src[i] = reinterpret_cast<const char *>(static_cast<const T *>(which ? g.yb : g.xb) + r * g.rs + c);
+            U.off[i] = r * g.rs + c;
         }
     }
 }
 
 template <typename T>
-__device__ __forceinline__ void prefetch(uint4 (&pf)[PFQ], const Units &U, const Geo &g, int64_t r0) {
-    const int64_t off = r0 * g.rs * (int64_t)sizeof(T);
+__device__ __forceinline__ void prefetch(uint4 (&px)[PFQ], uint4 (&py)[PFQ], const Units &U, const Geo &g,
+                                         int64_t r0) {
+    const int64_t base = r0 * g.rs;
 #pragma unroll
     for (int i = 0; i < PFQ; ++i) {
-        pf[i] = make_uint4(0u, 0u, 0u, 0u);
-        if (U.r[i] >= 0 && r0 + U.r[i] < g.H && U.ncols[i] > 0)
-            pf[i] = load_raw<T>(reinterpret_cast<const T *>(U.src[i] + off), U.ncols[i], U.packed[i]);
+        px[i] = py[i] = make_uint4(0u, 0u, 0u, 0u);
+        if (U.r[i] >= 0 && r0 + U.r[i] < g.H && U.ncols[i] > 0) {
+            px[i] = load_raw<T>(static_cast<const T *>(g.xb) + base + U.off[i], U.ncols[i], U.packed[i]);
+            py[i] = load_raw<T>(static_cast<const T *>(g.yb) + base + U.off[i], U.ncols[i], U.packed[i]);
+        }
     }
 }
 
 template <typename T>
-__device__ __forceinline__ void store_prefetch(Smem &S, const uint4 (&pf)[PFQ], const Units &U) {
+__device__ __forceinline__ void store_prefetch(Smem &S, const uint4 (&px)[PFQ], const uint4 (&py)[PFQ],
+                                               const Units &U) {
 #pragma unroll
     for (int i = 0; i < PFQ; ++i)
         if (U.r[i] >= 0)
-            *reinterpret_cast<float4 *>(reinterpret_cast<char *>(&S) + U.dst[i]) = convert_raw<T>(pf[i], U.packed[i]);
+            put_unit(S, U.r[i], U.q[i], convert_raw<T>(px[i], U.packed[i]), convert_raw<T>(py[i], U.packed[i]));
 }
 
 // 2x2 average of the owned part of the staged rows (absolute rows r0..r0+nr-1).
 __device__ __forceinline__ void downsample_rows(const Smem &S, const Geo &g, int64_t r0, int nr,
                                                 float *dsx, float *dsy) {
     const int64_t Hh = g.H >> 1, Wh = g.W >> 1;
-    constexpr int QC = (IW + 1) / 2;  // 37 column pairs staged
+    constexpr int QC = IW / 2;  // 37 column pairs staged
     for (int t = threadIdx.x; t < (nr >> 1) * QC; t += NT) {
         const int p = t / QC, q = t - p * QC;
         const int64_t r = r0 + 2 * p, c = g.j0 + 2 * q;
         if (r >= g.own_r1 || c >= g.own_c1) continue;
         const int64_t R = r >> 1, C = c >> 1;
         if (R >= Hh || C >= Wh) continue;
-        const float ax = (S.in_x[2 * p][2 * q] + S.in_x[2 * p][2 * q + 1]) +
-                         (S.in_x[2 * p + 1][2 * q] + S.in_x[2 * p + 1][2 * q + 1]);
-        const float ay = (S.in_y[2 * p][2 * q] + S.in_y[2 * p][2 * q + 1]) +
-                         (S.in_y[2 * p + 1][2 * q] + S.in_y[2 * p + 1][2 * q + 1]);
-        dsx[R * Wh + C] = 0.25f * ax;
-        dsy[R * Wh + C] = 0.25f * ay;
+        const float4 top = *reinterpret_cast<const float4 *>(&S.in[2 * p][2 * q]);
+        const float4 bot = *reinterpret_cast<const float4 *>(&S.in[2 * p + 1][2 * q]);
+        // top = (x00, y00, x01, y01), bot = (x10, y10, x11, y11)
+        dsx[R * Wh + C] = 0.25f * ((top.x + top.z) + (bot.x + bot.z));
+        dsy[R * Wh + C] = 0.25f * ((top.y + top.w) + (bot.y + bot.w));
     }
 }
 
 // Horizontal pass over staged rows 0..nr-1; results go to ring rows
 // (rel0 + r) & (RING-1), where rel0 is the row index relative to the segment.
-__device__ __forceinline__ void horizontal(Smem &S, int nr, int rel0, const Taps<K> &t) {
+__device__ __forceinline__ void horizontal(Smem &S, int nr, int rel0, const Taps<K> &t, const Taps2<K> &t2) {
     for (int task = threadIdx.x; task < nr * (TW / 4); task += NT) {
         const int r = task >> 4, g4 = (task & 15) * 4;
-        float xv[14], yv[14];
-        {
-            const float4 a0 = *reinterpret_cast<const float4 *>(&S.in_x[r][g4]);
-            const float4 a1 = *reinterpret_cast<const float4 *>(&S.in_x[r][g4 + 4]);
-            const float4 a2 = *reinterpret_cast<const float4 *>(&S.in_x[r][g4 + 8]);
-            const float2 a3 = *reinterpret_cast<const float2 *>(&S.in_x[r][g4 + 12]);
-            const float4 b0 = *reinterpret_cast<const float4 *>(&S.in_y[r][g4]);
-            const float4 b1 = *reinterpret_cast<const float4 *>(&S.in_y[r][g4 + 4]);
-            const float4 b2 = *reinterpret_cast<const float4 *>(&S.in_y[r][g4 + 8]);
-            const float2 b3 = *reinterpret_cast<const float2 *>(&S.in_y[r][g4 + 12]);
-            xv[0] = a0.x; xv[1] = a0.y; xv[2] = a0.z; xv[3] = a0.w;
-            xv[4] = a1.x; xv[5] = a1.y; xv[6] = a1.z; xv[7] = a1.w;
-            xv[8] = a2.x; xv[9] = a2.y; xv[10] = a2.z; xv[11] = a2.w;
-            xv[12] = a3.x; xv[13] = a3.y;
-            yv[0] = b0.x; yv[1] = b0.y; yv[2] = b0.z; yv[3] = b0.w;
-            yv[4] = b1.x; yv[5] = b1.y; yv[6] = b1.z; yv[7] = b1.w;
-            yv[8] = b2.x; yv[9] = b2.y; yv[10] = b2.z; yv[11] = b2.w;
-            yv[12] = b3.x; yv[13] = b3.y;
+        float2 p[14];
+        const float4 *src = reinterpret_cast<const float4 *>(&S.in[r][g4]);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            const float4 v = src[k];
+            p[2 * k] = make_float2(v.x, v.y);
+            p[2 * k + 1] = make_float2(v.z, v.w);
         }
         // shift: pixel 7 lies in the windows of outputs 0..3 (centres 5..8)
-        const float cx = xv[7], cy = yv[7];
-        float mx[4], my[4], sxx[4], syy[4], sxy[4];
+        const float2 nc = make_float2(-p[7].x, -p[7].y);
+        float2 m[4], sq[4];
+        float sxy[4];
 #pragma unroll
-        for (int o = 0; o < 4; ++o) mx[o] = my[o] = sxx[o] = syy[o] = sxy[o] = 0.f;
+        for (int o = 0; o < 4; ++o) {
+            m[o] = sq[o] = make_float2(0.f, 0.f);
+            sxy[o] = 0.f;
+        }
 #pragma unroll
         for (int i = 0; i < 14; ++i) {
-            const float dx = xv[i] - cx, dy = yv[i] - cy;
-            const float pxx = dx * dx, pyy = dy * dy, pxy = dx * dy;
+            const float2 d = add2(p[i], nc);  // (dx, dy)
+            const float2 dd = mul2(d, d);     // (dx^2, dy^2)
+            const float pxy = d.x * d.y;
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
                 const int n = i - o;
                 if (n >= 0 && n < K) {
-                    const float w = t.g[n];
-                    mx[o] = fmaf(w, dx, mx[o]);
-                    my[o] = fmaf(w, dy, my[o]);
-                    sxx[o] = fmaf(w, pxx, sxx[o]);
-                    syy[o] = fmaf(w, pyy, syy[o]);
-                    sxy[o] = fmaf(w, pxy, sxy[o]);
+                    m[o] = fma2(t2.g2[n], d, m[o]);
+                    sq[o] = fma2(t2.g2[n], dd, sq[o]);
+                    sxy[o] = fmaf(t.g[n], pxy, sxy[o]);
                 }
             }
         }
         const int slot = (rel0 + r) & (RING - 1);
-        float4 o_mx, o_my, o_vx, o_vy, o_c;
-        o_mx.x = mx[0] + cx; o_mx.y = mx[1] + cx; o_mx.z = mx[2] + cx; o_mx.w = mx[3] + cx;
-        o_my.x = my[0] + cy; o_my.y = my[1] + cy; o_my.z = my[2] + cy; o_my.w = my[3] + cy;
-        o_vx.x = fmaf(-mx[0], mx[0], sxx[0]); o_vx.y = fmaf(-mx[1], mx[1], sxx[1]);
-        o_vx.z = fmaf(-mx[2], mx[2], sxx[2]); o_vx.w = fmaf(-mx[3], mx[3], sxx[3]);
-        o_vy.x = fmaf(-my[0], my[0], syy[0]); o_vy.y = fmaf(-my[1], my[1], syy[1]);
-        o_vy.z = fmaf(-my[2], my[2], syy[2]); o_vy.w = fmaf(-my[3], my[3], syy[3]);
-        o_c.x = fmaf(-mx[0], my[0], sxy[0]); o_c.y = fmaf(-mx[1], my[1], sxy[1]);
-        o_c.z = fmaf(-mx[2], my[2], sxy[2]); o_c.w = fmaf(-mx[3], my[3], sxy[3]);
-        *reinterpret_cast<float4 *>(&S.mu_x[slot][g4]) = o_mx;
-        *reinterpret_cast<float4 *>(&S.mu_y[slot][g4]) = o_my;
-        *reinterpret_cast<float4 *>(&S.v_x[slot][g4]) = o_vx;
-        *reinterpret_cast<float4 *>(&S.v_y[slot][g4]) = o_vy;
-        *reinterpret_cast<float4 *>(&S.c_xy[slot][g4]) = o_c;
-        if (slot < DUP) {
-            *reinterpret_cast<float4 *>(&S.mu_x[slot + RING][g4]) = o_mx;
-            *reinterpret_cast<float4 *>(&S.mu_y[slot + RING][g4]) = o_my;
-            *reinterpret_cast<float4 *>(&S.v_x[slot + RING][g4]) = o_vx;
-            *reinterpret_cast<float4 *>(&S.v_y[slot + RING][g4]) = o_vy;
-            *reinterpret_cast<float4 *>(&S.c_xy[slot + RING][g4]) = o_c;
+        const float2 cc = make_float2(-nc.x, -nc.y);
+        float2 om[4], ov[4];
+        float oc[4];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            om[o] = add2(m[o], cc);
+            ov[o] = fma2(make_float2(-m[o].x, -m[o].y), m[o], sq[o]);
+            oc[o] = fmaf(-m[o].x, m[o].y, sxy[o]);
+        }
+        const float4 m01 = make_float4(om[0].x, om[0].y, om[1].x, om[1].y);
+        const float4 m23 = make_float4(om[2].x, om[2].y, om[3].x, om[3].y);
+        const float4 v01 = make_float4(ov[0].x, ov[0].y, ov[1].x, ov[1].y);
+        const float4 v23 = make_float4(ov[2].x, ov[2].y, ov[3].x, ov[3].y);
+        const float4 c4 = make_float4(oc[0], oc[1], oc[2], oc[3]);
+#pragma unroll
+        for (int rep = 0; rep < 2; ++rep) {
+            const int sl = rep ? slot + RING : slot;
+            if (rep && slot >= DUP) break;
+            float4 *dm = reinterpret_cast<float4 *>(&S.mu[sl][g4]);
+            float4 *dv = reinterpret_cast<float4 *>(&S.v[sl][g4]);
+            dm[0] = m01;
+            dm[1] = m23;
+            dv[0] = v01;
+            dv[1] = v23;
+            *reinterpret_cast<float4 *>(&S.c[sl][g4]) = c4;
         }
     }
 }
@@ -359,32 +304,33 @@ __device__ __forceinline__ void horizontal(Smem &S, int nr, int rel0, const Taps
 // Vertical pass + SSIM formula for the 16 output rows starting at rel0
 // (relative to the segment); each thread does 4 rows of one column.
 __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, const Taps<K> &t,
-                                         const SsimConst &cc, float *map, int64_t map_ld, bool col_ok,
+                                         const Taps2<K> &t2, const SsimConst &cc, float *map, int64_t map_ld, bool col_ok,
                                          float &sumQ, float &sumCS) {
     const int col = threadIdx.x & (TW - 1);
     const int base = rel0 + 4 * (threadIdx.x >> 6);
     const int b0 = base & (RING - 1);  // multiple of 4; b0 + 13 < RROWS
-    const float bx = S.mu_x[b0 + 7][col], by = S.mu_y[b0 + 7][col];
-    float mx[4], my[4], sxx[4], syy[4], sxy[4];
+    const float2 b = S.mu[b0 + 7][col];
+    const float2 nb = make_float2(-b.x, -b.y);
+    float2 m[4], sq[4];
+    float sxy[4];
 #pragma unroll
-    for (int o = 0; o < 4; ++o) mx[o] = my[o] = sxx[o] = syy[o] = sxy[o] = 0.f;
+    for (int o = 0; o < 4; ++o) {
+        m[o] = sq[o] = make_float2(0.f, 0.f);
+        sxy[o] = 0.f;
+    }
 #pragma unroll
     for (int i = 0; i < 14; ++i) {
         const int s = b0 + i;
-        const float ex = S.mu_x[s][col] - bx, ey = S.mu_y[s][col] - by;
-        const float qxx = fmaf(ex, ex, S.v_x[s][col]);
-        const float qyy = fmaf(ey, ey, S.v_y[s][col]);
-        const float qxy = fmaf(ex, ey, S.c_xy[s][col]);
+        const float2 e = add2(S.mu[s][col], nb);   // (ex, ey)
+        const float2 q = fma2(e, e, S.v[s][col]);  // (ex^2 + v_x, ey^2 + v_y)
+        const float qxy = fmaf(e.x, e.y, S.c[s][col]);
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
             const int n = i - o;
             if (n >= 0 && n < K) {
-                const float w = t.g[n];
-                mx[o] = fmaf(w, ex, mx[o]);
-                my[o] = fmaf(w, ey, my[o]);
-                sxx[o] = fmaf(w, qxx, sxx[o]);
-                syy[o] = fmaf(w, qyy, syy[o]);
-                sxy[o] = fmaf(w, qxy, sxy[o]);
+                m[o] = fma2(t2.g2[n], e, m[o]);
+                sq[o] = fma2(t2.g2[n], q, sq[o]);
+                sxy[o] = fmaf(t.g[n], qxy, sxy[o]);
             }
         }
     }
@@ -394,18 +340,17 @@ __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, 
     sumCS = 0.f;
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
-        const float ux = mx[o] + bx, uy = my[o] + by;
-        const float vx = fmaf(-mx[o], mx[o], sxx[o]);
-        const float vy = fmaf(-my[o], my[o], syy[o]);
-        const float cv = fmaf(-mx[o], my[o], sxy[o]);
-        const float A1 = fmaf(2.f * ux, uy, cc.C1), B1 = fmaf(ux, ux, fmaf(uy, uy, cc.C1));
-        const float A2 = fmaf(2.f, cv, cc.C2), B2 = (vx + vy) + cc.C2;
+        const float2 u = add2(m[o], b);                                        // (mu_x, mu_y)
+        const float2 var = fma2(make_float2(-m[o].x, -m[o].y), m[o], sq[o]);  // (s_x^2, s_y^2)
+        const float cv = fmaf(-m[o].x, m[o].y, sxy[o]);
+        const float A1 = fmaf(2.f * u.x, u.y, cc.C1), B1 = fmaf(u.x, u.x, fmaf(u.y, u.y, cc.C1));
+        const float A2 = fmaf(2.f, cv, cc.C2), B2 = (var.x + var.y) + cc.C2;
         const float l = __fdividef(A1, B1), cs = __fdividef(A2, B2);
-        const float q = l * cs;
+        const float qv = l * cs;
         if (o < rows_left) {
-            sumQ += q;
+            sumQ += qv;
             sumCS += cs;
-            if (mrow) mrow[o * map_ld] = q;
+            if (mrow) mrow[o * map_ld] = qv;
         }
     }
 }
@@ -463,37 +408,37 @@ __global__ void __launch_bounds__(NT, 3) gauss11_kernel(const GaussLaunch L, int
     g.oend = min(g.o0 + (int64_t)L.seg_rows, g.OH);
     g.own_r1 = (seg == segs - 1) ? g.H : g.o0 + L.seg_rows;
     g.own_c1 = (strip == strips - 1) ? g.W : g.j0 + TW;
-    const int nchunks = (int)((g.oend - g.o0 + CH - 1) / CH);
     g.vec = L.vec;
+    const int nchunks = (int)((g.oend - g.o0 + CH - 1) / CH);
     float *map = L.map ? L.map + img * L.map_is : nullptr;
     const int64_t dsn = (g.H >> 1) * (g.W >> 1);
     float *dsx = L.ds_x ? L.ds_x + img * dsn : nullptr;
     float *dsy = L.ds_y ? L.ds_y + img * dsn : nullptr;
 
     KSum accQ, accCS;
-    uint4 pf[PFQ];
+    uint4 px[PFQ], py[PFQ];
     Units U;
-    make_units<T>(U, S, g);
+    make_units(U, g);
     const bool col_ok = g.j0 + (threadIdx.x & (TW - 1)) < g.OW;
 
     stage_direct<T>(S, g, g.o0, FIRST);
     __syncthreads();
     if (dsx) downsample_rows(S, g, g.o0, FIRST, dsx, dsy);
-    horizontal(S, FIRST, 0, L.taps);
+    horizontal(S, FIRST, 0, L.taps, L.taps2);
     for (int c = 0; c < nchunks; ++c) {
         const bool more = c + 1 < nchunks;
         const int64_t next_r0 = g.o0 + FIRST + (int64_t)CH * c;
-        if (more) prefetch<T>(pf, U, g, next_r0);
+        if (more) prefetch<T>(px, py, U, g, next_r0);
         __syncthreads();  // ring rows of chunk c complete; staging free
         float cq, ccs;
-        vertical(S, g, CH * c, L.taps, L.c, map, L.map_ld, col_ok, cq, ccs);
+        vertical(S, g, CH * c, L.taps, L.taps2, L.c, map, L.map_ld, col_ok, cq, ccs);
         accQ.add(cq);
         accCS.add(ccs);
-        if (more) store_prefetch<T>(S, pf, U);
+        if (more) store_prefetch<T>(S, px, py, U);
         __syncthreads();  // staging complete; ring rows of chunk c consumed
         if (more) {
             if (dsx) downsample_rows(S, g, next_r0, CH, dsx, dsy);
-            horizontal(S, CH, FIRST + CH * c, L.taps);
+            horizontal(S, CH, FIRST + CH * c, L.taps, L.taps2);
         }
     }
     double a, b;
@@ -591,6 +536,7 @@ cudaError_t launch_gauss11_t(const GaussLaunch &L, cudaStream_t st) {
     int strips, segs;
     gauss11_items(L.x.H, L.x.W, L.seg_rows, &strips, &segs);
     GaussLaunch A = L;
+    for (int n = 0; n < 11; ++n) A.taps2.g2[n] = make_float2(L.taps.g[n], L.taps.g[n]);
     const uintptr_t vbytes = 4 * sizeof(T);  // one 4-element vector
     A.vec = ((uintptr_t)L.x.data % vbytes == 0) && ((uintptr_t)L.y.data % vbytes == 0) &&
             (L.x.row_stride % 4 == 0) && (L.x.image_stride % 4 == 0) && (L.y.image_stride % 4 == 0);
