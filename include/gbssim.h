@@ -37,6 +37,7 @@ extern "C" {
 #define GBSSIM_MAX_SCALES 8
 #define GBSSIM_MAX_K 63
 #define GBSSIM_STATIC_SCRATCH_BYTES (1 << 20)
+#define GBSSIM_MAX_K_BACKWARD 31
 
 typedef enum gbssim_status {
     GBSSIM_OK = 0,
@@ -164,6 +165,32 @@ int gbssim_ssim_pool(const float *map, int64_t h, int64_t w, int64_t ld, int32_t
 int gbssim_msssim(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
                   double *score_out, double *per_scale_out, void *workspace,
                   size_t workspace_bytes, void *stream);
+
+/* Gradient of the pooled score with respect to the distorted image y, for
+ * SSIM (multiscale = 0: score = MSSIM, Background section) or MS-SSIM
+ * (multiscale = 1: score as gbssim_msssim).  The paper defines the score,
+ * not its derivative; this is the chain rule of those definitions: each
+ * window position p contributes w(q - p) [dQ/dmu_y + 2 (y(q) - mu_y) dQ/ds_y^2
+ * + (x(q) - mu_x) dQ/ds_xy] to pixel q, mean pooling divides by the map size,
+ * MS-SSIM multiplies level j by d score / d m_j (= score beta_j / m_j for the
+ * product) and carries coarser levels to finer ones through the adjoint of
+ * 2x2 average pooling (a quarter of each coarse gradient to each of its four
+ * pixels).  The window moments are recomputed, nothing from a forward call is
+ * reused.
+ *   grad_y[b] = grad_scale * g_b * d score_b / d y_b, where g_b = 1 when
+ *   grad_out is NULL, else grad_out[grad_out_per_image ? b : 0] (device
+ *   doubles, e.g. the incoming gradient of a loss).  grad_y (device) has
+ *   dtype grad_dtype (F32, F16 or BF16), rows grad_ld elements apart, images
+ *   grad_image_stride apart; every pixel of every image is written.
+ *   score_out: nullable, x.count doubles, the scores themselves.
+ *   Requires stride == 1 and k <= GBSSIM_MAX_K_BACKWARD (else
+ *   GBSSIM_ERR_UNSUPPORTED); workspace of gbssim_workspace_size with
+ *   GBSSIM_OP_BACKWARD (multiscale = 0) or GBSSIM_OP_BACKWARD_MS. */
+int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
+                         int32_t multiscale, double grad_scale, const double *grad_out,
+                         int32_t grad_out_per_image, void *grad_y, int32_t grad_dtype, int64_t grad_ld,
+                         int64_t grad_image_stride, double *score_out, void *workspace,
+                         size_t workspace_bytes, void *stream);
 
 /* gbssim_ssim_map without a workspace argument, for callers that cannot
  * allocate device memory: a plugin inside a host application that owns the

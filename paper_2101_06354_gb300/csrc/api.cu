@@ -123,7 +123,8 @@ struct MsPlan {
     size_t bytes;
 };
 
-int plan_levels(const gbssim_plane *x, const gbssim_params *p, int scales, MsPlan *P) {
+int plan_levels(const gbssim_plane *x, const gbssim_params *p, int scales, MsPlan *P,
+                bool float_path = false) {
     size_t off = 0;
     int64_t H = x->height, W = x->width;
     for (int j = 0; j < scales; ++j) {
@@ -133,6 +134,7 @@ int plan_levels(const gbssim_plane *x, const gbssim_params *p, int scales, MsPla
         L.W = W;
         const int dtype = j == 0 ? x->dtype : GBSSIM_F32;
         L.path = pick_path(dtype, p);
+        if (float_path && L.path == PATH_BOX_U8) L.path = PATH_GENERIC;
         L.seg_rows = 0;
         L.items = level_items(L.path, H, W, x->count, p, &L.seg_rows);
         L.part_off = off;
@@ -154,8 +156,13 @@ int plan_levels(const gbssim_plane *x, const gbssim_params *p, int scales, MsPla
 // partials/map as given; ds_x/ds_y (nullable) receive the next level.
 cudaError_t run_level(const Level &L, const ImgDesc &dx, const ImgDesc &dy, int dtype, int count,
                       const gbssim_params *p, float *map, int64_t map_ld, int64_t map_is,
-                      double2 *partials, float *ds_x, float *ds_y, cudaStream_t st) {
+                      double2 *partials, float *ds_x, float *ds_y, cudaStream_t st,
+                      const CoefOut *co = nullptr) {
     const SsimConst cc = make_const(p);
+    CoefOut none;
+    none.coef = nullptr;
+    none.which = 0;
+    none.sx = none.sy = 0.f;
     cudaError_t e = cudaSuccess;
     bool fused_ds = false;
     if (L.path == PATH_GAUSS11) {
@@ -173,6 +180,7 @@ cudaError_t run_level(const Level &L, const ImgDesc &dx, const ImgDesc &dy, int 
         make_taps(p, G.taps.g);
         G.c = cc;
         G.seg_rows = L.seg_rows;
+        G.co = co ? *co : none;
         e = launch_gauss11(G, st);
         fused_ds = true;
     } else if (L.path == PATH_BOX_U8) {
@@ -207,6 +215,7 @@ cudaError_t run_level(const Level &L, const ImgDesc &dx, const ImgDesc &dy, int 
         memset(G.taps.g, 0, sizeof G.taps.g);
         make_taps(p, G.taps.g);
         G.c = cc;
+        G.co = co ? *co : none;
         e = launch_generic(G, st);
     }
     if (e != cudaSuccess) return e;
@@ -216,6 +225,90 @@ cudaError_t run_level(const Level &L, const ImgDesc &dx, const ImgDesc &dy, int 
         e = launch_downsample(dy, dtype, count, ds_y, st);
     }
     return e;
+}
+
+// MS-SSIM forward over a planned workspace: level kernels (pyramid fused
+// where the path allows), then the finaliser.  Shared by gbssim_msssim and
+// the MS-SSIM backward.
+int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
+                          const MsPlan &P, char *ws, double *score_out, double *per_scale_out,
+                          cudaStream_t st) {
+    const int S = p->scales, n = x->count;
+    ImgDesc dx = desc_of(x), dy = desc_of(y);
+    int dtype = x->dtype;
+    MsFinalize F;
+    memset(&F, 0, sizeof F);
+    for (int j = 0; j < S; ++j) {
+        const Level &L = P.lv[j];
+        float *ds_x = nullptr, *ds_y = nullptr;
+        if (j + 1 < S) {
+            const Level &N = P.lv[j + 1];
+            ds_x = (float *)(ws + N.plane_off);
+            ds_y = ds_x + (size_t)N.H * N.W * n;
+        }
+        double2 *part = (double2 *)(ws + L.part_off);
+        cudaError_t e = run_level(L, dx, dy, dtype, n, p, nullptr, 0, 0, part, ds_x, ds_y, st);
+        if (e != cudaSuccess) return GBSSIM_ERR_CUDA;
+        const int64_t OH = out_dim(L.H, p->k, p->stride), OW = out_dim(L.W, p->k, p->stride);
+        F.lv[j].partials = part;
+        F.lv[j].items_per_image = L.items;
+        F.lv[j].inv_n = 1.0 / ((double)OH * (double)OW);
+        F.exps[j] = p->exponents[j];
+        if (j + 1 < S) {
+            const Level &N = P.lv[j + 1];
+            dx = ImgDesc{ds_x, N.H, N.W, N.W, N.H * N.W};
+            dy = ImgDesc{ds_y, N.H, N.W, N.W, N.H * N.W};
+            dtype = GBSSIM_F32;
+        }
+    }
+    F.scales = S;
+    F.count = n;
+    F.combine = p->combine;
+    F.score_out = score_out;
+    F.per_scale_out = per_scale_out;
+    return launch_finalize_msssim(F, st) == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
+}
+
+
+// Backward workspace: [MS-SSIM forward plan][score][per-scale means]
+// [coefficient-pass partials][A, B, C maps of level 0 (reused per level)]
+// [float gradients of levels 1..S-1].
+struct BwdPlan {
+    MsPlan fwd;   // forward plan (multiscale only)
+    MsPlan coef;  // per-level items of the coefficient pass (float path)
+    size_t score_off, per_off, cpart_off, coef_off, grad_off[GBSSIM_MAX_SCALES];
+    size_t bytes;
+};
+
+int plan_backward(const gbssim_plane *x, const gbssim_params *p, int multiscale, BwdPlan *B) {
+    const int S = multiscale ? p->scales : 1;
+    int rc;
+    size_t off = 0;
+    if (multiscale) {
+        rc = plan_levels(x, p, S, &B->fwd);
+        if (rc) return rc;
+        off = B->fwd.bytes;
+    }
+    rc = plan_levels(x, p, S, &B->coef, true);
+    if (rc) return rc;
+    B->score_off = off;
+    off = align_up(off + sizeof(double) * x->count);
+    B->per_off = off;
+    off = align_up(off + 2 * sizeof(double) * S * x->count);
+    int max_items = 0;
+    for (int j = 0; j < S; ++j) max_items = B->coef.lv[j].items > max_items ? B->coef.lv[j].items : max_items;
+    B->cpart_off = off;
+    off = align_up(off + sizeof(double2) * (size_t)max_items * x->count);
+    const int64_t OH = out_dim(x->height, p->k, 1), OW = out_dim(x->width, p->k, 1);
+    B->coef_off = off;
+    off = align_up(off + 3 * sizeof(float) * (size_t)OH * OW * x->count);
+    B->grad_off[0] = 0;
+    for (int j = 1; j < S; ++j) {
+        B->grad_off[j] = off;
+        off = align_up(off + sizeof(float) * (size_t)B->coef.lv[j].H * B->coef.lv[j].W * x->count);
+    }
+    B->bytes = off;
+    return GBSSIM_OK;
 }
 
 }  // namespace
@@ -270,6 +363,13 @@ int gbssim_workspace_size(const gbssim_plane *x, const gbssim_params *p, int op,
         rc = plan_levels(x, p, 1, &P);
     } else if (op == GBSSIM_OP_MSSSIM) {
         rc = plan_levels(x, p, p->scales, &P);
+    } else if (op == GBSSIM_OP_BACKWARD || op == GBSSIM_OP_BACKWARD_MS) {
+        if (p->stride != 1 || p->k > GBSSIM_MAX_K_BACKWARD) return GBSSIM_ERR_UNSUPPORTED;
+        BwdPlan B;
+        rc = plan_backward(x, p, op == GBSSIM_OP_BACKWARD_MS, &B);
+        if (rc) return rc;
+        *bytes = B.bytes;
+        return GBSSIM_OK;
     } else {
         return GBSSIM_ERR_INVALID_ARG;
     }
@@ -327,47 +427,106 @@ int gbssim_msssim(const gbssim_plane *x, const gbssim_plane *y, const gbssim_par
     rc = check_params(p);
     if (rc) return rc;
     if (!score_out) return GBSSIM_ERR_INVALID_ARG;
-    const int S = p->scales;
     MsPlan P;
-    rc = plan_levels(x, p, S, &P);
+    rc = plan_levels(x, p, p->scales, &P);
     if (rc) return rc;
     if (!workspace || workspace_bytes < P.bytes) return GBSSIM_ERR_WORKSPACE;
+    return msssim_forward(x, y, p, P, (char *)workspace, score_out, per_scale_out, (cudaStream_t)stream);
+}
+
+int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
+                         int32_t multiscale, double grad_scale, const double *grad_out,
+                         int32_t grad_out_per_image, void *grad_y, int32_t grad_dtype, int64_t grad_ld,
+                         int64_t grad_image_stride, double *score_out, void *workspace,
+                         size_t workspace_bytes, void *stream) {
+    int rc = check_pair(x, y);
+    if (rc) return rc;
+    rc = check_params(p);
+    if (rc) return rc;
+    if (p->stride != 1 || p->k > GBSSIM_MAX_K_BACKWARD) return GBSSIM_ERR_UNSUPPORTED;
+    if (!grad_y || (grad_dtype != GBSSIM_F32 && grad_dtype != GBSSIM_F16 && grad_dtype != GBSSIM_BF16))
+        return GBSSIM_ERR_INVALID_ARG;
+    if (grad_ld < x->width || (x->count > 1 && grad_image_stride < x->height * grad_ld))
+        return GBSSIM_ERR_INVALID_ARG;
+    if (!isfinite(grad_scale)) return GBSSIM_ERR_INVALID_ARG;
+    BwdPlan B;
+    rc = plan_backward(x, p, multiscale != 0, &B);
+    if (rc) return rc;
+    if (!workspace || workspace_bytes < B.bytes) return GBSSIM_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     char *ws = (char *)workspace;
-    const int n = x->count;
-    ImgDesc dx = desc_of(x), dy = desc_of(y);
-    int dtype = x->dtype;
-    MsFinalize F;
-    memset(&F, 0, sizeof F);
-    for (int j = 0; j < S; ++j) {
-        const Level &L = P.lv[j];
-        float *ds_x = nullptr, *ds_y = nullptr;
-        if (j + 1 < S) {
-            const Level &N = P.lv[j + 1];
-            ds_x = (float *)(ws + N.plane_off);
-            ds_y = ds_x + (size_t)N.H * N.W * n;
-        }
-        double2 *part = (double2 *)(ws + L.part_off);
-        cudaError_t e = run_level(L, dx, dy, dtype, n, p, nullptr, 0, 0, part, ds_x, ds_y, st);
-        if (e != cudaSuccess) return GBSSIM_ERR_CUDA;
-        const int64_t OH = out_dim(L.H, p->k, p->stride), OW = out_dim(L.W, p->k, p->stride);
-        F.lv[j].partials = part;
-        F.lv[j].items_per_image = L.items;
-        F.lv[j].inv_n = 1.0 / ((double)OH * (double)OW);
-        F.exps[j] = p->exponents[j];
-        if (j + 1 < S) {
-            const Level &N = P.lv[j + 1];
-            dx = ImgDesc{ds_x, N.H, N.W, N.W, N.H * N.W};
-            dy = ImgDesc{ds_y, N.H, N.W, N.W, N.H * N.W};
+    const int n = x->count, S = multiscale ? p->scales : 1;
+    double *score = (double *)(ws + B.score_off), *per = (double *)(ws + B.per_off);
+    if (multiscale) {
+        rc = msssim_forward(x, y, p, B.fwd, ws, score, per, st);
+        if (rc) return rc;
+    }
+    double esum = 0.0;
+    for (int j = 0; j < S; ++j) esum += p->exponents[j];
+    float *coef = (float *)(ws + B.coef_off);
+    double2 *cpart = (double2 *)(ws + B.cpart_off);
+    for (int j = S - 1; j >= 0; --j) {
+        const Level &L = B.coef.lv[j];
+        ImgDesc dx = desc_of(x), dy = desc_of(y);
+        int dtype = x->dtype;
+        if (j > 0) {
+            const float *px = (const float *)(ws + B.fwd.lv[j].plane_off);
+            dx = ImgDesc{px, L.H, L.W, L.W, L.H * L.W};
+            dy = ImgDesc{px + (size_t)L.H * L.W * n, L.H, L.W, L.W, L.H * L.W};
             dtype = GBSSIM_F32;
         }
+        CoefOut co;
+        co.coef = coef;
+        co.which = (multiscale && j < S - 1) ? 1 : 0;
+        co.sx = co.sy = (float)(0.5 * p->L);
+        cudaError_t e = run_level(L, dx, dy, dtype, n, p, nullptr, 0, 0, cpart, nullptr, nullptr, st, &co);
+        if (e != cudaSuccess) return GBSSIM_ERR_CUDA;
+        const int64_t OH = out_dim(L.H, p->k, 1), OW = out_dim(L.W, p->k, 1);
+        if (!multiscale && score_out) {
+            e = launch_finalize_ssim(cpart, n, L.items, 1.0 / ((double)OH * (double)OW), score_out, st);
+            if (e != cudaSuccess) return GBSSIM_ERR_CUDA;
+        }
+        GradLaunch G;
+        memset(&G, 0, sizeof G);
+        G.x = dx;
+        G.y = dy;
+        G.dtype = dtype;
+        G.count = n;
+        G.k = p->k;
+        G.coef = coef;
+        make_taps(p, G.taps.g);
+        G.sx = G.sy = co.sx;
+        G.base_scale = grad_scale / ((double)OH * (double)OW);
+        G.grad_out = grad_out;
+        G.grad_out_per_image = grad_out_per_image;
+        if (multiscale) {
+            G.ms_score = score;
+            G.ms_per_scale = per;
+            G.ms_scales = S;
+            G.ms_level = j;
+            G.ms_combine = p->combine;
+            G.ms_beta = p->exponents[j];
+            G.ms_beta_hat = p->exponents[j] / esum;
+        }
+        G.coarse = j + 1 < S ? (const float *)(ws + B.grad_off[j + 1]) : nullptr;
+        if (j == 0) {
+            G.out = grad_y;
+            G.out_dtype = grad_dtype;
+            G.out_ld = grad_ld;
+            G.out_is = x->count > 1 ? grad_image_stride : x->height * grad_ld;
+        } else {
+            G.out = ws + B.grad_off[j];
+            G.out_dtype = GBSSIM_F32;
+            G.out_ld = L.W;
+            G.out_is = L.H * L.W;
+        }
+        e = launch_grad(G, st);
+        if (e != cudaSuccess) return GBSSIM_ERR_CUDA;
     }
-    F.scales = S;
-    F.count = n;
-    F.combine = p->combine;
-    F.score_out = score_out;
-    F.per_scale_out = per_scale_out;
-    return launch_finalize_msssim(F, st) == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
+    if (multiscale && score_out &&
+        cudaMemcpyAsync(score_out, score, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return GBSSIM_ERR_CUDA;
+    return GBSSIM_OK;
 }
 
 int gbssim_window_sums(const gbssim_plane *x, const gbssim_plane *y, int32_t k, int32_t stride,

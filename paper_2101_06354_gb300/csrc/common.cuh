@@ -67,6 +67,44 @@ struct SsimConst {
     float C1, C2;
 };
 
+// ---------------------------------------------------------------- backward coefficients
+//
+// Derivative of Q (which = 0) or cs (which = 1) at one window position with
+// respect to the distorted image.  From the Background-section definitions,
+// with A1 = 2 mu_x mu_y + C1, B1 = mu_x^2 + mu_y^2 + C1, A2 = 2 s_xy + C2,
+// B2 = s_x^2 + s_y^2 + C2, l = A1/B1, cs = A2/B2:
+//   dQ/d mu_y (central moments fixed) = cs * 2 (mu_x - mu_y l) / B1
+//   dQ/d s_y^2 = -l cs / B2,    dQ/d s_xy = 2 l / B2
+// and a pixel q of the window moves mu_y by w, s_y^2 by 2 w (y(q) - mu_y) and
+// s_xy by w (x(q) - mu_x).  Writing y(q) - mu_y = (y(q) - s) - (mu_y - s) for
+// a fixed shift s (L/2), the contribution of window p to dQ/dy(q) is
+//   w(q - p) [A(p) + (y(q) - s) B(p) + (x(q) - s) C(p)]
+// with A = D_mu - 2 (mu_y - s) D_sy - (mu_x - s) D_sxy, B = 2 D_sy, C = D_sxy.
+struct CoefOut {
+    float *coef;   // nullable: A, B, C planes (OH x OW each), image b at coef + 3*b*OH*OW
+    int which;     // 0: Q, 1: cs
+    float sx, sy;  // shifts
+};
+
+__device__ __forceinline__ void ssim_coef(float ux, float uy, float A1, float B1, float A2, float B2,
+                                          int which, float sx, float sy, float &a, float &b, float &c) {
+    const float iB1 = __fdividef(1.f, B1), iB2 = __fdividef(1.f, B2);
+    const float l = A1 * iB1, cs = A2 * iB2;
+    float dmu, dvy, dcv;
+    if (which == 0) {
+        dmu = cs * 2.f * fmaf(-uy, l, ux) * iB1;
+        dvy = -l * cs * iB2;
+        dcv = 2.f * l * iB2;
+    } else {
+        dmu = 0.f;
+        dvy = -cs * iB2;
+        dcv = 2.f * iB2;
+    }
+    a = dmu - 2.f * (uy - sy) * dvy - (ux - sx) * dcv;
+    b = 2.f * dvy;
+    c = dcv;
+}
+
 // ---------------------------------------------------------------- block reduction
 
 // Sum two doubles over the CTA; the result is valid in thread 0.
@@ -113,6 +151,7 @@ struct GaussLaunch {
     SsimConst c;
     int seg_rows;       // output rows per work item (multiple of 16)
     bool vec;           // x/y rows aligned for 4-element vector loads (set by the launcher)
+    CoefOut co;         // backward: coefficient maps instead of (besides) pooling
 };
 int gauss11_items(int64_t H, int64_t W, int seg_rows, int *strips, int *segs);
 cudaError_t launch_gauss11(const GaussLaunch &L, cudaStream_t st);
@@ -126,6 +165,7 @@ struct GenericLaunch {
     double2 *partials;  // items: count * tiles
     TapsDyn taps;
     SsimConst c;
+    CoefOut co;
 };
 int generic_items(int64_t OH, int64_t OW);
 cudaError_t launch_generic(const GenericLaunch &L, cudaStream_t st);
@@ -162,6 +202,28 @@ struct MsFinalize {
     double *score_out, *per_scale_out;
 };
 cudaError_t launch_finalize_msssim(const MsFinalize &F, cudaStream_t st);
+// Backward gradient pass (k_bwd.cu): full correlation of the coefficient
+// maps with the window, combined with the images, plus the 2x2-average
+// adjoint of the next coarser level.
+struct GradLaunch {
+    ImgDesc x, y;          // this level's images
+    int dtype, count, k;
+    const float *coef;     // A, B, C planes of this level (dense OH x OW)
+    TapsDyn taps;
+    float sx, sy;
+    double base_scale;     // grad_scale / (number of map elements of this level)
+    const double *grad_out; // nullable device factor(s)
+    int grad_out_per_image;
+    const double *ms_score, *ms_per_scale;  // nullable: MS-SSIM forward results
+    int ms_scales, ms_level, ms_combine;
+    double ms_beta, ms_beta_hat;
+    const float *coarse;   // nullable: gradient of the next coarser level, dense (H/2) x (W/2)
+    void *out;
+    int out_dtype;
+    int64_t out_ld, out_is;
+};
+cudaError_t launch_grad(const GradLaunch &G, cudaStream_t st);
+
 cudaError_t launch_pool_mean(const float *map, int64_t h, int64_t w, int64_t ld, int count,
                              int64_t image_stride, double2 *partials, double *out,
                              cudaStream_t st);

@@ -250,13 +250,15 @@ cudaError_t launch_box_u8(const BoxLaunch &L, cudaStream_t st) {
                              (L.y.image_stride % 4 == 0);
         box_block_kernel<<<grid, NT, 0, st>>>(L, tx, ty, aligned4);
     } else {
-        static bool attr_set = false;
+        static bool attr_set[64] = {};
         const size_t smem = sizeof(SatSmem);
-        if (!attr_set) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (!attr_set[dev]) {
             cudaError_t e = cudaFuncSetAttribute(box_sat_kernel,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            attr_set = true;
+            attr_set[dev] = true;
         }
         box_sat_kernel<<<grid, NT, smem, st>>>(L, tx, ty);
     }

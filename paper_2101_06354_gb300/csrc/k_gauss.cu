@@ -303,9 +303,10 @@ __device__ __forceinline__ void horizontal(Smem &S, int nr, int rel0, const Taps
 
 // Vertical pass + SSIM formula for the 16 output rows starting at rel0
 // (relative to the segment); each thread does 4 rows of one column.
+template <bool COEF>
 __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, const Taps<K> &t,
                                          const Taps2<K> &t2, const SsimConst &cc, float *map, int64_t map_ld, bool col_ok,
-                                         float &sumQ, float &sumCS) {
+                                         const CoefOut &co, float *coef_img, float &sumQ, float &sumCS) {
     const int col = threadIdx.x & (TW - 1);
     const int base = rel0 + 4 * (threadIdx.x >> 6);
     const int b0 = base & (RING - 1);  // multiple of 4; b0 + 13 < RROWS
@@ -351,6 +352,15 @@ __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, 
             sumQ += qv;
             sumCS += cs;
             if (mrow) mrow[o * map_ld] = qv;
+            if (COEF) {
+                float ca, cb, ccf;
+                ssim_coef(u.x, u.y, A1, B1, A2, B2, co.which, co.sx, co.sy, ca, cb, ccf);
+                const int64_t plane = g.OH * g.OW;
+                float *dst = coef_img + (g.o0 + base + o) * g.OW + g.j0 + col;
+                dst[0] = ca;
+                dst[plane] = cb;
+                dst[2 * plane] = ccf;
+            }
         }
     }
 }
@@ -389,7 +399,7 @@ __device__ __forceinline__ void block_sum2f(float a, float b, float *red, double
         }
 }
 
-template <typename T>
+template <typename T, bool COEF>
 __global__ void __launch_bounds__(NT, 3) gauss11_kernel(const GaussLaunch L, int strips, int segs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
@@ -414,6 +424,7 @@ __global__ void __launch_bounds__(NT, 3) gauss11_kernel(const GaussLaunch L, int
     const int64_t dsn = (g.H >> 1) * (g.W >> 1);
     float *dsx = L.ds_x ? L.ds_x + img * dsn : nullptr;
     float *dsy = L.ds_y ? L.ds_y + img * dsn : nullptr;
+    float *coef_img = COEF ? L.co.coef + (int64_t)img * 3 * g.OH * g.OW : nullptr;
 
     KSum accQ, accCS;
     uint4 px[PFQ], py[PFQ];
@@ -431,7 +442,7 @@ __global__ void __launch_bounds__(NT, 3) gauss11_kernel(const GaussLaunch L, int
         if (more) prefetch<T>(px, py, U, g, next_r0);
         __syncthreads();  // ring rows of chunk c complete; staging free
         float cq, ccs;
-        vertical(S, g, CH * c, L.taps, L.taps2, L.c, map, L.map_ld, col_ok, cq, ccs);
+        vertical<COEF>(S, g, CH * c, L.taps, L.taps2, L.c, map, L.map_ld, col_ok, L.co, coef_img, cq, ccs);
         accQ.add(cq);
         accCS.add(ccs);
         if (more) store_prefetch<T>(S, px, py, U);
@@ -516,6 +527,15 @@ __global__ void __launch_bounds__(GT *GT) generic_kernel(const GenericLaunch L, 
         cs = __fdividef(A2, B2);
         q = l * cs;
         if (L.map) L.map[img * L.map_is + a * L.map_ld + b] = q;
+        if (L.co.coef) {
+            float ca, cb, ccf;
+            ssim_coef(ux, uy, A1, B1, A2, B2, L.co.which, L.co.sx, L.co.sy, ca, cb, ccf);
+            const int64_t plane = OH * OW;
+            float *dst = L.co.coef + (int64_t)img * 3 * plane + a * OW + b;
+            dst[0] = ca;
+            dst[plane] = cb;
+            dst[2 * plane] = ccf;
+        }
     }
     double sa = q, sb = cs;
     block_sum2(sa, sb, red);
@@ -523,15 +543,17 @@ __global__ void __launch_bounds__(GT *GT) generic_kernel(const GenericLaunch L, 
         L.partials[((int64_t)img * tiles_y + blockIdx.y) * tiles_x + blockIdx.x] = make_double2(sa, sb);
 }
 
-template <typename T>
+template <typename T, bool COEF>
 cudaError_t launch_gauss11_t(const GaussLaunch &L, cudaStream_t st) {
-    static bool attr_set = false;
+    static bool attr_set[64] = {};
     const size_t smem = sizeof(Smem);
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(gauss11_kernel<T>,
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(gauss11_kernel<T, COEF>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set[dev] = true;
     }
     int strips, segs;
     gauss11_items(L.x.H, L.x.W, L.seg_rows, &strips, &segs);
@@ -541,7 +563,7 @@ cudaError_t launch_gauss11_t(const GaussLaunch &L, cudaStream_t st) {
     A.vec = ((uintptr_t)L.x.data % vbytes == 0) && ((uintptr_t)L.y.data % vbytes == 0) &&
             (L.x.row_stride % 4 == 0) && (L.x.image_stride % 4 == 0) && (L.y.image_stride % 4 == 0);
     dim3 grid(strips, segs, L.count);
-    gauss11_kernel<T><<<grid, NT, smem, st>>>(A, strips, segs);
+    gauss11_kernel<T, COEF><<<grid, NT, smem, st>>>(A, strips, segs);
     return cudaGetLastError();
 }
 
@@ -564,11 +586,13 @@ int gauss11_items(int64_t H, int64_t W, int seg_rows, int *strips, int *segs) {
 }
 
 cudaError_t launch_gauss11(const GaussLaunch &L, cudaStream_t st) {
+    const bool coef = L.co.coef != nullptr;
     switch (L.dtype) {
-    case GBSSIM_U8: return launch_gauss11_t<uint8_t>(L, st);
-    case GBSSIM_F16: return launch_gauss11_t<__half>(L, st);
-    case GBSSIM_BF16: return launch_gauss11_t<__nv_bfloat16>(L, st);
-    case GBSSIM_F32: return launch_gauss11_t<float>(L, st);
+    case GBSSIM_U8: return coef ? launch_gauss11_t<uint8_t, true>(L, st) : launch_gauss11_t<uint8_t, false>(L, st);
+    case GBSSIM_F16: return coef ? launch_gauss11_t<__half, true>(L, st) : launch_gauss11_t<__half, false>(L, st);
+    case GBSSIM_BF16:
+        return coef ? launch_gauss11_t<__nv_bfloat16, true>(L, st) : launch_gauss11_t<__nv_bfloat16, false>(L, st);
+    case GBSSIM_F32: return coef ? launch_gauss11_t<float, true>(L, st) : launch_gauss11_t<float, false>(L, st);
     }
     return cudaErrorInvalidValue;
 }

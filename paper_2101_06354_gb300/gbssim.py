@@ -32,6 +32,7 @@ lib = ctypes.CDLL(LIB_PATH)
 
 MAX_SCALES = 8
 MAX_K = 63
+MAX_K_BACKWARD = 31
 MSSSIM_EXPONENTS = (0.0448, 0.2856, 0.3001, 0.2363, 0.1333)
 
 OK, ERR_INVALID_ARG, ERR_TOO_SMALL, ERR_UNSUPPORTED, ERR_CUDA, ERR_DOMAIN, ERR_TIMEOUT, ERR_WORKSPACE = \
@@ -71,6 +72,8 @@ _SIGS = {
     "gbssim_msssim": ([_P(Plane), _P(Plane), _P(Params), _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
     "gbssim_window_sums": ([_P(Plane), _P(Plane), _i32, _i32, _vp, _vp], ctypes.c_int),
     "gbssim_ssim_map_static": ([_P(Plane), _P(Plane), _P(Params), _vp, _i64, _i64, _vp, _vp], ctypes.c_int),
+    "gbssim_ssim_backward": ([_P(Plane), _P(Plane), _P(Params), _i32, ctypes.c_double, _vp, _i32, _vp, _i32, _i64,
+                              _i64, _vp, _vp, _sz, _vp], ctypes.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -262,3 +265,83 @@ def ssim_pool(qmap: torch.Tensor, kind: str = "mean") -> torch.Tensor:
                                 {"mean": POOL_MEAN}[kind], None, out.data_ptr(), ws.data_ptr(),
                                 ws.numel(), _stream(dev)), "gbssim_ssim_pool")
     return out
+
+
+_GDT = {torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}
+
+
+def ssim_backward(x: torch.Tensor, y: torch.Tensor, multiscale: bool = False, grad_scale: float = 1.0,
+                  grad_out: torch.Tensor = None, grad_dtype=None, return_score: bool = False,
+                  ws: torch.Tensor = None, **kw):
+    """d score / d y for each pair (gbssim_ssim_backward), shaped like y.
+
+    score is MSSIM (multiscale=False) or MS-SSIM.  The result is multiplied by
+    ``grad_scale`` and, when given, by the device float64 tensor ``grad_out``
+    (one element, or one per pair).  ``grad_dtype`` defaults to y's dtype for
+    floating inputs and float32 for uint8."""
+    host, dev, xb, yb = _prepare(x, y)
+    if multiscale:
+        kw.setdefault("exponents", MSSSIM_EXPONENTS[: kw.get("scales", 5)])
+    p = make_params(**kw)
+    px, py = plane(xb), plane(yb)
+    n, h, w = xb.shape
+    gdt = grad_dtype or (y.dtype if y.dtype in _GDT else torch.float32)
+    grad = torch.empty((n, h, w), dtype=gdt, device=dev)
+    if ws is None:
+        ws = workspace(px, p, OP_BACKWARD_MS if multiscale else OP_BACKWARD, dev)
+    score = torch.empty(n, dtype=torch.float64, device=dev) if return_score else None
+    go = None
+    if grad_out is not None:
+        go = grad_out.detach().to(device=dev, dtype=torch.float64).contiguous().reshape(-1)
+        if go.numel() not in (1, n):
+            raise ValueError("grad_out must have 1 or N elements")
+    _check(lib.gbssim_ssim_backward(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p), int(bool(multiscale)),
+                                    float(grad_scale), go.data_ptr() if go is not None else None,
+                                    int(go is not None and go.numel() == n and n > 1), grad.data_ptr(),
+                                    _GDT[gdt], grad.stride(1), grad.stride(0),
+                                    score.data_ptr() if score is not None else None,
+                                    ws.data_ptr(), ws.numel(), _stream(dev)), "gbssim_ssim_backward")
+    grad = grad.reshape(y.shape)
+    if host:
+        grad = grad.cpu()
+        score = score.cpu() if score is not None else None
+    return (grad, score) if return_score else grad
+
+
+class _SSIMLossFn(torch.autograd.Function):
+    """loss = 1 - mean over pairs of SSIM (or MS-SSIM); gradient w.r.t. y only
+    (x is the reference).  The backward recomputes the window moments in the
+    library; nothing but x and y is saved."""
+
+    @staticmethod
+    def forward(ctx, x, y, multiscale, kw):
+        score = msssim(x, y, **kw) if multiscale else ssim(x, y, **kw)
+        ctx.save_for_backward(x, y)
+        ctx.multiscale = multiscale
+        ctx.kw = kw
+        ctx.n = score.numel()
+        return 1.0 - score.mean()
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        x, y = ctx.saved_tensors
+        if not ctx.needs_input_grad[1]:
+            return None, None, None, None
+        g = ssim_backward(x, y, multiscale=ctx.multiscale, grad_scale=-1.0 / ctx.n, grad_out=grad_loss,
+                          grad_dtype=y.dtype, **ctx.kw)
+        return None, g, None, None
+
+
+class SSIMLoss(torch.nn.Module):
+    """1 - SSIM (or MS-SSIM with multiscale=True) averaged over the batch,
+    differentiable with respect to the second argument.  Inputs (H, W),
+    (N, H, W) or (B, C, H, W) float tensors on a CUDA device; keyword
+    arguments as ``make_params`` (e.g. L=1.0 for inputs in [0, 1])."""
+
+    def __init__(self, multiscale: bool = False, **kw):
+        super().__init__()
+        self.multiscale = multiscale
+        self.kw = kw
+
+    def forward(self, x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
+        return _SSIMLossFn.apply(x.detach(), y, self.multiscale, dict(self.kw))
