@@ -161,6 +161,52 @@ def cpu_baseline():
                                         % (sample, dt)}
 
 
+def run_extras(args, gbssim, synth, x, y, dev, timed, ws):
+    """Secondary figures on the same GPU: the 8x8 stride-4 integer box SSIM on
+    the same 64 pairs (the HBM-bound path), and the SSIM-loss forward+backward
+    of 32x3x512x512 float inputs in [0, 1] (fp32 and bf16 storage)."""
+    import torch
+
+    out = {}
+    k_steps = max(10, args.steps // 5)
+    hbm_peak, _ = _peaks()
+    pb = gbssim.make_params(window="box", k=8, stride=4)
+    wsb = gbssim.workspace(gbssim.plane(x), pb, gbssim.OP_SSIM, dev)
+    box = lambda: gbssim.ssim(x, y, ws=wsb, window="box", k=8, stride=4)
+    for _ in range(3):
+        box()
+    ms = timed(box, k_steps) / k_steps
+    in_bytes = 2 * N_PAIRS * PX_PER_PAIR
+    out["box8_s4"] = {"value": ws * N_PAIRS * PX_PER_PAIR / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+                      "hbm_gbs": in_bytes / (ms / 1e3) / 1e9, "hbm_frac": in_bytes / (ms / 1e3) / 1e9 / hbm_peak,
+                      "config": "same 64 pairs, box 8x8 stride 4, exact int sums (integral-image path)"}
+    lx, ly = synth.loss_pairs_float(32, 3, 512, 512)
+    px_step = 32 * 3 * 512 * 512
+    loss_res = {}
+    for name, dt in (("fp32", torch.float32), ("bf16", torch.bfloat16)):
+        xd = lx.to(dev, dt)
+        yd = ly.to(dev, dt).requires_grad_(True)
+        for ms_flag in (False, True):
+            lf = gbssim.SSIMLoss(multiscale=ms_flag, L=1.0)
+
+            def fb():
+                yd.grad = None
+                loss = lf(xd, yd)
+                loss.backward()
+                return loss
+
+            for _ in range(3):
+                fb()
+            kk = max(5, args.steps // 20)
+            t = timed(fb, kk) / kk
+            loss_res[("msssim_" if ms_flag else "ssim_") + name] = {
+                "value": ws * px_step / (t / 1e3) / 1e6, "unit": "Mpx/s", "ms_per_step": t}
+        del xd, yd
+    out["loss_fwd_bwd"] = dict(loss_res, config="32x3x512x512, L=1, loss = 1 - mean score, grad w.r.t. y",
+                               headline=loss_res["ssim_fp32"]["value"])
+    return out
+
+
 def run_gbssim(args):
     import torch
     import torch.distributed as dist
@@ -240,6 +286,10 @@ def run_gbssim(args):
     e2e = {"value": ws * N_PAIRS * PX_PER_PAIR / (ms_e2e / 1e3) / 1e6, "unit": UNIT,
            "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": 8 * N_PAIRS}
 
+    extra = {}
+    if not args.no_extras:
+        extra = run_extras(args, gbssim, synth, x, y, dev, timed, ws)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
@@ -255,6 +305,7 @@ def run_gbssim(args):
                              "kernel_ms": ms_k, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src},
                 "clocks": clocks,
                 "score_mean": float(score.double().mean().item())}
+        line.update(extra)
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))
@@ -269,6 +320,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbssim", choices=["gbssim", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the box-window and loss fwd+bwd figures")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

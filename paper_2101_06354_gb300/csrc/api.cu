@@ -152,6 +152,14 @@ int plan_levels(const gbssim_plane *x, const gbssim_params *p, int scales, MsPla
     return GBSSIM_OK;
 }
 
+// The uint8 box path's tile layout (and so its item count) depends on the
+// alignment of the actual planes; the plan sized the workspace for the larger.
+void fix_box_items(Level &L, const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p) {
+    if (L.path != PATH_BOX_U8) return;
+    const int64_t OH = out_dim(L.H, p->k, p->stride), OW = out_dim(L.W, p->k, p->stride);
+    L.items = box_path_items(OH, OW, p->k, p->stride, box_aligned16(desc_of(x), desc_of(y)));
+}
+
 // Launch one SSIM level: `in_x/in_y` describe the level's images (dtype),
 // partials/map as given; ds_x/ds_y (nullable) receive the next level.
 cudaError_t run_level(const Level &L, const ImgDesc &dx, const ImgDesc &dy, int dtype, int count,
@@ -236,13 +244,15 @@ int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_pa
     const int S = p->scales, n = x->count;
     ImgDesc dx = desc_of(x), dy = desc_of(y);
     int dtype = x->dtype;
+    MsPlan Pl = P;  // level 0 may take the aligned box layout
+    fix_box_items(Pl.lv[0], x, y, p);
     MsFinalize F;
     memset(&F, 0, sizeof F);
     for (int j = 0; j < S; ++j) {
-        const Level &L = P.lv[j];
+        const Level &L = Pl.lv[j];
         float *ds_x = nullptr, *ds_y = nullptr;
         if (j + 1 < S) {
-            const Level &N = P.lv[j + 1];
+            const Level &N = Pl.lv[j + 1];
             ds_x = (float *)(ws + N.plane_off);
             ds_y = ds_x + (size_t)N.H * N.W * n;
         }
@@ -255,7 +265,7 @@ int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_pa
         F.lv[j].inv_n = 1.0 / ((double)OH * (double)OW);
         F.exps[j] = p->exponents[j];
         if (j + 1 < S) {
-            const Level &N = P.lv[j + 1];
+            const Level &N = Pl.lv[j + 1];
             dx = ImgDesc{ds_x, N.H, N.W, N.W, N.H * N.W};
             dy = ImgDesc{ds_y, N.H, N.W, N.W, N.H * N.W};
             dtype = GBSSIM_F32;
@@ -394,6 +404,7 @@ int gbssim_ssim_map(const gbssim_plane *x, const gbssim_plane *y, const gbssim_p
     if (!map_out && !mean_out) return GBSSIM_ERR_INVALID_ARG;
     if (!workspace || workspace_bytes < P.bytes) return GBSSIM_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
+    fix_box_items(P.lv[0], x, y, p);
     double2 *part = (double2 *)((char *)workspace + P.lv[0].part_off);
     cudaError_t e = run_level(P.lv[0], desc_of(x), desc_of(y), x->dtype, x->count, p, map_out, map_ld,
                               map_image_stride, part, nullptr, nullptr, st);

@@ -180,7 +180,9 @@ struct BoxLaunch {
     int64_t *sums_out;  // nullable: 5 int64 per window position
     float C1k4, C2k4;   // C1 * k^4, C2 * k^4
 };
-int box_items_ks(int64_t OH, int64_t OW, int k, int s);
+int box_items_ks(int64_t OH, int64_t OW, int k, int s);  // workspace sizing (max over layouts)
+bool box_aligned16(const ImgDesc &x, const ImgDesc &y);
+int box_path_items(int64_t OH, int64_t OW, int k, int s, bool aligned16);  // items of the layout launched
 cudaError_t launch_box_u8(const BoxLaunch &L, cudaStream_t st);
 
 // 2x2 average downsample of a batch into dense float planes (k_pool.cu).

@@ -42,6 +42,138 @@ __device__ __forceinline__ void box_formula(const BoxOut &v, int k, float C1k4, 
     q = __fdividef(A1, B1) * cs;
 }
 
+// k <= 13: every integer quantity of the formula fits int32 (S2 <= 65025 k^2,
+// k^2 S2 <= 1.9e9); products of two sums are formed in fp32 (one rounding).
+__device__ __forceinline__ void box_formula32(int s1x, int s1y, int s2x, int s2y, int sxy, int kk,
+                                              float C1k4, float C2k4, float &q, float &cs) {
+    const float fx = (float)s1x, fy = (float)s1y;
+    const float A1 = fmaf(2.f * fx, fy, C1k4), B1 = fmaf(fx, fx, fmaf(fy, fy, C1k4));
+    const int nxy = kk * sxy - s1x * s1y, nxx = kk * s2x - s1x * s1x, nyy = kk * s2y - s1y * s1y;
+    const float A2 = fmaf(2.f, (float)nxy, C2k4), B2 = ((float)nxx + (float)nyy) + C2k4;
+    cs = __fdividef(A2, B2);
+    q = __fdividef(A1, B1) * cs;
+}
+
+// Sum (a, b) over the CTA: fp32 pairwise tree inside each warp, fp64 across
+// warps (thread 0 holds the result).
+__device__ __forceinline__ void block_sum2f(float a, float b, float *red, double &ra, double &rb) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) {
+        red[2 * warp] = a;
+        red[2 * warp + 1] = b;
+    }
+    __syncthreads();
+    ra = rb = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            ra += (double)red[2 * w];
+            rb += (double)red[2 * w + 1];
+        }
+}
+
+// ------------------------------------------------------------------ stride-4 vector path
+//
+// Stride 4, k = 4m (m <= 3), 16-byte aligned rows: each thread loads four
+// 16-byte row segments of x and y (16 pixels x 4 rows = four 4 x 4 blocks),
+// all issued before use, and forms the blocks' five sums with dp4a.  A CTA
+// loads 64 x 16 blocks (256 x 64 pixels) and produces VTOW x (17-m) windows;
+// VTOW is a multiple of 4 so that every tile starts on a 16-byte boundary
+// (tile column b starts at pixel 4 * VTOW * b), and VTOW + m - 1 <= 64.
+constexpr int VBW = 64, VBH = 16, VTOW = 60;
+
+__global__ void __launch_bounds__(NT) box_s4_kernel(const BoxLaunch L, int tiles_x, int tiles_y) {
+    __shared__ int Bs[5][VBH][VBW + 1];
+    __shared__ float red[2 * NT / 32];
+    const int m = L.k >> 2, kk = L.k * L.k;
+    const int tow = VTOW, toh = VBH - m + 1;
+    const int img = blockIdx.z;
+    const int64_t H = L.x.H, W = L.x.W, rs = L.x.row_stride;
+    const int64_t OH = out_dim(H, L.k, 4), OW = out_dim(W, L.k, 4);
+    const int64_t a0 = (int64_t)blockIdx.y * toh, b0 = (int64_t)blockIdx.x * tow;
+    const uint8_t *xb = static_cast<const uint8_t *>(L.x.data) + img * L.x.image_stride;
+    const uint8_t *yb = static_cast<const uint8_t *>(L.y.data) + img * L.y.image_stride;
+
+    // thread -> block row bi (0..15), four blocks starting at column 4*qd
+    const int bi = threadIdx.x >> 4, qd = threadIdx.x & 15;
+    const int64_t r0 = (a0 + bi) * 4, c0 = (b0 + 4 * qd) * 4;
+    uint4 vx[4], vy[4];
+    const bool rows_in = r0 + 4 <= H;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        vx[r] = vy[r] = make_uint4(0u, 0u, 0u, 0u);
+        if (rows_in && c0 + 16 <= W) {
+            vx[r] = __ldg(reinterpret_cast<const uint4 *>(xb + (r0 + r) * rs + c0));
+            vy[r] = __ldg(reinterpret_cast<const uint4 *>(yb + (r0 + r) * rs + c0));
+        } else if (rows_in) {  // ragged right edge: whole 4-pixel blocks only
+            unsigned wx[4] = {0u, 0u, 0u, 0u}, wy[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (c0 + 4 * b + 4 <= W) {
+                    wx[b] = __ldg(reinterpret_cast<const unsigned *>(xb + (r0 + r) * rs + c0) + b);
+                    wy[b] = __ldg(reinterpret_cast<const unsigned *>(yb + (r0 + r) * rs + c0) + b);
+                }
+            vx[r] = make_uint4(wx[0], wx[1], wx[2], wx[3]);
+            vy[r] = make_uint4(wy[0], wy[1], wy[2], wy[3]);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        unsigned sx = 0, sy = 0, sxx = 0, syy = 0, sxy = 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const unsigned wx = b == 0 ? vx[r].x : b == 1 ? vx[r].y : b == 2 ? vx[r].z : vx[r].w;
+            const unsigned wy = b == 0 ? vy[r].x : b == 1 ? vy[r].y : b == 2 ? vy[r].z : vy[r].w;
+            sx = __dp4a(wx, 0x01010101u, sx);
+            sy = __dp4a(wy, 0x01010101u, sy);
+            sxx = __dp4a(wx, wx, sxx);
+            syy = __dp4a(wy, wy, syy);
+            sxy = __dp4a(wx, wy, sxy);
+        }
+        const int bj = 4 * qd + b;
+        Bs[0][bi][bj] = (int)sx;
+        Bs[1][bi][bj] = (int)sy;
+        Bs[2][bi][bj] = (int)sxx;
+        Bs[3][bi][bj] = (int)syy;
+        Bs[4][bi][bj] = (int)sxy;
+    }
+    __syncthreads();
+
+    float accQ = 0.f, accCS = 0.f;
+    for (int t = threadIdx.x; t < tow * toh; t += NT) {
+        const int oi = t / tow, oj = t - oi * tow;
+        const int64_t a = a0 + oi, b = b0 + oj;
+        if (a >= OH || b >= OW) continue;
+        int acc[5] = {0, 0, 0, 0, 0};
+        for (int u = 0; u < m; ++u)
+            for (int v = 0; v < m; ++v)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) acc[q] += Bs[q][oi + u][oj + v];
+        if (L.sums_out) {
+            int64_t *dst = L.sums_out + 5 * (img * OH * OW + a * OW + b);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) dst[q] = acc[q];
+            continue;
+        }
+        float q, cs;
+        box_formula32(acc[0], acc[1], acc[2], acc[3], acc[4], kk, L.C1k4, L.C2k4, q, cs);
+        accQ += q;
+        accCS += cs;
+        if (L.map) L.map[img * L.map_is + a * L.map_ld + b] = q;
+    }
+    if (L.partials) {
+        double da, db;
+        block_sum2f(accQ, accCS, red, da, db);
+        if (threadIdx.x == 0)
+            L.partials[((int64_t)img * tiles_y + blockIdx.y) * tiles_x + blockIdx.x] = make_double2(da, db);
+    }
+}
+
 // ------------------------------------------------------------------ block path
 
 constexpr int BW = 32, BH = 16;  // blocks per CTA tile
@@ -49,7 +181,7 @@ constexpr int BW = 32, BH = 16;  // blocks per CTA tile
 __global__ void __launch_bounds__(NT) box_block_kernel(const BoxLaunch L, int tiles_x, int tiles_y,
                                                        int aligned4) {
     __shared__ unsigned Bs[5][BH][BW + 1];
-    __shared__ double red[2 * NT / 32];
+    __shared__ float red[2 * NT / 32];
     const int s = L.stride, m = L.k / L.stride, wps = s >> 2;
     const int tow = BW - m + 1, toh = BH - m + 1;
     const int img = blockIdx.z;
@@ -119,8 +251,8 @@ __global__ void __launch_bounds__(NT) box_block_kernel(const BoxLaunch L, int ti
         if (L.map) L.map[img * L.map_is + a * L.map_ld + b] = q;
     }
     if (L.partials) {
-        double da = accQ, db = accCS;
-        block_sum2(da, db, red);
+        double da, db;
+        block_sum2f(accQ, accCS, red, da, db);
         if (threadIdx.x == 0)
             L.partials[((int64_t)img * tiles_y + blockIdx.y) * tiles_x + blockIdx.x] = make_double2(da, db);
     }
@@ -133,7 +265,7 @@ constexpr int SP = RMAX + 1;         // SAT pitch (first row/column are zero)
 
 struct SatSmem {
     int sat[5][SP][SP + 1];
-    double red[2 * NT / 32];
+    float red[2 * NT / 32];
 };
 
 __host__ __device__ inline int sat_tile_outputs(int k, int s) {
@@ -208,17 +340,22 @@ __global__ void __launch_bounds__(NT) box_sat_kernel(const BoxLaunch L, int tile
         if (L.map) L.map[img * L.map_is + a * L.map_ld + b] = q;
     }
     if (L.partials) {
-        double da = accQ, db = accCS;
-        block_sum2(da, db, S.red);
+        double da, db;
+        block_sum2f(accQ, accCS, S.red, da, db);
         if (threadIdx.x == 0)
             L.partials[((int64_t)img * tiles_y + blockIdx.y) * tiles_x + blockIdx.x] = make_double2(da, db);
     }
 }
 
 bool use_block_path(int k, int s) { return s % 4 == 0 && k % s == 0 && k <= 16; }
+bool use_s4_path(int k, int s) { return s == 4 && k % 4 == 0 && k <= 12 && VTOW + k / 4 - 1 <= VBW; }
 
-void box_tiles(int64_t OH, int64_t OW, int k, int s, int *tx, int *ty) {
-    if (use_block_path(k, s)) {
+void box_tiles(int64_t OH, int64_t OW, int k, int s, int *tx, int *ty, bool s4) {
+    if (s4) {
+        const int m = k / 4;
+        *tx = (int)((OW + VTOW - 1) / VTOW);
+        *ty = (int)((OH + VBH - m) / (VBH - m + 1));
+    } else if (use_block_path(k, s)) {
         const int m = k / s;
         const int tow = BW - m + 1, toh = BH - m + 1;
         *tx = (int)((OW + tow - 1) / tow);
@@ -232,18 +369,35 @@ void box_tiles(int64_t OH, int64_t OW, int k, int s, int *tx, int *ty) {
 
 }  // namespace
 
-int box_items_ks(int64_t OH, int64_t OW, int k, int s) {
+// The stride-4 vector path needs 16-byte aligned rows.  Workspace sizing uses
+// the larger item count of the two block layouts (box_items_ks); a launch
+// uses the layout its pointers allow, and the host pools box_path_items of it.
+bool box_aligned16(const ImgDesc &x, const ImgDesc &y) {
+    const uintptr_t bx = (uintptr_t)x.data, by = (uintptr_t)y.data;
+    return bx % 16 == 0 && by % 16 == 0 && x.row_stride % 16 == 0 && y.row_stride % 16 == 0 &&
+           x.image_stride % 16 == 0 && y.image_stride % 16 == 0;
+}
+
+int box_path_items(int64_t OH, int64_t OW, int k, int s, bool aligned16) {
     int tx, ty;
-    box_tiles(OH, OW, k, s, &tx, &ty);
+    box_tiles(OH, OW, k, s, &tx, &ty, aligned16 && use_s4_path(k, s));
     return tx * ty;
+}
+
+int box_items_ks(int64_t OH, int64_t OW, int k, int s) {
+    const int a = box_path_items(OH, OW, k, s, false), b = box_path_items(OH, OW, k, s, true);
+    return a > b ? a : b;
 }
 
 cudaError_t launch_box_u8(const BoxLaunch &L, cudaStream_t st) {
     const int64_t OH = out_dim(L.x.H, L.k, L.stride), OW = out_dim(L.x.W, L.k, L.stride);
+    const bool s4 = box_aligned16(L.x, L.y) && use_s4_path(L.k, L.stride);
     int tx, ty;
-    box_tiles(OH, OW, L.k, L.stride, &tx, &ty);
+    box_tiles(OH, OW, L.k, L.stride, &tx, &ty, s4);
     dim3 grid(tx, ty, L.count);
-    if (use_block_path(L.k, L.stride)) {
+    if (s4) {
+        box_s4_kernel<<<grid, NT, 0, st>>>(L, tx, ty);
+    } else if (use_block_path(L.k, L.stride)) {
         const uintptr_t bx = (uintptr_t)L.x.data, by = (uintptr_t)L.y.data;
         const int aligned4 = (bx % 4 == 0) && (by % 4 == 0) && (L.x.row_stride % 4 == 0) &&
                              (L.y.row_stride % 4 == 0) && (L.x.image_stride % 4 == 0) &&

@@ -168,7 +168,8 @@ def test_ssim_generic_windows_and_strides(g, synth, window, k, sigma, stride, dt
 
 # --------------------------------------------------------------------------- box / integral images
 
-@pytest.mark.parametrize("k,s,h,w", [(8, 4, 270, 481), (8, 4, 8, 8), (11, 1, 100, 130), (7, 3, 64, 100),
+@pytest.mark.parametrize("k,s,h,w", [(8, 4, 270, 481), (8, 4, 300, 1024), (12, 4, 150, 768), (4, 4, 97, 512),
+                                     (8, 4, 8, 8), (11, 1, 100, 130), (7, 3, 64, 100),
                                      (16, 8, 100, 200), (4, 4, 33, 70), (63, 1, 70, 80), (1, 1, 20, 20),
                                      (12, 4, 50, 90), (5, 2, 41, 77)])
 def test_window_sums_bit_exact(g, synth, k, s, h, w):
@@ -189,9 +190,11 @@ def test_window_sums_unaligned_and_extremes(g):
         np.testing.assert_array_equal(got, oracle.box_sums(x[0].numpy(), y[0].numpy(), k, s))
 
 
-@pytest.mark.parametrize("k,s", [(8, 4), (11, 1), (7, 3), (16, 8)])
-def test_box_ssim_u8(g, synth, k, s):
-    x, y = synth.luma_pairs_u8(2, 150, 210)
+@pytest.mark.parametrize("k,s,w", [(8, 4, 210), (8, 4, 1024), (12, 4, 528), (4, 4, 1040), (11, 1, 210), (7, 3, 210),
+                                   (16, 8, 210)])
+def test_box_ssim_u8(g, synth, k, s, w):
+    # widths that are multiples of 16 take the 16-byte vector path over several tile columns
+    x, y = synth.luma_pairs_u8(2, 150, w)
     mean, qmap = g.ssim(x.to(DEV), y.to(DEV), return_map=True, window="box", k=k, stride=s)
     for i in range(2):
         ref_mean, ref_q, _, _ = oracle.box_ssim(x[i].numpy(), y[i].numpy(), k, s)
