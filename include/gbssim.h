@@ -192,6 +192,60 @@ int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbs
                          int64_t grad_image_stride, double *score_out, void *workspace,
                          size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------------------------------ ragged batch
+ * SSIM or MS-SSIM of many pairs of different sizes in ONE persistent kernel
+ * launch (plus a memset and a finaliser), suitable for CUDA-graph capture.
+ * Restricted to the fused 11-tap path: k = 11, stride 1 (Gaussian or box
+ * window), any input dtype shared by the whole batch. */
+typedef struct gbssim_batch gbssim_batch;
+
+/* Tuning knobs of a batch plan (chosen by the Python autotuner); zero = default. */
+typedef struct gbssim_tuning {
+    int32_t seg_rows;      /* output rows per work item, multiple of 16 (default 256) */
+    int32_t ctas_per_sm;   /* resident CTAs per SM of the persistent grid (default: maximum) */
+    uint32_t wait_limit;   /* spin iterations before a level dependency wait gives up (default 4M) */
+    int32_t flags;         /* GBSSIM_TUNING_* */
+} gbssim_tuning;
+
+/* Test hook: image 0's level-1 items wait for one more level-0 item than
+ * exists, so their bounded wait runs out and the run reports
+ * GBSSIM_ERR_TIMEOUT through gbssim_batch_status.  Never set in production. */
+#define GBSSIM_TUNING_TEST_STALL 1
+
+/* Build a plan for n entries: entry e pairs xs[e] with ys[e] (identical
+ * shape; each entry may itself hold count >= 1 equally sized images); all
+ * entries share one dtype.  The plan is bound to these device pointers: a run
+ * reads whatever they hold at that time.  This call allocates (one device
+ * buffer for the work tables) and copies to it synchronously; it is the only
+ * allocating call of the library.  multiscale = 0: SSIM; 1: MS-SSIM with
+ * p->scales levels.  tuning may be NULL.  Errors: GBSSIM_ERR_UNSUPPORTED
+ * unless k = 11 and stride = 1; GBSSIM_ERR_TOO_SMALL if a level is below k. */
+int gbssim_batch_plan(const gbssim_plane *xs, const gbssim_plane *ys, int32_t n, const gbssim_params *p,
+                      int32_t multiscale, const gbssim_tuning *tuning, gbssim_batch **plan_out);
+
+/* Workspace bytes a run of this plan needs (pyramid levels, pooling slots,
+ * work counter, dependency counters, status word). */
+int gbssim_batch_workspace_size(const gbssim_batch *plan, size_t *bytes);
+
+/* Images in the plan, work items, persistent grid size, rows per item
+ * (any pointer may be NULL). */
+int gbssim_batch_info(const gbssim_batch *plan, int32_t *n_images, int32_t *total_items, int32_t *grid,
+                      int32_t *seg_rows);
+
+/* Enqueue one run: scores_out receives one double per image (entries
+ * expanded in order), per_scale_out (nullable) images x scales x 2 doubles
+ * (mean cs_j, mean Q_j).  Asynchronous and graph-capturable. */
+int gbssim_batch_run(const gbssim_batch *plan, double *scores_out, double *per_scale_out, void *workspace,
+                     size_t workspace_bytes, void *stream);
+
+/* Copy the run's device status word (GBSSIM_OK, or GBSSIM_ERR_TIMEOUT when a
+ * bounded dependency wait gave up) to the device int32 *status_out, ordered
+ * after the run on `stream`. */
+int gbssim_batch_status(const gbssim_batch *plan, const void *workspace, int32_t *status_out, void *stream);
+
+/* Release the plan's device tables (NULL is ignored). */
+void gbssim_batch_free(gbssim_batch *plan);
+
 /* gbssim_ssim_map without a workspace argument, for callers that cannot
  * allocate device memory: a plugin inside a host application that owns the
  * GPU allocator and gives it only input and output buffers, or a real-time

@@ -156,6 +156,41 @@ struct GaussLaunch {
 int gauss11_items(int64_t H, int64_t W, int seg_rows, int *strips, int *segs);
 cudaError_t launch_gauss11(const GaussLaunch &L, cudaStream_t st);
 
+// Ragged persistent batch (k_gauss.cu).  Device tables built by the host
+// plan; offsets are relative to the run's workspace base `ws`.
+struct BatchLevel {
+    const void *x, *y;      // level 0: the caller's planes
+    int64_t x_off;          // levels >= 1: x plane (then y plane) in the workspace
+    int64_t H, W, rs;
+    int64_t ds_off;         // next level's planes in the workspace, -1 at the last level
+    int64_t part_off;       // this (image, level)'s item slots in the workspace
+    int level, strips, segs, seg_rows, items, vec;
+    int wait_target;        // completion count dependants wait for (= items)
+    int pad;
+};
+struct BatchItem {
+    int level_index;        // into the BatchLevel array (image-major: image * scales + level)
+    int strip, seg, pad;
+};
+struct BatchTable {
+    const BatchLevel *levels;
+    const BatchItem *items;
+    void *ws;
+    int64_t counter_off, done_off, status_off;
+    int total_items, n_images, scales, dtype;
+    unsigned wait_limit;
+};
+cudaError_t launch_batch(const BatchTable &B, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st);
+int gauss11_batch_max_ctas_per_sm();
+struct BatchFinalize {
+    const BatchLevel *levels;
+    const void *ws;
+    int n_images, scales, combine;
+    double exps[GBSSIM_MAX_SCALES];
+    double *score_out, *per_scale_out;
+};
+cudaError_t launch_finalize_batch(const BatchFinalize &F, cudaStream_t st);
+
 // Generic path: any k <= GBSSIM_MAX_K, any stride, separable taps.
 struct GenericLaunch {
     ImgDesc x, y;

@@ -92,25 +92,33 @@ __device__ __forceinline__ float u8f(unsigned w, int k) {
 // element k's bits (only the first `ncols` are read).  Keeping the data raw
 // lets the register prefetch defer the conversion until after the barrier,
 // so the load latency overlaps the vertical pass.
-template <typename T>
+// LD = 0: read-only path (__ldg); LD = 1: L2-coherent loads (__ldcg), for
+// data written by other CTAs earlier in the same launch.
+template <int LD, typename U>
+__device__ __forceinline__ U ld(const U *p) {
+    if (LD) return __ldcg(p);
+    return __ldg(p);
+}
+
+template <typename T, int LD = 0>
 __device__ __forceinline__ uint4 load_raw(const T *p, int ncols, bool packed) {
     uint4 r = make_uint4(0u, 0u, 0u, 0u);
     if (packed) {
-        if (sizeof(T) == 1) r.x = __ldg(reinterpret_cast<const unsigned *>(p));
+        if (sizeof(T) == 1) r.x = ld<LD>(reinterpret_cast<const unsigned *>(p));
         else if (sizeof(T) == 2) {
-            const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+            const uint2 v = ld<LD>(reinterpret_cast<const uint2 *>(p));
             r.x = v.x;
             r.y = v.y;
-        } else r = __ldg(reinterpret_cast<const uint4 *>(p));
+        } else r = ld<LD>(reinterpret_cast<const uint4 *>(p));
         return r;
     }
     unsigned v[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int k = 0; k < 4; ++k)
         if (k < ncols) {
-            if (sizeof(T) == 1) v[k] = __ldg(reinterpret_cast<const unsigned char *>(p) + k);
-            else if (sizeof(T) == 2) v[k] = __ldg(reinterpret_cast<const unsigned short *>(p) + k);
-            else v[k] = __ldg(reinterpret_cast<const unsigned *>(p) + k);
+            if (sizeof(T) == 1) v[k] = ld<LD>(reinterpret_cast<const unsigned char *>(p) + k);
+            else if (sizeof(T) == 2) v[k] = ld<LD>(reinterpret_cast<const unsigned short *>(p) + k);
+            else v[k] = ld<LD>(reinterpret_cast<const unsigned *>(p) + k);
         }
     return make_uint4(v[0], v[1], v[2], v[3]);
 }
@@ -146,7 +154,7 @@ __device__ __forceinline__ void put_unit(Smem &S, int r, int q, float4 a, float4
 
 // Stage `nr` input rows starting at absolute row r0 into in rows 0..nr-1
 // (used once per segment, for the first FIRST rows).
-template <typename T>
+template <typename T, int LD = 0>
 __device__ __forceinline__ void stage_direct(Smem &S, const Geo &g, int64_t r0, int nr) {
     for (int t = threadIdx.x; t < nr * QUADS; t += NT) {
         const int r = t / QUADS, q = t - r * QUADS;
@@ -155,8 +163,8 @@ __device__ __forceinline__ void stage_direct(Smem &S, const Geo &g, int64_t r0, 
         const bool packed = g.vec && ncols == 4;
         uint4 rx = make_uint4(0u, 0u, 0u, 0u), ry = rx;
         if (row < g.H && ncols > 0) {
-            rx = load_raw<T>(static_cast<const T *>(g.xb) + row * g.rs + c, ncols, packed);
-            ry = load_raw<T>(static_cast<const T *>(g.yb) + row * g.rs + c, ncols, packed);
+            rx = load_raw<T, LD>(static_cast<const T *>(g.xb) + row * g.rs + c, ncols, packed);
+            ry = load_raw<T, LD>(static_cast<const T *>(g.yb) + row * g.rs + c, ncols, packed);
         }
         put_unit(S, r, q, convert_raw<T>(rx, packed), convert_raw<T>(ry, packed));
     }
@@ -192,7 +200,7 @@ __device__ __forceinline__ void make_units(Units &U, const Geo &g) {
     }
 }
 
-template <typename T>
+template <typename T, int LD = 0>
 __device__ __forceinline__ void prefetch(uint4 (&px)[PFQ], uint4 (&py)[PFQ], const Units &U, const Geo &g,
                                          int64_t r0) {
     const int64_t base = r0 * g.rs;
@@ -200,8 +208,8 @@ __device__ __forceinline__ void prefetch(uint4 (&px)[PFQ], uint4 (&py)[PFQ], con
     for (int i = 0; i < PFQ; ++i) {
         px[i] = py[i] = make_uint4(0u, 0u, 0u, 0u);
         if (U.r[i] >= 0 && r0 + U.r[i] < g.H && U.ncols[i] > 0) {
-            px[i] = load_raw<T>(static_cast<const T *>(g.xb) + base + U.off[i], U.ncols[i], U.packed[i]);
-            py[i] = load_raw<T>(static_cast<const T *>(g.yb) + base + U.off[i], U.ncols[i], U.packed[i]);
+            px[i] = load_raw<T, LD>(static_cast<const T *>(g.xb) + base + U.off[i], U.ncols[i], U.packed[i]);
+            py[i] = load_raw<T, LD>(static_cast<const T *>(g.yb) + base + U.off[i], U.ncols[i], U.packed[i]);
         }
     }
 }
@@ -399,32 +407,39 @@ __device__ __forceinline__ void block_sum2f(float a, float b, float *red, double
         }
 }
 
-template <typename T, bool COEF>
-__global__ void __launch_bounds__(NT, 3) gauss11_kernel(const GaussLaunch L, int strips, int segs) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
-    const int strip = blockIdx.x, seg = blockIdx.y, img = blockIdx.z;
+// One work item: a strip of TW output columns x a segment of output rows of
+// one image.  Used by the grid kernel (one item per CTA) and by the
+// persistent ragged-batch kernel (items pulled from a queue).
+struct Item {
+    const void *xb, *yb;   // image (or pyramid level) base pointers
+    int64_t H, W, rs;
+    int strip, seg, strips, segs, seg_rows;
+    bool vec;
+    float *map;            // image map base (nullable)
+    int64_t map_ld;
+    float *dsx, *dsy;      // next-level planes of this image (nullable)
+    float *coef_img;       // COEF mode: A, B, C planes of this image
+    double2 *partial;      // this item's (sum Q, sum cs) slot
+};
 
+template <typename T, bool COEF, int LD = 0>
+__device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps<K> &taps, const Taps2<K> &taps2,
+                                             const SsimConst &cc, const CoefOut &co) {
     Geo g;
-    g.H = L.x.H;
-    g.W = L.x.W;
-    g.rs = L.x.row_stride;
+    g.H = it.H;
+    g.W = it.W;
+    g.rs = it.rs;
     g.OH = g.H - HALO;
     g.OW = g.W - HALO;
-    g.xb = static_cast<const T *>(L.x.data) + img * L.x.image_stride;
-    g.yb = static_cast<const T *>(L.y.data) + img * L.y.image_stride;
-    g.j0 = (int64_t)strip * TW;
-    g.o0 = (int64_t)seg * L.seg_rows;
-    g.oend = min(g.o0 + (int64_t)L.seg_rows, g.OH);
-    g.own_r1 = (seg == segs - 1) ? g.H : g.o0 + L.seg_rows;
-    g.own_c1 = (strip == strips - 1) ? g.W : g.j0 + TW;
-    g.vec = L.vec;
+    g.xb = it.xb;
+    g.yb = it.yb;
+    g.j0 = (int64_t)it.strip * TW;
+    g.o0 = (int64_t)it.seg * it.seg_rows;
+    g.oend = min(g.o0 + (int64_t)it.seg_rows, g.OH);
+    g.own_r1 = (it.seg == it.segs - 1) ? g.H : g.o0 + it.seg_rows;
+    g.own_c1 = (it.strip == it.strips - 1) ? g.W : g.j0 + TW;
+    g.vec = it.vec;
     const int nchunks = (int)((g.oend - g.o0 + CH - 1) / CH);
-    float *map = L.map ? L.map + img * L.map_is : nullptr;
-    const int64_t dsn = (g.H >> 1) * (g.W >> 1);
-    float *dsx = L.ds_x ? L.ds_x + img * dsn : nullptr;
-    float *dsy = L.ds_y ? L.ds_y + img * dsn : nullptr;
-    float *coef_img = COEF ? L.co.coef + (int64_t)img * 3 * g.OH * g.OW : nullptr;
 
     KSum accQ, accCS;
     uint4 px[PFQ], py[PFQ];
@@ -432,30 +447,150 @@ __global__ void __launch_bounds__(NT, 3) gauss11_kernel(const GaussLaunch L, int
     make_units(U, g);
     const bool col_ok = g.j0 + (threadIdx.x & (TW - 1)) < g.OW;
 
-    stage_direct<T>(S, g, g.o0, FIRST);
+    stage_direct<T, LD>(S, g, g.o0, FIRST);
     __syncthreads();
-    if (dsx) downsample_rows(S, g, g.o0, FIRST, dsx, dsy);
-    horizontal(S, FIRST, 0, L.taps, L.taps2);
+    if (it.dsx) downsample_rows(S, g, g.o0, FIRST, it.dsx, it.dsy);
+    horizontal(S, FIRST, 0, taps, taps2);
     for (int c = 0; c < nchunks; ++c) {
         const bool more = c + 1 < nchunks;
         const int64_t next_r0 = g.o0 + FIRST + (int64_t)CH * c;
-        if (more) prefetch<T>(px, py, U, g, next_r0);
+        if (more) prefetch<T, LD>(px, py, U, g, next_r0);
         __syncthreads();  // ring rows of chunk c complete; staging free
         float cq, ccs;
-        vertical<COEF>(S, g, CH * c, L.taps, L.taps2, L.c, map, L.map_ld, col_ok, L.co, coef_img, cq, ccs);
+        vertical<COEF>(S, g, CH * c, taps, taps2, cc, it.map, it.map_ld, col_ok, co, it.coef_img, cq, ccs);
         accQ.add(cq);
         accCS.add(ccs);
         if (more) store_prefetch<T>(S, px, py, U);
         __syncthreads();  // staging complete; ring rows of chunk c consumed
         if (more) {
-            if (dsx) downsample_rows(S, g, next_r0, CH, dsx, dsy);
-            horizontal(S, CH, FIRST + CH * c, L.taps, L.taps2);
+            if (it.dsx) downsample_rows(S, g, next_r0, CH, it.dsx, it.dsy);
+            horizontal(S, CH, FIRST + CH * c, taps, taps2);
         }
     }
     double a, b;
     block_sum2f(accQ.s - accQ.c, accCS.s - accCS.c, S.red, a, b);
-    if (threadIdx.x == 0)
-        L.partials[((int64_t)img * segs + seg) * strips + strip] = make_double2(a, b);
+    if (threadIdx.x == 0) *it.partial = make_double2(a, b);
+}
+
+template <typename T, bool COEF>
+__global__ void __launch_bounds__(NT, 3) gauss11_kernel(const GaussLaunch L, int strips, int segs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    const int strip = blockIdx.x, seg = blockIdx.y, img = blockIdx.z;
+    Item it;
+    it.H = L.x.H;
+    it.W = L.x.W;
+    it.rs = L.x.row_stride;
+    it.xb = static_cast<const T *>(L.x.data) + img * L.x.image_stride;
+    it.yb = static_cast<const T *>(L.y.data) + img * L.y.image_stride;
+    it.strip = strip;
+    it.seg = seg;
+    it.strips = strips;
+    it.segs = segs;
+    it.seg_rows = L.seg_rows;
+    it.vec = L.vec;
+    it.map = L.map ? L.map + img * L.map_is : nullptr;
+    it.map_ld = L.map_ld;
+    const int64_t dsn = (it.H >> 1) * (it.W >> 1);
+    it.dsx = L.ds_x ? L.ds_x + img * dsn : nullptr;
+    it.dsy = L.ds_y ? L.ds_y + img * dsn : nullptr;
+    it.coef_img = COEF ? L.co.coef + (int64_t)img * 3 * (it.H - HALO) * (it.W - HALO) : nullptr;
+    it.partial = L.partials + ((int64_t)img * segs + seg) * strips + strip;
+    gauss11_item<T, COEF>(S, it, L.taps, L.taps2, L.c, L.co);
+}
+
+// ----------------------------------------------------------------- ragged persistent batch
+//
+// One launch of (#SMs x CTAs-per-SM) CTAs for a whole ragged batch.  Work
+// items (image, level, strip, segment) are listed level-major; each CTA takes
+// the next item from an atomic counter.  A level-j item needs the 2x2 pyramid
+// of its image written by all of its level-(j-1) items: after an item, thread
+// 0 fences and bumps the (image, level) completion counter; before a level-j
+// item it waits (bounded) until the counter of level j-1 reaches that level's
+// item count.  Items are handed out in order, so every item waited on is held
+// by a running CTA that waits only on earlier items: no deadlock.  If a wait
+// exceeds its limit the kernel records GBSSIM_ERR_TIMEOUT in the status word
+// and carries on (the scores are then meaningless but the launch ends).
+// Pooling slots are fixed per item, so scores are deterministic whichever CTA
+// ran which item.
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT, 3) gauss11_batch_kernel(const BatchTable B, Taps<K> taps, Taps2<K> taps2,
+                                                             SsimConst cc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    __shared__ int s_item;
+    char *ws = static_cast<char *>(B.ws);
+    unsigned *counter = reinterpret_cast<unsigned *>(ws + B.counter_off);
+    unsigned *done = reinterpret_cast<unsigned *>(ws + B.done_off);
+    int *status = reinterpret_cast<int *>(ws + B.status_off);
+    CoefOut co;
+    co.coef = nullptr;
+    co.which = 0;
+    co.sx = co.sy = 0.f;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int i = (int)atomicAdd(counter, 1u);
+            int item = i < B.total_items ? i : -1;
+            if (item >= 0) {
+                const BatchItem bi = B.items[item];
+                const BatchLevel &lv = B.levels[bi.level_index];
+                if (lv.level > 0) {
+                    const BatchLevel &prev = B.levels[bi.level_index - 1];
+                    const unsigned *flag = done + (bi.level_index - 1);
+                    unsigned spins = 0;
+                    while (ld_acquire(flag) < (unsigned)prev.wait_target) {
+                        if (++spins > B.wait_limit) {
+                            atomicExch(status, (int)GBSSIM_ERR_TIMEOUT);
+                            break;
+                        }
+                        __nanosleep(256);
+                    }
+                }
+            }
+            s_item = item;
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item < 0) break;
+        const BatchItem bi = B.items[item];
+        const BatchLevel &lv = B.levels[bi.level_index];
+        Item it;
+        it.H = lv.H;
+        it.W = lv.W;
+        it.rs = lv.rs;
+        it.strip = bi.strip;
+        it.seg = bi.seg;
+        it.strips = lv.strips;
+        it.segs = lv.segs;
+        it.seg_rows = lv.seg_rows;
+        it.vec = lv.vec != 0;
+        it.map = nullptr;
+        it.map_ld = 0;
+        it.dsx = lv.ds_off >= 0 ? reinterpret_cast<float *>(ws + lv.ds_off) : nullptr;
+        it.dsy = lv.ds_off >= 0 ? it.dsx + (lv.H >> 1) * (lv.W >> 1) : nullptr;
+        it.coef_img = nullptr;
+        it.partial = reinterpret_cast<double2 *>(ws + lv.part_off) + (int64_t)bi.seg * lv.strips + bi.strip;
+        if (lv.level == 0) {
+            it.xb = lv.x;
+            it.yb = lv.y;
+            gauss11_item<T, false, 0>(S, it, taps, taps2, cc, co);
+        } else {
+            it.xb = ws + lv.x_off;
+            it.yb = ws + lv.x_off + sizeof(float) * lv.H * lv.W;
+            gauss11_item<float, false, 1>(S, it, taps, taps2, cc, co);
+        }
+        __syncthreads();  // every thread's partial and pyramid stores issued
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(done + bi.level_index, 1u);
+        }
+    }
 }
 
 // ----------------------------------------------------------------- generic path
@@ -593,6 +728,47 @@ cudaError_t launch_gauss11(const GaussLaunch &L, cudaStream_t st) {
     case GBSSIM_BF16:
         return coef ? launch_gauss11_t<__nv_bfloat16, true>(L, st) : launch_gauss11_t<__nv_bfloat16, false>(L, st);
     case GBSSIM_F32: return coef ? launch_gauss11_t<float, true>(L, st) : launch_gauss11_t<float, false>(L, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_batch_t(const BatchTable &B, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st) {
+    static bool attr_set[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(gauss11_batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(Smem));
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    Taps2<11> t2;
+    for (int n = 0; n < 11; ++n) t2.g2[n] = make_float2(taps.g[n], taps.g[n]);
+    gauss11_batch_kernel<T><<<grid, NT, sizeof(Smem), st>>>(B, taps, t2, cc);
+    return cudaGetLastError();
+}
+
+// Resident CTAs per SM of the persistent kernel (all dtype instantiations
+// share the launch shape); the >48 KB dynamic shared memory attribute must be
+// set before the occupancy query sees it.
+int gauss11_batch_max_ctas_per_sm() {
+    if (cudaFuncSetAttribute(gauss11_batch_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(Smem)) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gauss11_batch_kernel<uint8_t>, NT, sizeof(Smem)) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+cudaError_t launch_batch(const BatchTable &B, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st) {
+    switch (B.dtype) {
+    case GBSSIM_U8: return launch_batch_t<uint8_t>(B, taps, cc, grid, st);
+    case GBSSIM_F16: return launch_batch_t<__half>(B, taps, cc, grid, st);
+    case GBSSIM_BF16: return launch_batch_t<__nv_bfloat16>(B, taps, cc, grid, st);
+    case GBSSIM_F32: return launch_batch_t<float>(B, taps, cc, grid, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -76,6 +76,52 @@ __global__ void __launch_bounds__(32 * GBSSIM_MAX_SCALES) finalize_msssim_kernel
     }
 }
 
+// Ragged batch: one CTA per image, one warp per scale (item counts differ
+// per image and level).
+__global__ void __launch_bounds__(32 * GBSSIM_MAX_SCALES) finalize_batch_kernel(const BatchFinalize F) {
+    __shared__ double term[GBSSIM_MAX_SCALES], mq[GBSSIM_MAX_SCALES], mcs[GBSSIM_MAX_SCALES];
+    const int img = blockIdx.x, j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S = F.scales;
+    if (j < S) {
+        const BatchLevel &lv = F.levels[img * S + j];
+        const double2 *p = reinterpret_cast<const double2 *>(static_cast<const char *>(F.ws) + lv.part_off);
+        double a = 0.0, b = 0.0;
+        for (int i = lane; i < lv.items; i += 32) {
+            a += p[i].x;
+            b += p[i].y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) {
+            const double inv_n = 1.0 / ((double)(lv.H - 10) * (double)(lv.W - 10));
+            mq[j] = a * inv_n;
+            mcs[j] = b * inv_n;
+            const double m = j == S - 1 ? mq[j] : mcs[j];
+            if (F.combine == GBSSIM_COMBINE_SUM) {
+                double wsum = 0.0;
+                for (int t = 0; t < S; ++t) wsum += F.exps[t];
+                term[j] = F.exps[j] / wsum * m;
+            } else {
+                term[j] = pow(m, F.exps[j]);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double score = F.combine == GBSSIM_COMBINE_SUM ? 0.0 : 1.0;
+        for (int t = 0; t < S; ++t) score = F.combine == GBSSIM_COMBINE_SUM ? score + term[t] : score * term[t];
+        F.score_out[img] = score;
+        if (F.per_scale_out)
+            for (int t = 0; t < S; ++t) {
+                F.per_scale_out[((int64_t)img * S + t) * 2] = mcs[t];
+                F.per_scale_out[((int64_t)img * S + t) * 2 + 1] = mq[t];
+            }
+    }
+}
+
 template <typename T>
 __global__ void downsample_kernel(ImgDesc in, float *out) {
     const int64_t Hh = in.H >> 1, Wh = in.W >> 1;
@@ -119,6 +165,11 @@ cudaError_t launch_finalize_ssim(const double2 *partials, int count, int items_p
 
 cudaError_t launch_finalize_msssim(const MsFinalize &F, cudaStream_t st) {
     finalize_msssim_kernel<<<F.count, 32 * F.scales, 0, st>>>(F);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batch(const BatchFinalize &F, cudaStream_t st) {
+    finalize_batch_kernel<<<F.n_images, 32 * F.scales, 0, st>>>(F);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,14 @@ OP_SSIM, OP_MSSSIM, OP_BACKWARD, OP_BACKWARD_MS, OP_POOL = 0, 1, 2, 3, 4
 POOL_MEAN = 0
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("seg_rows", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("wait_limit", ctypes.c_uint32),
+                ("flags", ctypes.c_int32)]
+
+
+TUNING_TEST_STALL = 1
+
+
 class Plane(ctypes.Structure):
     _fields_ = [("data", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("count", ctypes.c_int32),
                 ("height", ctypes.c_int64), ("width", ctypes.c_int64),
@@ -72,6 +80,12 @@ _SIGS = {
     "gbssim_msssim": ([_P(Plane), _P(Plane), _P(Params), _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
     "gbssim_window_sums": ([_P(Plane), _P(Plane), _i32, _i32, _vp, _vp], ctypes.c_int),
     "gbssim_ssim_map_static": ([_P(Plane), _P(Plane), _P(Params), _vp, _i64, _i64, _vp, _vp], ctypes.c_int),
+    "gbssim_batch_plan": ([_P(Plane), _P(Plane), _i32, _P(Params), _i32, _P(Tuning), _P(_vp)], ctypes.c_int),
+    "gbssim_batch_workspace_size": ([_vp, _P(_sz)], ctypes.c_int),
+    "gbssim_batch_info": ([_vp, _P(_i32), _P(_i32), _P(_i32), _P(_i32)], ctypes.c_int),
+    "gbssim_batch_run": ([_vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "gbssim_batch_status": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+    "gbssim_batch_free": ([_vp], None),
     "gbssim_ssim_backward": ([_P(Plane), _P(Plane), _P(Params), _i32, ctypes.c_double, _vp, _i32, _vp, _i32, _i64,
                               _i64, _vp, _vp, _sz, _vp], ctypes.c_int),
 }
@@ -345,3 +359,84 @@ class SSIMLoss(torch.nn.Module):
 
     def forward(self, x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
         return _SSIMLossFn.apply(x.detach(), y, self.multiscale, dict(self.kw))
+
+
+class BatchPlan:
+    """A ragged batch (gbssim_batch_plan): SSIM or MS-SSIM of pairs of mixed
+    sizes in one persistent kernel launch.  ``xs``/``ys`` are lists of CUDA
+    tensors (H, W) or (N, H, W) of one dtype; the plan is bound to these
+    tensors (keep them alive; refill them in place to score new data).
+
+    ``run()`` enqueues one run and returns the float64 scores (one per image,
+    entries expanded in order).  ``capture()`` records one run into a CUDA
+    graph; ``replay()`` launches it again."""
+
+    def __init__(self, xs, ys, multiscale: bool = False, seg_rows: int = 0, ctas_per_sm: int = 0,
+                 wait_limit: int = 0, flags: int = 0, **kw):
+        if len(xs) != len(ys) or not xs:
+            raise ValueError("xs and ys must be non-empty lists of equal length")
+        self.xs = [_as_batch(t) for t in xs]
+        self.ys = [_as_batch(t) for t in ys]
+        self.device = self.xs[0].device
+        if multiscale:
+            kw.setdefault("exponents", MSSSIM_EXPONENTS[: kw.get("scales", 5)])
+        self.params = make_params(**kw)
+        self.multiscale = bool(multiscale)
+        px = (Plane * len(xs))(*[plane(t) for t in self.xs])
+        py = (Plane * len(ys))(*[plane(t) for t in self.ys])
+        tun = Tuning(int(seg_rows), int(ctas_per_sm), int(wait_limit), int(flags))
+        self._plan = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib.gbssim_batch_plan(px, py, len(xs), ctypes.byref(self.params), int(self.multiscale),
+                                         ctypes.byref(tun), ctypes.byref(self._plan)), "gbssim_batch_plan")
+        n = ctypes.c_size_t()
+        _check(lib.gbssim_batch_workspace_size(self._plan, ctypes.byref(n)), "gbssim_batch_workspace_size")
+        self.ws = torch.empty(max(int(n.value), 1), dtype=torch.uint8, device=self.device)
+        ni, items, grid, rows = (ctypes.c_int32() for _ in range(4))
+        lib.gbssim_batch_info(self._plan, ctypes.byref(ni), ctypes.byref(items), ctypes.byref(grid), ctypes.byref(rows))
+        self.n_images, self.total_items, self.grid, self.seg_rows = ni.value, items.value, grid.value, rows.value
+        scales = self.params.scales if self.multiscale else 1
+        self.scores = torch.empty(self.n_images, dtype=torch.float64, device=self.device)
+        self.per_scale = torch.empty((self.n_images, scales, 2), dtype=torch.float64, device=self.device)
+        self._status = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.graph = None
+
+    def run(self) -> torch.Tensor:
+        _check(lib.gbssim_batch_run(self._plan, self.scores.data_ptr(), self.per_scale.data_ptr(),
+                                    self.ws.data_ptr(), self.ws.numel(), _stream(self.device)),
+               "gbssim_batch_run")
+        return self.scores
+
+    def status(self) -> int:
+        """Status word of the last run (0, or ERR_TIMEOUT); synchronises."""
+        _check(lib.gbssim_batch_status(self._plan, self.ws.data_ptr(), self._status.data_ptr(),
+                                       _stream(self.device)), "gbssim_batch_status")
+        return int(self._status.item())
+
+    def capture(self):
+        """Record one run into a CUDA graph (after one eager warm-up run)."""
+        self.run()
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                self.run()
+        torch.cuda.current_stream(self.device).wait_stream(s)
+        self.graph = g
+        return g
+
+    def replay(self) -> torch.Tensor:
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+        return self.scores
+
+    def __del__(self):
+        try:
+            if self._plan:
+                lib.gbssim_batch_free(self._plan)
+                self._plan = ctypes.c_void_p()
+        except Exception:
+            pass

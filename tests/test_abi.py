@@ -138,3 +138,22 @@ def test_pool_validation(g):
                                   1 << 20, None) == g.ERR_INVALID_ARG  # ld < w
     assert g.lib.gbssim_ssim_pool(m, 10, 10, 10, 1, 0, 42, None, ctypes.c_void_p(0x10), ctypes.c_void_p(0x20),
                                   1 << 20, None) == g.ERR_UNSUPPORTED
+
+
+def test_batch_plan_validation_on_host(g):
+    p = g.make_params()
+    x = (g.Plane * 2)(_plane(g, 100, 120), _plane(g, 50, 60))
+    out = ctypes.c_void_p()
+    assert g.lib.gbssim_batch_plan(x, x, 0, ctypes.byref(p), 0, None, ctypes.byref(out)) == g.ERR_INVALID_ARG
+    p7 = g.make_params(k=7, sigma=1.0)
+    assert g.lib.gbssim_batch_plan(x, x, 2, ctypes.byref(p7), 0, None, ctypes.byref(out)) == g.ERR_UNSUPPORTED
+    p2 = g.make_params(stride=2)
+    assert g.lib.gbssim_batch_plan(x, x, 2, ctypes.byref(p2), 0, None, ctypes.byref(out)) == g.ERR_UNSUPPORTED
+    # 50 x 60 halves to 25 x 30, 12 x 15, then 6 x 7 < 11
+    assert g.lib.gbssim_batch_plan(x, x, 2, ctypes.byref(p), 1, None, ctypes.byref(out)) == g.ERR_TOO_SMALL
+    mixed = (g.Plane * 2)(_plane(g, 100, 120), _plane(g, 50, 60, dtype=3))
+    assert g.lib.gbssim_batch_plan(mixed, mixed, 2, ctypes.byref(p), 0, None, ctypes.byref(out)) == g.ERR_INVALID_ARG
+    bad = g.Tuning(24, 0, 0, 0)   # rows per item must be a multiple of 16
+    assert g.lib.gbssim_batch_plan(x, x, 2, ctypes.byref(p), 0, ctypes.byref(bad), ctypes.byref(out)) \
+        == g.ERR_INVALID_ARG
+    assert out.value is None
