@@ -301,13 +301,14 @@ def colour_score(s_y: float, s_u: float, s_v: float, weights=(6.0, 1.0, 1.0)) ->
     return (wy * s_y + wu * s_u + wv * s_v) / (wy + wu + wv)
 
 
-def temporal_pool(frame_scores, percentile: float = 10.0):
+def temporal_pool(frame_scores, percentile: float = 10.0, r: float = 4.0):
     """Temporal pooling of frame scores (Section "Spatio-temporal Aggregation
-    of Quality Scores"): the temporal mean, the p-th percentile by linear
-    interpolation between order statistics (position h = p/100 (n-1) in the
-    sorted list), and the percentile-pooled mean with r_t = 1 taken over the
-    frames whose score is at or below that percentile (Section "Percentile
-    Pooling")."""
+    of Quality Scores"): the temporal mean; the p-th percentile of the scores
+    by linear interpolation between order statistics (position
+    h = p/100 (n-1) in the sorted list); and percentile pooling (Section
+    "Percentile Pooling"): every score in the lowest p percent (at or below
+    that percentile) is divided by r and the results are averaged,
+    S_PP = (1/n) sum_t Q~(t) with Q~ = Q/r in the lowest p percent, else Q."""
     v = np.sort(_f64(frame_scores).ravel())
     n = v.size
     mean_ = float(v.sum() / n)
@@ -315,5 +316,5 @@ def temporal_pool(frame_scores, percentile: float = 10.0):
     lo = int(math.floor(h))
     hi = min(lo + 1, n - 1)
     pct = float(v[lo] + (h - lo) * (v[hi] - v[lo]))
-    low = v[v <= pct]
-    return mean_, pct, float(low.sum() / low.size)
+    w = np.where(v <= pct, v / r, v)
+    return mean_, pct, float(w.sum() / n)

@@ -370,11 +370,14 @@ def test_colour_combination():
 
 def test_temporal_pooling():
     v = np.array([0.9, 0.5, 0.7, 0.95, 0.6, 0.8, 0.85, 0.75, 0.65, 0.99, 0.55])
-    m, p10, pp = oracle.temporal_pool(v, 10.0)
+    m, p10, pp = oracle.temporal_pool(v, 10.0, r=4.0)
     assert m == pytest.approx(v.mean(), abs=1e-15)
     assert p10 == pytest.approx(np.percentile(v, 10.0), abs=1e-15)   # library routine
-    # n = 11: h = 1.0 -> the second smallest value exactly; PP mean of {0.5, 0.55}
-    assert p10 == 0.55 and pp == pytest.approx(0.525, abs=1e-15)
+    # n = 11: h = 1.0 -> the second smallest value exactly; PP divides {0.5, 0.55} by r
+    assert p10 == 0.55
+    assert pp == pytest.approx((v.sum() - 0.5 - 0.55 + (0.5 + 0.55) / 4.0) / 11, abs=1e-15)
+    # r = 1 leaves every score unchanged: PP reduces to the mean (Section "Percentile Pooling")
+    assert oracle.temporal_pool(v, 10.0, r=1.0)[2] == pytest.approx(m, abs=1e-15)
     r = _rng(17)
     w = r.uniform(0.5, 1.0, 120)
     _, p, _ = oracle.temporal_pool(w, 10.0)
