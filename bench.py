@@ -204,6 +204,41 @@ def run_extras(args, gbssim, synth, x, y, dev, timed, ws):
         del xd, yd
     out["loss_fwd_bwd"] = dict(loss_res, config="32x3x512x512, L=1, loss = 1 - mean score, grad w.r.t. y",
                                headline=loss_res["ssim_fp32"]["value"])
+
+    # ragged batch: 512 pairs drawn from six resolutions 640x360..3840x2160 plus
+    # 64 odd sizes, one persistent launch per run, replayed from a CUDA graph
+    from paper_2101_06354_gb300 import tune
+
+    sizes = synth.ragged_sizes(512, 64)
+    xs, ys = synth.ragged_pairs_u8(sizes, device=dev)
+    px_total = sum(h * w for h, w in sizes)
+    rb = {"pairs": len(sizes), "mpx_pairs": px_total / 1e6}
+    for name, msf in (("ssim", False), ("msssim", True)):
+        rows, ctas, _ = tune.tune(xs, ys, multiscale=msf, reps=2)
+        plan = gbssim.BatchPlan(xs, ys, multiscale=msf, seg_rows=rows, ctas_per_sm=ctas)
+        plan.capture()
+        kk = max(3, args.steps // 50)
+        t = timed(plan.replay, kk) / kk
+        rb[name] = {"value": ws * px_total / (t / 1e3) / 1e6, "unit": UNIT, "ms_per_run": t,
+                    "seg_rows": rows, "ctas_per_sm": ctas, "grid": plan.grid, "items": plan.total_items,
+                    "status": plan.status()}
+        del plan
+    out["ragged_batch"] = rb
+    del xs, ys
+
+    # video: 120 frames of 3840x2160 YUV 4:2:0, per-plane SSIM, 6:1:1 colour
+    # weights, temporal mean / 10th percentile / percentile pooling
+    v = synth.video_yuv420_u8(120, 2160, 3840, device=dev)
+    vx = [v[p][0] for p in "yuv"]
+    vy = [v[p][1] for p in "yuv"]
+    gbssim.video_ssim(vx, vy)
+    kk = max(3, args.steps // 100)
+    t = timed(lambda: gbssim.video_ssim(vx, vy), kk) / kk
+    vpx = 120 * (3840 * 2160 + 2 * 1920 * 1080)
+    fr, ps, vid = gbssim.video_ssim(vx, vy)
+    out["video_yuv420_4k"] = {"value": ws * vpx / (t / 1e3) / 1e6, "unit": UNIT, "ms_per_video": t,
+                              "frames": 120, "mean": vid[0].item(), "p10": vid[1].item(), "pp": vid[2].item()}
+    del v, vx, vy
     return out
 
 

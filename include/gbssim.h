@@ -192,6 +192,25 @@ int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbs
                          int64_t grad_image_stride, double *score_out, void *workspace,
                          size_t workspace_bytes, void *stream);
 
+/* Colour and temporal pooling of a YUV video (any chroma subsampling).
+ * planes = {x_Y, y_Y, x_U, y_U, x_V, y_V}, each a batch of `frames` images
+ * (count = frames, the same for all six); each plane pair is scored at its
+ * own resolution with gbssim_ssim_map's MSSIM.  Then (Section "Channel-wise
+ * SSIM") frame score F(t) = (w_Y S_Y + w_U S_U + w_V S_V) / (w_Y + w_U + w_V)
+ * with weights = {w_Y, w_U, w_V} (e.g. 6, 1, 1 or 0.8, 0.1, 0.1), and
+ * (Sections "Spatio-temporal Aggregation of Quality Scores", "Percentile
+ * Pooling") video_out[0] = mean_t F, video_out[1] = the `percentile`-th
+ * percentile of F (linear interpolation at h = p/100 (frames-1) of the
+ * sorted scores), video_out[2] = percentile pooling: the mean of F after the
+ * scores at or below that percentile are divided by pp_r.
+ *   frame_out (nullable): frames doubles F(t); plane_out (nullable):
+ *   3 x frames doubles S_Y(t) | S_U(t) | S_V(t); video_out: 3 doubles (all
+ *   device).  frames <= 4096.  Workspace: gbssim_video_workspace_size. */
+int gbssim_video_workspace_size(const gbssim_plane planes[6], const gbssim_params *p, size_t *bytes);
+int gbssim_video(const gbssim_plane planes[6], const gbssim_params *p, const double weights[3], double percentile,
+                 double pp_r, double *frame_out, double *plane_out, double *video_out, void *workspace,
+                 size_t workspace_bytes, void *stream);
+
 /* ------------------------------------------------------------------ ragged batch
  * SSIM or MS-SSIM of many pairs of different sizes in ONE persistent kernel
  * launch (plus a memset and a finaliser), suitable for CUDA-graph capture.

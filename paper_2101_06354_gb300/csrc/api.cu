@@ -540,6 +540,77 @@ int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbs
     return GBSSIM_OK;
 }
 
+// Workspace of gbssim_video: per-plane SSIM partials, then the per-plane
+// frame means (3 x frames doubles).
+static int plan_video(const gbssim_plane planes[6], const gbssim_params *p, MsPlan P[3], size_t offs[4],
+                      size_t *bytes) {
+    size_t off = 0;
+    for (int q = 0; q < 3; ++q) {
+        int rc = plan_levels(&planes[2 * q], p, 1, &P[q]);
+        if (rc) return rc;
+        offs[q] = off;
+        off = align_up(off + P[q].bytes);
+    }
+    offs[3] = off;
+    off = align_up(off + 3 * sizeof(double) * planes[0].count);
+    *bytes = off;
+    return GBSSIM_OK;
+}
+
+int gbssim_video_workspace_size(const gbssim_plane planes[6], const gbssim_params *p, size_t *bytes) {
+    if (!planes || !bytes) return GBSSIM_ERR_INVALID_ARG;
+    for (int q = 0; q < 3; ++q) {
+        int rc = check_pair(&planes[2 * q], &planes[2 * q + 1]);
+        if (rc) return rc;
+    }
+    int rc = check_params(p);
+    if (rc) return rc;
+    MsPlan P[3];
+    size_t offs[4];
+    return plan_video(planes, p, P, offs, bytes);
+}
+
+int gbssim_video(const gbssim_plane planes[6], const gbssim_params *p, const double weights[3], double percentile,
+                 double pp_r, double *frame_out, double *plane_out, double *video_out, void *workspace,
+                 size_t workspace_bytes, void *stream) {
+    if (!planes || !weights || !video_out) return GBSSIM_ERR_INVALID_ARG;
+    for (int q = 0; q < 3; ++q) {
+        int rc = check_pair(&planes[2 * q], &planes[2 * q + 1]);
+        if (rc) return rc;
+        if (planes[2 * q].count != planes[0].count) return GBSSIM_ERR_INVALID_ARG;
+    }
+    int rc = check_params(p);
+    if (rc) return rc;
+    const int n = planes[0].count;
+    if (n > kVideoMaxFrames) return GBSSIM_ERR_UNSUPPORTED;
+    if (!(percentile >= 0.0 && percentile <= 100.0) || !(pp_r > 0.0) || !isfinite(pp_r)) return GBSSIM_ERR_INVALID_ARG;
+    const double wsum = weights[0] + weights[1] + weights[2];
+    if (!isfinite(wsum) || wsum == 0.0) return GBSSIM_ERR_INVALID_ARG;
+    MsPlan P[3];
+    size_t offs[4], need;
+    rc = plan_video(planes, p, P, offs, &need);
+    if (rc) return rc;
+    if (!workspace || workspace_bytes < need) return GBSSIM_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)workspace;
+    double *means = plane_out ? plane_out : (double *)(ws + offs[3]);
+    for (int q = 0; q < 3; ++q) {
+        const gbssim_plane *x = &planes[2 * q], *y = &planes[2 * q + 1];
+        Level L = P[q].lv[0];
+        fix_box_items(L, x, y, p);
+        double2 *part = (double2 *)(ws + offs[q] + L.part_off);
+        cudaError_t e = run_level(L, desc_of(x), desc_of(y), x->dtype, n, p, nullptr, 0, 0, part, nullptr, nullptr, st);
+        if (e != cudaSuccess) return GBSSIM_ERR_CUDA;
+        const int64_t OH = out_dim(x->height, p->k, p->stride), OW = out_dim(x->width, p->k, p->stride);
+        e = launch_finalize_ssim(part, n, L.items, 1.0 / ((double)OH * (double)OW), means + (size_t)q * n, st);
+        if (e != cudaSuccess) return GBSSIM_ERR_CUDA;
+    }
+    return launch_video_pool(means, means + n, means + 2 * (size_t)n, n, weights, percentile, pp_r, frame_out,
+                             video_out, st) == cudaSuccess
+               ? GBSSIM_OK
+               : GBSSIM_ERR_CUDA;
+}
+
 int gbssim_window_sums(const gbssim_plane *x, const gbssim_plane *y, int32_t k, int32_t stride,
                        int64_t *sums_out, void *stream) {
     int rc = check_pair(x, y);

@@ -261,6 +261,10 @@ struct GradLaunch {
 };
 cudaError_t launch_grad(const GradLaunch &G, cudaStream_t st);
 
+cudaError_t launch_video_pool(const double *sY, const double *sU, const double *sV, int n, const double w[3],
+                              double pct, double r, double *frame_out, double *video_out, cudaStream_t st);
+constexpr int kVideoMaxFrames = 4096;  // 32 KB of shared memory for the sort
+
 cudaError_t launch_pool_mean(const float *map, int64_t h, int64_t w, int64_t ld, int count,
                              int64_t image_stride, double2 *partials, double *out,
                              cudaStream_t st);

@@ -168,6 +168,93 @@ cudaError_t launch_finalize_msssim(const MsFinalize &F, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Colour + temporal pooling of per-plane frame scores (one CTA): frame score
+// F(t) = (wY S_Y + wU S_U + wV S_V) / (wY + wU + wV) (Section "Channel-wise
+// SSIM"); temporal mean; p-th percentile of F with linear interpolation at
+// h = p/100 (n-1) of the sorted scores; percentile pooling S_PP = mean of F
+// with the scores at or below that percentile divided by r (Section
+// "Percentile Pooling").  Sums run in a fixed tree order (deterministic).
+constexpr int VP_THREADS = 1024;
+
+__device__ double vp_block_sum(double v, double *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) red[0] = r;
+    __syncthreads();
+    r = red[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(VP_THREADS) video_pool_kernel(const double *sY, const double *sU, const double *sV,
+                                                                int n, double wY, double wU, double wV, double pct,
+                                                                double r, double *frame_out, double *video_out) {
+    extern __shared__ double sv[];  // P doubles, P = next power of two >= n
+    __shared__ double red[32];
+    int P = 1;
+    while (P < n) P <<= 1;
+    const double wsum = wY + wU + wV;
+    double local = 0.0;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        double f = INFINITY;
+        if (i < n) {
+            f = (wY * sY[i] + wU * sU[i] + wV * sV[i]) / wsum;
+            if (frame_out) frame_out[i] = f;
+            local += f;
+        }
+        sv[i] = f;
+    }
+    const double mean = vp_block_sum(local, red) / n;
+    // bitonic sort, ascending
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const double a = sv[i], b = sv[l];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        sv[i] = b;
+                        sv[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    const double h = pct / 100.0 * (n - 1);
+    const int lo = (int)floor(h);
+    const int hi = lo + 1 < n ? lo + 1 : n - 1;
+    const double pv = sv[lo] + (h - lo) * (sv[hi] - sv[lo]);
+    double lp = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) lp += sv[i] <= pv ? sv[i] / r : sv[i];
+    const double pp = vp_block_sum(lp, red) / n;
+    if (threadIdx.x == 0) {
+        video_out[0] = mean;
+        video_out[1] = pv;
+        video_out[2] = pp;
+    }
+}
+
+cudaError_t launch_video_pool(const double *sY, const double *sU, const double *sV, int n, const double w[3],
+                              double pct, double r, double *frame_out, double *video_out, cudaStream_t st) {
+    int P = 1;
+    while (P < n) P <<= 1;
+    video_pool_kernel<<<1, VP_THREADS, sizeof(double) * P, st>>>(sY, sU, sV, n, w[0], w[1], w[2], pct, r, frame_out,
+                                                                  video_out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize_batch(const BatchFinalize &F, cudaStream_t st) {
     finalize_batch_kernel<<<F.n_images, 32 * F.scales, 0, st>>>(F);
     return cudaGetLastError();

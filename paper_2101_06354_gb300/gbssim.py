@@ -80,6 +80,9 @@ _SIGS = {
     "gbssim_msssim": ([_P(Plane), _P(Plane), _P(Params), _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
     "gbssim_window_sums": ([_P(Plane), _P(Plane), _i32, _i32, _vp, _vp], ctypes.c_int),
     "gbssim_ssim_map_static": ([_P(Plane), _P(Plane), _P(Params), _vp, _i64, _i64, _vp, _vp], ctypes.c_int),
+    "gbssim_video_workspace_size": ([_P(Plane), _P(Params), _P(_sz)], ctypes.c_int),
+    "gbssim_video": ([_P(Plane), _P(Params), _P(ctypes.c_double), ctypes.c_double, ctypes.c_double, _vp, _vp, _vp,
+                      _vp, _sz, _vp], ctypes.c_int),
     "gbssim_batch_plan": ([_P(Plane), _P(Plane), _i32, _P(Params), _i32, _P(Tuning), _P(_vp)], ctypes.c_int),
     "gbssim_batch_workspace_size": ([_vp, _P(_sz)], ctypes.c_int),
     "gbssim_batch_info": ([_vp, _P(_i32), _P(_i32), _P(_i32), _P(_i32)], ctypes.c_int),
@@ -359,6 +362,37 @@ class SSIMLoss(torch.nn.Module):
 
     def forward(self, x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
         return _SSIMLossFn.apply(x.detach(), y, self.multiscale, dict(self.kw))
+
+
+def video_ssim(xs, ys, weights=(6.0, 1.0, 1.0), percentile: float = 10.0, pp_r: float = 4.0, **kw):
+    """Colour + temporal SSIM of a YUV video (gbssim_video).  xs = (Y, U, V)
+    reference planes and ys = (Y, U, V) distorted planes, each a CUDA tensor
+    (frames, H_p, W_p).  Returns (frame_scores, plane_scores (3, frames),
+    (mean, percentile, percentile_pooled))."""
+    if len(xs) != 3 or len(ys) != 3:
+        raise ValueError("expected (Y, U, V) planes")
+    pl = []
+    keep = []
+    for a, b in zip(xs, ys):
+        a, b = _as_batch(a), _as_batch(b)
+        if a.stride() != b.stride():
+            a, b = a.contiguous(), b.contiguous()
+        keep += [a, b]
+        pl += [plane(a), plane(b)]
+    planes = (Plane * 6)(*pl)
+    p = make_params(**kw)
+    dev = keep[0].device
+    n = ctypes.c_size_t()
+    _check(lib.gbssim_video_workspace_size(planes, ctypes.byref(p), ctypes.byref(n)), "gbssim_video_workspace_size")
+    ws = torch.empty(max(int(n.value), 1), dtype=torch.uint8, device=dev)
+    frames = keep[0].shape[0]
+    fr = torch.empty(frames, dtype=torch.float64, device=dev)
+    ps = torch.empty((3, frames), dtype=torch.float64, device=dev)
+    vid = torch.empty(3, dtype=torch.float64, device=dev)
+    w = (ctypes.c_double * 3)(*[float(t) for t in weights])
+    _check(lib.gbssim_video(planes, ctypes.byref(p), w, float(percentile), float(pp_r), fr.data_ptr(), ps.data_ptr(),
+                            vid.data_ptr(), ws.data_ptr(), ws.numel(), _stream(dev)), "gbssim_video")
+    return fr, ps, vid
 
 
 class BatchPlan:
