@@ -93,8 +93,13 @@ typedef struct gbssim_params {
     int32_t scales;   /* MS-SSIM scales, 1..GBSSIM_MAX_SCALES (5 in MS-SSIM) */
     double exponents[GBSSIM_MAX_SCALES];  /* beta_j per scale, finest first */
     int32_t combine;  /* gbssim_combine */
-    int32_t flags;    /* reserved, must be 0 */
+    int32_t flags;    /* GBSSIM_FLAG_* (0 = defaults) */
 } gbssim_params;
+
+/* uint8 box windows at stride 4 with 16-byte aligned planes: load tiles with
+ * double-buffered bulk tensor copies (TMA) instead of per-thread vector loads.
+ * Same results (exact integer sums); which is faster depends on the GPU. */
+#define GBSSIM_FLAG_BOX_TMA 1
 
 /* Operation codes for gbssim_workspace_size. */
 typedef enum gbssim_op {
@@ -293,6 +298,10 @@ int gbssim_ssim_map_static(const gbssim_plane *x, const gbssim_plane *y, const g
  * row-major map order, image b at sums_out + 5*b*OH*OW.  k <= GBSSIM_MAX_K. */
 int gbssim_window_sums(const gbssim_plane *x, const gbssim_plane *y, int32_t k, int32_t stride,
                        int64_t *sums_out, void *stream);
+/* As gbssim_window_sums with GBSSIM_FLAG_* flags (GBSSIM_FLAG_BOX_TMA selects
+ * the bulk-tensor-copy tile loader for stride 4 on aligned planes). */
+int gbssim_window_sums_ex(const gbssim_plane *x, const gbssim_plane *y, int32_t k, int32_t stride, int32_t flags,
+                          int64_t *sums_out, void *stream);
 
 #ifdef __cplusplus
 }

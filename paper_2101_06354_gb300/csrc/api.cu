@@ -50,7 +50,7 @@ int check_params(const gbssim_params *p) {
     for (int j = 0; j < p->scales; ++j)
         if (!isfinite(p->exponents[j])) return GBSSIM_ERR_INVALID_ARG;
     if (p->combine != GBSSIM_COMBINE_PRODUCT && p->combine != GBSSIM_COMBINE_SUM) return GBSSIM_ERR_INVALID_ARG;
-    if (p->flags != 0) return GBSSIM_ERR_INVALID_ARG;
+    if (p->flags & ~GBSSIM_FLAG_BOX_TMA) return GBSSIM_ERR_INVALID_ARG;
     return GBSSIM_OK;
 }
 
@@ -120,6 +120,7 @@ struct Level {
 
 struct MsPlan {
     Level lv[GBSSIM_MAX_SCALES];
+    size_t counter_off, done_off, status_off, zero_bytes;  // persistent path counters
     size_t bytes;
 };
 
@@ -148,6 +149,11 @@ int plan_levels(const gbssim_plane *x, const gbssim_params *p, int scales, MsPla
         H >>= 1;
         W >>= 1;
     }
+    P->counter_off = off;
+    P->done_off = off + 16;
+    P->status_off = P->done_off + sizeof(unsigned) * (size_t)scales * x->count;
+    P->zero_bytes = P->status_off + 16 - P->counter_off;
+    off = align_up(P->counter_off + P->zero_bytes);
     P->bytes = off;
     return GBSSIM_OK;
 }
@@ -203,6 +209,7 @@ cudaError_t run_level(const Level &L, const ImgDesc &dx, const ImgDesc &dy, int 
         B.map_is = map_is;
         B.partials = partials;
         B.sums_out = nullptr;
+        B.use_tma = (p->flags & GBSSIM_FLAG_BOX_TMA) != 0;
         const double k4 = pow((double)p->k, 4.0);
         const double c1 = (p->K1 * p->L) * (p->K1 * p->L), c2 = (p->K2 * p->L) * (p->K2 * p->L);
         B.C1k4 = (float)(c1 * k4);
@@ -238,10 +245,83 @@ cudaError_t run_level(const Level &L, const ImgDesc &dx, const ImgDesc &dy, int 
 // MS-SSIM forward over a planned workspace: level kernels (pyramid fused
 // where the path allows), then the finaliser.  Shared by gbssim_msssim and
 // the MS-SSIM backward.
+// Rows per work item of the persistent MS-SSIM path (the ragged-batch
+// autotuner's choice on 1080p / 4K batches).
+constexpr int kPersistentSegRows = 512;
+
 int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
                           const MsPlan &P, char *ws, double *score_out, double *per_scale_out,
                           cudaStream_t st) {
     const int S = p->scales, n = x->count;
+    bool persistent = true;
+    for (int j = 0; j < S; ++j) persistent = persistent && P.lv[j].path == PATH_GAUSS11;
+    if (persistent) {
+        // one launch over all levels and images: level-major items, a level-j
+        // item of an image waits (bounded) for that image's level-(j-1) items
+        UniformBatch U;
+        memset(&U, 0, sizeof U);
+        U.x = x->data;
+        U.y = y->data;
+        U.rs = x->row_stride;
+        U.image_stride = desc_of(x).image_stride;
+        U.dtype = x->dtype;
+        U.count = n;
+        U.scales = S;
+        int64_t begin = 0;
+        MsFinalize F;
+        memset(&F, 0, sizeof F);
+        for (int j = 0; j < S; ++j) {
+            const Level &L = P.lv[j];
+            UniformLevel &u = U.lv[j];
+            u.H = L.H;
+            u.W = L.W;
+            u.seg_rows = kPersistentSegRows;
+            u.strips = (int)((L.W - 10 + 63) / 64);
+            u.segs = (int)((L.H - 10 + kPersistentSegRows - 1) / kPersistentSegRows);
+            u.items_per_image = u.strips * u.segs;
+            if (j == 0) {
+                const size_t esz = x->dtype == GBSSIM_U8 ? 1 : x->dtype == GBSSIM_F32 ? 4 : 2;
+                const uintptr_t vb = 4 * esz;
+                u.vec = ((uintptr_t)x->data % vb == 0) && ((uintptr_t)y->data % vb == 0) && (U.rs % 4 == 0) &&
+                        (U.image_stride % 4 == 0);
+            } else {
+                u.vec = L.W % 4 == 0;
+            }
+            u.item_begin = begin;
+            begin += (int64_t)u.items_per_image * n;
+            u.x_off = j > 0 ? (int64_t)L.plane_off : -1;
+            u.part_off = (int64_t)L.part_off;
+            const int64_t OH = L.H - 10, OW = L.W - 10;
+            F.lv[j].partials = (const double2 *)(ws + L.part_off);
+            F.lv[j].items_per_image = u.items_per_image;
+            F.lv[j].inv_n = 1.0 / ((double)OH * (double)OW);
+            F.exps[j] = p->exponents[j];
+        }
+        U.total_items = begin;
+        U.ws = ws;
+        U.counter_off = (int64_t)P.counter_off;
+        U.done_off = (int64_t)P.done_off;
+        U.status_off = (int64_t)P.status_off;
+        U.wait_limit = 1u << 22;
+        if (begin > 0x7fffffff) return GBSSIM_ERR_UNSUPPORTED;
+        if (cudaMemsetAsync(ws + P.counter_off, 0, P.zero_bytes, st) != cudaSuccess) return GBSSIM_ERR_CUDA;
+        Taps<11> taps;
+        make_taps(p, taps.g);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int per_sm = gauss11_batch_max_ctas_per_sm();
+        if (per_sm < 1) return GBSSIM_ERR_CUDA;
+        const int64_t want = (int64_t)sms * per_sm;
+        const int grid = (int)(want < begin ? want : begin);
+        if (launch_uniform(U, taps, make_const(p), grid, st) != cudaSuccess) return GBSSIM_ERR_CUDA;
+        F.scales = S;
+        F.count = n;
+        F.combine = p->combine;
+        F.score_out = score_out;
+        F.per_scale_out = per_scale_out;
+        return launch_finalize_msssim(F, st) == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
+    }
     ImgDesc dx = desc_of(x), dy = desc_of(y);
     int dtype = x->dtype;
     MsPlan Pl = P;  // level 0 may take the aligned box layout
@@ -613,6 +693,11 @@ int gbssim_video(const gbssim_plane planes[6], const gbssim_params *p, const dou
 
 int gbssim_window_sums(const gbssim_plane *x, const gbssim_plane *y, int32_t k, int32_t stride,
                        int64_t *sums_out, void *stream) {
+    return gbssim_window_sums_ex(x, y, k, stride, 0, sums_out, stream);
+}
+
+int gbssim_window_sums_ex(const gbssim_plane *x, const gbssim_plane *y, int32_t k, int32_t stride, int32_t flags,
+                          int64_t *sums_out, void *stream) {
     int rc = check_pair(x, y);
     if (rc) return rc;
     if (x->dtype != GBSSIM_U8) return GBSSIM_ERR_UNSUPPORTED;
@@ -626,6 +711,7 @@ int gbssim_window_sums(const gbssim_plane *x, const gbssim_plane *y, int32_t k, 
     B.k = k;
     B.stride = stride;
     B.sums_out = sums_out;
+    B.use_tma = (flags & GBSSIM_FLAG_BOX_TMA) != 0;
     return launch_box_u8(B, (cudaStream_t)stream) == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
 }
 

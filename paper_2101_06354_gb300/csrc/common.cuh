@@ -181,6 +181,27 @@ struct BatchTable {
     unsigned wait_limit;
 };
 cudaError_t launch_batch(const BatchTable &B, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st);
+
+// Equally sized images (gbssim_msssim's persistent path): no table, the item
+// list is arithmetic; offsets are into gbssim_msssim's workspace.
+struct UniformLevel {
+    int64_t H, W;
+    int strips, segs, seg_rows, items_per_image, vec, pad;
+    int64_t item_begin;   // first item of this level (level-major order)
+    int64_t x_off;        // levels >= 1: x planes of all images, then y planes
+    int64_t part_off;     // pooling slots: image-major, items_per_image each
+};
+struct UniformBatch {
+    const void *x, *y;
+    int64_t rs, image_stride;  // level 0, in elements
+    int dtype, count, scales;
+    UniformLevel lv[GBSSIM_MAX_SCALES];
+    int64_t total_items;
+    void *ws;
+    int64_t counter_off, done_off, status_off;
+    unsigned wait_limit;
+};
+cudaError_t launch_uniform(const UniformBatch &U, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st);
 int gauss11_batch_max_ctas_per_sm();
 struct BatchFinalize {
     const BatchLevel *levels;
@@ -214,6 +235,7 @@ struct BoxLaunch {
     double2 *partials;  // nullable when sums_out is set
     int64_t *sums_out;  // nullable: 5 int64 per window position
     float C1k4, C2k4;   // C1 * k^4, C2 * k^4
+    bool use_tma;       // stride-4 aligned tiles through bulk tensor copies
 };
 int box_items_ks(int64_t OH, int64_t OW, int k, int s);  // workspace sizing (max over layouts)
 bool box_aligned16(const ImgDesc &x, const ImgDesc &y);

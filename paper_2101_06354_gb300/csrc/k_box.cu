@@ -18,12 +18,20 @@
 //  * integral-image path (any k <= 63, any stride): five summed-area tables
 //    of a <= 64 x 64 input tile in shared memory (int32, zero first row and
 //    column) and the paper's four-corner formula per window.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 
 namespace gbssim {
 namespace {
 
 constexpr int NT = 256;
+// stride-4 tiles: 64 x 16 blocks of 4 x 4 pixels loaded, VTOW x (17 - m)
+// windows produced; VTOW is a multiple of 4 so every tile starts on a
+// 16-byte boundary (tile column b starts at pixel 4 * VTOW * b) and
+// VTOW + m - 1 <= 64.
+constexpr int VBW = 64, VBH = 16, VTOW = 60;
 
 struct BoxOut {
     int64_t s1x, s1y, s2x, s2y, sxy;
@@ -52,6 +60,69 @@ __device__ __forceinline__ void box_formula32(int s1x, int s1y, int s2x, int s2y
     const float A2 = fmaf(2.f, (float)nxy, C2k4), B2 = ((float)nxx + (float)nyy) + C2k4;
     cs = __fdividef(A2, B2);
     q = __fdividef(A1, B1) * cs;
+}
+
+// Same formula from the five window sums held as exact floats (integers below
+// 2^24: k <= 12 keeps S2 <= 65025 * 144).  k^2 S2 - S1^2 is formed without
+// cancellation: S1^2 = p + e exactly (p = fl(S1 S1), e = fma(S1, S1, -p),
+// Dekker's TwoProduct), then fma(k^2, S2, -p) rounds once and e is taken off
+// (two roundings in all, relative to the result).
+__device__ __forceinline__ float exact_diff(float kk, float s2, float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    return fmaf(kk, s2, -p) - e;
+}
+__device__ __forceinline__ void box_formula_f(float s1x, float s1y, float s2x, float s2y, float sxy, float kk,
+                                              float C1k4, float C2k4, float &q, float &cs) {
+    const float A1 = fmaf(2.f * s1x, s1y, C1k4), B1 = fmaf(s1x, s1x, fmaf(s1y, s1y, C1k4));
+    const float nxy = exact_diff(kk, sxy, s1x, s1y);
+    const float nxx = exact_diff(kk, s2x, s1x, s1x), nyy = exact_diff(kk, s2y, s1y, s1y);
+    const float A2 = fmaf(2.f, nxy, C2k4), B2 = (nxx + nyy) + C2k4;
+    cs = __fdividef(A2, B2);
+    q = __fdividef(A1, B1) * cs;
+}
+
+// Output phase of the stride-4 kernels: M x M blocks per window, block sums
+// in shared memory as exact floats.
+template <int M>
+__device__ __forceinline__ void box_outputs(const float (&Bs)[5][VBH][VBW + 1], const BoxLaunch &L, int img,
+                                            int64_t a0, int64_t b0, int tow, int toh, int64_t OH, int64_t OW,
+                                            float &accQ, float &accCS) {
+    const float kk = (float)(L.k * L.k);
+    for (int o = threadIdx.x; o < tow * toh; o += NT) {
+        const int oi = o / tow, oj = o - oi * tow;
+        const int64_t a = a0 + oi, b = b0 + oj;
+        if (a >= OH || b >= OW) continue;
+        float acc[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            float sacc = 0.f;
+#pragma unroll
+            for (int u = 0; u < M; ++u)
+#pragma unroll
+                for (int v = 0; v < M; ++v) sacc += Bs[q][oi + u][oj + v];
+            acc[q] = sacc;
+        }
+        if (L.sums_out) {
+            int64_t *dst = L.sums_out + 5 * (img * OH * OW + a * OW + b);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) dst[q] = (int64_t)acc[q];
+            continue;
+        }
+        float qv, cs;
+        box_formula_f(acc[0], acc[1], acc[2], acc[3], acc[4], kk, L.C1k4, L.C2k4, qv, cs);
+        accQ += qv;
+        accCS += cs;
+        if (L.map) L.map[img * L.map_is + a * L.map_ld + b] = qv;
+    }
+}
+
+__device__ __forceinline__ void box_outputs_m(int m, const float (&Bs)[5][VBH][VBW + 1], const BoxLaunch &L,
+                                              int img, int64_t a0, int64_t b0, int tow, int toh, int64_t OH,
+                                              int64_t OW, float &accQ, float &accCS) {
+    if (m == 1) box_outputs<1>(Bs, L, img, a0, b0, tow, toh, OH, OW, accQ, accCS);
+    else if (m == 2) box_outputs<2>(Bs, L, img, a0, b0, tow, toh, OH, OW, accQ, accCS);
+    else box_outputs<3>(Bs, L, img, a0, b0, tow, toh, OH, OW, accQ, accCS);
 }
 
 // Sum (a, b) over the CTA: fp32 pairwise tree inside each warp, fp64 across
@@ -85,12 +156,12 @@ __device__ __forceinline__ void block_sum2f(float a, float b, float *red, double
 // loads 64 x 16 blocks (256 x 64 pixels) and produces VTOW x (17-m) windows;
 // VTOW is a multiple of 4 so that every tile starts on a 16-byte boundary
 // (tile column b starts at pixel 4 * VTOW * b), and VTOW + m - 1 <= 64.
-constexpr int VBW = 64, VBH = 16, VTOW = 60;
+
 
 __global__ void __launch_bounds__(NT) box_s4_kernel(const BoxLaunch L, int tiles_x, int tiles_y) {
-    __shared__ int Bs[5][VBH][VBW + 1];
+    __shared__ float Bs[5][VBH][VBW + 1];
     __shared__ float red[2 * NT / 32];
-    const int m = L.k >> 2, kk = L.k * L.k;
+    const int m = L.k >> 2;
     const int tow = VTOW, toh = VBH - m + 1;
     const int img = blockIdx.z;
     const int64_t H = L.x.H, W = L.x.W, rs = L.x.row_stride;
@@ -136,42 +207,198 @@ __global__ void __launch_bounds__(NT) box_s4_kernel(const BoxLaunch L, int tiles
             sxy = __dp4a(wx, wy, sxy);
         }
         const int bj = 4 * qd + b;
-        Bs[0][bi][bj] = (int)sx;
-        Bs[1][bi][bj] = (int)sy;
-        Bs[2][bi][bj] = (int)sxx;
-        Bs[3][bi][bj] = (int)syy;
-        Bs[4][bi][bj] = (int)sxy;
+        Bs[0][bi][bj] = (float)sx;
+        Bs[1][bi][bj] = (float)sy;
+        Bs[2][bi][bj] = (float)sxx;
+        Bs[3][bi][bj] = (float)syy;
+        Bs[4][bi][bj] = (float)sxy;
     }
     __syncthreads();
 
     float accQ = 0.f, accCS = 0.f;
-    for (int t = threadIdx.x; t < tow * toh; t += NT) {
-        const int oi = t / tow, oj = t - oi * tow;
-        const int64_t a = a0 + oi, b = b0 + oj;
-        if (a >= OH || b >= OW) continue;
-        int acc[5] = {0, 0, 0, 0, 0};
-        for (int u = 0; u < m; ++u)
-            for (int v = 0; v < m; ++v)
-#pragma unroll
-                for (int q = 0; q < 5; ++q) acc[q] += Bs[q][oi + u][oj + v];
-        if (L.sums_out) {
-            int64_t *dst = L.sums_out + 5 * (img * OH * OW + a * OW + b);
-#pragma unroll
-            for (int q = 0; q < 5; ++q) dst[q] = acc[q];
-            continue;
-        }
-        float q, cs;
-        box_formula32(acc[0], acc[1], acc[2], acc[3], acc[4], kk, L.C1k4, L.C2k4, q, cs);
-        accQ += q;
-        accCS += cs;
-        if (L.map) L.map[img * L.map_is + a * L.map_ld + b] = q;
-    }
+    box_outputs_m(m, Bs, L, img, a0, b0, tow, toh, OH, OW, accQ, accCS);
     if (L.partials) {
         double da, db;
         block_sum2f(accQ, accCS, red, da, db);
         if (threadIdx.x == 0)
             L.partials[((int64_t)img * tiles_y + blockIdx.y) * tiles_x + blockIdx.x] = make_double2(da, db);
     }
+}
+
+// ------------------------------------------------------------------ stride-4 TMA path
+//
+// Persistent CTAs walk their tiles round-robin (tile t = blockIdx.x + k *
+// gridDim.x, so the pooling slots stay deterministic).  Per tile one thread
+// issues two 3-D bulk tensor copies (x and y: 256 x 64 bytes of image z at
+// (x0, y0)) into one of two shared-memory stages and arms that stage's
+// mbarrier with the expected byte count; the copy of tile k+2 is in flight
+// while tile k is summed.  Out-of-image bytes arrive as zeros and only feed
+// windows outside the map.  Every mbarrier wait is bounded: on timeout the
+// CTA writes NaN into the pooling slots of its remaining tiles (the score
+// then reads NaN), waits (bounded) for its own copies still in flight and
+// returns.
+constexpr int TMA_W = 256, TMA_H = 64;          // bytes per row, rows per tile
+constexpr unsigned TMA_TILE = TMA_W * TMA_H;    // bytes per image per tile
+constexpr unsigned kWaitLimit = 1u << 26;
+
+struct __align__(128) TmaSmem {
+    unsigned char st[2][2][TMA_H][TMA_W];  // [stage][x|y][row][byte]
+    float Bs[5][VBH][VBW + 1];
+    float red[2 * NT / 32];
+    unsigned long long bar[2];
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
+    for (unsigned i = 0; i < kWaitLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__global__ void __launch_bounds__(NT) box_tma_kernel(const __grid_constant__ CUtensorMap tmx,
+                                                     const __grid_constant__ CUtensorMap tmy, const BoxLaunch L,
+                                                     int tiles_x, int tiles_y) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TmaSmem &S = *reinterpret_cast<TmaSmem *>(smem_raw);
+    const int m = L.k >> 2;
+    const int toh = VBH - m + 1;
+    const int64_t OH = out_dim(L.x.H, L.k, 4), OW = out_dim(L.x.W, L.k, 4);
+    const int per_img = tiles_x * tiles_y;
+    const int total = per_img * L.count;
+    const int ntiles = blockIdx.x < total ? (total - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int k, int stage) {
+        const int t = blockIdx.x + k * gridDim.x;
+        const int img = t / per_img, rem = t - img * per_img;
+        const int ty = rem / tiles_x, tx = rem - ty * tiles_x;
+        const int x0 = tx * VTOW * 4, y0 = ty * toh * 4;
+        mbar_expect_tx(&S.bar[stage], 2 * TMA_TILE);
+        tma_load_3d(&S.st[stage][0][0][0], &tmx, x0, y0, img, &S.bar[stage]);
+        tma_load_3d(&S.st[stage][1][0][0], &tmy, x0, y0, img, &S.bar[stage]);
+    };
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 2 && k < ntiles; ++k) issue(k, k);
+
+    const int bi = threadIdx.x >> 4, qd = threadIdx.x & 15;
+    for (int k = 0; k < ntiles; ++k) {
+        const int stage = k & 1;
+        const unsigned parity = (k >> 1) & 1;
+        const bool ok = mbar_wait_bounded(&S.bar[stage], parity);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                for (int r = k; r < ntiles; ++r) {
+                    const int t = blockIdx.x + r * gridDim.x;
+                    if (L.partials) L.partials[t] = make_double2(nan(""), nan(""));
+                }
+                // drain this CTA's copies still in flight (tiles k and k+1)
+                for (int r = k; r < ntiles && r < k + 2; ++r) mbar_wait_bounded(&S.bar[r & 1], (r >> 1) & 1);
+            }
+            __syncthreads();
+            return;
+        }
+        const int t = blockIdx.x + k * gridDim.x;
+        const int img = t / per_img, rem = t - img * per_img;
+        const int tyi = rem / tiles_x, txi = rem - tyi * tiles_x;
+        // block sums of the four 4x4 blocks (rows 4bi..4bi+3, columns 16qd..16qd+15)
+        uint4 vx[4], vy[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            vx[r] = *reinterpret_cast<const uint4 *>(&S.st[stage][0][4 * bi + r][16 * qd]);
+            vy[r] = *reinterpret_cast<const uint4 *>(&S.st[stage][1][4 * bi + r][16 * qd]);
+        }
+        __syncthreads();  // the stage is consumed: refill it with tile k + 2
+        if (threadIdx.x == 0 && k + 2 < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(k + 2, stage);
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            unsigned sx = 0, sy = 0, sxx = 0, syy = 0, sxy = 0;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const unsigned wx = b == 0 ? vx[r].x : b == 1 ? vx[r].y : b == 2 ? vx[r].z : vx[r].w;
+                const unsigned wy = b == 0 ? vy[r].x : b == 1 ? vy[r].y : b == 2 ? vy[r].z : vy[r].w;
+                sx = __dp4a(wx, 0x01010101u, sx);
+                sy = __dp4a(wy, 0x01010101u, sy);
+                sxx = __dp4a(wx, wx, sxx);
+                syy = __dp4a(wy, wy, syy);
+                sxy = __dp4a(wx, wy, sxy);
+            }
+            const int bj = 4 * qd + b;
+            S.Bs[0][bi][bj] = (float)sx;
+            S.Bs[1][bi][bj] = (float)sy;
+            S.Bs[2][bi][bj] = (float)sxx;
+            S.Bs[3][bi][bj] = (float)syy;
+            S.Bs[4][bi][bj] = (float)sxy;
+        }
+        __syncthreads();
+        const int64_t a0 = (int64_t)tyi * toh, b0 = (int64_t)txi * VTOW;
+        float accQ = 0.f, accCS = 0.f;
+        box_outputs_m(m, S.Bs, L, img, a0, b0, VTOW, toh, OH, OW, accQ, accCS);
+        double da, db;
+        block_sum2f(accQ, accCS, S.red, da, db);  // also orders the Bs reads before the next tile's writes
+        if (threadIdx.x == 0 && L.partials) L.partials[t] = make_double2(da, db);
+    }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no
+// link-time dependency on the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool encode_u8_map(CUtensorMap *map, const ImgDesc &d, int count) {
+    auto fn = tensor_map_encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)d.W, (cuuint64_t)d.H, (cuuint64_t)count};
+    const cuuint64_t strides[2] = {(cuuint64_t)d.row_stride, (cuuint64_t)d.image_stride};
+    const cuuint32_t box[3] = {TMA_W, TMA_H, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void *>(d.data), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // ------------------------------------------------------------------ block path
@@ -395,7 +622,26 @@ cudaError_t launch_box_u8(const BoxLaunch &L, cudaStream_t st) {
     int tx, ty;
     box_tiles(OH, OW, L.k, L.stride, &tx, &ty, s4);
     dim3 grid(tx, ty, L.count);
-    if (s4) {
+    CUtensorMap mx, my;
+    const bool tma = L.use_tma && s4 && L.count >= 1 && L.x.image_stride % 16 == 0 &&
+                     encode_u8_map(&mx, L.x, L.count) && encode_u8_map(&my, L.y, L.count);
+    if (tma) {
+        static bool attr_set[64] = {};
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (!attr_set[dev]) {
+            cudaError_t e = cudaFuncSetAttribute(box_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)sizeof(TmaSmem));
+            if (e != cudaSuccess) return e;
+            attr_set[dev] = true;
+        }
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, box_tma_kernel, NT, sizeof(TmaSmem));
+        const int total = tx * ty * L.count;
+        const int g = min(total, max(1, sms * max(per_sm, 1)));
+        box_tma_kernel<<<g, NT, sizeof(TmaSmem), st>>>(mx, my, L, tx, ty);
+    } else if (s4) {
         box_s4_kernel<<<grid, NT, 0, st>>>(L, tx, ty);
     } else if (use_block_path(L.k, L.stride)) {
         const uintptr_t bx = (uintptr_t)L.x.data, by = (uintptr_t)L.y.data;

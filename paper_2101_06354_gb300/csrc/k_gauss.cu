@@ -519,48 +519,25 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     return v;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(NT, 3) gauss11_batch_kernel(const BatchTable B, Taps<K> taps, Taps2<K> taps2,
-                                                             SsimConst cc) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
-    __shared__ int s_item;
-    char *ws = static_cast<char *>(B.ws);
-    unsigned *counter = reinterpret_cast<unsigned *>(ws + B.counter_off);
-    unsigned *done = reinterpret_cast<unsigned *>(ws + B.done_off);
-    int *status = reinterpret_cast<int *>(ws + B.status_off);
-    CoefOut co;
-    co.coef = nullptr;
-    co.which = 0;
-    co.sx = co.sy = 0.f;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const int i = (int)atomicAdd(counter, 1u);
-            int item = i < B.total_items ? i : -1;
-            if (item >= 0) {
-                const BatchItem bi = B.items[item];
-                const BatchLevel &lv = B.levels[bi.level_index];
-                if (lv.level > 0) {
-                    const BatchLevel &prev = B.levels[bi.level_index - 1];
-                    const unsigned *flag = done + (bi.level_index - 1);
-                    unsigned spins = 0;
-                    while (ld_acquire(flag) < (unsigned)prev.wait_target) {
-                        if (++spins > B.wait_limit) {
-                            atomicExch(status, (int)GBSSIM_ERR_TIMEOUT);
-                            break;
-                        }
-                        __nanosleep(256);
-                    }
-                }
-            }
-            s_item = item;
-        }
-        __syncthreads();
-        const int item = s_item;
-        if (item < 0) break;
+// What one work item needs, from either source below.
+struct Resolved {
+    Item it;          // all fields but xb / yb
+    const void *xb, *yb;
+    bool pyramid;     // level >= 1: float planes written earlier in this launch
+    int done_index;   // completion counter this item bumps
+    int dep_index;    // counter it waits on (-1: none)
+    unsigned dep_target;
+};
+
+// Ragged batches: per-(image, level) records and a per-item list built by
+// the host plan (gbssim_batch_plan).
+struct TableSource {
+    BatchTable B;
+    __device__ int total() const { return B.total_items; }
+    __device__ void resolve(int item, char *ws, Resolved &R) const {
         const BatchItem bi = B.items[item];
         const BatchLevel &lv = B.levels[bi.level_index];
-        Item it;
+        Item &it = R.it;
         it.H = lv.H;
         it.W = lv.W;
         it.rs = lv.rs;
@@ -576,19 +553,125 @@ __global__ void __launch_bounds__(NT, 3) gauss11_batch_kernel(const BatchTable B
         it.dsy = lv.ds_off >= 0 ? it.dsx + (lv.H >> 1) * (lv.W >> 1) : nullptr;
         it.coef_img = nullptr;
         it.partial = reinterpret_cast<double2 *>(ws + lv.part_off) + (int64_t)bi.seg * lv.strips + bi.strip;
+        R.pyramid = lv.level > 0;
         if (lv.level == 0) {
-            it.xb = lv.x;
-            it.yb = lv.y;
-            gauss11_item<T, false, 0>(S, it, taps, taps2, cc, co);
+            R.xb = lv.x;
+            R.yb = lv.y;
         } else {
-            it.xb = ws + lv.x_off;
-            it.yb = ws + lv.x_off + sizeof(float) * lv.H * lv.W;
-            gauss11_item<float, false, 1>(S, it, taps, taps2, cc, co);
+            R.xb = ws + lv.x_off;
+            R.yb = ws + lv.x_off + sizeof(float) * lv.H * lv.W;
         }
+        R.done_index = bi.level_index;
+        R.dep_index = lv.level > 0 ? bi.level_index - 1 : -1;
+        R.dep_target = lv.level > 0 ? (unsigned)B.levels[bi.level_index - 1].wait_target : 0u;
+    }
+};
+
+// Batches of equally sized images (gbssim_msssim): the item list is
+// arithmetic (level-major, then image, segment, strip), so no table exists;
+// the pyramid and pooling slots use gbssim_msssim's workspace layout.
+struct UniformSource {
+    UniformBatch U;
+    __device__ int total() const { return (int)U.total_items; }
+    __device__ void resolve(int item, char *ws, Resolved &R) const {
+        int j = 0;
+        while (j + 1 < U.scales && item >= U.lv[j + 1].item_begin) ++j;
+        const UniformLevel &lv = U.lv[j];
+        const int local = item - (int)lv.item_begin;
+        const int img = local / lv.items_per_image, rem = local - img * lv.items_per_image;
+        const int seg = rem / lv.strips, strip = rem - seg * lv.strips;
+        Item &it = R.it;
+        it.H = lv.H;
+        it.W = lv.W;
+        it.rs = j == 0 ? U.rs : lv.W;
+        it.strip = strip;
+        it.seg = seg;
+        it.strips = lv.strips;
+        it.segs = lv.segs;
+        it.seg_rows = lv.seg_rows;
+        it.vec = lv.vec != 0;
+        it.map = nullptr;
+        it.map_ld = 0;
+        const int64_t plane = lv.H * lv.W;
+        if (j + 1 < U.scales) {
+            const int64_t nplane = (lv.H >> 1) * (lv.W >> 1);
+            it.dsx = reinterpret_cast<float *>(ws + U.lv[j + 1].x_off) + img * nplane;
+            it.dsy = reinterpret_cast<float *>(ws + U.lv[j + 1].x_off) + (U.count + img) * nplane;
+        } else {
+            it.dsx = it.dsy = nullptr;
+        }
+        it.coef_img = nullptr;
+        it.partial = reinterpret_cast<double2 *>(ws + lv.part_off) + (int64_t)img * lv.items_per_image + rem;
+        R.pyramid = j > 0;
+        if (j == 0) {
+            const size_t esz = U.dtype == GBSSIM_U8 ? 1 : U.dtype == GBSSIM_F32 ? 4 : 2;
+            R.xb = static_cast<const char *>(U.x) + esz * img * U.image_stride;
+            R.yb = static_cast<const char *>(U.y) + esz * img * U.image_stride;
+        } else {
+            R.xb = reinterpret_cast<const float *>(ws + lv.x_off) + img * plane;
+            R.yb = reinterpret_cast<const float *>(ws + lv.x_off) + (U.count + img) * plane;
+        }
+        R.done_index = img * U.scales + j;
+        R.dep_index = j > 0 ? img * U.scales + j - 1 : -1;
+        R.dep_target = j > 0 ? (unsigned)U.lv[j - 1].items_per_image : 0u;
+    }
+};
+
+template <typename T, typename Src>
+__global__ void __launch_bounds__(NT, 3) gauss11_persistent_kernel(const Src src, void *ws_ptr, int64_t counter_off,
+                                                                  int64_t done_off, int64_t status_off,
+                                                                  unsigned wait_limit, Taps<K> taps, Taps2<K> taps2,
+                                                                  SsimConst cc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    __shared__ int s_item, s_late;
+    char *ws = static_cast<char *>(ws_ptr);
+    unsigned *counter = reinterpret_cast<unsigned *>(ws + counter_off);
+    unsigned *done = reinterpret_cast<unsigned *>(ws + done_off);
+    int *status = reinterpret_cast<int *>(ws + status_off);
+    CoefOut co;
+    co.coef = nullptr;
+    co.which = 0;
+    co.sx = co.sy = 0.f;
+    const int total = src.total();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int i = (int)atomicAdd(counter, 1u);
+            const int item = i < total ? i : -1;
+            int late = 0;
+            if (item >= 0) {
+                Resolved R;
+                src.resolve(item, ws, R);
+                if (R.dep_index >= 0) {
+                    const unsigned *flag = done + R.dep_index;
+                    unsigned spins = 0;
+                    while (ld_acquire(flag) < R.dep_target) {
+                        if (++spins > wait_limit) {
+                            atomicExch(status, (int)GBSSIM_ERR_TIMEOUT);
+                            late = 1;
+                            break;
+                        }
+                        __nanosleep(256);
+                    }
+                }
+            }
+            s_item = item;
+            s_late = late;
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item < 0) break;
+        Resolved R;
+        src.resolve(item, ws, R);
+        R.it.xb = R.xb;
+        R.it.yb = R.yb;
+        if (!R.pyramid) gauss11_item<T, false, 0>(S, R.it, taps, taps2, cc, co);
+        else gauss11_item<float, false, 1>(S, R.it, taps, taps2, cc, co);
         __syncthreads();  // every thread's partial and pyramid stores issued
         if (threadIdx.x == 0) {
+            if (s_late) *R.it.partial = make_double2(nan(""), nan(""));  // the score reads NaN
             __threadfence();
-            atomicAdd(done + bi.level_index, 1u);
+            atomicAdd(done + R.done_index, 1u);
         }
     }
 }
@@ -732,45 +815,65 @@ cudaError_t launch_gauss11(const GaussLaunch &L, cudaStream_t st) {
     return cudaErrorInvalidValue;
 }
 
-template <typename T>
-cudaError_t launch_batch_t(const BatchTable &B, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st) {
+template <typename T, typename Src>
+cudaError_t launch_persistent_t(const Src &src, void *ws, int64_t counter_off, int64_t done_off, int64_t status_off,
+                                unsigned wait_limit, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st) {
     static bool attr_set[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_set[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(gauss11_batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(Smem));
+        cudaError_t e = cudaFuncSetAttribute(gauss11_persistent_kernel<T, Src>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
     Taps2<11> t2;
     for (int n = 0; n < 11; ++n) t2.g2[n] = make_float2(taps.g[n], taps.g[n]);
-    gauss11_batch_kernel<T><<<grid, NT, sizeof(Smem), st>>>(B, taps, t2, cc);
+    gauss11_persistent_kernel<T, Src><<<grid, NT, sizeof(Smem), st>>>(src, ws, counter_off, done_off, status_off,
+                                                                     wait_limit, taps, t2, cc);
     return cudaGetLastError();
 }
 
-// Resident CTAs per SM of the persistent kernel (all dtype instantiations
-// share the launch shape); the >48 KB dynamic shared memory attribute must be
-// set before the occupancy query sees it.
+template <typename Src>
+cudaError_t launch_persistent(int dtype, const Src &src, void *ws, int64_t counter_off, int64_t done_off,
+                              int64_t status_off, unsigned wait_limit, const Taps<11> &taps, SsimConst cc, int grid,
+                              cudaStream_t st) {
+    switch (dtype) {
+    case GBSSIM_U8:
+        return launch_persistent_t<uint8_t>(src, ws, counter_off, done_off, status_off, wait_limit, taps, cc, grid, st);
+    case GBSSIM_F16:
+        return launch_persistent_t<__half>(src, ws, counter_off, done_off, status_off, wait_limit, taps, cc, grid, st);
+    case GBSSIM_BF16:
+        return launch_persistent_t<__nv_bfloat16>(src, ws, counter_off, done_off, status_off, wait_limit, taps, cc,
+                                                  grid, st);
+    case GBSSIM_F32:
+        return launch_persistent_t<float>(src, ws, counter_off, done_off, status_off, wait_limit, taps, cc, grid, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Resident CTAs per SM of the persistent kernels (all instantiations share
+// the launch shape); the >48 KB dynamic shared memory attribute must be set
+// before the occupancy query sees it.
 int gauss11_batch_max_ctas_per_sm() {
-    if (cudaFuncSetAttribute(gauss11_batch_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(Smem)) != cudaSuccess)
+    auto kern = gauss11_persistent_kernel<uint8_t, TableSource>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem)) != cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gauss11_batch_kernel<uint8_t>, NT, sizeof(Smem)) !=
-        cudaSuccess)
-        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, sizeof(Smem)) != cudaSuccess) return 0;
     return n;
 }
 
 cudaError_t launch_batch(const BatchTable &B, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st) {
-    switch (B.dtype) {
-    case GBSSIM_U8: return launch_batch_t<uint8_t>(B, taps, cc, grid, st);
-    case GBSSIM_F16: return launch_batch_t<__half>(B, taps, cc, grid, st);
-    case GBSSIM_BF16: return launch_batch_t<__nv_bfloat16>(B, taps, cc, grid, st);
-    case GBSSIM_F32: return launch_batch_t<float>(B, taps, cc, grid, st);
-    }
-    return cudaErrorInvalidValue;
+    TableSource src{B};
+    return launch_persistent(B.dtype, src, B.ws, B.counter_off, B.done_off, B.status_off, B.wait_limit, taps, cc,
+                             grid, st);
+}
+
+cudaError_t launch_uniform(const UniformBatch &U, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st) {
+    UniformSource src{U};
+    return launch_persistent(U.dtype, src, U.ws, U.counter_off, U.done_off, U.status_off, U.wait_limit, taps, cc,
+                             grid, st);
 }
 
 int generic_items(int64_t OH, int64_t OW) {

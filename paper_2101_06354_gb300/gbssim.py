@@ -44,6 +44,7 @@ WIN_GAUSSIAN, WIN_BOX = 0, 1
 COMBINE_PRODUCT, COMBINE_SUM = 0, 1
 OP_SSIM, OP_MSSSIM, OP_BACKWARD, OP_BACKWARD_MS, OP_POOL = 0, 1, 2, 3, 4
 POOL_MEAN = 0
+FLAG_BOX_TMA = 1
 
 
 class Tuning(ctypes.Structure):
@@ -79,6 +80,7 @@ _SIGS = {
     "gbssim_ssim_pool": ([_vp, _i64, _i64, _i64, _i32, _i64, _i32, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
     "gbssim_msssim": ([_P(Plane), _P(Plane), _P(Params), _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
     "gbssim_window_sums": ([_P(Plane), _P(Plane), _i32, _i32, _vp, _vp], ctypes.c_int),
+    "gbssim_window_sums_ex": ([_P(Plane), _P(Plane), _i32, _i32, _i32, _vp, _vp], ctypes.c_int),
     "gbssim_ssim_map_static": ([_P(Plane), _P(Plane), _P(Params), _vp, _i64, _i64, _vp, _vp], ctypes.c_int),
     "gbssim_video_workspace_size": ([_P(Plane), _P(Params), _P(_sz)], ctypes.c_int),
     "gbssim_video": ([_P(Plane), _P(Params), _P(ctypes.c_double), ctypes.c_double, ctypes.c_double, _vp, _vp, _vp,
@@ -118,7 +120,7 @@ _DTYPES = {torch.uint8: U8, torch.float16: F16, torch.bfloat16: BF16, torch.floa
 
 def make_params(window: str = "gaussian", k: int = 11, sigma: float = 1.5, K1: float = 0.01,
                 K2: float = 0.03, L: float = 255.0, stride: int = 1, scales: int = 5,
-                exponents=None, combine: str = "product") -> Params:
+                exponents=None, combine: str = "product", flags: int = 0) -> Params:
     p = Params()
     lib.gbssim_params_default(ctypes.byref(p))
     p.window = {"gaussian": WIN_GAUSSIAN, "box": WIN_BOX}[window]
@@ -130,6 +132,7 @@ def make_params(window: str = "gaussian", k: int = 11, sigma: float = 1.5, K1: f
         for j in range(MAX_SCALES):
             p.exponents[j] = float(exponents[j]) if j < len(exponents) else 0.0
     p.combine = {"product": COMBINE_PRODUCT, "sum": COMBINE_SUM}[combine]
+    p.flags = int(flags)
     return p
 
 
@@ -256,15 +259,15 @@ def msssim(x: torch.Tensor, y: torch.Tensor, per_scale: bool = False, ws: torch.
     return (score, per) if per_scale else score
 
 
-def window_sums(x: torch.Tensor, y: torch.Tensor, k: int, stride: int = 1) -> torch.Tensor:
+def window_sums(x: torch.Tensor, y: torch.Tensor, k: int, stride: int = 1, flags: int = 0) -> torch.Tensor:
     """Exact int64 window sums (N, OH, OW, 5) of a uint8 pair batch."""
     host, dev, xb, yb = _prepare(x, y)
     n, h, w = xb.shape
     oh, ow = out_shape(h, w, k, stride)
     out = torch.empty((n, max(oh, 0), max(ow, 0), 5), dtype=torch.int64, device=dev)
     px, py = plane(xb), plane(yb)
-    _check(lib.gbssim_window_sums(ctypes.byref(px), ctypes.byref(py), int(k), int(stride),
-                                  out.data_ptr(), _stream(dev)), "gbssim_window_sums")
+    _check(lib.gbssim_window_sums_ex(ctypes.byref(px), ctypes.byref(py), int(k), int(stride), int(flags),
+                                     out.data_ptr(), _stream(dev)), "gbssim_window_sums_ex")
     return out.cpu() if host else out
 
 

@@ -82,7 +82,7 @@ def test_workspace_sizes(g):
 
 @pytest.mark.parametrize("field,value,status", [
     ("k", 0, -1), ("k", 64, -1), ("stride", 0, -1), ("scales", 0, -1), ("scales", 9, -1),
-    ("window", 7, -1), ("sigma", 0.0, -1), ("L", -1.0, -1), ("combine", 3, -1), ("flags", 1, -1),
+    ("window", 7, -1), ("sigma", 0.0, -1), ("L", -1.0, -1), ("combine", 3, -1), ("flags", 2, -1),
 ])
 def test_bad_params_rejected(g, field, value, status):
     p = g.make_params()

@@ -180,6 +180,18 @@ def test_window_sums_bit_exact(g, synth, k, s, h, w):
     np.testing.assert_array_equal(got, ref)
 
 
+@pytest.mark.parametrize("flags", [0, 1])
+@pytest.mark.parametrize("k,n,h,w", [(8, 3, 100, 160), (4, 2, 70, 64), (12, 2, 300, 1040), (8, 5, 1080, 1920)])
+def test_window_sums_batched_aligned(g, synth, k, n, h, w, flags):
+    """Batched, 16-byte aligned planes (vector loads, or with flags=1 the
+    bulk-tensor-copy loader), widths below and above one 256-byte tile,
+    ragged last tiles."""
+    x, y = synth.luma_pairs_u8(n, h, w)
+    got = g.window_sums(x.to(DEV), y.to(DEV), k, 4, flags=flags).cpu().numpy()
+    for i in range(n):
+        np.testing.assert_array_equal(got[i], oracle.box_sums(x[i].numpy(), y[i].numpy(), k, 4))
+
+
 def test_window_sums_unaligned_and_extremes(g):
     # odd row stride forces the byte-gather path; 255 everywhere stresses int ranges
     x = torch.full((1, 40, 51), 255, dtype=torch.uint8)
@@ -200,6 +212,17 @@ def test_box_ssim_u8(g, synth, k, s, w):
         ref_mean, ref_q, _, _ = oracle.box_ssim(x[i].numpy(), y[i].numpy(), k, s)
         _check_map(qmap[i].cpu().numpy(), ref_q)
         assert abs(mean[i].item() - ref_mean) <= POOL_TOL
+
+
+@pytest.mark.parametrize("k", [4, 8, 12])
+def test_box_ssim_tma_loader_matches(g, synth, k):
+    x, y = synth.luma_pairs_u8(3, 333, 1040)
+    a, ma = g.ssim(x.to(DEV), y.to(DEV), return_map=True, window="box", k=k, stride=4)
+    b, mb = g.ssim(x.to(DEV), y.to(DEV), return_map=True, window="box", k=k, stride=4, flags=g.FLAG_BOX_TMA)
+    assert torch.equal(ma, mb)
+    assert torch.allclose(a, b, rtol=0, atol=1e-9)
+    ref_mean, ref_q, _, _ = oracle.box_ssim(x[1].numpy(), y[1].numpy(), k, 4)
+    _check_map(mb[1].cpu().numpy(), ref_q)
 
 
 def test_box_ssim_adversarial(g):
