@@ -391,7 +391,7 @@ int plan_backward(const gbssim_plane *x, const gbssim_params *p, int multiscale,
     off = align_up(off + sizeof(double2) * (size_t)max_items * x->count);
     const int64_t OH = out_dim(x->height, p->k, 1), OW = out_dim(x->width, p->k, 1);
     B->coef_off = off;
-    off = align_up(off + 3 * sizeof(float) * (size_t)OH * OW * x->count);
+    off = align_up(off + 3 * sizeof(float) * (size_t)OH * coef_ld(OW) * x->count);
     B->grad_off[0] = 0;
     for (int j = 1; j < S; ++j) {
         B->grad_off[j] = off;

@@ -80,8 +80,12 @@ struct SsimConst {
 // a fixed shift s (L/2), the contribution of window p to dQ/dy(q) is
 //   w(q - p) [A(p) + (y(q) - s) B(p) + (x(q) - s) C(p)]
 // with A = D_mu - 2 (mu_y - s) D_sy - (mu_x - s) D_sxy, B = 2 D_sy, C = D_sxy.
+// Row pitch (floats) of the coefficient planes: OW rounded up to 4 so rows
+// start on 16-byte boundaries.
+__host__ __device__ inline int64_t coef_ld(int64_t OW) { return (OW + 3) & ~(int64_t)3; }
+
 struct CoefOut {
-    float *coef;   // nullable: A, B, C planes (OH x OW each), image b at coef + 3*b*OH*OW
+    float *coef;   // nullable: A, B, C planes (OH rows x coef_ld(OW)), image b at coef + 3*b*OH*coef_ld(OW)
     int which;     // 0: Q, 1: cs
     float sx, sy;  // shifts
 };

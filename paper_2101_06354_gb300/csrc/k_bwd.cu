@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(NT) grad_kernel(const GradLaunch L) {
     const int img = blockIdx.z;
     const int64_t H = L.x.H, W = L.x.W, OH = H - hk, OW = W - hk;
     const int64_t r0 = (int64_t)blockIdx.y * TH, c0 = (int64_t)blockIdx.x * TW;
-    const int64_t plane = OH * OW;
+    const int64_t cld = coef_ld(OW), plane = OH * cld;
     const float *coef = L.coef + (int64_t)img * 3 * plane;
 
     if (threadIdx.x == 0) {
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(NT) grad_kernel(const GradLaunch L) {
         const int r = rem / RW, c = rem - r * RW;
         const int64_t pr = r0 - hk + r, pc = c0 - hk + c;
         float v = 0.f;
-        if (pr >= 0 && pr < OH && pc >= 0 && pc < OW) v = __ldg(coef + m * plane + pr * OW + pc);
+        if (pr >= 0 && pr < OH && pc >= 0 && pc < OW) v = __ldg(coef + m * plane + pr * cld + pc);
         raw[t] = v;
     }
     __syncthreads();
@@ -108,32 +108,94 @@ __global__ void __launch_bounds__(NT) grad_kernel(const GradLaunch L) {
     }
 }
 
-// ------------------------------------------------------------ 11-tap specialisation
+// ------------------------------------------------------------ 11-tap strip kernel
 //
-// Same computation, register-blocked: (A, B) travel as float2 pairs (packed
-// f32x2 instructions), C as a scalar; each thread filters 4 adjacent columns
-// of one row in the horizontal pass and 4 adjacent rows of one column in the
-// vertical pass, so every shared-memory value loaded feeds up to 4 outputs.
+// The same computation organised like the forward kernel: a CTA owns a strip
+// of 64 gradient columns and a segment of rows and walks it in chunks of 16
+// rows.  Gradient row q needs coefficient rows q-10..q; numbering coefficient
+// rows from the segment start minus 10, output row t uses ring rows t..t+10,
+// so each coefficient row is filtered horizontally once per segment.  The
+// maps are staged with 16-byte asynchronous copies (cp.async, zero-filled
+// outside the map), double-buffered so the next chunk's rows arrive while the
+// current chunk is filtered.
 constexpr int K11 = 11, H11 = K11 - 1;
-constexpr int RH11 = TH + H11, RW11 = 4 * ((TW + H11 + 3) / 4);  // 42 x 76
+constexpr int GCH = 16, GFIRST = GCH + H11;   // rows per chunk / first stage
+constexpr int GRING = 32, GDUP = 10, GRROWS = GRING + GDUP;
+constexpr int GQ = 20, GSW = 4 * GQ;          // staged quads / floats per row (columns c0-12 .. c0+67)
 
 struct __align__(16) Grad11Smem {
-    float2 ab[RH11][RW11];
-    float c[RH11][RW11];
-    float2 hab[RH11][TW];
-    float hc[RH11][TW];
+    float st[3][GFIRST + GCH][GSW];   // staging: [map][row][col]; rows 0..25 buffer 0, 26..41 buffer 1
+    float h[3][GRROWS][TW];           // ring of horizontal results
 };
 
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Issue the copies of `nr` coefficient rows starting at map row pr0 into
+// staging rows row0..row0+nr-1 (all three maps).
+__device__ __forceinline__ void stage_coef(Grad11Smem &S, const float *coef, int64_t plane, int64_t cld, int64_t OH,
+                                           int64_t OW, int64_t pr0, int nr, int row0, int64_t pc0) {
+    for (int t = threadIdx.x; t < 3 * nr * GQ; t += NT) {
+        const int m = t / (nr * GQ), rem = t - m * nr * GQ;
+        const int r = rem / GQ, q = rem - r * GQ;
+        const int64_t pr = pr0 + r, pc = pc0 + 4 * q;
+        int bytes = 0;
+        const float *src = coef;
+        if (pr >= 0 && pr < OH && pc >= 0 && pc < OW) {
+            bytes = (int)(min((int64_t)4, OW - pc) * 4);
+            src = coef + m * plane + pr * cld + pc;
+        }
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(&S.st[m][row0 + r][4 * q])),
+                     "l"(src), "r"(bytes)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Horizontal pass over staged rows row0..row0+nr-1 into ring rows (rel0 + r).
+__device__ __forceinline__ void grad_horizontal(Grad11Smem &S, int row0, int nr, int rel0, const TapsDyn &t) {
+    for (int task = threadIdx.x; task < 3 * nr * (TW / 4); task += NT) {
+        const int m = task / (nr * (TW / 4)), rem = task - m * nr * (TW / 4);
+        const int r = rem >> 4, g4 = (rem & 15) * 4;
+        float v[16];
+        const float4 *src = reinterpret_cast<const float4 *>(&S.st[m][row0 + r][g4]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 a = src[k];
+            v[4 * k] = a.x;
+            v[4 * k + 1] = a.y;
+            v[4 * k + 2] = a.z;
+            v[4 * k + 3] = a.w;
+        }
+        // output column j = g4 + o (gradient column c0 + j) takes staged columns j + 2 .. j + 12:
+        // h(j) = sum_n w(n) M(c0 + j - n), staged index j + 12 - n
+        float h[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 2; i < 16; ++i)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                const int n = o + 12 - i;
+                if (n >= 0 && n < K11) h[o] = fmaf(t.g[n], v[i], h[o]);
+            }
+        const int slot = (rel0 + r) & (GRING - 1);
+        const float4 hv = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4 *>(&S.h[m][slot][g4]) = hv;
+        if (slot < GDUP) *reinterpret_cast<float4 *>(&S.h[m][slot + GRING][g4]) = hv;
+    }
+}
+
 template <typename T, typename G>
-__global__ void __launch_bounds__(NT) grad11_kernel(const GradLaunch L, Taps2<K11> t2) {
+__global__ void __launch_bounds__(NT, 3) grad11_kernel(const GradLaunch L, int strips, int segs, int seg_rows) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Grad11Smem &S = *reinterpret_cast<Grad11Smem *>(smem_raw);
     __shared__ float fac;
-    const int img = blockIdx.z;
+    const int strip = blockIdx.x, seg = blockIdx.y, img = blockIdx.z;
     const int64_t H = L.x.H, W = L.x.W, OH = H - H11, OW = W - H11;
-    const int64_t r0 = (int64_t)blockIdx.y * TH, c0 = (int64_t)blockIdx.x * TW;
-    const int64_t plane = OH * OW;
+    const int64_t cld = coef_ld(OW), plane = OH * cld;
     const float *coef = L.coef + (int64_t)img * 3 * plane;
+    const int64_t c0 = (int64_t)strip * TW, q0 = (int64_t)seg * seg_rows;
+    const int64_t qend = min(q0 + (int64_t)seg_rows, H);
+    const int nchunks = (int)((qend - q0 + GCH - 1) / GCH);
+    const int64_t pr0 = q0 - H11, pc0 = c0 - 12;
 
     if (threadIdx.x == 0) {
         double f = L.base_scale;
@@ -143,115 +205,75 @@ __global__ void __launch_bounds__(NT) grad11_kernel(const GradLaunch L, Taps2<K1
                 f *= L.ms_beta_hat;
             } else {
                 const int Sc = L.ms_scales, j = L.ms_level;
-                const double m = L.ms_per_scale[((int64_t)img * Sc + j) * 2 + (j == Sc - 1 ? 1 : 0)];
-                f *= L.ms_score[img] * L.ms_beta / m;
+                const double mv = L.ms_per_scale[((int64_t)img * Sc + j) * 2 + (j == Sc - 1 ? 1 : 0)];
+                f *= L.ms_score[img] * L.ms_beta / mv;
             }
         }
         fac = (float)f;
     }
-    // stage positions [r0 - 10, r0 + TH) x [c0 - 10, c0 + RW11 - 10), zero outside the map
-    for (int t = threadIdx.x; t < RH11 * RW11; t += NT) {
-        const int r = t / RW11, c = t - r * RW11;
-        const int64_t pr = r0 - H11 + r, pc = c0 - H11 + c;
-        float a = 0.f, b = 0.f, cc = 0.f;
-        if (pr >= 0 && pr < OH && pc >= 0 && pc < OW) {
-            const float *src = coef + pr * OW + pc;
-            a = __ldg(src);
-            b = __ldg(src + plane);
-            cc = __ldg(src + 2 * plane);
-        }
-        S.ab[r][c] = make_float2(a, b);
-        S.c[r][c] = cc;
-    }
+    // chunk c's staged rows: c == 0 rows 0..25; c >= 1 rows 0..15 (c even) or 26..41 (c odd)
+    auto buf_row = [](int c) { return (c & 1) ? GFIRST : 0; };
+    stage_coef(S, coef, plane, cld, OH, OW, pr0, GFIRST, 0, pc0);
+    if (nchunks > 1) stage_coef(S, coef, plane, cld, OH, OW, pr0 + GFIRST, GCH, buf_row(1), pc0);
+    asm volatile("cp.async.wait_group %0;" ::"n"(1) : "memory");
     __syncthreads();
-    // horizontal: h(r, c) = sum_n w(n) M(r, c + 10 - n), 4 columns per task
-    for (int task = threadIdx.x; task < RH11 * (TW / 4); task += NT) {
-        const int r = task >> 4, g4 = (task & 15) * 4;
-        float2 pab[14];
-        float pc[14];
-        const float4 *sab = reinterpret_cast<const float4 *>(&S.ab[r][g4]);
-#pragma unroll
-        for (int k = 0; k < 7; ++k) {
-            const float4 v = sab[k];
-            pab[2 * k] = make_float2(v.x, v.y);
-            pab[2 * k + 1] = make_float2(v.z, v.w);
-        }
-        const float4 *sc = reinterpret_cast<const float4 *>(&S.c[r][g4]);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float4 v = sc[k];
-            pc[4 * k] = v.x;
-            pc[4 * k + 1] = v.y;
-            pc[4 * k + 2] = v.z;
-            pc[4 * k + 3] = v.w;
-        }
-        {
-            const float2 v = *reinterpret_cast<const float2 *>(&S.c[r][g4 + 12]);
-            pc[12] = v.x;
-            pc[13] = v.y;
-        }
-        float2 hab[4];
-        float hc[4];
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-            hab[o] = make_float2(0.f, 0.f);
-            hc[o] = 0.f;
-        }
-#pragma unroll
-        for (int i = 0; i < 14; ++i)
-#pragma unroll
-            for (int o = 0; o < 4; ++o) {
-                const int n = H11 + o - i;  // tap applied to column i for output o
-                if (n >= 0 && n < K11) {
-                    hab[o] = __ffma2_rn(t2.g2[n], pab[i], hab[o]);
-                    hc[o] = fmaf(t2.g2[n].x, pc[i], hc[o]);
-                }
-            }
-        float4 *dab = reinterpret_cast<float4 *>(&S.hab[r][g4]);
-        dab[0] = make_float4(hab[0].x, hab[0].y, hab[1].x, hab[1].y);
-        dab[1] = make_float4(hab[2].x, hab[2].y, hab[3].x, hab[3].y);
-        *reinterpret_cast<float4 *>(&S.hc[r][g4]) = make_float4(hc[0], hc[1], hc[2], hc[3]);
-    }
-    __syncthreads();
-    // vertical + combine: 4 rows of one column per task
+    grad_horizontal(S, 0, GFIRST, 0, L.taps);
+
     const T *xb = static_cast<const T *>(L.x.data) + img * L.x.image_stride;
     const T *yb = static_cast<const T *>(L.y.data) + img * L.y.image_stride;
     const int64_t Hh = H >> 1, Wh = W >> 1;
     const float *coarse = L.coarse ? L.coarse + (int64_t)img * Hh * Wh : nullptr;
-    const float f = fac;
-    for (int task = threadIdx.x; task < TW * (TH / 4); task += NT) {
-        const int c = task & (TW - 1), r4 = (task >> 6) * 4;
-        float2 gab[4];
-        float gc[4];
+    const int col = threadIdx.x & (TW - 1), grp = threadIdx.x >> 6;
+    const int64_t qc = c0 + col;
+    for (int c = 0; c < nchunks; ++c) {
+        __syncthreads();  // ring rows of chunk c complete
+        {
+            const int base = GCH * c + 4 * grp;
+            const int b0 = base & (GRING - 1);
+            float acc[3][4];
 #pragma unroll
-        for (int o = 0; o < 4; ++o) {
-            gab[o] = make_float2(0.f, 0.f);
-            gc[o] = 0.f;
-        }
+            for (int m = 0; m < 3; ++m)
 #pragma unroll
-        for (int i = 0; i < 14; ++i) {
-            const float2 v = S.hab[r4 + i][c];
-            const float vc = S.hc[r4 + i][c];
+                for (int o = 0; o < 4; ++o) acc[m][o] = 0.f;
 #pragma unroll
-            for (int o = 0; o < 4; ++o) {
-                const int n = H11 + o - i;
-                if (n >= 0 && n < K11) {
-                    gab[o] = __ffma2_rn(t2.g2[n], v, gab[o]);
-                    gc[o] = fmaf(t2.g2[n].x, vc, gc[o]);
+            for (int i = 0; i < 14; ++i) {
+                const float va = S.h[0][b0 + i][col], vb = S.h[1][b0 + i][col], vc = S.h[2][b0 + i][col];
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    const int n = o + H11 - i;
+                    if (n >= 0 && n < K11) {
+                        const float w = L.taps.g[n];
+                        acc[0][o] = fmaf(w, va, acc[0][o]);
+                        acc[1][o] = fmaf(w, vb, acc[1][o]);
+                        acc[2][o] = fmaf(w, vc, acc[2][o]);
+                    }
+                }
+            }
+            const float f = fac;
+            if (qc < W) {
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    const int64_t q = q0 + base + o;
+                    if (q >= qend) break;
+                    const float xv = load_f32<T>(xb + q * L.x.row_stride + qc);
+                    const float yv = load_f32<T>(yb + q * L.y.row_stride + qc);
+                    float gval = f * fmaf(yv - L.sy, acc[1][o], fmaf(xv - L.sx, acc[2][o], acc[0][o]));
+                    if (coarse && (q >> 1) < Hh && (qc >> 1) < Wh)
+                        gval = fmaf(0.25f, coarse[(q >> 1) * Wh + (qc >> 1)], gval);
+                    store_grad<G>(L.out, img * L.out_is + q * L.out_ld + qc, gval);
                 }
             }
         }
-        const int64_t qc = c0 + c;
-        if (qc >= W) continue;
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-            const int64_t q = r0 + r4 + o;
-            if (q >= H) break;
-            const float xv = load_f32<T>(xb + q * L.x.row_stride + qc);
-            const float yv = load_f32<T>(yb + q * L.y.row_stride + qc);
-            float gval = f * fmaf(yv - L.sy, gab[o].y, fmaf(xv - L.sx, gc[o], gab[o].x));
-            if (coarse && (q >> 1) < Hh && (qc >> 1) < Wh) gval = fmaf(0.25f, coarse[(q >> 1) * Wh + (qc >> 1)], gval);
-            store_grad<G>(L.out, img * L.out_is + q * L.out_ld + qc, gval);
+        if (c + 1 < nchunks) {
+            if (c + 2 < nchunks) {
+                stage_coef(S, coef, plane, cld, OH, OW, pr0 + GFIRST + (int64_t)GCH * (c + 1), GCH, buf_row(c + 2),
+                           pc0);
+                asm volatile("cp.async.wait_group %0;" ::"n"(1) : "memory");
+            } else {
+                asm volatile("cp.async.wait_group %0;" ::"n"(0) : "memory");
+            }
+            __syncthreads();  // chunk c+1 staged; ring rows of chunk c consumed
+            grad_horizontal(S, buf_row(c + 1), GCH, GFIRST + GCH * c, L.taps);
         }
     }
 }
@@ -267,10 +289,12 @@ cudaError_t launch_grad11(const GradLaunch &L, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
-    Taps2<K11> t2;
-    for (int n = 0; n < K11; ++n) t2.g2[n] = make_float2(L.taps.g[n], L.taps.g[n]);
-    dim3 grid((unsigned)((L.x.W + TW - 1) / TW), (unsigned)((L.x.H + TH - 1) / TH), L.count);
-    grad11_kernel<T, G><<<grid, NT, sizeof(Grad11Smem), st>>>(L, t2);
+    const int strips = (int)((L.x.W + TW - 1) / TW);
+    int seg_rows = 256;
+    while (seg_rows > 32 && (int64_t)strips * ((L.x.H + seg_rows - 1) / seg_rows) * L.count < 4 * 456) seg_rows -= 32;
+    const int segs = (int)((L.x.H + seg_rows - 1) / seg_rows);
+    dim3 grid(strips, segs, L.count);
+    grad11_kernel<T, G><<<grid, NT, sizeof(Grad11Smem), st>>>(L, strips, segs, seg_rows);
     return cudaGetLastError();
 }
 

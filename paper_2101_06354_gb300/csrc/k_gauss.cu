@@ -363,8 +363,8 @@ __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, 
             if (COEF) {
                 float ca, cb, ccf;
                 ssim_coef(u.x, u.y, A1, B1, A2, B2, co.which, co.sx, co.sy, ca, cb, ccf);
-                const int64_t plane = g.OH * g.OW;
-                float *dst = coef_img + (g.o0 + base + o) * g.OW + g.j0 + col;
+                const int64_t ld = coef_ld(g.OW), plane = g.OH * ld;
+                float *dst = coef_img + (g.o0 + base + o) * ld + g.j0 + col;
                 dst[0] = ca;
                 dst[plane] = cb;
                 dst[2 * plane] = ccf;
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(NT, 3) gauss11_kernel(const GaussLaunch L, int
     const int64_t dsn = (it.H >> 1) * (it.W >> 1);
     it.dsx = L.ds_x ? L.ds_x + img * dsn : nullptr;
     it.dsy = L.ds_y ? L.ds_y + img * dsn : nullptr;
-    it.coef_img = COEF ? L.co.coef + (int64_t)img * 3 * (it.H - HALO) * (it.W - HALO) : nullptr;
+    it.coef_img = COEF ? L.co.coef + (int64_t)img * 3 * (it.H - HALO) * coef_ld(it.W - HALO) : nullptr;
     it.partial = L.partials + ((int64_t)img * segs + seg) * strips + strip;
     gauss11_item<T, COEF>(S, it, L.taps, L.taps2, L.c, L.co);
 }
@@ -748,8 +748,8 @@ __global__ void __launch_bounds__(GT *GT) generic_kernel(const GenericLaunch L, 
         if (L.co.coef) {
             float ca, cb, ccf;
             ssim_coef(ux, uy, A1, B1, A2, B2, L.co.which, L.co.sx, L.co.sy, ca, cb, ccf);
-            const int64_t plane = OH * OW;
-            float *dst = L.co.coef + (int64_t)img * 3 * plane + a * OW + b;
+            const int64_t ld = coef_ld(OW), plane = OH * ld;
+            float *dst = L.co.coef + (int64_t)img * 3 * plane + a * ld + b;
             dst[0] = ca;
             dst[plane] = cb;
             dst[2 * plane] = ccf;
