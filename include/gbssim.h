@@ -187,15 +187,20 @@ int gbssim_msssim(const gbssim_plane *x, const gbssim_plane *y, const gbssim_par
  *   doubles, e.g. the incoming gradient of a loss).  grad_y (device) has
  *   dtype grad_dtype (F32, F16 or BF16), rows grad_ld elements apart, images
  *   grad_image_stride apart; every pixel of every image is written.
+ *   fwd_score, fwd_per_scale (MS-SSIM only, nullable, both or neither):
+ *   device outputs (score_out, per_scale_out) of a gbssim_msssim call on the
+ *   same x, y and parameters.  When given, the backward does not re-run the
+ *   MS-SSIM forward to pool the scales; it only rebuilds the pyramid planes
+ *   (the window moments are still recomputed).  Ignored for SSIM.
  *   score_out: nullable, x.count doubles, the scores themselves.
  *   Requires stride == 1 and k <= GBSSIM_MAX_K_BACKWARD (else
  *   GBSSIM_ERR_UNSUPPORTED); workspace of gbssim_workspace_size with
  *   GBSSIM_OP_BACKWARD (multiscale = 0) or GBSSIM_OP_BACKWARD_MS. */
 int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
                          int32_t multiscale, double grad_scale, const double *grad_out,
-                         int32_t grad_out_per_image, void *grad_y, int32_t grad_dtype, int64_t grad_ld,
-                         int64_t grad_image_stride, double *score_out, void *workspace,
-                         size_t workspace_bytes, void *stream);
+                         int32_t grad_out_per_image, const double *fwd_score, const double *fwd_per_scale,
+                         void *grad_y, int32_t grad_dtype, int64_t grad_ld, int64_t grad_image_stride,
+                         double *score_out, void *workspace, size_t workspace_bytes, void *stream);
 
 /* Colour and temporal pooling of a YUV video (any chroma subsampling).
  * planes = {x_Y, y_Y, x_U, y_U, x_V, y_V}, each a batch of `frames` images

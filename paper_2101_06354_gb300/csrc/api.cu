@@ -527,9 +527,9 @@ int gbssim_msssim(const gbssim_plane *x, const gbssim_plane *y, const gbssim_par
 
 int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
                          int32_t multiscale, double grad_scale, const double *grad_out,
-                         int32_t grad_out_per_image, void *grad_y, int32_t grad_dtype, int64_t grad_ld,
-                         int64_t grad_image_stride, double *score_out, void *workspace,
-                         size_t workspace_bytes, void *stream) {
+                         int32_t grad_out_per_image, const double *fwd_score, const double *fwd_per_scale,
+                         void *grad_y, int32_t grad_dtype, int64_t grad_ld, int64_t grad_image_stride,
+                         double *score_out, void *workspace, size_t workspace_bytes, void *stream) {
     int rc = check_pair(x, y);
     if (rc) return rc;
     rc = check_params(p);
@@ -540,6 +540,7 @@ int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbs
     if (grad_ld < x->width || (x->count > 1 && grad_image_stride < x->height * grad_ld))
         return GBSSIM_ERR_INVALID_ARG;
     if (!isfinite(grad_scale)) return GBSSIM_ERR_INVALID_ARG;
+    if ((fwd_score == nullptr) != (fwd_per_scale == nullptr)) return GBSSIM_ERR_INVALID_ARG;
     BwdPlan B;
     rc = plan_backward(x, p, multiscale != 0, &B);
     if (rc) return rc;
@@ -548,7 +549,25 @@ int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbs
     char *ws = (char *)workspace;
     const int n = x->count, S = multiscale ? p->scales : 1;
     double *score = (double *)(ws + B.score_off), *per = (double *)(ws + B.per_off);
-    if (multiscale) {
+    const double *ms_score = score, *ms_per = per;
+    if (multiscale && fwd_score) {
+        // the caller's forward already pooled every scale: only the pyramid
+        // planes are rebuilt (2x2 average pooling), the moments are recomputed below
+        ms_score = fwd_score;
+        ms_per = fwd_per_scale;
+        ImgDesc dx = desc_of(x), dy = desc_of(y);
+        int dtype = x->dtype;
+        for (int j = 1; j < S; ++j) {
+            const Level &N = B.fwd.lv[j];
+            float *px = (float *)(ws + N.plane_off), *py = px + (size_t)N.H * N.W * n;
+            if (launch_downsample(dx, dtype, n, px, st) != cudaSuccess ||
+                launch_downsample(dy, dtype, n, py, st) != cudaSuccess)
+                return GBSSIM_ERR_CUDA;
+            dx = ImgDesc{px, N.H, N.W, N.W, N.H * N.W};
+            dy = ImgDesc{py, N.H, N.W, N.W, N.H * N.W};
+            dtype = GBSSIM_F32;
+        }
+    } else if (multiscale) {
         rc = msssim_forward(x, y, p, B.fwd, ws, score, per, st);
         if (rc) return rc;
     }
@@ -591,8 +610,8 @@ int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbs
         G.grad_out = grad_out;
         G.grad_out_per_image = grad_out_per_image;
         if (multiscale) {
-            G.ms_score = score;
-            G.ms_per_scale = per;
+            G.ms_score = ms_score;
+            G.ms_per_scale = ms_per;
             G.ms_scales = S;
             G.ms_level = j;
             G.ms_combine = p->combine;
@@ -615,7 +634,7 @@ int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbs
         if (e != cudaSuccess) return GBSSIM_ERR_CUDA;
     }
     if (multiscale && score_out &&
-        cudaMemcpyAsync(score_out, score, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        cudaMemcpyAsync(score_out, ms_score, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return GBSSIM_ERR_CUDA;
     return GBSSIM_OK;
 }

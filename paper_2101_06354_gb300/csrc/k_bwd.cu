@@ -214,8 +214,12 @@ __global__ void __launch_bounds__(NT, 3) grad11_kernel(const GradLaunch L, int s
     // chunk c's staged rows: c == 0 rows 0..25; c >= 1 rows 0..15 (c even) or 26..41 (c odd)
     auto buf_row = [](int c) { return (c & 1) ? GFIRST : 0; };
     stage_coef(S, coef, plane, cld, OH, OW, pr0, GFIRST, 0, pc0);
-    if (nchunks > 1) stage_coef(S, coef, plane, cld, OH, OW, pr0 + GFIRST, GCH, buf_row(1), pc0);
-    asm volatile("cp.async.wait_group %0;" ::"n"(1) : "memory");
+    if (nchunks > 1) {
+        stage_coef(S, coef, plane, cld, OH, OW, pr0 + GFIRST, GCH, buf_row(1), pc0);
+        asm volatile("cp.async.wait_group %0;" ::"n"(1) : "memory");  // chunk 0 landed, chunk 1 may fly
+    } else {
+        asm volatile("cp.async.wait_group %0;" ::"n"(0) : "memory");  // the only group must land
+    }
     __syncthreads();
     grad_horizontal(S, 0, GFIRST, 0, L.taps);
 

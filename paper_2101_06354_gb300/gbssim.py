@@ -91,8 +91,8 @@ _SIGS = {
     "gbssim_batch_run": ([_vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
     "gbssim_batch_status": ([_vp, _vp, _vp, _vp], ctypes.c_int),
     "gbssim_batch_free": ([_vp], None),
-    "gbssim_ssim_backward": ([_P(Plane), _P(Plane), _P(Params), _i32, ctypes.c_double, _vp, _i32, _vp, _i32, _i64,
-                              _i64, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "gbssim_ssim_backward": ([_P(Plane), _P(Plane), _P(Params), _i32, ctypes.c_double, _vp, _i32, _vp, _vp, _vp,
+                              _i32, _i64, _i64, _vp, _vp, _sz, _vp], ctypes.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -292,7 +292,8 @@ _GDT = {torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}
 
 def ssim_backward(x: torch.Tensor, y: torch.Tensor, multiscale: bool = False, grad_scale: float = 1.0,
                   grad_out: torch.Tensor = None, grad_dtype=None, return_score: bool = False,
-                  ws: torch.Tensor = None, **kw):
+                  ws: torch.Tensor = None, fwd_score: torch.Tensor = None, fwd_per_scale: torch.Tensor = None,
+                  **kw):
     """d score / d y for each pair (gbssim_ssim_backward), shaped like y.
 
     score is MSSIM (multiscale=False) or MS-SSIM.  The result is multiplied by
@@ -315,9 +316,15 @@ def ssim_backward(x: torch.Tensor, y: torch.Tensor, multiscale: bool = False, gr
         go = grad_out.detach().to(device=dev, dtype=torch.float64).contiguous().reshape(-1)
         if go.numel() not in (1, n):
             raise ValueError("grad_out must have 1 or N elements")
+    if (fwd_score is None) != (fwd_per_scale is None):
+        raise ValueError("fwd_score and fwd_per_scale go together")
+    fs = fwd_score.contiguous() if fwd_score is not None else None
+    fp = fwd_per_scale.contiguous() if fwd_per_scale is not None else None
     _check(lib.gbssim_ssim_backward(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p), int(bool(multiscale)),
                                     float(grad_scale), go.data_ptr() if go is not None else None,
-                                    int(go is not None and go.numel() == n and n > 1), grad.data_ptr(),
+                                    int(go is not None and go.numel() == n and n > 1),
+                                    fs.data_ptr() if fs is not None else None,
+                                    fp.data_ptr() if fp is not None else None, grad.data_ptr(),
                                     _GDT[gdt], grad.stride(1), grad.stride(0),
                                     score.data_ptr() if score is not None else None,
                                     ws.data_ptr(), ws.numel(), _stream(dev)), "gbssim_ssim_backward")
@@ -335,8 +342,12 @@ class _SSIMLossFn(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, x, y, multiscale, kw):
-        score = msssim(x, y, **kw) if multiscale else ssim(x, y, **kw)
-        ctx.save_for_backward(x, y)
+        if multiscale:
+            score, per = msssim(x, y, per_scale=True, **kw)
+            ctx.save_for_backward(x, y, score, per)   # pooled scalars only
+        else:
+            score = ssim(x, y, **kw)
+            ctx.save_for_backward(x, y)
         ctx.multiscale = multiscale
         ctx.kw = kw
         ctx.n = score.numel()
@@ -344,11 +355,13 @@ class _SSIMLossFn(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, grad_loss):
-        x, y = ctx.saved_tensors
+        saved = ctx.saved_tensors
+        x, y = saved[0], saved[1]
         if not ctx.needs_input_grad[1]:
             return None, None, None, None
+        extra = dict(fwd_score=saved[2], fwd_per_scale=saved[3]) if ctx.multiscale else {}
         g = ssim_backward(x, y, multiscale=ctx.multiscale, grad_scale=-1.0 / ctx.n, grad_out=grad_loss,
-                          grad_dtype=y.dtype, **ctx.kw)
+                          grad_dtype=y.dtype, **extra, **ctx.kw)
         return None, g, None, None
 
 

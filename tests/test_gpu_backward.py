@@ -44,7 +44,7 @@ def _np64(t):
     return t.detach().double().cpu().numpy()
 
 
-@pytest.mark.parametrize("h,w", [(64, 70), (140, 131), (11, 11), (12, 40), (200, 97)])
+@pytest.mark.parametrize("h,w", [(64, 70), (140, 131), (11, 11), (12, 40), (200, 97), (27, 300), (16, 16)])
 @pytest.mark.parametrize("dtype,L", [(torch.float32, 1.0), (torch.uint8, 255.0)])
 def test_ssim_gradient_matches_oracle(g, synth, h, w, dtype, L):
     if dtype == torch.uint8:
@@ -83,6 +83,18 @@ def test_msssim_gradient_matches_oracle(g, synth, h, w, combine):
         ref_score, ref = oracle.msssim_grad(_np64(xs[i]), _np64(ys[i]), L=1.0, combine=combine)
         assert _rel_err(grad[i].double().cpu().numpy(), ref) <= 1e-4
         assert abs(score[i].item() - ref_score) <= 1e-6
+
+
+def test_msssim_backward_with_forward_results(g, synth):
+    """Passing the forward's pooled scales skips the re-run of the forward: the
+    gradient must be identical to the self-contained call."""
+    x, y = synth.loss_pairs_float(1, 3, 190, 200)
+    xs, ys = x.reshape(3, 190, 200).to(DEV), y.reshape(3, 190, 200).to(DEV)
+    score, per = g.msssim(xs, ys, per_scale=True, L=1.0)
+    a = g.ssim_backward(xs, ys, multiscale=True, L=1.0)
+    b, sb = g.ssim_backward(xs, ys, multiscale=True, L=1.0, fwd_score=score, fwd_per_scale=per, return_score=True)
+    assert torch.equal(sb, score)
+    assert torch.allclose(a, b, rtol=0, atol=1e-6 * a.abs().max().item())
 
 
 def test_msssim_gradient_three_scales_u8(g, synth):
