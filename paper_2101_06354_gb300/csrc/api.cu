@@ -70,7 +70,7 @@ void make_taps(const gbssim_params *p, float *g) {
 
 SsimConst make_const(const gbssim_params *p) {
     const double c1 = (p->K1 * p->L) * (p->K1 * p->L), c2 = (p->K2 * p->L) * (p->K2 * p->L);
-    return SsimConst{(float)c1, (float)c2};
+    return ssim_const(c1, c2);
 }
 
 ImgDesc desc_of(const gbssim_plane *p) {

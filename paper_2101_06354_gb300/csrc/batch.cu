@@ -237,7 +237,7 @@ int gbssim_batch_run(const gbssim_batch *plan, double *scores_out, double *per_s
         for (int t = 0; t < 11; ++t) taps.g[t] = (float)(v[t] / z);
     }
     const double c1 = (p->K1 * p->L) * (p->K1 * p->L), c2 = (p->K2 * p->L) * (p->K2 * p->L);
-    SsimConst cc{(float)c1, (float)c2};
+    const SsimConst cc = ssim_const(c1, c2);
     if (launch_batch(T, taps, cc, plan->grid, st) != cudaSuccess) return GBSSIM_ERR_CUDA;
     BatchFinalize F;
     memset(&F, 0, sizeof F);

@@ -65,7 +65,12 @@ struct Taps2 {
 // SSIM constants of one launch.
 struct SsimConst {
     float C1, C2;
+    float C1x2, C2x2;  // 2 C1, 2 C2 (the (u, w) form of the formula)
 };
+// The only constructor: C1 = (K1 L)^2 and C2 = (K2 L)^2 given in double.
+inline SsimConst ssim_const(double c1, double c2) {
+    return SsimConst{(float)c1, (float)c2, 2.f * (float)c1, 2.f * (float)c2};
+}
 
 // ---------------------------------------------------------------- backward coefficients
 //

@@ -8,6 +8,16 @@
 // mu_y^2 + C1) (Eq. lum_term), cs = (2 sigma_xy + C2)/(sigma_x^2 + sigma_y^2
 // + C2) (the C3 = C2/2 form) and Q = l cs, mean-pooled per image.
 //
+// Four moments instead of five.  The formula needs sigma_x^2 + sigma_y^2 and
+// sigma_xy only through A2 = 2 sigma_xy + C2 and B2 = sigma_x^2 + sigma_y^2
+// + C2, and mu_x, mu_y only through A1 and B1.  With u = x + y and w = x - y,
+// Var u = s_x^2 + s_y^2 + 2 s_xy and Var w = s_x^2 + s_y^2 - 2 s_xy, so
+//   cs = (Var u - Var w + 2 C2) / (Var u + Var w + 2 C2),
+//   l  = (mu_u^2 - mu_w^2 + 2 C1) / (mu_u^2 + mu_w^2 + 2 C1),
+// an exact regrouping of Eq. lum_term and the cs term.  The kernel therefore
+// filters the pair (u, w) and its squares: two packed f32x2 moments per
+// window, with no scalar cross product.
+//
 // Precision.  sigma^2 = sum w x^2 - mu^2 cancels catastrophically in fp32 on
 // flat windows far from zero (x ~ 255: sum w x^2 ~ 65025 with an ulp of
 // 0.004, while |dQ/d sigma^2| <= 1/C2 = 0.017), which alone breaks a 1e-5
@@ -15,13 +25,13 @@
 // the two directions through the law of total variance:
 //   horizontal: for a group of 4 adjacent outputs of one row, subtract one
 //     pixel c of that row lying inside all 4 windows (offset <= 2 taps from
-//     each centre), and accumulate sum g d, sum g d^2, sum g dx dy with
-//     d = x - c; the row-window mean is c + sum g d and its variance
+//     each centre), and accumulate sum g d and sum g d^2 with d = p - c
+//     (p = u or w); the row-window mean is c + sum g d and its variance
 //     sum g d^2 - (sum g d)^2;
 //   vertical: for a group of 4 adjacent outputs of one column, subtract the
 //     row-window mean b of one row inside all 4 windows and accumulate
-//     sum g e, sum g (e^2 + v_row), sum g (ex ey + c_row) with e = mu_row - b;
-//     the window variance is sum g (e^2 + v_row) - (sum g e)^2.
+//     sum g e and sum g (e^2 + v_row) with e = mu_row - b; the window
+//     variance is sum g (e^2 + v_row) - (sum g e)^2.
 // Because the shift lies inside every window of its group, the shifted second
 // moment is at most (1 + 1/g_min) times the variance it yields (g_min = the
 // tap 2 away from the centre, 0.109 for sigma = 1.5), so rounding error stays
@@ -51,20 +61,19 @@ constexpr int IW = TW + HALO;     // input columns per strip (74)
 constexpr int QUADS = (IW + 3) / 4;                 // 4-column staging units per row (19)
 constexpr int IWP = 4 * QUADS;                      // staged row pitch in (x, y) pairs (76)
 constexpr int NT = 256;
-constexpr int PFQ = (CH * QUADS + NT - 1) / NT;     // prefetched units per thread (2)
 // The vertical pass of a thread reads ring rows base..base+13 with base a
 // multiple of 4 below RING; rows 0..DUP-1 are also stored at RING..RING+DUP-1
 // so those reads never wrap.
 constexpr int DUP = 10;
 constexpr int RROWS = RING + DUP;
 
-// x and y travel together as float2 pairs so that every moment of the pair
-// is one packed f32x2 instruction (FFMA2 / FADD2 / FMUL2 on sm_100+).
+// u = x + y and w = x - y travel together as float2 pairs so that every
+// moment of the pair is one packed f32x2 instruction (FFMA2 / FADD2 / FMUL2
+// on sm_100+).
 struct __align__(16) Smem {
-    float2 in[FIRST][IWP];   // staged input rows, (x, y) per column
-    float2 mu[RROWS][TW];    // row-window means (mu_x, mu_y)
-    float2 v[RROWS][TW];     // row-window variances (v_x, v_y)
-    float c[RROWS][TW];      // row-window covariances
+    float2 in[FIRST][IWP];   // staged input rows, (u, w) per column
+    float2 mu[RROWS][TW];    // row-window means (mu_u, mu_w)
+    float2 v[RROWS][TW];     // row-window variances (v_u, v_w)
     float red[2 * NT / 32];
 };
 
@@ -145,100 +154,140 @@ __device__ __forceinline__ float4 convert_raw(uint4 r, bool packed) {
                        elem_f32<T>(r.y >> 16));
 }
 
-// Store one staged unit: columns 4q..4q+3 of x and y, interleaved.
-__device__ __forceinline__ void put_unit(Smem &S, int r, int q, float4 a, float4 b) {
-    float4 *d = reinterpret_cast<float4 *>(&S.in[r][4 * q]);
-    d[0] = make_float4(a.x, b.x, a.y, b.y);
-    d[1] = make_float4(a.z, b.z, a.w, b.w);
+// (u, w) = (x + y, x - y).  For uint8 data both come straight from the
+// magic floats 2^23 + x and 2^23 + y: (xm - 2^24) + ym = x + y and
+// xm - ym = x - y, every step exact.
+__device__ __forceinline__ float2 uw_of(float x, float y) { return make_float2(x + y, x - y); }
+__device__ __forceinline__ float2 uw_of_magic(float xm, float ym) {
+    return make_float2((xm - 16777216.0f) + ym, xm - ym);
 }
 
-// Stage `nr` input rows starting at absolute row r0 into in rows 0..nr-1
-// (used once per segment, for the first FIRST rows).
-template <typename T, int LD = 0>
-__device__ __forceinline__ void stage_direct(Smem &S, const Geo &g, int64_t r0, int nr) {
-    for (int t = threadIdx.x; t < nr * QUADS; t += NT) {
-        const int r = t / QUADS, q = t - r * QUADS;
-        const int64_t row = r0 + r, c = g.j0 + 4 * q;
-        const int ncols = (int)max((int64_t)0, min((int64_t)4, g.W - c));
-        const bool packed = g.vec && ncols == 4;
-        uint4 rx = make_uint4(0u, 0u, 0u, 0u), ry = rx;
-        if (row < g.H && ncols > 0) {
-            rx = load_raw<T, LD>(static_cast<const T *>(g.xb) + row * g.rs + c, ncols, packed);
-            ry = load_raw<T, LD>(static_cast<const T *>(g.yb) + row * g.rs + c, ncols, packed);
+// byte k of w as the float 2^23 + byte (exact)
+__device__ __forceinline__ float u8m(unsigned w, int k) {
+    return __int_as_float(__byte_perm(w, 0x4B000000u, 0x7540u + k));
+}
+
+// Convert a raw unit of x and y (four columns each) into four (u, w) pairs.
+template <typename T>
+__device__ __forceinline__ void convert_uw(uint4 rx, uint4 ry, bool packed, float2 (&o)[4]) {
+    if (sizeof(T) == 1) {
+        if (packed) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) o[k] = uw_of_magic(u8m(rx.x, k), u8m(ry.x, k));
+        } else {
+            o[0] = uw_of_magic(u8m(rx.x, 0), u8m(ry.x, 0));
+            o[1] = uw_of_magic(u8m(rx.y, 0), u8m(ry.y, 0));
+            o[2] = uw_of_magic(u8m(rx.z, 0), u8m(ry.z, 0));
+            o[3] = uw_of_magic(u8m(rx.w, 0), u8m(ry.w, 0));
         }
-        put_unit(S, r, q, convert_raw<T>(rx, packed), convert_raw<T>(ry, packed));
+        return;
     }
+    const float4 a = convert_raw<T>(rx, packed), b = convert_raw<T>(ry, packed);
+    o[0] = uw_of(a.x, b.x);
+    o[1] = uw_of(a.y, b.y);
+    o[2] = uw_of(a.z, b.z);
+    o[3] = uw_of(a.w, b.w);
 }
 
-// Per-thread staging units of a 16-row chunk, fixed for the whole CTA.
-struct Units {
-    int64_t off[PFQ];  // element offset of the unit in chunk row 0 (from the image start)
-    int r[PFQ];        // row within the chunk (-1: no unit)
-    int q[PFQ];        // quad
-    int ncols[PFQ];    // columns inside the image (0..4)
-    bool packed[PFQ];
+// Store one staged unit: columns 4q..4q+3 as (u, w) pairs.
+template <typename T>
+__device__ __forceinline__ void put_unit(Smem &S, int r, int q, uint4 rx, uint4 ry, bool packed) {
+    float2 o[4];
+    convert_uw<T>(rx, ry, packed, o);
+    float4 *d = reinterpret_cast<float4 *>(&S.in[r][4 * q]);
+    d[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+    d[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+}
+
+// Staging unit: one quad (4 columns) of two adjacent input rows.  Holding
+// both rows lets the thread form the 2x2 averages of the next pyramid level
+// straight from the raw x and y values before they become (u, w) pairs.
+struct Unit {
+    int64_t off;  // element offset of the quad in row 2p of the staged block (from the image start)
+    int p, q;     // row pair (-1: no unit), quad
+    int ncols;    // columns inside the image (0..4)
+    bool packed;
 };
 
-__device__ __forceinline__ void make_units(Units &U, const Geo &g) {
-#pragma unroll
-    for (int i = 0; i < PFQ; ++i) {
-        const int t = threadIdx.x + i * NT;
-        U.r[i] = -1;
-        U.q[i] = 0;
-        U.ncols[i] = 0;
-        U.packed[i] = false;
-        U.off[i] = 0;
-        if (t < CH * QUADS) {
-            const int r = t / QUADS, q = t - r * QUADS;
-            const int64_t c = g.j0 + 4 * q;
-            U.r[i] = r;
-            U.q[i] = q;
-            U.ncols[i] = (int)max((int64_t)0, min((int64_t)4, g.W - c));
-            U.packed[i] = g.vec && U.ncols[i] == 4;
-            U.off[i] = r * g.rs + c;
-        }
+__device__ __forceinline__ void make_unit(Unit &U, const Geo &g, int t, int npairs) {
+    U.p = -1;
+    U.q = 0;
+    U.ncols = 0;
+    U.packed = false;
+    U.off = 0;
+    if (t < npairs * QUADS) {
+        const int p = t / QUADS, q = t - p * QUADS;
+        const int64_t c = g.j0 + 4 * q;
+        U.p = p;
+        U.q = q;
+        U.ncols = (int)max((int64_t)0, min((int64_t)4, g.W - c));
+        U.packed = g.vec && U.ncols == 4;
+        U.off = 2 * p * g.rs + c;
     }
 }
 
+struct Raw {
+    uint4 x0, y0, x1, y1;  // rows 2p and 2p + 1
+};
+
+// Raw loads of a unit of the block whose first row is r0 (rows at or past H read as 0).
 template <typename T, int LD = 0>
-__device__ __forceinline__ void prefetch(uint4 (&px)[PFQ], uint4 (&py)[PFQ], const Units &U, const Geo &g,
-                                         int64_t r0) {
-    const int64_t base = r0 * g.rs;
-#pragma unroll
-    for (int i = 0; i < PFQ; ++i) {
-        px[i] = py[i] = make_uint4(0u, 0u, 0u, 0u);
-        if (U.r[i] >= 0 && r0 + U.r[i] < g.H && U.ncols[i] > 0) {
-            px[i] = load_raw<T, LD>(static_cast<const T *>(g.xb) + base + U.off[i], U.ncols[i], U.packed[i]);
-            py[i] = load_raw<T, LD>(static_cast<const T *>(g.yb) + base + U.off[i], U.ncols[i], U.packed[i]);
-        }
+__device__ __forceinline__ void load_unit(Raw &R, const Unit &U, const Geo &g, int64_t r0) {
+    R.x0 = R.y0 = R.x1 = R.y1 = make_uint4(0u, 0u, 0u, 0u);
+    if (U.p < 0 || U.ncols <= 0) return;
+    const int64_t row = r0 + 2 * U.p, o = r0 * g.rs + U.off;
+    const T *xp = static_cast<const T *>(g.xb) + o;
+    const T *yp = static_cast<const T *>(g.yb) + o;
+    if (row < g.H) {
+        R.x0 = load_raw<T, LD>(xp, U.ncols, U.packed);
+        R.y0 = load_raw<T, LD>(yp, U.ncols, U.packed);
+    }
+    if (row + 1 < g.H) {
+        R.x1 = load_raw<T, LD>(xp + g.rs, U.ncols, U.packed);
+        R.y1 = load_raw<T, LD>(yp + g.rs, U.ncols, U.packed);
     }
 }
 
+// 2x2 averages of the owned blocks of a unit (absolute rows r0 + 2p, +1).
 template <typename T>
-__device__ __forceinline__ void store_prefetch(Smem &S, const uint4 (&px)[PFQ], const uint4 (&py)[PFQ],
-                                               const Units &U) {
-#pragma unroll
-    for (int i = 0; i < PFQ; ++i)
-        if (U.r[i] >= 0)
-            put_unit(S, U.r[i], U.q[i], convert_raw<T>(px[i], U.packed[i]), convert_raw<T>(py[i], U.packed[i]));
+__device__ __forceinline__ void downsample_unit(const Raw &R, const Unit &U, const Geo &g, int64_t r0, float *dsx,
+                                                float *dsy) {
+    const int64_t r = r0 + 2 * U.p;  // even: segment and chunk starts are even
+    const int64_t Hh = g.H >> 1, Wh = g.W >> 1, Rr = r >> 1;
+    if (r >= g.own_r1 || Rr >= Hh) return;
+    const float4 x0 = convert_raw<T>(R.x0, U.packed), x1 = convert_raw<T>(R.x1, U.packed);
+    const float4 y0 = convert_raw<T>(R.y0, U.packed), y1 = convert_raw<T>(R.y1, U.packed);
+    const int64_t c = g.j0 + 4 * U.q;
+    if (c < g.own_c1 && (c >> 1) < Wh) {
+        dsx[Rr * Wh + (c >> 1)] = 0.25f * ((x0.x + x0.y) + (x1.x + x1.y));
+        dsy[Rr * Wh + (c >> 1)] = 0.25f * ((y0.x + y0.y) + (y1.x + y1.y));
+    }
+    if (c + 2 < g.own_c1 && ((c + 2) >> 1) < Wh) {
+        dsx[Rr * Wh + (c >> 1) + 1] = 0.25f * ((x0.z + x0.w) + (x1.z + x1.w));
+        dsy[Rr * Wh + (c >> 1) + 1] = 0.25f * ((y0.z + y0.w) + (y1.z + y1.w));
+    }
 }
 
-// 2x2 average of the owned part of the staged rows (absolute rows r0..r0+nr-1).
-__device__ __forceinline__ void downsample_rows(const Smem &S, const Geo &g, int64_t r0, int nr,
-                                                float *dsx, float *dsy) {
-    const int64_t Hh = g.H >> 1, Wh = g.W >> 1;
-    constexpr int QC = IW / 2;  // 37 column pairs staged
-    for (int t = threadIdx.x; t < (nr >> 1) * QC; t += NT) {
-        const int p = t / QC, q = t - p * QC;
-        const int64_t r = r0 + 2 * p, c = g.j0 + 2 * q;
-        if (r >= g.own_r1 || c >= g.own_c1) continue;
-        const int64_t R = r >> 1, C = c >> 1;
-        if (R >= Hh || C >= Wh) continue;
-        const float4 top = *reinterpret_cast<const float4 *>(&S.in[2 * p][2 * q]);
-        const float4 bot = *reinterpret_cast<const float4 *>(&S.in[2 * p + 1][2 * q]);
-        // top = (x00, y00, x01, y01), bot = (x10, y10, x11, y11)
-        dsx[R * Wh + C] = 0.25f * ((top.x + top.z) + (bot.x + bot.z));
-        dsy[R * Wh + C] = 0.25f * ((top.y + top.w) + (bot.y + bot.w));
+// Store a unit into staged rows row0 + 2p, row0 + 2p + 1 (and its pyramid blocks).
+template <typename T>
+__device__ __forceinline__ void store_unit(Smem &S, const Raw &R, const Unit &U, const Geo &g, int64_t r0, int row0,
+                                           float *dsx, float *dsy) {
+    if (U.p < 0) return;
+    if (dsx) downsample_unit<T>(R, U, g, r0, dsx, dsy);
+    put_unit<T>(S, row0 + 2 * U.p, U.q, R.x0, R.y0, U.packed);
+    put_unit<T>(S, row0 + 2 * U.p + 1, U.q, R.x1, R.y1, U.packed);
+}
+
+// Stage `nr` (even) input rows starting at absolute row r0 into in rows
+// 0..nr-1 (once per segment, for the first FIRST rows).
+template <typename T, int LD = 0>
+__device__ __forceinline__ void stage_direct(Smem &S, const Geo &g, int64_t r0, int nr, float *dsx, float *dsy) {
+    for (int t = threadIdx.x; t < (nr >> 1) * QUADS; t += NT) {
+        Unit U;
+        make_unit(U, g, t, nr >> 1);
+        Raw R;
+        load_unit<T, LD>(R, U, g, r0);
+        store_unit<T>(S, R, U, g, r0, 0, dsx, dsy);
     }
 }
 
@@ -258,42 +307,33 @@ __device__ __forceinline__ void horizontal(Smem &S, int nr, int rel0, const Taps
         // shift: pixel 7 lies in the windows of outputs 0..3 (centres 5..8)
         const float2 nc = make_float2(-p[7].x, -p[7].y);
         float2 m[4], sq[4];
-        float sxy[4];
 #pragma unroll
-        for (int o = 0; o < 4; ++o) {
-            m[o] = sq[o] = make_float2(0.f, 0.f);
-            sxy[o] = 0.f;
-        }
+        for (int o = 0; o < 4; ++o) m[o] = sq[o] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < 14; ++i) {
-            const float2 d = add2(p[i], nc);  // (dx, dy)
-            const float2 dd = mul2(d, d);     // (dx^2, dy^2)
-            const float pxy = d.x * d.y;
+            const float2 d = add2(p[i], nc);  // (du, dw)
+            const float2 dd = mul2(d, d);     // (du^2, dw^2)
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
                 const int n = i - o;
                 if (n >= 0 && n < K) {
                     m[o] = fma2(t2.g2[n], d, m[o]);
                     sq[o] = fma2(t2.g2[n], dd, sq[o]);
-                    sxy[o] = fmaf(t.g[n], pxy, sxy[o]);
                 }
             }
         }
         const int slot = (rel0 + r) & (RING - 1);
         const float2 cc = make_float2(-nc.x, -nc.y);
         float2 om[4], ov[4];
-        float oc[4];
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
             om[o] = add2(m[o], cc);
             ov[o] = fma2(make_float2(-m[o].x, -m[o].y), m[o], sq[o]);
-            oc[o] = fmaf(-m[o].x, m[o].y, sxy[o]);
         }
         const float4 m01 = make_float4(om[0].x, om[0].y, om[1].x, om[1].y);
         const float4 m23 = make_float4(om[2].x, om[2].y, om[3].x, om[3].y);
         const float4 v01 = make_float4(ov[0].x, ov[0].y, ov[1].x, ov[1].y);
         const float4 v23 = make_float4(ov[2].x, ov[2].y, ov[3].x, ov[3].y);
-        const float4 c4 = make_float4(oc[0], oc[1], oc[2], oc[3]);
 #pragma unroll
         for (int rep = 0; rep < 2; ++rep) {
             const int sl = rep ? slot + RING : slot;
@@ -304,7 +344,6 @@ __device__ __forceinline__ void horizontal(Smem &S, int nr, int rel0, const Taps
             dm[1] = m23;
             dv[0] = v01;
             dv[1] = v23;
-            *reinterpret_cast<float4 *>(&S.c[sl][g4]) = c4;
         }
     }
 }
@@ -321,25 +360,19 @@ __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, 
     const float2 b = S.mu[b0 + 7][col];
     const float2 nb = make_float2(-b.x, -b.y);
     float2 m[4], sq[4];
-    float sxy[4];
 #pragma unroll
-    for (int o = 0; o < 4; ++o) {
-        m[o] = sq[o] = make_float2(0.f, 0.f);
-        sxy[o] = 0.f;
-    }
+    for (int o = 0; o < 4; ++o) m[o] = sq[o] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int i = 0; i < 14; ++i) {
         const int s = b0 + i;
-        const float2 e = add2(S.mu[s][col], nb);   // (ex, ey)
-        const float2 q = fma2(e, e, S.v[s][col]);  // (ex^2 + v_x, ey^2 + v_y)
-        const float qxy = fmaf(e.x, e.y, S.c[s][col]);
+        const float2 e = add2(S.mu[s][col], nb);   // (eu, ew)
+        const float2 q = fma2(e, e, S.v[s][col]);  // (eu^2 + v_u, ew^2 + v_w)
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
             const int n = i - o;
             if (n >= 0 && n < K) {
                 m[o] = fma2(t2.g2[n], e, m[o]);
                 sq[o] = fma2(t2.g2[n], q, sq[o]);
-                sxy[o] = fmaf(t.g[n], qxy, sxy[o]);
             }
         }
     }
@@ -349,11 +382,12 @@ __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, 
     sumCS = 0.f;
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
-        const float2 u = add2(m[o], b);                                        // (mu_x, mu_y)
-        const float2 var = fma2(make_float2(-m[o].x, -m[o].y), m[o], sq[o]);  // (s_x^2, s_y^2)
-        const float cv = fmaf(-m[o].x, m[o].y, sxy[o]);
-        const float A1 = fmaf(2.f * u.x, u.y, cc.C1), B1 = fmaf(u.x, u.x, fmaf(u.y, u.y, cc.C1));
-        const float A2 = fmaf(2.f, cv, cc.C2), B2 = (var.x + var.y) + cc.C2;
+        const float2 u = add2(m[o], b);                                        // (mu_u, mu_w)
+        const float2 var = fma2(make_float2(-m[o].x, -m[o].y), m[o], sq[o]);  // (Var u, Var w)
+        // 2 A1, 2 B1, 2 A2, 2 B2 of the (x, y) form
+        const float A1 = fmaf(u.x, u.x, fmaf(-u.y, u.y, cc.C1x2)), B1 = fmaf(u.x, u.x, fmaf(u.y, u.y, cc.C1x2));
+        const float t2c = var.x + cc.C2x2;
+        const float A2 = t2c - var.y, B2 = t2c + var.y;
         const float l = __fdividef(A1, B1), cs = __fdividef(A2, B2);
         const float qv = l * cs;
         if (o < rows_left) {
@@ -362,7 +396,8 @@ __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, 
             if (mrow) mrow[o * map_ld] = qv;
             if (COEF) {
                 float ca, cb, ccf;
-                ssim_coef(u.x, u.y, A1, B1, A2, B2, co.which, co.sx, co.sy, ca, cb, ccf);
+                ssim_coef(0.5f * (u.x + u.y), 0.5f * (u.x - u.y), 0.5f * A1, 0.5f * B1, 0.5f * A2, 0.5f * B2,
+                          co.which, co.sx, co.sy, ca, cb, ccf);
                 const int64_t ld = coef_ld(g.OW), plane = g.OH * ld;
                 float *dst = coef_img + (g.o0 + base + o) * ld + g.j0 + col;
                 dst[0] = ca;
@@ -442,30 +477,26 @@ __device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps
     const int nchunks = (int)((g.oend - g.o0 + CH - 1) / CH);
 
     KSum accQ, accCS;
-    uint4 px[PFQ], py[PFQ];
-    Units U;
-    make_units(U, g);
+    Raw raw;
+    Unit U;
+    make_unit(U, g, threadIdx.x, CH / 2);
     const bool col_ok = g.j0 + (threadIdx.x & (TW - 1)) < g.OW;
 
-    stage_direct<T, LD>(S, g, g.o0, FIRST);
+    stage_direct<T, LD>(S, g, g.o0, FIRST, it.dsx, it.dsy);
     __syncthreads();
-    if (it.dsx) downsample_rows(S, g, g.o0, FIRST, it.dsx, it.dsy);
     horizontal(S, FIRST, 0, taps, taps2);
     for (int c = 0; c < nchunks; ++c) {
         const bool more = c + 1 < nchunks;
         const int64_t next_r0 = g.o0 + FIRST + (int64_t)CH * c;
-        if (more) prefetch<T, LD>(px, py, U, g, next_r0);
+        if (more) load_unit<T, LD>(raw, U, g, next_r0);
         __syncthreads();  // ring rows of chunk c complete; staging free
         float cq, ccs;
         vertical<COEF>(S, g, CH * c, taps, taps2, cc, it.map, it.map_ld, col_ok, co, it.coef_img, cq, ccs);
         accQ.add(cq);
         accCS.add(ccs);
-        if (more) store_prefetch<T>(S, px, py, U);
+        if (more) store_unit<T>(S, raw, U, g, next_r0, 0, it.dsx, it.dsy);
         __syncthreads();  // staging complete; ring rows of chunk c consumed
-        if (more) {
-            if (it.dsx) downsample_rows(S, g, next_r0, CH, it.dsx, it.dsy);
-            horizontal(S, CH, FIRST + CH * c, taps, taps2);
-        }
+        if (more) horizontal(S, CH, FIRST + CH * c, taps, taps2);
     }
     double a, b;
     block_sum2f(accQ.s - accQ.c, accCS.s - accCS.c, S.red, a, b);
