@@ -77,6 +77,15 @@ struct __align__(16) Smem {
     float red[2 * NT / 32];
 };
 
+// Shared-memory swizzle.  The horizontal pass reads and writes 16-byte slots
+// at a 32-byte lane stride (four outputs per thread), a 2-way bank conflict
+// on every access; flipping bit 0 of the slot index when bit 3 is set spreads
+// each quarter-warp over all eight 16-byte bank groups.  The vertical pass
+// reads 8-byte elements at consecutive lanes; the same permutation stays
+// within each aligned group of eight slots, so those reads stay conflict-free.
+__device__ __forceinline__ int swz(int slot) { return slot ^ ((slot >> 3) & 1); }     // 16-byte slots
+__device__ __forceinline__ int swz2(int col) { return col ^ ((col >> 3) & 2); }        // 8-byte elements
+
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -194,9 +203,9 @@ template <typename T>
 __device__ __forceinline__ void put_unit(Smem &S, int r, int q, uint4 rx, uint4 ry, bool packed) {
     float2 o[4];
     convert_uw<T>(rx, ry, packed, o);
-    float4 *d = reinterpret_cast<float4 *>(&S.in[r][4 * q]);
-    d[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
-    d[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+    float4 *d = reinterpret_cast<float4 *>(&S.in[r][0]);
+    d[swz(2 * q)] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+    d[swz(2 * q + 1)] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
 }
 
 // Staging unit: one quad (4 columns) of two adjacent input rows.  Holding
@@ -297,10 +306,10 @@ __device__ __forceinline__ void horizontal(Smem &S, int nr, int rel0, const Taps
     for (int task = threadIdx.x; task < nr * (TW / 4); task += NT) {
         const int r = task >> 4, g4 = (task & 15) * 4;
         float2 p[14];
-        const float4 *src = reinterpret_cast<const float4 *>(&S.in[r][g4]);
+        const float4 *src = reinterpret_cast<const float4 *>(&S.in[r][0]);
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
-            const float4 v = src[k];
+            const float4 v = src[swz((g4 >> 1) + k)];
             p[2 * k] = make_float2(v.x, v.y);
             p[2 * k + 1] = make_float2(v.z, v.w);
         }
@@ -338,12 +347,12 @@ __device__ __forceinline__ void horizontal(Smem &S, int nr, int rel0, const Taps
         for (int rep = 0; rep < 2; ++rep) {
             const int sl = rep ? slot + RING : slot;
             if (rep && slot >= DUP) break;
-            float4 *dm = reinterpret_cast<float4 *>(&S.mu[sl][g4]);
-            float4 *dv = reinterpret_cast<float4 *>(&S.v[sl][g4]);
-            dm[0] = m01;
-            dm[1] = m23;
-            dv[0] = v01;
-            dv[1] = v23;
+            float4 *dm = reinterpret_cast<float4 *>(&S.mu[sl][0]);
+            float4 *dv = reinterpret_cast<float4 *>(&S.v[sl][0]);
+            dm[swz(g4 >> 1)] = m01;
+            dm[swz((g4 >> 1) + 1)] = m23;
+            dv[swz(g4 >> 1)] = v01;
+            dv[swz((g4 >> 1) + 1)] = v23;
         }
     }
 }
@@ -354,10 +363,10 @@ template <bool COEF>
 __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, const Taps<K> &t,
                                          const Taps2<K> &t2, const SsimConst &cc, float *map, int64_t map_ld, bool col_ok,
                                          const CoefOut &co, float *coef_img, float &sumQ, float &sumCS) {
-    const int col = threadIdx.x & (TW - 1);
+    const int col = threadIdx.x & (TW - 1), scol = swz2(col);
     const int base = rel0 + 4 * (threadIdx.x >> 6);
     const int b0 = base & (RING - 1);  // multiple of 4; b0 + 13 < RROWS
-    const float2 b = S.mu[b0 + 7][col];
+    const float2 b = S.mu[b0 + 7][scol];
     const float2 nb = make_float2(-b.x, -b.y);
     float2 m[4], sq[4];
 #pragma unroll
@@ -365,8 +374,8 @@ __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, 
 #pragma unroll
     for (int i = 0; i < 14; ++i) {
         const int s = b0 + i;
-        const float2 e = add2(S.mu[s][col], nb);   // (eu, ew)
-        const float2 q = fma2(e, e, S.v[s][col]);  // (eu^2 + v_u, ew^2 + v_w)
+        const float2 e = add2(S.mu[s][scol], nb);   // (eu, ew)
+        const float2 q = fma2(e, e, S.v[s][scol]);  // (eu^2 + v_u, ew^2 + v_w)
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
             const int n = i - o;
