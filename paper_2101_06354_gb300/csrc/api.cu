@@ -163,7 +163,8 @@ int plan_levels(const gbssim_plane *x, const gbssim_params *p, int scales, MsPla
 void fix_box_items(Level &L, const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p) {
     if (L.path != PATH_BOX_U8) return;
     const int64_t OH = out_dim(L.H, p->k, p->stride), OW = out_dim(L.W, p->k, p->stride);
-    L.items = box_path_items(OH, OW, p->k, p->stride, box_aligned16(desc_of(x), desc_of(y)));
+    L.items = box_path_items(OH, OW, p->k, p->stride, box_aligned16(desc_of(x), desc_of(y)),
+                             (p->flags & GBSSIM_FLAG_BOX_TMA) != 0);
 }
 
 // Launch one SSIM level: `in_x/in_y` describe the level's images (dtype),

@@ -248,7 +248,7 @@ struct BoxLaunch {
 };
 int box_items_ks(int64_t OH, int64_t OW, int k, int s);  // workspace sizing (max over layouts)
 bool box_aligned16(const ImgDesc &x, const ImgDesc &y);
-int box_path_items(int64_t OH, int64_t OW, int k, int s, bool aligned16);  // items of the layout launched
+int box_path_items(int64_t OH, int64_t OW, int k, int s, bool aligned16, bool tma);  // items of the layout launched
 cudaError_t launch_box_u8(const BoxLaunch &L, cudaStream_t st);
 
 // 2x2 average downsample of a batch into dense float planes (k_pool.cu).

@@ -82,7 +82,18 @@ __device__ __forceinline__ void box_formula_f(float s1x, float s1y, float s2x, f
     q = __fdividef(A1, B1) * cs;
 }
 
-// Output phase of the stride-4 kernels: M x M blocks per window, block sums
+// Compensated (Kahan) fp32 running sum.
+struct KSumF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+// Output phase of the TMA stride-4 kernel: M x M blocks per window, block sums
 // in shared memory as exact floats.
 template <int M>
 __device__ __forceinline__ void box_outputs(const float (&Bs)[5][VBH][VBW + 1], const BoxLaunch &L, int img,
@@ -148,80 +159,178 @@ __device__ __forceinline__ void block_sum2f(float a, float b, float *red, double
         }
 }
 
-// ------------------------------------------------------------------ stride-4 vector path
+// ------------------------------------------------------------------ stride-4 column walk
 //
-// Stride 4, k = 4m (m <= 3), 16-byte aligned rows: each thread loads four
-// 16-byte row segments of x and y (16 pixels x 4 rows = four 4 x 4 blocks),
-// all issued before use, and forms the blocks' five sums with dp4a.  A CTA
-// loads 64 x 16 blocks (256 x 64 pixels) and produces VTOW x (17-m) windows;
-// VTOW is a multiple of 4 so that every tile starts on a 16-byte boundary
-// (tile column b starts at pixel 4 * VTOW * b), and VTOW + m - 1 <= 64.
+// Stride 4, k = 4M (M <= 3), 16-byte aligned rows.  One warp is one work
+// item: a strip of 32 lanes x VB blocks of 4 x 4 pixels walked down a
+// segment of block rows.  Per block row each lane loads 4 VB bytes of four
+// pixel rows of x and y (one vector load per row and image), forms the five
+// sums of its VB blocks with dp4a, takes the first M-1 block sums of the
+// next lane by shuffle and adds the M blocks of each of its VB window
+// columns (exact int32); the M rows of a window are added from a rolling
+// register copy of the previous M-1 block rows.  Lane 31 only feeds lane 30,
+// so strips advance by 31 lanes (31 VB window columns; 124 VB pixels keep
+// the vector loads aligned).  Every input byte comes from HBM once; the M-1
+// halo block rows of a segment are re-read, normally from L2.  Nothing goes
+// through shared memory.
+constexpr int S4C_VB = 2;                // blocks per lane
+constexpr int CW_STEP = 31 * S4C_VB;     // window columns per strip
 
+__device__ __forceinline__ float i2f_exact(int v) { return __int2float_rn(v); }  // |v| < 2^24 here
 
-__global__ void __launch_bounds__(NT) box_s4_kernel(const BoxLaunch L, int tiles_x, int tiles_y) {
-    __shared__ float Bs[5][VBH][VBW + 1];
-    __shared__ float red[2 * NT / 32];
-    const int m = L.k >> 2;
-    const int tow = VTOW, toh = VBH - m + 1;
-    const int img = blockIdx.z;
+template <int VB>
+struct VecOf;
+template <>
+struct VecOf<4> {
+    using T = uint4;
+    static __device__ __forceinline__ unsigned get(const uint4 &v, int b) {
+        return b == 0 ? v.x : b == 1 ? v.y : b == 2 ? v.z : v.w;
+    }
+    static __device__ __forceinline__ uint4 make(const unsigned (&w)[4]) { return make_uint4(w[0], w[1], w[2], w[3]); }
+};
+template <>
+struct VecOf<2> {
+    using T = uint2;
+    static __device__ __forceinline__ unsigned get(const uint2 &v, int b) { return b == 0 ? v.x : v.y; }
+    static __device__ __forceinline__ uint2 make(const unsigned (&w)[2]) { return make_uint2(w[0], w[1]); }
+};
+
+template <int M, int VB>
+__global__ void __launch_bounds__(NT) box_s4c_kernel(const BoxLaunch L, int strips, int segs, int seg_rows) {
+    static_assert(M - 1 <= VB, "the next lane must hold the M-1 halo blocks");
+    using V = VecOf<VB>;
+    using VT = typename V::T;
+    constexpr int MP = M > 1 ? M - 1 : 1;
+    const int lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
+    const int64_t per_img = (int64_t)strips * segs;
+    if (item >= per_img * L.count) return;  // whole warps only
+    const int img = (int)(item / per_img);
+    const int rem = (int)(item - (int64_t)img * per_img);
+    const int seg = rem / strips, strip = rem - seg * strips;
     const int64_t H = L.x.H, W = L.x.W, rs = L.x.row_stride;
-    const int64_t OH = out_dim(H, L.k, 4), OW = out_dim(W, L.k, 4);
-    const int64_t a0 = (int64_t)blockIdx.y * toh, b0 = (int64_t)blockIdx.x * tow;
+    const int64_t OH = out_dim(H, 4 * M, 4), OW = out_dim(W, 4 * M, 4);
     const uint8_t *xb = static_cast<const uint8_t *>(L.x.data) + img * L.x.image_stride;
     const uint8_t *yb = static_cast<const uint8_t *>(L.y.data) + img * L.y.image_stride;
-
-    // thread -> block row bi (0..15), four blocks starting at column 4*qd
-    const int bi = threadIdx.x >> 4, qd = threadIdx.x & 15;
-    const int64_t r0 = (a0 + bi) * 4, c0 = (b0 + 4 * qd) * 4;
-    uint4 vx[4], vy[4];
-    const bool rows_in = r0 + 4 <= H;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        vx[r] = vy[r] = make_uint4(0u, 0u, 0u, 0u);
-        if (rows_in && c0 + 16 <= W) {
-            vx[r] = __ldg(reinterpret_cast<const uint4 *>(xb + (r0 + r) * rs + c0));
-            vy[r] = __ldg(reinterpret_cast<const uint4 *>(yb + (r0 + r) * rs + c0));
-        } else if (rows_in) {  // ragged right edge: whole 4-pixel blocks only
-            unsigned wx[4] = {0u, 0u, 0u, 0u}, wy[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-                if (c0 + 4 * b + 4 <= W) {
-                    wx[b] = __ldg(reinterpret_cast<const unsigned *>(xb + (r0 + r) * rs + c0) + b);
-                    wy[b] = __ldg(reinterpret_cast<const unsigned *>(yb + (r0 + r) * rs + c0) + b);
-                }
-            vx[r] = make_uint4(wx[0], wx[1], wx[2], wx[3]);
-            vy[r] = make_uint4(wy[0], wy[1], wy[2], wy[3]);
-        }
-    }
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        unsigned sx = 0, sy = 0, sxx = 0, syy = 0, sxy = 0;
+    const int64_t bc = (int64_t)strip * (31 * VB) + VB * lane;  // first block (= window) column of the lane
+    const int64_t c0 = 4 * bc;                               // its first pixel column
+    const int64_t a_begin = (int64_t)seg * seg_rows;
+    const int nout = (int)min((int64_t)seg_rows, OH - a_begin);
+    const float kk = (float)(16 * M * M);
+    int hp[MP][VB][5];  // window-column sums of the previous M-1 block rows
+    KSumF accQ, accCS;
+    for (int i = 0; i < nout + M - 1; ++i) {
+        const int64_t br = a_begin + i;
+        VT vx[4], vy[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            const unsigned wx = b == 0 ? vx[r].x : b == 1 ? vx[r].y : b == 2 ? vx[r].z : vx[r].w;
-            const unsigned wy = b == 0 ? vy[r].x : b == 1 ? vy[r].y : b == 2 ? vy[r].z : vy[r].w;
-            sx = __dp4a(wx, 0x01010101u, sx);
-            sy = __dp4a(wy, 0x01010101u, sy);
-            sxx = __dp4a(wx, wx, sxx);
-            syy = __dp4a(wy, wy, syy);
-            sxy = __dp4a(wx, wy, sxy);
+            unsigned wx[VB], wy[VB];
+#pragma unroll
+            for (int b = 0; b < VB; ++b) wx[b] = wy[b] = 0u;
+            vx[r] = V::make(wx);
+            vy[r] = V::make(wy);
+            const int64_t row = 4 * br + r;
+            if (row >= H) continue;
+            const uint8_t *px = xb + row * rs + c0, *py = yb + row * rs + c0;
+            if (c0 + 4 * VB <= W) {
+                vx[r] = __ldg(reinterpret_cast<const VT *>(px));
+                vy[r] = __ldg(reinterpret_cast<const VT *>(py));
+            } else {  // ragged right edge: whole 4-pixel blocks only
+#pragma unroll
+                for (int b = 0; b < VB; ++b)
+                    if (c0 + 4 * b + 4 <= W) {
+                        wx[b] = __ldg(reinterpret_cast<const unsigned *>(px) + b);
+                        wy[b] = __ldg(reinterpret_cast<const unsigned *>(py) + b);
+                    }
+                vx[r] = V::make(wx);
+                vy[r] = V::make(wy);
+            }
         }
-        const int bj = 4 * qd + b;
-        Bs[0][bi][bj] = (float)sx;
-        Bs[1][bi][bj] = (float)sy;
-        Bs[2][bi][bj] = (float)sxx;
-        Bs[3][bi][bj] = (float)syy;
-        Bs[4][bi][bj] = (float)sxy;
+        int B[VB][5];
+#pragma unroll
+        for (int b = 0; b < VB; ++b) {
+            unsigned sx = 0, sy = 0, sxx = 0, syy = 0, sxy = 0;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const unsigned wx = V::get(vx[r], b);
+                const unsigned wy = V::get(vy[r], b);
+                sx = __dp4a(wx, 0x01010101u, sx);
+                sy = __dp4a(wy, 0x01010101u, sy);
+                sxx = __dp4a(wx, wx, sxx);
+                syy = __dp4a(wy, wy, syy);
+                sxy = __dp4a(wx, wy, sxy);
+            }
+            B[b][0] = (int)sx;
+            B[b][1] = (int)sy;
+            B[b][2] = (int)sxx;
+            B[b][3] = (int)syy;
+            B[b][4] = (int)sxy;
+        }
+        int N[MP][5];  // first M-1 blocks of the next lane
+#pragma unroll
+        for (int j = 0; j < M - 1; ++j)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) N[j][q] = __shfl_down_sync(0xffffffffu, B[j][q], 1);
+        int Hc[VB][5];
+#pragma unroll
+        for (int t = 0; t < VB; ++t)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                int v = 0;
+#pragma unroll
+                for (int j = 0; j < M; ++j) v += t + j < VB ? B[t + j][q] : N[t + j - VB][q];
+                Hc[t][q] = v;
+            }
+        if (i >= M - 1) {
+            const int64_t a = br - (M - 1);
+#pragma unroll
+            for (int t = 0; t < VB; ++t) {
+                int w[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    int v = Hc[t][q];
+#pragma unroll
+                    for (int j = 0; j < M - 1; ++j) v += hp[j][t][q];
+                    w[q] = v;
+                }
+                const int64_t b = bc + t;
+                if (lane < 31 && b < OW) {
+                    if (L.sums_out) {
+                        int64_t *dst = L.sums_out + 5 * ((int64_t)img * OH * OW + a * OW + b);
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) dst[q] = w[q];
+                    } else {
+                        float qv, cs;
+                        box_formula_f(i2f_exact(w[0]), i2f_exact(w[1]), i2f_exact(w[2]), i2f_exact(w[3]),
+                                      i2f_exact(w[4]), kk, L.C1k4, L.C2k4, qv, cs);
+                        accQ.add(qv);
+                        accCS.add(cs);
+                        if (L.map) L.map[img * L.map_is + a * L.map_ld + b] = qv;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j + 1 < M - 1; ++j)
+#pragma unroll
+            for (int t = 0; t < VB; ++t)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) hp[j][t][q] = hp[j + 1][t][q];
+        if (M > 1) {
+#pragma unroll
+            for (int t = 0; t < VB; ++t)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) hp[MP - 1][t][q] = Hc[t][q];
+        }
     }
-    __syncthreads();
-
-    float accQ = 0.f, accCS = 0.f;
-    box_outputs_m(m, Bs, L, img, a0, b0, tow, toh, OH, OW, accQ, accCS);
     if (L.partials) {
-        double da, db;
-        block_sum2f(accQ, accCS, red, da, db);
-        if (threadIdx.x == 0)
-            L.partials[((int64_t)img * tiles_y + blockIdx.y) * tiles_x + blockIdx.x] = make_double2(da, db);
+        double sq = (double)accQ.s - (double)accQ.c, sc = (double)accCS.s - (double)accCS.c;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sq += __shfl_down_sync(0xffffffffu, sq, o);
+            sc += __shfl_down_sync(0xffffffffu, sc, o);
+        }
+        if (lane == 0) L.partials[item] = make_double2(sq, sc);
     }
 }
 
@@ -577,12 +686,25 @@ __global__ void __launch_bounds__(NT) box_sat_kernel(const BoxLaunch L, int tile
 bool use_block_path(int k, int s) { return s % 4 == 0 && k % s == 0 && k <= 16; }
 bool use_s4_path(int k, int s) { return s == 4 && k % 4 == 0 && k <= 12 && VTOW + k / 4 - 1 <= VBW; }
 
-void box_tiles(int64_t OH, int64_t OW, int k, int s, int *tx, int *ty, bool s4) {
-    if (s4) {
+// Block rows (= output rows) per warp item of the column-walk kernel.
+constexpr int kS4cSeg = 8;
+
+enum BoxLayout { LAYOUT_S4C, LAYOUT_TMA, LAYOUT_BLOCK, LAYOUT_SAT };
+
+BoxLayout box_layout(int k, int s, bool aligned16, bool tma) {
+    if (aligned16 && use_s4_path(k, s)) return tma ? LAYOUT_TMA : LAYOUT_S4C;
+    return use_block_path(k, s) ? LAYOUT_BLOCK : LAYOUT_SAT;
+}
+
+void box_tiles(int64_t OH, int64_t OW, int k, int s, BoxLayout lay, int *tx, int *ty) {
+    if (lay == LAYOUT_S4C) {
+        *tx = (int)((OW + CW_STEP - 1) / CW_STEP);
+        *ty = (int)((OH + kS4cSeg - 1) / kS4cSeg);
+    } else if (lay == LAYOUT_TMA) {
         const int m = k / 4;
         *tx = (int)((OW + VTOW - 1) / VTOW);
         *ty = (int)((OH + VBH - m) / (VBH - m + 1));
-    } else if (use_block_path(k, s)) {
+    } else if (lay == LAYOUT_BLOCK) {
         const int m = k / s;
         const int tow = BW - m + 1, toh = BH - m + 1;
         *tx = (int)((OW + tow - 1) / tow);
@@ -596,36 +718,40 @@ void box_tiles(int64_t OH, int64_t OW, int k, int s, int *tx, int *ty, bool s4) 
 
 }  // namespace
 
-// The stride-4 vector path needs 16-byte aligned rows.  Workspace sizing uses
-// the larger item count of the two block layouts (box_items_ks); a launch
-// uses the layout its pointers allow, and the host pools box_path_items of it.
+// The stride-4 paths need 16-byte aligned rows, and the opt-in TMA kernel
+// has its own tiles.  Workspace sizing uses the largest item count of all
+// layouts (box_items_ks); a launch uses the layout its pointers and flags
+// select, and the host pools box_path_items of that layout.
 bool box_aligned16(const ImgDesc &x, const ImgDesc &y) {
     const uintptr_t bx = (uintptr_t)x.data, by = (uintptr_t)y.data;
     return bx % 16 == 0 && by % 16 == 0 && x.row_stride % 16 == 0 && y.row_stride % 16 == 0 &&
            x.image_stride % 16 == 0 && y.image_stride % 16 == 0;
 }
 
-int box_path_items(int64_t OH, int64_t OW, int k, int s, bool aligned16) {
+int box_path_items(int64_t OH, int64_t OW, int k, int s, bool aligned16, bool tma) {
     int tx, ty;
-    box_tiles(OH, OW, k, s, &tx, &ty, aligned16 && use_s4_path(k, s));
+    box_tiles(OH, OW, k, s, box_layout(k, s, aligned16, tma), &tx, &ty);
     return tx * ty;
 }
 
 int box_items_ks(int64_t OH, int64_t OW, int k, int s) {
-    const int a = box_path_items(OH, OW, k, s, false), b = box_path_items(OH, OW, k, s, true);
-    return a > b ? a : b;
+    int best = 0;
+    for (int a = 0; a < 2; ++a)
+        for (int t = 0; t < 2; ++t) best = max(best, box_path_items(OH, OW, k, s, a != 0, t != 0));
+    return best;
 }
 
 cudaError_t launch_box_u8(const BoxLaunch &L, cudaStream_t st) {
     const int64_t OH = out_dim(L.x.H, L.k, L.stride), OW = out_dim(L.x.W, L.k, L.stride);
-    const bool s4 = box_aligned16(L.x, L.y) && use_s4_path(L.k, L.stride);
+    if (L.count <= 0 || OH <= 0 || OW <= 0) return cudaSuccess;
+    const BoxLayout lay = box_layout(L.k, L.stride, box_aligned16(L.x, L.y), L.use_tma);
     int tx, ty;
-    box_tiles(OH, OW, L.k, L.stride, &tx, &ty, s4);
+    box_tiles(OH, OW, L.k, L.stride, lay, &tx, &ty);
     dim3 grid(tx, ty, L.count);
-    CUtensorMap mx, my;
-    const bool tma = L.use_tma && s4 && L.count >= 1 && L.x.image_stride % 16 == 0 &&
-                     encode_u8_map(&mx, L.x, L.count) && encode_u8_map(&my, L.y, L.count);
-    if (tma) {
+    if (lay == LAYOUT_TMA) {
+        CUtensorMap mx, my;
+        // the item count was fixed for this layout: no silent fallback
+        if (!encode_u8_map(&mx, L.x, L.count) || !encode_u8_map(&my, L.y, L.count)) return cudaErrorInvalidValue;
         static bool attr_set[64] = {};
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
@@ -641,8 +767,14 @@ cudaError_t launch_box_u8(const BoxLaunch &L, cudaStream_t st) {
         const int total = tx * ty * L.count;
         const int g = min(total, max(1, sms * max(per_sm, 1)));
         box_tma_kernel<<<g, NT, sizeof(TmaSmem), st>>>(mx, my, L, tx, ty);
-    } else if (s4) {
-        box_s4_kernel<<<grid, NT, 0, st>>>(L, tx, ty);
+    } else if (lay == LAYOUT_S4C) {
+        const int64_t warps = (int64_t)tx * ty * L.count;
+        const int64_t ctas = (warps + NT / 32 - 1) / (NT / 32);
+        if (ctas > 0x7fffffff) return cudaErrorInvalidValue;
+        const int m = L.k / 4;
+        if (m == 1) box_s4c_kernel<1, S4C_VB><<<(unsigned)ctas, NT, 0, st>>>(L, tx, ty, kS4cSeg);
+        else if (m == 2) box_s4c_kernel<2, S4C_VB><<<(unsigned)ctas, NT, 0, st>>>(L, tx, ty, kS4cSeg);
+        else box_s4c_kernel<3, S4C_VB><<<(unsigned)ctas, NT, 0, st>>>(L, tx, ty, kS4cSeg);
     } else if (use_block_path(L.k, L.stride)) {
         const uintptr_t bx = (uintptr_t)L.x.data, by = (uintptr_t)L.y.data;
         const int aligned4 = (bx % 4 == 0) && (by % 4 == 0) && (L.x.row_stride % 4 == 0) &&

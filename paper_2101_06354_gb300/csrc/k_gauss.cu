@@ -59,7 +59,14 @@ constexpr int RING = 32;          // ring rows (>= CH + HALO, power of two)
 constexpr int FIRST = CH + HALO;  // input rows staged for the first chunk
 constexpr int IW = TW + HALO;     // input columns per strip (74)
 constexpr int QUADS = (IW + 3) / 4;                 // 4-column staging units per row (19)
-constexpr int IWP = 4 * QUADS;                      // staged row pitch in (x, y) pairs (76)
+// Row pitches of the staged rows (78 pairs = 39 16-byte slots) and of the
+// moment ring (66 pairs = 33 slots) are odd in 16-byte slots: the horizontal
+// pass gives each quarter-warp 4 output groups of 2 adjacent rows, whose
+// 16-byte accesses then fall on the even and the odd bank groups
+// respectively, so no access of the pass conflicts and every tap offset is a
+// compile-time constant.
+constexpr int IWP = 4 * QUADS + 2;                  // staged row pitch in (u, w) pairs (78)
+constexpr int RWP = TW + 2;                         // ring row pitch in pairs (66)
 constexpr int NT = 256;
 // The vertical pass of a thread reads ring rows base..base+13 with base a
 // multiple of 4 below RING; rows 0..DUP-1 are also stored at RING..RING+DUP-1
@@ -72,19 +79,10 @@ constexpr int RROWS = RING + DUP;
 // on sm_100+).
 struct __align__(16) Smem {
     float2 in[FIRST][IWP];   // staged input rows, (u, w) per column
-    float2 mu[RROWS][TW];    // row-window means (mu_u, mu_w)
-    float2 v[RROWS][TW];     // row-window variances (v_u, v_w)
+    float2 mu[RROWS][RWP];   // row-window means (mu_u, mu_w)
+    float2 v[RROWS][RWP];    // row-window variances (v_u, v_w)
     float red[2 * NT / 32];
 };
-
-// Shared-memory swizzle.  The horizontal pass reads and writes 16-byte slots
-// at a 32-byte lane stride (four outputs per thread), a 2-way bank conflict
-// on every access; flipping bit 0 of the slot index when bit 3 is set spreads
-// each quarter-warp over all eight 16-byte bank groups.  The vertical pass
-// reads 8-byte elements at consecutive lanes; the same permutation stays
-// within each aligned group of eight slots, so those reads stay conflict-free.
-__device__ __forceinline__ int swz(int slot) { return slot ^ ((slot >> 3) & 1); }     // 16-byte slots
-__device__ __forceinline__ int swz2(int col) { return col ^ ((col >> 3) & 2); }        // 8-byte elements
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -203,9 +201,9 @@ template <typename T>
 __device__ __forceinline__ void put_unit(Smem &S, int r, int q, uint4 rx, uint4 ry, bool packed) {
     float2 o[4];
     convert_uw<T>(rx, ry, packed, o);
-    float4 *d = reinterpret_cast<float4 *>(&S.in[r][0]);
-    d[swz(2 * q)] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
-    d[swz(2 * q + 1)] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+    float4 *d = reinterpret_cast<float4 *>(&S.in[r][4 * q]);
+    d[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+    d[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
 }
 
 // Staging unit: one quad (4 columns) of two adjacent input rows.  Holding
@@ -300,16 +298,26 @@ __device__ __forceinline__ void stage_direct(Smem &S, const Geo &g, int64_t r0, 
     }
 }
 
-// Horizontal pass over staged rows 0..nr-1; results go to ring rows
-// (rel0 + r) & (RING-1), where rel0 is the row index relative to the segment.
-__device__ __forceinline__ void horizontal(Smem &S, int nr, int rel0, const Taps<K> &t, const Taps2<K> &t2) {
-    for (int task = threadIdx.x; task < nr * (TW / 4); task += NT) {
-        const int r = task >> 4, g4 = (task & 15) * 4;
+// Horizontal pass over staged rows 0..NR-1 (NR even); results go to ring
+// rows (rel0 + r) & (RING-1), where rel0 is the row index relative to the
+// segment.  Task t: warp w = t / 32 takes rows 2w, 2w + 1; within a
+// quarter-warp (8 lanes) lanes 0-3 and 4-7 take 4 consecutive groups of 4
+// outputs of the first and the second row.
+template <int NR>
+__device__ __forceinline__ void horizontal(Smem &S, int rel0, const Taps2<K> &t2) {
+    static_assert(NR % 2 == 0, "rows come in pairs");
+#pragma unroll 1
+    for (int pass = 0; pass < (NR * (TW / 4) + NT - 1) / NT; ++pass) {
+        const int task = threadIdx.x + pass * NT;
+        if (NR * (TW / 4) % NT != 0 && task >= NR * (TW / 4)) break;
+        const int lane = task & 31;
+        const int r = 2 * (task >> 5) + ((lane >> 2) & 1);
+        const int g4 = 4 * (4 * (lane >> 3) + (lane & 3));
         float2 p[14];
-        const float4 *src = reinterpret_cast<const float4 *>(&S.in[r][0]);
+        const float4 *src = reinterpret_cast<const float4 *>(&S.in[r][g4]);
 #pragma unroll
         for (int k = 0; k < 7; ++k) {
-            const float4 v = src[swz((g4 >> 1) + k)];
+            const float4 v = src[k];
             p[2 * k] = make_float2(v.x, v.y);
             p[2 * k + 1] = make_float2(v.z, v.w);
         }
@@ -347,12 +355,12 @@ __device__ __forceinline__ void horizontal(Smem &S, int nr, int rel0, const Taps
         for (int rep = 0; rep < 2; ++rep) {
             const int sl = rep ? slot + RING : slot;
             if (rep && slot >= DUP) break;
-            float4 *dm = reinterpret_cast<float4 *>(&S.mu[sl][0]);
-            float4 *dv = reinterpret_cast<float4 *>(&S.v[sl][0]);
-            dm[swz(g4 >> 1)] = m01;
-            dm[swz((g4 >> 1) + 1)] = m23;
-            dv[swz(g4 >> 1)] = v01;
-            dv[swz((g4 >> 1) + 1)] = v23;
+            float4 *dm = reinterpret_cast<float4 *>(&S.mu[sl][g4]);
+            float4 *dv = reinterpret_cast<float4 *>(&S.v[sl][g4]);
+            dm[0] = m01;
+            dm[1] = m23;
+            dv[0] = v01;
+            dv[1] = v23;
         }
     }
 }
@@ -363,10 +371,10 @@ template <bool COEF>
 __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, const Taps<K> &t,
                                          const Taps2<K> &t2, const SsimConst &cc, float *map, int64_t map_ld, bool col_ok,
                                          const CoefOut &co, float *coef_img, float &sumQ, float &sumCS) {
-    const int col = threadIdx.x & (TW - 1), scol = swz2(col);
+    const int col = threadIdx.x & (TW - 1);
     const int base = rel0 + 4 * (threadIdx.x >> 6);
     const int b0 = base & (RING - 1);  // multiple of 4; b0 + 13 < RROWS
-    const float2 b = S.mu[b0 + 7][scol];
+    const float2 b = S.mu[b0 + 7][col];
     const float2 nb = make_float2(-b.x, -b.y);
     float2 m[4], sq[4];
 #pragma unroll
@@ -374,8 +382,8 @@ __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, 
 #pragma unroll
     for (int i = 0; i < 14; ++i) {
         const int s = b0 + i;
-        const float2 e = add2(S.mu[s][scol], nb);   // (eu, ew)
-        const float2 q = fma2(e, e, S.v[s][scol]);  // (eu^2 + v_u, ew^2 + v_w)
+        const float2 e = add2(S.mu[s][col], nb);   // (eu, ew)
+        const float2 q = fma2(e, e, S.v[s][col]);  // (eu^2 + v_u, ew^2 + v_w)
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
             const int n = i - o;
@@ -493,7 +501,7 @@ __device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps
 
     stage_direct<T, LD>(S, g, g.o0, FIRST, it.dsx, it.dsy);
     __syncthreads();
-    horizontal(S, FIRST, 0, taps, taps2);
+    horizontal<FIRST>(S, 0, taps2);
     for (int c = 0; c < nchunks; ++c) {
         const bool more = c + 1 < nchunks;
         const int64_t next_r0 = g.o0 + FIRST + (int64_t)CH * c;
@@ -505,7 +513,7 @@ __device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps
         accCS.add(ccs);
         if (more) store_unit<T>(S, raw, U, g, next_r0, 0, it.dsx, it.dsy);
         __syncthreads();  // staging complete; ring rows of chunk c consumed
-        if (more) horizontal(S, CH, FIRST + CH * c, taps, taps2);
+        if (more) horizontal<CH>(S, FIRST + CH * c, taps2);
     }
     double a, b;
     block_sum2f(accQ.s - accQ.c, accCS.s - accCS.c, S.red, a, b);

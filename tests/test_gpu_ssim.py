@@ -220,9 +220,11 @@ def test_box_ssim_tma_loader_matches(g, synth, k):
     a, ma = g.ssim(x.to(DEV), y.to(DEV), return_map=True, window="box", k=k, stride=4)
     b, mb = g.ssim(x.to(DEV), y.to(DEV), return_map=True, window="box", k=k, stride=4, flags=g.FLAG_BOX_TMA)
     assert torch.equal(ma, mb)
-    assert torch.allclose(a, b, rtol=0, atol=1e-9)
+    # same map, pooled with different fp32 groupings (per-warp strips vs tiles)
+    assert torch.allclose(a, b, rtol=0, atol=1e-7)
     ref_mean, ref_q, _, _ = oracle.box_ssim(x[1].numpy(), y[1].numpy(), k, 4)
     _check_map(mb[1].cpu().numpy(), ref_q)
+    assert abs(a[1].item() - ref_mean) <= POOL_TOL
 
 
 def test_box_ssim_adversarial(g):
