@@ -173,7 +173,8 @@ __device__ __forceinline__ void block_sum2f(float a, float b, float *red, double
 // the vector loads aligned).  Every input byte comes from HBM once; the M-1
 // halo block rows of a segment are re-read, normally from L2.  Nothing goes
 // through shared memory.
-constexpr int S4C_VB = 2;                // blocks per lane
+constexpr int S4C_VB = 4;                // blocks per lane
+constexpr int S4C_STAGES = 3;            // block rows in flight per warp
 constexpr int CW_STEP = 31 * S4C_VB;     // window columns per strip
 
 __device__ __forceinline__ float i2f_exact(int v) { return __int2float_rn(v); }  // |v| < 2^24 here
@@ -195,11 +196,33 @@ struct VecOf<2> {
     static __device__ __forceinline__ uint2 make(const unsigned (&w)[2]) { return make_uint2(w[0], w[1]); }
 };
 
-template <int M, int VB>
+// Asynchronous copy of `bytes` (8 or 16) from global to shared memory; the
+// first src_size bytes are read and the rest of the destination is zeroed
+// (src_size 0: nothing is read).
+template <int BYTES>
+__device__ __forceinline__ void cp_async_zfill(void *dst, const void *src, int src_size) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_size) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(src_size) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Dynamic shared memory of box_s4c_kernel<M, VB, S>: per warp, S stages of
+// (x, y) x 4 pixel rows x 32 lanes of 4 VB bytes.
+template <int VB, int S>
+constexpr size_t s4c_smem() { return (size_t)(NT / 32) * S * 2 * 4 * 32 * 4 * VB; }
+
+template <int M, int VB, int S>
 __global__ void __launch_bounds__(NT) box_s4c_kernel(const BoxLaunch L, int strips, int segs, int seg_rows) {
     static_assert(M - 1 <= VB, "the next lane must hold the M-1 halo blocks");
+    static_assert(S >= 2, "at least double buffering");
     using V = VecOf<VB>;
     using VT = typename V::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int MP = M > 1 ? M - 1 : 1;
     const int lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
@@ -219,32 +242,44 @@ __global__ void __launch_bounds__(NT) box_s4c_kernel(const BoxLaunch L, int stri
     const float kk = (float)(16 * M * M);
     int hp[MP][VB][5];  // window-column sums of the previous M-1 block rows
     KSumF accQ, accCS;
-    for (int i = 0; i < nout + M - 1; ++i) {
+    // Per-lane staging ring: block row i lives in stage i % S.  Each lane
+    // copies and later reads only its own bytes, so no barrier is needed; the
+    // copy of block row i + S - 1 is issued before row i is summed and
+    // overwrites the stage of row i - 1, whose values were consumed in the
+    // previous iteration.  Ragged right edge: whole 4-pixel blocks only (the
+    // rest zero-filled); rows past the image bottom are zero-filled.
+    VT *ring = reinterpret_cast<VT *>(smem_raw) + (size_t)(threadIdx.x >> 5) * S * 2 * 4 * 32 + lane;
+    const int nrows = nout + M - 1;
+    const int nb = (int)max((int64_t)0, min((int64_t)VB, (W - c0) / 4));  // whole blocks inside the image
+    auto issue = [&](int i) {
         const int64_t br = a_begin + i;
+        VT *st = ring + (size_t)(i % S) * 2 * 4 * 32;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int64_t row = 4 * br + r;
+            const bool in = row < H && nb > 0;
+            const int bytes = in ? 4 * nb : 0;
+            const uint8_t *px = in ? xb + row * rs + c0 : xb, *py = in ? yb + row * rs + c0 : yb;
+            cp_async_zfill<4 * VB>(st + r * 32, px, bytes);
+            cp_async_zfill<4 * VB>(st + (4 + r) * 32, py, bytes);
+        }
+    };
+#pragma unroll
+    for (int i = 0; i < S - 1; ++i) {
+        if (i < nrows) issue(i);
+        cp_async_commit();
+    }
+    for (int i = 0; i < nrows; ++i) {
+        const int64_t br = a_begin + i;
+        if (i + S - 1 < nrows) issue(i + S - 1);
+        cp_async_commit();
+        cp_async_wait<S - 1>();  // block row i has landed
+        const VT *st = ring + (size_t)(i % S) * 2 * 4 * 32;
         VT vx[4], vy[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            unsigned wx[VB], wy[VB];
-#pragma unroll
-            for (int b = 0; b < VB; ++b) wx[b] = wy[b] = 0u;
-            vx[r] = V::make(wx);
-            vy[r] = V::make(wy);
-            const int64_t row = 4 * br + r;
-            if (row >= H) continue;
-            const uint8_t *px = xb + row * rs + c0, *py = yb + row * rs + c0;
-            if (c0 + 4 * VB <= W) {
-                vx[r] = __ldg(reinterpret_cast<const VT *>(px));
-                vy[r] = __ldg(reinterpret_cast<const VT *>(py));
-            } else {  // ragged right edge: whole 4-pixel blocks only
-#pragma unroll
-                for (int b = 0; b < VB; ++b)
-                    if (c0 + 4 * b + 4 <= W) {
-                        wx[b] = __ldg(reinterpret_cast<const unsigned *>(px) + b);
-                        wy[b] = __ldg(reinterpret_cast<const unsigned *>(py) + b);
-                    }
-                vx[r] = V::make(wx);
-                vy[r] = V::make(wy);
-            }
+            vx[r] = st[r * 32];
+            vy[r] = st[(4 + r) * 32];
         }
         int B[VB][5];
 #pragma unroll
@@ -741,6 +776,22 @@ int box_items_ks(int64_t OH, int64_t OW, int k, int s) {
     return best;
 }
 
+template <int M>
+cudaError_t launch_s4c(const BoxLaunch &L, int tx, int ty, unsigned ctas, cudaStream_t st) {
+    constexpr size_t smem = s4c_smem<S4C_VB, S4C_STAGES>();
+    static bool attr_set[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set[dev]) {
+        const cudaError_t e = cudaFuncSetAttribute(box_s4c_kernel<M, S4C_VB, S4C_STAGES>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    box_s4c_kernel<M, S4C_VB, S4C_STAGES><<<ctas, NT, smem, st>>>(L, tx, ty, kS4cSeg);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_box_u8(const BoxLaunch &L, cudaStream_t st) {
     const int64_t OH = out_dim(L.x.H, L.k, L.stride), OW = out_dim(L.x.W, L.k, L.stride);
     if (L.count <= 0 || OH <= 0 || OW <= 0) return cudaSuccess;
@@ -772,9 +823,9 @@ cudaError_t launch_box_u8(const BoxLaunch &L, cudaStream_t st) {
         const int64_t ctas = (warps + NT / 32 - 1) / (NT / 32);
         if (ctas > 0x7fffffff) return cudaErrorInvalidValue;
         const int m = L.k / 4;
-        if (m == 1) box_s4c_kernel<1, S4C_VB><<<(unsigned)ctas, NT, 0, st>>>(L, tx, ty, kS4cSeg);
-        else if (m == 2) box_s4c_kernel<2, S4C_VB><<<(unsigned)ctas, NT, 0, st>>>(L, tx, ty, kS4cSeg);
-        else box_s4c_kernel<3, S4C_VB><<<(unsigned)ctas, NT, 0, st>>>(L, tx, ty, kS4cSeg);
+        if (m == 1) return launch_s4c<1>(L, tx, ty, (unsigned)ctas, st);
+        if (m == 2) return launch_s4c<2>(L, tx, ty, (unsigned)ctas, st);
+        return launch_s4c<3>(L, tx, ty, (unsigned)ctas, st);
     } else if (use_block_path(L.k, L.stride)) {
         const uintptr_t bx = (uintptr_t)L.x.data, by = (uintptr_t)L.y.data;
         const int aligned4 = (bx % 4 == 0) && (by % 4 == 0) && (L.x.row_stride % 4 == 0) &&

@@ -397,6 +397,7 @@ __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, 
     float *mrow = map ? map + (g.o0 + base) * map_ld + g.j0 + col : nullptr;
     sumQ = 0.f;
     sumCS = 0.f;
+    float qs[4], css[4];
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
         const float2 u = add2(m[o], b);                                        // (mu_u, mu_w)
@@ -406,22 +407,34 @@ __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, 
         const float t2c = var.x + cc.C2x2;
         const float A2 = t2c - var.y, B2 = t2c + var.y;
         const float l = __fdividef(A1, B1), cs = __fdividef(A2, B2);
-        const float qv = l * cs;
-        if (o < rows_left) {
-            sumQ += qv;
-            sumCS += cs;
-            if (mrow) mrow[o * map_ld] = qv;
-            if (COEF) {
-                float ca, cb, ccf;
-                ssim_coef(0.5f * (u.x + u.y), 0.5f * (u.x - u.y), 0.5f * A1, 0.5f * B1, 0.5f * A2, 0.5f * B2,
-                          co.which, co.sx, co.sy, ca, cb, ccf);
-                const int64_t ld = coef_ld(g.OW), plane = g.OH * ld;
-                float *dst = coef_img + (g.o0 + base + o) * ld + g.j0 + col;
-                dst[0] = ca;
-                dst[plane] = cb;
-                dst[2 * plane] = ccf;
-            }
+        qs[o] = l * cs;
+        css[o] = cs;
+        if (COEF && o < rows_left) {
+            float ca, cb, ccf;
+            ssim_coef(0.5f * (u.x + u.y), 0.5f * (u.x - u.y), 0.5f * A1, 0.5f * B1, 0.5f * A2, 0.5f * B2, co.which,
+                      co.sx, co.sy, ca, cb, ccf);
+            const int64_t ld = coef_ld(g.OW), plane = g.OH * ld;
+            float *dst = coef_img + (g.o0 + base + o) * ld + g.j0 + col;
+            dst[0] = ca;
+            dst[plane] = cb;
+            dst[2 * plane] = ccf;
         }
+    }
+    if (rows_left >= 4) {  // the common case: all four outputs exist
+        sumQ = (qs[0] + qs[1]) + (qs[2] + qs[3]);
+        sumCS = (css[0] + css[1]) + (css[2] + css[3]);
+    } else {
+#pragma unroll
+        for (int o = 0; o < 4; ++o)
+            if (o < rows_left) {
+                sumQ += qs[o];
+                sumCS += css[o];
+            }
+    }
+    if (mrow) {
+#pragma unroll
+        for (int o = 0; o < 4; ++o)
+            if (o < rows_left) mrow[o * map_ld] = qs[o];
     }
 }
 
