@@ -42,6 +42,8 @@ FLOP_PER_OUTPUT = 240
 LEVELS = [(H >> j, W >> j) for j in range(5)]
 # kernels of libgbssim per MS-SSIM step: the persistent level kernel and the finaliser
 LAUNCHES_PER_STEP = 2
+# pairs of the end-to-end step are copied and scored in this many chunks
+E2E_CHUNKS = 4
 # DRAM bytes (read + write) of one persistent launch on this workload, from the
 # ncu capture summarised in profiles/gauss11_msssim_1080p_x64.md; valid only for
 # the kernel sources it was taken on (sha256 of the files below, first 16 hex).
@@ -204,7 +206,25 @@ def run_extras(args, gbssim, synth, x, y, dev, timed, ws):
     in_bytes = 2 * N_PAIRS * PX_PER_PAIR
     out["box8_s4"] = {"value": ws * N_PAIRS * PX_PER_PAIR / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms,
                       "hbm_gbs": in_bytes / (ms / 1e3) / 1e9, "hbm_frac": in_bytes / (ms / 1e3) / 1e9 / hbm_peak,
-                      "config": "same 64 pairs, box 8x8 stride 4, exact int sums (integral-image path)"}
+                      "config": "same 64 pairs, box 8x8 stride 4, exact int sums (column-walk kernel)"}
+    # pooling family on the 64 stored SSIM maps (1070 x 1910 floats each):
+    # time per call and the bandwidth of the map passes each kind makes
+    _, qmap = gbssim.ssim(x, y, return_map=True)
+    nq, hq, wq = qmap.shape
+    pq = gbssim.Plane(qmap.data_ptr(), gbssim.F32, nq, hq, wq, qmap.stride(1), qmap.stride(0))
+    wsq = gbssim.workspace(pq, gbssim.Params(), gbssim.OP_POOL, dev)
+    map_bytes = qmap.numel() * 4
+    pool_res = {}
+    for kind, pargs, passes in (("mean", (), 1), ("cov", (), 2), ("minkowski", (4.0,), 1), ("fns", (), 4),
+                                ("pp", (6.0, 4000.0), 5)):
+        fpool = lambda: gbssim.ssim_pool(qmap, kind, *pargs, ws=wsq)
+        for _ in range(3):
+            fpool()
+        tq = timed(fpool, k_steps) / k_steps
+        gbs = passes * map_bytes / (tq / 1e3) / 1e9
+        pool_res[kind] = {"ms": tq, "map_passes": passes, "gbs": gbs, "hbm_frac": gbs / hbm_peak}
+    out["pool_maps"] = dict(pool_res, config="64 SSIM maps 1070x1910 fp32 (523 MB), one double per map")
+    del qmap
     lx, ly = synth.loss_pairs_float(32, 3, 512, 512)
     px_step = 32 * 3 * 512 * 512
     loss_res = {}
@@ -340,14 +360,20 @@ def run_gbssim(args):
     in_bytes = 2 * N_PAIRS * PX_PER_PAIR
     hbm_frac = in_bytes / (ms_step / 1e3) / 1e9 / hbm_peak
 
-    # end to end: pinned host inputs, H2D copies + device->host score inside the timed region
+    # end to end: pinned host inputs through gbssim_msssim_host (host->device
+    # copies of the step's pairs overlapped chunk by chunk with the level
+    # kernels, scores copied back), synchronised every step
     xh = x.cpu().pin_memory()
     yh = y.cpu().pin_memory()
+    wsh = gbssim.host_workspace(xh, E2E_CHUNKS)
+    outh = torch.empty(N_PAIRS, dtype=torch.float64).pin_memory()
+    e2e_step = lambda: gbssim.msssim_host(xh, yh, chunks=E2E_CHUNKS, ws=wsh, out=outh)
     for _ in range(2):
-        gbssim.msssim(xh, yh, ws=wsp)
-    ms_e2e = timed(lambda: gbssim.msssim(xh, yh, ws=wsp), max(2, args.steps // 2)) / max(2, args.steps // 2)
-    e2e = {"value": ws * N_PAIRS * PX_PER_PAIR / (ms_e2e / 1e3) / 1e6, "unit": UNIT,
-           "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": 8 * N_PAIRS}
+        e2e_step()
+    ke = max(2, args.steps // 5)
+    ms_e2e = timed(e2e_step, ke) / ke
+    e2e = {"value": ws * N_PAIRS * PX_PER_PAIR / (ms_e2e / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms_e2e,
+           "chunks": E2E_CHUNKS, "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": 8 * N_PAIRS}
 
     extra = {}
     if not args.no_extras:

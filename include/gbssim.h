@@ -110,9 +110,31 @@ typedef enum gbssim_op {
     GBSSIM_OP_POOL = 4
 } gbssim_op;
 
-/* Pooling kinds for gbssim_ssim_pool. */
+/* Pooling kinds for gbssim_ssim_pool (Background section for the mean;
+ * Section "Spatio-temporal Aggregation of Quality Scores" for the rest).
+ * Q is a map value, n the number of values, mu_Q their mean.  `args` (host
+ * memory) holds the parameters listed. */
 typedef enum gbssim_pool_kind {
-    GBSSIM_POOL_MEAN = 0   /* mean of the map (Background section, MSSIM) */
+    GBSSIM_POOL_MEAN = 0,        /* mean of the map (MSSIM) */
+    GBSSIM_POOL_COV = 1,         /* sigma_Q / mu_Q, sigma the population standard deviation */
+    GBSSIM_POOL_MINKOWSKI = 2,   /* (1/n) sum (1 - Q)^p;                 args[0] = p >= 0 */
+    GBSSIM_POOL_DW = 3,          /* sum (1-Q)^p Q / sum (1-Q)^p;          args[0] = p >= 0 */
+    GBSSIM_POOL_MD = 4,          /* ((1/n) sum |Q - mu_Q|^p)^(o/p);       args = p > 0, o */
+    GBSSIM_POOL_GM_DSSIM = 5,    /* geometric mean of 1 - Q */
+    GBSSIM_POOL_HM_DSSIM = 6,    /* harmonic mean of 1 - Q (0 if some Q = 1) */
+    GBSSIM_POOL_PERCENTILE = 7,  /* p-th percentile, linear between order statistics at
+                                    h = p/100 (n-1);                      args[0] = p in [0, 100] */
+    GBSSIM_POOL_MEDIAN = 8,      /* the 50th percentile */
+    GBSSIM_POOL_FNS = 9,         /* five-number summary (min + Q1 + median + Q3 + max) / 5 */
+    GBSSIM_POOL_PP = 10,         /* percentile pooling: values at or below the p-th percentile
+                                    divided by r, then averaged;          args = p in [0, 100], r > 0 */
+    /* series only (gbssim_series_pool): temporal pooling of frame scores */
+    GBSSIM_POOL_GM = 11,         /* geometric mean of the scores */
+    GBSSIM_POOL_HM = 12,         /* harmonic mean of the scores */
+    GBSSIM_POOL_W_AM = 13,       /* mean over the n-k+1 windows of k frames of the window's mean; args[0] = k */
+    GBSSIM_POOL_W_GM = 14,       /* ... of the window's geometric mean;  args[0] = k */
+    GBSSIM_POOL_W_HM = 15,       /* ... of the window's harmonic mean;   args[0] = k */
+    GBSSIM_POOL_W_COV = 16       /* ... of the window's sigma / mean;    args[0] = k */
 } gbssim_pool_kind;
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -148,13 +170,29 @@ int gbssim_ssim_map(const gbssim_plane *x, const gbssim_plane *y, const gbssim_p
                     void *workspace, size_t workspace_bytes, void *stream);
 
 /* Pool `count` float maps (h x w, rows `ld` floats apart, images
- * `image_stride` floats apart) into one double each.  kind = GBSSIM_POOL_MEAN
- * is the Background section's mean pooling; `args` is unused for it (may be
- * NULL).  Needs gbssim_workspace_size(GBSSIM_OP_POOL) bytes of workspace
- * computed for a plane of the map's shape. */
+ * `image_stride` floats apart) into one double each (device memory `out`).
+ * kind is a gbssim_pool_kind; `args` is a host array of its parameters (NULL
+ * for the kinds without).  Moment kinds sum fp32 terms per thread with
+ * compensation and per block in fp64; order statistics are selected exactly
+ * (radix select), so percentiles equal those of the sorted map.  Needs
+ * gbssim_workspace_size(GBSSIM_OP_POOL) bytes of workspace computed for a
+ * plane of the map's shape (height h, width w, count maps).  Errors:
+ * GBSSIM_ERR_INVALID_ARG for a bad kind or parameter, GBSSIM_ERR_UNSUPPORTED
+ * for maps of 2^32 values or more. */
 int gbssim_ssim_pool(const float *map, int64_t h, int64_t w, int64_t ld, int32_t count,
                      int64_t image_stride, int32_t kind, const double *args, double *out,
                      void *workspace, size_t workspace_bytes, void *stream);
+
+/* Temporal pooling of `count` series of n frame scores (doubles, device
+ * memory, series b at scores + b*stride) into one double each (device `out`),
+ * in fp64 (Section "Spatio-temporal Aggregation of Quality Scores").  Every
+ * gbssim_pool_kind applies: the map kinds as for gbssim_ssim_pool, plus
+ * GM / HM and the windowed means W-AM, W-GM, W-HM, W-CoV over the n-k+1
+ * windows of k consecutive frames (args[0] = k, 1 <= k <= n).  `args` is a
+ * host array.  n in 1..4096, count in 1..65535, stride >= n; no workspace.
+ * Errors: GBSSIM_ERR_INVALID_ARG for a bad kind, size or parameter. */
+int gbssim_series_pool(const double *scores, int32_t n, int32_t count, int64_t stride, int32_t kind,
+                       const double *args, double *out, void *stream);
 
 /* MS-SSIM of each pair (Introduction; Section "Salient Features of SSIM and
  * MS-SSIM Implementations"): scale 1 is the input, scale j+1 the 2x2 average
@@ -170,6 +208,36 @@ int gbssim_ssim_pool(const float *map, int64_t h, int64_t w, int64_t ld, int32_t
 int gbssim_msssim(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
                   double *score_out, double *per_scale_out, void *workspace,
                   size_t workspace_bytes, void *stream);
+
+/* MS-SSIM of pairs held in HOST memory, with the host-to-device copies
+ * overlapped with compute (the computation is gbssim_msssim's; this call only
+ * adds the transfers; the paper has no counterpart).  The count images are
+ * split into `chunks` chunks of ceil(count / chunks) images; chunk c+1 is
+ * copied on `copy_stream` into one of two device stages while chunk c is
+ * scored on `stream`, and the scores come back with one device-to-host copy.
+ *   x, y         : host planes (any pitch; pinned memory gives the overlap,
+ *                  pageable memory is correct but copied synchronously).
+ *                  They must stay valid until `stream` has completed.
+ *   chunks       : >= 1 (clamped to count).
+ *   score_host   : x.count doubles in host memory (pinned for an asynchronous
+ *                  return), valid once `stream` has completed.
+ *   workspace    : device buffer of gbssim_msssim_host_workspace_size bytes;
+ *                  every earlier call on `stream` that used it is finished
+ *                  before this call's copies overwrite it.
+ *   stream, copy_stream : two different streams (GBSSIM_ERR_INVALID_ARG if
+ *                  equal); all work of the call is ordered before the end of
+ *                  `stream`.
+ *   stream2      : nullable third stream.  When given, odd chunks are scored
+ *                  on it (each stage has its own MS-SSIM workspace), so one
+ *                  chunk's kernel fills the GPU while the previous one drains;
+ *                  it must differ from the other two.
+ * Six CUDA events are created per call and released when the streams pass
+ * them. */
+int gbssim_msssim_host_workspace_size(const gbssim_plane *x, const gbssim_params *p, int32_t chunks,
+                                      size_t *bytes);
+int gbssim_msssim_host(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t chunks,
+                       double *score_host, void *workspace, size_t workspace_bytes, void *stream,
+                       void *copy_stream, void *stream2);
 
 /* Gradient of the pooled score with respect to the distorted image y, for
  * SSIM (multiscale = 0: score = MSSIM, Background section) or MS-SSIM

@@ -111,10 +111,20 @@ int level_items(Path path, int64_t H, int64_t W, int count, const gbssim_params 
     }
 }
 
+// Rows per work item of the persistent MS-SSIM path at pyramid level j.
+// Level 0 takes long items (the ragged-batch autotuner's choice on 1080p /
+// 4K batches); the small upper levels take short ones, which shortens the
+// chain of dependent items of the last images at the end of the launch.
+int persistent_seg_rows(int j) {
+    static const int rows[5] = {512, 256, 128, 64, 32};
+    return j < 5 ? rows[j] : rows[4];
+}
+
 struct Level {
     int64_t H, W;
     Path path;
     int items, seg_rows;
+    int pitems, pseg_rows;       // the persistent MS-SSIM path's items per image and rows per item
     size_t part_off, plane_off;  // plane_off: x then y planes of this level (j >= 1)
 };
 
@@ -138,8 +148,15 @@ int plan_levels(const gbssim_plane *x, const gbssim_params *p, int scales, MsPla
         if (float_path && L.path == PATH_BOX_U8) L.path = PATH_GENERIC;
         L.seg_rows = 0;
         L.items = level_items(L.path, H, W, x->count, p, &L.seg_rows);
-        L.part_off = off;
-        off = align_up(off + sizeof(double2) * (size_t)L.items * x->count);
+        L.pseg_rows = 0;
+        L.pitems = 0;
+        if (L.path == PATH_GAUSS11) {
+            int strips, segs;
+            L.pseg_rows = persistent_seg_rows(j);
+            L.pitems = gauss11_items(H, W, L.pseg_rows, &strips, &segs);
+        }
+        L.part_off = off;  // pooling slots for whichever layout runs
+        off = align_up(off + sizeof(double2) * (size_t)(L.items > L.pitems ? L.items : L.pitems) * x->count);
         if (j > 0) {
             L.plane_off = off;
             off = align_up(off + 2 * sizeof(float) * (size_t)H * W * x->count);
@@ -246,9 +263,6 @@ cudaError_t run_level(const Level &L, const ImgDesc &dx, const ImgDesc &dy, int 
 // MS-SSIM forward over a planned workspace: level kernels (pyramid fused
 // where the path allows), then the finaliser.  Shared by gbssim_msssim and
 // the MS-SSIM backward.
-// Rows per work item of the persistent MS-SSIM path (the ragged-batch
-// autotuner's choice on 1080p / 4K batches).
-constexpr int kPersistentSegRows = 512;
 
 int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
                           const MsPlan &P, char *ws, double *score_out, double *per_scale_out,
@@ -276,10 +290,11 @@ int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_pa
             UniformLevel &u = U.lv[j];
             u.H = L.H;
             u.W = L.W;
-            u.seg_rows = kPersistentSegRows;
+            u.seg_rows = L.pseg_rows;
             u.strips = (int)((L.W - 10 + 63) / 64);
-            u.segs = (int)((L.H - 10 + kPersistentSegRows - 1) / kPersistentSegRows);
+            u.segs = (int)((L.H - 10 + L.pseg_rows - 1) / L.pseg_rows);
             u.items_per_image = u.strips * u.segs;
+            if (u.items_per_image != L.pitems) return GBSSIM_ERR_INVALID_ARG;  // plan and launch disagree
             if (j == 0) {
                 const size_t esz = x->dtype == GBSSIM_U8 ? 1 : x->dtype == GBSSIM_F32 ? 4 : 2;
                 const uintptr_t vb = 4 * esz;
@@ -402,6 +417,66 @@ int plan_backward(const gbssim_plane *x, const gbssim_params *p, int multiscale,
     return GBSSIM_OK;
 }
 
+// Host-input MS-SSIM: layout of the device buffer.  Two stages of `per`
+// images each (x then y, rows padded to 16 bytes), the MS-SSIM workspace for
+// one chunk, and the scores of all images.
+struct HostPlan {
+    int per, chunks;
+    int64_t pitch_elems;        // device row pitch in elements
+    size_t esz, stage_bytes, plane_bytes;
+    size_t stage_off[2], ws_off[2], score_off, bytes;  // stage s computes in workspace s
+    MsPlan ms;                  // for a chunk of `per` images
+};
+
+int plan_host(const gbssim_plane *x, const gbssim_params *p, int32_t chunks, HostPlan *H) {
+    if (chunks < 1) return GBSSIM_ERR_INVALID_ARG;
+    const int n = x->count;
+    H->chunks = chunks < n ? chunks : n;
+    H->per = (n + H->chunks - 1) / H->chunks;
+    H->chunks = (n + H->per - 1) / H->per;
+    H->esz = x->dtype == GBSSIM_U8 ? 1 : x->dtype == GBSSIM_F32 ? 4 : 2;
+    const size_t row_bytes = (size_t)x->width * H->esz;
+    const size_t pitch = (row_bytes + 15) / 16 * 16;
+    H->pitch_elems = (int64_t)(pitch / H->esz);
+    H->plane_bytes = pitch * (size_t)x->height * (size_t)H->per;
+    H->stage_bytes = 2 * H->plane_bytes;
+    gbssim_plane c = *x;
+    c.count = H->per;
+    c.row_stride = H->pitch_elems;
+    c.image_stride = H->pitch_elems * x->height;
+    int rc = plan_levels(&c, p, p->scales, &H->ms);
+    if (rc) return rc;
+    size_t off = 0;
+    H->stage_off[0] = off;
+    off = align_up(off + H->stage_bytes);
+    H->stage_off[1] = off;
+    off = align_up(off + H->stage_bytes);
+    H->ws_off[0] = off;
+    off = align_up(off + H->ms.bytes);
+    H->ws_off[1] = off;
+    off = align_up(off + H->ms.bytes);
+    H->score_off = off;
+    off = align_up(off + sizeof(double) * (size_t)n);
+    H->bytes = off;
+    return GBSSIM_OK;
+}
+
+// Copy images [i0, i0 + m) of a host plane into a dense pitched device plane.
+cudaError_t copy_images_h2d(const gbssim_plane *h, int i0, int m, const HostPlan &H, char *dst, cudaStream_t cs) {
+    const size_t row_bytes = (size_t)h->width * H.esz, pitch = (size_t)H.pitch_elems * H.esz;
+    const int64_t img_stride = h->count > 1 ? h->image_stride : h->height * h->row_stride;
+    const char *src = static_cast<const char *>(h->data) + (size_t)i0 * img_stride * H.esz;
+    if ((size_t)h->row_stride * H.esz == pitch && img_stride == h->height * h->row_stride)
+        return cudaMemcpyAsync(dst, src, pitch * (size_t)h->height * m, cudaMemcpyHostToDevice, cs);
+    for (int i = 0; i < m; ++i) {
+        const cudaError_t e = cudaMemcpy2DAsync(dst + (size_t)i * pitch * h->height, pitch,
+                                                src + (size_t)i * img_stride * H.esz, (size_t)h->row_stride * H.esz,
+                                                row_bytes, (size_t)h->height, cudaMemcpyHostToDevice, cs);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
@@ -444,7 +519,7 @@ int gbssim_workspace_size(const gbssim_plane *x, const gbssim_params *p, int op,
     int rc = check_plane(x);
     if (rc) return rc;
     if (op == GBSSIM_OP_POOL) {
-        *bytes = align_up(sizeof(double2) * (size_t)pool_items(x->height, x->width) * x->count);
+        *bytes = pool_layout(x->height, x->width, x->count).bytes;
         return GBSSIM_OK;
     }
     rc = check_params(p);
@@ -500,14 +575,91 @@ int gbssim_ssim_map(const gbssim_plane *x, const gbssim_plane *y, const gbssim_p
 int gbssim_ssim_pool(const float *map, int64_t h, int64_t w, int64_t ld, int32_t count,
                      int64_t image_stride, int32_t kind, const double *args, double *out,
                      void *workspace, size_t workspace_bytes, void *stream) {
-    (void)args;
     if (!map || !out || h < 1 || w < 1 || ld < w || count < 1 || count > 65535) return GBSSIM_ERR_INVALID_ARG;
     if (count > 1 && image_stride < h * ld) return GBSSIM_ERR_INVALID_ARG;
-    if (kind != GBSSIM_POOL_MEAN) return GBSSIM_ERR_UNSUPPORTED;
-    const size_t need = align_up(sizeof(double2) * (size_t)pool_items(h, w) * count);
-    if (!workspace || workspace_bytes < need) return GBSSIM_ERR_WORKSPACE;
-    cudaError_t e = launch_pool_mean(map, h, w, ld, count, count > 1 ? image_stride : h * ld,
-                                     (double2 *)workspace, out, (cudaStream_t)stream);
+    if (h * w > 0xffffffffLL) return GBSSIM_ERR_UNSUPPORTED;  // ranks are 32-bit
+    double a0 = 0.0, a1 = 0.0;
+    switch (kind) {
+    case GBSSIM_POOL_MEAN:
+    case GBSSIM_POOL_COV:
+    case GBSSIM_POOL_GM_DSSIM:
+    case GBSSIM_POOL_HM_DSSIM:
+    case GBSSIM_POOL_MEDIAN:
+    case GBSSIM_POOL_FNS: break;
+    case GBSSIM_POOL_MINKOWSKI:
+    case GBSSIM_POOL_DW:
+        if (!args || !(isfinite(args[0]) && args[0] >= 0.0)) return GBSSIM_ERR_INVALID_ARG;
+        a0 = args[0];
+        break;
+    case GBSSIM_POOL_MD:
+        if (!args || !(isfinite(args[0]) && args[0] > 0.0 && isfinite(args[1]))) return GBSSIM_ERR_INVALID_ARG;
+        a0 = args[0];
+        a1 = args[1];
+        break;
+    case GBSSIM_POOL_PERCENTILE:
+        if (!args || !(args[0] >= 0.0 && args[0] <= 100.0)) return GBSSIM_ERR_INVALID_ARG;
+        a0 = args[0];
+        break;
+    case GBSSIM_POOL_PP:
+        if (!args || !(args[0] >= 0.0 && args[0] <= 100.0) || !(isfinite(args[1]) && args[1] > 0.0))
+            return GBSSIM_ERR_INVALID_ARG;
+        a0 = args[0];
+        a1 = args[1];
+        break;
+    default: return GBSSIM_ERR_INVALID_ARG;
+    }
+    const PoolLayout L = pool_layout(h, w, count);
+    if (!workspace || workspace_bytes < L.bytes) return GBSSIM_ERR_WORKSPACE;
+    const cudaError_t e = launch_pool_map(map, h, w, ld, count, count > 1 ? image_stride : h * ld, kind, a0, a1,
+                                          (char *)workspace, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
+}
+
+int gbssim_series_pool(const double *scores, int32_t n, int32_t count, int64_t stride, int32_t kind,
+                       const double *args, double *out, void *stream) {
+    if (!scores || !out || n < 1 || n > kVideoMaxFrames || count < 1 || count > 65535) return GBSSIM_ERR_INVALID_ARG;
+    if (count > 1 && stride < n) return GBSSIM_ERR_INVALID_ARG;
+    double a0 = 0.0, a1 = 0.0;
+    switch (kind) {
+    case GBSSIM_POOL_MEAN:
+    case GBSSIM_POOL_COV:
+    case GBSSIM_POOL_GM_DSSIM:
+    case GBSSIM_POOL_HM_DSSIM:
+    case GBSSIM_POOL_MEDIAN:
+    case GBSSIM_POOL_FNS:
+    case GBSSIM_POOL_GM:
+    case GBSSIM_POOL_HM: break;
+    case GBSSIM_POOL_MINKOWSKI:
+    case GBSSIM_POOL_DW:
+        if (!args || !(isfinite(args[0]) && args[0] >= 0.0)) return GBSSIM_ERR_INVALID_ARG;
+        a0 = args[0];
+        break;
+    case GBSSIM_POOL_MD:
+        if (!args || !(isfinite(args[0]) && args[0] > 0.0 && isfinite(args[1]))) return GBSSIM_ERR_INVALID_ARG;
+        a0 = args[0];
+        a1 = args[1];
+        break;
+    case GBSSIM_POOL_PERCENTILE:
+        if (!args || !(args[0] >= 0.0 && args[0] <= 100.0)) return GBSSIM_ERR_INVALID_ARG;
+        a0 = args[0];
+        break;
+    case GBSSIM_POOL_PP:
+        if (!args || !(args[0] >= 0.0 && args[0] <= 100.0) || !(isfinite(args[1]) && args[1] > 0.0))
+            return GBSSIM_ERR_INVALID_ARG;
+        a0 = args[0];
+        a1 = args[1];
+        break;
+    case GBSSIM_POOL_W_AM:
+    case GBSSIM_POOL_W_GM:
+    case GBSSIM_POOL_W_HM:
+    case GBSSIM_POOL_W_COV:
+        if (!args || !(args[0] >= 1.0 && args[0] <= n && args[0] == floor(args[0]))) return GBSSIM_ERR_INVALID_ARG;
+        a0 = args[0];
+        break;
+    default: return GBSSIM_ERR_INVALID_ARG;
+    }
+    const cudaError_t e =
+        launch_series_pool(scores, n, count, count > 1 ? stride : n, kind, a0, a1, out, (cudaStream_t)stream);
     return e == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
 }
 
@@ -524,6 +676,83 @@ int gbssim_msssim(const gbssim_plane *x, const gbssim_plane *y, const gbssim_par
     if (rc) return rc;
     if (!workspace || workspace_bytes < P.bytes) return GBSSIM_ERR_WORKSPACE;
     return msssim_forward(x, y, p, P, (char *)workspace, score_out, per_scale_out, (cudaStream_t)stream);
+}
+
+int gbssim_msssim_host_workspace_size(const gbssim_plane *x, const gbssim_params *p, int32_t chunks,
+                                      size_t *bytes) {
+    int rc = check_plane(x);
+    if (rc) return rc;
+    rc = check_params(p);
+    if (rc) return rc;
+    if (!bytes) return GBSSIM_ERR_INVALID_ARG;
+    HostPlan H;
+    rc = plan_host(x, p, chunks, &H);
+    if (rc) return rc;
+    *bytes = H.bytes;
+    return GBSSIM_OK;
+}
+
+int gbssim_msssim_host(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t chunks,
+                       double *score_host, void *workspace, size_t workspace_bytes, void *stream,
+                       void *copy_stream, void *stream2) {
+    int rc = check_pair(x, y);
+    if (rc) return rc;
+    rc = check_params(p);
+    if (rc) return rc;
+    if (!score_host) return GBSSIM_ERR_INVALID_ARG;
+    HostPlan H;
+    rc = plan_host(x, p, chunks, &H);
+    if (rc) return rc;
+    if (!workspace || workspace_bytes < H.bytes) return GBSSIM_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream, cs = (cudaStream_t)copy_stream;
+    cudaStream_t cst[2] = {st, stream2 ? (cudaStream_t)stream2 : st};  // compute stream of stage s
+    if (cs == st || cs == cst[1] || (stream2 && cst[1] == st)) return GBSSIM_ERR_INVALID_ARG;
+    char *ws = (char *)workspace;
+    double *score_dev = (double *)(ws + H.score_off);
+    // events: the caller's prior work, per stage "copied" / "consumed", and
+    // the second compute stream's end
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    for (auto &e : ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            for (auto &f : ev)
+                if (f) cudaEventDestroy(f);
+            return GBSSIM_ERR_CUDA;
+        }
+    cudaEvent_t prior = ev[0], copied[2] = {ev[1], ev[2]}, consumed[2] = {ev[3], ev[4]}, done2 = ev[5];
+    cudaError_t e = cudaEventRecord(prior, st);  // earlier calls on `stream` may still read the buffers
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, prior, 0);
+    if (e == cudaSuccess && stream2) e = cudaStreamWaitEvent(cst[1], prior, 0);
+    for (int c = 0; c < H.chunks && e == cudaSuccess && rc == GBSSIM_OK; ++c) {
+        const int s = c & 1, i0 = c * H.per, m = x->count - i0 < H.per ? x->count - i0 : H.per;
+        char *xs = ws + H.stage_off[s], *ysg = xs + H.plane_bytes;
+        if (c >= 2) e = cudaStreamWaitEvent(cs, consumed[s], 0);  // chunk c-2 done with this stage
+        if (e == cudaSuccess) e = copy_images_h2d(x, i0, m, H, xs, cs);
+        if (e == cudaSuccess) e = copy_images_h2d(y, i0, m, H, ysg, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(copied[s], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cst[s], copied[s], 0);
+        if (e != cudaSuccess) break;
+        gbssim_plane dx = *x, dy = *y;
+        dx.data = xs;
+        dy.data = ysg;
+        dx.count = dy.count = m;
+        dx.row_stride = dy.row_stride = H.pitch_elems;
+        dx.image_stride = dy.image_stride = H.pitch_elems * x->height;
+        MsPlan P;  // a short last chunk has fewer items: re-plan its layout (it fits the full one)
+        rc = plan_levels(&dx, p, p->scales, &P);
+        if (rc == GBSSIM_OK && P.bytes > H.ms.bytes) rc = GBSSIM_ERR_WORKSPACE;
+        if (rc == GBSSIM_OK)
+            rc = msssim_forward(&dx, &dy, p, P, ws + H.ws_off[s], score_dev + i0, nullptr, cst[s]);
+        if (rc == GBSSIM_OK) e = cudaEventRecord(consumed[s], cst[s]);
+    }
+    if (e == cudaSuccess && rc == GBSSIM_OK && stream2) {  // `stream` ends after the second compute stream
+        e = cudaEventRecord(done2, cst[1]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, done2, 0);
+    }
+    if (e == cudaSuccess && rc == GBSSIM_OK)
+        e = cudaMemcpyAsync(score_host, score_dev, sizeof(double) * (size_t)x->count, cudaMemcpyDeviceToHost, st);
+    for (auto &f : ev) cudaEventDestroy(f);  // released once the streams are past them
+    if (rc != GBSSIM_OK) return rc;
+    return e == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
 }
 
 int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,

@@ -296,9 +296,17 @@ cudaError_t launch_video_pool(const double *sY, const double *sU, const double *
                               double pct, double r, double *frame_out, double *video_out, cudaStream_t st);
 constexpr int kVideoMaxFrames = 4096;  // 32 KB of shared memory for the sort
 
-cudaError_t launch_pool_mean(const float *map, int64_t h, int64_t w, int64_t ld, int count,
-                             int64_t image_stride, double2 *partials, double *out,
-                             cudaStream_t st);
-int pool_items(int64_t h, int64_t w);
+// Pooling family on stored maps (k_poolmap.cu).
+constexpr int kPoolMaxRanks = 10;  // order statistics one call selects (five-number summary: 5 x 2)
+struct PoolLayout {
+    int items;                          // row blocks per map
+    size_t partials, center, state, hist, bytes;
+};
+PoolLayout pool_layout(int64_t h, int64_t w, int count);
+// Temporal pooling of frame-score series (k_series.cu).
+cudaError_t launch_series_pool(const double *scores, int n, int count, int64_t stride, int kind, double a0,
+                               double a1, double *out, cudaStream_t st);
+cudaError_t launch_pool_map(const float *map, int64_t h, int64_t w, int64_t ld, int count, int64_t is, int kind,
+                            double a0, double a1, char *ws, double *out, cudaStream_t st);
 
 }  // namespace gbssim

@@ -50,18 +50,6 @@ __device__ __forceinline__ void box_formula(const BoxOut &v, int k, float C1k4, 
     q = __fdividef(A1, B1) * cs;
 }
 
-// k <= 13: every integer quantity of the formula fits int32 (S2 <= 65025 k^2,
-// k^2 S2 <= 1.9e9); products of two sums are formed in fp32 (one rounding).
-__device__ __forceinline__ void box_formula32(int s1x, int s1y, int s2x, int s2y, int sxy, int kk,
-                                              float C1k4, float C2k4, float &q, float &cs) {
-    const float fx = (float)s1x, fy = (float)s1y;
-    const float A1 = fmaf(2.f * fx, fy, C1k4), B1 = fmaf(fx, fx, fmaf(fy, fy, C1k4));
-    const int nxy = kk * sxy - s1x * s1y, nxx = kk * s2x - s1x * s1x, nyy = kk * s2y - s1y * s1y;
-    const float A2 = fmaf(2.f, (float)nxy, C2k4), B2 = ((float)nxx + (float)nyy) + C2k4;
-    cs = __fdividef(A2, B2);
-    q = __fdividef(A1, B1) * cs;
-}
-
 // Same formula from the five window sums held as exact floats (integers below
 // 2^24: k <= 12 keeps S2 <= 65025 * 144).  k^2 S2 - S1^2 is formed without
 // cancellation: S1^2 = p + e exactly (p = fl(S1 S1), e = fma(S1, S1, -p),
@@ -174,7 +162,7 @@ __device__ __forceinline__ void block_sum2f(float a, float b, float *red, double
 // halo block rows of a segment are re-read, normally from L2.  Nothing goes
 // through shared memory.
 constexpr int S4C_VB = 4;                // blocks per lane
-constexpr int S4C_STAGES = 3;            // block rows in flight per warp
+constexpr int S4C_STAGES = 2;            // block rows in flight per warp
 constexpr int CW_STEP = 31 * S4C_VB;     // window columns per strip
 
 __device__ __forceinline__ float i2f_exact(int v) { return __int2float_rn(v); }  // |v| < 2^24 here
@@ -222,7 +210,7 @@ __global__ void __launch_bounds__(NT) box_s4c_kernel(const BoxLaunch L, int stri
     static_assert(S >= 2, "at least double buffering");
     using V = VecOf<VB>;
     using VT = typename V::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int MP = M > 1 ? M - 1 : 1;
     const int lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
@@ -644,7 +632,7 @@ __host__ __device__ inline int sat_tile_outputs(int k, int s) {
 }
 
 __global__ void __launch_bounds__(NT) box_sat_kernel(const BoxLaunch L, int tiles_x, int tiles_y) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     SatSmem &S = *reinterpret_cast<SatSmem *>(smem_raw);
     const int k = L.k, s = L.stride;
     const int to = sat_tile_outputs(k, s);
@@ -722,7 +710,7 @@ bool use_block_path(int k, int s) { return s % 4 == 0 && k % s == 0 && k <= 16; 
 bool use_s4_path(int k, int s) { return s == 4 && k % 4 == 0 && k <= 12 && VTOW + k / 4 - 1 <= VBW; }
 
 // Block rows (= output rows) per warp item of the column-walk kernel.
-constexpr int kS4cSeg = 8;
+constexpr int kS4cSeg = 32;
 
 enum BoxLayout { LAYOUT_S4C, LAYOUT_TMA, LAYOUT_BLOCK, LAYOUT_SAT };
 

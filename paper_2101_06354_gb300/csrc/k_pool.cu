@@ -135,26 +135,6 @@ __global__ void downsample_kernel(ImgDesc in, float *out) {
     out[img * Hh * Wh + R * Wh + C] = 0.25f * s;
 }
 
-constexpr int PT = 64;  // rows per pool item
-
-__global__ void __launch_bounds__(NT) pool_mean_kernel(const float *map, int64_t h, int64_t w,
-                                                       int64_t ld, int64_t is, int items,
-                                                       double2 *partials) {
-    __shared__ double red[2 * NT / 32];
-    const int img = blockIdx.y;
-    const int64_t r0 = (int64_t)blockIdx.x * PT;
-    const float *m = map + img * is;
-    double a = 0.0;
-    for (int64_t r = r0; r < min(r0 + PT, h); ++r) {
-        float acc = 0.f;
-        for (int64_t c = threadIdx.x; c < w; c += NT) acc += m[r * ld + c];
-        a += acc;
-    }
-    double b = 0.0;
-    block_sum2(a, b, red);
-    if (threadIdx.x == 0) partials[(int64_t)img * items + blockIdx.x] = make_double2(a, 0.0);
-}
-
 }  // namespace
 
 cudaError_t launch_finalize_ssim(const double2 *partials, int count, int items_per_image,
@@ -273,19 +253,6 @@ cudaError_t launch_downsample(const ImgDesc &in, int dtype, int count, float *ou
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
-}
-
-int pool_items(int64_t h, int64_t w) { return (int)((h + PT - 1) / PT); }
-
-cudaError_t launch_pool_mean(const float *map, int64_t h, int64_t w, int64_t ld, int count,
-                             int64_t image_stride, double2 *partials, double *out,
-                             cudaStream_t st) {
-    const int items = pool_items(h, w);
-    dim3 grid(items, count);
-    pool_mean_kernel<<<grid, NT, 0, st>>>(map, h, w, ld, image_stride, items, partials);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return launch_finalize_ssim(partials, count, items, 1.0 / ((double)h * (double)w), out, st);
 }
 
 }  // namespace gbssim

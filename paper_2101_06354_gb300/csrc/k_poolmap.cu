@@ -1,0 +1,407 @@
+// k_poolmap.cu -- the pooling family on stored SSIM maps (Section
+// "Spatio-temporal Aggregation of Quality Scores" of arXiv 2101.06354):
+// coefficient of variation, Minkowski, distortion-weighted, mean-deviation,
+// geometric / harmonic means of 1 - Q, percentiles, median, five-number
+// summary and percentile pooling of `count` float maps.
+//
+// Moment kinds: one pass (two for the kinds that need the mean first) of
+// per-item partial sums -- fp32 per element, compensated fp32 per thread,
+// fp64 across the CTA -- combined per image in a fixed order in fp64, so the
+// result is deterministic.
+//
+// Order statistics: an exact radix select on the order-preserving 32-bit key
+// of each float (sign-magnitude flipped to unsigned order), 8 bits per pass.
+// Pass 0 counts the top byte of every key; a one-warp-per-image step finds,
+// for every wanted rank, the bin that holds it; passes 1-3 count the next
+// byte of the keys inside each wanted bin.  Four reads of the map give the
+// exact k-th smallest values, the values a sort would give, so percentiles
+// interpolate between the same order statistics as a sorted list (position
+// h = p/100 (n-1), linear).  Shared-memory counts are aggregated per warp
+// (one atomic per distinct bin), since SSIM values crowd into few bins.
+#include "common.cuh"
+
+namespace gbssim {
+namespace {
+
+constexpr int NT = 256;
+constexpr int PR = 16;          // map rows per item (moment partial sums, select counts)
+constexpr int NBIN = 256;       // histogram bins per select pass (8 key bits)
+constexpr int UNR = 8;          // loads in flight per thread and row
+
+struct KSumP {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ float get() const { return s - c; }
+};
+
+__device__ __forceinline__ unsigned f2key(float f) {
+    const unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key2f(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+enum MomentOp { M_SUM = 0, M_SQDEV = 1, M_ABSDEV_P = 2, M_MINK = 3, M_DW = 4, M_LOG_D = 5, M_INV_D = 6, M_PP = 7 };
+
+// Per-element contribution (a, b) of moment op `op`; m = the image's mean
+// (or the PP threshold), p, r = arguments.
+__device__ __forceinline__ void contrib(int op, float q, float m, float p, float r, float &a, float &b) {
+    b = 0.f;
+    switch (op) {
+    case M_SUM: a = q; break;
+    case M_SQDEV: { const float d = q - m; a = d * d; } break;
+    case M_ABSDEV_P: a = powf(fabsf(q - m), p); break;
+    case M_MINK: a = powf(1.f - q, p); break;
+    case M_DW: { const float w = powf(1.f - q, p); a = w * q; b = w; } break;
+    // a zero dissimilarity is counted in b (its log / reciprocal is infinite,
+    // which a compensated sum cannot carry); any such value makes GM / HM 0
+    case M_LOG_D: { const float d = 1.f - q; a = d == 0.f ? 0.f : logf(d); b = d == 0.f ? 1.f : 0.f; } break;
+    case M_INV_D: { const float d = 1.f - q; a = d == 0.f ? 0.f : 1.f / d; b = d == 0.f ? 1.f : 0.f; } break;
+    default: a = q <= m ? q / r : q; break;  // M_PP
+    }
+}
+
+__device__ __forceinline__ void block_sum2d(double &a, double &b, double *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) {
+        red[2 * warp] = a;
+        red[2 * warp + 1] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a = b = 0.0;
+        for (int w = 0; w < NT / 32; ++w) {
+            a += red[2 * w];
+            b += red[2 * w + 1];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NT) moment_kernel(const float *map, int64_t h, int64_t w, int64_t ld, int64_t is,
+                                                    int items, int op, const double *center, float p, float r,
+                                                    double2 *partials) {
+    __shared__ double red[2 * NT / 32];
+    const int img = blockIdx.y;
+    const int64_t r0 = (int64_t)blockIdx.x * PR;
+    const float *m = map + img * is;
+    float c = 0.f;
+    if (center) {
+        // the largest float not above the (double) centre: for float q,
+        // q <= c holds exactly when q <= centre does (percentile pooling's test)
+        const double cd = center[img];
+        c = (float)cd;
+        if ((double)c > cd) c = nextafterf(c, -INFINITY);
+    }
+    KSumP sa, sb;
+    for (int64_t row = r0; row < min(r0 + PR, h); ++row) {
+        const float *rp = m + row * ld;
+        for (int64_t c0 = 0; c0 < w; c0 += UNR * NT) {
+            float v[UNR];
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {  // all loads first
+                const int64_t col = c0 + threadIdx.x + k * NT;
+                v[k] = col < w ? __ldg(rp + col) : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < UNR; ++k)
+                if (c0 + threadIdx.x + k * NT < w) {
+                    float a, b;
+                    contrib(op, v[k], c, p, r, a, b);
+                    sa.add(a);
+                    sb.add(b);
+                }
+        }
+    }
+    double da = (double)sa.get(), db = (double)sb.get();
+    block_sum2d(da, db, red);
+    if (threadIdx.x == 0) partials[(int64_t)img * items + blockIdx.x] = make_double2(da, db);
+}
+
+// One thread per image: fixed-order sum of the image's partials.
+__device__ __forceinline__ double2 image_sum(const double2 *partials, int items, int img) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < items; ++i) {
+        const double2 v = partials[(int64_t)img * items + i];
+        a += v.x;
+        b += v.y;
+    }
+    return make_double2(a, b);
+}
+
+// Finish a moment kind.  stage 0 writes the mean into `center` (kinds that
+// need a second pass); stage 1 writes the result.
+__global__ void moment_finalize_kernel(const double2 *partials, int items, int count, double n, int kind,
+                                       double p, double o, int stage, double *center, double *out) {
+    const int img = blockIdx.x * blockDim.x + threadIdx.x;
+    if (img >= count) return;
+    const double2 s = image_sum(partials, items, img);
+    if (stage == 0) {
+        center[img] = s.x / n;
+        return;
+    }
+    double v;
+    switch (kind) {
+    case GBSSIM_POOL_MEAN: v = s.x / n; break;
+    case GBSSIM_POOL_COV: v = sqrt(s.x / n) / center[img]; break;
+    case GBSSIM_POOL_MINKOWSKI: v = s.x / n; break;
+    case GBSSIM_POOL_DW: v = s.x / s.y; break;
+    case GBSSIM_POOL_MD: v = pow(pow(s.x / n, 1.0 / p), o); break;
+    case GBSSIM_POOL_GM_DSSIM: v = s.y > 0.0 ? 0.0 : exp(s.x / n); break;
+    case GBSSIM_POOL_HM_DSSIM: v = s.y > 0.0 ? 0.0 : n / s.x; break;
+    default: v = s.x / n; break;  // GBSSIM_POOL_PP
+    }
+    out[img] = v;
+}
+
+// ------------------------------------------------------------------ radix select
+
+struct SelState {
+    unsigned prefix[kPoolMaxRanks];  // key bits fixed so far (high bits), per wanted rank
+    unsigned rank[kPoolMaxRanks];    // rank still to find inside the bucket
+    unsigned uprefix[kPoolMaxRanks]; // the distinct prefixes; each value matches at most one
+    int slot[kPoolMaxRanks];         // wanted rank -> its prefix's histogram slot
+    int nt, nu;
+};
+
+// Rebuild the distinct-prefix table after the prefixes changed.
+__device__ void unique_prefixes(SelState &s) {
+    s.nu = 0;
+    for (int t = 0; t < s.nt; ++t) {
+        int u = 0;
+        while (u < s.nu && s.uprefix[u] != s.prefix[t]) ++u;
+        if (u == s.nu) s.uprefix[s.nu++] = s.prefix[t];
+        s.slot[t] = u;
+    }
+}
+
+// Pass q (0..3) counts key bits 31-8q .. 24-8q of the values whose higher
+// 8q bits equal one of the distinct wanted prefixes (pass 0: of all values,
+// into slot 0).  Each thread keeps a run-length count of its last (slot, bin)
+// and only adds to shared memory when the bin changes: neighbouring SSIM
+// values mostly share a bin, so few shared atomics contend.
+__global__ void __launch_bounds__(NT) select_hist_kernel(const float *map, int64_t h, int64_t w, int64_t ld,
+                                                         int64_t is, int pass, const SelState *st,
+                                                         unsigned *hist) {
+    __shared__ unsigned sh[kPoolMaxRanks][NBIN];
+    __shared__ unsigned up[kPoolMaxRanks];
+    const int img = blockIdx.y;
+    const int nu = pass == 0 ? 1 : st[img].nu;
+    for (int i = threadIdx.x; i < nu * NBIN; i += NT) (&sh[0][0])[i] = 0u;
+    if (threadIdx.x < nu) up[threadIdx.x] = pass == 0 ? 0u : st[img].uprefix[threadIdx.x];
+    __syncthreads();
+    const int64_t r0 = (int64_t)blockIdx.x * PR;
+    const float *m = map + img * is;
+    const int fixed = 32 - 8 * pass;  // bits above `fixed` are already known
+    unsigned run_key = 0xffffffffu, run_n = 0u;  // (slot << 8 | bin) of the current run
+    auto count = [&](unsigned key) {
+        if (key == run_key) {
+            ++run_n;
+        } else {
+            if (run_n) atomicAdd(&(&sh[0][0])[run_key], run_n);
+            run_key = key;
+            run_n = 1u;
+        }
+    };
+    for (int64_t row = r0; row < min(r0 + PR, h); ++row) {
+        const float *rp = m + row * ld;
+        for (int64_t c0 = 0; c0 < w; c0 += UNR * NT) {
+            float v[UNR];
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {
+                const int64_t col = c0 + threadIdx.x + k * NT;
+                v[k] = col < w ? __ldg(rp + col) : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {
+                if (c0 + threadIdx.x + k * NT >= w) continue;
+                const unsigned key = f2key(v[k]);
+                const unsigned bin = (key >> (fixed - 8)) & (NBIN - 1);
+                if (pass == 0) {
+                    count(bin);
+                } else {
+                    const unsigned hb = key >> fixed;
+                    for (int u = 0; u < nu; ++u)
+                        if (hb == up[u]) {
+                            count(((unsigned)u << 8) | bin);
+                            break;
+                        }
+                }
+            }
+        }
+    }
+    if (run_n) atomicAdd(&(&sh[0][0])[run_key], run_n);
+    __syncthreads();
+    unsigned *hi = hist + (int64_t)img * kPoolMaxRanks * NBIN;
+    for (int i = threadIdx.x; i < nu * NBIN; i += NT) {
+        const unsigned v = (&sh[0][0])[i];
+        if (v) atomicAdd(&hi[i], v);
+    }
+}
+
+// One warp per image: walk each wanted rank's histogram to the bin that
+// holds it; extend the prefix by that bin and keep the rank within it.
+__global__ void select_step_kernel(SelState *st, const unsigned *hist, int pass) {
+    const int img = blockIdx.x;
+    SelState &s = st[img];
+    const unsigned *hi = hist + (int64_t)img * kPoolMaxRanks * NBIN;
+    for (int t = threadIdx.x; t < s.nt; t += blockDim.x) {
+        const unsigned *hb = hi + (pass == 0 ? 0 : s.slot[t] * NBIN);
+        const unsigned want = s.rank[t];
+        unsigned acc = 0u;
+        int b = 0;
+        for (; b < NBIN - 1; ++b) {
+            if (acc + hb[b] > want) break;
+            acc += hb[b];
+        }
+        s.prefix[t] = pass == 0 ? (unsigned)b : (s.prefix[t] << 8) | (unsigned)b;
+        s.rank[t] = want - acc;
+    }
+    __syncwarp();
+    if (threadIdx.x == 0) unique_prefixes(s);
+}
+
+// Ranks of the order statistics a percentile needs: floor(h) and floor(h)+1
+// (clamped), h = p/100 (n-1).
+__host__ __device__ inline void pct_ranks(double p, double n, unsigned &lo, unsigned &hi, double &frac) {
+    const double hh = p / 100.0 * (n - 1.0);
+    const double fl = floor(hh);
+    lo = (unsigned)fl;
+    hi = (unsigned)fmin(fl + 1.0, n - 1.0);
+    frac = hh - fl;
+}
+
+__global__ void select_init_kernel(SelState *st, int count, double n, int kind, double parg) {
+    const int img = blockIdx.x * blockDim.x + threadIdx.x;
+    if (img >= count) return;
+    SelState s;
+    double ps[5];
+    int np = 0;
+    if (kind == GBSSIM_POOL_FNS) {
+        ps[0] = 0.0; ps[1] = 25.0; ps[2] = 50.0; ps[3] = 75.0; ps[4] = 100.0;
+        np = 5;
+    } else {
+        ps[0] = kind == GBSSIM_POOL_MEDIAN ? 50.0 : parg;
+        np = 1;
+    }
+    s.nt = 2 * np;
+    for (int i = 0; i < np; ++i) {
+        unsigned lo, hi;
+        double f;
+        pct_ranks(ps[i], n, lo, hi, f);
+        s.rank[2 * i] = lo;
+        s.rank[2 * i + 1] = hi;
+        s.prefix[2 * i] = s.prefix[2 * i + 1] = 0u;
+    }
+    unique_prefixes(s);
+    st[img] = s;
+}
+
+// Values of the selected order statistics -> percentile interpolation.
+// For PP the threshold goes to `center` (stage 0), else the result to `out`.
+__global__ void select_finalize_kernel(const SelState *st, int count, double n, int kind, double parg,
+                                       double *center, double *out) {
+    const int img = blockIdx.x * blockDim.x + threadIdx.x;
+    if (img >= count) return;
+    const SelState s = st[img];
+    auto pct = [&](int i, double p) {
+        unsigned lo, hi;
+        double f;
+        pct_ranks(p, n, lo, hi, f);
+        const double a = (double)key2f(s.prefix[2 * i]), b = (double)key2f(s.prefix[2 * i + 1]);
+        return a + f * (b - a);
+    };
+    if (kind == GBSSIM_POOL_FNS) {
+        out[img] = (pct(0, 0.0) + pct(1, 25.0) + pct(2, 50.0) + pct(3, 75.0) + pct(4, 100.0)) / 5.0;
+    } else if (kind == GBSSIM_POOL_PP) {
+        center[img] = pct(0, parg);
+    } else {
+        out[img] = pct(0, kind == GBSSIM_POOL_MEDIAN ? 50.0 : parg);
+    }
+}
+
+}  // namespace
+
+// Workspace: partials, per-image centre, selection state, histograms.
+PoolLayout pool_layout(int64_t h, int64_t w, int count) {
+    PoolLayout L;
+    L.items = (int)((h + PR - 1) / PR);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = (off + bytes + 255) / 256 * 256;
+        return at;
+    };
+    L.partials = take(sizeof(double2) * (size_t)L.items * count);
+    L.center = take(sizeof(double) * (size_t)count);
+    L.state = take(sizeof(SelState) * (size_t)count);
+    L.hist = take(sizeof(unsigned) * (size_t)kPoolMaxRanks * NBIN * count);
+    L.bytes = off;
+    return L;
+}
+
+cudaError_t launch_pool_map(const float *map, int64_t h, int64_t w, int64_t ld, int count, int64_t is, int kind,
+                            double a0, double a1, char *ws, double *out, cudaStream_t st) {
+    const PoolLayout L = pool_layout(h, w, count);
+    double2 *part = reinterpret_cast<double2 *>(ws + L.partials);
+    double *center = reinterpret_cast<double *>(ws + L.center);
+    SelState *sel = reinterpret_cast<SelState *>(ws + L.state);
+    unsigned *hist = reinterpret_cast<unsigned *>(ws + L.hist);
+    const double n = (double)h * (double)w;
+    const dim3 grid(L.items, count);
+    const int fb = (count + 127) / 128;
+    cudaError_t e = cudaSuccess;
+    auto moment = [&](int op, const double *c, double p, double r, int kindv, int stage) {
+        moment_kernel<<<grid, NT, 0, st>>>(map, h, w, ld, is, L.items, op, c, (float)p, (float)r, part);
+        moment_finalize_kernel<<<fb, 128, 0, st>>>(part, L.items, count, n, kindv, p, a1, stage, center, out);
+        return cudaGetLastError();
+    };
+    auto select = [&](double parg) {
+        select_init_kernel<<<fb, 128, 0, st>>>(sel, count, n, kind, parg);
+        for (int pass = 0; pass < 4; ++pass) {
+            cudaError_t r = cudaMemsetAsync(hist, 0, sizeof(unsigned) * (size_t)kPoolMaxRanks * NBIN * count, st);
+            if (r != cudaSuccess) return r;
+            select_hist_kernel<<<grid, NT, 0, st>>>(map, h, w, ld, is, pass, sel, hist);
+            select_step_kernel<<<count, 32, 0, st>>>(sel, hist, pass);
+        }
+        select_finalize_kernel<<<fb, 128, 0, st>>>(sel, count, n, kind, parg, center, out);
+        return cudaGetLastError();
+    };
+    switch (kind) {
+    case GBSSIM_POOL_MEAN: e = moment(M_SUM, nullptr, 0, 0, kind, 1); break;
+    case GBSSIM_POOL_COV:
+        e = moment(M_SUM, nullptr, 0, 0, kind, 0);
+        if (e == cudaSuccess) e = moment(M_SQDEV, center, 0, 0, kind, 1);
+        break;
+    case GBSSIM_POOL_MD:
+        e = moment(M_SUM, nullptr, 0, 0, kind, 0);
+        if (e == cudaSuccess) e = moment(M_ABSDEV_P, center, a0, 0, kind, 1);
+        break;
+    case GBSSIM_POOL_MINKOWSKI: e = moment(M_MINK, nullptr, a0, 0, kind, 1); break;
+    case GBSSIM_POOL_DW: e = moment(M_DW, nullptr, a0, 0, kind, 1); break;
+    case GBSSIM_POOL_GM_DSSIM: e = moment(M_LOG_D, nullptr, 0, 0, kind, 1); break;
+    case GBSSIM_POOL_HM_DSSIM: e = moment(M_INV_D, nullptr, 0, 0, kind, 1); break;
+    case GBSSIM_POOL_PERCENTILE:
+    case GBSSIM_POOL_MEDIAN:
+    case GBSSIM_POOL_FNS: e = select(a0); break;
+    case GBSSIM_POOL_PP:
+        e = select(a0);
+        if (e == cudaSuccess) e = moment(M_PP, center, 0, a1, kind, 1);
+        break;
+    default: e = cudaErrorInvalidValue;
+    }
+    return e;
+}
+
+}  // namespace gbssim

@@ -43,7 +43,12 @@ U8, F16, BF16, F32 = 0, 1, 2, 3
 WIN_GAUSSIAN, WIN_BOX = 0, 1
 COMBINE_PRODUCT, COMBINE_SUM = 0, 1
 OP_SSIM, OP_MSSSIM, OP_BACKWARD, OP_BACKWARD_MS, OP_POOL = 0, 1, 2, 3, 4
-POOL_MEAN = 0
+POOL_MEAN, POOL_COV, POOL_MINKOWSKI, POOL_DW, POOL_MD, POOL_GM_DSSIM, POOL_HM_DSSIM, POOL_PERCENTILE, \
+    POOL_MEDIAN, POOL_FNS, POOL_PP, POOL_GM, POOL_HM, POOL_W_AM, POOL_W_GM, POOL_W_HM, POOL_W_COV = range(17)
+POOL_KINDS = {"mean": POOL_MEAN, "cov": POOL_COV, "minkowski": POOL_MINKOWSKI, "dw": POOL_DW, "md": POOL_MD,
+              "gm_dssim": POOL_GM_DSSIM, "hm_dssim": POOL_HM_DSSIM, "percentile": POOL_PERCENTILE,
+              "median": POOL_MEDIAN, "fns": POOL_FNS, "pp": POOL_PP, "gm": POOL_GM, "hm": POOL_HM,
+              "w_am": POOL_W_AM, "w_gm": POOL_W_GM, "w_hm": POOL_W_HM, "w_cov": POOL_W_COV}
 FLAG_BOX_TMA = 1
 
 
@@ -93,6 +98,9 @@ _SIGS = {
     "gbssim_batch_free": ([_vp], None),
     "gbssim_ssim_backward": ([_P(Plane), _P(Plane), _P(Params), _i32, ctypes.c_double, _vp, _i32, _vp, _vp, _vp,
                               _i32, _i64, _i64, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "gbssim_msssim_host_workspace_size": ([_P(Plane), _P(Params), _i32, _P(_sz)], ctypes.c_int),
+    "gbssim_series_pool": ([_vp, _i32, _i32, _i64, _i32, _vp, _vp, _vp], ctypes.c_int),
+    "gbssim_msssim_host": ([_P(Plane), _P(Plane), _P(Params), _i32, _vp, _vp, _sz, _vp, _vp, _vp], ctypes.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -238,9 +246,68 @@ def ssim_static(x: torch.Tensor, y: torch.Tensor, return_map: bool = False, **kw
     return (mean, mp) if return_map else mean
 
 
+_side_streams = {}
+
+
+def _copy_stream(dev, which: int = 0) -> torch.cuda.Stream:
+    """Side streams of the host pipeline (0: copies, 1: second compute stream)."""
+    key = (dev, which)
+    if key not in _side_streams:
+        _side_streams[key] = torch.cuda.Stream(device=dev)
+    return _side_streams[key]
+
+
+def host_workspace(x: torch.Tensor, chunks: int, **kw) -> torch.Tensor:
+    """Device workspace for msssim_host on host planes shaped like x."""
+    kw.setdefault("exponents", MSSSIM_EXPONENTS[: kw.get("scales", 5)])
+    p = make_params(**kw)
+    px = plane(_as_batch(x))
+    nb = ctypes.c_size_t()
+    _check(lib.gbssim_msssim_host_workspace_size(ctypes.byref(px), ctypes.byref(p), int(chunks), ctypes.byref(nb)),
+           "gbssim_msssim_host_workspace_size")
+    return torch.empty(max(int(nb.value), 1), dtype=torch.uint8, device=torch.device("cuda", torch.cuda.current_device()))
+
+
+def msssim_host(x: torch.Tensor, y: torch.Tensor, chunks: int = 4, ws: torch.Tensor = None,
+                out: torch.Tensor = None, sync: bool = True, two_compute_streams: bool = True,
+                **kw) -> torch.Tensor:
+    """MS-SSIM of pairs held in host memory (gbssim_msssim_host): chunks of
+    the batch are copied on a side stream while the previous chunk is scored
+    on the current stream.  Returns a pinned CPU float64 tensor of length N,
+    valid at return when sync=True (else once the current stream completes).
+    x and y should be pinned for the copies to overlap."""
+    if x.device.type != "cpu" or y.device.type != "cpu":
+        raise ValueError("msssim_host takes host tensors")
+    if y.dtype != x.dtype or y.shape != x.shape:
+        raise ValueError("x and y must share dtype and shape")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    xb, yb = _as_batch(x), _as_batch(y)
+    if xb.stride() != yb.stride():
+        xb, yb = xb.contiguous(), yb.contiguous()
+    kw.setdefault("exponents", MSSSIM_EXPONENTS[: kw.get("scales", 5)])
+    p = make_params(**kw)
+    px, py = plane(xb), plane(yb)
+    n = xb.shape[0]
+    if ws is None:
+        ws = host_workspace(xb, chunks, **kw)
+    if out is None:
+        out = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    cs, s2 = _copy_stream(dev, 0), _copy_stream(dev, 1)
+    _check(lib.gbssim_msssim_host(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p), int(chunks), out.data_ptr(),
+                                  ws.data_ptr(), ws.numel(), _stream(dev), cs.cuda_stream,
+                                  s2.cuda_stream if two_compute_streams else None), "gbssim_msssim_host")
+    if sync:
+        torch.cuda.current_stream(dev).synchronize()
+    return out
+
+
 def msssim(x: torch.Tensor, y: torch.Tensor, per_scale: bool = False, ws: torch.Tensor = None, **kw):
     """MS-SSIM of each pair (float64 tensor of length N); with per_scale=True
-    also the (N, scales, 2) tensor of (mean cs_j, mean Q_j)."""
+    also the (N, scales, 2) tensor of (mean cs_j, mean Q_j).  Host tensors go
+    through msssim_host (copies overlapped with compute) unless per_scale is
+    asked for."""
+    if x.device.type == "cpu" and y.device.type == "cpu" and not per_scale:
+        return msssim_host(x, y, **kw)
     host, dev, xb, yb = _prepare(x, y)
     kw.setdefault("exponents", MSSSIM_EXPONENTS[: kw.get("scales", 5)])
     p = make_params(**kw)
@@ -271,19 +338,38 @@ def window_sums(x: torch.Tensor, y: torch.Tensor, k: int, stride: int = 1, flags
     return out.cpu() if host else out
 
 
-def ssim_pool(qmap: torch.Tensor, kind: str = "mean") -> torch.Tensor:
-    """Pool float maps (H, W) or (N, H, W) into one double each."""
+def ssim_pool(qmap: torch.Tensor, kind: str = "mean", *args: float, ws: torch.Tensor = None) -> torch.Tensor:
+    """Pool float maps (H, W) or (N, H, W) into one double each.  kind is a
+    key of POOL_KINDS; args are its parameters: minkowski / dw (p),
+    md (p, o), percentile (p), pp (p, r)."""
     m = qmap if qmap.dim() == 3 else qmap.unsqueeze(0)
     if m.dtype != torch.float32 or m.stride(-1) != 1:
         raise TypeError("expected float32 maps with unit column stride")
     n, h, w = m.shape
     dev = m.device
     px = Plane(m.data_ptr(), F32, n, h, w, m.stride(1), m.stride(0) if n > 1 else h * m.stride(1))
-    ws = workspace(px, Params(), OP_POOL, dev)
+    if ws is None:
+        ws = workspace(px, Params(), OP_POOL, dev)
     out = torch.empty(n, dtype=torch.float64, device=dev)
-    _check(lib.gbssim_ssim_pool(m.data_ptr(), h, w, m.stride(1), n, px.image_stride,
-                                {"mean": POOL_MEAN}[kind], None, out.data_ptr(), ws.data_ptr(),
-                                ws.numel(), _stream(dev)), "gbssim_ssim_pool")
+    a = (ctypes.c_double * 2)(*(list(map(float, args)) + [0.0, 0.0])[:2]) if args else None
+    _check(lib.gbssim_ssim_pool(m.data_ptr(), h, w, m.stride(1), n, px.image_stride, POOL_KINDS[kind], a,
+                                out.data_ptr(), ws.data_ptr(), ws.numel(), _stream(dev)), "gbssim_ssim_pool")
+    return out
+
+
+def series_pool(scores: torch.Tensor, kind: str = "mean", *args: float) -> torch.Tensor:
+    """Temporal pooling (gbssim_series_pool) of frame-score series (T,) or
+    (N, T) on the GPU into one double each.  kind is a key of POOL_KINDS;
+    args as for ssim_pool, and k for the windowed kinds w_am, w_gm, w_hm,
+    w_cov."""
+    s = scores if scores.dim() == 2 else scores.unsqueeze(0)
+    if s.dtype != torch.float64 or s.device.type != "cuda" or s.stride(-1) != 1:
+        raise TypeError("expected float64 CUDA series with unit stride")
+    n_series, t = s.shape
+    out = torch.empty(n_series, dtype=torch.float64, device=s.device)
+    a = (ctypes.c_double * 2)(*(list(map(float, args)) + [0.0, 0.0])[:2]) if args else None
+    _check(lib.gbssim_series_pool(s.data_ptr(), t, n_series, s.stride(0) if n_series > 1 else t, POOL_KINDS[kind], a,
+                                  out.data_ptr(), _stream(s.device)), "gbssim_series_pool")
     return out
 
 

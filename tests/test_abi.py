@@ -137,7 +137,21 @@ def test_pool_validation(g):
     assert g.lib.gbssim_ssim_pool(m, 10, 10, 5, 1, 0, 0, None, ctypes.c_void_p(0x10), ctypes.c_void_p(0x20),
                                   1 << 20, None) == g.ERR_INVALID_ARG  # ld < w
     assert g.lib.gbssim_ssim_pool(m, 10, 10, 10, 1, 0, 42, None, ctypes.c_void_p(0x10), ctypes.c_void_p(0x20),
-                                  1 << 20, None) == g.ERR_UNSUPPORTED
+                                  1 << 20, None) == g.ERR_INVALID_ARG  # unknown kind
+
+    def pool(kind, args, ws_bytes=1 << 20):
+        a = (ctypes.c_double * 2)(*args) if args is not None else None
+        return g.lib.gbssim_ssim_pool(m, 10, 10, 10, 1, 0, kind, a, ctypes.c_void_p(0x10), ctypes.c_void_p(0x20),
+                                      ws_bytes, None)
+
+    assert pool(g.POOL_MINKOWSKI, None) == g.ERR_INVALID_ARG       # p missing
+    assert pool(g.POOL_DW, (-1.0, 0.0)) == g.ERR_INVALID_ARG       # p < 0
+    assert pool(g.POOL_MD, (0.0, 1.0)) == g.ERR_INVALID_ARG        # p must be > 0
+    assert pool(g.POOL_PERCENTILE, (101.0, 0.0)) == g.ERR_INVALID_ARG
+    assert pool(g.POOL_PP, (10.0, 0.0)) == g.ERR_INVALID_ARG       # r must be > 0
+    assert pool(g.POOL_PP, (float("nan"), 4.0)) == g.ERR_INVALID_ARG
+    for kind in (g.POOL_COV, g.POOL_FNS, g.POOL_MEDIAN):
+        assert pool(kind, None, ws_bytes=16) == g.ERR_WORKSPACE    # checked before any launch
 
 
 def test_batch_plan_validation_on_host(g):
