@@ -46,9 +46,9 @@ LAUNCHES_PER_STEP = 2
 E2E_CHUNKS = 4
 # DRAM bytes (read + write) of one persistent launch on this workload, from the
 # ncu capture summarised in profiles/gauss11_msssim_1080p_x64.md; valid only for
-# the kernel sources it was taken on (sha256 of the files below, first 16 hex).
-TRAFFIC = {"bytes": None, "sources_sha": None}
-TRAFFIC_SOURCES = ("paper_2101_06354_gb300/csrc/k_gauss.cu", "paper_2101_06354_gb300/csrc/common.cuh")
+# the kernel source it was taken on (sha256 of the file below, first 16 hex).
+TRAFFIC = {"bytes": 597.10e6 + 336.19e6, "sources_sha": "358c03e140b31421"}
+TRAFFIC_SOURCES = ("paper_2101_06354_gb300/csrc/k_gauss.cu",)
 
 
 def _sources_sha():
@@ -283,6 +283,17 @@ def run_extras(args, gbssim, synth, x, y, dev, timed, ws):
     fr, ps, vid = gbssim.video_ssim(vx, vy)
     out["video_yuv420_4k"] = {"value": ws * vpx / (t / 1e3) / 1e6, "unit": UNIT, "ms_per_video": t,
                               "frames": 120, "mean": vid[0].item(), "p10": vid[1].item(), "pp": vid[2].item()}
+    # SSIM-3D (11 x 11 x 5 rectangular windows, exact integer sums) on the
+    # 120 luma frames of the same video
+    v3x, v3y = vx[0].contiguous(), vy[0].contiguous()
+    fn3 = lambda: gbssim.ssim3d(v3x, v3y, kt=5, k=11)
+    fn3()
+    t3 = timed(fn3, kk) / kk
+    px3 = 120 * 3840 * 2160
+    s3, _ = fn3()
+    out["ssim3d_4k_y"] = {"value": ws * px3 / (t3 / 1e3) / 1e6, "unit": UNIT, "ms_per_video": t3, "frames": 120,
+                          "kt": 5, "k": 11, "hbm_gbs": 2 * px3 / (t3 / 1e3) / 1e9,
+                          "hbm_frac": 2 * px3 / (t3 / 1e3) / 1e9 / hbm_peak, "score": s3.item()}
     del v, vx, vy
     return out
 
@@ -407,6 +418,53 @@ def run_gbssim(args):
         dist.destroy_process_group()
 
 
+def run_case(args):
+    """One of the bench's secondary workloads alone, `warmup` + `steps` calls,
+    for profilers: scale0 = gbssim_ssim_map on the 64 1080p pairs (the
+    scale-0 Gaussian level); box8s4 = the 8x8 stride-4 box SSIM on them;
+    loss = SSIMLoss forward + backward on 32x3x512x512 fp32; ssim3d = SSIM-3D
+    (11 x 11 x 5) of 40 luma frames of 1920x1080.  Prints one JSON
+    line with the mean time per call (CUDA events)."""
+    import torch
+
+    from paper_2101_06354_gb300 import build
+
+    build.build()
+    from paper_2101_06354_gb300 import gbssim, synth
+
+    dev = torch.device("cuda", 0)
+    if args.case in ("scale0", "box8s4"):
+        x, y = synth.luma_pairs_u8(N_PAIRS, H, W)
+        x, y = x.to(dev), y.to(dev)
+        kw = {} if args.case == "scale0" else dict(window="box", k=8, stride=4)
+        wsc = gbssim.workspace(gbssim.plane(x), gbssim.make_params(**kw), gbssim.OP_SSIM, dev)
+        fn = lambda: gbssim.ssim(x, y, ws=wsc, **kw)
+    elif args.case == "ssim3d":
+        v = synth.video_yuv420_u8(40, H, W)
+        vx, vy = v["y"][0].contiguous().to(dev), v["y"][1].contiguous().to(dev)
+        fn = lambda: gbssim.ssim3d(vx, vy, kt=5, k=11)
+    else:
+        lx, ly = synth.loss_pairs_float(32, 3, 512, 512)
+        xd, yd = lx.to(dev), ly.to(dev).requires_grad_(True)
+        lf = gbssim.SSIMLoss(L=1.0)
+
+        def fn():
+            yd.grad = None
+            lf(xd, yd).backward()
+
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_call": e0.elapsed_time(e1) / max(args.steps, 1)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -415,7 +473,12 @@ def main():
     ap.add_argument("--impl", default="gbssim", choices=["gbssim", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the box-window and loss fwd+bwd figures")
+    ap.add_argument("--case", choices=["scale0", "box8s4", "loss", "ssim3d"], default=None,
+                    help="run one secondary workload alone (for profilers) instead of the benchmark")
     args = ap.parse_args()
+    if args.case:
+        run_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

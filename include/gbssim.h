@@ -194,6 +194,29 @@ int gbssim_ssim_pool(const float *map, int64_t h, int64_t w, int64_t ld, int32_t
 int gbssim_series_pool(const double *scores, int32_t n, int32_t count, int64_t stride, int32_t kind,
                        const double *args, double *out, void *stream);
 
+/* SSIM-3D of a uint8 video pair (Section "Spatio-Temporal SSIM"): SSIM whose
+ * local statistics (mean, variance, covariance) are taken over k x k x kt
+ * rectangular spatio-temporal neighbourhoods instead of k x k ones.  The
+ * window of output frame t covers input frames t .. t+kt-1 (the window
+ * ending at frame t+kt-1); like the spatial map, only windows inside the
+ * video count, so there are T-kt+1 output frames of (H-k+1) x (W-k+1)
+ * positions.  The window sums are exact integers (int32, int64 numerators).
+ *   x, y       : the T frames as a batch (count = T, image_stride = frame stride).
+ *   p          : window = GBSSIM_WIN_BOX, k <= 31, stride 1; K1, K2, L as usual.
+ *   kt         : frames per window, 1 <= kt <= T, k^2 kt 255^2 < 2^31.
+ *   frame_out  : nullable; T-kt+1 doubles, the mean Q of each output frame.
+ *   score_out  : nullable; one double, the mean over all output frames.
+ *   map_out    : nullable; Q of output frame t at map_out + t*map_frame_stride,
+ *                rows map_ld floats apart.
+ *   workspace  : gbssim_ssim3d_workspace_size bytes.
+ * Errors: GBSSIM_ERR_UNSUPPORTED for other dtypes, windows, strides or sizes
+ * past the exact-integer range; GBSSIM_ERR_TOO_SMALL if T < kt or a frame is
+ * smaller than k. */
+int gbssim_ssim3d_workspace_size(const gbssim_plane *x, const gbssim_params *p, int32_t kt, size_t *bytes);
+int gbssim_ssim3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t kt,
+                  double *frame_out, double *score_out, float *map_out, int64_t map_ld, int64_t map_frame_stride,
+                  void *workspace, size_t workspace_bytes, void *stream);
+
 /* MS-SSIM of each pair (Introduction; Section "Salient Features of SSIM and
  * MS-SSIM Implementations"): scale 1 is the input, scale j+1 the 2x2 average
  * of scale j (floor size); the contrast-structure term is mean-pooled at every

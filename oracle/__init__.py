@@ -50,6 +50,8 @@ def _load():
         lib.oracle_box_sums_direct.argtypes = [_u8p, _u8p, L, L, L, I, I, _i64p]
         lib.oracle_box_sums_integral.argtypes = [_u8p, _u8p, L, L, L, I, I, _i64p]
         lib.oracle_box_ssim_from_sums.argtypes = [_i64p, L, I, D, D, _dp, _dp]
+        lib.oracle_box3d_sums_direct.argtypes = [_u8p, _u8p, L, L, L, L, L, I, I, _i64p]
+        lib.oracle_box_ssim_from_sums_n.argtypes = [_i64p, L, D, D, D, _dp, _dp]
         lib.oracle_downsample2x2.argtypes = [_dp, L, L, _dp]
         lib.oracle_ssim_grad.argtypes = [_dp, _dp, L, L, _dp, I, I, D, D, I, _dp]
         lib.oracle_num_threads.restype = I
@@ -201,6 +203,38 @@ def box_ssim(x, y, k: int = 8, stride: int = 4, K1: float = 0.01, K2: float = 0.
     cs = np.empty(sums.shape[:2], np.float64)
     _check(_load().oracle_box_ssim_from_sums(_ptr(sums, _i64p), n, k, C1, C2, _ptr(q), _ptr(cs)))
     return mean(q), q, cs, sums
+
+
+def box3d_sums(x, y, k: int = 11, kt: int = 5) -> np.ndarray:
+    """SSIM-3D window sums (Section "Spatio-Temporal SSIM"): the five exact
+    int64 sums of every k x k x kt neighbourhood of a uint8 video pair
+    (T, H, W), shape (T-kt+1, H-k+1, W-k+1, 5); output frame t covers input
+    frames t .. t+kt-1 (the window ending at frame t+kt-1)."""
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    y = np.ascontiguousarray(y, dtype=np.uint8)
+    T, H, W = x.shape
+    if y.shape != x.shape or T < kt or H < k or W < k or k < 1 or kt < 1:
+        raise ValueError("bad shapes")
+    out = np.empty((T - kt + 1, H - k + 1, W - k + 1, 5), np.int64)
+    _check(_load().oracle_box3d_sums_direct(_ptr(x, _u8p), _ptr(y, _u8p), T, H, W, W, H * W, k, kt,
+                                            _ptr(out, _i64p)))
+    return out
+
+
+def ssim3d(x, y, k: int = 11, kt: int = 5, K1: float = 0.01, K2: float = 0.03, L: float = 255.0):
+    """SSIM-3D of a uint8 video pair (T, H, W) (Section "Spatio-Temporal
+    SSIM"): SSIM whose local statistics are taken over k x k x kt rectangular
+    spatio-temporal neighbourhoods.  Reading: like the spatial map, only
+    windows inside the video count, so output frames are the T-kt+1 frames
+    with a full temporal window.  Returns (video score, per-frame mean Q of
+    the T-kt+1 output frames, Q maps)."""
+    C1, C2 = constants(K1, K2, L)
+    sums = box3d_sums(x, y, k, kt)
+    n = sums.shape[0] * sums.shape[1] * sums.shape[2]
+    q = np.empty(sums.shape[:3], np.float64)
+    _check(_load().oracle_box_ssim_from_sums_n(_ptr(sums, _i64p), n, float(k * k * kt), C1, C2, _ptr(q), None))
+    frames = np.array([mean(q[t]) for t in range(q.shape[0])])
+    return float(frames.sum() / frames.size), frames, q
 
 
 def downsample2x2(img) -> np.ndarray:

@@ -195,6 +195,60 @@ int oracle_box_sums_integral(const uint8_t *x, const uint8_t *y, long H, long W,
 /* Statistics from local sums, Eqs. mean_from_sum .. corr_from_sum:
  *   mu = S/k^2,  var = S2/k^2 - mu^2,  cov = S12/k^2 - mu1 mu2,
  * then the SSIM terms as in oracle_ssim_terms.  q / cs may be NULL. */
+/* SSIM-3D window sums (Section "Spatio-Temporal SSIM"): the five sums of the
+ * k x k x Kt rectangular neighbourhood over frames t .. t+Kt-1 (the window
+ * ending at frame t+Kt-1), for every valid spatial position and every
+ * t = 0 .. T-Kt.  Direct summation.  Frames are `frame_stride` bytes apart,
+ * rows `pitch` bytes.  Output: int64[(T-Kt+1) * OH * OW * 5], frame-major. */
+int oracle_box3d_sums_direct(const uint8_t *x, const uint8_t *y, long T, long H, long W, long pitch,
+                             long frame_stride, int k, int kt, int64_t *out)
+{
+    if (!x || !y || !out || k < 1 || kt < 1 || T < kt || H < k || W < k || pitch < W ||
+        frame_stride < H * pitch) return ORACLE_BAD_ARG;
+    long OH = H - k + 1, OW = W - k + 1, OT = T - kt + 1;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long ta = 0; ta < OT * OH; ++ta) {
+        long t = ta / OH, a = ta % OH;
+        for (long b = 0; b < OW; ++b) {
+            int64_t v[5] = {0, 0, 0, 0, 0};
+            for (int o = 0; o < kt; ++o)
+                for (int m = 0; m < k; ++m)
+                    for (int n = 0; n < k; ++n) {
+                        long at = (t + o) * frame_stride + (a + m) * pitch + b + n;
+                        int64_t p = x[at], q = y[at];
+                        v[0] += p;
+                        v[1] += q;
+                        v[2] += p * p;
+                        v[3] += q * q;
+                        v[4] += p * q;
+                    }
+            memcpy(out + 5 * ((t * OH + a) * OW + b), v, sizeof v);
+        }
+    }
+    return ORACLE_OK;
+}
+
+/* Q and cs from window sums over windows of `count` pixels (the local
+ * statistics of Eqs. mean_from_sum .. corr_from_sum with the window size
+ * k^2 replaced by the number of pixels in the neighbourhood). */
+int oracle_box_ssim_from_sums_n(const int64_t *sums, long n, double count, double C1, double C2,
+                                double *q, double *cs)
+{
+    if (!sums || !(count > 0.0) || n < 0) return ORACLE_BAD_ARG;
+    for (long o = 0; o < n; ++o) {
+        const int64_t *t = sums + 5 * o;
+        double mu1 = (double)t[0] / count, mu2 = (double)t[1] / count;
+        double var1 = (double)t[2] / count - mu1 * mu1;
+        double var2 = (double)t[3] / count - mu2 * mu2;
+        double cov = (double)t[4] / count - mu1 * mu2;
+        double l = (2.0 * mu1 * mu2 + C1) / (mu1 * mu1 + mu2 * mu2 + C1);
+        double c = (2.0 * cov + C2) / (var1 + var2 + C2);
+        if (q) q[o] = l * c;
+        if (cs) cs[o] = c;
+    }
+    return ORACLE_OK;
+}
+
 int oracle_box_ssim_from_sums(const int64_t *sums, long n, int k, double C1, double C2,
                               double *q, double *cs)
 {

@@ -663,6 +663,65 @@ int gbssim_series_pool(const double *scores, int32_t n, int32_t count, int64_t s
     return e == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
 }
 
+namespace {
+int check_ssim3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t kt) {
+    int rc = check_pair(x, y);
+    if (rc) return rc;
+    rc = check_params(p);
+    if (rc) return rc;
+    if (x->dtype != GBSSIM_U8 || p->window != GBSSIM_WIN_BOX || p->stride != 1 || p->k > kSsim3dMaxK)
+        return GBSSIM_ERR_UNSUPPORTED;
+    if (kt < 1) return GBSSIM_ERR_INVALID_ARG;
+    if (x->count < kt || x->height < p->k || x->width < p->k) return GBSSIM_ERR_TOO_SMALL;
+    // exact int32 window sums: k^2 kt 255^2 < 2^31
+    if ((double)p->k * p->k * kt * 65025.0 >= 2147483648.0) return GBSSIM_ERR_UNSUPPORTED;
+    return GBSSIM_OK;
+}
+
+size_t ssim3d_ws_bytes(const gbssim_plane *x, const gbssim_params *p, int32_t kt) {
+    int tx, ty;
+    ssim3d_tiles(x->height, x->width, p->k, &tx, &ty);
+    return align_up(sizeof(double) * (size_t)(x->count - kt + 1) * tx * ty);
+}
+}  // namespace
+
+int gbssim_ssim3d_workspace_size(const gbssim_plane *x, const gbssim_params *p, int32_t kt, size_t *bytes) {
+    const int rc = check_ssim3d(x, x, p, kt);
+    if (rc) return rc;
+    if (!bytes) return GBSSIM_ERR_INVALID_ARG;
+    *bytes = ssim3d_ws_bytes(x, p, kt);
+    return GBSSIM_OK;
+}
+
+int gbssim_ssim3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t kt,
+                  double *frame_out, double *score_out, float *map_out, int64_t map_ld, int64_t map_frame_stride,
+                  void *workspace, size_t workspace_bytes, void *stream) {
+    int rc = check_ssim3d(x, y, p, kt);
+    if (rc) return rc;
+    const int64_t OH = x->height - p->k + 1, OW = x->width - p->k + 1;
+    if (!frame_out && !score_out && !map_out) return GBSSIM_ERR_INVALID_ARG;
+    if (map_out && (map_ld < OW || map_frame_stride < OH * map_ld)) return GBSSIM_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < ssim3d_ws_bytes(x, p, kt)) return GBSSIM_ERR_WORKSPACE;
+    Ssim3dLaunch L;
+    L.x = desc_of(x);
+    L.y = desc_of(y);
+    L.T = x->count;
+    L.k = p->k;
+    L.kt = kt;
+    L.map = map_out;
+    L.map_ld = map_ld;
+    L.map_fs = map_frame_stride;
+    L.partials = (double *)workspace;
+    L.vec4 = (uintptr_t)x->data % 4 == 0 && (uintptr_t)y->data % 4 == 0 && L.x.row_stride % 4 == 0 &&
+             L.x.image_stride % 4 == 0;
+    const double n = (double)p->k * p->k * kt;
+    const double c1 = (p->K1 * p->L) * (p->K1 * p->L), c2 = (p->K2 * p->L) * (p->K2 * p->L);
+    L.C1n2 = (float)(c1 * n * n);
+    L.C2n2 = (float)(c2 * n * n);
+    const cudaError_t e = launch_ssim3d(L, frame_out, score_out, (cudaStream_t)stream);
+    return e == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
+}
+
 int gbssim_msssim(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
                   double *score_out, double *per_scale_out, void *workspace,
                   size_t workspace_bytes, void *stream) {

@@ -303,6 +303,20 @@ struct PoolLayout {
     size_t partials, center, state, hist, bytes;
 };
 PoolLayout pool_layout(int64_t h, int64_t w, int count);
+// SSIM-3D (k_ssim3d.cu): uint8 video pair, k x k x kt rectangular windows.
+constexpr int kSsim3dMaxK = 31;
+struct Ssim3dLaunch {
+    ImgDesc x, y;          // frames as images: count = T, image_stride = frame stride
+    int T, k, kt;
+    float *map;            // nullable: (T-kt+1) maps, frames map_fs floats apart, rows map_ld
+    int64_t map_ld, map_fs;
+    double *partials;      // (T-kt+1) x tiles
+    float C1n2, C2n2;      // C1 N^2, C2 N^2 with N = k^2 kt
+    bool vec4;             // data, row and frame strides 4-byte aligned (word loads)
+};
+void ssim3d_tiles(int64_t H, int64_t W, int k, int *tx, int *ty);
+cudaError_t launch_ssim3d(const Ssim3dLaunch &L, double *frame_out, double *score_out, cudaStream_t st);
+
 // Temporal pooling of frame-score series (k_series.cu).
 cudaError_t launch_series_pool(const double *scores, int n, int count, int64_t stride, int kind, double a0,
                                double a1, double *out, cudaStream_t st);

@@ -234,6 +234,19 @@ __global__ void __launch_bounds__(NT, 3) grad11_kernel(const GradLaunch L, int s
         {
             const int base = GCH * c + 4 * grp;
             const int b0 = base & (GRING - 1);
+            // this chunk's x, y (and coarse-level) values, loaded before the
+            // vertical pass so their latency overlaps its arithmetic
+            float xv[4], yv[4], cv[4];
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                const int64_t q = q0 + base + o;
+                xv[o] = yv[o] = cv[o] = 0.f;
+                if (qc < W && q < qend) {
+                    xv[o] = load_f32<T>(xb + q * L.x.row_stride + qc);
+                    yv[o] = load_f32<T>(yb + q * L.y.row_stride + qc);
+                    if (coarse && (q >> 1) < Hh && (qc >> 1) < Wh) cv[o] = coarse[(q >> 1) * Wh + (qc >> 1)];
+                }
+            }
             float acc[3][4];
 #pragma unroll
             for (int m = 0; m < 3; ++m)
@@ -259,11 +272,8 @@ __global__ void __launch_bounds__(NT, 3) grad11_kernel(const GradLaunch L, int s
                 for (int o = 0; o < 4; ++o) {
                     const int64_t q = q0 + base + o;
                     if (q >= qend) break;
-                    const float xv = load_f32<T>(xb + q * L.x.row_stride + qc);
-                    const float yv = load_f32<T>(yb + q * L.y.row_stride + qc);
-                    float gval = f * fmaf(yv - L.sy, acc[1][o], fmaf(xv - L.sx, acc[2][o], acc[0][o]));
-                    if (coarse && (q >> 1) < Hh && (qc >> 1) < Wh)
-                        gval = fmaf(0.25f, coarse[(q >> 1) * Wh + (qc >> 1)], gval);
+                    float gval = f * fmaf(yv[o] - L.sy, acc[1][o], fmaf(xv[o] - L.sx, acc[2][o], acc[0][o]));
+                    if (coarse) gval = fmaf(0.25f, cv[o], gval);  // 0 outside the coarse level
                     store_grad<G>(L.out, img * L.out_is + q * L.out_ld + qc, gval);
                 }
             }

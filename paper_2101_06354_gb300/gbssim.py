@@ -100,6 +100,9 @@ _SIGS = {
                               _i32, _i64, _i64, _vp, _vp, _sz, _vp], ctypes.c_int),
     "gbssim_msssim_host_workspace_size": ([_P(Plane), _P(Params), _i32, _P(_sz)], ctypes.c_int),
     "gbssim_series_pool": ([_vp, _i32, _i32, _i64, _i32, _vp, _vp, _vp], ctypes.c_int),
+    "gbssim_ssim3d_workspace_size": ([_P(Plane), _P(Params), _i32, _P(_sz)], ctypes.c_int),
+    "gbssim_ssim3d": ([_P(Plane), _P(Plane), _P(Params), _i32, _vp, _vp, _vp, _i64, _i64, _vp, _sz, _vp],
+                      ctypes.c_int),
     "gbssim_msssim_host": ([_P(Plane), _P(Plane), _P(Params), _i32, _vp, _vp, _sz, _vp, _vp, _vp], ctypes.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -269,7 +272,7 @@ def host_workspace(x: torch.Tensor, chunks: int, **kw) -> torch.Tensor:
 
 
 def msssim_host(x: torch.Tensor, y: torch.Tensor, chunks: int = 4, ws: torch.Tensor = None,
-                out: torch.Tensor = None, sync: bool = True, two_compute_streams: bool = True,
+                out: torch.Tensor = None, sync: bool = True, two_compute_streams: bool = False,
                 **kw) -> torch.Tensor:
     """MS-SSIM of pairs held in host memory (gbssim_msssim_host): chunks of
     the batch are copied on a side stream while the previous chunk is scored
@@ -371,6 +374,32 @@ def series_pool(scores: torch.Tensor, kind: str = "mean", *args: float) -> torch
     _check(lib.gbssim_series_pool(s.data_ptr(), t, n_series, s.stride(0) if n_series > 1 else t, POOL_KINDS[kind], a,
                                   out.data_ptr(), _stream(s.device)), "gbssim_series_pool")
     return out
+
+
+def ssim3d(x: torch.Tensor, y: torch.Tensor, kt: int = 5, k: int = 11, return_map: bool = False,
+           ws: torch.Tensor = None, **kw):
+    """SSIM-3D (gbssim_ssim3d) of a uint8 video pair (T, H, W): k x k x kt
+    rectangular windows.  Returns (video score, per-frame scores of the T-kt+1
+    output frames[, maps])."""
+    if x.dtype != torch.uint8 or x.dim() != 3 or y.shape != x.shape or y.dtype != x.dtype:
+        raise ValueError("expected two uint8 videos (T, H, W) of one shape")
+    dev = x.device
+    xb, yb = x.contiguous(), y.contiguous()
+    p = make_params(window="box", k=k, **kw)
+    px, py = plane(xb), plane(yb)
+    T, H, W = x.shape
+    if ws is None:
+        nb = ctypes.c_size_t()
+        _check(lib.gbssim_ssim3d_workspace_size(ctypes.byref(px), ctypes.byref(p), int(kt), ctypes.byref(nb)),
+               "gbssim_ssim3d_workspace_size")
+        ws = torch.empty(max(int(nb.value), 1), dtype=torch.uint8, device=dev)
+    frames = torch.empty(T - kt + 1, dtype=torch.float64, device=dev)
+    score = torch.empty(1, dtype=torch.float64, device=dev)
+    qmap = torch.empty((T - kt + 1, H - k + 1, W - k + 1), dtype=torch.float32, device=dev) if return_map else None
+    _check(lib.gbssim_ssim3d(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p), int(kt), frames.data_ptr(),
+                             score.data_ptr(), qmap.data_ptr() if return_map else None, W - k + 1,
+                             (H - k + 1) * (W - k + 1), ws.data_ptr(), ws.numel(), _stream(dev)), "gbssim_ssim3d")
+    return (score[0], frames, qmap) if return_map else (score[0], frames)
 
 
 _GDT = {torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}

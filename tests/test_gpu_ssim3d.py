@@ -1,0 +1,79 @@
+"""GPU parity of SSIM-3D (gbssim_ssim3d, Section "Spatio-Temporal SSIM")
+against the FP64 oracle's direct k x k x kt window sums.  The GPU window sums
+are exact integers, so only the final fp32 formula rounds: maps within 1e-5
+per element, frame and video means within 1e-6."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2101_06354_gb300 import build
+
+    build.build()
+    from paper_2101_06354_gb300 import gbssim
+
+    return gbssim
+
+
+def _video(T, H, W, seed=0):
+    from paper_2101_06354_gb300 import synth
+
+    v = synth.video_yuv420_u8(T, H, W, seeds=(seed, seed + 1, seed + 2))
+    return v["y"][0].contiguous(), v["y"][1].contiguous()
+
+
+@pytest.mark.parametrize("T,H,W,k,kt", [(9, 40, 70, 11, 5), (6, 33, 150, 5, 3), (4, 26, 64, 11, 1),
+                                        (12, 20, 21, 3, 12), (7, 80, 129, 8, 4)])
+def test_ssim3d_matches_oracle(g, T, H, W, k, kt):
+    x, y = _video(T, H, W, seed=T + k)
+    score, frames, q = g.ssim3d(x.to(DEV), y.to(DEV), kt=kt, k=k, return_map=True)
+    rs, rf, rq = oracle.ssim3d(x.numpy(), y.numpy(), k=k, kt=kt)
+    assert q.shape == rq.shape
+    assert np.abs(q.double().cpu().numpy() - rq).max() <= 1e-5
+    assert np.abs(frames.cpu().numpy() - rf).max() <= 1e-6
+    assert abs(score.item() - rs) <= 1e-6
+
+
+def test_kt1_equals_framewise_box_ssim(g):
+    x, y = _video(5, 60, 96, seed=3)
+    _, frames, q = g.ssim3d(x.to(DEV), y.to(DEV), kt=1, k=8, return_map=True)
+    m2, q2 = g.ssim(x.to(DEV), y.to(DEV), return_map=True, window="box", k=8, stride=1)
+    assert torch.allclose(q, q2, rtol=0, atol=1e-6)
+    assert torch.allclose(frames, m2, rtol=0, atol=1e-6)
+
+
+def test_ssim3d_full_hd_sampled(g):
+    """1080p, 10 frames, kt = 5: sampled output positions against the oracle
+    on the crop that holds their window (the window is local)."""
+    x, y = _video(10, 1080, 1920, seed=7)
+    k, kt = 11, 5
+    score, frames, q = g.ssim3d(x.to(DEV), y.to(DEV), kt=kt, k=k, return_map=True)
+    qc = q.cpu().numpy()
+    r = np.random.default_rng(1)
+    for _ in range(40):
+        t, a, b = r.integers(0, 10 - kt + 1), r.integers(0, 1070), r.integers(0, 1910)
+        xs = x[t:t + kt, a:a + k, b:b + k].numpy()
+        ys = y[t:t + kt, a:a + k, b:b + k].numpy()
+        _, _, rq = oracle.ssim3d(xs, ys, k=k, kt=kt)
+        assert abs(qc[t, a, b] - rq[0, 0, 0]) <= 1e-5
+    assert abs(score.item() - frames.mean().item()) <= 1e-12
+    assert torch.isfinite(q).all()
+
+
+def test_ssim3d_rejects_unsupported(g):
+    x = torch.zeros((4, 32, 32), dtype=torch.uint8, device=DEV)
+    with pytest.raises(g.GbssimError) as e:
+        g.ssim3d(x, x, kt=5)                      # kt > T
+    assert e.value.status == g.ERR_TOO_SMALL
+    with pytest.raises(g.GbssimError) as e:
+        g.ssim3d(x, x, kt=2, k=11, stride=2)      # spatial stride
+    assert e.value.status == g.ERR_UNSUPPORTED
