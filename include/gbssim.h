@@ -100,6 +100,14 @@ typedef struct gbssim_params {
  * double-buffered bulk tensor copies (TMA) instead of per-thread vector loads.
  * Same results (exact integer sums); which is faster depends on the GPU. */
 #define GBSSIM_FLAG_BOX_TMA 1
+/* MS-SSIM pyramid from the 9/7 biorthogonal wavelet low-pass instead of the
+ * 2x2 average (Section "Salient Features of SSIM and MS-SSIM
+ * Implementations", the LIBVMAF variant): the CDF 9/7 analysis low-pass
+ * (JPEG 2000 irreversible transform, scaled to unit DC gain) along rows and
+ * columns with whole-sample symmetric extension, keeping the even samples;
+ * level sizes stay floor(H/2) x floor(W/2).  Forward only (the backward and
+ * the batch API reject it with GBSSIM_ERR_UNSUPPORTED). */
+#define GBSSIM_FLAG_PYRAMID_97 2
 
 /* Operation codes for gbssim_workspace_size. */
 typedef enum gbssim_op {
@@ -182,6 +190,35 @@ int gbssim_ssim_map(const gbssim_plane *x, const gbssim_plane *y, const gbssim_p
 int gbssim_ssim_pool(const float *map, int64_t h, int64_t w, int64_t ld, int32_t count,
                      int64_t image_stride, int32_t kind, const double *args, double *out,
                      void *workspace, size_t workspace_bytes, void *stream);
+
+/* Automatic downscaling factor Z (the recommended implementation's "if
+ * min(M, N) > 256, resize so that min(M, N) = 256"; Section "Transforming
+ * across Various Scales").  rule GBSSIM_DOWNSCALE_ROUND_MIN:
+ * max(1, round(min(h, w) / 256)) with halves rounded up (LIBVMAF);
+ * GBSSIM_DOWNSCALE_CEIL_H: max(1, ceil(h / 256)).  Host function; returns Z,
+ * or GBSSIM_ERR_INVALID_ARG for a bad rule or size. */
+#define GBSSIM_DOWNSCALE_ROUND_MIN 0
+#define GBSSIM_DOWNSCALE_CEIL_H 1
+int gbssim_downscale_factor(int64_t h, int64_t w, int32_t rule);
+
+/* Z x Z block means of each image of `in` (floor size (H / Z) x (W / Z)) into
+ * float planes: image b at out + b*out_image_stride, rows out_ld floats apart
+ * (out_ld >= W / Z, out_image_stride >= (H / Z) out_ld).  The averaging
+ * filter of width Z followed by keeping every Z-th sample, with
+ * non-overlapping blocks (Z = 2 is the MS-SSIM 2x2 pyramid step).  1 <= Z <=
+ * min(H, W).  Any input dtype; sums in fp32. */
+int gbssim_downscale(const gbssim_plane *in, int32_t z, float *out, int64_t out_ld, int64_t out_image_stride,
+                     void *stream);
+
+/* BT.709 luma and colour differences of planar RGB images as the paper
+ * prints them (Section "Channel-wise SSIM"): Y = 0.213 R + 0.715 G + 0.072 B,
+ * Cb = 0.539 (B - Y), Cr = 0.635 (R - Y), on the inputs' own scale (no
+ * offset, no clipping; Cb and Cr are signed).  r, g, b: planes of one shape
+ * and dtype; outputs: float planes, image i at out + i*out_image_stride,
+ * rows out_ld floats apart.  Feed the three planes to gbssim_video (weights
+ * e.g. 0.8, 0.1, 0.1, or 1, alpha, beta) for the channel-weighted SSIM. */
+int gbssim_rgb_to_ycbcr(const gbssim_plane *r, const gbssim_plane *g, const gbssim_plane *b, float *y_out,
+                        float *cb_out, float *cr_out, int64_t out_ld, int64_t out_image_stride, void *stream);
 
 /* Temporal pooling of `count` series of n frame scores (doubles, device
  * memory, series b at scores + b*stride) into one double each (device `out`),

@@ -248,10 +248,12 @@ def downsample2x2(img) -> np.ndarray:
 
 def msssim(x, y, scales: int = 5, exponents=MSSSIM_EXPONENTS, combine: str = "product",
            window_kind: str = "gaussian", k: int = 11, sigma: float = 1.5,
-           K1: float = 0.01, K2: float = 0.03, L: float = 255.0):
+           K1: float = 0.01, K2: float = 0.03, L: float = 255.0, pyramid: str = "avg2"):
     """MS-SSIM (Introduction; Section "Salient Features ...").
 
-    Scale 1 is the input; scale j+1 is the 2x2 average of scale j.  The
+    Scale 1 is the input; scale j+1 is the 2x2 average of scale j
+    (pyramid="avg2"), or its 9/7 wavelet low-pass (pyramid="97",
+    ``oracle.scales.pyramid_97``, the LIBVMAF variant of that section).  The
     contrast-structure term is pooled at every scale and the luminance term
     only at the coarsest: m_j = mean cs_j for j < S and m_S = mean Q_S.
     combine="product": prod_j m_j^beta_j.  combine="sum" (Scikit-Video):
@@ -270,7 +272,14 @@ def msssim(x, y, scales: int = 5, exponents=MSSSIM_EXPONENTS, combine: str = "pr
         _, cs, q = ssim_terms(st, C1, C2)
         per.append((mean(cs), mean(q)))
         if j + 1 < scales:
-            a, b = downsample2x2(a), downsample2x2(b)
+            if pyramid == "avg2":
+                a, b = downsample2x2(a), downsample2x2(b)
+            elif pyramid == "97":
+                from .scales import pyramid_97
+
+                a, b = pyramid_97(a), pyramid_97(b)
+            else:
+                raise ValueError(pyramid)
     m = np.array([per[j][0] for j in range(scales - 1)] + [per[-1][1]])
     if combine == "product":
         with np.errstate(invalid="ignore"):

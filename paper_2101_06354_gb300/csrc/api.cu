@@ -50,7 +50,7 @@ int check_params(const gbssim_params *p) {
     for (int j = 0; j < p->scales; ++j)
         if (!isfinite(p->exponents[j])) return GBSSIM_ERR_INVALID_ARG;
     if (p->combine != GBSSIM_COMBINE_PRODUCT && p->combine != GBSSIM_COMBINE_SUM) return GBSSIM_ERR_INVALID_ARG;
-    if (p->flags & ~GBSSIM_FLAG_BOX_TMA) return GBSSIM_ERR_INVALID_ARG;
+    if (p->flags & ~(GBSSIM_FLAG_BOX_TMA | GBSSIM_FLAG_PYRAMID_97)) return GBSSIM_ERR_INVALID_ARG;
     return GBSSIM_OK;
 }
 
@@ -197,6 +197,13 @@ cudaError_t run_level(const Level &L, const ImgDesc &dx, const ImgDesc &dy, int 
     none.sx = none.sy = 0.f;
     cudaError_t e = cudaSuccess;
     bool fused_ds = false;
+    const bool p97 = (p->flags & GBSSIM_FLAG_PYRAMID_97) != 0;  // the 9/7 pyramid is never fused
+    if (p97 && L.path == PATH_GAUSS11 && ds_x) {  // the level alone, then the 9/7 step
+        e = run_level(L, dx, dy, dtype, count, p, map, map_ld, map_is, partials, nullptr, nullptr, st, co);
+        if (e == cudaSuccess && ds_x) e = launch_pyramid97(dx, dtype, count, ds_x, st);
+        if (e == cudaSuccess && ds_y) e = launch_pyramid97(dy, dtype, count, ds_y, st);
+        return e;
+    }
     if (L.path == PATH_GAUSS11) {
         GaussLaunch G;
         G.x = dx;
@@ -252,7 +259,11 @@ cudaError_t run_level(const Level &L, const ImgDesc &dx, const ImgDesc &dy, int 
         e = launch_generic(G, st);
     }
     if (e != cudaSuccess) return e;
-    if (ds_x && !fused_ds) {
+    if (ds_x && !fused_ds && p97) {
+        e = launch_pyramid97(dx, dtype, count, ds_x, st);
+        if (e != cudaSuccess) return e;
+        e = launch_pyramid97(dy, dtype, count, ds_y, st);
+    } else if (ds_x && !fused_ds) {
         e = launch_downsample(dx, dtype, count, ds_x, st);
         if (e != cudaSuccess) return e;
         e = launch_downsample(dy, dtype, count, ds_y, st);
@@ -268,7 +279,7 @@ int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_pa
                           const MsPlan &P, char *ws, double *score_out, double *per_scale_out,
                           cudaStream_t st) {
     const int S = p->scales, n = x->count;
-    bool persistent = true;
+    bool persistent = (p->flags & GBSSIM_FLAG_PYRAMID_97) == 0;  // the persistent path fuses the 2x2 pyramid
     for (int j = 0; j < S; ++j) persistent = persistent && P.lv[j].path == PATH_GAUSS11;
     if (persistent) {
         // one launch over all levels and images: level-major items, a level-j
@@ -722,6 +733,45 @@ int gbssim_ssim3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_par
     return e == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
 }
 
+int gbssim_rgb_to_ycbcr(const gbssim_plane *r, const gbssim_plane *g, const gbssim_plane *b, float *y_out,
+                        float *cb_out, float *cr_out, int64_t out_ld, int64_t out_image_stride, void *stream) {
+    int rc = check_pair(r, g);
+    if (rc) return rc;
+    rc = check_pair(r, b);
+    if (rc) return rc;
+    if (!y_out || !cb_out || !cr_out || out_ld < r->width || (r->count > 1 && out_image_stride < r->height * out_ld))
+        return GBSSIM_ERR_INVALID_ARG;
+    const cudaError_t e =
+        launch_rgb_ycbcr(desc_of(r), desc_of(g), desc_of(b), r->dtype, r->count, y_out, cb_out, cr_out, out_ld,
+                         r->count > 1 ? out_image_stride : r->height * out_ld, (cudaStream_t)stream);
+    return e == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
+}
+
+int gbssim_downscale_factor(int64_t h, int64_t w, int32_t rule) {
+    if (h < 1 || w < 1) return GBSSIM_ERR_INVALID_ARG;
+    if (rule == GBSSIM_DOWNSCALE_ROUND_MIN) {
+        const int64_t z = ((h < w ? h : w) + 128) / 256;
+        return (int)(z > 1 ? z : 1);
+    }
+    if (rule == GBSSIM_DOWNSCALE_CEIL_H) {
+        const int64_t z = (h + 255) / 256;
+        return (int)(z > 1 ? z : 1);
+    }
+    return GBSSIM_ERR_INVALID_ARG;
+}
+
+int gbssim_downscale(const gbssim_plane *in, int32_t z, float *out, int64_t out_ld, int64_t out_image_stride,
+                     void *stream) {
+    int rc = check_plane(in);
+    if (rc) return rc;
+    if (!out || z < 1 || z > in->height || z > in->width) return GBSSIM_ERR_INVALID_ARG;
+    const int64_t oh = in->height / z, ow = in->width / z;
+    if (out_ld < ow || (in->count > 1 && out_image_stride < oh * out_ld)) return GBSSIM_ERR_INVALID_ARG;
+    const cudaError_t e = launch_block_mean(desc_of(in), in->dtype, in->count, z, out, out_ld,
+                                            in->count > 1 ? out_image_stride : oh * out_ld, (cudaStream_t)stream);
+    return e == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
+}
+
 int gbssim_msssim(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
                   double *score_out, double *per_scale_out, void *workspace,
                   size_t workspace_bytes, void *stream) {
@@ -824,6 +874,7 @@ int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbs
     rc = check_params(p);
     if (rc) return rc;
     if (p->stride != 1 || p->k > GBSSIM_MAX_K_BACKWARD) return GBSSIM_ERR_UNSUPPORTED;
+    if (p->flags & GBSSIM_FLAG_PYRAMID_97) return GBSSIM_ERR_UNSUPPORTED;  // no adjoint of the 9/7 step
     if (!grad_y || (grad_dtype != GBSSIM_F32 && grad_dtype != GBSSIM_F16 && grad_dtype != GBSSIM_BF16))
         return GBSSIM_ERR_INVALID_ARG;
     if (grad_ld < x->width || (x->count > 1 && grad_image_stride < x->height * grad_ld))

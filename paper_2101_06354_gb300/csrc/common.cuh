@@ -317,6 +317,13 @@ struct Ssim3dLaunch {
 void ssim3d_tiles(int64_t H, int64_t W, int k, int *tx, int *ty);
 cudaError_t launch_ssim3d(const Ssim3dLaunch &L, double *frame_out, double *score_out, cudaStream_t st);
 
+// Scale handling (k_scale.cu): Z x Z block means and the 9/7 wavelet pyramid step.
+cudaError_t launch_block_mean(const ImgDesc &in, int dtype, int count, int z, float *out, int64_t out_ld,
+                              int64_t out_is, cudaStream_t st);
+cudaError_t launch_pyramid97(const ImgDesc &in, int dtype, int count, float *out, cudaStream_t st);
+cudaError_t launch_rgb_ycbcr(const ImgDesc &r, const ImgDesc &g, const ImgDesc &b, int dtype, int count, float *y,
+                             float *cb, float *cr, int64_t out_ld, int64_t out_is, cudaStream_t st);
+
 // Temporal pooling of frame-score series (k_series.cu).
 cudaError_t launch_series_pool(const double *scores, int n, int count, int64_t stride, int kind, double a0,
                                double a1, double *out, cudaStream_t st);

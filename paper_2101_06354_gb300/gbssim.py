@@ -101,6 +101,9 @@ _SIGS = {
     "gbssim_msssim_host_workspace_size": ([_P(Plane), _P(Params), _i32, _P(_sz)], ctypes.c_int),
     "gbssim_series_pool": ([_vp, _i32, _i32, _i64, _i32, _vp, _vp, _vp], ctypes.c_int),
     "gbssim_ssim3d_workspace_size": ([_P(Plane), _P(Params), _i32, _P(_sz)], ctypes.c_int),
+    "gbssim_downscale_factor": ([_i64, _i64, _i32], ctypes.c_int),
+    "gbssim_downscale": ([_P(Plane), _i32, _vp, _i64, _i64, _vp], ctypes.c_int),
+    "gbssim_rgb_to_ycbcr": ([_P(Plane), _P(Plane), _P(Plane), _vp, _vp, _vp, _i64, _i64, _vp], ctypes.c_int),
     "gbssim_ssim3d": ([_P(Plane), _P(Plane), _P(Params), _i32, _vp, _vp, _vp, _i64, _i64, _vp, _sz, _vp],
                       ctypes.c_int),
     "gbssim_msssim_host": ([_P(Plane), _P(Plane), _P(Params), _i32, _vp, _vp, _sz, _vp, _vp, _vp], ctypes.c_int),
@@ -313,6 +316,8 @@ def msssim(x: torch.Tensor, y: torch.Tensor, per_scale: bool = False, ws: torch.
         return msssim_host(x, y, **kw)
     host, dev, xb, yb = _prepare(x, y)
     kw.setdefault("exponents", MSSSIM_EXPONENTS[: kw.get("scales", 5)])
+    if kw.pop("pyramid", "avg2") == "97":
+        kw["flags"] = kw.get("flags", 0) | FLAG_PYRAMID_97
     p = make_params(**kw)
     px, py = plane(xb), plane(yb)
     n = xb.shape[0]
@@ -400,6 +405,56 @@ def ssim3d(x: torch.Tensor, y: torch.Tensor, kt: int = 5, k: int = 11, return_ma
                              score.data_ptr(), qmap.data_ptr() if return_map else None, W - k + 1,
                              (H - k + 1) * (W - k + 1), ws.data_ptr(), ws.numel(), _stream(dev)), "gbssim_ssim3d")
     return (score[0], frames, qmap) if return_map else (score[0], frames)
+
+
+FLAG_PYRAMID_97 = 2
+DOWNSCALE_RULES = {"round_min": 0, "ceil_h": 1}
+
+
+def downscale_factor(h: int, w: int, rule: str = "round_min") -> int:
+    """Automatic downscaling factor Z (gbssim_downscale_factor)."""
+    z = lib.gbssim_downscale_factor(int(h), int(w), DOWNSCALE_RULES[rule])
+    _check(OK if z > 0 else z, "gbssim_downscale_factor")
+    return z
+
+
+def downscale(x: torch.Tensor, z: int) -> torch.Tensor:
+    """Z x Z block means (gbssim_downscale) of (H, W) or (N, H, W) planes on
+    the GPU into float32 (N, H // z, W // z)."""
+    xb = _as_batch(x)
+    if xb.device.type != "cuda":
+        raise ValueError("downscale takes CUDA tensors")
+    n, h, w = xb.shape
+    out = torch.empty((n, h // z, w // z), dtype=torch.float32, device=xb.device)
+    px = plane(xb)
+    _check(lib.gbssim_downscale(ctypes.byref(px), int(z), out.data_ptr(), w // z, (h // z) * (w // z),
+                                _stream(xb.device)), "gbssim_downscale")
+    return out if x.dim() != 2 else out[0]
+
+
+def rgb_to_ycbcr(r: torch.Tensor, g: torch.Tensor, b: torch.Tensor):
+    """BT.709 Y, Cb, Cr float planes (gbssim_rgb_to_ycbcr) of planar RGB
+    CUDA tensors (H, W) or (N, H, W)."""
+    rb, gb, bb = _as_batch(r).contiguous(), _as_batch(g).contiguous(), _as_batch(b).contiguous()
+    n, h, w = rb.shape
+    out = torch.empty((3, n, h, w), dtype=torch.float32, device=rb.device)
+    pr, pg, pb = plane(rb), plane(gb), plane(bb)
+    _check(lib.gbssim_rgb_to_ycbcr(ctypes.byref(pr), ctypes.byref(pg), ctypes.byref(pb), out[0].data_ptr(),
+                                   out[1].data_ptr(), out[2].data_ptr(), w, h * w, _stream(rb.device)),
+           "gbssim_rgb_to_ycbcr")
+    return out[0], out[1], out[2]
+
+
+def colour_ssim(ref_rgb, dis_rgb, weights=(0.8, 0.1, 0.1), **kw):
+    """Channel-weighted colour SSIM of planar RGB frames (Section
+    "Channel-wise SSIM"): BT.709 Y, Cb, Cr of both, SSIM of each plane, frame
+    score (w_Y S_Y + w_Cb S_Cb + w_Cr S_Cr) / (w_Y + w_Cb + w_Cr).  ref_rgb and
+    dis_rgb are (R, G, B) tuples of CUDA tensors (frames, H, W).  Returns
+    gbssim_video's (frame_scores, plane_scores, (mean, p10, pp)).  The paper's
+    tuned weights are 1, -0.3, -0.3."""
+    xs = rgb_to_ycbcr(*ref_rgb)
+    ys = rgb_to_ycbcr(*dis_rgb)
+    return video_ssim(xs, ys, weights=weights, **kw)
 
 
 _GDT = {torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}

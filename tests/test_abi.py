@@ -82,7 +82,7 @@ def test_workspace_sizes(g):
 
 @pytest.mark.parametrize("field,value,status", [
     ("k", 0, -1), ("k", 64, -1), ("stride", 0, -1), ("scales", 0, -1), ("scales", 9, -1),
-    ("window", 7, -1), ("sigma", 0.0, -1), ("L", -1.0, -1), ("combine", 3, -1), ("flags", 2, -1),
+    ("window", 7, -1), ("sigma", 0.0, -1), ("L", -1.0, -1), ("combine", 3, -1), ("flags", 4, -1),
 ])
 def test_bad_params_rejected(g, field, value, status):
     p = g.make_params()
@@ -158,6 +158,8 @@ def test_batch_plan_validation_on_host(g):
     p = g.make_params()
     x = (g.Plane * 2)(_plane(g, 100, 120), _plane(g, 50, 60))
     out = ctypes.c_void_p()
+    p97 = g.make_params(flags=g.FLAG_PYRAMID_97)  # the persistent batch kernel fuses the 2x2 pyramid
+    assert g.lib.gbssim_batch_plan(x, x, 2, ctypes.byref(p97), 1, None, ctypes.byref(out)) == g.ERR_UNSUPPORTED
     assert g.lib.gbssim_batch_plan(x, x, 0, ctypes.byref(p), 0, None, ctypes.byref(out)) == g.ERR_INVALID_ARG
     p7 = g.make_params(k=7, sigma=1.0)
     assert g.lib.gbssim_batch_plan(x, x, 2, ctypes.byref(p7), 0, None, ctypes.byref(out)) == g.ERR_UNSUPPORTED
@@ -171,3 +173,13 @@ def test_batch_plan_validation_on_host(g):
     assert g.lib.gbssim_batch_plan(x, x, 2, ctypes.byref(p), 0, ctypes.byref(bad), ctypes.byref(out)) \
         == g.ERR_INVALID_ARG
     assert out.value is None
+
+
+def test_downscale_factor_matches_oracle(g):
+    from oracle import scales
+
+    for h, w in [(1080, 1920), (200, 300), (384, 1000), (383, 1000), (510, 900), (520, 900), (2160, 3840), (1, 1)]:
+        assert g.downscale_factor(h, w) == scales.downscale_factor(h, w)
+        assert g.downscale_factor(h, w, "ceil_h") == scales.downscale_factor(h, w, "ceil_h")
+    assert g.lib.gbssim_downscale_factor(100, 100, 7) == g.ERR_INVALID_ARG
+    assert g.lib.gbssim_downscale_factor(0, 100, 0) == g.ERR_INVALID_ARG

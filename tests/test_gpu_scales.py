@@ -1,0 +1,120 @@
+"""GPU parity of the scale handling: Z x Z block-mean downscaling
+(gbssim_downscale) and MS-SSIM over the 9/7 wavelet pyramid
+(GBSSIM_FLAG_PYRAMID_97), against oracle/scales.py and the oracle's
+MS-SSIM with pyramid="97"."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import scales as S
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2101_06354_gb300 import build
+
+    build.build()
+    from paper_2101_06354_gb300 import gbssim
+
+    return gbssim
+
+
+@pytest.mark.parametrize("z", [1, 2, 3, 4, 7])
+@pytest.mark.parametrize("dtype", [torch.uint8, torch.float32])
+def test_downscale_matches_oracle(g, z, dtype):
+    from paper_2101_06354_gb300 import synth
+
+    x, _ = synth.luma_pairs_u8(3, 101, 133)
+    if dtype == torch.float32:
+        x = x.float() / 255
+    got = g.downscale(x.to(DEV), z).cpu().double().numpy()
+    for i in range(3):
+        ref = S.downscale_block(x[i].double().numpy(), z)
+        assert got[i].shape == ref.shape
+        assert np.abs(got[i] - ref).max() <= 1e-6 * max(1.0, np.abs(ref).max())
+
+
+def test_downscale_then_ssim_at_the_factor(g):
+    """The recommended implementation's flow on a 1080p pair: Z from the
+    round-min rule (4), block means, then SSIM of the downscaled pair."""
+    from paper_2101_06354_gb300 import synth
+
+    x, y = synth.luma_pairs_u8(1, 1080, 1920)
+    z = g.downscale_factor(1080, 1920)
+    assert z == 4
+    xs, ys = g.downscale(x.to(DEV), z), g.downscale(y.to(DEV), z)
+    got = g.ssim(xs, ys).item()
+    ref, _ = oracle.ssim(S.downscale_block(x[0].numpy(), z), S.downscale_block(y[0].numpy(), z))
+    assert abs(got - ref) <= 1e-6
+
+
+@pytest.mark.parametrize("h,w", [(200, 232), (181, 203)])
+def test_msssim_97_pyramid_matches_oracle(g, h, w):
+    from paper_2101_06354_gb300 import synth
+
+    x, y = synth.luma_pairs_u8(2, h, w)
+    got = g.msssim(x.to(DEV), y.to(DEV), pyramid="97").cpu().numpy()
+    for i in range(2):
+        ref, _ = oracle.msssim(x[i].numpy(), y[i].numpy(), pyramid="97")
+        assert abs(got[i] - ref) <= 1e-6
+    avg = g.msssim(x.to(DEV), y.to(DEV)).cpu().numpy()
+    assert np.all(np.abs(avg - got) > 0)  # a different pyramid gives a different score
+
+
+def test_msssim_97_float_three_scales(g):
+    from paper_2101_06354_gb300 import synth
+
+    x, y = synth.loss_pairs_float(1, 2, 150, 170)
+    xs, ys = x.reshape(2, 150, 170), y.reshape(2, 150, 170)
+    kw = dict(L=1.0, scales=3, exponents=(0.3, 0.3, 0.4))
+    got = g.msssim(xs.to(DEV), ys.to(DEV), pyramid="97", **kw).cpu().numpy()
+    for i in range(2):
+        ref, _ = oracle.msssim(xs[i].double().numpy(), ys[i].double().numpy(), pyramid="97", **kw)
+        assert abs(got[i] - ref) <= 1e-6
+
+
+def test_97_pyramid_rejected_where_unsupported(g):
+    x = torch.zeros((1, 200, 200), device=DEV)
+    with pytest.raises(g.GbssimError) as e:
+        g.ssim_backward(x, x, multiscale=True, flags=g.FLAG_PYRAMID_97)
+    assert e.value.status == g.ERR_UNSUPPORTED
+
+
+def _rgb(n, h, w, seed):
+    from paper_2101_06354_gb300 import synth
+
+    planes = [synth.luma_pairs_u8(n, h, w, seed_ref=seed + c, seed_dist=seed + 10 + c) for c in range(3)]
+    ref = tuple(p[0] for p in planes)
+    dis = tuple(p[1] for p in planes)
+    return ref, dis
+
+
+@pytest.mark.parametrize("dtype", [torch.uint8, torch.float32])
+def test_rgb_to_ycbcr_matches_oracle(g, dtype):
+    ref, _ = _rgb(2, 37, 53, 5)
+    if dtype == torch.float32:
+        ref = tuple(t.float() / 255 for t in ref)
+    y, cb, cr = g.rgb_to_ycbcr(*(t.to(DEV) for t in ref))
+    ry, rcb, rcr = S.rgb_to_ycbcr(*(t.double().numpy() for t in ref))
+    scale = 255.0 if dtype == torch.uint8 else 1.0
+    for got, want in ((y, ry), (cb, rcb), (cr, rcr)):
+        assert np.abs(got.cpu().double().numpy() - want).max() <= 2e-7 * scale * 4
+
+
+@pytest.mark.parametrize("weights", [(0.8, 0.1, 0.1), (1.0, -0.3, -0.3)])
+def test_colour_ssim_matches_oracle(g, weights):
+    ref, dis = _rgb(3, 90, 120, 9)
+    fr, ps, vid = g.colour_ssim(tuple(t.to(DEV) for t in ref), tuple(t.to(DEV) for t in dis), weights=weights)
+    for t in range(3):
+        rr = S.rgb_to_ycbcr(*(c[t].double().numpy() for c in ref))
+        dd = S.rgb_to_ycbcr(*(c[t].double().numpy() for c in dis))
+        s = [oracle.ssim(a, b)[0] for a, b in zip(rr, dd)]
+        assert np.abs(ps[:, t].cpu().numpy() - s).max() <= 1e-5  # fp32 planes vs fp64
+        assert abs(fr[t].item() - oracle.colour_score(*s, weights=weights)) <= 1e-5 / abs(sum(weights)) * 3
+    assert abs(vid[0].item() - fr.mean().item()) <= 1e-12
