@@ -220,6 +220,23 @@ int gbssim_downscale(const gbssim_plane *in, int32_t z, float *out, int64_t out_
 int gbssim_rgb_to_ycbcr(const gbssim_plane *r, const gbssim_plane *g, const gbssim_plane *b, float *y_out,
                         float *cb_out, float *cr_out, int64_t out_ld, int64_t out_image_stride, void *stream);
 
+/* Window-weighted local mean of x at every valid (strided) map position, the
+ * mu_1 of Eq. local_means, with p's window (Gaussian k, sigma or box k) and
+ * stride; float output laid out like a map (rows out_ld floats apart, images
+ * out_image_stride apart).  Any input dtype; fp32 sums.  It is the input of
+ * luminance-weighted pooling. */
+int gbssim_local_mean(const gbssim_plane *x, const gbssim_params *p, float *out, int64_t out_ld,
+                      int64_t out_image_stride, void *stream);
+
+/* Luminance-weighted pooling (Section "Spatio-temporal Aggregation of Quality
+ * Scores", LW pooling): S_LW = (1/n) sum w(mu_1) Q with w = 0 for mu_1 < a,
+ * (mu_1 - a)/b on [a, a + b), 1 from a + b on (b = 0: a step at a); mu_ref
+ * holds mu_1 (gbssim_local_mean of the reference) in the map's layout.
+ * a = b = 0 is the plain mean.  Workspace: gbssim_workspace_size(GBSSIM_OP_POOL). */
+int gbssim_ssim_pool_lw(const float *map, const float *mu_ref, int64_t h, int64_t w, int64_t ld, int32_t count,
+                        int64_t image_stride, double a, double b, double *out, void *workspace, size_t workspace_bytes,
+                        void *stream);
+
 /* Temporal pooling of `count` series of n frame scores (doubles, device
  * memory, series b at scores + b*stride) into one double each (device `out`),
  * in fp64 (Section "Spatio-temporal Aggregation of Quality Scores").  Every
@@ -329,6 +346,29 @@ int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbs
                          int32_t grad_out_per_image, const double *fwd_score, const double *fwd_per_scale,
                          void *grad_y, int32_t grad_dtype, int64_t grad_ld, int64_t grad_image_stride,
                          double *score_out, void *workspace, size_t workspace_bytes, void *stream);
+
+/* The SSIM / MS-SSIM loss split into a forward that keeps what the backward
+ * needs and a backward that reuses it (the computation of
+ * gbssim_ssim_backward without recomputing the window moments; the paper
+ * defines the score only, the gradient is the chain rule of its
+ * definitions).  gbssim_loss_forward runs every level once in coefficient
+ * mode (moments, Q, cs and the three coefficient maps per output, 2x2 pyramid
+ * fused) and writes the scores (score_out, nullable; per_scale_out as for
+ * gbssim_msssim, nullable) and, in `saved`, the coefficient maps, pooled
+ * values and pyramid planes.  gbssim_loss_backward then writes
+ * grad_scale * grad_out * d(score)/dy into grad_y from `saved` alone (x, y and
+ * p must be those of the forward; `saved` is not modified except for its
+ * coarse-gradient scratch).  `saved` is caller-owned device memory of
+ * gbssim_loss_saved_size bytes; it must stay untouched between the two calls.
+ * Arguments and restrictions otherwise as gbssim_ssim_backward (stride 1,
+ * k <= 31, no 9/7 pyramid). */
+int gbssim_loss_saved_size(const gbssim_plane *x, const gbssim_params *p, int32_t multiscale, size_t *bytes);
+int gbssim_loss_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t multiscale,
+                        double *score_out, double *per_scale_out, void *saved, size_t saved_bytes, void *stream);
+int gbssim_loss_backward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t multiscale,
+                         double grad_scale, const double *grad_out, int32_t grad_out_per_image, const void *saved,
+                         size_t saved_bytes, void *grad_y, int32_t grad_dtype, int64_t grad_ld,
+                         int64_t grad_image_stride, void *stream);
 
 /* Colour and temporal pooling of a YUV video (any chroma subsampling).
  * planes = {x_Y, y_Y, x_U, y_U, x_V, y_V}, each a batch of `frames` images

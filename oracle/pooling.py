@@ -141,3 +141,18 @@ def windowed(values, k: int, kind: str = "am") -> float:
         raise ValueError("window size must be in 1..n")
     f = {"am": mean, "gm": gm, "hm": hm, "cov": cov}[kind]
     return float(sum(f(v[t:t + k]) for t in range(n - k + 1)) / (n - k + 1))
+
+
+def local_mean(img, w, stride: int = 1):
+    """Window-weighted local mean mu(i, j) = sum_{m,n} w(m, n) img(i s + m, j s + n)
+    at every valid strided position (Eq. local_means): the mu_1 map that
+    luminance-weighted pooling weights by."""
+    a = np.asarray(img, dtype=np.float64)
+    k = w.shape[0]
+    oh = (a.shape[0] - k) // stride + 1
+    ow = (a.shape[1] - k) // stride + 1
+    out = np.zeros((oh, ow))
+    for m in range(k):
+        for n in range(k):
+            out += w[m, n] * a[m:m + stride * (oh - 1) + 1:stride, n:n + stride * (ow - 1) + 1:stride]
+    return out

@@ -428,6 +428,56 @@ int plan_backward(const gbssim_plane *x, const gbssim_params *p, int multiscale,
     return GBSSIM_OK;
 }
 
+// Saved state of the loss path (gbssim_loss_forward -> gbssim_loss_backward):
+// per level the coefficient maps, the pooling partials and (levels >= 1) the
+// pyramid planes; the scores and per-scale means; the coarse gradients the
+// backward passes down the pyramid.
+struct SavedPlan {
+    MsPlan lv;  // per-level geometry and items (float path)
+    size_t coef_off[GBSSIM_MAX_SCALES], part_off[GBSSIM_MAX_SCALES], plane_off[GBSSIM_MAX_SCALES];
+    size_t grad_off[GBSSIM_MAX_SCALES], score_off, per_off, bytes;
+};
+
+int plan_saved(const gbssim_plane *x, const gbssim_params *p, int multiscale, SavedPlan *Sv) {
+    const int S = multiscale ? p->scales : 1;
+    int rc = plan_levels(x, p, S, &Sv->lv, true);
+    if (rc) return rc;
+    const int n = x->count;
+    size_t off = 0;
+    for (int j = 0; j < S; ++j) {
+        const Level &L = Sv->lv.lv[j];
+        const int64_t OH = out_dim(L.H, p->k, 1), OW = out_dim(L.W, p->k, 1);
+        Sv->coef_off[j] = off;
+        off = align_up(off + 3 * sizeof(float) * (size_t)OH * coef_ld(OW) * n);
+        Sv->part_off[j] = off;
+        off = align_up(off + sizeof(double2) * (size_t)L.items * n);
+        Sv->plane_off[j] = 0;
+        Sv->grad_off[j] = 0;
+        if (j > 0) {
+            Sv->plane_off[j] = off;
+            off = align_up(off + 2 * sizeof(float) * (size_t)L.H * L.W * n);
+            Sv->grad_off[j] = off;
+            off = align_up(off + sizeof(float) * (size_t)L.H * L.W * n);
+        }
+    }
+    Sv->score_off = off;
+    off = align_up(off + sizeof(double) * n);
+    Sv->per_off = off;
+    off = align_up(off + 2 * sizeof(double) * (size_t)S * n);
+    Sv->bytes = off;
+    return GBSSIM_OK;
+}
+
+int check_loss(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p) {
+    int rc = check_pair(x, y);
+    if (rc) return rc;
+    rc = check_params(p);
+    if (rc) return rc;
+    if (p->stride != 1 || p->k > GBSSIM_MAX_K_BACKWARD) return GBSSIM_ERR_UNSUPPORTED;
+    if (p->flags & GBSSIM_FLAG_PYRAMID_97) return GBSSIM_ERR_UNSUPPORTED;
+    return GBSSIM_OK;
+}
+
 // Host-input MS-SSIM: layout of the device buffer.  Two stages of `per`
 // images each (x then y, rows padded to 16 bytes), the MS-SSIM workspace for
 // one chunk, and the scores of all images.
@@ -747,6 +797,36 @@ int gbssim_rgb_to_ycbcr(const gbssim_plane *r, const gbssim_plane *g, const gbss
     return e == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
 }
 
+int gbssim_local_mean(const gbssim_plane *x, const gbssim_params *p, float *out, int64_t out_ld,
+                      int64_t out_image_stride, void *stream) {
+    int rc = check_plane(x);
+    if (rc) return rc;
+    rc = check_params(p);
+    if (rc) return rc;
+    if (!out || x->height < p->k || x->width < p->k) return out ? GBSSIM_ERR_TOO_SMALL : GBSSIM_ERR_INVALID_ARG;
+    const int64_t OH = out_dim(x->height, p->k, p->stride), OW = out_dim(x->width, p->k, p->stride);
+    if (out_ld < OW || (x->count > 1 && out_image_stride < OH * out_ld)) return GBSSIM_ERR_INVALID_ARG;
+    TapsDyn taps;
+    memset(taps.g, 0, sizeof taps.g);
+    make_taps(p, taps.g);
+    const cudaError_t e = launch_local_mean(desc_of(x), x->dtype, x->count, taps, p->k, p->stride, out, out_ld,
+                                            x->count > 1 ? out_image_stride : OH * out_ld, (cudaStream_t)stream);
+    return e == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
+}
+
+int gbssim_ssim_pool_lw(const float *map, const float *mu_ref, int64_t h, int64_t w, int64_t ld, int32_t count,
+                        int64_t image_stride, double a, double b, double *out, void *workspace, size_t workspace_bytes,
+                        void *stream) {
+    if (!map || !mu_ref || !out || h < 1 || w < 1 || ld < w || count < 1 || count > 65535) return GBSSIM_ERR_INVALID_ARG;
+    if (count > 1 && image_stride < h * ld) return GBSSIM_ERR_INVALID_ARG;
+    if (!isfinite(a) || !isfinite(b) || b < 0.0) return GBSSIM_ERR_INVALID_ARG;
+    const PoolLayout L = pool_layout(h, w, count);
+    if (!workspace || workspace_bytes < L.bytes) return GBSSIM_ERR_WORKSPACE;
+    const cudaError_t e = launch_pool_map(map, h, w, ld, count, count > 1 ? image_stride : h * ld, kPoolLW, a, b,
+                                          (char *)workspace, out, (cudaStream_t)stream, mu_ref);
+    return e == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
+}
+
 int gbssim_downscale_factor(int64_t h, int64_t w, int32_t rule) {
     if (h < 1 || w < 1) return GBSSIM_ERR_INVALID_ARG;
     if (rule == GBSSIM_DOWNSCALE_ROUND_MIN) {
@@ -976,6 +1056,143 @@ int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbs
     if (multiscale && score_out &&
         cudaMemcpyAsync(score_out, ms_score, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return GBSSIM_ERR_CUDA;
+    return GBSSIM_OK;
+}
+
+int gbssim_loss_saved_size(const gbssim_plane *x, const gbssim_params *p, int32_t multiscale, size_t *bytes) {
+    int rc = check_loss(x, x, p);
+    if (rc) return rc;
+    if (!bytes) return GBSSIM_ERR_INVALID_ARG;
+    SavedPlan Sv;
+    rc = plan_saved(x, p, multiscale != 0, &Sv);
+    if (rc) return rc;
+    *bytes = Sv.bytes;
+    return GBSSIM_OK;
+}
+
+int gbssim_loss_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t multiscale,
+                        double *score_out, double *per_scale_out, void *saved, size_t saved_bytes, void *stream) {
+    int rc = check_loss(x, y, p);
+    if (rc) return rc;
+    SavedPlan Sv;
+    rc = plan_saved(x, p, multiscale != 0, &Sv);
+    if (rc) return rc;
+    if (!saved || saved_bytes < Sv.bytes) return GBSSIM_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)saved;
+    const int n = x->count, S = multiscale ? p->scales : 1;
+    MsFinalize F;
+    memset(&F, 0, sizeof F);
+    for (int j = 0; j < S; ++j) {
+        const Level &L = Sv.lv.lv[j];
+        ImgDesc dx = desc_of(x), dy = desc_of(y);
+        int dtype = x->dtype;
+        if (j > 0) {
+            const float *px = (const float *)(ws + Sv.plane_off[j]);
+            dx = ImgDesc{px, L.H, L.W, L.W, L.H * L.W};
+            dy = ImgDesc{px + (size_t)L.H * L.W * n, L.H, L.W, L.W, L.H * L.W};
+            dtype = GBSSIM_F32;
+        }
+        float *ds_x = nullptr, *ds_y = nullptr;
+        if (j + 1 < S) {
+            const Level &N = Sv.lv.lv[j + 1];
+            ds_x = (float *)(ws + Sv.plane_off[j + 1]);
+            ds_y = ds_x + (size_t)N.H * N.W * n;
+        }
+        CoefOut co;
+        co.coef = (float *)(ws + Sv.coef_off[j]);
+        co.which = (multiscale && j < S - 1) ? 1 : 0;
+        co.sx = co.sy = (float)(0.5 * p->L);
+        double2 *part = (double2 *)(ws + Sv.part_off[j]);
+        if (run_level(L, dx, dy, dtype, n, p, nullptr, 0, 0, part, ds_x, ds_y, st, &co) != cudaSuccess)
+            return GBSSIM_ERR_CUDA;
+        const int64_t OH = out_dim(L.H, p->k, 1), OW = out_dim(L.W, p->k, 1);
+        F.lv[j].partials = part;
+        F.lv[j].items_per_image = L.items;
+        F.lv[j].inv_n = 1.0 / ((double)OH * (double)OW);
+        F.exps[j] = multiscale ? p->exponents[j] : 1.0;
+    }
+    double *score = (double *)(ws + Sv.score_off), *per = (double *)(ws + Sv.per_off);
+    F.scales = S;
+    F.count = n;
+    F.combine = multiscale ? p->combine : GBSSIM_COMBINE_PRODUCT;
+    F.score_out = score;
+    F.per_scale_out = per;
+    if (launch_finalize_msssim(F, st) != cudaSuccess) return GBSSIM_ERR_CUDA;
+    if (score_out && cudaMemcpyAsync(score_out, score, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return GBSSIM_ERR_CUDA;
+    if (per_scale_out &&
+        cudaMemcpyAsync(per_scale_out, per, 2 * sizeof(double) * S * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return GBSSIM_ERR_CUDA;
+    return GBSSIM_OK;
+}
+
+int gbssim_loss_backward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t multiscale,
+                         double grad_scale, const double *grad_out, int32_t grad_out_per_image, const void *saved,
+                         size_t saved_bytes, void *grad_y, int32_t grad_dtype, int64_t grad_ld,
+                         int64_t grad_image_stride, void *stream) {
+    int rc = check_loss(x, y, p);
+    if (rc) return rc;
+    if (!grad_y || (grad_dtype != GBSSIM_F32 && grad_dtype != GBSSIM_F16 && grad_dtype != GBSSIM_BF16))
+        return GBSSIM_ERR_INVALID_ARG;
+    if (grad_ld < x->width || (x->count > 1 && grad_image_stride < x->height * grad_ld)) return GBSSIM_ERR_INVALID_ARG;
+    if (!isfinite(grad_scale)) return GBSSIM_ERR_INVALID_ARG;
+    SavedPlan Sv;
+    rc = plan_saved(x, p, multiscale != 0, &Sv);
+    if (rc) return rc;
+    if (!saved || saved_bytes < Sv.bytes) return GBSSIM_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)const_cast<void *>(saved);  // the backward writes only the coarse-gradient planes
+    const int n = x->count, S = multiscale ? p->scales : 1;
+    double esum = 0.0;
+    for (int j = 0; j < S; ++j) esum += p->exponents[j];
+    for (int j = S - 1; j >= 0; --j) {
+        const Level &L = Sv.lv.lv[j];
+        ImgDesc dx = desc_of(x), dy = desc_of(y);
+        int dtype = x->dtype;
+        if (j > 0) {
+            const float *px = (const float *)(ws + Sv.plane_off[j]);
+            dx = ImgDesc{px, L.H, L.W, L.W, L.H * L.W};
+            dy = ImgDesc{px + (size_t)L.H * L.W * n, L.H, L.W, L.W, L.H * L.W};
+            dtype = GBSSIM_F32;
+        }
+        const int64_t OH = out_dim(L.H, p->k, 1), OW = out_dim(L.W, p->k, 1);
+        GradLaunch G;
+        memset(&G, 0, sizeof G);
+        G.x = dx;
+        G.y = dy;
+        G.dtype = dtype;
+        G.count = n;
+        G.k = p->k;
+        G.coef = (const float *)(ws + Sv.coef_off[j]);
+        make_taps(p, G.taps.g);
+        G.sx = G.sy = (float)(0.5 * p->L);
+        G.base_scale = grad_scale / ((double)OH * (double)OW);
+        G.grad_out = grad_out;
+        G.grad_out_per_image = grad_out_per_image;
+        if (multiscale) {
+            G.ms_score = (const double *)(ws + Sv.score_off);
+            G.ms_per_scale = (const double *)(ws + Sv.per_off);
+            G.ms_scales = S;
+            G.ms_level = j;
+            G.ms_combine = p->combine;
+            G.ms_beta = p->exponents[j];
+            G.ms_beta_hat = p->exponents[j] / esum;
+        }
+        G.coarse = j + 1 < S ? (const float *)(ws + Sv.grad_off[j + 1]) : nullptr;
+        if (j == 0) {
+            G.out = grad_y;
+            G.out_dtype = grad_dtype;
+            G.out_ld = grad_ld;
+            G.out_is = x->count > 1 ? grad_image_stride : x->height * grad_ld;
+        } else {
+            G.out = ws + Sv.grad_off[j];
+            G.out_dtype = GBSSIM_F32;
+            G.out_ld = L.W;
+            G.out_is = L.H * L.W;
+        }
+        if (launch_grad(G, st) != cudaSuccess) return GBSSIM_ERR_CUDA;
+    }
     return GBSSIM_OK;
 }
 

@@ -327,7 +327,10 @@ cudaError_t launch_rgb_ycbcr(const ImgDesc &r, const ImgDesc &g, const ImgDesc &
 // Temporal pooling of frame-score series (k_series.cu).
 cudaError_t launch_series_pool(const double *scores, int n, int count, int64_t stride, int kind, double a0,
                                double a1, double *out, cudaStream_t st);
+constexpr int kPoolLW = 100;       // internal kind: luminance-weighted pooling (aux = mu_1 map)
 cudaError_t launch_pool_map(const float *map, int64_t h, int64_t w, int64_t ld, int count, int64_t is, int kind,
-                            double a0, double a1, char *ws, double *out, cudaStream_t st);
+                            double a0, double a1, char *ws, double *out, cudaStream_t st, const float *aux = nullptr);
+cudaError_t launch_local_mean(const ImgDesc &x, int dtype, int count, const TapsDyn &taps, int k, int s, float *out,
+                              int64_t out_ld, int64_t out_is, cudaStream_t st);
 
 }  // namespace gbssim

@@ -47,13 +47,19 @@ __device__ __forceinline__ float key2f(unsigned k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-enum MomentOp { M_SUM = 0, M_SQDEV = 1, M_ABSDEV_P = 2, M_MINK = 3, M_DW = 4, M_LOG_D = 5, M_INV_D = 6, M_PP = 7 };
+enum MomentOp { M_SUM = 0, M_SQDEV = 1, M_ABSDEV_P = 2, M_MINK = 3, M_DW = 4, M_LOG_D = 5, M_INV_D = 6, M_PP = 7,
+                M_LW = 8 };
 
 // Per-element contribution (a, b) of moment op `op`; m = the image's mean
-// (or the PP threshold), p, r = arguments.
-__device__ __forceinline__ void contrib(int op, float q, float m, float p, float r, float &a, float &b) {
+// (or the PP threshold), p, r = arguments; mu = the auxiliary map's value
+// (luminance-weighted pooling: the reference's local mean, p = a_s, r = b_s).
+__device__ __forceinline__ void contrib(int op, float q, float m, float p, float r, float mu, float &a, float &b) {
     b = 0.f;
     switch (op) {
+    case M_LW: {
+        const float wl = mu < p ? 0.f : (mu < p + r ? (mu - p) / r : 1.f);
+        a = wl * q;
+    } break;
     case M_SUM: a = q; break;
     case M_SQDEV: { const float d = q - m; a = d * d; } break;
     case M_ABSDEV_P: a = powf(fabsf(q - m), p); break;
@@ -91,11 +97,12 @@ __device__ __forceinline__ void block_sum2d(double &a, double &b, double *red) {
 
 __global__ void __launch_bounds__(NT) moment_kernel(const float *map, int64_t h, int64_t w, int64_t ld, int64_t is,
                                                     int items, int op, const double *center, float p, float r,
-                                                    double2 *partials) {
+                                                    const float *aux, double2 *partials) {
     __shared__ double red[2 * NT / 32];
     const int img = blockIdx.y;
     const int64_t r0 = (int64_t)blockIdx.x * PR;
     const float *m = map + img * is;
+    const float *ax = aux ? aux + img * is : nullptr;
     float c = 0.f;
     if (center) {
         // the largest float not above the (double) centre: for float q,
@@ -107,18 +114,20 @@ __global__ void __launch_bounds__(NT) moment_kernel(const float *map, int64_t h,
     KSumP sa, sb;
     for (int64_t row = r0; row < min(r0 + PR, h); ++row) {
         const float *rp = m + row * ld;
+        const float *ap = ax ? ax + row * ld : nullptr;
         for (int64_t c0 = 0; c0 < w; c0 += UNR * NT) {
-            float v[UNR];
+            float v[UNR], u[UNR];
 #pragma unroll
             for (int k = 0; k < UNR; ++k) {  // all loads first
                 const int64_t col = c0 + threadIdx.x + k * NT;
                 v[k] = col < w ? __ldg(rp + col) : 0.f;
+                u[k] = ap && col < w ? __ldg(ap + col) : 0.f;
             }
 #pragma unroll
             for (int k = 0; k < UNR; ++k)
                 if (c0 + threadIdx.x + k * NT < w) {
                     float a, b;
-                    contrib(op, v[k], c, p, r, a, b);
+                    contrib(op, v[k], c, p, r, u[k], a, b);
                     sa.add(a);
                     sb.add(b);
                 }
@@ -331,7 +340,40 @@ __global__ void select_finalize_kernel(const SelState *st, int count, double n, 
     }
 }
 
+// Window-weighted local mean of one image per output (Eq. local_means):
+// sum_m g_m sum_n g_n x(i s + m, j s + n), the separable weights in fp32.
+template <typename T>
+__global__ void local_mean_kernel(ImgDesc x, TapsDyn taps, int k, int s, float *out, int64_t out_ld,
+                                  int64_t out_is) {
+    const int64_t oh = (x.H - k) / s + 1, ow = (x.W - k) / s + 1;
+    const int img = blockIdx.z;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+    if (j >= ow || i >= oh) return;
+    const T *b = static_cast<const T *>(x.data) + img * x.image_stride + i * s * x.row_stride + j * s;
+    float acc = 0.f;
+    for (int m = 0; m < k; ++m) {
+        float hsum = 0.f;
+        for (int n = 0; n < k; ++n) hsum = fmaf(taps.g[n], load_f32<T>(b + m * x.row_stride + n), hsum);
+        acc = fmaf(taps.g[m], hsum, acc);
+    }
+    out[img * out_is + i * out_ld + j] = acc;
+}
+
 }  // namespace
+
+cudaError_t launch_local_mean(const ImgDesc &x, int dtype, int count, const TapsDyn &taps, int k, int s, float *out,
+                              int64_t out_ld, int64_t out_is, cudaStream_t st) {
+    const int64_t oh = (x.H - k) / s + 1, ow = (x.W - k) / s + 1;
+    const dim3 grid((unsigned)((ow + 127) / 128), (unsigned)oh, count);
+    switch (dtype) {
+    case GBSSIM_U8: local_mean_kernel<uint8_t><<<grid, 128, 0, st>>>(x, taps, k, s, out, out_ld, out_is); break;
+    case GBSSIM_F16: local_mean_kernel<__half><<<grid, 128, 0, st>>>(x, taps, k, s, out, out_ld, out_is); break;
+    case GBSSIM_BF16: local_mean_kernel<__nv_bfloat16><<<grid, 128, 0, st>>>(x, taps, k, s, out, out_ld, out_is); break;
+    case GBSSIM_F32: local_mean_kernel<float><<<grid, 128, 0, st>>>(x, taps, k, s, out, out_ld, out_is); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 // Workspace: partials, per-image centre, selection state, histograms.
 PoolLayout pool_layout(int64_t h, int64_t w, int count) {
@@ -352,7 +394,7 @@ PoolLayout pool_layout(int64_t h, int64_t w, int count) {
 }
 
 cudaError_t launch_pool_map(const float *map, int64_t h, int64_t w, int64_t ld, int count, int64_t is, int kind,
-                            double a0, double a1, char *ws, double *out, cudaStream_t st) {
+                            double a0, double a1, char *ws, double *out, cudaStream_t st, const float *aux) {
     const PoolLayout L = pool_layout(h, w, count);
     double2 *part = reinterpret_cast<double2 *>(ws + L.partials);
     double *center = reinterpret_cast<double *>(ws + L.center);
@@ -363,7 +405,7 @@ cudaError_t launch_pool_map(const float *map, int64_t h, int64_t w, int64_t ld, 
     const int fb = (count + 127) / 128;
     cudaError_t e = cudaSuccess;
     auto moment = [&](int op, const double *c, double p, double r, int kindv, int stage) {
-        moment_kernel<<<grid, NT, 0, st>>>(map, h, w, ld, is, L.items, op, c, (float)p, (float)r, part);
+        moment_kernel<<<grid, NT, 0, st>>>(map, h, w, ld, is, L.items, op, c, (float)p, (float)r, aux, part);
         moment_finalize_kernel<<<fb, 128, 0, st>>>(part, L.items, count, n, kindv, p, a1, stage, center, out);
         return cudaGetLastError();
     };
@@ -399,6 +441,7 @@ cudaError_t launch_pool_map(const float *map, int64_t h, int64_t w, int64_t ld, 
         e = select(a0);
         if (e == cudaSuccess) e = moment(M_PP, center, 0, a1, kind, 1);
         break;
+    case kPoolLW: e = moment(M_LW, nullptr, a0, a1, kind, 1); break;  // sum w(mu) Q / n
     default: e = cudaErrorInvalidValue;
     }
     return e;

@@ -104,6 +104,13 @@ _SIGS = {
     "gbssim_downscale_factor": ([_i64, _i64, _i32], ctypes.c_int),
     "gbssim_downscale": ([_P(Plane), _i32, _vp, _i64, _i64, _vp], ctypes.c_int),
     "gbssim_rgb_to_ycbcr": ([_P(Plane), _P(Plane), _P(Plane), _vp, _vp, _vp, _i64, _i64, _vp], ctypes.c_int),
+    "gbssim_loss_saved_size": ([_P(Plane), _P(Params), _i32, _P(_sz)], ctypes.c_int),
+    "gbssim_local_mean": ([_P(Plane), _P(Params), _vp, _i64, _i64, _vp], ctypes.c_int),
+    "gbssim_ssim_pool_lw": ([_vp, _vp, _i64, _i64, _i64, _i32, _i64, ctypes.c_double, ctypes.c_double, _vp, _vp, _sz,
+                             _vp], ctypes.c_int),
+    "gbssim_loss_forward": ([_P(Plane), _P(Plane), _P(Params), _i32, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "gbssim_loss_backward": ([_P(Plane), _P(Plane), _P(Params), _i32, ctypes.c_double, _vp, _i32, _vp, _sz, _vp,
+                              _i32, _i64, _i64, _vp], ctypes.c_int),
     "gbssim_ssim3d": ([_P(Plane), _P(Plane), _P(Params), _i32, _vp, _vp, _vp, _i64, _i64, _vp, _sz, _vp],
                       ctypes.c_int),
     "gbssim_msssim_host": ([_P(Plane), _P(Plane), _P(Params), _i32, _vp, _vp, _sz, _vp, _vp, _vp], ctypes.c_int),
@@ -365,6 +372,38 @@ def ssim_pool(qmap: torch.Tensor, kind: str = "mean", *args: float, ws: torch.Te
     return out
 
 
+def local_mean(x: torch.Tensor, **kw) -> torch.Tensor:
+    """Window-weighted local mean (gbssim_local_mean) of (H, W) or (N, H, W)
+    CUDA planes at every valid strided position; keyword arguments as
+    make_params (window, k, sigma, stride)."""
+    xb = _as_batch(x)
+    p = make_params(**kw)
+    n, h, w = xb.shape
+    oh, ow = out_shape(h, w, p.k, p.stride)
+    out = torch.empty((n, oh, ow), dtype=torch.float32, device=xb.device)
+    px = plane(xb)
+    _check(lib.gbssim_local_mean(ctypes.byref(px), ctypes.byref(p), out.data_ptr(), ow, oh * ow, _stream(xb.device)),
+           "gbssim_local_mean")
+    return out if x.dim() != 2 else out[0]
+
+
+def ssim_pool_lw(qmap: torch.Tensor, mu_ref: torch.Tensor, a: float, b: float) -> torch.Tensor:
+    """Luminance-weighted pooling (gbssim_ssim_pool_lw) of float maps with the
+    reference's local-mean maps of the same shape."""
+    m = qmap if qmap.dim() == 3 else qmap.unsqueeze(0)
+    u = mu_ref if mu_ref.dim() == 3 else mu_ref.unsqueeze(0)
+    m, u = m.contiguous(), u.contiguous()
+    if m.shape != u.shape or m.dtype != torch.float32 or u.dtype != torch.float32:
+        raise ValueError("expected float32 maps of one shape")
+    n, h, w = m.shape
+    px = Plane(m.data_ptr(), F32, n, h, w, w, h * w)
+    ws = workspace(px, Params(), OP_POOL, m.device)
+    out = torch.empty(n, dtype=torch.float64, device=m.device)
+    _check(lib.gbssim_ssim_pool_lw(m.data_ptr(), u.data_ptr(), h, w, w, n, h * w, float(a), float(b), out.data_ptr(),
+                                   ws.data_ptr(), ws.numel(), _stream(m.device)), "gbssim_ssim_pool_lw")
+    return out
+
+
 def series_pool(scores: torch.Tensor, kind: str = "mean", *args: float) -> torch.Tensor:
     """Temporal pooling (gbssim_series_pool) of frame-score series (T,) or
     (N, T) on the GPU into one double each.  kind is a key of POOL_KINDS;
@@ -507,32 +546,51 @@ def ssim_backward(x: torch.Tensor, y: torch.Tensor, multiscale: bool = False, gr
 
 class _SSIMLossFn(torch.autograd.Function):
     """loss = 1 - mean over pairs of SSIM (or MS-SSIM); gradient w.r.t. y only
-    (x is the reference).  The backward recomputes the window moments in the
-    library; nothing but x and y is saved."""
+    (x is the reference).  The forward (gbssim_loss_forward) runs each level
+    once in coefficient mode and keeps the coefficient maps, the pyramid and
+    the pooled values in a device buffer; the backward (gbssim_loss_backward)
+    runs only the gradient kernels from it."""
 
     @staticmethod
     def forward(ctx, x, y, multiscale, kw):
+        xb, yb = _as_batch(x), _as_batch(y)
+        if xb.stride() != yb.stride():
+            xb, yb = xb.contiguous(), yb.contiguous()
+        kw = dict(kw)
         if multiscale:
-            score, per = msssim(x, y, per_scale=True, **kw)
-            ctx.save_for_backward(x, y, score, per)   # pooled scalars only
-        else:
-            score = ssim(x, y, **kw)
-            ctx.save_for_backward(x, y)
+            kw.setdefault("exponents", MSSSIM_EXPONENTS[: kw.get("scales", 5)])
+        p = make_params(**kw)
+        px, py = plane(xb), plane(yb)
+        dev = xb.device
+        nb = ctypes.c_size_t()
+        _check(lib.gbssim_loss_saved_size(ctypes.byref(px), ctypes.byref(p), int(multiscale), ctypes.byref(nb)),
+               "gbssim_loss_saved_size")
+        saved = torch.empty(max(int(nb.value), 1), dtype=torch.uint8, device=dev)
+        score = torch.empty(xb.shape[0], dtype=torch.float64, device=dev)
+        _check(lib.gbssim_loss_forward(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p), int(multiscale),
+                                       score.data_ptr(), None, saved.data_ptr(), saved.numel(), _stream(dev)),
+               "gbssim_loss_forward")
+        ctx.save_for_backward(xb, yb, saved)
         ctx.multiscale = multiscale
-        ctx.kw = kw
+        ctx.params = p
+        ctx.y_shape = y.shape
         ctx.n = score.numel()
         return 1.0 - score.mean()
 
     @staticmethod
     def backward(ctx, grad_loss):
-        saved = ctx.saved_tensors
-        x, y = saved[0], saved[1]
         if not ctx.needs_input_grad[1]:
             return None, None, None, None
-        extra = dict(fwd_score=saved[2], fwd_per_scale=saved[3]) if ctx.multiscale else {}
-        g = ssim_backward(x, y, multiscale=ctx.multiscale, grad_scale=-1.0 / ctx.n, grad_out=grad_loss,
-                          grad_dtype=y.dtype, **extra, **ctx.kw)
-        return None, g, None, None
+        xb, yb, saved = ctx.saved_tensors
+        n, h, w = yb.shape
+        g = torch.empty((n, h, w), dtype=yb.dtype, device=yb.device)
+        go = grad_loss.to(torch.float64).contiguous()
+        px, py = plane(xb), plane(yb)
+        _check(lib.gbssim_loss_backward(ctypes.byref(px), ctypes.byref(py), ctypes.byref(ctx.params),
+                                        int(ctx.multiscale), -1.0 / ctx.n, go.data_ptr(), 0, saved.data_ptr(),
+                                        saved.numel(), g.data_ptr(), _GDT[yb.dtype], w, h * w, _stream(yb.device)),
+               "gbssim_loss_backward")
+        return None, g.reshape(ctx.y_shape), None, None
 
 
 class SSIMLoss(torch.nn.Module):

@@ -176,3 +176,22 @@ def test_backward_rejects_unsupported(g):
     with pytest.raises(g.GbssimError) as e:
         g.ssim_backward(x, x, k=33, sigma=5.0)
     assert e.value.status == g.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("multiscale,dtype", [(False, torch.float32), (True, torch.float32), (False, torch.bfloat16)])
+def test_saved_loss_path_equals_recompute_path(g, synth, multiscale, dtype):
+    """SSIMLoss keeps the forward's coefficient maps (gbssim_loss_forward /
+    gbssim_loss_backward); its gradient must match gbssim_ssim_backward, which
+    recomputes them."""
+    x, y = synth.loss_pairs_float(2, 2, 190, 200)
+    xd, yd = x.to(DEV, dtype), y.to(DEV, dtype).requires_grad_(True)
+    loss = g.SSIMLoss(multiscale=multiscale, L=1.0)(xd, yd)
+    loss.backward()
+    xs, ys = xd.detach().reshape(4, 190, 200), yd.detach().reshape(4, 190, 200)
+    kw = dict(exponents=g.MSSSIM_EXPONENTS) if multiscale else {}
+    ref = g.ssim_backward(xs, ys, multiscale=multiscale, grad_scale=-0.25, L=1.0, grad_dtype=torch.float32, **kw)
+    got = yd.grad.reshape(4, 190, 200).float()
+    tol = 1e-6 if dtype == torch.float32 else 1e-2
+    assert (got - ref).abs().max().item() <= tol * ref.abs().max().item()
+    score = (g.msssim if multiscale else g.ssim)(xs, ys, L=1.0)
+    assert abs(loss.item() - (1.0 - score.mean().item())) <= 1e-7

@@ -106,3 +106,34 @@ def test_pitched_maps_and_full_size(g):
     got = g.ssim_pool(view, "cov").cpu().tolist()
     for a, b in zip(got, _refs(q, P.cov)):
         assert abs(a - b) <= 1e-6 * max(1.0, abs(b))
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(window="box", k=8, stride=4), dict(window="gaussian", k=7, sigma=1.0)])
+def test_local_mean_matches_oracle(g, kw):
+    import oracle
+    from paper_2101_06354_gb300 import synth
+
+    x, _ = synth.luma_pairs_u8(2, 90, 117)
+    got = g.local_mean(x.to(DEV), **kw).cpu().double().numpy()
+    k, s = kw.get("k", 11), kw.get("stride", 1)
+    w = oracle.window(kw.get("window", "gaussian"), k, kw.get("sigma", 1.5))
+    for i in range(2):
+        ref = P.local_mean(x[i].numpy(), w, s)
+        assert np.abs(got[i] - ref).max() <= 1e-6 * 255
+
+
+@pytest.mark.parametrize("a,b", [(0.0, 0.0), (40.0, 30.0), (100.0, 50.0), (60.0, 0.0)])
+def test_luminance_weighted_pooling(g, maps, a, b):
+    from paper_2101_06354_gb300 import synth
+
+    x, y = synth.luma_pairs_u8(3, 200, 232)
+    _, q = g.ssim(x.to(DEV), y.to(DEV), return_map=True)
+    mu = g.local_mean(x.to(DEV))
+    got = g.ssim_pool_lw(q, mu, a, b).cpu().tolist()
+    qn, mn = q.double().cpu().numpy(), mu.double().cpu().numpy()
+    for i in range(3):
+        ref = P.lw(qn[i], mn[i], a, b)
+        assert abs(got[i] - ref) <= 1e-6, (a, b, got[i], ref)
+    base = g.ssim_pool(q, "mean").cpu().tolist()
+    if a == 0.0 and b == 0.0:
+        assert all(abs(u - v) <= 1e-7 for u, v in zip(got, base))

@@ -104,3 +104,15 @@ def test_luminance_weights_piecewise():
 
 def test_dw_all_perfect_is_nan():
     assert math.isnan(P.dw(np.ones(6), 1.0))
+
+
+def test_local_mean_is_the_window_statistic():
+    import oracle
+
+    r = _rng(9)
+    x = r.uniform(0, 255, (30, 41))
+    y = r.uniform(0, 255, (30, 41))
+    for kind, k, s in (("gaussian", 11, 1), ("box", 8, 4), ("gaussian", 7, 2)):
+        w = oracle.window(kind, k, 1.5 if k == 11 else 1.0)
+        st = oracle.window_stats(x, y, w, s)
+        np.testing.assert_allclose(P.local_mean(x, w, s), st["mu1"], rtol=0, atol=1e-10)
