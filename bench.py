@@ -294,6 +294,13 @@ def run_extras(args, gbssim, synth, x, y, dev, timed, ws):
     out["ssim3d_4k_y"] = {"value": ws * px3 / (t3 / 1e3) / 1e6, "unit": UNIT, "ms_per_video": t3, "frames": 120,
                           "kt": 5, "k": 11, "hbm_gbs": 2 * px3 / (t3 / 1e3) / 1e9,
                           "hbm_frac": 2 * px3 / (t3 / 1e3) / 1e9 / hbm_peak, "score": s3.item()}
+    # MS-SSIM-3D: the same windows on the 5 levels of each frame's pyramid
+    fn4 = lambda: gbssim.msssim3d(v3x, v3y, kt=5, k=11, scales=5)
+    fn4()
+    t4 = timed(fn4, kk) / kk
+    s4, _ = fn4()
+    out["msssim3d_4k_y"] = {"value": ws * px3 / (t4 / 1e3) / 1e6, "unit": UNIT, "ms_per_video": t4, "frames": 120,
+                            "kt": 5, "k": 11, "scales": 5, "score": s4.item()}
     del v, vx, vy
     return out
 
@@ -423,7 +430,10 @@ def run_case(args):
     for profilers: scale0 = gbssim_ssim_map on the 64 1080p pairs (the
     scale-0 Gaussian level); box8s4 = the 8x8 stride-4 box SSIM on them;
     loss = SSIMLoss forward + backward on 32x3x512x512 fp32; ssim3d = SSIM-3D
-    (11 x 11 x 5) of 40 luma frames of 1920x1080.  Prints one JSON
+    (11 x 11 x 5) of 40 luma frames of 1920x1080; msssim3d = MS-SSIM-3D (5
+    scales) of the same frames; ragged = one MS-SSIM run of a batch plan
+    over 72 ragged pairs (64 drawn from the six resolutions, 8 odd sizes;
+    default tuning).  Prints one JSON
     line with the mean time per call (CUDA events)."""
     import torch
 
@@ -439,10 +449,18 @@ def run_case(args):
         kw = {} if args.case == "scale0" else dict(window="box", k=8, stride=4)
         wsc = gbssim.workspace(gbssim.plane(x), gbssim.make_params(**kw), gbssim.OP_SSIM, dev)
         fn = lambda: gbssim.ssim(x, y, ws=wsc, **kw)
-    elif args.case == "ssim3d":
+    elif args.case in ("ssim3d", "msssim3d"):
         v = synth.video_yuv420_u8(40, H, W)
         vx, vy = v["y"][0].contiguous().to(dev), v["y"][1].contiguous().to(dev)
-        fn = lambda: gbssim.ssim3d(vx, vy, kt=5, k=11)
+        if args.case == "ssim3d":
+            fn = lambda: gbssim.ssim3d(vx, vy, kt=5, k=11)
+        else:
+            fn = lambda: gbssim.msssim3d(vx, vy, kt=5, k=11, scales=5)
+    elif args.case == "ragged":
+        sizes = synth.ragged_sizes(64, 8)
+        xs, ys = synth.ragged_pairs_u8(sizes, device=dev)
+        plan = gbssim.BatchPlan(xs, ys, multiscale=True)
+        fn = plan.run
     else:
         lx, ly = synth.loss_pairs_float(32, 3, 512, 512)
         xd, yd = lx.to(dev), ly.to(dev).requires_grad_(True)
@@ -473,7 +491,7 @@ def main():
     ap.add_argument("--impl", default="gbssim", choices=["gbssim", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the box-window and loss fwd+bwd figures")
-    ap.add_argument("--case", choices=["scale0", "box8s4", "loss", "ssim3d"], default=None,
+    ap.add_argument("--case", choices=["scale0", "box8s4", "loss", "ssim3d", "msssim3d", "ragged"], default=None,
                     help="run one secondary workload alone (for profilers) instead of the benchmark")
     args = ap.parse_args()
     if args.case:

@@ -271,6 +271,33 @@ int gbssim_ssim3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_par
                   double *frame_out, double *score_out, float *map_out, int64_t map_ld, int64_t map_frame_stride,
                   void *workspace, size_t workspace_bytes, void *stream);
 
+/* MS-SSIM-3D of a uint8 video pair (Section "Spatio-Temporal SSIM": the 3-D
+ * index computed over several spatial scales).  Every frame has its own 2x2
+ * average pyramid (floor sizes, as gbssim_msssim); level j of the video is
+ * the T frames at pyramid level j, and gbssim_ssim3d's k x k x kt box
+ * statistics on it give the cs and Q maps of the T-kt+1 output frames.  Per
+ * output frame, m_j = mean cs_j (j < S) and m_S = mean Q_S are combined like
+ * MS-SSIM (product of m_j^beta_j, or the normalised sum); the video score is
+ * the mean over output frames.  Pyramid values are multiples of 4^-j: the
+ * window sums stay exact (int64 sums of the values times 4^j).
+ *   p             : window = GBSSIM_WIN_BOX, k <= 29, stride 1; scales,
+ *                   exponents and combine as for gbssim_msssim.
+ *   kt            : frames per window, 1 <= kt <= T, with the exact-integer
+ *                   ranges k^2 kt 255^2 < 2^31 and, at every level j >= 1,
+ *                   2 (k^2 kt)^2 (255 4^j)^2 < 2^62.
+ *   frame_out     : nullable; T-kt+1 doubles, the score of each output frame.
+ *   score_out     : nullable; one double, the mean of the frame scores.
+ *   per_scale_out : nullable; (T-kt+1) * scales * 2 doubles, (mean cs_j,
+ *                   mean Q_j) of each output frame and scale, finest first.
+ *   workspace     : gbssim_msssim3d_workspace_size bytes (tile partials and
+ *                   the float pyramid, 4/3 of the input's bytes per video).
+ * Errors: as gbssim_ssim3d, GBSSIM_ERR_TOO_SMALL if a level is below k x k,
+ * GBSSIM_ERR_UNSUPPORTED for T > 65535 with more than one scale. */
+int gbssim_msssim3d_workspace_size(const gbssim_plane *x, const gbssim_params *p, int32_t kt, size_t *bytes);
+int gbssim_msssim3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t kt,
+                    double *frame_out, double *score_out, double *per_scale_out, void *workspace,
+                    size_t workspace_bytes, void *stream);
+
 /* MS-SSIM of each pair (Introduction; Section "Salient Features of SSIM and
  * MS-SSIM Implementations"): scale 1 is the input, scale j+1 the 2x2 average
  * of scale j (floor size); the contrast-structure term is mean-pooled at every

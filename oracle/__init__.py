@@ -237,6 +237,57 @@ def ssim3d(x, y, k: int = 11, kt: int = 5, K1: float = 0.01, K2: float = 0.03, L
     return float(frames.sum() / frames.size), frames, q
 
 
+def _box3d_stats(x, y, k: int, kt: int):
+    """Means, variances and covariance over every k x k x kt neighbourhood of
+    a float video pair (T, H, W), by direct fp64 summation of the window."""
+    a, b = _f64(x), _f64(y)
+    T, H, W = a.shape
+    ot, oh, ow = T - kt + 1, H - k + 1, W - k + 1
+    s = [np.zeros((ot, oh, ow)) for _ in range(5)]
+    for o in range(kt):
+        for m in range(k):
+            for n in range(k):
+                pa, pb = a[o:o + ot, m:m + oh, n:n + ow], b[o:o + ot, m:m + oh, n:n + ow]
+                s[0] += pa
+                s[1] += pb
+                s[2] += pa * pa
+                s[3] += pb * pb
+                s[4] += pa * pb
+    N = float(k * k * kt)
+    mu1, mu2 = s[0] / N, s[1] / N
+    return mu1, mu2, s[2] / N - mu1 * mu1, s[3] / N - mu2 * mu2, s[4] / N - mu1 * mu2
+
+
+def msssim3d(x, y, k: int = 11, kt: int = 5, scales: int = 5, exponents=MSSSIM_EXPONENTS,
+             combine: str = "product", K1: float = 0.01, K2: float = 0.03, L: float = 255.0):
+    """MS-SSIM-3D (Section "Spatio-Temporal SSIM": 3-D SSIM computed over
+    multiple spatial scales) of a video pair (T, H, W).  Reading: each frame
+    has its own 2x2 average pyramid; at every level the k x k x kt box
+    statistics give cs and Q maps for the T-kt+1 output frames; per output
+    frame, m_j = mean cs_j (j < S) and m_S = mean Q_S are combined as in
+    MS-SSIM; the video score is the temporal mean.  Returns (video score,
+    per-frame scores, per-level (T-kt+1, 2) of (mean cs_j, mean Q_j))."""
+    exps = np.asarray(exponents[:scales], np.float64)
+    C1, C2 = constants(K1, K2, L)
+    a, b = _f64(x), _f64(y)
+    per = []
+    for j in range(scales):
+        mu1, mu2, v1, v2, cv = _box3d_stats(a, b, k, kt)
+        lum = (2 * mu1 * mu2 + C1) / (mu1 * mu1 + mu2 * mu2 + C1)
+        cs = (2 * cv + C2) / (v1 + v2 + C2)
+        per.append(np.stack([cs.mean(axis=(1, 2)), (lum * cs).mean(axis=(1, 2))], axis=1))
+        if j + 1 < scales:
+            a = np.stack([downsample2x2(f) for f in a])
+            b = np.stack([downsample2x2(f) for f in b])
+    m = np.stack([per[j][:, 0] for j in range(scales - 1)] + [per[-1][:, 1]], axis=1)
+    if combine == "product":
+        with np.errstate(invalid="ignore"):
+            frames = np.prod(np.power(m, exps), axis=1)
+    else:
+        frames = (m * (exps / exps.sum())).sum(axis=1)
+    return float(frames.sum() / frames.size), frames, per
+
+
 def downsample2x2(img) -> np.ndarray:
     """2x2 average pooling, floor size (Daala / Scikit-Video / Tensorflow MS-SSIM)."""
     img = _f64(img)

@@ -725,62 +725,176 @@ int gbssim_series_pool(const double *scores, int32_t n, int32_t count, int64_t s
 }
 
 namespace {
-int check_ssim3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t kt) {
+// Checks shared by SSIM-3D (scales = 1) and MS-SSIM-3D.
+int check_ssim3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t kt, int scales) {
     int rc = check_pair(x, y);
     if (rc) return rc;
     rc = check_params(p);
     if (rc) return rc;
-    if (x->dtype != GBSSIM_U8 || p->window != GBSSIM_WIN_BOX || p->stride != 1 || p->k > kSsim3dMaxK)
+    if (x->dtype != GBSSIM_U8 || p->window != GBSSIM_WIN_BOX || p->stride != 1 ||
+        p->k > (scales > 1 ? kSsim3dMaxK64 : kSsim3dMaxK))
         return GBSSIM_ERR_UNSUPPORTED;
     if (kt < 1) return GBSSIM_ERR_INVALID_ARG;
-    if (x->count < kt || x->height < p->k || x->width < p->k) return GBSSIM_ERR_TOO_SMALL;
-    // exact int32 window sums: k^2 kt 255^2 < 2^31
-    if ((double)p->k * p->k * kt * 65025.0 >= 2147483648.0) return GBSSIM_ERR_UNSUPPORTED;
+    if (x->count < kt) return GBSSIM_ERR_TOO_SMALL;
+    for (int j = 0; j < scales; ++j)
+        if ((x->height >> j) < p->k || (x->width >> j) < p->k) return GBSSIM_ERR_TOO_SMALL;
+    const double n = (double)p->k * p->k * kt;
+    // level 0: exact int32 window sums, N 255^2 < 2^31
+    if (n * 65025.0 >= 2147483648.0) return GBSSIM_ERR_UNSUPPORTED;
+    // level j >= 1: values times 4^j are integers up to M = 255 4^j; every int64
+    // numerator is at most 2 N^2 M^2, kept below 2^62
+    for (int j = 1; j < scales; ++j) {
+        const double m = 255.0 * (double)(1 << (2 * j));
+        if (2.0 * n * n * m * m >= 4611686018427387904.0) return GBSSIM_ERR_UNSUPPORTED;
+    }
+    if (scales > 1 && x->count > 65535) return GBSSIM_ERR_UNSUPPORTED;  // pyramid grid's z extent
     return GBSSIM_OK;
 }
 
-size_t ssim3d_ws_bytes(const gbssim_plane *x, const gbssim_params *p, int32_t kt) {
-    int tx, ty;
-    ssim3d_tiles(x->height, x->width, p->k, &tx, &ty);
-    return align_up(sizeof(double) * (size_t)(x->count - kt + 1) * tx * ty);
+struct Ms3dPlan {
+    int frames, scales;
+    int64_t H[GBSSIM_MAX_SCALES], W[GBSSIM_MAX_SCALES];
+    int tiles[GBSSIM_MAX_SCALES];
+    size_t partials[GBSSIM_MAX_SCALES], pyr_x[GBSSIM_MAX_SCALES], pyr_y[GBSSIM_MAX_SCALES], frame_buf, bytes;
+};
+
+// Workspace: per level the (frame, tile) partials, one frame-score buffer,
+// then the float pyramid levels 1..S-1 of x and y (T dense frames each).
+Ms3dPlan plan_ms3d(const gbssim_plane *x, const gbssim_params *p, int32_t kt, int scales) {
+    Ms3dPlan P{};
+    P.frames = x->count - kt + 1;
+    P.scales = scales;
+    size_t off = 0;
+    for (int j = 0; j < scales; ++j) {
+        P.H[j] = x->height >> j;
+        P.W[j] = x->width >> j;
+        int tx, ty;
+        ssim3d_tiles(P.H[j], P.W[j], p->k, &tx, &ty);
+        P.tiles[j] = tx * ty;
+        P.partials[j] = off;
+        off = align_up(off + sizeof(double2) * (size_t)P.frames * P.tiles[j]);
+    }
+    P.frame_buf = off;
+    off = align_up(off + sizeof(double) * (size_t)P.frames);
+    for (int j = 1; j < scales; ++j) {
+        const size_t plane = sizeof(float) * (size_t)P.H[j] * P.W[j] * x->count;
+        P.pyr_x[j] = off;
+        off = align_up(off + plane);
+        P.pyr_y[j] = off;
+        off = align_up(off + plane);
+    }
+    P.bytes = off;
+    return P;
+}
+
+// SSIM-3D on every level of the frames' 2x2 pyramid, then the per-frame
+// combination (the MS-SSIM finaliser over frames) and the video mean.
+int run_ms3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t kt, int scales,
+             const double *exps, int combine, double *frame_out, double *score_out, double *per_scale_out,
+             float *map_out, int64_t map_ld, int64_t map_frame_stride, void *workspace, size_t workspace_bytes,
+             cudaStream_t st) {
+    const Ms3dPlan P = plan_ms3d(x, p, kt, scales);
+    if (!workspace || workspace_bytes < P.bytes) return GBSSIM_ERR_WORKSPACE;
+    char *ws = static_cast<char *>(workspace);
+    const double n = (double)p->k * p->k * kt;
+    const double c1 = (p->K1 * p->L) * (p->K1 * p->L), c2 = (p->K2 * p->L) * (p->K2 * p->L);
+    MsFinalize F{};
+    F.scales = scales;
+    F.count = P.frames;
+    F.combine = combine;
+    for (int j = 0; j < scales; ++j) {
+        F.exps[j] = exps[j];
+        Ssim3dLaunch L{};
+        const bool level0 = j == 0;
+        if (level0) {
+            L.x = desc_of(x);
+            L.y = desc_of(y);
+            L.vec4 = (uintptr_t)x->data % 4 == 0 && (uintptr_t)y->data % 4 == 0 && L.x.row_stride % 4 == 0 &&
+                     L.x.image_stride % 4 == 0;
+            L.scale = 1.f;
+        } else {
+            // level j from level j-1: uint8 input or the float level below
+            const ImgDesc src_x = j == 1 ? desc_of(x)
+                                         : ImgDesc{ws + P.pyr_x[j - 1], P.H[j - 1], P.W[j - 1], P.W[j - 1],
+                                                   P.H[j - 1] * P.W[j - 1]};
+            const ImgDesc src_y = j == 1 ? desc_of(y)
+                                         : ImgDesc{ws + P.pyr_y[j - 1], P.H[j - 1], P.W[j - 1], P.W[j - 1],
+                                                   P.H[j - 1] * P.W[j - 1]};
+            const int dt = j == 1 ? GBSSIM_U8 : GBSSIM_F32;
+            cudaError_t e = launch_downsample(src_x, dt, x->count, (float *)(ws + P.pyr_x[j]), st);
+            if (e == cudaSuccess) e = launch_downsample(src_y, dt, x->count, (float *)(ws + P.pyr_y[j]), st);
+            if (e != cudaSuccess) return GBSSIM_ERR_CUDA;
+            L.x = ImgDesc{ws + P.pyr_x[j], P.H[j], P.W[j], P.W[j], P.H[j] * P.W[j]};
+            L.y = ImgDesc{ws + P.pyr_y[j], P.H[j], P.W[j], P.W[j], P.H[j] * P.W[j]};
+            L.vec4 = P.W[j] % 4 == 0 && (uintptr_t)L.x.data % 16 == 0 && (uintptr_t)L.y.data % 16 == 0;
+            L.scale = (float)(1 << (2 * j));
+        }
+        const double sc2 = (double)L.scale * L.scale;
+        L.T = x->count;
+        L.k = p->k;
+        L.kt = kt;
+        L.map = level0 ? map_out : nullptr;
+        L.map_ld = map_ld;
+        L.map_fs = map_frame_stride;
+        L.partials = (double2 *)(ws + P.partials[j]);
+        L.C1n2 = (float)(c1 * sc2 * n * n);
+        L.C2n2 = (float)(c2 * sc2 * n * n);
+        if (launch_ssim3d_level(L, level0, st) != cudaSuccess) return GBSSIM_ERR_CUDA;
+        F.lv[j].partials = L.partials;
+        F.lv[j].items_per_image = P.tiles[j];
+        F.lv[j].inv_n = 1.0 / ((double)(P.H[j] - p->k + 1) * (double)(P.W[j] - p->k + 1));
+    }
+    double *frames = frame_out ? frame_out : (double *)(ws + P.frame_buf);
+    F.score_out = frames;
+    F.per_scale_out = per_scale_out;
+    if (launch_finalize_msssim(F, st) != cudaSuccess) return GBSSIM_ERR_CUDA;
+    if (score_out && launch_frame_mean(frames, P.frames, score_out, st) != cudaSuccess) return GBSSIM_ERR_CUDA;
+    return GBSSIM_OK;
 }
 }  // namespace
 
 int gbssim_ssim3d_workspace_size(const gbssim_plane *x, const gbssim_params *p, int32_t kt, size_t *bytes) {
-    const int rc = check_ssim3d(x, x, p, kt);
+    const int rc = check_ssim3d(x, x, p, kt, 1);
     if (rc) return rc;
     if (!bytes) return GBSSIM_ERR_INVALID_ARG;
-    *bytes = ssim3d_ws_bytes(x, p, kt);
+    *bytes = plan_ms3d(x, p, kt, 1).bytes;
     return GBSSIM_OK;
 }
 
 int gbssim_ssim3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t kt,
                   double *frame_out, double *score_out, float *map_out, int64_t map_ld, int64_t map_frame_stride,
                   void *workspace, size_t workspace_bytes, void *stream) {
-    int rc = check_ssim3d(x, y, p, kt);
+    const int rc = check_ssim3d(x, y, p, kt, 1);
     if (rc) return rc;
     const int64_t OH = x->height - p->k + 1, OW = x->width - p->k + 1;
     if (!frame_out && !score_out && !map_out) return GBSSIM_ERR_INVALID_ARG;
     if (map_out && (map_ld < OW || map_frame_stride < OH * map_ld)) return GBSSIM_ERR_INVALID_ARG;
-    if (!workspace || workspace_bytes < ssim3d_ws_bytes(x, p, kt)) return GBSSIM_ERR_WORKSPACE;
-    Ssim3dLaunch L;
-    L.x = desc_of(x);
-    L.y = desc_of(y);
-    L.T = x->count;
-    L.k = p->k;
-    L.kt = kt;
-    L.map = map_out;
-    L.map_ld = map_ld;
-    L.map_fs = map_frame_stride;
-    L.partials = (double *)workspace;
-    L.vec4 = (uintptr_t)x->data % 4 == 0 && (uintptr_t)y->data % 4 == 0 && L.x.row_stride % 4 == 0 &&
-             L.x.image_stride % 4 == 0;
-    const double n = (double)p->k * p->k * kt;
-    const double c1 = (p->K1 * p->L) * (p->K1 * p->L), c2 = (p->K2 * p->L) * (p->K2 * p->L);
-    L.C1n2 = (float)(c1 * n * n);
-    L.C2n2 = (float)(c2 * n * n);
-    const cudaError_t e = launch_ssim3d(L, frame_out, score_out, (cudaStream_t)stream);
-    return e == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
+    // one level: the normalised sum with weight 1 is the mean Q itself
+    const double one = 1.0;
+    return run_ms3d(x, y, p, kt, 1, &one, GBSSIM_COMBINE_SUM, frame_out, score_out, nullptr, map_out, map_ld,
+                    map_frame_stride, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+int gbssim_msssim3d_workspace_size(const gbssim_plane *x, const gbssim_params *p, int32_t kt, size_t *bytes) {
+    const int rc = check_params(p);
+    if (rc) return rc;
+    const int rc2 = check_ssim3d(x, x, p, kt, p->scales);
+    if (rc2) return rc2;
+    if (!bytes) return GBSSIM_ERR_INVALID_ARG;
+    *bytes = plan_ms3d(x, p, kt, p->scales).bytes;
+    return GBSSIM_OK;
+}
+
+int gbssim_msssim3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t kt,
+                    double *frame_out, double *score_out, double *per_scale_out, void *workspace,
+                    size_t workspace_bytes, void *stream) {
+    const int rc = check_params(p);
+    if (rc) return rc;
+    const int rc2 = check_ssim3d(x, y, p, kt, p->scales);
+    if (rc2) return rc2;
+    if (!frame_out && !score_out && !per_scale_out) return GBSSIM_ERR_INVALID_ARG;
+    return run_ms3d(x, y, p, kt, p->scales, p->exponents, p->combine, frame_out, score_out, per_scale_out, nullptr,
+                    0, 0, workspace, workspace_bytes, (cudaStream_t)stream);
 }
 
 int gbssim_rgb_to_ycbcr(const gbssim_plane *r, const gbssim_plane *g, const gbssim_plane *b, float *y_out,

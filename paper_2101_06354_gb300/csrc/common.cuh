@@ -303,19 +303,25 @@ struct PoolLayout {
     size_t partials, center, state, hist, bytes;
 };
 PoolLayout pool_layout(int64_t h, int64_t w, int count);
-// SSIM-3D (k_ssim3d.cu): uint8 video pair, k x k x kt rectangular windows.
-constexpr int kSsim3dMaxK = 31;
+// SSIM-3D and MS-SSIM-3D (k_ssim3d.cu): k x k x kt rectangular windows over
+// a uint8 video pair (level 0, int32 sums) or one float pyramid level of it
+// (int64 sums of the values times `scale`).
+constexpr int kSsim3dMaxK = 31;    // int32 sums: 119 KB of shared memory per CTA
+constexpr int kSsim3dMaxK64 = 29;  // int64 sums: 225 KB per CTA
 struct Ssim3dLaunch {
-    ImgDesc x, y;          // frames as images: count = T, image_stride = frame stride
+    ImgDesc x, y;          // frames as images: count = T, image_stride = frame stride (elements)
     int T, k, kt;
-    float *map;            // nullable: (T-kt+1) maps, frames map_fs floats apart, rows map_ld
+    float *map;            // nullable: (T-kt+1) maps of Q, frames map_fs floats apart, rows map_ld
     int64_t map_ld, map_fs;
-    double *partials;      // (T-kt+1) x tiles
-    float C1n2, C2n2;      // C1 N^2, C2 N^2 with N = k^2 kt
-    bool vec4;             // data, row and frame strides 4-byte aligned (word loads)
+    double2 *partials;     // (T-kt+1) x tiles of (sum Q, sum cs)
+    float scale;           // float levels: values times scale are exact integers (4^j at level j)
+    float C1n2, C2n2;      // C1 N^2, C2 N^2 with N = k^2 kt (times scale^2 for a scaled level)
+    bool vec4;             // data, row and frame strides allow 4-element vector loads
 };
 void ssim3d_tiles(int64_t H, int64_t W, int k, int *tx, int *ty);
-cudaError_t launch_ssim3d(const Ssim3dLaunch &L, double *frame_out, double *score_out, cudaStream_t st);
+// level0: uint8 frames with int32 sums; else float frames with int64 sums.
+cudaError_t launch_ssim3d_level(const Ssim3dLaunch &L, bool level0, cudaStream_t st);
+cudaError_t launch_frame_mean(const double *frames, int n, double *out, cudaStream_t st);
 
 // Scale handling (k_scale.cu): Z x Z block means and the 9/7 wavelet pyramid step.
 cudaError_t launch_block_mean(const ImgDesc &in, int dtype, int count, int z, float *out, int64_t out_ld,

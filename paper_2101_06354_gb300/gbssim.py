@@ -113,6 +113,8 @@ _SIGS = {
                               _i32, _i64, _i64, _vp], ctypes.c_int),
     "gbssim_ssim3d": ([_P(Plane), _P(Plane), _P(Params), _i32, _vp, _vp, _vp, _i64, _i64, _vp, _sz, _vp],
                       ctypes.c_int),
+    "gbssim_msssim3d_workspace_size": ([_P(Plane), _P(Params), _i32, _P(_sz)], ctypes.c_int),
+    "gbssim_msssim3d": ([_P(Plane), _P(Plane), _P(Params), _i32, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
     "gbssim_msssim_host": ([_P(Plane), _P(Plane), _P(Params), _i32, _vp, _vp, _sz, _vp, _vp, _vp], ctypes.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -444,6 +446,34 @@ def ssim3d(x: torch.Tensor, y: torch.Tensor, kt: int = 5, k: int = 11, return_ma
                              score.data_ptr(), qmap.data_ptr() if return_map else None, W - k + 1,
                              (H - k + 1) * (W - k + 1), ws.data_ptr(), ws.numel(), _stream(dev)), "gbssim_ssim3d")
     return (score[0], frames, qmap) if return_map else (score[0], frames)
+
+
+def msssim3d(x: torch.Tensor, y: torch.Tensor, kt: int = 5, k: int = 11, per_scale: bool = False,
+             ws: torch.Tensor = None, **kw):
+    """MS-SSIM-3D (gbssim_msssim3d) of a uint8 video pair (T, H, W): SSIM-3D
+    with k x k x kt windows on every level of the frames' 2x2 pyramid,
+    combined per output frame like MS-SSIM.  Returns (video score, per-frame
+    scores[, (T-kt+1, scales, 2) of (mean cs_j, mean Q_j)])."""
+    if x.dtype != torch.uint8 or x.dim() != 3 or y.shape != x.shape or y.dtype != x.dtype:
+        raise ValueError("expected two uint8 videos (T, H, W) of one shape")
+    dev = x.device
+    xb, yb = x.contiguous(), y.contiguous()
+    kw.setdefault("exponents", MSSSIM_EXPONENTS[: kw.get("scales", 5)])
+    p = make_params(window="box", k=k, **kw)
+    px, py = plane(xb), plane(yb)
+    T = x.shape[0]
+    if ws is None:
+        nb = ctypes.c_size_t()
+        _check(lib.gbssim_msssim3d_workspace_size(ctypes.byref(px), ctypes.byref(p), int(kt), ctypes.byref(nb)),
+               "gbssim_msssim3d_workspace_size")
+        ws = torch.empty(max(int(nb.value), 1), dtype=torch.uint8, device=dev)
+    frames = torch.empty(T - kt + 1, dtype=torch.float64, device=dev)
+    score = torch.empty(1, dtype=torch.float64, device=dev)
+    per = torch.empty((T - kt + 1, p.scales, 2), dtype=torch.float64, device=dev) if per_scale else None
+    _check(lib.gbssim_msssim3d(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p), int(kt), frames.data_ptr(),
+                               score.data_ptr(), per.data_ptr() if per_scale else None, ws.data_ptr(), ws.numel(),
+                               _stream(dev)), "gbssim_msssim3d")
+    return (score[0], frames, per) if per_scale else (score[0], frames)
 
 
 FLAG_PYRAMID_97 = 2

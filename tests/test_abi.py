@@ -183,3 +183,35 @@ def test_downscale_factor_matches_oracle(g):
         assert g.downscale_factor(h, w, "ceil_h") == scales.downscale_factor(h, w, "ceil_h")
     assert g.lib.gbssim_downscale_factor(100, 100, 7) == g.ERR_INVALID_ARG
     assert g.lib.gbssim_downscale_factor(0, 100, 0) == g.ERR_INVALID_ARG
+
+
+def _ws3d(g, x, p, kt, fn="gbssim_msssim3d_workspace_size"):
+    n = ctypes.c_size_t()
+    rc = getattr(g.lib, fn)(ctypes.byref(x), ctypes.byref(p), int(kt), ctypes.byref(n))
+    return rc, n.value
+
+
+def test_ssim3d_and_msssim3d_validation(g):
+    box = dict(window="box")
+    v = _plane(g, 1080, 1920, 40)
+    rc, n1 = _ws3d(g, v, g.make_params(k=11, **box), 5, "gbssim_ssim3d_workspace_size")
+    assert rc == 0 and n1 >= 36 * 16 * 68 * 30 // 2
+    rc, n5 = _ws3d(g, v, g.make_params(k=11, **box), 5)
+    # the float pyramid of levels 1..4, x and y
+    pyr = sum((1080 >> j) * (1920 >> j) for j in range(1, 5)) * 40 * 2 * 4
+    assert rc == 0 and n5 >= pyr
+    # int64 levels keep k <= 29 (shared memory); one level allows 31
+    assert _ws3d(g, _plane(g, 256, 256, 4), g.make_params(k=31, scales=2, **box), 2)[0] == g.ERR_UNSUPPORTED
+    assert _ws3d(g, _plane(g, 256, 256, 4), g.make_params(k=31, scales=1, **box), 2)[0] == 0
+    assert _ws3d(g, _plane(g, 256, 256, 4), g.make_params(k=29, scales=2, **box), 2)[0] == 0
+    # exact-integer range: level 0 k^2 kt 255^2 < 2^31; level 4 2 N^2 (255 16^2)^2 < 2^62
+    assert _ws3d(g, _plane(g, 512, 512, 40), g.make_params(k=29, scales=1, **box), 40)[0] == g.ERR_UNSUPPORTED
+    assert _ws3d(g, _plane(g, 512, 512, 40), g.make_params(k=29, scales=5, **box), 27)[0] == 0
+    assert _ws3d(g, _plane(g, 512, 512, 40), g.make_params(k=29, scales=5, **box), 28)[0] == g.ERR_UNSUPPORTED
+    # levels below k, kt > T, Gaussian windows, other dtypes
+    assert _ws3d(g, _plane(g, 100, 100, 4), g.make_params(k=11, scales=5, **box), 2)[0] == g.ERR_TOO_SMALL
+    assert _ws3d(g, _plane(g, 100, 100, 4), g.make_params(k=11, scales=3, **box), 5)[0] == g.ERR_TOO_SMALL
+    assert _ws3d(g, _plane(g, 100, 100, 4), g.make_params(k=11, scales=2), 2)[0] == g.ERR_UNSUPPORTED
+    assert _ws3d(g, _plane(g, 100, 100, 4, dtype=3), g.make_params(k=11, scales=2, **box), 2)[0] == \
+        g.ERR_UNSUPPORTED
+    assert _ws3d(g, _plane(g, 100, 100, 4), g.make_params(k=11, scales=2, **box), 0)[0] == g.ERR_INVALID_ARG

@@ -77,3 +77,59 @@ def test_ssim3d_rejects_unsupported(g):
     with pytest.raises(g.GbssimError) as e:
         g.ssim3d(x, x, kt=2, k=11, stride=2)      # spatial stride
     assert e.value.status == g.ERR_UNSUPPORTED
+
+
+# ---------------------------------------------------------------- MS-SSIM-3D
+
+@pytest.mark.parametrize("T,H,W,k,kt,scales,combine", [
+    (6, 96, 136, 5, 3, 3, "product"),   # every level's width a multiple of 4: vector loads
+    (5, 97, 131, 5, 2, 3, "sum"),       # odd sizes: floor halving, scalar loads on the upper levels
+    (4, 176, 200, 11, 2, 4, "product"),
+    (3, 232, 240, 29, 3, 4, "product"),  # largest window of the int64 levels
+    (7, 70, 90, 3, 7, 2, "sum"),        # one output frame
+])
+def test_msssim3d_matches_oracle(g, T, H, W, k, kt, scales, combine):
+    x, y = _video(T, H, W, seed=T + k + scales)
+    exps = tuple(oracle.MSSSIM_EXPONENTS[:scales]) if scales == 5 else tuple([1.0 / scales] * scales)
+    score, frames, per = g.msssim3d(x.to(DEV), y.to(DEV), kt=kt, k=k, scales=scales, exponents=exps,
+                                    combine=combine, per_scale=True)
+    rs, rf, rper = oracle.msssim3d(x.numpy(), y.numpy(), k=k, kt=kt, scales=scales, exponents=exps, combine=combine)
+    pc = per.cpu().numpy()
+    for j in range(scales):
+        assert np.abs(pc[:, j, :] - rper[j]).max() <= 1e-6, j
+    assert np.abs(frames.cpu().numpy() - rf).max() <= 1e-6
+    assert abs(score.item() - rs) <= 1e-6
+
+
+def test_msssim3d_one_scale_equals_ssim3d(g):
+    x, y = _video(8, 120, 200, seed=11)
+    s3, f3 = g.ssim3d(x.to(DEV), y.to(DEV), kt=4, k=11)
+    s, f = g.msssim3d(x.to(DEV), y.to(DEV), kt=4, k=11, scales=1, exponents=(1.0,), combine="sum")
+    assert torch.equal(f, f3)
+    assert s.item() == s3.item()
+
+
+def test_msssim3d_full_hd_kt1_is_framewise_box_msssim(g):
+    """1080p, 4 frames, kt = 1: every frame's MS-SSIM-3D is the frame's
+    MS-SSIM with the k x k box window (the same statistics, another kernel)."""
+    x, y = _video(4, 1080, 1920, seed=12)
+    xd, yd = x.to(DEV), y.to(DEV)
+    _, f = g.msssim3d(xd, yd, kt=1, k=8, scales=5)
+    ref = g.msssim(xd, yd, window="box", k=8, scales=5)
+    assert torch.allclose(f, ref, rtol=0, atol=1e-6)
+    s, f5 = g.msssim3d(xd, yd, kt=3, k=8, scales=5)
+    assert torch.isfinite(f5).all() and f5.shape == (2,)
+    assert abs(s.item() - f5.mean().item()) <= 1e-12
+
+
+def test_msssim3d_rejects_unsupported(g):
+    x = torch.zeros((4, 64, 64), dtype=torch.uint8, device=DEV)
+    with pytest.raises(g.GbssimError) as e:
+        g.msssim3d(x, x, kt=2, k=31, scales=2, exponents=(0.5, 0.5))   # int64 levels take k <= 29
+    assert e.value.status == g.ERR_UNSUPPORTED
+    with pytest.raises(g.GbssimError) as e:
+        g.msssim3d(x, x, kt=2, k=11, scales=4, exponents=(0.25,) * 4)  # level 3 is 8 x 8 (64 >> 3)
+    assert e.value.status == g.ERR_TOO_SMALL
+    with pytest.raises(g.GbssimError) as e:
+        g.msssim3d(x, x, kt=5, k=5, scales=2, exponents=(0.5, 0.5))    # kt > T
+    assert e.value.status == g.ERR_TOO_SMALL

@@ -54,3 +54,29 @@ def test_identity_constant_and_shapes():
     C1, _ = oracle.constants()
     _, _, q = oracle.ssim3d(xc, yc, k=11, kt=2)
     np.testing.assert_allclose(q, (2 * a * b + C1) / (a * a + b * b + C1), rtol=1e-12)
+
+
+def test_msssim3d_one_scale_is_ssim3d():
+    x, y = _video(T=6, H=30, W=33, seed=4)
+    s3, f3, _ = oracle.ssim3d(x, y, k=5, kt=3)
+    s, f, per = oracle.msssim3d(x, y, k=5, kt=3, scales=1, exponents=(1.0,))
+    np.testing.assert_allclose(f, f3, rtol=0, atol=1e-12)
+    assert s == pytest.approx(s3, abs=1e-12)
+
+
+def test_msssim3d_kt1_is_framewise_msssim_with_box_window():
+    x, y = _video(T=3, H=60, W=70, seed=5)
+    _, frames, _ = oracle.msssim3d(x, y, k=5, kt=1, scales=3, exponents=(0.3, 0.3, 0.4))
+    for t in range(3):
+        ref, _ = oracle.msssim(x[t], y[t], scales=3, exponents=(0.3, 0.3, 0.4), window_kind="box", k=5)
+        assert frames[t] == pytest.approx(ref, abs=1e-12)
+
+
+def test_msssim3d_identity_and_static_video():
+    x, y = _video(T=1, H=64, W=72, seed=6)
+    xs, ys = np.repeat(x, 4, axis=0), np.repeat(y, 4, axis=0)
+    s, frames, _ = oracle.msssim3d(xs, ys, k=5, kt=2, scales=3, exponents=(0.3, 0.3, 0.4))
+    ref, _ = oracle.msssim(x[0], y[0], scales=3, exponents=(0.3, 0.3, 0.4), window_kind="box", k=5)
+    np.testing.assert_allclose(frames, ref, rtol=0, atol=1e-12)
+    s1, _, _ = oracle.msssim3d(xs, xs, k=5, kt=2, scales=3, exponents=(0.3, 0.3, 0.4))
+    assert s1 == pytest.approx(1.0, abs=1e-12)
