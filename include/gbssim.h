@@ -280,7 +280,7 @@ int gbssim_ssim3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_par
  * MS-SSIM (product of m_j^beta_j, or the normalised sum); the video score is
  * the mean over output frames.  Pyramid values are multiples of 4^-j: the
  * window sums stay exact (int64 sums of the values times 4^j).
- *   p             : window = GBSSIM_WIN_BOX, k <= 29, stride 1; scales,
+ *   p             : window = GBSSIM_WIN_BOX, k <= 31, stride 1; scales,
  *                   exponents and combine as for gbssim_msssim.
  *   kt            : frames per window, 1 <= kt <= T, with the exact-integer
  *                   ranges k^2 kt 255^2 < 2^31 and, at every level j >= 1,

@@ -731,8 +731,7 @@ int check_ssim3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_para
     if (rc) return rc;
     rc = check_params(p);
     if (rc) return rc;
-    if (x->dtype != GBSSIM_U8 || p->window != GBSSIM_WIN_BOX || p->stride != 1 ||
-        p->k > (scales > 1 ? kSsim3dMaxK64 : kSsim3dMaxK))
+    if (x->dtype != GBSSIM_U8 || p->window != GBSSIM_WIN_BOX || p->stride != 1 || p->k > kSsim3dMaxK)
         return GBSSIM_ERR_UNSUPPORTED;
     if (kt < 1) return GBSSIM_ERR_INVALID_ARG;
     if (x->count < kt) return GBSSIM_ERR_TOO_SMALL;
@@ -769,7 +768,7 @@ Ms3dPlan plan_ms3d(const gbssim_plane *x, const gbssim_params *p, int32_t kt, in
         P.H[j] = x->height >> j;
         P.W[j] = x->width >> j;
         int tx, ty;
-        ssim3d_tiles(P.H[j], P.W[j], p->k, &tx, &ty);
+        ssim3d_tiles(P.H[j], P.W[j], p->k, j == 0, &tx, &ty);
         P.tiles[j] = tx * ty;
         P.partials[j] = off;
         off = align_up(off + sizeof(double2) * (size_t)P.frames * P.tiles[j]);

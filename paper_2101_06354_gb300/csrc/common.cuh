@@ -306,8 +306,7 @@ PoolLayout pool_layout(int64_t h, int64_t w, int count);
 // SSIM-3D and MS-SSIM-3D (k_ssim3d.cu): k x k x kt rectangular windows over
 // a uint8 video pair (level 0, int32 sums) or one float pyramid level of it
 // (int64 sums of the values times `scale`).
-constexpr int kSsim3dMaxK = 31;    // int32 sums: 119 KB of shared memory per CTA
-constexpr int kSsim3dMaxK64 = 29;  // int64 sums: 225 KB per CTA
+constexpr int kSsim3dMaxK = 31;  // shared memory per CTA at k = 31: 119 KB (int32), 173 KB (int64, 8-row tiles)
 struct Ssim3dLaunch {
     ImgDesc x, y;          // frames as images: count = T, image_stride = frame stride (elements)
     int T, k, kt;
@@ -318,7 +317,7 @@ struct Ssim3dLaunch {
     float C1n2, C2n2;      // C1 N^2, C2 N^2 with N = k^2 kt (times scale^2 for a scaled level)
     bool vec4;             // data, row and frame strides allow 4-element vector loads
 };
-void ssim3d_tiles(int64_t H, int64_t W, int k, int *tx, int *ty);
+void ssim3d_tiles(int64_t H, int64_t W, int k, bool level0, int *tx, int *ty);
 // level0: uint8 frames with int32 sums; else float frames with int64 sums.
 cudaError_t launch_ssim3d_level(const Ssim3dLaunch &L, bool level0, cudaStream_t st);
 cudaError_t launch_frame_mean(const double *frames, int n, double *out, cudaStream_t st);

@@ -30,7 +30,13 @@ namespace gbssim {
 namespace {
 
 constexpr int NT = 256;
-constexpr int OW3 = 64, OH3 = 16;  // output tile
+constexpr int OW3 = 64;  // output tile width
+// Output tile height: 16 rows with int32 sums; 8 with int64 sums, so that two
+// CTAs fit an SM's shared memory.
+template <typename A>
+struct TileRows {
+    static constexpr int v = sizeof(A) == 4 ? 16 : 8;
+};
 constexpr int RB = 4;              // rows per warp whose loads are in flight together
 
 template <typename A>
@@ -49,7 +55,7 @@ struct S3Geo {
 };
 
 // Dynamic shared memory (accumulator type A): Ts[5][ih][pw] temporal sums of
-// the input tile, then Vs[5][OH3][pw] vertical window sums of Ts (turned into
+// the input tile, then Vs[5][OH][pw] vertical window sums of Ts (turned into
 // row prefix sums in place), then the reduction scratch.
 template <typename A>
 __device__ __forceinline__ A *ts_of(A *sm, const S3Geo &g, int q) {
@@ -57,7 +63,7 @@ __device__ __forceinline__ A *ts_of(A *sm, const S3Geo &g, int q) {
 }
 template <typename A>
 __device__ __forceinline__ A *vs_of(A *sm, const S3Geo &g, int q) {
-    return sm + 5 * g.ih * g.pw + q * OH3 * g.pw;
+    return sm + 5 * g.ih * g.pw + q * TileRows<A>::v * g.pw;
 }
 
 // Up to 4 pixels of one row, raw (a 4-byte word, or a float4), zero past
@@ -122,8 +128,9 @@ __device__ __forceinline__ void add4(long long *t, const long long (&d)[4]) {
 }
 
 template <typename A, typename In>
-__global__ void __launch_bounds__(NT, sizeof(A) == 4 ? 4 : 2) ssim3d_kernel(const Ssim3dLaunch L, int tiles_x, int tiles_y) {
+__global__ void __launch_bounds__(NT, sizeof(A) == 4 ? 3 : 2) ssim3d_kernel(const Ssim3dLaunch L, int tiles_x, int tiles_y) {
     using U = typename Unsigned<A>::T;
+    constexpr int OH3 = TileRows<A>::v;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     A *sm = reinterpret_cast<A *>(smem_raw);
     S3Geo g;
@@ -291,6 +298,7 @@ __global__ void frame_mean_kernel(const double *frames, int n, double *out) {
 
 template <typename A>
 size_t smem_bytes(int k) {
+    constexpr int OH3 = TileRows<A>::v;
     const size_t ih = OH3 + k - 1, iw = OW3 + k - 1, pw = (iw + 4) & ~(size_t)3;
     return sizeof(A) * (5 * ih * pw + 5 * OH3 * pw) + sizeof(float) * 2 * (NT / 32);
 }
@@ -298,13 +306,13 @@ size_t smem_bytes(int k) {
 template <typename A, typename In>
 cudaError_t launch_level(const Ssim3dLaunch &L, cudaStream_t st) {
     int tx, ty;
-    ssim3d_tiles(L.x.H, L.x.W, L.k, &tx, &ty);
+    ssim3d_tiles(L.x.H, L.x.W, L.k, sizeof(A) == 4, &tx, &ty);
     static bool attr_set[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_set[dev]) {
         const cudaError_t e = cudaFuncSetAttribute(ssim3d_kernel<A, In>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)smem_bytes<A>(sizeof(A) == 4 ? kSsim3dMaxK : kSsim3dMaxK64));
+                                                   (int)smem_bytes<A>(kSsim3dMaxK));
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
@@ -314,9 +322,10 @@ cudaError_t launch_level(const Ssim3dLaunch &L, cudaStream_t st) {
 
 }  // namespace
 
-void ssim3d_tiles(int64_t H, int64_t W, int k, int *tx, int *ty) {
+void ssim3d_tiles(int64_t H, int64_t W, int k, bool level0, int *tx, int *ty) {
+    const int oh = level0 ? TileRows<int>::v : TileRows<long long>::v;
     *tx = (int)((W - k + 1 + OW3 - 1) / OW3);
-    *ty = (int)((H - k + 1 + OH3 - 1) / OH3);
+    *ty = (int)((H - k + 1 + oh - 1) / oh);
 }
 
 cudaError_t launch_ssim3d_level(const Ssim3dLaunch &L, bool level0, cudaStream_t st) {

@@ -200,10 +200,10 @@ def test_ssim3d_and_msssim3d_validation(g):
     # the float pyramid of levels 1..4, x and y
     pyr = sum((1080 >> j) * (1920 >> j) for j in range(1, 5)) * 40 * 2 * 4
     assert rc == 0 and n5 >= pyr
-    # int64 levels keep k <= 29 (shared memory); one level allows 31
-    assert _ws3d(g, _plane(g, 256, 256, 4), g.make_params(k=31, scales=2, **box), 2)[0] == g.ERR_UNSUPPORTED
+    # windows up to 31 x 31 on every level
+    assert _ws3d(g, _plane(g, 256, 256, 4), g.make_params(k=32, scales=2, **box), 2)[0] == g.ERR_UNSUPPORTED
     assert _ws3d(g, _plane(g, 256, 256, 4), g.make_params(k=31, scales=1, **box), 2)[0] == 0
-    assert _ws3d(g, _plane(g, 256, 256, 4), g.make_params(k=29, scales=2, **box), 2)[0] == 0
+    assert _ws3d(g, _plane(g, 256, 256, 4), g.make_params(k=31, scales=2, **box), 2)[0] == 0
     # exact-integer range: level 0 k^2 kt 255^2 < 2^31; level 4 2 N^2 (255 16^2)^2 < 2^62
     assert _ws3d(g, _plane(g, 512, 512, 40), g.make_params(k=29, scales=1, **box), 40)[0] == g.ERR_UNSUPPORTED
     assert _ws3d(g, _plane(g, 512, 512, 40), g.make_params(k=29, scales=5, **box), 27)[0] == 0

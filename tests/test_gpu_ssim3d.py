@@ -85,7 +85,7 @@ def test_ssim3d_rejects_unsupported(g):
     (6, 96, 136, 5, 3, 3, "product"),   # every level's width a multiple of 4: vector loads
     (5, 97, 131, 5, 2, 3, "sum"),       # odd sizes: floor halving, scalar loads on the upper levels
     (4, 176, 200, 11, 2, 4, "product"),
-    (3, 232, 240, 29, 3, 4, "product"),  # largest window of the int64 levels
+    (3, 248, 256, 31, 3, 4, "product"),  # largest window
     (7, 70, 90, 3, 7, 2, "sum"),        # one output frame
 ])
 def test_msssim3d_matches_oracle(g, T, H, W, k, kt, scales, combine):
@@ -125,7 +125,7 @@ def test_msssim3d_full_hd_kt1_is_framewise_box_msssim(g):
 def test_msssim3d_rejects_unsupported(g):
     x = torch.zeros((4, 64, 64), dtype=torch.uint8, device=DEV)
     with pytest.raises(g.GbssimError) as e:
-        g.msssim3d(x, x, kt=2, k=31, scales=2, exponents=(0.5, 0.5))   # int64 levels take k <= 29
+        g.msssim3d(x, x, kt=2, k=32, scales=2, exponents=(0.5, 0.5))   # windows up to 31 x 31
     assert e.value.status == g.ERR_UNSUPPORTED
     with pytest.raises(g.GbssimError) as e:
         g.msssim3d(x, x, kt=2, k=11, scales=4, exponents=(0.25,) * 4)  # level 3 is 8 x 8 (64 >> 3)
