@@ -254,10 +254,13 @@ int gbssim_series_pool(const double *scores, int32_t n, int32_t count, int64_t s
  * window of output frame t covers input frames t .. t+kt-1 (the window
  * ending at frame t+kt-1); like the spatial map, only windows inside the
  * video count, so there are T-kt+1 output frames of (H-k+1) x (W-k+1)
- * positions.  The window sums are exact integers (int32, int64 numerators).
+ * positions.  The window sums are exact integers (int32 or int64, int64
+ * numerators).
  *   x, y       : the T frames as a batch (count = T, image_stride = frame stride).
  *   p          : window = GBSSIM_WIN_BOX, k <= 31, stride 1; K1, K2, L as usual.
- *   kt         : frames per window, 1 <= kt <= T, k^2 kt 255^2 < 2^31.
+ *   kt         : frames per window, 1 <= kt <= T, 5 (k^2 kt)^2 255^2 < 2^63
+ *                (the exact int64 numerators; int32 window sums while
+ *                k^2 kt 510^2 < 2^31, int64 beyond).
  *   frame_out  : nullable; T-kt+1 doubles, the mean Q of each output frame.
  *   score_out  : nullable; one double, the mean over all output frames.
  *   map_out    : nullable; Q of output frame t at map_out + t*map_frame_stride,
@@ -283,8 +286,7 @@ int gbssim_ssim3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_par
  *   p             : window = GBSSIM_WIN_BOX, k <= 31, stride 1; scales,
  *                   exponents and combine as for gbssim_msssim.
  *   kt            : frames per window, 1 <= kt <= T, with the exact-integer
- *                   ranges k^2 kt 255^2 < 2^31 and, at every level j >= 1,
- *                   2 (k^2 kt)^2 (255 4^j)^2 < 2^62.
+ *                   range 5 (k^2 kt)^2 (255 4^j)^2 < 2^63 at every level j.
  *   frame_out     : nullable; T-kt+1 doubles, the score of each output frame.
  *   score_out     : nullable; one double, the mean of the frame scores.
  *   per_scale_out : nullable; (T-kt+1) * scales * 2 doubles, (mean cs_j,

@@ -737,27 +737,31 @@ int check_ssim3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_para
     if (x->count < kt) return GBSSIM_ERR_TOO_SMALL;
     for (int j = 0; j < scales; ++j)
         if ((x->height >> j) < p->k || (x->width >> j) < p->k) return GBSSIM_ERR_TOO_SMALL;
+    // exact int64 numerators: at level j the values times 4^j are integers up
+    // to M = 255 4^j, |u| <= 2M, |w| <= M, and every numerator is at most
+    // 5 N^2 M^2 (Su^2 + Sw^2, Vu + Vw), kept below 2^63
     const double n = (double)p->k * p->k * kt;
-    // level 0: exact int32 window sums, N 255^2 < 2^31
-    if (n * 65025.0 >= 2147483648.0) return GBSSIM_ERR_UNSUPPORTED;
-    // level j >= 1: values times 4^j are integers up to M = 255 4^j; every int64
-    // numerator is at most 2 N^2 M^2, kept below 2^62
-    for (int j = 1; j < scales; ++j) {
+    for (int j = 0; j < scales; ++j) {
         const double m = 255.0 * (double)(1 << (2 * j));
-        if (2.0 * n * n * m * m >= 4611686018427387904.0) return GBSSIM_ERR_UNSUPPORTED;
+        if (5.0 * n * n * m * m >= 9223372036854775808.0) return GBSSIM_ERR_UNSUPPORTED;
     }
     if (scales > 1 && x->count > 65535) return GBSSIM_ERR_UNSUPPORTED;  // pyramid grid's z extent
     return GBSSIM_OK;
 }
 
+// uint8 level 0 sums in int32 while N (2 255)^2 < 2^31 (the largest sum of u^2).
+bool ssim3d_wide0(const gbssim_params *p, int32_t kt) {
+    return (double)p->k * p->k * kt * 260100.0 >= 2147483648.0;
+}
+
 struct Ms3dPlan {
     int frames, scales;
     int64_t H[GBSSIM_MAX_SCALES], W[GBSSIM_MAX_SCALES];
-    int tiles[GBSSIM_MAX_SCALES];
+    int items[GBSSIM_MAX_SCALES];  // partials (tiles) per output frame
     size_t partials[GBSSIM_MAX_SCALES], pyr_x[GBSSIM_MAX_SCALES], pyr_y[GBSSIM_MAX_SCALES], frame_buf, bytes;
 };
 
-// Workspace: per level the (frame, tile) partials, one frame-score buffer,
+// Workspace: per level the (frame, tile) partials, a frame-score buffer,
 // then the float pyramid levels 1..S-1 of x and y (T dense frames each).
 Ms3dPlan plan_ms3d(const gbssim_plane *x, const gbssim_params *p, int32_t kt, int scales) {
     Ms3dPlan P{};
@@ -767,11 +771,12 @@ Ms3dPlan plan_ms3d(const gbssim_plane *x, const gbssim_params *p, int32_t kt, in
     for (int j = 0; j < scales; ++j) {
         P.H[j] = x->height >> j;
         P.W[j] = x->width >> j;
+        const bool wide = j > 0 || ssim3d_wide0(p, kt);
         int tx, ty;
-        ssim3d_tiles(P.H[j], P.W[j], p->k, j == 0, &tx, &ty);
-        P.tiles[j] = tx * ty;
+        ssim3d_tiles(P.H[j], P.W[j], p->k, wide, &tx, &ty);
+        P.items[j] = tx * ty;
         P.partials[j] = off;
-        off = align_up(off + sizeof(double2) * (size_t)P.frames * P.tiles[j]);
+        off = align_up(off + sizeof(double2) * (size_t)P.frames * P.items[j]);
     }
     P.frame_buf = off;
     off = align_up(off + sizeof(double) * (size_t)P.frames);
@@ -797,9 +802,9 @@ int run_ms3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *
     char *ws = static_cast<char *>(workspace);
     const double n = (double)p->k * p->k * kt;
     const double c1 = (p->K1 * p->L) * (p->K1 * p->L), c2 = (p->K2 * p->L) * (p->K2 * p->L);
-    MsFinalize F{};
+    Ms3dFinalize F{};
     F.scales = scales;
-    F.count = P.frames;
+    F.frames = P.frames;
     F.combine = combine;
     for (int j = 0; j < scales; ++j) {
         F.exps[j] = exps[j];
@@ -836,19 +841,18 @@ int run_ms3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *
         L.map_ld = map_ld;
         L.map_fs = map_frame_stride;
         L.partials = (double2 *)(ws + P.partials[j]);
-        L.C1n2 = (float)(c1 * sc2 * n * n);
-        L.C2n2 = (float)(c2 * sc2 * n * n);
-        if (launch_ssim3d_level(L, level0, st) != cudaSuccess) return GBSSIM_ERR_CUDA;
-        F.lv[j].partials = L.partials;
-        F.lv[j].items_per_image = P.tiles[j];
-        F.lv[j].inv_n = 1.0 / ((double)(P.H[j] - p->k + 1) * (double)(P.W[j] - p->k + 1));
+        L.C1x2n2 = (float)(2.0 * c1 * sc2 * n * n);
+        L.C2x2n2 = (float)(2.0 * c2 * sc2 * n * n);
+        const bool wide = !level0 || ssim3d_wide0(p, kt);
+        if (launch_ssim3d_level(L, level0, wide, st) != cudaSuccess) return GBSSIM_ERR_CUDA;
+        F.partials[j] = L.partials;
+        F.items[j] = P.items[j];
+        F.inv_n[j] = 1.0 / ((double)(P.H[j] - p->k + 1) * (double)(P.W[j] - p->k + 1));
     }
     double *frames = frame_out ? frame_out : (double *)(ws + P.frame_buf);
-    F.score_out = frames;
-    F.per_scale_out = per_scale_out;
-    if (launch_finalize_msssim(F, st) != cudaSuccess) return GBSSIM_ERR_CUDA;
-    if (score_out && launch_frame_mean(frames, P.frames, score_out, st) != cudaSuccess) return GBSSIM_ERR_CUDA;
-    return GBSSIM_OK;
+    return launch_ssim3d_finalize(F, frames, per_scale_out, score_out, st) == cudaSuccess
+               ? GBSSIM_OK
+               : GBSSIM_ERR_CUDA;
 }
 }  // namespace
 

@@ -304,23 +304,32 @@ struct PoolLayout {
 };
 PoolLayout pool_layout(int64_t h, int64_t w, int count);
 // SSIM-3D and MS-SSIM-3D (k_ssim3d.cu): k x k x kt rectangular windows over
-// a uint8 video pair (level 0, int32 sums) or one float pyramid level of it
-// (int64 sums of the values times `scale`).
-constexpr int kSsim3dMaxK = 31;  // shared memory per CTA at k = 31: 119 KB (int32), 173 KB (int64, 8-row tiles)
+// a uint8 video pair (level 0) or one float pyramid level of it (values times
+// `scale` are exact integers); int32 or int64 ("wide") window sums.
+constexpr int kSsim3dMaxK = 31;  // shared memory per CTA at k = 31: 98 KB (int32), 188 KB (int64)
 struct Ssim3dLaunch {
-    ImgDesc x, y;          // frames as images: count = T, image_stride = frame stride (elements)
+    ImgDesc x, y;           // frames as images: count = T, image_stride = frame stride (elements)
     int T, k, kt;
-    float *map;            // nullable: (T-kt+1) maps of Q, frames map_fs floats apart, rows map_ld
+    float *map;             // nullable: (T-kt+1) maps of Q, frames map_fs floats apart, rows map_ld
     int64_t map_ld, map_fs;
-    double2 *partials;     // (T-kt+1) x tiles of (sum Q, sum cs)
-    float scale;           // float levels: values times scale are exact integers (4^j at level j)
-    float C1n2, C2n2;      // C1 N^2, C2 N^2 with N = k^2 kt (times scale^2 for a scaled level)
-    bool vec4;             // data, row and frame strides allow 4-element vector loads
+    double2 *partials;      // (T-kt+1) x tiles of (sum Q, sum cs)
+    float scale;            // float levels: values times scale are exact integers (4^j at level j)
+    float C1x2n2, C2x2n2;   // 2 C1 N^2, 2 C2 N^2 with N = k^2 kt (times scale^2 for a scaled level)
+    bool vec4;              // data, row and frame strides allow 4-element vector loads
 };
-void ssim3d_tiles(int64_t H, int64_t W, int k, bool level0, int *tx, int *ty);
-// level0: uint8 frames with int32 sums; else float frames with int64 sums.
-cudaError_t launch_ssim3d_level(const Ssim3dLaunch &L, bool level0, cudaStream_t st);
-cudaError_t launch_frame_mean(const double *frames, int n, double *out, cudaStream_t st);
+void ssim3d_tiles(int64_t H, int64_t W, int k, bool wide, int *tx, int *ty);
+cudaError_t launch_ssim3d_level(const Ssim3dLaunch &L, bool u8_input, bool wide, cudaStream_t st);
+// Per-frame combination of the levels' (frame, item) partials.
+struct Ms3dFinalize {
+    const double2 *partials[GBSSIM_MAX_SCALES];  // level j: frames x items[j] of (sum Q, sum cs)
+    int items[GBSSIM_MAX_SCALES];
+    double inv_n[GBSSIM_MAX_SCALES];             // 1 / positions of a frame at level j
+    double exps[GBSSIM_MAX_SCALES];
+    int scales, frames, combine;
+};
+// frame_scores: frames doubles (written); per_scale_out, score_out nullable.
+cudaError_t launch_ssim3d_finalize(const Ms3dFinalize &F, double *frame_scores, double *per_scale_out,
+                                   double *score_out, cudaStream_t st);
 
 // Scale handling (k_scale.cu): Z x Z block means and the 9/7 wavelet pyramid step.
 cudaError_t launch_block_mean(const ImgDesc &in, int dtype, int count, int z, float *out, int64_t out_ld,

@@ -122,17 +122,52 @@ __global__ void __launch_bounds__(32 * GBSSIM_MAX_SCALES) finalize_batch_kernel(
     }
 }
 
+// 8 consecutive elements as floats, zero past n: one 8- or 16-byte vector
+// load when `vec` (the address is aligned for it), else element by element.
 template <typename T>
-__global__ void downsample_kernel(ImgDesc in, float *out) {
+__device__ __forceinline__ void load8(const T *p, int n, bool vec, float (&v)[8]) {
+    if (vec && n == 8) {
+        if constexpr (sizeof(T) == 1) {
+            const uint2 w = __ldg(reinterpret_cast<const uint2 *>(p));
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                v[e] = (float)((w.x >> (8 * e)) & 255u);
+                v[4 + e] = (float)((w.y >> (8 * e)) & 255u);
+            }
+            return;
+        } else if constexpr (sizeof(T) == 4) {
+            const float4 a = __ldg(reinterpret_cast<const float4 *>(p)), b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+            v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+            return;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = e < n ? load_f32<T>(p + e) : 0.f;
+}
+
+// 2x2 averages, 4 outputs per thread; the sum order (a + b) + (c + d) of
+// each 2x2 block is that of the scalar definition.
+template <typename T>
+__global__ void downsample_kernel(ImgDesc in, float *out, bool vec_in, bool vec_out) {
     const int64_t Hh = in.H >> 1, Wh = in.W >> 1;
     const int img = blockIdx.z;
-    const int64_t C = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t C = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
     const int64_t R = blockIdx.y;
     if (C >= Wh) return;
+    const int n = (int)min((int64_t)4, Wh - C);
     const T *b = static_cast<const T *>(in.data) + img * in.image_stride + 2 * R * in.row_stride + 2 * C;
-    const float s = (load_f32<T>(b) + load_f32<T>(b + 1)) +
-                    (load_f32<T>(b + in.row_stride) + load_f32<T>(b + in.row_stride + 1));
-    out[img * Hh * Wh + R * Wh + C] = 0.25f * s;
+    float r0[8], r1[8];
+    load8<T>(b, 2 * n, vec_in, r0);
+    load8<T>(b + in.row_stride, 2 * n, vec_in, r1);
+    float o[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) o[e] = 0.25f * ((r0[2 * e] + r0[2 * e + 1]) + (r1[2 * e] + r1[2 * e + 1]));
+    float *op = out + img * Hh * Wh + R * Wh + C;
+    if (vec_out && n == 4) {
+        *reinterpret_cast<float4 *>(op) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+        for (int e = 0; e < n; ++e) op[e] = o[e];
+    }
 }
 
 }  // namespace
@@ -244,12 +279,19 @@ cudaError_t launch_downsample(const ImgDesc &in, int dtype, int count, float *ou
                               cudaStream_t st) {
     const int64_t Hh = in.H >> 1, Wh = in.W >> 1;
     if (Hh == 0 || Wh == 0) return cudaSuccess;
-    dim3 grid((unsigned)((Wh + 127) / 128), (unsigned)Hh, count);
+    dim3 grid((unsigned)((Wh + 511) / 512), (unsigned)Hh, count);
+    // vector loads: 8 u8 (8 B) or 8 f32 (2 x 16 B) at every even-column group
+    // start, which is aligned when the base and both strides are
+    const int64_t vb = dtype == GBSSIM_U8 ? 8 : dtype == GBSSIM_F32 ? 16 : 0;
+    const int64_t es = dtype == GBSSIM_U8 ? 1 : dtype == GBSSIM_F32 ? 4 : 2;
+    const bool vec_in = vb > 0 && (uintptr_t)in.data % vb == 0 && (in.row_stride * es) % vb == 0 &&
+                        (in.image_stride * es) % vb == 0;
+    const bool vec_out = (uintptr_t)out % 16 == 0 && Wh % 4 == 0;
     switch (dtype) {
-    case GBSSIM_U8: downsample_kernel<uint8_t><<<grid, 128, 0, st>>>(in, out); break;
-    case GBSSIM_F16: downsample_kernel<__half><<<grid, 128, 0, st>>>(in, out); break;
-    case GBSSIM_BF16: downsample_kernel<__nv_bfloat16><<<grid, 128, 0, st>>>(in, out); break;
-    case GBSSIM_F32: downsample_kernel<float><<<grid, 128, 0, st>>>(in, out); break;
+    case GBSSIM_U8: downsample_kernel<uint8_t><<<grid, 128, 0, st>>>(in, out, vec_in, vec_out); break;
+    case GBSSIM_F16: downsample_kernel<__half><<<grid, 128, 0, st>>>(in, out, false, vec_out); break;
+    case GBSSIM_BF16: downsample_kernel<__nv_bfloat16><<<grid, 128, 0, st>>>(in, out, false, vec_out); break;
+    case GBSSIM_F32: downsample_kernel<float><<<grid, 128, 0, st>>>(in, out, vec_in, vec_out); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -6,24 +6,34 @@
 // average pyramid.
 //
 // The paper keeps rolling temporal sums T(i,j,k) of the last Kt frames and
-// forms the spatial window sums of T.  Here one CTA owns a tile of 64 x 16
-// output positions and walks the video in time: per input frame f it adds
-// frame f and subtracts frame f-Kt from the tile's five exact integer
-// temporal sums in shared memory (frame f-Kt was read Kt steps earlier by the
-// same CTA and is normally still in L2), sums k rows of T down each column
-// (running sums, lanes over consecutive columns), turns each row of those
-// column sums into prefix sums with a warp scan, and takes every window sum
-// as the difference of two prefix values.  The box formula is evaluated with
-// exact int64 numerators over N = k^2 Kt pixels.  Each input byte comes from
-// HBM once.  Per (tile, output frame) partial sums of Q and cs are combined
-// per frame in a fixed order.  Prefix sums may pass the accumulator's range
-// for the largest windows; they are kept in wrapping unsigned arithmetic,
-// which leaves every difference (a window sum inside the range) exact.
+// forms the spatial window sums of T.  Here one CTA owns a tile of 64 output
+// columns and OH output rows and walks the video in time.  Per input frame f:
+//   1. the tile's temporal sums in shared memory gain frame f and lose frame
+//      f-Kt (read Kt steps earlier by the same CTA, normally still in L2);
+//      each thread owns fixed 4-column groups, so this step needs no barrier
+//      between frames;
+//   2. once Kt frames are in, running sums down each column give the k-row
+//      sums of the OH output rows, stored transposed (column-major);
+//   3. running sums along each output row over those column sums give the
+//      k x k x Kt window sums of 8 consecutive outputs per thread, and the
+//      formula is evaluated right away.
+// Two barriers per output frame.  Each input byte comes from HBM once.
 //
-// Level 0 of uint8 video runs with int32 sums; pyramid levels j >= 1 hold
-// multiples of 4^-j (averages of 4^j pixels), which the kernel scales by 4^j
-// to exact integers and sums in int64, with C1 and C2 scaled by 16^j so that
-// l and cs are those of the unscaled level.
+// The window statistics are carried in the (u, w) = (x + y, x - y) form:
+// sums of u, w, u^2, w^2 (four quantities instead of five).  With
+// Su = sum u, Sw = sum w, Vu = N sum u^2 - Su^2, Vw = N sum w^2 - Sw^2 over
+// N = k^2 Kt pixels, the Background-section factors are exactly
+//   l  = (Su^2 - Sw^2 + 2 C1 N^2) / (Su^2 + Sw^2 + 2 C1 N^2),
+//   cs = (Vu - Vw + 2 C2 N^2) / (Vu + Vw + 2 C2 N^2),
+// since Su^2 - Sw^2 = 4 sx sy, Su^2 + Sw^2 = 2 (sx^2 + sy^2),
+// Vu - Vw = 4 (N sxy - sx sy) and Vu + Vw = 2 (N sxx - sx^2 + N syy - sy^2).
+// All sums are exact integers; the int64 numerators are rounded to fp32 once
+// (with int32 sums, l is formed in fp32 from the exact Su, Sw).
+//
+// uint8 video runs with int32 sums while N (2 255)^2 < 2^31, else int64;
+// pyramid levels j >= 1 hold multiples of 4^-j (averages of 4^j pixels),
+// which the kernel scales by 4^j to exact integers and sums in int64, with
+// C1 and C2 scaled by 16^j so that l and cs are those of the unscaled level.
 #include "common.cuh"
 
 namespace gbssim {
@@ -31,39 +41,36 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int OW3 = 64;  // output tile width
-// Output tile height: 16 rows with int32 sums; 8 with int64 sums, so that two
-// CTAs fit an SM's shared memory.
-template <typename A>
-struct TileRows {
-    static constexpr int v = sizeof(A) == 4 ? 16 : 8;
-};
-constexpr int RB = 4;              // rows per warp whose loads are in flight together
+constexpr int SEG = 8;   // consecutive outputs of one row per thread in step 3
+constexpr int RB = 2;    // 4-column groups per thread whose loads are in flight together
 
+// Tile height (16 rows) and the pitch of the transposed column sums
+// (elements).  The pitches make step 3's reads (lanes over rows, then two
+// 8-column segments per warp) and step 2's stores (lanes over columns)
+// conflict-free: 18 int32 (9 pairs for the paired stores, two segments 16
+// banks apart), 17 int64 (8-byte accesses, half a warp per wavefront).
 template <typename A>
-struct Unsigned;
-template <>
-struct Unsigned<int> {
-    using T = unsigned;
-};
-template <>
-struct Unsigned<long long> {
-    using T = unsigned long long;
+struct Tile3 {
+    static constexpr int OH = 16;
+    static constexpr int PV = sizeof(A) == 4 ? 18 : 17;
+    static constexpr int TASKS3 = OH * (OW3 / SEG);  // step-3 threads
+    static constexpr int WARPS3 = TASKS3 / 32;       // step-3 warps
 };
 
 struct S3Geo {
-    int k, iw, ih, pw;  // window, input tile width and height, row pitch of the sums (elements)
+    int k, iw, ih, pw, groups;  // window, input tile width and height, Ts pitch, 4-column groups per row
 };
 
-// Dynamic shared memory (accumulator type A): Ts[5][ih][pw] temporal sums of
-// the input tile, then Vs[5][OH][pw] vertical window sums of Ts (turned into
-// row prefix sums in place), then the reduction scratch.
+// Dynamic shared memory: Ts[4][ih][pw] temporal sums of the input tile, then
+// Vs[4][iw][PV] the k-row column sums (column-major), then the step-3 warp
+// sums (double2 per warp; every part starts on a 16-byte boundary).
 template <typename A>
 __device__ __forceinline__ A *ts_of(A *sm, const S3Geo &g, int q) {
     return sm + q * g.ih * g.pw;
 }
 template <typename A>
 __device__ __forceinline__ A *vs_of(A *sm, const S3Geo &g, int q) {
-    return sm + 5 * g.ih * g.pw + q * TileRows<A>::v * g.pw;
+    return sm + 4 * g.ih * g.pw + q * g.iw * Tile3<A>::PV;
 }
 
 // Up to 4 pixels of one row, raw (a 4-byte word, or a float4), zero past
@@ -127,169 +134,300 @@ __device__ __forceinline__ void add4(long long *t, const long long (&d)[4]) {
     t2[1] = b;
 }
 
+// Step 2's column of OH k-row sums, stored column-major: int32 as pairs
+// (8-byte stores), int64 one by one.
+template <int OH>
+__device__ __forceinline__ void store_col(int *vc, const int (&v)[OH]) {
+#pragma unroll
+    for (int i = 0; i < OH; i += 2) *reinterpret_cast<int2 *>(vc + i) = make_int2(v[i], v[i + 1]);
+}
+template <int OH>
+__device__ __forceinline__ void store_col(long long *vc, const long long (&v)[OH]) {
+#pragma unroll
+    for (int i = 0; i < OH; ++i) vc[i] = v[i];
+}
+
 template <typename A, typename In>
-__global__ void __launch_bounds__(NT, sizeof(A) == 4 ? 3 : 2) ssim3d_kernel(const Ssim3dLaunch L, int tiles_x, int tiles_y) {
-    using U = typename Unsigned<A>::T;
-    constexpr int OH3 = TileRows<A>::v;
+__global__ void __launch_bounds__(NT, sizeof(A) == 4 ? 4 : 2)
+    ssim3d_kernel(const Ssim3dLaunch L, int tiles_x, int tiles_y, int t_chunk) {
+    constexpr int OH = Tile3<A>::OH, PV = Tile3<A>::PV;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     A *sm = reinterpret_cast<A *>(smem_raw);
     S3Geo g;
     g.k = L.k;
     g.iw = OW3 + L.k - 1;
-    g.ih = OH3 + L.k - 1;
-    g.pw = (g.iw + 4) & ~3;  // >= iw + 1 (a zero column in front of the prefix sums), multiple of 4
-    float *red = reinterpret_cast<float *>(sm + 5 * g.ih * g.pw + 5 * OH3 * g.pw);
-    const int tile = blockIdx.x;
+    g.ih = OH + L.k - 1;
+    g.pw = (g.iw + 3) & ~3;
+    g.groups = (g.iw + 3) >> 2;
+    const int tile = blockIdx.x % (tiles_x * tiles_y);
+    // output frames t_begin .. t_end-1 from input frames f_begin .. f_end-1
+    const int t_begin = (blockIdx.x / (tiles_x * tiles_y)) * t_chunk;
+    const int t_end = min(t_begin + t_chunk, L.T - L.kt + 1);
+    const int f_begin = t_begin, f_end = t_end + L.kt - 1;
     const int tx = tile % tiles_x, ty = tile / tiles_x;
     const int64_t H = L.x.H, W = L.x.W, rs = L.x.row_stride, fs = L.x.image_stride;
-    const int64_t OH = H - L.k + 1, OW = W - L.k + 1;
-    const int64_t x0 = (int64_t)tx * OW3, y0 = (int64_t)ty * OH3;
+    const int64_t OHt = H - L.k + 1, OWt = W - L.k + 1;
+    const int64_t x0 = (int64_t)tx * OW3, y0 = (int64_t)ty * OH;
     const In *xb = static_cast<const In *>(L.x.data), *yb = static_cast<const In *>(L.y.data);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < 5 * g.ih * g.pw; i += NT) sm[i] = 0;
+    const int lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < 4 * g.ih * g.pw; i += NT) sm[i] = 0;
+    __syncthreads();
     const int64_t N = (int64_t)L.k * L.k * L.kt;
     const bool words = L.vec4;  // 4-element vector loads (rows and frames aligned; tiles start at multiples of 64)
     const float scale = L.scale;
-    for (int f = 0; f < L.T; ++f) {
-        __syncthreads();  // the previous frame's readers of Ts / Vs are done
-        // 1. temporal sums: + frame f, - frame f - kt.  Warp w takes rows
-        //    w, w+8, ... in groups of RB (all loads of a group issued first);
-        //    lane l the 4 pixels at columns 4l .. 4l+3, updated with 16-byte
-        //    shared accesses (conflict-free).
-        const bool old = f >= L.kt;
-        for (int rg = warp; rg < g.ih; rg += RB * (NT / 32)) {
+    const int units = g.ih * g.groups;
+    int pending = -1;  // output frame whose warp sums wait in red
+    auto flush = [&](int tp) {
+        const double2 *red = reinterpret_cast<const double2 *>(vs_of(sm, g, 4));
+        double sq = 0.0, sc = 0.0;
+#pragma unroll
+        for (int w = 0; w < Tile3<A>::WARPS3; ++w) {
+            sq += red[w].x;
+            sc += red[w].y;
+        }
+        L.partials[(int64_t)tp * (tiles_x * tiles_y) + tile] = make_double2(sq, sc);
+    };
+    // the first RB groups of this thread: offsets and widths hoisted out of
+    // the frame loop; their bytes of frame f+1 and of frame f+1-kt (the one
+    // leaving the window) are loaded while frame f is in steps 2 and 3
+    int64_t o0[RB];
+    int n40[RB], at0[RB];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+        const int unit = threadIdx.x + u * NT;
+        const int r = unit / g.groups, c = 4 * (unit - r * g.groups);
+        const int64_t row = y0 + r;
+        n40[u] = 0;
+        if (unit < units && row < H)
+            n40[u] = (int)max((int64_t)0, min((int64_t)4, min((int64_t)(g.iw - c), W - (x0 + c))));
+        at0[u] = r * g.pw + c;
+        o0[u] = row * rs + x0 + c;
+    }
+    Raw<In> px[RB], py[RB], pxo[RB], pyo[RB];  // frame f and frame f - kt of those groups
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+        load_raw(xb + f_begin * fs + o0[u], n40[u], words, px[u]);
+        load_raw(yb + f_begin * fs + o0[u], n40[u], words, py[u]);
+        load_raw(xb, 0, words, pxo[u]);  // no frame leaves the window yet
+        load_raw(yb, 0, words, pyo[u]);
+    }
+    for (int f = f_begin; f < f_end; ++f) {
+        // 1. temporal sums: + frame f, - frame f - kt.  Thread t owns the
+        //    4-column groups t, t + NT, ... (row-major over the input tile),
+        //    RB of them with their loads in flight together; 16-byte shared
+        //    accesses, consecutive across a warp.
+        const bool old = f - L.kt >= f_begin;
+        const In *xf = xb + f * fs, *yf = yb + f * fs;
+        const In *xo = xb + (f - L.kt) * fs, *yo = yb + (f - L.kt) * fs;
+        for (int u0 = threadIdx.x; u0 < units; u0 += RB * NT) {
+            const bool first = u0 == threadIdx.x;
             Raw<In> rx[RB], ry[RB], qx[RB], qy[RB];
-            int n4[RB];
+            int n4[RB], at[RB];
 #pragma unroll
             for (int u = 0; u < RB; ++u) {
-                const int r = rg + u * (NT / 32);
-                const int c = 4 * lane;
-                const int64_t row = y0 + r;
-                n4[u] = 0;
-                if (r < g.ih && row < H && c < g.iw)
-                    n4[u] = (int)max((int64_t)0, min((int64_t)4, min((int64_t)(g.iw - c), W - (x0 + c))));
-                const int64_t o = row * rs + x0 + c;
-                load_raw(xb + f * fs + o, n4[u], words, rx[u]);
-                load_raw(yb + f * fs + o, n4[u], words, ry[u]);
-                load_raw(xb + (f - L.kt) * fs + o, old ? n4[u] : 0, words, qx[u]);
-                load_raw(yb + (f - L.kt) * fs + o, old ? n4[u] : 0, words, qy[u]);
+                if (first) {
+                    n4[u] = n40[u];
+                    at[u] = at0[u];
+                    rx[u] = px[u];
+                    ry[u] = py[u];
+                    qx[u] = pxo[u];
+                    qy[u] = pyo[u];
+                } else {
+                    const int unit = u0 + u * NT;
+                    const int r = unit / g.groups, c = 4 * (unit - r * g.groups);
+                    const int64_t row = y0 + r;
+                    n4[u] = 0;
+                    if (unit < units && row < H)
+                        n4[u] = (int)max((int64_t)0, min((int64_t)4, min((int64_t)(g.iw - c), W - (x0 + c))));
+                    at[u] = r * g.pw + c;
+                    const int64_t o = row * rs + x0 + c;
+                    load_raw(xf + o, n4[u], words, rx[u]);
+                    load_raw(yf + o, n4[u], words, ry[u]);
+                    load_raw(xo + o, old ? n4[u] : 0, words, qx[u]);
+                    load_raw(yo + o, old ? n4[u] : 0, words, qy[u]);
+                }
+            }
+            if (first && f + 1 < f_end) {
+                const bool old1 = f + 1 - L.kt >= f_begin;
+#pragma unroll
+                for (int u = 0; u < RB; ++u) {
+                    load_raw(xf + fs + o0[u], n40[u], words, px[u]);
+                    load_raw(yf + fs + o0[u], n40[u], words, py[u]);
+                    load_raw(xo + fs + o0[u], old1 ? n40[u] : 0, words, pxo[u]);
+                    load_raw(yo + fs + o0[u], old1 ? n40[u] : 0, words, pyo[u]);
+                }
             }
 #pragma unroll
             for (int u = 0; u < RB; ++u) {
                 if (n4[u] <= 0) continue;  // values past n4 are zero: they add nothing
-                const int r = rg + u * (NT / 32);
-                A d[5][4];
+                A d[4][4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const A p = unpack(rx[u], e, scale), q = unpack(ry[u], e, scale);
-                    const A po = unpack(qx[u], e, scale), qo = unpack(qy[u], e, scale);
-                    d[0][e] = p - po;
-                    d[1][e] = q - qo;
-                    d[2][e] = p * p - po * po;
-                    d[3][e] = q * q - qo * qo;
-                    d[4][e] = p * q - po * qo;
+                    const int p = unpack(rx[u], e, scale), q = unpack(ry[u], e, scale);
+                    const int po = unpack(qx[u], e, scale), qo = unpack(qy[u], e, scale);
+                    const A uu = (A)p + q, ww = (A)p - q, uo = (A)po + qo, wo = (A)po - qo;
+                    d[0][e] = uu - uo;
+                    d[1][e] = ww - wo;
+                    d[2][e] = (uu - uo) * (uu + uo);  // u^2 - uo^2
+                    d[3][e] = (ww - wo) * (ww + wo);
                 }
-                const int at = r * g.pw + 4 * lane;
 #pragma unroll
-                for (int qd = 0; qd < 5; ++qd) add4(ts_of(sm, g, qd) + at, d[qd]);
+                for (int qd = 0; qd < 4; ++qd) add4(ts_of(sm, g, qd) + at[u], d[qd]);
             }
         }
-        if (f < L.kt - 1) continue;
+        if (f < f_begin + L.kt - 1) continue;
         const int t = f - L.kt + 1;  // output frame
-        __syncthreads();
-        // 2. vertical k-sums of Ts for the OH3 output rows: one thread per
-        //    (quantity, column), running down the rows; stored one column to
-        //    the right (column 0 of Vs stays 0 for the prefix sums)
-        for (int task = threadIdx.x; task < 5 * g.iw; task += NT) {
+        __syncthreads();             // Ts holds frames t .. f; red holds frame t-1's warp sums
+        if (threadIdx.x == 0 && pending >= 0) flush(pending);
+        // 2. k-row sums down each column for the OH output rows: one thread
+        //    per (quantity, column), lanes over consecutive columns
+        for (int task = threadIdx.x; task < 4 * g.iw; task += NT) {
             const int q = task / g.iw, c = task - q * g.iw;
             const A *tc = ts_of(sm, g, q) + c;
-            A *vc = vs_of(sm, g, q) + c + 1;
+            A v[OH];
             A s = 0;
+#pragma unroll 4
             for (int m = 0; m < g.k; ++m) s += tc[m * g.pw];
-            vc[0] = s;
-            for (int i = 1; i < OH3; ++i) {
-                s += tc[(i + g.k - 1) * g.pw] - tc[(i - 1) * g.pw];
-                vc[i * g.pw] = s;
-            }
-        }
-        __syncthreads();
-        // 3. inclusive prefix sums along each Vs row (5 x OH3 rows), in place:
-        //    one warp per row, 3 columns per lane, a shuffle scan of the lane totals
-        for (int rr = warp; rr < 5 * OH3; rr += NT / 32) {
-            U *vr = reinterpret_cast<U *>(vs_of(sm, g, rr / OH3) + (rr % OH3) * g.pw);
-            const int c0 = 1 + 3 * lane;  // columns c0 .. c0+2 (1 .. iw hold data)
-            U v0 = c0 <= g.iw ? vr[c0] : (U)0, v1 = c0 + 1 <= g.iw ? vr[c0 + 1] : (U)0,
-              v2 = c0 + 2 <= g.iw ? vr[c0 + 2] : (U)0;
-            v1 += v0;
-            v2 += v1;
-            U incl = v2;
+            v[0] = s;
+            const A *tn = tc + g.k * g.pw;  // row entering the window
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const U u = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += u;
+            for (int i = 1; i < OH; ++i) {
+                s += tn[(i - 1) * g.pw] - tc[(i - 1) * g.pw];
+                v[i] = s;
             }
-            const U excl = incl - v2;
-            if (c0 <= g.iw) vr[c0] = v0 + excl;
-            if (c0 + 1 <= g.iw) vr[c0 + 1] = v1 + excl;
-            if (c0 + 2 <= g.iw) vr[c0 + 2] = v2 + excl;
-            if (lane == 0) vr[0] = (U)0;
+            store_col<OH>(vs_of(sm, g, q) + c * PV, v);
         }
-        __syncthreads();
-        // 4. window sums = P[j + k] - P[j] (P shifted by the zero column), formula
-        float accQ = 0.f, accC = 0.f;
-        for (int o = threadIdx.x; o < OH3 * OW3; o += NT) {
-            const int i = o / OW3, j = o - i * OW3;
-            const int64_t a = y0 + i, b = x0 + j;
-            if (a >= OH || b >= OW) continue;
-            A s[5];
+        __syncthreads();  // Vs holds the column sums of frame t
+        // 3. row running sums over the column sums (k x k x kt window sums of
+        //    SEG outputs per thread, lanes over rows) and the formula
+        if (threadIdx.x < Tile3<A>::TASKS3) {
+            const int i = threadIdx.x % OH, j0 = (threadIdx.x / OH) * SEG;
+            const int64_t a = y0 + i;
+            float accQ = 0.f, accC = 0.f;
+            if (a < OHt && x0 + j0 < OWt) {
+                const A *v0 = vs_of(sm, g, 0) + j0 * PV + i, *v1 = vs_of(sm, g, 1) + j0 * PV + i;
+                const A *v2 = vs_of(sm, g, 2) + j0 * PV + i, *v3 = vs_of(sm, g, 3) + j0 * PV + i;
+                A su = 0, sw = 0, su2 = 0, sw2 = 0;
+#pragma unroll 4
+                for (int m = 0; m < g.k; ++m) {
+                    su += v0[m * PV];
+                    sw += v1[m * PV];
+                    su2 += v2[m * PV];
+                    sw2 += v3[m * PV];
+                }
+                const int nout = (int)min((int64_t)SEG, OWt - (x0 + j0));
+                float *mrow = L.map ? L.map + t * L.map_fs + a * L.map_ld + x0 + j0 : nullptr;
 #pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                const U *vr = reinterpret_cast<const U *>(vs_of(sm, g, q) + i * g.pw);
-                s[q] = (A)(vr[j + g.k] - vr[j]);
+                for (int e = 0; e < SEG; ++e) {
+                    if (e > 0) {
+                        const int in = (e + g.k - 1) * PV, out = (e - 1) * PV;
+                        su += v0[in] - v0[out];
+                        sw += v1[in] - v1[out];
+                        su2 += v2[in] - v2[out];
+                        sw2 += v3[in] - v3[out];
+                    }
+                    if (e < nout) {
+                        float A1, B1;
+                        int64_t Vu, Vw;
+                        if constexpr (sizeof(A) == 4) {
+                            // |Su|, |Sw| <= 510 N < 2^23 (N < 8256 here): exact in fp32, and
+                            // Su^2 - Sw^2 = (Su - Sw)(Su + Sw) rounds once
+                            const float fu = (float)su, fw = (float)sw;
+                            A1 = fmaf(fu - fw, fu + fw, L.C1x2n2);
+                            B1 = fmaf(fu, fu, fmaf(fw, fw, L.C1x2n2));
+                            const int n32 = (int)N;
+                            Vu = (int64_t)n32 * su2 - (int64_t)su * su;
+                            Vw = (int64_t)n32 * sw2 - (int64_t)sw * sw;
+                        } else {
+                            const int64_t U2 = (int64_t)su * su, W2 = (int64_t)sw * sw;
+                            Vu = N * (int64_t)su2 - U2;
+                            Vw = N * (int64_t)sw2 - W2;
+                            A1 = __ll2float_rn(U2 - W2) + L.C1x2n2;
+                            B1 = __ll2float_rn(U2 + W2) + L.C1x2n2;
+                        }
+                        // variances need the exact int64 differences
+                        const float A2 = __ll2float_rn(Vu - Vw) + L.C2x2n2, B2 = __ll2float_rn(Vu + Vw) + L.C2x2n2;
+                        const float cs = __fdividef(A2, B2);
+                        const float qv = __fdividef(A1, B1) * cs;
+                        accQ += qv;
+                        accC += cs;
+                        if (mrow) mrow[e] = qv;
+                    }
+                }
             }
-            // exact int64 numerators over N pixels (the box formula times N^2)
-            const int64_t s1x = s[0], s1y = s[1];
-            const int64_t P2 = 2 * s1x * s1y, Q1 = s1x * s1x + s1y * s1y;
-            const int64_t Nxy = N * (int64_t)s[4] - s1x * s1y;
-            const int64_t T2 = (N * (int64_t)s[2] - s1x * s1x) + (N * (int64_t)s[3] - s1y * s1y);
-            const float A1 = __ll2float_rn(P2) + L.C1n2, B1 = __ll2float_rn(Q1) + L.C1n2;
-            const float A2 = fmaf(2.f, __ll2float_rn(Nxy), L.C2n2), B2 = __ll2float_rn(T2) + L.C2n2;
-            const float cs = __fdividef(A2, B2);
-            const float qv = __fdividef(A1, B1) * cs;
-            accQ += qv;
-            accC += cs;
-            if (L.map) L.map[t * L.map_fs + a * L.map_ld + b] = qv;
-        }
-        // CTA sums -> this (tile, frame) partial
+            // warp sums -> red[warp]; thread 0 adds them up after the next
+            // barrier (or after the loop) into this (frame, tile) partial
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            accQ += __shfl_down_sync(0xffffffffu, accQ, o);
-            accC += __shfl_down_sync(0xffffffffu, accC, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                accQ += __shfl_down_sync(0xffffffffu, accQ, o);
+                accC += __shfl_down_sync(0xffffffffu, accC, o);
+            }
+            if (lane == 0)
+                reinterpret_cast<double2 *>(vs_of(sm, g, 4))[threadIdx.x >> 5] =
+                    make_double2((double)accQ, (double)accC);
         }
-        if (lane == 0) {
-            red[2 * warp] = accQ;
-            red[2 * warp + 1] = accC;
+        pending = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && pending >= 0) flush(pending);
+}
+
+// One CTA per output frame: per level, the fixed-order sum of the frame's
+// tile partials times 1 / positions -> (mean Q_j, mean cs_j); then the frame
+// score (m_j = mean cs_j for j < S, m_S = mean Q_S, combined as in MS-SSIM).
+__global__ void __launch_bounds__(256) frame_scores_kernel(const Ms3dFinalize F, double *frame_scores,
+                                                           double *per_scale_out) {
+    __shared__ double rq[256], rc[256];
+    __shared__ double mq[GBSSIM_MAX_SCALES], mc[GBSSIM_MAX_SCALES];
+    const int t = blockIdx.x;
+    for (int j = 0; j < F.scales; ++j) {
+        const double2 *p = F.partials[j] + (int64_t)t * F.items[j];
+        double q = 0.0, c = 0.0;
+        for (int i = threadIdx.x; i < F.items[j]; i += 256) {
+            q += p[i].x;
+            c += p[i].y;
         }
+        rq[threadIdx.x] = q;
+        rc[threadIdx.x] = c;
         __syncthreads();
+        for (int s = 128; s > 0; s >>= 1) {
+            if (threadIdx.x < s) {
+                rq[threadIdx.x] += rq[threadIdx.x + s];
+                rc[threadIdx.x] += rc[threadIdx.x + s];
+            }
+            __syncthreads();
+        }
         if (threadIdx.x == 0) {
-            double sq = 0.0, sc = 0.0;
-            for (int w = 0; w < NT / 32; ++w) {
-                sq += (double)red[2 * w];
-                sc += (double)red[2 * w + 1];
-            }
-            L.partials[(int64_t)t * tiles_x * tiles_y + tile] = make_double2(sq, sc);
+            mq[j] = rq[0] * F.inv_n[j];
+            mc[j] = rc[0] * F.inv_n[j];
         }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double wsum = 0.0;
+        for (int j = 0; j < F.scales; ++j) wsum += F.exps[j];
+        double v = F.combine == GBSSIM_COMBINE_SUM ? 0.0 : 1.0;
+        for (int j = 0; j < F.scales; ++j) {
+            const double m = j == F.scales - 1 ? mq[j] : mc[j];
+            if (F.combine == GBSSIM_COMBINE_SUM) v += F.exps[j] / wsum * m;
+            else v *= pow(m, F.exps[j]);  // NaN for m < 0 under a non-integer exponent
+            if (per_scale_out) {
+                per_scale_out[((int64_t)t * F.scales + j) * 2] = mc[j];
+                per_scale_out[((int64_t)t * F.scales + j) * 2 + 1] = mq[j];
+            }
+        }
+        frame_scores[t] = v;
     }
 }
 
 // Mean of the frame scores in a fixed order (one CTA).
-__global__ void frame_mean_kernel(const double *frames, int n, double *out) {
+__global__ void __launch_bounds__(256) frame_mean_kernel(const double *frames, int n, double *out) {
     __shared__ double red[256];
     double loc = 0.0;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) loc += frames[t];
+    for (int t = threadIdx.x; t < n; t += 256) loc += frames[t];
     red[threadIdx.x] = loc;
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    for (int s = 128; s > 0; s >>= 1) {
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
@@ -298,42 +436,68 @@ __global__ void frame_mean_kernel(const double *frames, int n, double *out) {
 
 template <typename A>
 size_t smem_bytes(int k) {
-    constexpr int OH3 = TileRows<A>::v;
-    const size_t ih = OH3 + k - 1, iw = OW3 + k - 1, pw = (iw + 4) & ~(size_t)3;
-    return sizeof(A) * (5 * ih * pw + 5 * OH3 * pw) + sizeof(float) * 2 * (NT / 32);
+    const size_t ih = Tile3<A>::OH + k - 1, iw = OW3 + k - 1, pw = (iw + 3) & ~(size_t)3;
+    return sizeof(A) * (4 * ih * pw + 4 * iw * Tile3<A>::PV) + sizeof(double2) * Tile3<A>::WARPS3;
 }
 
 template <typename A, typename In>
 cudaError_t launch_level(const Ssim3dLaunch &L, cudaStream_t st) {
     int tx, ty;
-    ssim3d_tiles(L.x.H, L.x.W, L.k, sizeof(A) == 4, &tx, &ty);
+    ssim3d_tiles(L.x.H, L.x.W, L.k, sizeof(A) == 8, &tx, &ty);
     static bool attr_set[64] = {};
+    static int slots[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const size_t smem = smem_bytes<A>(L.k);
     if (!attr_set[dev]) {
         const cudaError_t e = cudaFuncSetAttribute(ssim3d_kernel<A, In>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)smem_bytes<A>(kSsim3dMaxK));
         if (e != cudaSuccess) return e;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return cudaErrorUnknown;
+        slots[dev] = sms;
         attr_set[dev] = true;
     }
-    ssim3d_kernel<A, In><<<tx * ty, NT, smem_bytes<A>(L.k), st>>>(L, tx, ty);
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ssim3d_kernel<A, In>, NT, smem) != cudaSuccess)
+        return cudaErrorUnknown;
+    // Split the output frames into chunks (each CTA primes its own temporal
+    // sums with kt-1 frames) when the tiles alone fill fewer than two waves;
+    // chunks keep at least max(2, kt) output frames.  Every output frame is
+    // computed by one CTA with exact integer sums: the result does not depend
+    // on the split.
+    const int tiles = tx * ty, frames = L.T - L.kt + 1;
+    const int wave = max(1, per_sm) * slots[dev];
+    int chunks = 1;
+    if (tiles < 2 * wave) {
+        const int want = (2 * wave + tiles - 1) / tiles;
+        chunks = max(1, min(want, frames / max(2, L.kt)));
+    }
+    const int t_chunk = (frames + chunks - 1) / chunks;
+    chunks = (frames + t_chunk - 1) / t_chunk;
+    ssim3d_kernel<A, In><<<tiles * chunks, NT, smem, st>>>(L, tx, ty, t_chunk);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-void ssim3d_tiles(int64_t H, int64_t W, int k, bool level0, int *tx, int *ty) {
-    const int oh = level0 ? TileRows<int>::v : TileRows<long long>::v;
+void ssim3d_tiles(int64_t H, int64_t W, int k, bool wide, int *tx, int *ty) {
+    const int oh = wide ? Tile3<long long>::OH : Tile3<int>::OH;
     *tx = (int)((W - k + 1 + OW3 - 1) / OW3);
     *ty = (int)((H - k + 1 + oh - 1) / oh);
 }
 
-cudaError_t launch_ssim3d_level(const Ssim3dLaunch &L, bool level0, cudaStream_t st) {
-    return level0 ? launch_level<int, uint8_t>(L, st) : launch_level<long long, float>(L, st);
+cudaError_t launch_ssim3d_level(const Ssim3dLaunch &L, bool u8_input, bool wide, cudaStream_t st) {
+    if (!u8_input) return launch_level<long long, float>(L, st);
+    return wide ? launch_level<long long, uint8_t>(L, st) : launch_level<int, uint8_t>(L, st);
 }
 
-cudaError_t launch_frame_mean(const double *frames, int n, double *out, cudaStream_t st) {
-    frame_mean_kernel<<<1, 256, 0, st>>>(frames, n, out);
+cudaError_t launch_ssim3d_finalize(const Ms3dFinalize &F, double *frame_scores, double *per_scale_out,
+                                   double *score_out, cudaStream_t st) {
+    frame_scores_kernel<<<F.frames, 256, 0, st>>>(F, frame_scores, per_scale_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !score_out) return e;
+    frame_mean_kernel<<<1, 256, 0, st>>>(frame_scores, F.frames, score_out);
     return cudaGetLastError();
 }
 

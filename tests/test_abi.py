@@ -204,10 +204,15 @@ def test_ssim3d_and_msssim3d_validation(g):
     assert _ws3d(g, _plane(g, 256, 256, 4), g.make_params(k=32, scales=2, **box), 2)[0] == g.ERR_UNSUPPORTED
     assert _ws3d(g, _plane(g, 256, 256, 4), g.make_params(k=31, scales=1, **box), 2)[0] == 0
     assert _ws3d(g, _plane(g, 256, 256, 4), g.make_params(k=31, scales=2, **box), 2)[0] == 0
-    # exact-integer range: level 0 k^2 kt 255^2 < 2^31; level 4 2 N^2 (255 16^2)^2 < 2^62
-    assert _ws3d(g, _plane(g, 512, 512, 40), g.make_params(k=29, scales=1, **box), 40)[0] == g.ERR_UNSUPPORTED
-    assert _ws3d(g, _plane(g, 512, 512, 40), g.make_params(k=29, scales=5, **box), 27)[0] == 0
-    assert _ws3d(g, _plane(g, 512, 512, 40), g.make_params(k=29, scales=5, **box), 28)[0] == g.ERR_UNSUPPORTED
+    # exact-integer range 5 N^2 (255 4^j)^2 < 2^63 with N = k^2 kt: level 0
+    # takes N < 5.3e6 (int64 sums past N = 8256), level 4 N <= 20800
+    assert _ws3d(g, _plane(g, 512, 512, 40), g.make_params(k=29, scales=1, **box), 40)[0] == 0
+    assert _ws3d(g, _plane(g, 64, 64, 6000), g.make_params(k=31, scales=1, **box), 5600,
+                 "gbssim_ssim3d_workspace_size")[0] == g.ERR_UNSUPPORTED
+    assert _ws3d(g, _plane(g, 64, 64, 6000), g.make_params(k=31, scales=1, **box), 5500,
+                 "gbssim_ssim3d_workspace_size")[0] == 0
+    assert _ws3d(g, _plane(g, 512, 512, 40), g.make_params(k=29, scales=5, **box), 24)[0] == 0
+    assert _ws3d(g, _plane(g, 512, 512, 40), g.make_params(k=29, scales=5, **box), 25)[0] == g.ERR_UNSUPPORTED
     # levels below k, kt > T, Gaussian windows, other dtypes
     assert _ws3d(g, _plane(g, 100, 100, 4), g.make_params(k=11, scales=5, **box), 2)[0] == g.ERR_TOO_SMALL
     assert _ws3d(g, _plane(g, 100, 100, 4), g.make_params(k=11, scales=3, **box), 5)[0] == g.ERR_TOO_SMALL

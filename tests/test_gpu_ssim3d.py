@@ -32,7 +32,9 @@ def _video(T, H, W, seed=0):
 
 
 @pytest.mark.parametrize("T,H,W,k,kt", [(9, 40, 70, 11, 5), (6, 33, 150, 5, 3), (4, 26, 64, 11, 1),
-                                        (12, 20, 21, 3, 12), (7, 80, 129, 8, 4)])
+                                        (12, 20, 21, 3, 12), (7, 80, 129, 8, 4),
+                                        (10, 40, 100, 31, 9),   # N = 8649: int64 window sums
+                                        (20, 24, 40, 3, 2), (16, 30, 50, 5, 3)])  # few tiles: frames split over CTAs
 def test_ssim3d_matches_oracle(g, T, H, W, k, kt):
     x, y = _video(T, H, W, seed=T + k)
     score, frames, q = g.ssim3d(x.to(DEV), y.to(DEV), kt=kt, k=k, return_map=True)
@@ -87,6 +89,7 @@ def test_ssim3d_rejects_unsupported(g):
     (4, 176, 200, 11, 2, 4, "product"),
     (3, 248, 256, 31, 3, 4, "product"),  # largest window
     (7, 70, 90, 3, 7, 2, "sum"),        # one output frame
+    (14, 64, 72, 3, 2, 3, "product"),   # frames split over CTAs on every level
 ])
 def test_msssim3d_matches_oracle(g, T, H, W, k, kt, scales, combine):
     x, y = _video(T, H, W, seed=T + k + scales)
