@@ -439,7 +439,8 @@ def run_case(args):
     (11 x 11 x 5) of 40 luma frames of 1920x1080; msssim3d = MS-SSIM-3D (5
     scales) of the same frames; ragged = one MS-SSIM run of a batch plan
     over 72 ragged pairs (64 drawn from the six resolutions, 8 odd sizes;
-    default tuning).  Prints one JSON
+    default tuning); pool = mean pooling of the 64 stored SSIM maps
+    (1070 x 1910 fp32).  Prints one JSON
     line with the mean time per call (CUDA events)."""
     import torch
 
@@ -462,6 +463,13 @@ def run_case(args):
             fn = lambda: gbssim.ssim3d(vx, vy, kt=5, k=11)
         else:
             fn = lambda: gbssim.msssim3d(vx, vy, kt=5, k=11, scales=5)
+    elif args.case == "pool":
+        x, y = synth.luma_pairs_u8(N_PAIRS, H, W)
+        _, qmap = gbssim.ssim(x.to(dev), y.to(dev), return_map=True)
+        nq, hq, wq = qmap.shape
+        pq = gbssim.Plane(qmap.data_ptr(), gbssim.F32, nq, hq, wq, qmap.stride(1), qmap.stride(0))
+        wsq = gbssim.workspace(pq, gbssim.Params(), gbssim.OP_POOL, dev)
+        fn = lambda: gbssim.ssim_pool(qmap, "mean", ws=wsq)
     elif args.case == "ragged":
         sizes = synth.ragged_sizes(64, 8)
         xs, ys = synth.ragged_pairs_u8(sizes, device=dev)
@@ -497,7 +505,8 @@ def main():
     ap.add_argument("--impl", default="gbssim", choices=["gbssim", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the box-window and loss fwd+bwd figures")
-    ap.add_argument("--case", choices=["scale0", "box8s4", "loss", "ssim3d", "msssim3d", "ragged"], default=None,
+    ap.add_argument("--case", choices=["scale0", "box8s4", "loss", "ssim3d", "msssim3d", "ragged", "pool"],
+                    default=None,
                     help="run one secondary workload alone (for profilers) instead of the benchmark")
     args = ap.parse_args()
     if args.case:

@@ -27,6 +27,67 @@ constexpr int NT = 256;
 constexpr int PR = 16;          // map rows per item (moment partial sums, select counts)
 constexpr int NBIN = 256;       // histogram bins per select pass (8 key bits)
 constexpr int UNR = 8;          // loads in flight per thread and row
+constexpr int64_t CHK = 32768;  // map elements per item of a dense map (flat chunks)
+constexpr int UNR4 = 4;         // float4 loads in flight per thread (dense maps)
+
+// Calls f(q, mu) for every element of one work item: with DENSE (ld == w and
+// 16-byte aligned images) the flat chunk [item CHK, (item + 1) CHK) read as
+// float4 groups, UNR4 of them in flight per thread; else PR rows, UNR scalar
+// loads in flight per thread and row.  `ax` (nullable) is read alongside.
+template <bool DENSE, typename F>
+__device__ __forceinline__ void for_item(const float *m, const float *ax, int64_t h, int64_t w, int64_t ld,
+                                         int item, F &&f) {
+    if constexpr (DENSE) {
+        const int64_t n = h * w, e0 = (int64_t)item * CHK, e1 = min(e0 + CHK, n);
+        for (int64_t g0 = e0 + 4 * threadIdx.x; g0 < e1; g0 += 4 * NT * UNR4) {
+            float4 v[UNR4], u[UNR4];
+#pragma unroll
+            for (int k = 0; k < UNR4; ++k) {  // all loads first
+                const int64_t e = g0 + 4 * NT * k;
+                v[k] = u[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (e + 4 <= e1) {
+                    v[k] = __ldg(reinterpret_cast<const float4 *>(m + e));
+                    if (ax) u[k] = __ldg(reinterpret_cast<const float4 *>(ax + e));
+                } else if (e < e1) {
+                    v[k].x = __ldg(m + e);
+                    if (e + 1 < e1) v[k].y = __ldg(m + e + 1);
+                    if (e + 2 < e1) v[k].z = __ldg(m + e + 2);
+                    if (ax) {
+                        u[k].x = __ldg(ax + e);
+                        if (e + 1 < e1) u[k].y = __ldg(ax + e + 1);
+                        if (e + 2 < e1) u[k].z = __ldg(ax + e + 2);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < UNR4; ++k) {
+                const int64_t e = g0 + 4 * NT * k;
+                if (e < e1) f(v[k].x, u[k].x);
+                if (e + 1 < e1) f(v[k].y, u[k].y);
+                if (e + 2 < e1) f(v[k].z, u[k].z);
+                if (e + 3 < e1) f(v[k].w, u[k].w);
+            }
+        }
+    } else {
+        const int64_t r0 = (int64_t)item * PR;
+        for (int64_t row = r0; row < min(r0 + PR, h); ++row) {
+            const float *rp = m + row * ld;
+            const float *ap = ax ? ax + row * ld : nullptr;
+            for (int64_t c0 = 0; c0 < w; c0 += UNR * NT) {
+                float v[UNR], u[UNR];
+#pragma unroll
+                for (int k = 0; k < UNR; ++k) {  // all loads first
+                    const int64_t col = c0 + threadIdx.x + k * NT;
+                    v[k] = col < w ? __ldg(rp + col) : 0.f;
+                    u[k] = ap && col < w ? __ldg(ap + col) : 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < UNR; ++k)
+                    if (c0 + threadIdx.x + k * NT < w) f(v[k], u[k]);
+            }
+        }
+    }
+}
 
 struct KSumP {
     float s = 0.f, c = 0.f;
@@ -50,10 +111,27 @@ __device__ __forceinline__ float key2f(unsigned k) {
 enum MomentOp { M_SUM = 0, M_SQDEV = 1, M_ABSDEV_P = 2, M_MINK = 3, M_DW = 4, M_LOG_D = 5, M_INV_D = 6, M_PP = 7,
                 M_LW = 8 };
 
+// d^p, by multiplication for the small integer exponents (uniform across
+// the launch, so the branch costs nothing), else powf.
+__device__ __forceinline__ float pow_arg(float d, float p) {
+    if (p == 1.f) return d;
+    if (p == 2.f) return d * d;
+    if (p == 3.f) return d * d * d;
+    if (p == 4.f) {
+        const float d2 = d * d;
+        return d2 * d2;
+    }
+    return powf(d, p);
+}
+
+// Ops whose second sum b is not always zero.
+__host__ __device__ constexpr bool has_b(int op) { return op == M_DW || op == M_LOG_D || op == M_INV_D; }
+
 // Per-element contribution (a, b) of moment op `op`; m = the image's mean
 // (or the PP threshold), p, r = arguments; mu = the auxiliary map's value
 // (luminance-weighted pooling: the reference's local mean, p = a_s, r = b_s).
-__device__ __forceinline__ void contrib(int op, float q, float m, float p, float r, float mu, float &a, float &b) {
+template <int op>
+__device__ __forceinline__ void contrib(float q, float m, float p, float r, float mu, float &a, float &b) {
     b = 0.f;
     switch (op) {
     case M_LW: {
@@ -62,9 +140,9 @@ __device__ __forceinline__ void contrib(int op, float q, float m, float p, float
     } break;
     case M_SUM: a = q; break;
     case M_SQDEV: { const float d = q - m; a = d * d; } break;
-    case M_ABSDEV_P: a = powf(fabsf(q - m), p); break;
-    case M_MINK: a = powf(1.f - q, p); break;
-    case M_DW: { const float w = powf(1.f - q, p); a = w * q; b = w; } break;
+    case M_ABSDEV_P: a = pow_arg(fabsf(q - m), p); break;
+    case M_MINK: a = pow_arg(1.f - q, p); break;
+    case M_DW: { const float w = pow_arg(1.f - q, p); a = w * q; b = w; } break;
     // a zero dissimilarity is counted in b (its log / reciprocal is infinite,
     // which a compensated sum cannot carry); any such value makes GM / HM 0
     case M_LOG_D: { const float d = 1.f - q; a = d == 0.f ? 0.f : logf(d); b = d == 0.f ? 1.f : 0.f; } break;
@@ -95,12 +173,12 @@ __device__ __forceinline__ void block_sum2d(double &a, double &b, double *red) {
     }
 }
 
+template <bool DENSE, int op>
 __global__ void __launch_bounds__(NT) moment_kernel(const float *map, int64_t h, int64_t w, int64_t ld, int64_t is,
-                                                    int items, int op, const double *center, float p, float r,
+                                                    int items, const double *center, float p, float r,
                                                     const float *aux, double2 *partials) {
     __shared__ double red[2 * NT / 32];
     const int img = blockIdx.y;
-    const int64_t r0 = (int64_t)blockIdx.x * PR;
     const float *m = map + img * is;
     const float *ax = aux ? aux + img * is : nullptr;
     float c = 0.f;
@@ -112,27 +190,12 @@ __global__ void __launch_bounds__(NT) moment_kernel(const float *map, int64_t h,
         if ((double)c > cd) c = nextafterf(c, -INFINITY);
     }
     KSumP sa, sb;
-    for (int64_t row = r0; row < min(r0 + PR, h); ++row) {
-        const float *rp = m + row * ld;
-        const float *ap = ax ? ax + row * ld : nullptr;
-        for (int64_t c0 = 0; c0 < w; c0 += UNR * NT) {
-            float v[UNR], u[UNR];
-#pragma unroll
-            for (int k = 0; k < UNR; ++k) {  // all loads first
-                const int64_t col = c0 + threadIdx.x + k * NT;
-                v[k] = col < w ? __ldg(rp + col) : 0.f;
-                u[k] = ap && col < w ? __ldg(ap + col) : 0.f;
-            }
-#pragma unroll
-            for (int k = 0; k < UNR; ++k)
-                if (c0 + threadIdx.x + k * NT < w) {
-                    float a, b;
-                    contrib(op, v[k], c, p, r, u[k], a, b);
-                    sa.add(a);
-                    sb.add(b);
-                }
-        }
-    }
+    for_item<DENSE>(m, op == M_LW ? ax : nullptr, h, w, ld, blockIdx.x, [&](float q, float mu) {
+        float a, b;
+        contrib<op>(q, c, p, r, mu, a, b);
+        sa.add(a);
+        if constexpr (has_b(op)) sb.add(b);
+    });
     double da = (double)sa.get(), db = (double)sb.get();
     block_sum2d(da, db, red);
     if (threadIdx.x == 0) partials[(int64_t)img * items + blockIdx.x] = make_double2(da, db);
@@ -200,6 +263,7 @@ __device__ void unique_prefixes(SelState &s) {
 // into slot 0).  Each thread keeps a run-length count of its last (slot, bin)
 // and only adds to shared memory when the bin changes: neighbouring SSIM
 // values mostly share a bin, so few shared atomics contend.
+template <bool DENSE>
 __global__ void __launch_bounds__(NT) select_hist_kernel(const float *map, int64_t h, int64_t w, int64_t ld,
                                                          int64_t is, int pass, const SelState *st,
                                                          unsigned *hist) {
@@ -210,7 +274,6 @@ __global__ void __launch_bounds__(NT) select_hist_kernel(const float *map, int64
     for (int i = threadIdx.x; i < nu * NBIN; i += NT) (&sh[0][0])[i] = 0u;
     if (threadIdx.x < nu) up[threadIdx.x] = pass == 0 ? 0u : st[img].uprefix[threadIdx.x];
     __syncthreads();
-    const int64_t r0 = (int64_t)blockIdx.x * PR;
     const float *m = map + img * is;
     const int fixed = 32 - 8 * pass;  // bits above `fixed` are already known
     unsigned run_key = 0xffffffffu, run_n = 0u;  // (slot << 8 | bin) of the current run
@@ -223,33 +286,20 @@ __global__ void __launch_bounds__(NT) select_hist_kernel(const float *map, int64
             run_n = 1u;
         }
     };
-    for (int64_t row = r0; row < min(r0 + PR, h); ++row) {
-        const float *rp = m + row * ld;
-        for (int64_t c0 = 0; c0 < w; c0 += UNR * NT) {
-            float v[UNR];
-#pragma unroll
-            for (int k = 0; k < UNR; ++k) {
-                const int64_t col = c0 + threadIdx.x + k * NT;
-                v[k] = col < w ? __ldg(rp + col) : 0.f;
-            }
-#pragma unroll
-            for (int k = 0; k < UNR; ++k) {
-                if (c0 + threadIdx.x + k * NT >= w) continue;
-                const unsigned key = f2key(v[k]);
-                const unsigned bin = (key >> (fixed - 8)) & (NBIN - 1);
-                if (pass == 0) {
-                    count(bin);
-                } else {
-                    const unsigned hb = key >> fixed;
-                    for (int u = 0; u < nu; ++u)
-                        if (hb == up[u]) {
-                            count(((unsigned)u << 8) | bin);
-                            break;
-                        }
+    for_item<DENSE>(m, nullptr, h, w, ld, blockIdx.x, [&](float q, float) {
+        const unsigned key = f2key(q);
+        const unsigned bin = (key >> (fixed - 8)) & (NBIN - 1);
+        if (pass == 0) {
+            count(bin);
+        } else {
+            const unsigned hb = key >> fixed;
+            for (int u = 0; u < nu; ++u)
+                if (hb == up[u]) {
+                    count(((unsigned)u << 8) | bin);
+                    break;
                 }
-            }
         }
-    }
+    });
     if (run_n) atomicAdd(&(&sh[0][0])[run_key], run_n);
     __syncthreads();
     unsigned *hi = hist + (int64_t)img * kPoolMaxRanks * NBIN;
@@ -378,7 +428,8 @@ cudaError_t launch_local_mean(const ImgDesc &x, int dtype, int count, const Taps
 // Workspace: partials, per-image centre, selection state, histograms.
 PoolLayout pool_layout(int64_t h, int64_t w, int count) {
     PoolLayout L;
-    L.items = (int)((h + PR - 1) / PR);
+    // partial slots for either item form (PR rows, or CHK flat elements)
+    L.items = (int)max((h + PR - 1) / PR, (h * w + CHK - 1) / CHK);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t at = off;
@@ -401,12 +452,36 @@ cudaError_t launch_pool_map(const float *map, int64_t h, int64_t w, int64_t ld, 
     SelState *sel = reinterpret_cast<SelState *>(ws + L.state);
     unsigned *hist = reinterpret_cast<unsigned *>(ws + L.hist);
     const double n = (double)h * (double)w;
-    const dim3 grid(L.items, count);
+    // dense maps (and mu_1 maps) with 16-byte aligned images: flat chunks
+    const bool dense = ld == w && (uintptr_t)map % 16 == 0 && (count == 1 || is % 4 == 0) &&
+                       (!aux || (uintptr_t)aux % 16 == 0);
+    const int items = dense ? (int)((h * w + CHK - 1) / CHK) : (int)((h + PR - 1) / PR);
+    const dim3 grid(items, count);
     const int fb = (count + 127) / 128;
     cudaError_t e = cudaSuccess;
     auto moment = [&](int op, const double *c, double p, double r, int kindv, int stage) {
-        moment_kernel<<<grid, NT, 0, st>>>(map, h, w, ld, is, L.items, op, c, (float)p, (float)r, aux, part);
-        moment_finalize_kernel<<<fb, 128, 0, st>>>(part, L.items, count, n, kindv, p, a1, stage, center, out);
+        const float pf = (float)p, rf = (float)r;
+#define GBSSIM_MOMENT(OP)                                                                                           \
+    case OP:                                                                                                        \
+        if (dense)                                                                                                  \
+            moment_kernel<true, OP><<<grid, NT, 0, st>>>(map, h, w, ld, is, items, c, pf, rf, aux, part);          \
+        else                                                                                                        \
+            moment_kernel<false, OP><<<grid, NT, 0, st>>>(map, h, w, ld, is, items, c, pf, rf, aux, part);         \
+        break;
+        switch (op) {
+            GBSSIM_MOMENT(M_SUM)
+            GBSSIM_MOMENT(M_SQDEV)
+            GBSSIM_MOMENT(M_ABSDEV_P)
+            GBSSIM_MOMENT(M_MINK)
+            GBSSIM_MOMENT(M_DW)
+            GBSSIM_MOMENT(M_LOG_D)
+            GBSSIM_MOMENT(M_INV_D)
+            GBSSIM_MOMENT(M_PP)
+            GBSSIM_MOMENT(M_LW)
+        default: return cudaErrorInvalidValue;
+        }
+#undef GBSSIM_MOMENT
+        moment_finalize_kernel<<<fb, 128, 0, st>>>(part, items, count, n, kindv, p, a1, stage, center, out);
         return cudaGetLastError();
     };
     auto select = [&](double parg) {
@@ -414,7 +489,10 @@ cudaError_t launch_pool_map(const float *map, int64_t h, int64_t w, int64_t ld, 
         for (int pass = 0; pass < 4; ++pass) {
             cudaError_t r = cudaMemsetAsync(hist, 0, sizeof(unsigned) * (size_t)kPoolMaxRanks * NBIN * count, st);
             if (r != cudaSuccess) return r;
-            select_hist_kernel<<<grid, NT, 0, st>>>(map, h, w, ld, is, pass, sel, hist);
+            if (dense)
+                select_hist_kernel<true><<<grid, NT, 0, st>>>(map, h, w, ld, is, pass, sel, hist);
+            else
+                select_hist_kernel<false><<<grid, NT, 0, st>>>(map, h, w, ld, is, pass, sel, hist);
             select_step_kernel<<<count, 32, 0, st>>>(sel, hist, pass);
         }
         select_finalize_kernel<<<fb, 128, 0, st>>>(sel, count, n, kind, parg, center, out);

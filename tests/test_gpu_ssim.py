@@ -307,8 +307,9 @@ def test_msssim_identity_and_negative_domain(g, synth):
 
 
 def test_msssim_1080p_batch_sampled(g, synth):
-    """The benchmark's configuration (64 pairs of 1920x1080, one launch per
-    level) checked on sampled pairs against the oracle."""
+    """The benchmark's configuration (64 pairs of 1920x1080, the one
+    persistent launch over all levels that bench.py times) checked on sampled
+    pairs against the oracle."""
     n = 64
     x, y = synth.luma_pairs_u8(n, 1080, 1920, device=DEV)
     score, per = g.msssim(x, y, per_scale=True)
