@@ -161,13 +161,39 @@ def mean(v) -> float:
     return float(_load().oracle_mean(_ptr(v), v.size))
 
 
+def extend_border(img, k: int, border: str = "valid") -> np.ndarray:
+    """The image extended for a k x k window (Section "Salient Features of
+    SSIM and MS-SSIM Implementations", the border-handling column: zero
+    padding, reflection padding, or only valid outputs).  Reading:
+    floor((k-1)/2) rows / columns before and the rest of k-1 after, so the
+    valid windows of the extended image give one output per input pixel at
+    stride 1; "zero" fills with 0, "reflect" mirrors about the image border
+    with the edge sample repeated (x(-1-i) = x(i), x(H+i) = x(H-1-i));
+    "valid" returns the image unchanged."""
+    a = _f64(img)
+    if border == "valid":
+        return a
+    before = (k - 1) // 2
+    after = k - 1 - before
+    H, W = a.shape
+    if border == "zero":
+        return np.pad(a, ((before, after), (before, after)), mode="constant")
+    if border == "reflect":
+        if min(H, W) < after:
+            raise ValueError("image smaller than the mirrored border")
+        return np.pad(a, ((before, after), (before, after)), mode="symmetric")
+    raise ValueError(border)
+
+
 def ssim(x, y, window_kind: str = "gaussian", k: int = 11, sigma: float = 1.5,
-         K1: float = 0.01, K2: float = 0.03, L: float = 255.0, stride: int = 1):
-    """SSIM map and MSSIM of one pair, valid borders.
+         K1: float = 0.01, K2: float = 0.03, L: float = 255.0, stride: int = 1, border: str = "valid"):
+    """SSIM map and MSSIM of one pair; border = "valid" (only windows inside
+    the image), "zero" or "reflect" (extend_border first).
 
     Returns ``(mssim, maps)`` with maps = {"q", "cs", "l", and the statistics}.
     """
     C1, C2 = constants(K1, K2, L)
+    x, y = extend_border(x, k, border), extend_border(y, k, border)
     st = window_stats(x, y, window(window_kind, k, sigma), stride)
     l, cs, q = ssim_terms(st, C1, C2)
     maps = dict(st, l=l, cs=cs, q=q)
@@ -299,7 +325,8 @@ def downsample2x2(img) -> np.ndarray:
 
 def msssim(x, y, scales: int = 5, exponents=MSSSIM_EXPONENTS, combine: str = "product",
            window_kind: str = "gaussian", k: int = 11, sigma: float = 1.5,
-           K1: float = 0.01, K2: float = 0.03, L: float = 255.0, pyramid: str = "avg2"):
+           K1: float = 0.01, K2: float = 0.03, L: float = 255.0, pyramid: str = "avg2",
+           border: str = "valid"):
     """MS-SSIM (Introduction; Section "Salient Features ...").
 
     Scale 1 is the input; scale j+1 is the 2x2 average of scale j
@@ -308,7 +335,9 @@ def msssim(x, y, scales: int = 5, exponents=MSSSIM_EXPONENTS, combine: str = "pr
     contrast-structure term is pooled at every scale and the luminance term
     only at the coarsest: m_j = mean cs_j for j < S and m_S = mean Q_S.
     combine="product": prod_j m_j^beta_j.  combine="sum" (Scikit-Video):
-    sum_j (beta_j / sum beta) m_j, a convex combination.
+    sum_j (beta_j / sum beta) m_j, a convex combination.  With border "zero"
+    or "reflect" each level is extended (extend_border) for its own SSIM
+    map; the pyramid is formed from the unextended levels.
     Returns (score, per_scale) with per_scale[j] = (mean cs_j, mean Q_j).
     """
     exps = np.asarray(exponents[:scales], np.float64)
@@ -319,7 +348,7 @@ def msssim(x, y, scales: int = 5, exponents=MSSSIM_EXPONENTS, combine: str = "pr
     a, b = _f64(x), _f64(y)
     per = []
     for j in range(scales):
-        st = window_stats(a, b, w, 1)
+        st = window_stats(extend_border(a, k, border), extend_border(b, k, border), w, 1)
         _, cs, q = ssim_terms(st, C1, C2)
         per.append((mean(cs), mean(q)))
         if j + 1 < scales:

@@ -65,7 +65,8 @@ def _check_map(qmap, ref_q, tol=MAP_TOL):
 
 # --------------------------------------------------------------------------- SSIM, Gaussian 11
 
-@pytest.mark.parametrize("h,w", [(256, 256), (300, 333), (11, 11), (12, 600), (600, 12), (150, 75), (91, 200)])
+@pytest.mark.parametrize("h,w", [(256, 256), (300, 333), (11, 11), (12, 600), (600, 12), (150, 75), (91, 200),
+                                 (11, 20011), (3000, 11)])
 def test_ssim_u8_matches_oracle(g, synth, h, w):
     x, y = synth.single_pair_u8(h, w)
     mean, qmap = g.ssim(x.to(DEV), y.to(DEV), return_map=True)
@@ -318,6 +319,21 @@ def test_msssim_1080p_batch_sampled(g, synth):
         assert abs(score[i].item() - ref) <= POOL_TOL
         np.testing.assert_allclose(per[i].cpu().numpy(), np.array(ref_per), rtol=0, atol=POOL_TOL)
     assert torch.isfinite(score).all() and (score > 0.5).all() and (score < 1).all()
+
+
+def test_8k_pair_full_map_and_msssim(g, synth):
+    """The largest frame size in the paper's workloads' range (7680 x 4320
+    UHD-2): every element of the SSIM map, the pooled score and MS-SSIM
+    against the oracle."""
+    x, y = synth.single_pair_u8(4320, 7680)
+    xd, yd = x.to(DEV), y.to(DEV)
+    mean, q = g.ssim(xd, yd, return_map=True)
+    ref_mean, ref = oracle.ssim(x.numpy(), y.numpy())
+    _check_map(q[0].cpu().numpy(), ref["q"])
+    assert abs(mean[0].item() - ref_mean) <= POOL_TOL
+    s = g.msssim(xd, yd)
+    ref_ms, _ = oracle.msssim(x.numpy(), y.numpy())
+    assert abs(s[0].item() - ref_ms) <= POOL_TOL
 
 
 def test_host_tensors_end_to_end(g, synth):

@@ -382,3 +382,75 @@ def test_temporal_pooling():
     w = r.uniform(0.5, 1.0, 120)
     _, p, _ = oracle.temporal_pool(w, 10.0)
     assert p == pytest.approx(np.percentile(w, 10.0), abs=1e-15)
+
+
+# ------------------------------------------------------------------ border extension
+
+def _embed_zero(a, before, after):
+    """Zero extension built by slice assignment (independent of np.pad)."""
+    H, W = a.shape
+    out = np.zeros((H + before + after, W + before + after))
+    out[before:before + H, before:before + W] = a
+    return out
+
+
+def _mirror_index(n, before, after):
+    """Indices of the half-sample mirror extension, x(-1-i) = x(i), x(n+i) = x(n-1-i)."""
+    left = list(range(before - 1, -1, -1))
+    right = list(range(n - 1, n - 1 - after, -1))
+    return np.array(left + list(range(n)) + right)
+
+
+@pytest.mark.parametrize("k", [11, 8, 3])
+def test_border_extension_layout(k):
+    r = np.random.default_rng(40)
+    a = r.uniform(0, 255, (23, 31))
+    before, after = (k - 1) // 2, k - 1 - (k - 1) // 2
+    np.testing.assert_array_equal(oracle.extend_border(a, k, "zero"), _embed_zero(a, before, after))
+    ri, ci = _mirror_index(23, before, after), _mirror_index(31, before, after)
+    np.testing.assert_array_equal(oracle.extend_border(a, k, "reflect"), a[np.ix_(ri, ci)])
+    np.testing.assert_array_equal(oracle.extend_border(a, k, "valid"), a)
+
+
+@pytest.mark.parametrize("border", ["zero", "reflect"])
+def test_border_maps_have_one_output_per_pixel_and_keep_the_interior(border):
+    r = np.random.default_rng(41)
+    x = r.uniform(0, 255, (40, 52))
+    y = np.clip(x + r.normal(0, 9, x.shape), 0, 255)
+    _, valid = oracle.ssim(x, y)
+    _, ext = oracle.ssim(x, y, border=border)
+    assert ext["q"].shape == x.shape
+    # windows wholly inside the image are the valid map, shifted by the border
+    np.testing.assert_allclose(ext["q"][5:-5, 5:-5], valid["q"], rtol=0, atol=1e-13)
+    # stride: the strided extended map keeps every s-th output
+    _, ext2 = oracle.ssim(x, y, border=border, stride=3)
+    np.testing.assert_allclose(ext2["q"], ext["q"][::3, ::3], rtol=0, atol=1e-13)
+
+
+def test_reflect_border_of_a_constant_image_is_constant():
+    x = np.full((30, 30), 90.0)
+    y = np.full((30, 30), 120.0)
+    C1, _ = oracle.constants()
+    _, m = oracle.ssim(x, y, border="reflect")
+    np.testing.assert_allclose(m["q"], (2 * 90 * 120 + C1) / (90 ** 2 + 120 ** 2 + C1), rtol=1e-10)
+    # zero extension lowers the corner means: the corner window sees 36 of 121 pixels weighted
+    _, z = oracle.ssim(x, y, border="zero", window_kind="box")
+    f = 36 / 121
+    mx, my = 90 * f, 120 * f
+    vx, vy, cxy = 90 ** 2 * f - mx ** 2, 120 ** 2 * f - my ** 2, 90 * 120 * f - mx * my
+    _, C2 = oracle.constants()
+    q00 = (2 * mx * my + C1) / (mx ** 2 + my ** 2 + C1) * (2 * cxy + C2) / (vx + vy + C2)
+    assert z["q"][0, 0] == pytest.approx(q00, rel=1e-12)
+
+
+def test_msssim_border_uses_unextended_pyramid():
+    r = np.random.default_rng(42)
+    x = r.uniform(0, 255, (96, 112))
+    y = np.clip(x + r.normal(0, 12, x.shape), 0, 255)
+    s, per = oracle.msssim(x, y, scales=3, exponents=(0.3, 0.3, 0.4), border="zero")
+    a, b = x, y
+    for j in range(3):
+        _, m = oracle.ssim(a, b, border="zero")
+        assert per[j][0] == pytest.approx(m["cs"].mean(), abs=1e-14)
+        assert per[j][1] == pytest.approx(m["q"].mean(), abs=1e-14)
+        a, b = oracle.downsample2x2(a), oracle.downsample2x2(b)
