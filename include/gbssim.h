@@ -108,6 +108,19 @@ typedef struct gbssim_params {
  * level sizes stay floor(H/2) x floor(W/2).  Forward only (the backward and
  * the batch API reject it with GBSSIM_ERR_UNSUPPORTED). */
 #define GBSSIM_FLAG_PYRAMID_97 2
+/* Border extension (Section "Salient Features of SSIM and MS-SSIM
+ * Implementations", border handling): instead of valid windows only, each
+ * level's image is extended by floor((k-1)/2) rows / columns before and
+ * k-1-floor((k-1)/2) after, with zeros (BORDER_ZERO) or with its mirror image
+ * about the border, edge samples repeated (BORDER_REFLECT: x(-1-i) = x(i)),
+ * and the valid windows of the extended image make the map: one output per
+ * input pixel at stride 1, floor((H-1)/s)+1 x floor((W-1)/s)+1 in general.
+ * The MS-SSIM pyramid is formed from the unextended levels.  Every level
+ * must be at least ceil((k-1)/2) pixels high and wide (else
+ * GBSSIM_ERR_TOO_SMALL).  gbssim_ssim_map and gbssim_msssim only; the other
+ * entry points return GBSSIM_ERR_UNSUPPORTED.  At most one of the two. */
+#define GBSSIM_FLAG_BORDER_ZERO 4
+#define GBSSIM_FLAG_BORDER_REFLECT 8
 
 /* Operation codes for gbssim_workspace_size. */
 typedef enum gbssim_op {

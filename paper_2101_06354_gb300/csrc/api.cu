@@ -50,8 +50,26 @@ int check_params(const gbssim_params *p) {
     for (int j = 0; j < p->scales; ++j)
         if (!isfinite(p->exponents[j])) return GBSSIM_ERR_INVALID_ARG;
     if (p->combine != GBSSIM_COMBINE_PRODUCT && p->combine != GBSSIM_COMBINE_SUM) return GBSSIM_ERR_INVALID_ARG;
-    if (p->flags & ~(GBSSIM_FLAG_BOX_TMA | GBSSIM_FLAG_PYRAMID_97)) return GBSSIM_ERR_INVALID_ARG;
+    if (p->flags & ~(GBSSIM_FLAG_BOX_TMA | GBSSIM_FLAG_PYRAMID_97 | GBSSIM_FLAG_BORDER_ZERO |
+                     GBSSIM_FLAG_BORDER_REFLECT))
+        return GBSSIM_ERR_INVALID_ARG;
+    if ((p->flags & GBSSIM_FLAG_BORDER_ZERO) && (p->flags & GBSSIM_FLAG_BORDER_REFLECT))
+        return GBSSIM_ERR_INVALID_ARG;
     return GBSSIM_OK;
+}
+
+// Border extension mode of the params: 0 valid only, 1 zero, 2 mirror.
+int border_mode(const gbssim_params *p) {
+    if (p->flags & GBSSIM_FLAG_BORDER_ZERO) return 1;
+    if (p->flags & GBSSIM_FLAG_BORDER_REFLECT) return 2;
+    return 0;
+}
+
+// check_params for the entry points that take valid windows only.
+int check_params_valid(const gbssim_params *p) {
+    const int rc = check_params(p);
+    if (rc) return rc;
+    return border_mode(p) ? GBSSIM_ERR_UNSUPPORTED : GBSSIM_OK;
 }
 
 void make_taps(const gbssim_params *p, float *g) {
@@ -121,7 +139,8 @@ int persistent_seg_rows(int j) {
 }
 
 struct Level {
-    int64_t H, W;
+    int64_t H, W;    // the level's image (pyramid level j)
+    int64_t RH, RW;  // the image the SSIM kernel runs on: H x W, or extended by k-1 (border modes)
     Path path;
     int items, seg_rows;
     int pitems, pseg_rows;       // the persistent MS-SSIM path's items per image and rows per item
@@ -131,6 +150,7 @@ struct Level {
 struct MsPlan {
     Level lv[GBSSIM_MAX_SCALES];
     size_t counter_off, done_off, status_off, zero_bytes;  // persistent path counters
+    size_t pad_off, pad_plane;                             // border modes: extended x then y (scratch)
     size_t bytes;
 };
 
@@ -138,19 +158,32 @@ int plan_levels(const gbssim_plane *x, const gbssim_params *p, int scales, MsPla
                 bool float_path = false) {
     size_t off = 0;
     int64_t H = x->height, W = x->width;
+    const int border = border_mode(p);
+    const int64_t ext = border ? p->k - 1 : 0;
+    size_t pad_plane = 0;
     for (int j = 0; j < scales; ++j) {
-        if (H < p->k || W < p->k) return GBSSIM_ERR_TOO_SMALL;
+        if (border ? (H < p->k - 1 - (p->k - 1) / 2 || H < 1 || W < p->k - 1 - (p->k - 1) / 2 || W < 1)
+                   : (H < p->k || W < p->k))
+            return GBSSIM_ERR_TOO_SMALL;
         Level &L = P->lv[j];
         L.H = H;
         L.W = W;
+        L.RH = H + ext;
+        L.RW = W + ext;
         const int dtype = j == 0 ? x->dtype : GBSSIM_F32;
+        if (border) {
+            if (L.RH > 65535) return GBSSIM_ERR_UNSUPPORTED;  // the extension grid's y extent
+            const size_t esz = dtype == GBSSIM_U8 ? 1 : (dtype == GBSSIM_F32 ? 4 : 2);
+            const size_t plane = esz * (size_t)L.RH * L.RW * x->count;
+            if (plane > pad_plane) pad_plane = plane;
+        }
         L.path = pick_path(dtype, p);
         if (float_path && L.path == PATH_BOX_U8) L.path = PATH_GENERIC;
         L.seg_rows = 0;
-        L.items = level_items(L.path, H, W, x->count, p, &L.seg_rows);
+        L.items = level_items(L.path, L.RH, L.RW, x->count, p, &L.seg_rows);
         L.pseg_rows = 0;
         L.pitems = 0;
-        if (L.path == PATH_GAUSS11) {
+        if (L.path == PATH_GAUSS11 && !border) {
             int strips, segs;
             L.pseg_rows = persistent_seg_rows(j);
             L.pitems = gauss11_items(H, W, L.pseg_rows, &strips, &segs);
@@ -171,17 +204,34 @@ int plan_levels(const gbssim_plane *x, const gbssim_params *p, int scales, MsPla
     P->status_off = P->done_off + sizeof(unsigned) * (size_t)scales * x->count;
     P->zero_bytes = P->status_off + 16 - P->counter_off;
     off = align_up(P->counter_off + P->zero_bytes);
+    P->pad_off = off;
+    P->pad_plane = align_up(pad_plane);
+    off += 2 * P->pad_plane;
     P->bytes = off;
     return GBSSIM_OK;
 }
 
 // The uint8 box path's tile layout (and so its item count) depends on the
 // alignment of the actual planes; the plan sized the workspace for the larger.
-void fix_box_items(Level &L, const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p) {
+void fix_box_items(Level &L, const ImgDesc &dx, const ImgDesc &dy, const gbssim_params *p) {
     if (L.path != PATH_BOX_U8) return;
-    const int64_t OH = out_dim(L.H, p->k, p->stride), OW = out_dim(L.W, p->k, p->stride);
-    L.items = box_path_items(OH, OW, p->k, p->stride, box_aligned16(desc_of(x), desc_of(y)),
-                             (p->flags & GBSSIM_FLAG_BOX_TMA) != 0);
+    const int64_t OH = out_dim(L.RH, p->k, p->stride), OW = out_dim(L.RW, p->k, p->stride);
+    L.items = box_path_items(OH, OW, p->k, p->stride, box_aligned16(dx, dy), (p->flags & GBSSIM_FLAG_BOX_TMA) != 0);
+}
+
+// Border modes: the level's images extended into the plan's scratch (dense
+// RH x RW planes of the same dtype); valid mode: the images themselves.
+cudaError_t extend_level(const Level &L, const MsPlan &P, char *ws, const gbssim_params *p, int dtype, int count,
+                         ImgDesc &dx, ImgDesc &dy, cudaStream_t st) {
+    const int border = border_mode(p);
+    if (!border) return cudaSuccess;
+    const int before = (p->k - 1) / 2;
+    char *px = ws + P.pad_off, *py = px + P.pad_plane;
+    cudaError_t e = launch_pad(dx, dtype, count, px, L.RH, L.RW, before, before, border - 1, st);
+    if (e == cudaSuccess) e = launch_pad(dy, dtype, count, py, L.RH, L.RW, before, before, border - 1, st);
+    dx = ImgDesc{px, L.RH, L.RW, L.RW, L.RH * L.RW};
+    dy = ImgDesc{py, L.RH, L.RW, L.RW, L.RH * L.RW};
+    return e;
 }
 
 // Launch one SSIM level: `in_x/in_y` describe the level's images (dtype),
@@ -279,7 +329,8 @@ int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_pa
                           const MsPlan &P, char *ws, double *score_out, double *per_scale_out,
                           cudaStream_t st) {
     const int S = p->scales, n = x->count;
-    bool persistent = (p->flags & GBSSIM_FLAG_PYRAMID_97) == 0;  // the persistent path fuses the 2x2 pyramid
+    // the persistent path fuses the 2x2 pyramid into valid-window levels
+    bool persistent = (p->flags & GBSSIM_FLAG_PYRAMID_97) == 0 && !border_mode(p);
     for (int j = 0; j < S; ++j) persistent = persistent && P.lv[j].path == PATH_GAUSS11;
     if (persistent) {
         // one launch over all levels and images: level-major items, a level-j
@@ -352,11 +403,12 @@ int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_pa
     ImgDesc dx = desc_of(x), dy = desc_of(y);
     int dtype = x->dtype;
     MsPlan Pl = P;  // level 0 may take the aligned box layout
-    fix_box_items(Pl.lv[0], x, y, p);
+    const bool border = border_mode(p) != 0;
+    if (!border) fix_box_items(Pl.lv[0], dx, dy, p);
     MsFinalize F;
     memset(&F, 0, sizeof F);
     for (int j = 0; j < S; ++j) {
-        const Level &L = Pl.lv[j];
+        Level &L = Pl.lv[j];
         float *ds_x = nullptr, *ds_y = nullptr;
         if (j + 1 < S) {
             const Level &N = Pl.lv[j + 1];
@@ -364,9 +416,26 @@ int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_pa
             ds_y = ds_x + (size_t)N.H * N.W * n;
         }
         double2 *part = (double2 *)(ws + L.part_off);
-        cudaError_t e = run_level(L, dx, dy, dtype, n, p, nullptr, 0, 0, part, ds_x, ds_y, st);
+        cudaError_t e;
+        if (border) {
+            // the level's SSIM on its extended images; the next level from the unextended ones
+            ImgDesc ex = dx, ey = dy;
+            e = extend_level(L, P, ws, p, dtype, n, ex, ey, st);
+            if (e == cudaSuccess) {
+                fix_box_items(L, ex, ey, p);
+                e = run_level(L, ex, ey, dtype, n, p, nullptr, 0, 0, part, nullptr, nullptr, st);
+            }
+            if (e == cudaSuccess && ds_x) {
+                const bool p97 = (p->flags & GBSSIM_FLAG_PYRAMID_97) != 0;
+                e = p97 ? launch_pyramid97(dx, dtype, n, ds_x, st) : launch_downsample(dx, dtype, n, ds_x, st);
+                if (e == cudaSuccess)
+                    e = p97 ? launch_pyramid97(dy, dtype, n, ds_y, st) : launch_downsample(dy, dtype, n, ds_y, st);
+            }
+        } else {
+            e = run_level(L, dx, dy, dtype, n, p, nullptr, 0, 0, part, ds_x, ds_y, st);
+        }
         if (e != cudaSuccess) return GBSSIM_ERR_CUDA;
-        const int64_t OH = out_dim(L.H, p->k, p->stride), OW = out_dim(L.W, p->k, p->stride);
+        const int64_t OH = out_dim(L.RH, p->k, p->stride), OW = out_dim(L.RW, p->k, p->stride);
         F.lv[j].partials = part;
         F.lv[j].items_per_image = L.items;
         F.lv[j].inv_n = 1.0 / ((double)OH * (double)OW);
@@ -471,7 +540,7 @@ int plan_saved(const gbssim_plane *x, const gbssim_params *p, int multiscale, Sa
 int check_loss(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p) {
     int rc = check_pair(x, y);
     if (rc) return rc;
-    rc = check_params(p);
+    rc = check_params_valid(p);
     if (rc) return rc;
     if (p->stride != 1 || p->k > GBSSIM_MAX_K_BACKWARD) return GBSSIM_ERR_UNSUPPORTED;
     if (p->flags & GBSSIM_FLAG_PYRAMID_97) return GBSSIM_ERR_UNSUPPORTED;
@@ -591,7 +660,7 @@ int gbssim_workspace_size(const gbssim_plane *x, const gbssim_params *p, int op,
     } else if (op == GBSSIM_OP_MSSSIM) {
         rc = plan_levels(x, p, p->scales, &P);
     } else if (op == GBSSIM_OP_BACKWARD || op == GBSSIM_OP_BACKWARD_MS) {
-        if (p->stride != 1 || p->k > GBSSIM_MAX_K_BACKWARD) return GBSSIM_ERR_UNSUPPORTED;
+        if (p->stride != 1 || p->k > GBSSIM_MAX_K_BACKWARD || border_mode(p)) return GBSSIM_ERR_UNSUPPORTED;
         BwdPlan B;
         rc = plan_backward(x, p, op == GBSSIM_OP_BACKWARD_MS, &B);
         if (rc) return rc;
@@ -615,16 +684,19 @@ int gbssim_ssim_map(const gbssim_plane *x, const gbssim_plane *y, const gbssim_p
     MsPlan P;
     rc = plan_levels(x, p, 1, &P);
     if (rc) return rc;
-    const int64_t OH = out_dim(x->height, p->k, p->stride), OW = out_dim(x->width, p->k, p->stride);
+    const int64_t OH = out_dim(P.lv[0].RH, p->k, p->stride), OW = out_dim(P.lv[0].RW, p->k, p->stride);
     if (map_out && (map_ld < OW || (x->count > 1 && map_image_stride < OH * map_ld)))
         return GBSSIM_ERR_INVALID_ARG;
     if (!map_out && !mean_out) return GBSSIM_ERR_INVALID_ARG;
     if (!workspace || workspace_bytes < P.bytes) return GBSSIM_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
-    fix_box_items(P.lv[0], x, y, p);
+    ImgDesc dx = desc_of(x), dy = desc_of(y);
+    if (extend_level(P.lv[0], P, (char *)workspace, p, x->dtype, x->count, dx, dy, st) != cudaSuccess)
+        return GBSSIM_ERR_CUDA;
+    fix_box_items(P.lv[0], dx, dy, p);
     double2 *part = (double2 *)((char *)workspace + P.lv[0].part_off);
-    cudaError_t e = run_level(P.lv[0], desc_of(x), desc_of(y), x->dtype, x->count, p, map_out, map_ld,
-                              map_image_stride, part, nullptr, nullptr, st);
+    cudaError_t e = run_level(P.lv[0], dx, dy, x->dtype, x->count, p, map_out, map_ld, map_image_stride, part,
+                              nullptr, nullptr, st);
     if (e != cudaSuccess) return GBSSIM_ERR_CUDA;
     if (mean_out) {
         e = launch_finalize_ssim(part, x->count, P.lv[0].items, 1.0 / ((double)OH * (double)OW), mean_out, st);
@@ -729,7 +801,7 @@ namespace {
 int check_ssim3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t kt, int scales) {
     int rc = check_pair(x, y);
     if (rc) return rc;
-    rc = check_params(p);
+    rc = check_params_valid(p);
     if (rc) return rc;
     if (x->dtype != GBSSIM_U8 || p->window != GBSSIM_WIN_BOX || p->stride != 1 || p->k > kSsim3dMaxK)
         return GBSSIM_ERR_UNSUPPORTED;
@@ -879,7 +951,7 @@ int gbssim_ssim3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_par
 }
 
 int gbssim_msssim3d_workspace_size(const gbssim_plane *x, const gbssim_params *p, int32_t kt, size_t *bytes) {
-    const int rc = check_params(p);
+    const int rc = check_params_valid(p);
     if (rc) return rc;
     const int rc2 = check_ssim3d(x, x, p, kt, p->scales);
     if (rc2) return rc2;
@@ -891,7 +963,7 @@ int gbssim_msssim3d_workspace_size(const gbssim_plane *x, const gbssim_params *p
 int gbssim_msssim3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t kt,
                     double *frame_out, double *score_out, double *per_scale_out, void *workspace,
                     size_t workspace_bytes, void *stream) {
-    const int rc = check_params(p);
+    const int rc = check_params_valid(p);
     if (rc) return rc;
     const int rc2 = check_ssim3d(x, y, p, kt, p->scales);
     if (rc2) return rc2;
@@ -918,7 +990,7 @@ int gbssim_local_mean(const gbssim_plane *x, const gbssim_params *p, float *out,
                       int64_t out_image_stride, void *stream) {
     int rc = check_plane(x);
     if (rc) return rc;
-    rc = check_params(p);
+    rc = check_params_valid(p);
     if (rc) return rc;
     if (!out || x->height < p->k || x->width < p->k) return out ? GBSSIM_ERR_TOO_SMALL : GBSSIM_ERR_INVALID_ARG;
     const int64_t OH = out_dim(x->height, p->k, p->stride), OW = out_dim(x->width, p->k, p->stride);
@@ -988,7 +1060,7 @@ int gbssim_msssim_host_workspace_size(const gbssim_plane *x, const gbssim_params
                                       size_t *bytes) {
     int rc = check_plane(x);
     if (rc) return rc;
-    rc = check_params(p);
+    rc = check_params_valid(p);
     if (rc) return rc;
     if (!bytes) return GBSSIM_ERR_INVALID_ARG;
     HostPlan H;
@@ -1003,7 +1075,7 @@ int gbssim_msssim_host(const gbssim_plane *x, const gbssim_plane *y, const gbssi
                        void *copy_stream, void *stream2) {
     int rc = check_pair(x, y);
     if (rc) return rc;
-    rc = check_params(p);
+    rc = check_params_valid(p);
     if (rc) return rc;
     if (!score_host) return GBSSIM_ERR_INVALID_ARG;
     HostPlan H;
@@ -1068,7 +1140,7 @@ int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbs
                          double *score_out, void *workspace, size_t workspace_bytes, void *stream) {
     int rc = check_pair(x, y);
     if (rc) return rc;
-    rc = check_params(p);
+    rc = check_params_valid(p);
     if (rc) return rc;
     if (p->stride != 1 || p->k > GBSSIM_MAX_K_BACKWARD) return GBSSIM_ERR_UNSUPPORTED;
     if (p->flags & GBSSIM_FLAG_PYRAMID_97) return GBSSIM_ERR_UNSUPPORTED;  // no adjoint of the 9/7 step
@@ -1336,7 +1408,7 @@ int gbssim_video_workspace_size(const gbssim_plane planes[6], const gbssim_param
         int rc = check_pair(&planes[2 * q], &planes[2 * q + 1]);
         if (rc) return rc;
     }
-    int rc = check_params(p);
+    int rc = check_params_valid(p);
     if (rc) return rc;
     MsPlan P[3];
     size_t offs[4];
@@ -1352,7 +1424,7 @@ int gbssim_video(const gbssim_plane planes[6], const gbssim_params *p, const dou
         if (rc) return rc;
         if (planes[2 * q].count != planes[0].count) return GBSSIM_ERR_INVALID_ARG;
     }
-    int rc = check_params(p);
+    int rc = check_params_valid(p);
     if (rc) return rc;
     const int n = planes[0].count;
     if (n > kVideoMaxFrames) return GBSSIM_ERR_UNSUPPORTED;
@@ -1370,7 +1442,7 @@ int gbssim_video(const gbssim_plane planes[6], const gbssim_params *p, const dou
     for (int q = 0; q < 3; ++q) {
         const gbssim_plane *x = &planes[2 * q], *y = &planes[2 * q + 1];
         Level L = P[q].lv[0];
-        fix_box_items(L, x, y, p);
+        fix_box_items(L, desc_of(x), desc_of(y), p);
         double2 *part = (double2 *)(ws + offs[q] + L.part_off);
         cudaError_t e = run_level(L, desc_of(x), desc_of(y), x->dtype, n, p, nullptr, 0, 0, part, nullptr, nullptr, st);
         if (e != cudaSuccess) return GBSSIM_ERR_CUDA;

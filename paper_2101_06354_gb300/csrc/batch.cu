@@ -49,7 +49,8 @@ int gbssim_batch_plan(const gbssim_plane *xs, const gbssim_plane *ys, int32_t n,
     *plan_out = nullptr;
     if (p->window != GBSSIM_WIN_GAUSSIAN && p->window != GBSSIM_WIN_BOX) return GBSSIM_ERR_INVALID_ARG;
     if (p->k != 11 || p->stride != 1) return GBSSIM_ERR_UNSUPPORTED;
-    if (p->flags & GBSSIM_FLAG_PYRAMID_97) return GBSSIM_ERR_UNSUPPORTED;  // the persistent kernel fuses 2x2
+    if (p->flags & (GBSSIM_FLAG_PYRAMID_97 | GBSSIM_FLAG_BORDER_ZERO | GBSSIM_FLAG_BORDER_REFLECT))
+        return GBSSIM_ERR_UNSUPPORTED;  // the persistent kernel fuses the 2x2 pyramid into valid-window levels
     if (!(p->L > 0.0) || p->K1 < 0.0 || p->K2 < 0.0 || p->flags != 0) return GBSSIM_ERR_INVALID_ARG;
     if (p->window == GBSSIM_WIN_GAUSSIAN && !(p->sigma > 0.0)) return GBSSIM_ERR_INVALID_ARG;
     const int S = multiscale ? p->scales : 1;

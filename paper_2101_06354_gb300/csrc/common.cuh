@@ -335,6 +335,10 @@ cudaError_t launch_ssim3d_finalize(const Ms3dFinalize &F, double *frame_scores, 
 cudaError_t launch_block_mean(const ImgDesc &in, int dtype, int count, int z, float *out, int64_t out_ld,
                               int64_t out_is, cudaStream_t st);
 cudaError_t launch_pyramid97(const ImgDesc &in, int dtype, int count, float *out, cudaStream_t st);
+// Border extension into dense PH x PW planes of the same dtype (mode 0 zero,
+// 1 mirror with the edge repeated).
+cudaError_t launch_pad(const ImgDesc &in, int dtype, int count, void *out, int64_t PH, int64_t PW, int top,
+                       int left, int mode, cudaStream_t st);
 cudaError_t launch_rgb_ycbcr(const ImgDesc &r, const ImgDesc &g, const ImgDesc &b, int dtype, int count, float *y,
                              float *cb, float *cr, int64_t out_ld, int64_t out_is, cudaStream_t st);
 

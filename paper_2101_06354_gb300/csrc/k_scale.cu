@@ -77,6 +77,27 @@ __global__ void rgb_ycbcr_kernel(ImgDesc r, ImgDesc g, ImgDesc b, float *yo, flo
     cro[o] = 0.635f * (R - Y);
 }
 
+// Border extension of a batch into dense planes (PH x PW per image): the
+// source pixel at (r - top, c - left), or 0 outside the image (mode 0), or
+// its mirror about the border with the edge repeated (mode 1; the host
+// guarantees one reflection suffices).  Elements are copied as raw bits.
+template <typename E>
+__global__ void pad_kernel(ImgDesc in, E *out, int64_t PH, int64_t PW, int top, int left, int mode) {
+    const int img = blockIdx.z;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+    if (c >= PW) return;
+    int64_t sr = r - top, sc = c - left;
+    bool inside = sr >= 0 && sr < in.H && sc >= 0 && sc < in.W;
+    if (!inside && mode == 1) {
+        sr = sr < 0 ? -1 - sr : (sr >= in.H ? 2 * in.H - 1 - sr : sr);
+        sc = sc < 0 ? -1 - sc : (sc >= in.W ? 2 * in.W - 1 - sc : sc);
+        inside = true;
+    }
+    E v = 0;
+    if (inside) v = static_cast<const E *>(in.data)[img * in.image_stride + sr * in.row_stride + sc];
+    out[((int64_t)img * PH + r) * PW + c] = v;
+}
+
 }  // namespace
 
 cudaError_t launch_rgb_ycbcr(const ImgDesc &r, const ImgDesc &g, const ImgDesc &b, int dtype, int count, float *y,
@@ -117,6 +138,20 @@ cudaError_t launch_pyramid97(const ImgDesc &in, int dtype, int count, float *out
     case GBSSIM_F16: pyramid97_kernel<__half><<<grid, 128, 0, st>>>(in, out); break;
     case GBSSIM_BF16: pyramid97_kernel<__nv_bfloat16><<<grid, 128, 0, st>>>(in, out); break;
     case GBSSIM_F32: pyramid97_kernel<float><<<grid, 128, 0, st>>>(in, out); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pad(const ImgDesc &in, int dtype, int count, void *out, int64_t PH, int64_t PW, int top,
+                       int left, int mode, cudaStream_t st) {
+    if (PH > 65535 || count > 65535) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((PW + 255) / 256), (unsigned)PH, count);
+    switch (dtype) {
+    case GBSSIM_U8: pad_kernel<uint8_t><<<grid, 256, 0, st>>>(in, (uint8_t *)out, PH, PW, top, left, mode); break;
+    case GBSSIM_F16:
+    case GBSSIM_BF16: pad_kernel<uint16_t><<<grid, 256, 0, st>>>(in, (uint16_t *)out, PH, PW, top, left, mode); break;
+    case GBSSIM_F32: pad_kernel<uint32_t><<<grid, 256, 0, st>>>(in, (uint32_t *)out, PH, PW, top, left, mode); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

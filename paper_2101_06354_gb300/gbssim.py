@@ -141,9 +141,17 @@ def _check(rc: int, where: str):
 _DTYPES = {torch.uint8: U8, torch.float16: F16, torch.bfloat16: BF16, torch.float32: F32}
 
 
+FLAG_BORDER_ZERO = 4
+FLAG_BORDER_REFLECT = 8
+BORDERS = {"valid": 0, "zero": FLAG_BORDER_ZERO, "reflect": FLAG_BORDER_REFLECT}
+
+
 def make_params(window: str = "gaussian", k: int = 11, sigma: float = 1.5, K1: float = 0.01,
                 K2: float = 0.03, L: float = 255.0, stride: int = 1, scales: int = 5,
-                exponents=None, combine: str = "product", flags: int = 0) -> Params:
+                exponents=None, combine: str = "product", flags: int = 0, border: str = "valid") -> Params:
+    """The C ABI's gbssim_params.  border = "valid" (only windows inside the
+    image), "zero" or "reflect" (the image extended by k-1 pixels:
+    GBSSIM_FLAG_BORDER_ZERO / _REFLECT)."""
     p = Params()
     lib.gbssim_params_default(ctypes.byref(p))
     p.window = {"gaussian": WIN_GAUSSIAN, "box": WIN_BOX}[window]
@@ -155,7 +163,7 @@ def make_params(window: str = "gaussian", k: int = 11, sigma: float = 1.5, K1: f
         for j in range(MAX_SCALES):
             p.exponents[j] = float(exponents[j]) if j < len(exponents) else 0.0
     p.combine = {"product": COMBINE_PRODUCT, "sum": COMBINE_SUM}[combine]
-    p.flags = int(flags)
+    p.flags = int(flags) | BORDERS[border]
     return p
 
 
@@ -205,6 +213,12 @@ def workspace(px: Plane, p: Params, op: int, dev) -> torch.Tensor:
     return torch.empty(max(int(n.value), 1), dtype=torch.uint8, device=dev)
 
 
+def map_shape(h: int, w: int, p: Params):
+    """(OH, OW) of the SSIM map for params p (border modes extend by k-1)."""
+    ext = p.k - 1 if p.flags & (FLAG_BORDER_ZERO | FLAG_BORDER_REFLECT) else 0
+    return out_shape(h + ext, w + ext, p.k, p.stride)
+
+
 def out_shape(h: int, w: int, k: int, stride: int):
     return ((h - k) // stride + 1, (w - k) // stride + 1)
 
@@ -221,7 +235,7 @@ def ssim(x: torch.Tensor, y: torch.Tensor, return_map: bool = False, ws: torch.T
     mean = torch.empty(n, dtype=torch.float64, device=dev)
     mp = None
     if return_map:
-        oh, ow = out_shape(xb.shape[1], xb.shape[2], p.k, p.stride)
+        oh, ow = map_shape(xb.shape[1], xb.shape[2], p)
         mp = torch.empty((n, oh, ow), dtype=torch.float32, device=dev)
     _check(lib.gbssim_ssim_map(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p),
                                mp.data_ptr() if mp is not None else None,
@@ -247,7 +261,7 @@ def ssim_static(x: torch.Tensor, y: torch.Tensor, return_map: bool = False, **kw
     mean = torch.empty(n, dtype=torch.float64, device=dev)
     mp = None
     if return_map:
-        oh, ow = out_shape(xb.shape[1], xb.shape[2], p.k, p.stride)
+        oh, ow = map_shape(xb.shape[1], xb.shape[2], p)
         mp = torch.empty((n, oh, ow), dtype=torch.float32, device=dev)
     _check(lib.gbssim_ssim_map_static(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p),
                                       mp.data_ptr() if mp is not None else None,

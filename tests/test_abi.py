@@ -82,7 +82,7 @@ def test_workspace_sizes(g):
 
 @pytest.mark.parametrize("field,value,status", [
     ("k", 0, -1), ("k", 64, -1), ("stride", 0, -1), ("scales", 0, -1), ("scales", 9, -1),
-    ("window", 7, -1), ("sigma", 0.0, -1), ("L", -1.0, -1), ("combine", 3, -1), ("flags", 4, -1),
+    ("window", 7, -1), ("sigma", 0.0, -1), ("L", -1.0, -1), ("combine", 3, -1), ("flags", 16, -1), ("flags", 12, -1),
 ])
 def test_bad_params_rejected(g, field, value, status):
     p = g.make_params()
@@ -220,3 +220,26 @@ def test_ssim3d_and_msssim3d_validation(g):
     assert _ws3d(g, _plane(g, 100, 100, 4, dtype=3), g.make_params(k=11, scales=2, **box), 2)[0] == \
         g.ERR_UNSUPPORTED
     assert _ws3d(g, _plane(g, 100, 100, 4), g.make_params(k=11, scales=2, **box), 0)[0] == g.ERR_INVALID_ARG
+
+
+def test_border_modes_on_host(g):
+    x = _plane(g, 7, 9)  # below k = 11: valid windows only are too small, extended ones fit
+    for border in ("zero", "reflect"):
+        p = g.make_params(border=border)
+        rc, n = _ws(g, x, p, g.OP_SSIM)
+        assert rc == 0 and n >= 2 * (7 + 10) * (9 + 10)       # the two extended planes
+        rc, n = _ws(g, _plane(g, 4, 9), p, g.OP_SSIM)
+        assert rc == g.ERR_TOO_SMALL                           # below the mirrored 5 rows
+        # five levels of 100 x 100 end at 6 x 6 >= 5
+        assert _ws(g, _plane(g, 100, 100), p, g.OP_MSSSIM)[0] == 0
+        assert _ws(g, _plane(g, 100, 100), p, g.OP_BACKWARD)[0] == g.ERR_UNSUPPORTED
+        xs = (g.Plane * 2)(_plane(g, 100, 120), _plane(g, 50, 60))
+        out = ctypes.c_void_p()
+        assert g.lib.gbssim_batch_plan(xs, xs, 2, ctypes.byref(p), 0, None, ctypes.byref(out)) == g.ERR_UNSUPPORTED
+        pb = g.make_params(window="box", border=border)
+        assert _ws3d(g, _plane(g, 64, 64, 4), pb, 2, "gbssim_ssim3d_workspace_size")[0] == g.ERR_UNSUPPORTED
+    assert _ws(g, x, g.make_params(), g.OP_SSIM)[0] == g.ERR_TOO_SMALL
+    both = g.make_params(flags=g.FLAG_BORDER_ZERO | g.FLAG_BORDER_REFLECT)
+    assert _ws(g, x, both, g.OP_SSIM)[0] == g.ERR_INVALID_ARG
+    assert g.map_shape(7, 9, g.make_params(border="zero")) == (7, 9)
+    assert g.map_shape(1080, 1920, g.make_params(border="reflect", window="box", k=8, stride=4)) == (270, 480)

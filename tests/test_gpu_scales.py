@@ -118,3 +118,58 @@ def test_colour_ssim_matches_oracle(g, weights):
         assert np.abs(ps[:, t].cpu().numpy() - s).max() <= 1e-5  # fp32 planes vs fp64
         assert abs(fr[t].item() - oracle.colour_score(*s, weights=weights)) <= 1e-5 / abs(sum(weights)) * 3
     assert abs(vid[0].item() - fr.mean().item()) <= 1e-12
+
+
+# ---------------------------------------------------------------- border extension
+
+@pytest.mark.parametrize("border", ["zero", "reflect"])
+@pytest.mark.parametrize("h,w,kw", [
+    (120, 150, {}),                                          # Gaussian 11, uint8: the fused kernel on extended planes
+    (7, 9, {}),                                              # smaller than the window
+    (97, 131, dict(window="box", k=8, stride=4)),            # exact integer box path
+    (64, 70, dict(window="gaussian", k=7, sigma=1.0, stride=2)),  # generic path, strided
+])
+def test_ssim_border_matches_oracle(g, border, h, w, kw):
+    from paper_2101_06354_gb300 import synth
+
+    x, y = synth.single_pair_u8(h, w, seed_ref=h, seed_noise=w)
+    mean, q = g.ssim(x.to(DEV), y.to(DEV), return_map=True, border=border, **kw)
+    okw = dict(kw)
+    okw["window_kind"] = okw.pop("window", "gaussian")
+    ref_mean, ref = oracle.ssim(x.numpy(), y.numpy(), border=border, **okw)
+    assert q.shape[1:] == ref["q"].shape
+    assert np.abs(q[0].double().cpu().numpy() - ref["q"]).max() <= 1e-5
+    assert abs(mean[0].item() - ref_mean) <= 1e-6
+
+
+@pytest.mark.parametrize("border", ["zero", "reflect"])
+def test_ssim_border_float_batch(g, border):
+    from paper_2101_06354_gb300 import synth
+
+    x, y = synth.luma_pairs_u8(3, 90, 101)
+    xf, yf = x.float() / 255, y.float() / 255
+    mean, q = g.ssim(xf.to(DEV), yf.to(DEV), return_map=True, border=border, L=1.0)
+    for i in range(3):
+        ref_mean, ref = oracle.ssim(xf[i].numpy(), yf[i].numpy(), border=border, L=1.0)
+        assert np.abs(q[i].double().cpu().numpy() - ref["q"]).max() <= 1e-5
+        assert abs(mean[i].item() - ref_mean) <= 1e-6
+
+
+@pytest.mark.parametrize("border", ["zero", "reflect"])
+@pytest.mark.parametrize("pyramid", ["avg2", "97"])
+def test_msssim_border_matches_oracle(g, border, pyramid):
+    from paper_2101_06354_gb300 import synth
+
+    x, y = synth.luma_pairs_u8(2, 150, 171)
+    s, per = g.msssim(x.to(DEV), y.to(DEV), per_scale=True, border=border, pyramid=pyramid)
+    for i in range(2):
+        ref, ref_per = oracle.msssim(x[i].numpy(), y[i].numpy(), border=border, pyramid=pyramid)
+        assert abs(s[i].item() - ref) <= 1e-6
+        np.testing.assert_allclose(per[i].cpu().numpy(), np.array(ref_per), rtol=0, atol=1e-6)
+
+
+def test_border_rejected_where_unsupported(g):
+    x = torch.zeros((1, 64, 64), dtype=torch.uint8, device=DEV)
+    with pytest.raises(g.GbssimError) as e:
+        g.SSIMLoss(border="zero")(x.float(), x.float().requires_grad_(True)).backward()
+    assert e.value.status == g.ERR_UNSUPPORTED
