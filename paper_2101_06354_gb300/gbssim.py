@@ -540,6 +540,25 @@ def colour_ssim(ref_rgb, dis_rgb, weights=(0.8, 0.1, 0.1), **kw):
     return video_ssim(xs, ys, weights=weights, **kw)
 
 
+def enhanced_ssim(x: torch.Tensor, y: torch.Tensor, z: int = None, rule: str = "round_min", k: int = 11,
+                  stride: int = 5, return_map: bool = False, **kw):
+    """Enhanced SSIM (the paper's recommended variant, Concluding section):
+    luminance planes, z x z block-mean downscaling (gbssim_downscale; z
+    from gbssim_downscale_factor's `rule` when not given), k x k rectangular
+    windows at the given stride (exact integer window sums on uint8 input
+    when z = 1), and coefficient-of-variation pooling of each Q map
+    (gbssim_ssim_pool).  (H, W) or (N, H, W) CUDA tensors; returns the CoV
+    score per pair (float64, N)[, and the Q maps]."""
+    xb, yb = _as_batch(x), _as_batch(y)
+    if z is None:
+        z = downscale_factor(xb.shape[1], xb.shape[2], rule)
+    if z > 1:
+        xb, yb = downscale(xb, z), downscale(yb, z)
+    _, q = ssim(xb, yb, return_map=True, window="box", k=k, stride=stride, **kw)
+    score = ssim_pool(q, "cov")
+    return (score, q) if return_map else score
+
+
 _GDT = {torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}
 
 

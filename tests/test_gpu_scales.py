@@ -173,3 +173,23 @@ def test_border_rejected_where_unsupported(g):
     with pytest.raises(g.GbssimError) as e:
         g.SSIMLoss(border="zero")(x.float(), x.float().requires_grad_(True)).backward()
     assert e.value.status == g.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("h,w,z", [(1080, 1920, None), (300, 420, 1), (512, 640, 2)])
+def test_enhanced_ssim_matches_oracle(g, h, w, z):
+    """Enhanced SSIM: z x z downscaling, 11 x 11 rectangular windows at
+    stride 5, CoV pooling; against the oracle's composition of the same
+    steps."""
+    from oracle import pooling as P
+    from paper_2101_06354_gb300 import synth
+
+    x, y = synth.luma_pairs_u8(2, h, w)
+    score, q = g.enhanced_ssim(x.to(DEV), y.to(DEV), z=z, return_map=True)
+    zz = z if z is not None else S.downscale_factor(h, w)
+    for i in range(2):
+        a, b = x[i].numpy(), y[i].numpy()
+        if zz > 1:
+            a, b = S.downscale_block(a, zz), S.downscale_block(b, zz)
+        _, ref = oracle.ssim(a, b, window_kind="box", k=11, stride=5)
+        assert np.abs(q[i].double().cpu().numpy() - ref["q"]).max() <= 1e-5
+        assert abs(score[i].item() - P.cov(ref["q"])) <= 1e-6
