@@ -313,6 +313,31 @@ int gbssim_msssim3d(const gbssim_plane *x, const gbssim_plane *y, const gbssim_p
                     double *frame_out, double *score_out, double *per_scale_out, void *workspace,
                     size_t workspace_bytes, void *stream);
 
+/* CMSSIM of `count` pairs of RGB images (Section "CMSSIM"): RGB -> CIE XYZ
+ * -> the luminance, red-green and blue-yellow planes (the section's forward
+ * matrix) -> Gaussian smoothing of the two chromatic planes -> XYZ (the
+ * section's inverse matrix, as printed) -> CIE 1976 L*, a*, b*; the SSIM map
+ * of the two L* planes (dynamic range 100) is weighted at every position by
+ * (1 - Delta E / 45), Delta E the CIELAB distance of the two images at the
+ * window's centre pixel, and mean-pooled.  Readings: linear RGB in [0, 1]
+ * (uint8 values / 255, no transfer curve) with the BT.709 / sRGB primaries
+ * and D65 white; the smoothing kernel is the params' Gaussian window with one
+ * output per pixel (planes extended by mirroring about the border); CIELAB
+ * relative to that D65 white.
+ *   rgb_x, rgb_y : three planes each (R, G, B), all of one shape and dtype.
+ *   p            : window = GBSSIM_WIN_GAUSSIAN (k, sigma), K1, K2, stride;
+ *                  L is fixed at 100 (the L* range); no flags.
+ *   score_out    : count doubles (device).
+ *   map_out      : nullable; the weighted map of each pair, rows map_ld floats
+ *                  apart, images map_image_stride floats apart.
+ *   workspace    : gbssim_cmssim_workspace_size bytes (r's shape and p).
+ * Errors: GBSSIM_ERR_UNSUPPORTED for a box window or border flags;
+ * GBSSIM_ERR_TOO_SMALL if the images are smaller than k x k. */
+int gbssim_cmssim_workspace_size(const gbssim_plane *r, const gbssim_params *p, size_t *bytes);
+int gbssim_cmssim(const gbssim_plane rgb_x[3], const gbssim_plane rgb_y[3], const gbssim_params *p,
+                  double *score_out, float *map_out, int64_t map_ld, int64_t map_image_stride, void *workspace,
+                  size_t workspace_bytes, void *stream);
+
 /* MS-SSIM of each pair (Introduction; Section "Salient Features of SSIM and
  * MS-SSIM Implementations"): scale 1 is the input, scale j+1 the 2x2 average
  * of scale j (floor size); the contrast-structure term is mean-pooled at every

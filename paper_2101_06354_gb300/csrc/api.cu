@@ -1016,6 +1016,138 @@ int gbssim_ssim_pool_lw(const float *map, const float *mu_ref, int64_t h, int64_
     return e == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
 }
 
+namespace {
+// CMSSIM's matrices: linear BT.709 / sRGB RGB to XYZ (D65), and the
+// section's XYZ -> opponent and opponent -> XYZ matrices as printed.
+const double kRgbToXyz[9] = {0.4124, 0.3576, 0.1805, 0.2126, 0.7152, 0.0722, 0.0193, 0.1192, 0.9505};
+const double kXyzToOpp[9] = {0.279, 0.72, -0.107, -0.449, 0.29, -0.077, 0.086, -0.59, 0.501};
+const double kOppToXyz[9] = {0.6204, -1.8704, -0.1553, 1.3661, 0.9316, 0.4339, 1.5013, 1.4176, 2.5331};
+
+struct CmPlan {
+    int64_t H, W, OH, OW, PH, PW, plane;
+    size_t lab_off, pad_off, map_off, ssim_off, pool_off, bytes;
+    MsPlan ssim;
+    gbssim_params ps;  // the SSIM of L*: the caller's window and K1, K2 with L = 100
+};
+
+int plan_cmssim(const gbssim_plane *x, const gbssim_params *p, CmPlan *C) {
+    int rc = check_params_valid(p);
+    if (rc) return rc;
+    if (p->window != GBSSIM_WIN_GAUSSIAN) return GBSSIM_ERR_UNSUPPORTED;
+    if (x->height < p->k || x->width < p->k) return GBSSIM_ERR_TOO_SMALL;
+    const int64_t n = x->count;
+    C->H = x->height;
+    C->W = x->width;
+    C->plane = C->H * C->W;
+    C->OH = out_dim(C->H, p->k, p->stride);
+    C->OW = out_dim(C->W, p->k, p->stride);
+    C->PH = C->H + p->k - 1;
+    C->PW = C->W + p->k - 1;
+    if (C->PH > 65535 || C->H > 65535) return GBSSIM_ERR_UNSUPPORTED;  // grid y extents
+    C->ps = *p;
+    C->ps.L = 100.0;
+    C->ps.scales = 1;
+    C->ps.flags = 0;
+    gbssim_plane lp{x->data, GBSSIM_F32, x->count, C->H, C->W, C->W, C->plane};
+    rc = plan_levels(&lp, &C->ps, 1, &C->ssim);
+    if (rc) return rc;
+    size_t off = 0;
+    C->lab_off = off;
+    off = align_up(off + 6 * sizeof(float) * (size_t)C->plane * n);
+    C->pad_off = off;
+    off = align_up(off + sizeof(float) * (size_t)C->PH * C->PW * n);
+    C->map_off = off;
+    off = align_up(off + sizeof(float) * (size_t)C->OH * C->OW * n);
+    C->ssim_off = off;
+    off = align_up(off + C->ssim.bytes);
+    C->pool_off = off;
+    off = align_up(off + pool_layout(C->OH, C->OW, x->count).bytes);
+    C->bytes = off;
+    return GBSSIM_OK;
+}
+}  // namespace
+
+int gbssim_cmssim_workspace_size(const gbssim_plane *r, const gbssim_params *p, size_t *bytes) {
+    int rc = check_plane(r);
+    if (rc) return rc;
+    if (!bytes) return GBSSIM_ERR_INVALID_ARG;
+    CmPlan C;
+    rc = plan_cmssim(r, p, &C);
+    if (rc) return rc;
+    *bytes = C.bytes;
+    return GBSSIM_OK;
+}
+
+int gbssim_cmssim(const gbssim_plane rgb_x[3], const gbssim_plane rgb_y[3], const gbssim_params *p,
+                  double *score_out, float *map_out, int64_t map_ld, int64_t map_image_stride, void *workspace,
+                  size_t workspace_bytes, void *stream) {
+    if (!rgb_x || !rgb_y || !score_out) return GBSSIM_ERR_INVALID_ARG;
+    for (int c = 0; c < 3; ++c) {
+        int rc = check_pair(&rgb_x[0], &rgb_x[c]);
+        if (!rc) rc = check_pair(&rgb_x[0], &rgb_y[c]);
+        if (rc) return rc;
+    }
+    CmPlan C;
+    int rc = plan_cmssim(&rgb_x[0], p, &C);
+    if (rc) return rc;
+    const int n = rgb_x[0].count;
+    if (map_out && (map_ld < C.OW || (n > 1 && map_image_stride < C.OH * map_ld))) return GBSSIM_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < C.bytes) return GBSSIM_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *ws = (char *)workspace;
+    const int64_t cs = C.plane * n;  // channel stride of the L*, a*, b* arrays
+    float *lab[2] = {(float *)(ws + C.lab_off), (float *)(ws + C.lab_off) + 3 * cs};
+    // RGB -> XYZ -> opponent planes, in one matrix product formed in double
+    double m[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int t = 0; t < 3; ++t) acc += kXyzToOpp[3 * i + t] * kRgbToXyz[3 * t + j];
+            m[3 * i + j] = acc;
+        }
+    const double white[3] = {kRgbToXyz[0] + kRgbToXyz[1] + kRgbToXyz[2], kRgbToXyz[3] + kRgbToXyz[4] + kRgbToXyz[5],
+                             kRgbToXyz[6] + kRgbToXyz[7] + kRgbToXyz[8]};
+    TapsDyn taps;
+    memset(taps.g, 0, sizeof taps.g);
+    make_taps(p, taps.g);
+    const int before = (p->k - 1) / 2;
+    float *pad = (float *)(ws + C.pad_off);
+    for (int s = 0; s < 2; ++s) {
+        const gbssim_plane *rgb = s ? rgb_y : rgb_x;
+        float *q = lab[s];
+        if (launch_rgb_opp(desc_of(&rgb[0]), desc_of(&rgb[1]), desc_of(&rgb[2]), rgb[0].dtype, n, m, q, q + cs,
+                           q + 2 * cs, st) != cudaSuccess)
+            return GBSSIM_ERR_CUDA;
+        // the chromatic planes smoothed in place: mirror extension, then the window mean
+        for (int c = 1; c < 3; ++c) {
+            const ImgDesc d{q + c * cs, C.H, C.W, C.W, C.plane};
+            if (launch_pad(d, GBSSIM_F32, n, pad, C.PH, C.PW, before, before, 1, st) != cudaSuccess)
+                return GBSSIM_ERR_CUDA;
+            const ImgDesc pd{pad, C.PH, C.PW, C.PW, C.PH * C.PW};
+            if (launch_local_mean(pd, GBSSIM_F32, n, taps, p->k, 1, q + c * cs, C.W, C.plane, st) != cudaSuccess)
+                return GBSSIM_ERR_CUDA;
+        }
+        if (launch_opp_lab(q, q + cs, q + 2 * cs, cs, kOppToXyz, white, st) != cudaSuccess) return GBSSIM_ERR_CUDA;
+    }
+    // SSIM map of the L* planes, weighted by (1 - Delta E / 45), mean-pooled
+    float *map = map_out ? map_out : (float *)(ws + C.map_off);
+    const int64_t ld = map_out ? map_ld : C.OW;
+    const int64_t is = map_out ? (n > 1 ? map_image_stride : C.OH * map_ld) : C.OH * C.OW;
+    const ImgDesc lx{lab[0], C.H, C.W, C.W, C.plane}, ly{lab[1], C.H, C.W, C.W, C.plane};
+    Level L = C.ssim.lv[0];
+    char *sws = ws + C.ssim_off;
+    double2 *part = (double2 *)(sws + L.part_off);
+    if (run_level(L, lx, ly, GBSSIM_F32, n, &C.ps, map, ld, is, part, nullptr, nullptr, st) != cudaSuccess)
+        return GBSSIM_ERR_CUDA;
+    if (launch_cmssim_weight(map, C.OH, C.OW, ld, is, n, lab[0], lab[1], C.H, C.W, cs, before, p->stride, st) !=
+        cudaSuccess)
+        return GBSSIM_ERR_CUDA;
+    return launch_pool_map(map, C.OH, C.OW, ld, n, is, GBSSIM_POOL_MEAN, 0.0, 0.0, ws + C.pool_off, score_out, st) ==
+                   cudaSuccess
+               ? GBSSIM_OK
+               : GBSSIM_ERR_CUDA;
+}
+
 int gbssim_downscale_factor(int64_t h, int64_t w, int32_t rule) {
     if (h < 1 || w < 1) return GBSSIM_ERR_INVALID_ARG;
     if (rule == GBSSIM_DOWNSCALE_ROUND_MIN) {

@@ -342,6 +342,16 @@ cudaError_t launch_pad(const ImgDesc &in, int dtype, int count, void *out, int64
 cudaError_t launch_rgb_ycbcr(const ImgDesc &r, const ImgDesc &g, const ImgDesc &b, int dtype, int count, float *y,
                              float *cb, float *cr, int64_t out_ld, int64_t out_is, cudaStream_t st);
 
+// CMSSIM colour steps (k_colour.cu).  Planes are dense H x W floats; the
+// three channels of a batch are separate arrays (channel stride cs).
+cudaError_t launch_rgb_opp(const ImgDesc &r, const ImgDesc &g, const ImgDesc &b, int dtype, int count,
+                           const double m[9], float *q1, float *q2, float *q3, cudaStream_t st);
+cudaError_t launch_opp_lab(float *p1, float *p2, float *p3, int64_t n, const double inv[9], const double white[3],
+                           cudaStream_t st);
+cudaError_t launch_cmssim_weight(float *map, int64_t oh, int64_t ow, int64_t map_ld, int64_t map_is, int count,
+                                 const float *lab_x, const float *lab_y, int64_t H, int64_t W, int64_t cs, int centre,
+                                 int stride, cudaStream_t st);
+
 // Temporal pooling of frame-score series (k_series.cu).
 cudaError_t launch_series_pool(const double *scores, int n, int count, int64_t stride, int kind, double a0,
                                double a1, double *out, cudaStream_t st);

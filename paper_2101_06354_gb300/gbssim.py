@@ -115,6 +115,8 @@ _SIGS = {
                       ctypes.c_int),
     "gbssim_msssim3d_workspace_size": ([_P(Plane), _P(Params), _i32, _P(_sz)], ctypes.c_int),
     "gbssim_msssim3d": ([_P(Plane), _P(Plane), _P(Params), _i32, _vp, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "gbssim_cmssim_workspace_size": ([_P(Plane), _P(Params), _P(_sz)], ctypes.c_int),
+    "gbssim_cmssim": ([_P(Plane), _P(Plane), _P(Params), _vp, _vp, _i64, _i64, _vp, _sz, _vp], ctypes.c_int),
     "gbssim_msssim_host": ([_P(Plane), _P(Plane), _P(Params), _i32, _vp, _vp, _sz, _vp, _vp, _vp], ctypes.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -557,6 +559,37 @@ def enhanced_ssim(x: torch.Tensor, y: torch.Tensor, z: int = None, rule: str = "
     _, q = ssim(xb, yb, return_map=True, window="box", k=k, stride=stride, **kw)
     score = ssim_pool(q, "cov")
     return (score, q) if return_map else score
+
+
+def cmssim(ref_rgb, dis_rgb, return_map: bool = False, ws: torch.Tensor = None, **kw):
+    """CMSSIM (gbssim_cmssim) of RGB pairs: ref_rgb and dis_rgb are (R, G, B)
+    tuples of CUDA tensors (H, W) or (N, H, W), linear RGB in [0, 1] (uint8
+    values are divided by 255).  Keyword arguments as make_params (Gaussian
+    window k, sigma; K1, K2; stride).  Returns the score per pair (float64,
+    N)[, and the weighted maps]."""
+    xs = [_as_batch(t).contiguous() for t in ref_rgb]
+    ys = [_as_batch(t).contiguous() for t in dis_rgb]
+    if len(xs) != 3 or len(ys) != 3:
+        raise ValueError("expected (R, G, B) planes")
+    dev = xs[0].device
+    p = make_params(**kw)
+    px = (Plane * 3)(*[plane(t) for t in xs])
+    py = (Plane * 3)(*[plane(t) for t in ys])
+    n, h, w = xs[0].shape
+    if ws is None:
+        nb = ctypes.c_size_t()
+        _check(lib.gbssim_cmssim_workspace_size(ctypes.byref(px[0]), ctypes.byref(p), ctypes.byref(nb)),
+               "gbssim_cmssim_workspace_size")
+        ws = torch.empty(max(int(nb.value), 1), dtype=torch.uint8, device=dev)
+    score = torch.empty(n, dtype=torch.float64, device=dev)
+    mp = None
+    if return_map:
+        oh, ow = out_shape(h, w, p.k, p.stride)
+        mp = torch.empty((n, oh, ow), dtype=torch.float32, device=dev)
+    _check(lib.gbssim_cmssim(px, py, ctypes.byref(p), score.data_ptr(), mp.data_ptr() if mp is not None else None,
+                             mp.stride(1) if mp is not None else 0, mp.stride(0) if mp is not None else 0,
+                             ws.data_ptr(), ws.numel(), _stream(dev)), "gbssim_cmssim")
+    return (score, mp) if return_map else score
 
 
 _GDT = {torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}

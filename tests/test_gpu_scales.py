@@ -193,3 +193,44 @@ def test_enhanced_ssim_matches_oracle(g, h, w, z):
         _, ref = oracle.ssim(a, b, window_kind="box", k=11, stride=5)
         assert np.abs(q[i].double().cpu().numpy() - ref["q"]).max() <= 1e-5
         assert abs(score[i].item() - P.cov(ref["q"])) <= 1e-6
+
+
+# ---------------------------------------------------------------- CMSSIM
+
+def _rgb_pair(n, h, w, seed):
+    from paper_2101_06354_gb300 import synth
+
+    xs, ys = [], []
+    for c in range(3):
+        x, y = synth.luma_pairs_u8(n, h, w, seed_ref=seed + 10 * c, seed_dist=seed + 10 * c + 500)
+        xs.append(x)
+        ys.append(y)
+    return xs, ys
+
+
+@pytest.mark.parametrize("n,h,w,dtype,kw", [(2, 96, 130, torch.uint8, {}), (1, 64, 77, torch.float32, {}),
+                                            (1, 80, 90, torch.uint8, dict(k=7, sigma=1.0, stride=2))])
+def test_cmssim_matches_oracle(g, n, h, w, dtype, kw):
+    from oracle import colour as C
+
+    xs, ys = _rgb_pair(n, h, w, seed=h)
+    if dtype == torch.float32:
+        xs, ys = [t.float() / 255 for t in xs], [t.float() / 255 for t in ys]
+    score, wmap = g.cmssim([t.to(DEV) for t in xs], [t.to(DEV) for t in ys], return_map=True, **kw)
+    k, sigma, stride = kw.get("k", 11), kw.get("sigma", 1.5), kw.get("stride", 1)
+    for i in range(n):
+        fx = [t[i].double().numpy() / (255.0 if dtype == torch.uint8 else 1.0) for t in xs]
+        fy = [t[i].double().numpy() / (255.0 if dtype == torch.uint8 else 1.0) for t in ys]
+        if stride == 1:
+            ref, rmap, _ = C.cmssim(fx, fy, k=k, sigma=sigma)
+            assert np.abs(wmap[i].double().cpu().numpy() - rmap).max() <= 1e-5
+            assert abs(score[i].item() - ref) <= 1e-6
+        else:
+            _, rmap, _ = C.cmssim(fx, fy, k=k, sigma=sigma)
+            np.testing.assert_allclose(wmap[i].double().cpu().numpy(), rmap[::stride, ::stride], rtol=0, atol=1e-5)
+
+
+def test_cmssim_identity_is_one(g):
+    xs, _ = _rgb_pair(1, 70, 80, seed=3)
+    d = [t.to(DEV) for t in xs]
+    assert abs(g.cmssim(d, d).item() - 1.0) <= 1e-6
