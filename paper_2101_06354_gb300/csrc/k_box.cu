@@ -18,12 +18,26 @@
 //  * integral-image path (any k <= 63, any stride): five summed-area tables
 //    of a <= 64 x 64 input tile in shared memory (int32, zero first row and
 //    column) and the paper's four-corner formula per window.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 
-#include "common.cuh"
+#include "tma.cuh"
 
 namespace gbssim {
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
 namespace {
 
 constexpr int NT = 256;
@@ -371,7 +385,6 @@ __global__ void __launch_bounds__(NT) box_s4c_kernel(const BoxLaunch L, int stri
 // returns.
 constexpr int TMA_W = 256, TMA_H = 64;          // bytes per row, rows per tile
 constexpr unsigned TMA_TILE = TMA_W * TMA_H;    // bytes per image per tile
-constexpr unsigned kWaitLimit = 1u << 26;
 
 struct __align__(128) TmaSmem {
     unsigned char st[2][2][TMA_H][TMA_W];  // [stage][x|y][row][byte]
@@ -379,38 +392,6 @@ struct __align__(128) TmaSmem {
     float red[2 * NT / 32];
     unsigned long long bar[2];
 };
-
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
-    for (unsigned i = 0; i < kWaitLimit; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
-                                            unsigned long long *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-        : "memory");
-}
 
 __global__ void __launch_bounds__(NT) box_tma_kernel(const __grid_constant__ CUtensorMap tmx,
                                                      const __grid_constant__ CUtensorMap tmy, const BoxLaunch L,
@@ -427,7 +408,7 @@ __global__ void __launch_bounds__(NT) box_tma_kernel(const __grid_constant__ CUt
     if (threadIdx.x == 0) {
         mbar_init(&S.bar[0], 1);
         mbar_init(&S.bar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_mbar_init();
     }
     __syncthreads();
     auto issue = [&](int k, int stage) {
@@ -471,7 +452,7 @@ __global__ void __launch_bounds__(NT) box_tma_kernel(const __grid_constant__ CUt
         }
         __syncthreads();  // the stage is consumed: refill it with tile k + 2
         if (threadIdx.x == 0 && k + 2 < ntiles) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            fence_proxy_async_smem();
             issue(k + 2, stage);
         }
 #pragma unroll
@@ -502,23 +483,6 @@ __global__ void __launch_bounds__(NT) box_tma_kernel(const __grid_constant__ CUt
         block_sum2f(accQ, accCS, S.red, da, db);  // also orders the Bs reads before the next tile's writes
         if (threadIdx.x == 0 && L.partials) L.partials[t] = make_double2(da, db);
     }
-}
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no
-// link-time dependency on the driver library).
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
 }
 
 bool encode_u8_map(CUtensorMap *map, const ImgDesc &d, int count) {

@@ -10,7 +10,7 @@
 // of the zero-extended maps with the window (two separable passes through
 // shared memory), combines them with x(q), y(q), and adds a quarter of the
 // next coarser level's gradient at (q/2): the adjoint of 2x2 average pooling.
-#include "common.cuh"
+#include "tma.cuh"
 
 namespace gbssim {
 namespace {
@@ -123,19 +123,22 @@ constexpr int GCH = 16, GFIRST = GCH + H11;   // rows per chunk / first stage
 constexpr int GRING = 32, GDUP = 10, GRROWS = GRING + GDUP;
 constexpr int GQ = 20, GSW = 4 * GQ;          // staged quads / floats per row (columns c0-12 .. c0+67)
 
-struct __align__(16) Grad11Smem {
+struct __align__(128) Grad11Smem {
     float st[3][GFIRST + GCH][GSW];   // staging: [map][row][col]; rows 0..25 buffer 0, 26..41 buffer 1
     float h[3][GRROWS][TW];           // ring of horizontal results
+    unsigned long long bar[2];        // bulk-copy completion of buffers 0 and 1
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-// Issue the copies of `nr` coefficient rows starting at map row pr0 into
-// staging rows row0..row0+nr-1 (all three maps).
+// Issue the copies of NR coefficient rows starting at map row pr0 into
+// staging rows row0..row0+NR-1 (all three maps).  NR is a compile-time
+// constant so the task decomposition needs no integer division.
+template <int NR>
 __device__ __forceinline__ void stage_coef(Grad11Smem &S, const float *coef, int64_t plane, int64_t cld, int64_t OH,
-                                           int64_t OW, int64_t pr0, int nr, int row0, int64_t pc0) {
-    for (int t = threadIdx.x; t < 3 * nr * GQ; t += NT) {
-        const int m = t / (nr * GQ), rem = t - m * nr * GQ;
+                                           int64_t OW, int64_t pr0, int row0, int64_t pc0) {
+    for (int t = threadIdx.x; t < 3 * NR * GQ; t += NT) {
+        const int m = t / (NR * GQ), rem = t - m * NR * GQ;
         const int r = rem / GQ, q = rem - r * GQ;
         const int64_t pr = pr0 + r, pc = pc0 + 4 * q;
         int bytes = 0;
@@ -151,10 +154,11 @@ __device__ __forceinline__ void stage_coef(Grad11Smem &S, const float *coef, int
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// Horizontal pass over staged rows row0..row0+nr-1 into ring rows (rel0 + r).
-__device__ __forceinline__ void grad_horizontal(Grad11Smem &S, int row0, int nr, int rel0, const TapsDyn &t) {
-    for (int task = threadIdx.x; task < 3 * nr * (TW / 4); task += NT) {
-        const int m = task / (nr * (TW / 4)), rem = task - m * nr * (TW / 4);
+// Horizontal pass over staged rows row0..row0+NR-1 into ring rows (rel0 + r).
+template <int NR>
+__device__ __forceinline__ void grad_horizontal(Grad11Smem &S, int row0, int rel0, const TapsDyn &t) {
+    for (int task = threadIdx.x; task < 3 * NR * (TW / 4); task += NT) {
+        const int m = task / (NR * (TW / 4)), rem = task - m * NR * (TW / 4);
         const int r = rem >> 4, g4 = (rem & 15) * 4;
         float v[16];
         const float4 *src = reinterpret_cast<const float4 *>(&S.st[m][row0 + r][g4]);
@@ -183,9 +187,16 @@ __device__ __forceinline__ void grad_horizontal(Grad11Smem &S, int row0, int nr,
     }
 }
 
-template <typename T, typename G>
-__global__ void __launch_bounds__(NT, 3) grad11_kernel(const GradLaunch L, int strips, int segs, int seg_rows) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+// TMAS: the coefficient rows arrive as per-map 2-D tiles of bulk tensor
+// copies (tmA: 26-row tiles for the first chunk, tmB: 16-row tiles) on two
+// mbarriers, one thread issuing them; otherwise every thread issues 16-byte
+// cp.async copies.  A bulk-copy wait that gives up writes NaN into the rest
+// of the CTA's gradient, waits (bounded) for its copies in flight and returns.
+template <typename T, typename G, bool TMAS>
+__global__ void __launch_bounds__(NT, 3)
+    grad11_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                  const GradLaunch L, int strips, int segs, int seg_rows) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     Grad11Smem &S = *reinterpret_cast<Grad11Smem *>(smem_raw);
     __shared__ float fac;
     const int strip = blockIdx.x, seg = blockIdx.y, img = blockIdx.z;
@@ -213,22 +224,60 @@ __global__ void __launch_bounds__(NT, 3) grad11_kernel(const GradLaunch L, int s
     }
     // chunk c's staged rows: c == 0 rows 0..25; c >= 1 rows 0..15 (c even) or 26..41 (c odd)
     auto buf_row = [](int c) { return (c & 1) ? GFIRST : 0; };
-    stage_coef(S, coef, plane, cld, OH, OW, pr0, GFIRST, 0, pc0);
-    if (nchunks > 1) {
-        stage_coef(S, coef, plane, cld, OH, OW, pr0 + GFIRST, GCH, buf_row(1), pc0);
-        asm volatile("cp.async.wait_group %0;" ::"n"(1) : "memory");  // chunk 0 landed, chunk 1 may fly
-    } else {
-        asm volatile("cp.async.wait_group %0;" ::"n"(0) : "memory");  // the only group must land
-    }
-    __syncthreads();
-    grad_horizontal(S, 0, GFIRST, 0, L.taps);
-
     const T *xb = static_cast<const T *>(L.x.data) + img * L.x.image_stride;
     const T *yb = static_cast<const T *>(L.y.data) + img * L.y.image_stride;
     const int64_t Hh = H >> 1, Wh = W >> 1;
     const float *coarse = L.coarse ? L.coarse + (int64_t)img * Hh * Wh : nullptr;
     const int col = threadIdx.x & (TW - 1), grp = threadIdx.x >> 6;
     const int64_t qc = c0 + col;
+    // bulk copies of chunk c (thread 0): its NR rows of the three maps
+    auto issue = [&](int c) {
+        const bool first = c == 0;
+        const int row0 = first ? 0 : buf_row(c);
+        const int pr = (int)(first ? pr0 : pr0 + GFIRST + (int64_t)GCH * (c - 1));
+        unsigned long long *bar = &S.bar[c & 1];
+        mbar_expect_tx(bar, 3u * (first ? GFIRST : GCH) * GSW * (unsigned)sizeof(float));
+        for (int m = 0; m < 3; ++m) tma_load_3d(&S.st[m][row0][0], first ? &tmA : &tmB, (int)pc0, pr, img * 3 + m, bar);
+    };
+    // a wait gave up at chunk cf: NaN for this thread's outputs of chunks cf.., drain the copies in flight
+    auto give_up = [&](int cf) {
+        if (qc < W)
+            for (int c = cf; c < nchunks; ++c)
+                for (int o = 0; o < 4; ++o) {
+                    const int64_t q = q0 + GCH * c + 4 * grp + o;
+                    if (q < qend) store_grad<G>(L.out, img * L.out_is + q * L.out_ld + qc, nanf(""));
+                }
+        if (threadIdx.x == 0)
+            for (int c = cf; c < nchunks && c < cf + 2; ++c) mbar_wait_bounded(&S.bar[c & 1], (c >> 1) & 1);
+    };
+    if constexpr (TMAS) {
+        if (threadIdx.x == 0) {
+            mbar_init(&S.bar[0], 1);
+            mbar_init(&S.bar[1], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            issue(0);
+            if (nchunks > 1) issue(1);
+        }
+        const bool ok = mbar_wait_bounded(&S.bar[0], 0);
+        if (__syncthreads_or(!ok)) {
+            give_up(0);
+            return;
+        }
+    } else {
+        stage_coef<GFIRST>(S, coef, plane, cld, OH, OW, pr0, 0, pc0);
+        if (nchunks > 1) {
+            stage_coef<GCH>(S, coef, plane, cld, OH, OW, pr0 + GFIRST, buf_row(1), pc0);
+            asm volatile("cp.async.wait_group %0;" ::"n"(1) : "memory");  // chunk 0 landed, chunk 1 may fly
+        } else {
+            asm volatile("cp.async.wait_group %0;" ::"n"(0) : "memory");  // the only group must land
+        }
+        __syncthreads();
+    }
+    grad_horizontal<GFIRST>(S, 0, 0, L.taps);
+
     for (int c = 0; c < nchunks; ++c) {
         __syncthreads();  // ring rows of chunk c complete
         {
@@ -279,15 +328,29 @@ __global__ void __launch_bounds__(NT, 3) grad11_kernel(const GradLaunch L, int s
             }
         }
         if (c + 1 < nchunks) {
-            if (c + 2 < nchunks) {
-                stage_coef(S, coef, plane, cld, OH, OW, pr0 + GFIRST + (int64_t)GCH * (c + 1), GCH, buf_row(c + 2),
-                           pc0);
-                asm volatile("cp.async.wait_group %0;" ::"n"(1) : "memory");
+            if constexpr (TMAS) {
+                // chunk c's buffer was last read by its horizontal pass, before this
+                // iteration's first barrier: refill it with chunk c+2
+                if (threadIdx.x == 0 && c + 2 < nchunks) {
+                    fence_proxy_async_smem();
+                    issue(c + 2);
+                }
+                const bool ok = mbar_wait_bounded(&S.bar[(c + 1) & 1], ((c + 1) >> 1) & 1);
+                if (__syncthreads_or(!ok)) {  // chunk c+1 staged; ring rows of chunk c consumed
+                    give_up(c + 1);
+                    return;
+                }
             } else {
-                asm volatile("cp.async.wait_group %0;" ::"n"(0) : "memory");
+                if (c + 2 < nchunks) {
+                    stage_coef<GCH>(S, coef, plane, cld, OH, OW, pr0 + GFIRST + (int64_t)GCH * (c + 1),
+                                    buf_row(c + 2), pc0);
+                    asm volatile("cp.async.wait_group %0;" ::"n"(1) : "memory");
+                } else {
+                    asm volatile("cp.async.wait_group %0;" ::"n"(0) : "memory");
+                }
+                __syncthreads();  // chunk c+1 staged; ring rows of chunk c consumed
             }
-            __syncthreads();  // chunk c+1 staged; ring rows of chunk c consumed
-            grad_horizontal(S, buf_row(c + 1), GCH, GFIRST + GCH * c, L.taps);
+            grad_horizontal<GCH>(S, buf_row(c + 1), GFIRST + GCH * c, L.taps);
         }
     }
 }
@@ -298,17 +361,42 @@ cudaError_t launch_grad11(const GradLaunch &L, cudaStream_t st) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_set[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(grad11_kernel<T, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(grad11_kernel<T, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sizeof(Grad11Smem));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(grad11_kernel<T, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(Grad11Smem));
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
+    }
+    // the three coefficient planes of every image as one 3-D tensor
+    // (columns, rows, image * 3 + map); 80 x 26 and 80 x 16 float tiles
+    const int64_t OH = L.x.H - H11, OW = L.x.W - H11, cld = coef_ld(OW);
+    CUtensorMap tmA, tmB;
+    memset(&tmA, 0, sizeof tmA);
+    memset(&tmB, 0, sizeof tmB);
+    bool tma = false;
+    if (auto fn = tensor_map_encoder()) {
+        const cuuint64_t dims[3] = {(cuuint64_t)OW, (cuuint64_t)OH, (cuuint64_t)(3 * L.count)};
+        const cuuint64_t strides[2] = {(cuuint64_t)(cld * 4), (cuuint64_t)(OH * cld * 4)};
+        const cuuint32_t boxA[3] = {GSW, GFIRST, 1}, boxB[3] = {GSW, GCH, 1}, estr[3] = {1, 1, 1};
+        tma = (uintptr_t)L.coef % 16 == 0 &&
+              fn(&tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(L.coef), dims, strides, boxA, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS &&
+              fn(&tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(L.coef), dims, strides, boxB, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     }
     const int strips = (int)((L.x.W + TW - 1) / TW);
     int seg_rows = 256;
     while (seg_rows > 32 && (int64_t)strips * ((L.x.H + seg_rows - 1) / seg_rows) * L.count < 4 * 456) seg_rows -= 32;
     const int segs = (int)((L.x.H + seg_rows - 1) / seg_rows);
     dim3 grid(strips, segs, L.count);
-    grad11_kernel<T, G><<<grid, NT, sizeof(Grad11Smem), st>>>(L, strips, segs, seg_rows);
+    if (tma)
+        grad11_kernel<T, G, true><<<grid, NT, sizeof(Grad11Smem), st>>>(tmA, tmB, L, strips, segs, seg_rows);
+    else
+        grad11_kernel<T, G, false><<<grid, NT, sizeof(Grad11Smem), st>>>(tmA, tmB, L, strips, segs, seg_rows);
     return cudaGetLastError();
 }
 
