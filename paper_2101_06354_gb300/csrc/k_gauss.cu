@@ -46,7 +46,9 @@
 // registers while the current chunk is filtered.  For MS-SSIM the same CTA
 // also writes the 2x2 average of the input rows/columns it owns (the next
 // pyramid level), so the input is read from HBM once per level.
-#include "common.cuh"
+#include <type_traits>
+
+#include "tma.cuh"
 
 namespace gbssim {
 namespace {
@@ -77,12 +79,23 @@ constexpr int RROWS = RING + DUP;
 // u = x + y and w = x - y travel together as float2 pairs so that every
 // moment of the pair is one packed f32x2 instruction (FFMA2 / FADD2 / FMUL2
 // on sm_100+).
-struct __align__(16) Smem {
+// Level-0 chunks of 16 input rows may arrive by bulk tensor copies instead
+// of per-thread register prefetch: one 2-D tile of TMA_COLS elements x CH
+// rows per image (x, y) into `raw`, rows RAWP bytes apart at most, and the
+// staging threads then read their units from there.
+constexpr int TMA_COLS = 80;              // >= 4 * QUADS columns, 16-byte multiple for every dtype
+constexpr int RAWP = TMA_COLS * 4;        // bytes per staged raw row, widest dtype
+struct __align__(128) Smem {
     float2 in[FIRST][IWP];   // staged input rows, (u, w) per column
     float2 mu[RROWS][RWP];   // row-window means (mu_u, mu_w)
     float2 v[RROWS][RWP];    // row-window variances (v_u, v_w)
     float red[2 * NT / 32];
+    alignas(128) unsigned char raw[2][CH][RAWP];  // [x|y] bulk-copied rows of the next chunk
+    unsigned long long bar;                         // their completion
 };
+// Kernels that never take the bulk-copy path (the persistent ones) are
+// launched with the shared memory up to `raw` only.
+constexpr size_t kSmemNoBulk = offsetof(Smem, raw);
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -252,6 +265,35 @@ __device__ __forceinline__ void load_unit(Raw &R, const Unit &U, const Geo &g, i
     if (row + 1 < g.H) {
         R.x1 = load_raw<T, LD>(xp + g.rs, U.ncols, U.packed);
         R.y1 = load_raw<T, LD>(yp + g.rs, U.ncols, U.packed);
+    }
+}
+
+// A unit read from the bulk-copied rows in shared memory (packed layout as
+// load_raw's vector form; rows past H and columns past W hold zeros).
+template <typename T>
+__device__ __forceinline__ void load_unit_smem(Raw &R, const Unit &U, const Smem &S) {
+    R.x0 = R.y0 = R.x1 = R.y1 = make_uint4(0u, 0u, 0u, 0u);
+    if (U.p < 0) return;
+    constexpr int pitch = TMA_COLS * (int)sizeof(T);
+    const int off = 2 * U.p * pitch + 4 * U.q * (int)sizeof(T);
+    const unsigned char *bx = &S.raw[0][0][0] + off, *by = &S.raw[1][0][0] + off;
+    if (sizeof(T) == 1) {
+        R.x0.x = *reinterpret_cast<const unsigned *>(bx);
+        R.y0.x = *reinterpret_cast<const unsigned *>(by);
+        R.x1.x = *reinterpret_cast<const unsigned *>(bx + pitch);
+        R.y1.x = *reinterpret_cast<const unsigned *>(by + pitch);
+    } else if (sizeof(T) == 2) {
+        const uint2 a = *reinterpret_cast<const uint2 *>(bx), b = *reinterpret_cast<const uint2 *>(by);
+        const uint2 c = *reinterpret_cast<const uint2 *>(bx + pitch), d = *reinterpret_cast<const uint2 *>(by + pitch);
+        R.x0 = make_uint4(a.x, a.y, 0u, 0u);
+        R.y0 = make_uint4(b.x, b.y, 0u, 0u);
+        R.x1 = make_uint4(c.x, c.y, 0u, 0u);
+        R.y1 = make_uint4(d.x, d.y, 0u, 0u);
+    } else {
+        R.x0 = *reinterpret_cast<const uint4 *>(bx);
+        R.y0 = *reinterpret_cast<const uint4 *>(by);
+        R.x1 = *reinterpret_cast<const uint4 *>(bx + pitch);
+        R.y1 = *reinterpret_cast<const uint4 *>(by + pitch);
     }
 }
 
@@ -485,11 +527,18 @@ struct Item {
     float *dsx, *dsy;      // next-level planes of this image (nullable)
     float *coef_img;       // COEF mode: A, B, C planes of this image
     double2 *partial;      // this item's (sum Q, sum cs) slot
+    const CUtensorMap *tmx, *tmy;  // nullable: bulk-copy maps of the (level-0) x, y planes
+    int tz;                        // this image's index in them
 };
 
-template <typename T, bool COEF, int LD = 0>
+// BULK: the chunks after the first arrive by bulk tensor copies (it.tmx,
+// it.tmy); `phase`: parity of the bulk-copy mbarrier's next phase (the CTA's
+// running count of bulk-copied chunks); `tma_ok`: cleared for the rest of
+// the CTA's items when a bulk-copy wait gives up (that item's partial then
+// reads NaN).
+template <typename T, bool COEF, int LD, bool BULK>
 __device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps<K> &taps, const Taps2<K> &taps2,
-                                             const SsimConst &cc, const CoefOut &co) {
+                                             const SsimConst &cc, const CoefOut &co, unsigned &phase, bool &tma_ok) {
     Geo g;
     g.H = it.H;
     g.W = it.W;
@@ -512,21 +561,66 @@ __device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps
     make_unit(U, g, threadIdx.x, CH / 2);
     const bool col_ok = g.j0 + (threadIdx.x & (TW - 1)) < g.OW;
 
+    constexpr bool tma = BULK;
+    if (tma && !tma_ok) {  // an earlier bulk-copy wait of this CTA gave up
+        if (threadIdx.x == 0) *it.partial = make_double2(nan(""), nan(""));
+        return;
+    }
+    Unit Ut = U;
+    Ut.packed = true;  // bulk-copied units are complete (zeros past the image)
+    bool failed = false;
+
     stage_direct<T, LD>(S, g, g.o0, FIRST, it.dsx, it.dsy);
     __syncthreads();
     horizontal<FIRST>(S, 0, taps2);
     for (int c = 0; c < nchunks; ++c) {
         const bool more = c + 1 < nchunks;
         const int64_t next_r0 = g.o0 + FIRST + (int64_t)CH * c;
-        if (more) load_unit<T, LD>(raw, U, g, next_r0);
+        if (more) {
+            if (tma) {
+                // raw[] was last read before the previous barrier
+                if (threadIdx.x == 0) {
+                    fence_proxy_async_smem();
+                    mbar_expect_tx(&S.bar, 2u * CH * TMA_COLS * (unsigned)sizeof(T));
+                    tma_load_3d(&S.raw[0][0][0], it.tmx, (int)g.j0, (int)next_r0, it.tz, &S.bar);
+                    tma_load_3d(&S.raw[1][0][0], it.tmy, (int)g.j0, (int)next_r0, it.tz, &S.bar);
+                }
+            } else {
+                load_unit<T, LD>(raw, U, g, next_r0);
+            }
+        }
         __syncthreads();  // ring rows of chunk c complete; staging free
         float cq, ccs;
         vertical<COEF>(S, g, CH * c, taps, taps2, cc, it.map, it.map_ld, col_ok, co, it.coef_img, cq, ccs);
         accQ.add(cq);
         accCS.add(ccs);
-        if (more) store_unit<T>(S, raw, U, g, next_r0, 0, it.dsx, it.dsy);
-        __syncthreads();  // staging complete; ring rows of chunk c consumed
-        if (more) horizontal<CH>(S, FIRST + CH * c, taps2);
+        if (more) {
+            if (tma) {
+                const unsigned ph = phase;
+                phase ^= 1u;
+                if (mbar_wait_bounded(&S.bar, ph)) {
+                    load_unit_smem<T>(raw, U, S);
+                    store_unit<T>(S, raw, Ut, g, next_r0, 0, it.dsx, it.dsy);
+                } else {
+                    failed = true;
+                }
+                // staging complete; ring rows of chunk c consumed
+                if (__syncthreads_or(failed)) {
+                    if (threadIdx.x == 0) mbar_wait_bounded(&S.bar, ph);  // drain (bounded)
+                    tma_ok = false;
+                    break;
+                }
+            } else {
+                store_unit<T>(S, raw, U, g, next_r0, 0, it.dsx, it.dsy);
+                __syncthreads();  // staging complete; ring rows of chunk c consumed
+            }
+            horizontal<CH>(S, FIRST + CH * c, taps2);
+        }
+    }
+    if (tma && !tma_ok) {
+        if (threadIdx.x == 0) *it.partial = make_double2(nan(""), nan(""));  // the score reads NaN
+        __syncthreads();
+        return;
     }
     double a, b;
     block_sum2f(accQ.s - accQ.c, accCS.s - accCS.c, S.red, a, b);
@@ -534,9 +628,15 @@ __device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps
 }
 
 template <typename T, bool COEF>
-__global__ void __launch_bounds__(NT, 3) gauss11_kernel(const GaussLaunch L, int strips, int segs) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__global__ void __launch_bounds__(NT, 3)
+    gauss11_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy, bool use_tma,
+                   const GaussLaunch L, int strips, int segs) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    if (use_tma && threadIdx.x == 0) {
+        mbar_init(&S.bar, 1);
+        fence_mbar_init();
+    }
     const int strip = blockIdx.x, seg = blockIdx.y, img = blockIdx.z;
     Item it;
     it.H = L.x.H;
@@ -557,7 +657,14 @@ __global__ void __launch_bounds__(NT, 3) gauss11_kernel(const GaussLaunch L, int
     it.dsy = L.ds_y ? L.ds_y + img * dsn : nullptr;
     it.coef_img = COEF ? L.co.coef + (int64_t)img * 3 * (it.H - HALO) * coef_ld(it.W - HALO) : nullptr;
     it.partial = L.partials + ((int64_t)img * segs + seg) * strips + strip;
-    gauss11_item<T, COEF>(S, it, L.taps, L.taps2, L.c, L.co);
+    it.tmx = use_tma ? &tmx : nullptr;
+    it.tmy = use_tma ? &tmy : nullptr;
+    it.tz = img;
+    unsigned phase = 0;
+    bool tma_ok = true;
+    // the item's first barrier orders the mbarrier initialisation before any use
+    if (use_tma) gauss11_item<T, COEF, 0, true>(S, it, L.taps, L.taps2, L.c, L.co, phase, tma_ok);
+    else gauss11_item<T, COEF, 0, false>(S, it, L.taps, L.taps2, L.c, L.co, phase, tma_ok);
 }
 
 // ----------------------------------------------------------------- ragged persistent batch
@@ -584,6 +691,7 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
 struct Resolved {
     Item it;          // all fields but xb / yb
     const void *xb, *yb;
+    int img;          // image index (uniform batches; -1 in ragged ones)
     bool pyramid;     // level >= 1: float planes written earlier in this launch
     int done_index;   // completion counter this item bumps
     int dep_index;    // counter it waits on (-1: none)
@@ -615,6 +723,7 @@ struct TableSource {
         it.coef_img = nullptr;
         it.partial = reinterpret_cast<double2 *>(ws + lv.part_off) + (int64_t)bi.seg * lv.strips + bi.strip;
         R.pyramid = lv.level > 0;
+        R.img = -1;
         if (lv.level == 0) {
             R.xb = lv.x;
             R.yb = lv.y;
@@ -664,6 +773,7 @@ struct UniformSource {
         it.coef_img = nullptr;
         it.partial = reinterpret_cast<double2 *>(ws + lv.part_off) + (int64_t)img * lv.items_per_image + rem;
         R.pyramid = j > 0;
+        R.img = img;
         if (j == 0) {
             const size_t esz = U.dtype == GBSSIM_U8 ? 1 : U.dtype == GBSSIM_F32 ? 4 : 2;
             R.xb = static_cast<const char *>(U.x) + esz * img * U.image_stride;
@@ -678,13 +788,17 @@ struct UniformSource {
     }
 };
 
+// Register staging throughout (bulk copies measured slower here: the extra
+// code raised register spills of the many-item loop).
 template <typename T, typename Src>
 __global__ void __launch_bounds__(NT, 3) gauss11_persistent_kernel(const Src src, void *ws_ptr, int64_t counter_off,
                                                                   int64_t done_off, int64_t status_off,
                                                                   unsigned wait_limit, Taps<K> taps, Taps2<K> taps2,
                                                                   SsimConst cc) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    unsigned phase = 0;
+    bool tma_ok = true;
     __shared__ int s_item, s_late;
     char *ws = static_cast<char *>(ws_ptr);
     unsigned *counter = reinterpret_cast<unsigned *>(ws + counter_off);
@@ -726,8 +840,10 @@ __global__ void __launch_bounds__(NT, 3) gauss11_persistent_kernel(const Src src
         src.resolve(item, ws, R);
         R.it.xb = R.xb;
         R.it.yb = R.yb;
-        if (!R.pyramid) gauss11_item<T, false, 0>(S, R.it, taps, taps2, cc, co);
-        else gauss11_item<float, false, 1>(S, R.it, taps, taps2, cc, co);
+        R.it.tmx = R.it.tmy = nullptr;
+        R.it.tz = R.img;
+        if (R.pyramid) gauss11_item<float, false, 1, false>(S, R.it, taps, taps2, cc, co, phase, tma_ok);
+        else gauss11_item<T, false, 0, false>(S, R.it, taps, taps2, cc, co, phase, tma_ok);
         __syncthreads();  // every thread's partial and pyramid stores issued
         if (threadIdx.x == 0) {
             if (s_late) *R.it.partial = make_double2(nan(""), nan(""));  // the score reads NaN
@@ -822,6 +938,31 @@ __global__ void __launch_bounds__(GT *GT) generic_kernel(const GenericLaunch L, 
         L.partials[((int64_t)img * tiles_y + blockIdx.y) * tiles_x + blockIdx.x] = make_double2(sa, sb);
 }
 
+template <typename T>
+constexpr CUtensorMapDataType tma_dtype() {
+    return sizeof(T) == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                          : sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                           : (std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                              : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+}
+
+// Bulk-copy map of a batch of planes (columns, rows, image) with
+// TMA_COLS x CH tiles; false when the planes are not 16-byte aligned (base
+// and strides) or no encoder is available -- the register path runs then.
+template <typename T>
+bool encode_plane_map(CUtensorMap *m, const void *data, int64_t H, int64_t W, int64_t rs, int64_t is, int count) {
+    auto fn = tensor_map_encoder();
+    if (!fn) return false;
+    const int64_t esz = sizeof(T), istr = count > 1 ? is : H * rs;
+    if ((uintptr_t)data % 16 != 0 || (rs * esz) % 16 != 0 || (istr * esz) % 16 != 0) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)count};
+    const cuuint64_t strides[2] = {(cuuint64_t)(rs * esz), (cuuint64_t)(istr * esz)};
+    const cuuint32_t box[3] = {TMA_COLS, CH, 1}, estr[3] = {1, 1, 1};
+    return fn(m, tma_dtype<T>(), 3, const_cast<void *>(data), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <typename T, bool COEF>
 cudaError_t launch_gauss11_t(const GaussLaunch &L, cudaStream_t st) {
     static bool attr_set[64] = {};
@@ -842,7 +983,13 @@ cudaError_t launch_gauss11_t(const GaussLaunch &L, cudaStream_t st) {
     A.vec = ((uintptr_t)L.x.data % vbytes == 0) && ((uintptr_t)L.y.data % vbytes == 0) &&
             (L.x.row_stride % 4 == 0) && (L.x.image_stride % 4 == 0) && (L.y.image_stride % 4 == 0);
     dim3 grid(strips, segs, L.count);
-    gauss11_kernel<T, COEF><<<grid, NT, smem, st>>>(A, strips, segs);
+    CUtensorMap mx, my;
+    memset(&mx, 0, sizeof mx);
+    memset(&my, 0, sizeof my);
+    const bool tma =
+        encode_plane_map<T>(&mx, L.x.data, L.x.H, L.x.W, L.x.row_stride, L.x.image_stride, L.count) &&
+        encode_plane_map<T>(&my, L.y.data, L.y.H, L.y.W, L.y.row_stride, L.y.image_stride, L.count);
+    gauss11_kernel<T, COEF><<<grid, NT, smem, st>>>(mx, my, tma, A, strips, segs);
     return cudaGetLastError();
 }
 
@@ -884,14 +1031,14 @@ cudaError_t launch_persistent_t(const Src &src, void *ws, int64_t counter_off, i
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_set[dev]) {
         cudaError_t e = cudaFuncSetAttribute(gauss11_persistent_kernel<T, Src>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemNoBulk);
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
     Taps2<11> t2;
     for (int n = 0; n < 11; ++n) t2.g2[n] = make_float2(taps.g[n], taps.g[n]);
-    gauss11_persistent_kernel<T, Src><<<grid, NT, sizeof(Smem), st>>>(src, ws, counter_off, done_off, status_off,
-                                                                     wait_limit, taps, t2, cc);
+    gauss11_persistent_kernel<T, Src><<<grid, NT, kSmemNoBulk, st>>>(src, ws, counter_off, done_off, status_off,
+                                                                    wait_limit, taps, t2, cc);
     return cudaGetLastError();
 }
 
@@ -918,10 +1065,10 @@ cudaError_t launch_persistent(int dtype, const Src &src, void *ws, int64_t count
 // before the occupancy query sees it.
 int gauss11_batch_max_ctas_per_sm() {
     auto kern = gauss11_persistent_kernel<uint8_t, TableSource>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem)) != cudaSuccess)
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemNoBulk) != cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, sizeof(Smem)) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, kSmemNoBulk) != cudaSuccess) return 0;
     return n;
 }
 
