@@ -44,10 +44,10 @@ LEVELS = [(H >> j, W >> j) for j in range(5)]
 LAUNCHES_PER_STEP = 2
 # pairs of the end-to-end step are copied and scored in this many chunks
 E2E_CHUNKS = 4
-# DRAM bytes (read + write) of one persistent launch on this workload, from the
-# ncu capture summarised in profiles/gauss11_msssim_1080p_x64.md; valid only for
+# DRAM bytes (read + write) of one persistent launch on this workload, from an
+# ncu capture of dram__bytes_read.sum + dram__bytes_write.sum; valid only for
 # the kernel source it was taken on (sha256 of the file below, first 16 hex).
-TRAFFIC = {"bytes": 597.10e6 + 336.19e6, "sources_sha": "358c03e140b31421"}
+TRAFFIC = {"bytes": 595.67e6 + 334.95e6, "sources_sha": "950e4756410d0c09"}
 TRAFFIC_SOURCES = ("paper_2101_06354_gb300/csrc/k_gauss.cu",)
 
 
