@@ -34,7 +34,9 @@
 // pyramid levels j >= 1 hold multiples of 4^-j (averages of 4^j pixels),
 // which the kernel scales by 4^j to exact integers and sums in int64, with
 // C1 and C2 scaled by 16^j so that l and cs are those of the unscaled level.
-#include "common.cuh"
+#include <type_traits>
+
+#include "tma.cuh"
 
 namespace gbssim {
 namespace {
@@ -63,7 +65,13 @@ struct S3Geo {
 
 // Dynamic shared memory: Ts[4][ih][pw] temporal sums of the input tile, then
 // Vs[4][iw][PV] the k-row column sums (column-major), then the step-3 warp
-// sums (double2 per warp; every part starts on a 16-byte boundary).
+// sums (double2 per warp; every part starts on a 16-byte boundary); with
+// bulk copies (uint8 video) then, from a 128-byte boundary, the four byte
+// tiles of the next frame (x, y, x and y of the frame leaving the window),
+// ih rows of raw3_width(k) bytes each, and their mbarrier.
+// Bytes per bulk-copied tile row: the input tile width rounded up to 16
+// (covers every 4-column group, a multiple of 16 as bulk copies need).
+__host__ __device__ constexpr int raw3_width(int k) { return ((OW3 + k - 1) + 15) & ~15; }
 template <typename A>
 __device__ __forceinline__ A *ts_of(A *sm, const S3Geo &g, int q) {
     return sm + q * g.ih * g.pw;
@@ -147,11 +155,17 @@ __device__ __forceinline__ void store_col(long long *vc, const long long (&v)[OH
     for (int i = 0; i < OH; ++i) vc[i] = v[i];
 }
 
-template <typename A, typename In>
+// BULK (uint8 video): each frame's input tiles arrive by 2-D bulk tensor
+// copies (tmx, tmy: ih x 80-byte tiles of frame z) issued by one thread after
+// the previous frame's step 1, instead of per-thread loads.  A bulk-copy wait
+// that gives up writes NaN partials for the CTA's remaining output frames,
+// waits (bounded) for its copies in flight and returns.
+template <typename A, typename In, bool BULK>
 __global__ void __launch_bounds__(NT, sizeof(A) == 4 ? 4 : 2)
-    ssim3d_kernel(const Ssim3dLaunch L, int tiles_x, int tiles_y, int t_chunk) {
+    ssim3d_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy,
+                  const Ssim3dLaunch L, int tiles_x, int tiles_y, int t_chunk) {
     constexpr int OH = Tile3<A>::OH, PV = Tile3<A>::PV;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     A *sm = reinterpret_cast<A *>(smem_raw);
     S3Geo g;
     g.k = L.k;
@@ -170,6 +184,31 @@ __global__ void __launch_bounds__(NT, sizeof(A) == 4 ? 4 : 2)
     const int64_t x0 = (int64_t)tx * OW3, y0 = (int64_t)ty * OH;
     const In *xb = static_cast<const In *>(L.x.data), *yb = static_cast<const In *>(L.y.data);
     const int lane = threadIdx.x & 31;
+    // bulk-copy tiles and their mbarrier after the warp sums
+    const size_t bulk_off = ((reinterpret_cast<unsigned char *>(vs_of(sm, g, 4) + 0) - smem_raw) +
+                             sizeof(double2) * Tile3<A>::WARPS3 + 127) & ~(size_t)127;
+    unsigned char *raw = smem_raw + bulk_off;
+    const int rw = raw3_width(L.k);
+    const unsigned tile_bytes = (unsigned)(g.ih * rw);            // one tile
+    const unsigned tile_stride = (tile_bytes + 127u) & ~127u;      // tiles start on 128-byte boundaries
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(raw + 4 * tile_stride);
+    // frame ff's tiles (thread 0): x, y of ff, and of ff - kt when it leaves a window of this CTA
+    auto issue = [&](int ff) {
+        const bool with_old = ff - L.kt >= f_begin;
+        mbar_expect_tx(bar, (with_old ? 4u : 2u) * tile_bytes);
+        tma_load_3d(raw, &tmx, (int)x0, (int)y0, ff, bar);
+        tma_load_3d(raw + tile_stride, &tmy, (int)x0, (int)y0, ff, bar);
+        if (with_old) {
+            tma_load_3d(raw + 2 * tile_stride, &tmx, (int)x0, (int)y0, ff - L.kt, bar);
+            tma_load_3d(raw + 3 * tile_stride, &tmy, (int)x0, (int)y0, ff - L.kt, bar);
+        }
+    };
+    unsigned phase = 0;
+    if (BULK && threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        issue(f_begin);
+    }
     for (int i = threadIdx.x; i < 4 * g.ih * g.pw; i += NT) sm[i] = 0;
     __syncthreads();
     const int64_t N = (int64_t)L.k * L.k * L.kt;
@@ -206,8 +245,8 @@ __global__ void __launch_bounds__(NT, sizeof(A) == 4 ? 4 : 2)
     Raw<In> px[RB], py[RB], pxo[RB], pyo[RB];  // frame f and frame f - kt of those groups
 #pragma unroll
     for (int u = 0; u < RB; ++u) {
-        load_raw(xb + f_begin * fs + o0[u], n40[u], words, px[u]);
-        load_raw(yb + f_begin * fs + o0[u], n40[u], words, py[u]);
+        load_raw(xb + f_begin * fs + o0[u], BULK ? 0 : n40[u], words, px[u]);
+        load_raw(yb + f_begin * fs + o0[u], BULK ? 0 : n40[u], words, py[u]);
         load_raw(xb, 0, words, pxo[u]);  // no frame leaves the window yet
         load_raw(yb, 0, words, pyo[u]);
     }
@@ -217,6 +256,36 @@ __global__ void __launch_bounds__(NT, sizeof(A) == 4 ? 4 : 2)
         //    RB of them with their loads in flight together; 16-byte shared
         //    accesses, consecutive across a warp.
         const bool old = f - L.kt >= f_begin;
+        bool failed = false;
+        if constexpr (BULK) {
+            // the tiles of frame f, bulk-copied during the previous frame's steps 2 and 3
+            if (!mbar_wait_bounded(bar, phase)) failed = true;
+            phase ^= 1u;
+            if (!failed)
+                for (int unit = threadIdx.x; unit < units; unit += NT) {
+                    const int r = unit / g.groups, c = 4 * (unit - r * g.groups);
+                    const unsigned char *rp = raw + r * rw + c;
+                    Raw<In> ux, uy, ox, oy;
+                    ux.w = *reinterpret_cast<const unsigned *>(rp);
+                    uy.w = *reinterpret_cast<const unsigned *>(rp + tile_stride);
+                    ox.w = old ? *reinterpret_cast<const unsigned *>(rp + 2 * tile_stride) : 0u;
+                    oy.w = old ? *reinterpret_cast<const unsigned *>(rp + 3 * tile_stride) : 0u;
+                    A d[4][4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int p = unpack(ux, e, scale), q = unpack(uy, e, scale);
+                        const int po = unpack(ox, e, scale), qo = unpack(oy, e, scale);
+                        const A uu = (A)p + q, ww = (A)p - q, uo = (A)po + qo, wo = (A)po - qo;
+                        d[0][e] = uu - uo;
+                        d[1][e] = ww - wo;
+                        d[2][e] = (uu - uo) * (uu + uo);
+                        d[3][e] = (ww - wo) * (ww + wo);
+                    }
+                    const int at = r * g.pw + c;
+#pragma unroll
+                    for (int qd = 0; qd < 4; ++qd) add4(ts_of(sm, g, qd) + at, d[qd]);
+                }
+        } else {
         const In *xf = xb + f * fs, *yf = yb + f * fs;
         const In *xo = xb + (f - L.kt) * fs, *yo = yb + (f - L.kt) * fs;
         for (int u0 = threadIdx.x; u0 < units; u0 += RB * NT) {
@@ -275,9 +344,26 @@ __global__ void __launch_bounds__(NT, sizeof(A) == 4 ? 4 : 2)
                 for (int qd = 0; qd < 4; ++qd) add4(ts_of(sm, g, qd) + at[u], d[qd]);
             }
         }
-        if (f < f_begin + L.kt - 1) continue;
+        }  // register path
+        const bool out_frame = f >= f_begin + L.kt - 1;
+        if constexpr (BULK) {
+            // every thread is done with the tiles of frame f: thread 0 refills them with frame f+1
+            if (__syncthreads_or(failed)) {
+                if (threadIdx.x == 0) {
+                    mbar_wait_bounded(bar, phase ^ 1u);  // drain the copy that did not complete (bounded)
+                    for (int tt = max(t_begin, f - L.kt + 1); tt < t_end; ++tt)
+                        L.partials[(int64_t)tt * (tiles_x * tiles_y) + tile] = make_double2(nan(""), nan(""));
+                }
+                return;
+            }
+            if (threadIdx.x == 0 && f + 1 < f_end) {
+                fence_proxy_async_smem();
+                issue(f + 1);
+            }
+        }
+        if (!out_frame) continue;
         const int t = f - L.kt + 1;  // output frame
-        __syncthreads();             // Ts holds frames t .. f; red holds frame t-1's warp sums
+        if (!BULK) __syncthreads();  // Ts holds frames t .. f; red holds frame t-1's warp sums
         if (threadIdx.x == 0 && pending >= 0) flush(pending);
         // 2. k-row sums down each column for the OH output rows: one thread
         //    per (quantity, column), lanes over consecutive columns
@@ -435,23 +521,42 @@ __global__ void __launch_bounds__(256) frame_mean_kernel(const double *frames, i
 }
 
 template <typename A>
-size_t smem_bytes(int k) {
+size_t smem_bytes(int k, bool bulk) {
     const size_t ih = Tile3<A>::OH + k - 1, iw = OW3 + k - 1, pw = (iw + 3) & ~(size_t)3;
-    return sizeof(A) * (4 * ih * pw + 4 * iw * Tile3<A>::PV) + sizeof(double2) * Tile3<A>::WARPS3;
+    const size_t base = sizeof(A) * (4 * ih * pw + 4 * iw * Tile3<A>::PV) + sizeof(double2) * Tile3<A>::WARPS3;
+    if (!bulk) return base;
+    return ((base + 127) & ~(size_t)127) + 4 * ((ih * raw3_width(k) + 127) & ~(size_t)127) +
+           sizeof(unsigned long long);
 }
 
-template <typename A, typename In>
-cudaError_t launch_level(const Ssim3dLaunch &L, cudaStream_t st) {
+// Bulk-copy map of a uint8 video (columns, rows, frames) with rw x ih
+// tiles; false when rows or frames are not 16-byte aligned.
+bool encode_video_map(CUtensorMap *m, const ImgDesc &d, int T, int ih, int rw) {
+    auto fn = tensor_map_encoder();
+    if (!fn) return false;
+    if ((uintptr_t)d.data % 16 != 0 || d.row_stride % 16 != 0 || (T > 1 && d.image_stride % 16 != 0)) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)d.W, (cuuint64_t)d.H, (cuuint64_t)T};
+    const cuuint64_t strides[2] = {(cuuint64_t)d.row_stride,
+                                   (cuuint64_t)(T > 1 ? d.image_stride : d.H * d.row_stride)};
+    const cuuint32_t box[3] = {(cuuint32_t)rw, (cuuint32_t)ih, 1}, estr[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void *>(d.data), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename A, typename In, bool BULK>
+cudaError_t launch_level_k(const Ssim3dLaunch &L, const CUtensorMap &mx, const CUtensorMap &my, cudaStream_t st) {
     int tx, ty;
     ssim3d_tiles(L.x.H, L.x.W, L.k, sizeof(A) == 8, &tx, &ty);
     static bool attr_set[64] = {};
     static int slots[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    const size_t smem = smem_bytes<A>(L.k);
+    const size_t smem = smem_bytes<A>(L.k, BULK);
     if (!attr_set[dev]) {
-        const cudaError_t e = cudaFuncSetAttribute(ssim3d_kernel<A, In>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)smem_bytes<A>(kSsim3dMaxK));
+        const cudaError_t e = cudaFuncSetAttribute(ssim3d_kernel<A, In, BULK>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem_bytes<A>(kSsim3dMaxK, BULK));
         if (e != cudaSuccess) return e;
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return cudaErrorUnknown;
@@ -459,7 +564,7 @@ cudaError_t launch_level(const Ssim3dLaunch &L, cudaStream_t st) {
         attr_set[dev] = true;
     }
     int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ssim3d_kernel<A, In>, NT, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ssim3d_kernel<A, In, BULK>, NT, smem) != cudaSuccess)
         return cudaErrorUnknown;
     // Split the output frames into chunks (each CTA primes its own temporal
     // sums with kt-1 frames) when the tiles alone fill fewer than two waves;
@@ -475,8 +580,23 @@ cudaError_t launch_level(const Ssim3dLaunch &L, cudaStream_t st) {
     }
     const int t_chunk = (frames + chunks - 1) / chunks;
     chunks = (frames + t_chunk - 1) / t_chunk;
-    ssim3d_kernel<A, In><<<tiles * chunks, NT, smem, st>>>(L, tx, ty, t_chunk);
+    ssim3d_kernel<A, In, BULK><<<tiles * chunks, NT, smem, st>>>(mx, my, L, tx, ty, t_chunk);
     return cudaGetLastError();
+}
+
+// uint8 video with 16-byte aligned rows and frames: bulk-copied tiles.
+template <typename A, typename In>
+cudaError_t launch_level(const Ssim3dLaunch &L, cudaStream_t st) {
+    CUtensorMap mx, my;
+    memset(&mx, 0, sizeof mx);
+    memset(&my, 0, sizeof my);
+    if constexpr (std::is_same<In, uint8_t>::value) {
+        const int ih = Tile3<A>::OH + L.k - 1;
+        const int rw = raw3_width(L.k);
+        if (encode_video_map(&mx, L.x, L.T, ih, rw) && encode_video_map(&my, L.y, L.T, ih, rw))
+            return launch_level_k<A, In, true>(L, mx, my, st);
+    }
+    return launch_level_k<A, In, false>(L, mx, my, st);
 }
 
 }  // namespace

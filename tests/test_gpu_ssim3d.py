@@ -34,7 +34,8 @@ def _video(T, H, W, seed=0):
 @pytest.mark.parametrize("T,H,W,k,kt", [(9, 40, 70, 11, 5), (6, 33, 150, 5, 3), (4, 26, 64, 11, 1),
                                         (12, 20, 21, 3, 12), (7, 80, 129, 8, 4),
                                         (10, 40, 100, 31, 9),   # N = 8649: int64 window sums
-                                        (20, 24, 40, 3, 2), (16, 30, 50, 5, 3)])  # few tiles: frames split over CTAs
+                                        (20, 24, 40, 3, 2), (16, 30, 50, 5, 3),  # few tiles: frames split over CTAs
+                                        (6, 64, 128, 31, 2), (5, 50, 160, 19, 3)])  # 16-byte rows: bulk-copied tiles
 def test_ssim3d_matches_oracle(g, T, H, W, k, kt):
     x, y = _video(T, H, W, seed=T + k)
     score, frames, q = g.ssim3d(x.to(DEV), y.to(DEV), kt=kt, k=k, return_map=True)
