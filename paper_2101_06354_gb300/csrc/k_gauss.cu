@@ -561,41 +561,48 @@ __device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps
     make_unit(U, g, threadIdx.x, CH / 2);
     const bool col_ok = g.j0 + (threadIdx.x & (TW - 1)) < g.OW;
 
-    constexpr bool tma = BULK;
-    if (tma && !tma_ok) {  // an earlier bulk-copy wait of this CTA gave up
+    if (BULK && !tma_ok) {  // an earlier bulk-copy wait of this CTA gave up
         if (threadIdx.x == 0) *it.partial = make_double2(nan(""), nan(""));
         return;
     }
     Unit Ut = U;
     Ut.packed = true;  // bulk-copied units are complete (zeros past the image)
-    bool failed = false;
 
     stage_direct<T, LD>(S, g, g.o0, FIRST, it.dsx, it.dsy);
     __syncthreads();
     horizontal<FIRST>(S, 0, taps2);
-    for (int c = 0; c < nchunks; ++c) {
-        const bool more = c + 1 < nchunks;
-        const int64_t next_r0 = g.o0 + FIRST + (int64_t)CH * c;
-        if (more) {
-            if (tma) {
-                // raw[] was last read before the previous barrier
-                if (threadIdx.x == 0) {
-                    fence_proxy_async_smem();
-                    mbar_expect_tx(&S.bar, 2u * CH * TMA_COLS * (unsigned)sizeof(T));
-                    tma_load_3d(&S.raw[0][0][0], it.tmx, (int)g.j0, (int)next_r0, it.tz, &S.bar);
-                    tma_load_3d(&S.raw[1][0][0], it.tmy, (int)g.j0, (int)next_r0, it.tz, &S.bar);
-                }
-            } else {
-                load_unit<T, LD>(raw, U, g, next_r0);
-            }
+    if constexpr (!BULK) {
+        for (int c = 0; c < nchunks; ++c) {
+            const bool more = c + 1 < nchunks;
+            const int64_t next_r0 = g.o0 + FIRST + (int64_t)CH * c;
+            if (more) load_unit<T, LD>(raw, U, g, next_r0);
+            __syncthreads();  // ring rows of chunk c complete; staging free
+            float cq, ccs;
+            vertical<COEF>(S, g, CH * c, taps, taps2, cc, it.map, it.map_ld, col_ok, co, it.coef_img, cq, ccs);
+            accQ.add(cq);
+            accCS.add(ccs);
+            if (more) store_unit<T>(S, raw, U, g, next_r0, 0, it.dsx, it.dsy);
+            __syncthreads();  // staging complete; ring rows of chunk c consumed
+            if (more) horizontal<CH>(S, FIRST + CH * c, taps2);
         }
-        __syncthreads();  // ring rows of chunk c complete; staging free
-        float cq, ccs;
-        vertical<COEF>(S, g, CH * c, taps, taps2, cc, it.map, it.map_ld, col_ok, co, it.coef_img, cq, ccs);
-        accQ.add(cq);
-        accCS.add(ccs);
-        if (more) {
-            if (tma) {
+    } else {
+        for (int c = 0; c < nchunks; ++c) {
+            const bool more = c + 1 < nchunks;
+            const int64_t next_r0 = g.o0 + FIRST + (int64_t)CH * c;
+            // raw[] was last read before the previous barrier
+            if (more && threadIdx.x == 0) {
+                fence_proxy_async_smem();
+                mbar_expect_tx(&S.bar, 2u * CH * TMA_COLS * (unsigned)sizeof(T));
+                tma_load_3d(&S.raw[0][0][0], it.tmx, (int)g.j0, (int)next_r0, it.tz, &S.bar);
+                tma_load_3d(&S.raw[1][0][0], it.tmy, (int)g.j0, (int)next_r0, it.tz, &S.bar);
+            }
+            __syncthreads();  // ring rows of chunk c complete; staging free
+            float cq, ccs;
+            vertical<COEF>(S, g, CH * c, taps, taps2, cc, it.map, it.map_ld, col_ok, co, it.coef_img, cq, ccs);
+            accQ.add(cq);
+            accCS.add(ccs);
+            bool failed = false;
+            if (more) {
                 const unsigned ph = phase;
                 phase ^= 1u;
                 if (mbar_wait_bounded(&S.bar, ph)) {
@@ -604,23 +611,17 @@ __device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps
                 } else {
                     failed = true;
                 }
-                // staging complete; ring rows of chunk c consumed
-                if (__syncthreads_or(failed)) {
-                    if (threadIdx.x == 0) mbar_wait_bounded(&S.bar, ph);  // drain (bounded)
-                    tma_ok = false;
-                    break;
-                }
-            } else {
-                store_unit<T>(S, raw, U, g, next_r0, 0, it.dsx, it.dsy);
-                __syncthreads();  // staging complete; ring rows of chunk c consumed
             }
-            horizontal<CH>(S, FIRST + CH * c, taps2);
+            // staging complete; ring rows of chunk c consumed
+            if (__syncthreads_or(failed)) {
+                if (threadIdx.x == 0) mbar_wait_bounded(&S.bar, phase ^ 1u);  // drain (bounded)
+                tma_ok = false;
+                if (threadIdx.x == 0) *it.partial = make_double2(nan(""), nan(""));  // the score reads NaN
+                __syncthreads();
+                return;
+            }
+            if (more) horizontal<CH>(S, FIRST + CH * c, taps2);
         }
-    }
-    if (tma && !tma_ok) {
-        if (threadIdx.x == 0) *it.partial = make_double2(nan(""), nan(""));  // the score reads NaN
-        __syncthreads();
-        return;
     }
     double a, b;
     block_sum2f(accQ.s - accQ.c, accCS.s - accCS.c, S.red, a, b);
