@@ -789,15 +789,22 @@ struct UniformSource {
     }
 };
 
-// Register staging throughout (bulk copies measured slower here: the extra
-// code raised register spills of the many-item loop).
-template <typename T, typename Src>
-__global__ void __launch_bounds__(NT, 3) gauss11_persistent_kernel(const Src src, void *ws_ptr, int64_t counter_off,
-                                                                  int64_t done_off, int64_t status_off,
-                                                                  unsigned wait_limit, Taps<K> taps, Taps2<K> taps2,
-                                                                  SsimConst cc) {
+// BULK: level-0 items (uniform batches) take their chunks by bulk tensor
+// copies (tmx, tmy; the image index is the map's third coordinate); pyramid
+// levels keep register staging (their planes are written in this launch).
+// After a bulk-copy wait gives up, the CTA's remaining level-0 items write NaN
+// partials.  Without BULK the launch needs the shared memory up to `raw` only.
+template <typename T, typename Src, bool BULK>
+__global__ void __launch_bounds__(NT, 3)
+    gauss11_persistent_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy,
+                              const Src src, void *ws_ptr, int64_t counter_off, int64_t done_off,
+                              int64_t status_off, unsigned wait_limit, Taps<K> taps, Taps2<K> taps2, SsimConst cc) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    if (BULK && threadIdx.x == 0) {
+        mbar_init(&S.bar, 1);
+        fence_mbar_init();
+    }
     unsigned phase = 0;
     bool tma_ok = true;
     __shared__ int s_item, s_late;
@@ -841,10 +848,11 @@ __global__ void __launch_bounds__(NT, 3) gauss11_persistent_kernel(const Src src
         src.resolve(item, ws, R);
         R.it.xb = R.xb;
         R.it.yb = R.yb;
-        R.it.tmx = R.it.tmy = nullptr;
+        R.it.tmx = BULK ? &tmx : nullptr;
+        R.it.tmy = BULK ? &tmy : nullptr;
         R.it.tz = R.img;
         if (R.pyramid) gauss11_item<float, false, 1, false>(S, R.it, taps, taps2, cc, co, phase, tma_ok);
-        else gauss11_item<T, false, 0, false>(S, R.it, taps, taps2, cc, co, phase, tma_ok);
+        else gauss11_item<T, false, 0, BULK>(S, R.it, taps, taps2, cc, co, phase, tma_ok);
         __syncthreads();  // every thread's partial and pyramid stores issued
         if (threadIdx.x == 0) {
             if (s_late) *R.it.partial = make_double2(nan(""), nan(""));  // the score reads NaN
@@ -1024,22 +1032,39 @@ cudaError_t launch_gauss11(const GaussLaunch &L, cudaStream_t st) {
     return cudaErrorInvalidValue;
 }
 
+// mx, my: nullable level-0 bulk-copy maps (uniform batches only).
 template <typename T, typename Src>
 cudaError_t launch_persistent_t(const Src &src, void *ws, int64_t counter_off, int64_t done_off, int64_t status_off,
-                                unsigned wait_limit, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st) {
+                                unsigned wait_limit, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st,
+                                const CUtensorMap *mx = nullptr, const CUtensorMap *my = nullptr) {
+    constexpr bool can_bulk = std::is_same<Src, UniformSource>::value;
     static bool attr_set[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_set[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(gauss11_persistent_kernel<T, Src>,
+        cudaError_t e = cudaFuncSetAttribute(gauss11_persistent_kernel<T, Src, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemNoBulk);
+        if constexpr (can_bulk)
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(gauss11_persistent_kernel<T, Src, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
     Taps2<11> t2;
     for (int n = 0; n < 11; ++n) t2.g2[n] = make_float2(taps.g[n], taps.g[n]);
-    gauss11_persistent_kernel<T, Src><<<grid, NT, kSmemNoBulk, st>>>(src, ws, counter_off, done_off, status_off,
-                                                                    wait_limit, taps, t2, cc);
+    if constexpr (can_bulk) {
+        if (mx && my) {
+            gauss11_persistent_kernel<T, Src, true><<<grid, NT, sizeof(Smem), st>>>(
+                *mx, *my, src, ws, counter_off, done_off, status_off, wait_limit, taps, t2, cc);
+            return cudaGetLastError();
+        }
+    }
+    CUtensorMap zx, zy;
+    memset(&zx, 0, sizeof zx);
+    memset(&zy, 0, sizeof zy);
+    gauss11_persistent_kernel<T, Src, false><<<grid, NT, kSmemNoBulk, st>>>(
+        zx, zy, src, ws, counter_off, done_off, status_off, wait_limit, taps, t2, cc);
     return cudaGetLastError();
 }
 
@@ -1065,11 +1090,13 @@ cudaError_t launch_persistent(int dtype, const Src &src, void *ws, int64_t count
 // the launch shape); the >48 KB dynamic shared memory attribute must be set
 // before the occupancy query sees it.
 int gauss11_batch_max_ctas_per_sm() {
-    auto kern = gauss11_persistent_kernel<uint8_t, TableSource>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemNoBulk) != cudaSuccess)
+    // both variants fit the same CTAs per SM: the bulk one's extra shared
+    // memory (the staging area) stays within three CTAs' share
+    auto kern = gauss11_persistent_kernel<uint8_t, UniformSource, true>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem)) != cudaSuccess)
         return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, kSmemNoBulk) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, sizeof(Smem)) != cudaSuccess) return 0;
     return n;
 }
 
@@ -1079,10 +1106,24 @@ cudaError_t launch_batch(const BatchTable &B, const Taps<11> &taps, SsimConst cc
                              grid, st);
 }
 
-cudaError_t launch_uniform(const UniformBatch &U, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_uniform_t(const UniformBatch &U, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st) {
     UniformSource src{U};
-    return launch_persistent(U.dtype, src, U.ws, U.counter_off, U.done_off, U.status_off, U.wait_limit, taps, cc,
-                             grid, st);
+    CUtensorMap mx, my;
+    const bool bulk = encode_plane_map<T>(&mx, U.x, U.lv[0].H, U.lv[0].W, U.rs, U.image_stride, U.count) &&
+                      encode_plane_map<T>(&my, U.y, U.lv[0].H, U.lv[0].W, U.rs, U.image_stride, U.count);
+    return launch_persistent_t<T>(src, U.ws, U.counter_off, U.done_off, U.status_off, U.wait_limit, taps, cc, grid,
+                                  st, bulk ? &mx : nullptr, bulk ? &my : nullptr);
+}
+
+cudaError_t launch_uniform(const UniformBatch &U, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st) {
+    switch (U.dtype) {
+    case GBSSIM_U8: return launch_uniform_t<uint8_t>(U, taps, cc, grid, st);
+    case GBSSIM_F16: return launch_uniform_t<__half>(U, taps, cc, grid, st);
+    case GBSSIM_BF16: return launch_uniform_t<__nv_bfloat16>(U, taps, cc, grid, st);
+    case GBSSIM_F32: return launch_uniform_t<float>(U, taps, cc, grid, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 int generic_items(int64_t OH, int64_t OW) {
