@@ -362,7 +362,19 @@ int gbssim_msssim(const gbssim_plane *x, const gbssim_plane *y, const gbssim_par
  *   x, y         : host planes (any pitch; pinned memory gives the overlap,
  *                  pageable memory is correct but copied synchronously).
  *                  They must stay valid until `stream` has completed.
- *   chunks       : >= 1 (clamped to count).
+ *   chunks       : >= 1 (clamped to count); or 0, streamed: every image gets
+ *                  its own device slot and one MS-SSIM launch covers them all;
+ *                  the copy stream copies the images in up to 16 groups of
+ *                  consecutive images and after each group sets that group's
+ *                  arrival flag with a stream memory write; the level-0 work
+ *                  of an image waits (bounded) for its group's flag, so
+ *                  scoring starts as soon as the first group is in.  Streamed
+ *                  mode needs the Gaussian 11-tap window at stride 1 without
+ *                  the 9/7 pyramid or border flags (else
+ *                  GBSSIM_ERR_UNSUPPORTED) and a copy_stream created with
+ *                  cudaStreamNonBlocking (else GBSSIM_ERR_INVALID_ARG: a
+ *                  stream that synchronises with `stream` would hold the
+ *                  copies behind the launch).
  *   score_host   : x.count doubles in host memory (pinned for an asynchronous
  *                  return), valid once `stream` has completed.
  *   workspace    : device buffer of gbssim_msssim_host_workspace_size bytes;

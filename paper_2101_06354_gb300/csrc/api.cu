@@ -4,6 +4,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 
 using namespace gbssim;
@@ -325,13 +328,17 @@ cudaError_t run_level(const Level &L, const ImgDesc &dx, const ImgDesc &dy, int 
 // where the path allows), then the finaliser.  Shared by gbssim_msssim and
 // the MS-SSIM backward.
 
+// arrive (nullable, persistent path only): level-0 items of image i wait
+// (bounded) until arrive[i / arrive_group] != 0, their bytes being copied in
+// on another stream.
 int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
                           const MsPlan &P, char *ws, double *score_out, double *per_scale_out,
-                          cudaStream_t st) {
+                          cudaStream_t st, const unsigned *arrive = nullptr, int arrive_group = 1) {
     const int S = p->scales, n = x->count;
     // the persistent path fuses the 2x2 pyramid into valid-window levels
     bool persistent = (p->flags & GBSSIM_FLAG_PYRAMID_97) == 0 && !border_mode(p);
     for (int j = 0; j < S; ++j) persistent = persistent && P.lv[j].path == PATH_GAUSS11;
+    if (arrive && !persistent) return GBSSIM_ERR_UNSUPPORTED;  // only the persistent launch waits for arrivals
     if (persistent) {
         // one launch over all levels and images: level-major items, a level-j
         // item of an image waits (bounded) for that image's level-(j-1) items
@@ -381,6 +388,8 @@ int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_pa
         U.done_off = (int64_t)P.done_off;
         U.status_off = (int64_t)P.status_off;
         U.wait_limit = 1u << 22;
+        U.arrive = arrive;
+        U.arrive_group = arrive_group > 0 ? arrive_group : 1;
         if (begin > 0x7fffffff) return GBSSIM_ERR_UNSUPPORTED;
         if (cudaMemsetAsync(ws + P.counter_off, 0, P.zero_bytes, st) != cudaSuccess) return GBSSIM_ERR_CUDA;
         Taps<11> taps;
@@ -392,7 +401,9 @@ int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_pa
         if (per_sm < 1) return GBSSIM_ERR_CUDA;
         const int64_t want = (int64_t)sms * per_sm;
         const int grid = (int)(want < begin ? want : begin);
-        if (launch_uniform(U, taps, make_const(p), grid, st) != cudaSuccess) return GBSSIM_ERR_CUDA;
+        const cudaError_t le = launch_uniform(U, taps, make_const(p), grid, st);
+        if (le == cudaErrorNotSupported) return GBSSIM_ERR_UNSUPPORTED;  // arrival flags without bulk-copy maps
+        if (le != cudaSuccess) return GBSSIM_ERR_CUDA;
         F.scales = S;
         F.count = n;
         F.combine = p->combine;
@@ -551,16 +562,65 @@ int check_loss(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params
 // images each (x then y, rows padded to 16 bytes), the MS-SSIM workspace for
 // one chunk, and the scores of all images.
 struct HostPlan {
-    int per, chunks;
+    int per, chunks;            // chunks == 0: streamed (one launch, images start as they arrive)
     int64_t pitch_elems;        // device row pitch in elements
     size_t esz, stage_bytes, plane_bytes;
-    size_t stage_off[2], ws_off[2], score_off, bytes;  // stage s computes in workspace s
+    size_t stage_off[2], ws_off[2], score_off, flags_off, bytes;  // stage s computes in workspace s
     MsPlan ms;                  // for a chunk of `per` images
 };
 
+// The persistent MS-SSIM path (the one streamed mode runs) takes these params.
+bool persistent_params(const gbssim_params *p) {
+    return p->window == GBSSIM_WIN_GAUSSIAN && p->k == 11 && p->stride == 1 &&
+           (p->flags & (GBSSIM_FLAG_PYRAMID_97 | GBSSIM_FLAG_BORDER_ZERO | GBSSIM_FLAG_BORDER_REFLECT)) == 0;
+}
+
+// cuStreamWriteValue32 through the runtime's driver entry point (nullptr if
+// unavailable): the copy stream's arrival flags for the streamed mode.
+PFN_cuStreamWriteValue32_v11070 stream_write_value32() {
+    static PFN_cuStreamWriteValue32_v11070 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *q = nullptr;
+        cudaDriverEntryPointQueryResult r;
+        if (cudaGetDriverEntryPointByVersion("cuStreamWriteValue32", &q, 12000, cudaEnableDefault, &r) ==
+                cudaSuccess &&
+            r == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuStreamWriteValue32_v11070>(q);
+    }
+    return fn;
+}
+
 int plan_host(const gbssim_plane *x, const gbssim_params *p, int32_t chunks, HostPlan *H) {
-    if (chunks < 1) return GBSSIM_ERR_INVALID_ARG;
+    if (chunks < 0) return GBSSIM_ERR_INVALID_ARG;
     const int n = x->count;
+    if (chunks == 0) {  // streamed: every image resident at once, a flag per copy group (<= one per image)
+        if (!persistent_params(p) || p->scales < 1) return GBSSIM_ERR_UNSUPPORTED;
+        H->chunks = 0;
+        H->per = n;
+        H->esz = x->dtype == GBSSIM_U8 ? 1 : x->dtype == GBSSIM_F32 ? 4 : 2;
+        const size_t pitch = ((size_t)x->width * H->esz + 15) / 16 * 16;
+        H->pitch_elems = (int64_t)(pitch / H->esz);
+        H->plane_bytes = pitch * (size_t)x->height * (size_t)n;
+        H->stage_bytes = 2 * H->plane_bytes;
+        gbssim_plane c = *x;
+        c.row_stride = H->pitch_elems;
+        c.image_stride = H->pitch_elems * x->height;
+        int rc = plan_levels(&c, p, p->scales, &H->ms);
+        if (rc) return rc;
+        size_t off = 0;
+        H->stage_off[0] = H->stage_off[1] = off;
+        off = align_up(off + H->stage_bytes);
+        H->ws_off[0] = H->ws_off[1] = off;
+        off = align_up(off + H->ms.bytes);
+        H->flags_off = off;
+        off = align_up(off + sizeof(unsigned) * (size_t)n);
+        H->score_off = off;
+        off = align_up(off + sizeof(double) * (size_t)n);
+        H->bytes = off;
+        return GBSSIM_OK;
+    }
     H->chunks = chunks < n ? chunks : n;
     H->per = (n + H->chunks - 1) / H->chunks;
     H->chunks = (n + H->per - 1) / H->per;
@@ -587,6 +647,7 @@ int plan_host(const gbssim_plane *x, const gbssim_params *p, int32_t chunks, Hos
     off = align_up(off + H->ms.bytes);
     H->score_off = off;
     off = align_up(off + sizeof(double) * (size_t)n);
+    H->flags_off = 0;
     H->bytes = off;
     return GBSSIM_OK;
 }
@@ -1231,6 +1292,49 @@ int gbssim_msssim_host(const gbssim_plane *x, const gbssim_plane *y, const gbssi
     cudaEvent_t prior = ev[0], copied[2] = {ev[1], ev[2]}, consumed[2] = {ev[3], ev[4]}, done2 = ev[5];
     cudaError_t e = cudaEventRecord(prior, st);  // earlier calls on `stream` may still read the buffers
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, prior, 0);
+    if (H.chunks == 0) {
+        // streamed: clear the arrival flags (copy stream), launch the one
+        // MS-SSIM launch over all images (its level-0 items wait for their
+        // image's flag), then per image: copy x, y and set its flag with a
+        // stream memory write that orders the copies before it
+        auto write32 = stream_write_value32();
+        unsigned *flags = (unsigned *)(ws + H.flags_off);
+        const int group = (x->count + 15) / 16;  // images per copy group and arrival flag
+        char *xs = ws + H.stage_off[0], *ysg = xs + H.plane_bytes;
+        if (!write32) e = cudaErrorNotSupported;
+        // the copy stream must not wait for the launch (an implicitly
+        // synchronising stream would leave the level-0 items waiting)
+        unsigned cflags = 0;
+        if (e == cudaSuccess && (cudaStreamGetFlags(cs, &cflags) != cudaSuccess || !(cflags & cudaStreamNonBlocking)))
+            rc = GBSSIM_ERR_INVALID_ARG;
+        if (e == cudaSuccess && rc == GBSSIM_OK) e = cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)x->count, cs);
+        if (e == cudaSuccess && rc == GBSSIM_OK) e = cudaEventRecord(copied[0], cs);
+        if (e == cudaSuccess && rc == GBSSIM_OK) e = cudaStreamWaitEvent(st, copied[0], 0);
+        if (e == cudaSuccess && rc == GBSSIM_OK) {
+            gbssim_plane dx = *x, dy = *y;
+            dx.data = xs;
+            dy.data = ysg;
+            dx.row_stride = dy.row_stride = H.pitch_elems;
+            dx.image_stride = dy.image_stride = H.pitch_elems * x->height;
+            rc = msssim_forward(&dx, &dy, p, H.ms, ws + H.ws_off[0], score_dev, nullptr, st, flags, group);
+        }
+        // groups of images per copy and flag: 16 groups (fewer, larger copies)
+        const size_t img_bytes = (size_t)H.pitch_elems * H.esz * x->height;
+        for (int i0 = 0, f = 0; i0 < x->count && e == cudaSuccess && rc == GBSSIM_OK; i0 += group, ++f) {
+            const int m = x->count - i0 < group ? x->count - i0 : group;
+            e = copy_images_h2d(x, i0, m, H, xs + i0 * img_bytes, cs);
+            if (e == cudaSuccess) e = copy_images_h2d(y, i0, m, H, ysg + i0 * img_bytes, cs);
+            if (e == cudaSuccess && write32(cs, (CUdeviceptr)(flags + f), 1u, CU_STREAM_WRITE_VALUE_DEFAULT) !=
+                                        CUDA_SUCCESS)
+                e = cudaErrorUnknown;
+        }
+        if (e == cudaSuccess && rc == GBSSIM_OK)
+            e = cudaMemcpyAsync(score_host, score_dev, sizeof(double) * (size_t)x->count, cudaMemcpyDeviceToHost, st);
+        for (auto &f : ev) cudaEventDestroy(f);
+        if (rc != GBSSIM_OK) return rc;
+        if (e == cudaErrorNotSupported) return GBSSIM_ERR_UNSUPPORTED;
+        return e == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
+    }
     if (e == cudaSuccess && stream2) e = cudaStreamWaitEvent(cst[1], prior, 0);
     for (int c = 0; c < H.chunks && e == cudaSuccess && rc == GBSSIM_OK; ++c) {
         const int s = c & 1, i0 = c * H.per, m = x->count - i0 < H.per ? x->count - i0 : H.per;

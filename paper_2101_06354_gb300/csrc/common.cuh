@@ -209,6 +209,8 @@ struct UniformBatch {
     void *ws;
     int64_t counter_off, done_off, status_off;
     unsigned wait_limit;
+    const unsigned *arrive;  // nullable: level-0 items of image i wait (bounded) until arrive[i / arrive_group] != 0
+    int arrive_group;        // images per arrival flag (>= 1)
 };
 cudaError_t launch_uniform(const UniformBatch &U, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st);
 int gauss11_batch_max_ctas_per_sm();

@@ -697,6 +697,7 @@ struct Resolved {
     int done_index;   // completion counter this item bumps
     int dep_index;    // counter it waits on (-1: none)
     unsigned dep_target;
+    const unsigned *arrive;  // nullable: flag its input's arrival sets (non-zero)
 };
 
 // Ragged batches: per-(image, level) records and a per-item list built by
@@ -732,6 +733,7 @@ struct TableSource {
             R.xb = ws + lv.x_off;
             R.yb = ws + lv.x_off + sizeof(float) * lv.H * lv.W;
         }
+        R.arrive = nullptr;
         R.done_index = bi.level_index;
         R.dep_index = lv.level > 0 ? bi.level_index - 1 : -1;
         R.dep_target = lv.level > 0 ? (unsigned)B.levels[bi.level_index - 1].wait_target : 0u;
@@ -747,9 +749,10 @@ struct UniformSource {
     __device__ void resolve(int item, char *ws, Resolved &R) const {
         int j = 0;
         while (j + 1 < U.scales && item >= U.lv[j + 1].item_begin) ++j;
+        const int local = item - (int)U.lv[j].item_begin;
+        const int img = local / U.lv[j].items_per_image;
+        const int rem = local - img * U.lv[j].items_per_image;
         const UniformLevel &lv = U.lv[j];
-        const int local = item - (int)lv.item_begin;
-        const int img = local / lv.items_per_image, rem = local - img * lv.items_per_image;
         const int seg = rem / lv.strips, strip = rem - seg * lv.strips;
         Item &it = R.it;
         it.H = lv.H;
@@ -783,6 +786,7 @@ struct UniformSource {
             R.xb = reinterpret_cast<const float *>(ws + lv.x_off) + img * plane;
             R.yb = reinterpret_cast<const float *>(ws + lv.x_off) + (U.count + img) * plane;
         }
+        R.arrive = (j == 0 && U.arrive) ? U.arrive + img / U.arrive_group : nullptr;
         R.done_index = img * U.scales + j;
         R.dep_index = j > 0 ? img * U.scales + j - 1 : -1;
         R.dep_target = j > 0 ? (unsigned)U.lv[j - 1].items_per_image : 0u;
@@ -837,6 +841,18 @@ __global__ void __launch_bounds__(NT, 3)
                         __nanosleep(256);
                     }
                 }
+                if (R.arrive) {  // the image's bytes are still being copied in (bounded: 16x the level limit)
+                    unsigned long long spins = 0;
+                    while (ld_acquire(R.arrive) == 0u) {
+                        if (++spins > 16ull * wait_limit) {
+                            atomicExch(status, (int)GBSSIM_ERR_TIMEOUT);
+                            late = 1;
+                            break;
+                        }
+                        __nanosleep(256);
+                    }
+                    if (BULK) fence_proxy_async_global();  // before this CTA's bulk copies of those bytes
+                }
             }
             s_item = item;
             s_late = late;
@@ -852,7 +868,7 @@ __global__ void __launch_bounds__(NT, 3)
         R.it.tmy = BULK ? &tmy : nullptr;
         R.it.tz = R.img;
         if (R.pyramid) gauss11_item<float, false, 1, false>(S, R.it, taps, taps2, cc, co, phase, tma_ok);
-        else gauss11_item<T, false, 0, BULK>(S, R.it, taps, taps2, cc, co, phase, tma_ok);
+        else gauss11_item<T, false, BULK ? 1 : 0, BULK>(S, R.it, taps, taps2, cc, co, phase, tma_ok);
         __syncthreads();  // every thread's partial and pyramid stores issued
         if (threadIdx.x == 0) {
             if (s_late) *R.it.partial = make_double2(nan(""), nan(""));  // the score reads NaN
@@ -1112,6 +1128,10 @@ cudaError_t launch_uniform_t(const UniformBatch &U, const Taps<11> &taps, SsimCo
     CUtensorMap mx, my;
     const bool bulk = encode_plane_map<T>(&mx, U.x, U.lv[0].H, U.lv[0].W, U.rs, U.image_stride, U.count) &&
                       encode_plane_map<T>(&my, U.y, U.lv[0].H, U.lv[0].W, U.rs, U.image_stride, U.count);
+    // Arrival flags need the bulk-copy path: the register path's first rows
+    // go through the read-only data cache, which bytes copied in during the
+    // launch must not.
+    if (U.arrive && !bulk) return cudaErrorNotSupported;
     return launch_persistent_t<T>(src, U.ws, U.counter_off, U.done_off, U.status_off, U.wait_limit, taps, cc, grid,
                                   st, bulk ? &mx : nullptr, bulk ? &my : nullptr);
 }

@@ -54,6 +54,9 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// Global-memory writes this thread has observed (an acquired flag) are
+// ordered before its later bulk copies that read them.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no
 // link-time dependency on the driver library); nullptr if unavailable.

@@ -304,9 +304,11 @@ def msssim_host(x: torch.Tensor, y: torch.Tensor, chunks: int = 4, ws: torch.Ten
                 **kw) -> torch.Tensor:
     """MS-SSIM of pairs held in host memory (gbssim_msssim_host): chunks of
     the batch are copied on a side stream while the previous chunk is scored
-    on the current stream.  Returns a pinned CPU float64 tensor of length N,
-    valid at return when sync=True (else once the current stream completes).
-    x and y should be pinned for the copies to overlap."""
+    on the current stream; chunks=0 streams instead (one launch over all
+    pairs, each pair scored as soon as its copy lands).  Returns a pinned CPU
+    float64 tensor of length N, valid at return when sync=True (else once the
+    current stream completes).  x and y should be pinned for the copies to
+    overlap."""
     if x.device.type != "cpu" or y.device.type != "cpu":
         raise ValueError("msssim_host takes host tensors")
     if y.dtype != x.dtype or y.shape != x.shape:

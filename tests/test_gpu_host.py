@@ -33,7 +33,7 @@ def synth():
 
 
 @pytest.mark.parametrize("n,h,w,chunks", [(7, 200, 232, 3), (5, 181, 203, 1), (6, 256, 320, 6), (1, 200, 240, 4),
-                                          (9, 184, 200, 8)])
+                                          (9, 184, 200, 8), (7, 200, 232, 0), (5, 181, 203, 0), (1, 200, 240, 0)])
 def test_host_pipeline_equals_device_call(g, synth, n, h, w, chunks):
     x, y = synth.luma_pairs_u8(n, h, w)
     ref = g.msssim(x.to(DEV), y.to(DEV)).cpu()
@@ -51,6 +51,7 @@ def test_host_pipeline_strided_and_pageable(g, synth):
     xs, ys = x[:, :, 8:232], y[:, :, 8:232]  # row pitch 240 > width 224: per-image 2-D copies
     ref = g.msssim(xs.contiguous().to(DEV), ys.contiguous().to(DEV)).cpu()
     assert torch.equal(g.msssim_host(xs, ys, chunks=2), ref)  # pageable memory: correct, not overlapped
+    assert torch.equal(g.msssim_host(xs, ys, chunks=0), ref)  # streamed, pageable
     # the public call routes host tensors through the pipeline
     assert torch.equal(g.msssim(xs.contiguous().pin_memory(), ys.contiguous().pin_memory()), ref)
 
@@ -61,6 +62,7 @@ def test_host_pipeline_float_and_scales(g, synth):
     kw = dict(L=1.0, scales=3, exponents=(0.3, 0.3, 0.4))
     ref = g.msssim(xs.to(DEV), ys.to(DEV), **kw).cpu()
     assert torch.equal(g.msssim_host(xs.pin_memory(), ys.pin_memory(), chunks=3, **kw), ref)
+    assert torch.equal(g.msssim_host(xs.pin_memory(), ys.pin_memory(), chunks=0, **kw), ref)
 
 
 def test_host_pipeline_rejects_one_stream(g, synth):
@@ -82,3 +84,24 @@ def test_host_pipeline_rejects_one_stream(g, synth):
     rc = g.lib.gbssim_msssim_host(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p), 2, out.data_ptr(),
                                   ws.data_ptr(), nb.value - 1, st, cs, None)
     assert rc == g.ERR_WORKSPACE
+
+
+def test_streamed_mode_checks(g, synth):
+    """Streamed mode (chunks = 0) needs the persistent path's parameters and a
+    copy stream that never synchronises with the compute stream."""
+    x, y = synth.luma_pairs_u8(2, 64, 64)
+    px, py = g.plane(x), g.plane(y)
+    p = g.make_params(exponents=g.MSSSIM_EXPONENTS[:2], scales=2)
+    nb = ctypes.c_size_t()
+    assert g.lib.gbssim_msssim_host_workspace_size(ctypes.byref(px), ctypes.byref(p), 0, ctypes.byref(nb)) == 0
+    p7 = g.make_params(k=7, sigma=1.0, exponents=g.MSSSIM_EXPONENTS[:2], scales=2)
+    assert g.lib.gbssim_msssim_host_workspace_size(ctypes.byref(px), ctypes.byref(p7), 0,
+                                                   ctypes.byref(ctypes.c_size_t())) == g.ERR_UNSUPPORTED
+    ws = torch.empty(nb.value, dtype=torch.uint8, device=DEV)
+    out = torch.empty(2, dtype=torch.float64).pin_memory()
+    st = g._copy_stream(torch.device(DEV), 1).cuda_stream  # a non-blocking compute stream
+    # the legacy default stream as copy stream synchronises with every blocking stream: refused
+    rc = g.lib.gbssim_msssim_host(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p), 0, out.data_ptr(),
+                                  ws.data_ptr(), ws.numel(), st, None, None)
+    assert rc == g.ERR_INVALID_ARG
+    torch.cuda.synchronize()
