@@ -368,7 +368,13 @@ int gbssim_msssim(const gbssim_plane *x, const gbssim_plane *y, const gbssim_par
  *                  consecutive images and after each group sets that group's
  *                  arrival flag with a stream memory write; the level-0 work
  *                  of an image waits (bounded) for its group's flag, so
- *                  scoring starts as soon as the first group is in.  Streamed
+ *                  scoring starts as soon as the first group is in.  Work
+ *                  items run as a wavefront over the groups (level j of group
+ *                  g beside level 0 of group g + j), and the two largest
+ *                  levels use shorter items than gbssim_msssim's, so the
+ *                  scores agree with it to rounding (another fp32 summation
+ *                  order), not bit for bit; chunked mode is bit-identical.
+ *                  A wait that gives up yields NaN scores.  Streamed
  *                  mode needs the Gaussian 11-tap window at stride 1 without
  *                  the 9/7 pyramid or border flags (else
  *                  GBSSIM_ERR_UNSUPPORTED) and a copy_stream created with

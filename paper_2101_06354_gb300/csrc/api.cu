@@ -136,9 +136,13 @@ int level_items(Path path, int64_t H, int64_t W, int count, const gbssim_params 
 // Level 0 takes long items (the ragged-batch autotuner's choice on 1080p /
 // 4K batches); the small upper levels take short ones, which shortens the
 // chain of dependent items of the last images at the end of the launch.
-int persistent_seg_rows(int j) {
-    static const int rows[5] = {512, 256, 128, 64, 32};
-    return j < 5 ? rows[j] : rows[4];
+// Streamed launches (inputs still arriving) take short items at the two
+// large levels too: the chain after the last copy lands is the step's tail,
+// while the extra halo rows cost time the copies leave idle.
+int persistent_seg_rows(int j, bool streamed) {
+    static const int rows[5] = {512, 256, 128, 64, 32}, streamed_rows[5] = {128, 128, 64, 32, 32};
+    const int *r = streamed ? streamed_rows : rows;
+    return j < 5 ? r[j] : r[4];
 }
 
 struct Level {
@@ -158,7 +162,7 @@ struct MsPlan {
 };
 
 int plan_levels(const gbssim_plane *x, const gbssim_params *p, int scales, MsPlan *P,
-                bool float_path = false) {
+                bool float_path = false, bool streamed = false) {
     size_t off = 0;
     int64_t H = x->height, W = x->width;
     const int border = border_mode(p);
@@ -188,7 +192,7 @@ int plan_levels(const gbssim_plane *x, const gbssim_params *p, int scales, MsPla
         L.pitems = 0;
         if (L.path == PATH_GAUSS11 && !border) {
             int strips, segs;
-            L.pseg_rows = persistent_seg_rows(j);
+            L.pseg_rows = persistent_seg_rows(j, streamed);
             L.pitems = gauss11_items(H, W, L.pseg_rows, &strips, &segs);
         }
         L.part_off = off;  // pooling slots for whichever layout runs
@@ -388,9 +392,27 @@ int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_pa
         U.done_off = (int64_t)P.done_off;
         U.status_off = (int64_t)P.status_off;
         U.wait_limit = 1u << 22;
+        if (begin > 0x7fffffff) return GBSSIM_ERR_UNSUPPORTED;
         U.arrive = arrive;
         U.arrive_group = arrive_group > 0 ? arrive_group : 1;
-        if (begin > 0x7fffffff) return GBSSIM_ERR_UNSUPPORTED;
+        if (arrive) {
+            // wavefront over copy groups: wave w runs level 0 of group w while
+            // the upper levels of earlier groups fill the wait for copies
+            const int gs = U.arrive_group, G = (n + gs - 1) / gs;
+            if (G > kUniformMaxGroups) return GBSSIM_ERR_INVALID_ARG;
+            U.groups = G;
+            U.waves = G + S - 1;
+            U.wave_begin[0] = 0;
+            int64_t at = 0;
+            for (int w = 0; w < U.waves; ++w) {
+                for (int j = w - G + 1 > 0 ? w - G + 1 : 0; j <= w && j < S; ++j) {
+                    const int g = w - j, m = n - g * gs < gs ? n - g * gs : gs;
+                    at += (int64_t)m * U.lv[j].items_per_image;
+                }
+                U.wave_begin[w + 1] = (int)at;
+            }
+            if (at != begin) return GBSSIM_ERR_INVALID_ARG;  // the waves cover every item once
+        }
         if (cudaMemsetAsync(ws + P.counter_off, 0, P.zero_bytes, st) != cudaSuccess) return GBSSIM_ERR_CUDA;
         Taps<11> taps;
         make_taps(p, taps.g);
@@ -607,7 +629,7 @@ int plan_host(const gbssim_plane *x, const gbssim_params *p, int32_t chunks, Hos
         gbssim_plane c = *x;
         c.row_stride = H->pitch_elems;
         c.image_stride = H->pitch_elems * x->height;
-        int rc = plan_levels(&c, p, p->scales, &H->ms);
+        int rc = plan_levels(&c, p, p->scales, &H->ms, false, true);
         if (rc) return rc;
         size_t off = 0;
         H->stage_off[0] = H->stage_off[1] = off;
@@ -1299,7 +1321,7 @@ int gbssim_msssim_host(const gbssim_plane *x, const gbssim_plane *y, const gbssi
         // stream memory write that orders the copies before it
         auto write32 = stream_write_value32();
         unsigned *flags = (unsigned *)(ws + H.flags_off);
-        const int group = (x->count + 15) / 16;  // images per copy group and arrival flag
+        const int group = (x->count + kUniformMaxGroups - 1) / kUniformMaxGroups;  // images per copy group and flag
         char *xs = ws + H.stage_off[0], *ysg = xs + H.plane_bytes;
         if (!write32) e = cudaErrorNotSupported;
         // the copy stream must not wait for the launch (an implicitly
@@ -1318,7 +1340,7 @@ int gbssim_msssim_host(const gbssim_plane *x, const gbssim_plane *y, const gbssi
             dx.image_stride = dy.image_stride = H.pitch_elems * x->height;
             rc = msssim_forward(&dx, &dy, p, H.ms, ws + H.ws_off[0], score_dev, nullptr, st, flags, group);
         }
-        // groups of images per copy and flag: 16 groups (fewer, larger copies)
+        // groups of images per copy and flag: at most 16 groups (fewer, larger copies)
         const size_t img_bytes = (size_t)H.pitch_elems * H.esz * x->height;
         for (int i0 = 0, f = 0; i0 < x->count && e == cudaSuccess && rc == GBSSIM_OK; i0 += group, ++f) {
             const int m = x->count - i0 < group ? x->count - i0 : group;

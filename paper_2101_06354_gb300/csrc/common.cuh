@@ -200,6 +200,8 @@ struct UniformLevel {
     int64_t x_off;        // levels >= 1: x planes of all images, then y planes
     int64_t part_off;     // pooling slots: image-major, items_per_image each
 };
+constexpr int kUniformMaxGroups = 16;  // arrival flags (copy groups) of the streamed host mode
+constexpr int kUniformMaxWaves = kUniformMaxGroups + GBSSIM_MAX_SCALES - 1;
 struct UniformBatch {
     const void *x, *y;
     int64_t rs, image_stride;  // level 0, in elements
@@ -211,6 +213,11 @@ struct UniformBatch {
     unsigned wait_limit;
     const unsigned *arrive;  // nullable: level-0 items of image i wait (bounded) until arrive[i / arrive_group] != 0
     int arrive_group;        // images per arrival flag (>= 1)
+    // waves > 0 (with arrive): items in copy-group wavefront order, wave w
+    // holding level j of group w - j for every level (groups of arrive_group
+    // images); wave_begin[w] is its first item.  waves == 0: level-major.
+    int waves, groups;
+    int wave_begin[kUniformMaxWaves + 1];
 };
 cudaError_t launch_uniform(const UniformBatch &U, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st);
 int gauss11_batch_max_ctas_per_sm();

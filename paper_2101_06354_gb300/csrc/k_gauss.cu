@@ -741,17 +741,37 @@ struct TableSource {
 };
 
 // Batches of equally sized images (gbssim_msssim): the item list is
-// arithmetic (level-major, then image, segment, strip), so no table exists;
+// arithmetic (level-major, then image, segment, strip; or, with arrival
+// flags, the copy-group wavefront of UniformBatch::waves), so no table exists;
 // the pyramid and pooling slots use gbssim_msssim's workspace layout.
 struct UniformSource {
     UniformBatch U;
     __device__ int total() const { return (int)U.total_items; }
     __device__ void resolve(int item, char *ws, Resolved &R) const {
-        int j = 0;
-        while (j + 1 < U.scales && item >= U.lv[j + 1].item_begin) ++j;
-        const int local = item - (int)U.lv[j].item_begin;
-        const int img = local / U.lv[j].items_per_image;
-        const int rem = local - img * U.lv[j].items_per_image;
+        int j = 0, img, rem;
+        if (U.waves > 0) {
+            // wave w: level j of copy group w - j, levels in order; a level's
+            // dependency (the level below, same group) is one wave earlier
+            int w = 0;
+            while (w + 1 < U.waves && item >= U.wave_begin[w + 1]) ++w;
+            int r = item - U.wave_begin[w];
+            j = w - U.groups + 1 > 0 ? w - U.groups + 1 : 0;
+            int g = w - j, m;
+            for (;; ++j, --g) {
+                m = min(U.arrive_group, U.count - g * U.arrive_group);
+                const int c = m * U.lv[j].items_per_image;
+                if (r < c || j + 1 >= U.scales || g == 0) break;
+                r -= c;
+            }
+            const int k = r / U.lv[j].items_per_image;
+            img = g * U.arrive_group + k;
+            rem = r - k * U.lv[j].items_per_image;
+        } else {
+            while (j + 1 < U.scales && item >= U.lv[j + 1].item_begin) ++j;
+            const int local = item - (int)U.lv[j].item_begin;
+            img = local / U.lv[j].items_per_image;
+            rem = local - img * U.lv[j].items_per_image;
+        }
         const UniformLevel &lv = U.lv[j];
         const int seg = rem / lv.strips, strip = rem - seg * lv.strips;
         Item &it = R.it;

@@ -305,7 +305,8 @@ def msssim_host(x: torch.Tensor, y: torch.Tensor, chunks: int = 4, ws: torch.Ten
     """MS-SSIM of pairs held in host memory (gbssim_msssim_host): chunks of
     the batch are copied on a side stream while the previous chunk is scored
     on the current stream; chunks=0 streams instead (one launch over all
-    pairs, each pair scored as soon as its copy lands).  Returns a pinned CPU
+    pairs, each group of pairs scored as soon as its copy lands; equal to the
+    device call up to fp32 summation order).  Returns a pinned CPU
     float64 tensor of length N, valid at return when sync=True (else once the
     current stream completes).  x and y should be pinned for the copies to
     overlap."""
