@@ -1315,10 +1315,13 @@ int gbssim_msssim_host(const gbssim_plane *x, const gbssim_plane *y, const gbssi
     cudaError_t e = cudaEventRecord(prior, st);  // earlier calls on `stream` may still read the buffers
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, prior, 0);
     if (H.chunks == 0) {
-        // streamed: clear the arrival flags (copy stream), launch the one
+        // streamed: on the copy stream, clear the arrival flags, then per
+        // group of images copy x, y and set the group's flag with a stream
+        // memory write that orders the copies before it; then the one
         // MS-SSIM launch over all images (its level-0 items wait for their
-        // image's flag), then per image: copy x, y and set its flag with a
-        // stream memory write that orders the copies before it
+        // group's flag).  Every copy is enqueued before the launch, so the
+        // launch depends on no host call after it (a serialised or blocking
+        // launch still finds its inputs arriving).
         auto write32 = stream_write_value32();
         unsigned *flags = (unsigned *)(ws + H.flags_off);
         const int group = (x->count + kUniformMaxGroups - 1) / kUniformMaxGroups;  // images per copy group and flag
@@ -1331,15 +1334,6 @@ int gbssim_msssim_host(const gbssim_plane *x, const gbssim_plane *y, const gbssi
             rc = GBSSIM_ERR_INVALID_ARG;
         if (e == cudaSuccess && rc == GBSSIM_OK) e = cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)x->count, cs);
         if (e == cudaSuccess && rc == GBSSIM_OK) e = cudaEventRecord(copied[0], cs);
-        if (e == cudaSuccess && rc == GBSSIM_OK) e = cudaStreamWaitEvent(st, copied[0], 0);
-        if (e == cudaSuccess && rc == GBSSIM_OK) {
-            gbssim_plane dx = *x, dy = *y;
-            dx.data = xs;
-            dy.data = ysg;
-            dx.row_stride = dy.row_stride = H.pitch_elems;
-            dx.image_stride = dy.image_stride = H.pitch_elems * x->height;
-            rc = msssim_forward(&dx, &dy, p, H.ms, ws + H.ws_off[0], score_dev, nullptr, st, flags, group);
-        }
         // groups of images per copy and flag: at most 16 groups (fewer, larger copies)
         const size_t img_bytes = (size_t)H.pitch_elems * H.esz * x->height;
         for (int i0 = 0, f = 0; i0 < x->count && e == cudaSuccess && rc == GBSSIM_OK; i0 += group, ++f) {
@@ -1349,6 +1343,15 @@ int gbssim_msssim_host(const gbssim_plane *x, const gbssim_plane *y, const gbssi
             if (e == cudaSuccess && write32(cs, (CUdeviceptr)(flags + f), 1u, CU_STREAM_WRITE_VALUE_DEFAULT) !=
                                         CUDA_SUCCESS)
                 e = cudaErrorUnknown;
+        }
+        if (e == cudaSuccess && rc == GBSSIM_OK) e = cudaStreamWaitEvent(st, copied[0], 0);  // flags cleared
+        if (e == cudaSuccess && rc == GBSSIM_OK) {
+            gbssim_plane dx = *x, dy = *y;
+            dx.data = xs;
+            dy.data = ysg;
+            dx.row_stride = dy.row_stride = H.pitch_elems;
+            dx.image_stride = dy.image_stride = H.pitch_elems * x->height;
+            rc = msssim_forward(&dx, &dy, p, H.ms, ws + H.ws_off[0], score_dev, nullptr, st, flags, group);
         }
         if (e == cudaSuccess && rc == GBSSIM_OK)
             e = cudaMemcpyAsync(score_host, score_dev, sizeof(double) * (size_t)x->count, cudaMemcpyDeviceToHost, st);

@@ -849,11 +849,15 @@ __global__ void __launch_bounds__(NT, 3)
             if (item >= 0) {
                 Resolved R;
                 src.resolve(item, ws, R);
+                // Once any wait of the launch has given up (status set), the
+                // others give up at their next check, so a stalled launch
+                // ends after one wait limit, not one per item.
+                const volatile int *st_word = status;
                 if (R.dep_index >= 0) {
                     const unsigned *flag = done + R.dep_index;
                     unsigned spins = 0;
                     while (ld_acquire(flag) < R.dep_target) {
-                        if (++spins > wait_limit) {
+                        if (++spins > wait_limit || ((spins & 63u) == 0 && *st_word != 0)) {
                             atomicExch(status, (int)GBSSIM_ERR_TIMEOUT);
                             late = 1;
                             break;
@@ -864,7 +868,7 @@ __global__ void __launch_bounds__(NT, 3)
                 if (R.arrive) {  // the image's bytes are still being copied in (bounded: 16x the level limit)
                     unsigned long long spins = 0;
                     while (ld_acquire(R.arrive) == 0u) {
-                        if (++spins > 16ull * wait_limit) {
+                        if (++spins > 16ull * wait_limit || ((spins & 63u) == 0 && *st_word != 0)) {
                             atomicExch(status, (int)GBSSIM_ERR_TIMEOUT);
                             late = 1;
                             break;

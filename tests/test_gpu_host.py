@@ -5,6 +5,9 @@ chunking must not change a single bit of it.  Streamed mode (chunks = 0)
 cuts the two largest levels into shorter work items (another fp32 summation
 order), so it is held to the oracle at the pooled parity bound instead."""
 import ctypes
+import os
+import subprocess
+import sys
 
 import pytest
 import torch
@@ -62,6 +65,28 @@ def test_streamed_matches_oracle(g, synth, n, h, w):
         assert abs(got[i].item() - s) <= 1e-6
     # a second call on the same buffers (flags cleared per call)
     assert torch.equal(g.msssim_host(x.pin_memory(), y.pin_memory(), chunks=0), got)
+
+
+_BLOCKING_SCRIPT = """
+import torch
+from paper_2101_06354_gb300 import gbssim, synth
+x, y = synth.luma_pairs_u8(20, 176, 176)
+dev = gbssim.msssim(x.cuda(), y.cuda()).cpu()
+got = gbssim.msssim_host(x.pin_memory(), y.pin_memory(), chunks=0)
+assert torch.isfinite(got).all(), got
+assert torch.allclose(got, dev, rtol=0, atol=1e-6), (got - dev).abs().max()
+print("streamed ok")
+"""
+
+
+def test_streamed_with_blocking_launches(g):
+    """With every kernel launch blocking the host, the streamed launch must
+    still find its inputs arriving: all copies are enqueued before it."""
+    env = dict(os.environ, CUDA_LAUNCH_BLOCKING="1")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _BLOCKING_SCRIPT], env=env, cwd=root, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0 and "streamed ok" in r.stdout, r.stdout + r.stderr
 
 
 def test_host_pipeline_strided_and_pageable(g, synth):
