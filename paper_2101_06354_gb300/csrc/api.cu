@@ -600,17 +600,15 @@ bool persistent_params(const gbssim_params *p) {
 // cuStreamWriteValue32 through the runtime's driver entry point (nullptr if
 // unavailable): the copy stream's arrival flags for the streamed mode.
 PFN_cuStreamWriteValue32_v11070 stream_write_value32() {
-    static PFN_cuStreamWriteValue32_v11070 fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
+    static const PFN_cuStreamWriteValue32_v11070 fn = [] {  // looked up once (thread-safe static)
         void *q = nullptr;
         cudaDriverEntryPointQueryResult r;
         if (cudaGetDriverEntryPointByVersion("cuStreamWriteValue32", &q, 12000, cudaEnableDefault, &r) ==
                 cudaSuccess &&
             r == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuStreamWriteValue32_v11070>(q);
-    }
+            return reinterpret_cast<PFN_cuStreamWriteValue32_v11070>(q);
+        return (PFN_cuStreamWriteValue32_v11070) nullptr;
+    }();
     return fn;
 }
 

@@ -7,9 +7,21 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/gbssim.h"
 
 namespace gbssim {
+
+// Per-device once-flags of the launchers (a kernel's shared-memory attribute
+// set, a device figure cached).  Callers may launch from several host
+// threads: a flag read as set (acquire) implies the work before its set
+// (release); two threads may both do the (idempotent) work.
+struct DeviceOnce {
+    std::atomic<bool> done[64];
+    bool is_set(int dev) const { return done[dev].load(std::memory_order_acquire); }
+    void set(int dev) { done[dev].store(true, std::memory_order_release); }
+};
 
 // ---------------------------------------------------------------- element loads
 

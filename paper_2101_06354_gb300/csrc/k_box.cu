@@ -24,17 +24,15 @@
 namespace gbssim {
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {  // looked up once (thread-safe static)
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
+            return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+    }();
     return fn;
 }
 
@@ -731,14 +729,14 @@ int box_items_ks(int64_t OH, int64_t OW, int k, int s) {
 template <int M>
 cudaError_t launch_s4c(const BoxLaunch &L, int tx, int ty, unsigned ctas, cudaStream_t st) {
     constexpr size_t smem = s4c_smem<S4C_VB, S4C_STAGES>();
-    static bool attr_set[64] = {};
+    static DeviceOnce attr_set;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!attr_set[dev]) {
+    if (!attr_set.is_set(dev)) {
         const cudaError_t e = cudaFuncSetAttribute(box_s4c_kernel<M, S4C_VB, S4C_STAGES>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set[dev] = true;
+        attr_set.set(dev);
     }
     box_s4c_kernel<M, S4C_VB, S4C_STAGES><<<ctas, NT, smem, st>>>(L, tx, ty, kS4cSeg);
     return cudaGetLastError();
@@ -755,14 +753,14 @@ cudaError_t launch_box_u8(const BoxLaunch &L, cudaStream_t st) {
         CUtensorMap mx, my;
         // the item count was fixed for this layout: no silent fallback
         if (!encode_u8_map(&mx, L.x, L.count) || !encode_u8_map(&my, L.y, L.count)) return cudaErrorInvalidValue;
-        static bool attr_set[64] = {};
+        static DeviceOnce attr_set;
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-        if (!attr_set[dev]) {
+        if (!attr_set.is_set(dev)) {
             cudaError_t e = cudaFuncSetAttribute(box_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)sizeof(TmaSmem));
             if (e != cudaSuccess) return e;
-            attr_set[dev] = true;
+            attr_set.set(dev);
         }
         int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -785,15 +783,15 @@ cudaError_t launch_box_u8(const BoxLaunch &L, cudaStream_t st) {
                              (L.y.image_stride % 4 == 0);
         box_block_kernel<<<grid, NT, 0, st>>>(L, tx, ty, aligned4);
     } else {
-        static bool attr_set[64] = {};
+        static DeviceOnce attr_set;
         const size_t smem = sizeof(SatSmem);
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-        if (!attr_set[dev]) {
+        if (!attr_set.is_set(dev)) {
             cudaError_t e = cudaFuncSetAttribute(box_sat_kernel,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            attr_set[dev] = true;
+            attr_set.set(dev);
         }
         box_sat_kernel<<<grid, NT, smem, st>>>(L, tx, ty);
     }

@@ -357,17 +357,17 @@ __global__ void __launch_bounds__(NT, 3)
 
 template <typename T, typename G>
 cudaError_t launch_grad11(const GradLaunch &L, cudaStream_t st) {
-    static bool attr_set[64] = {};
+    static DeviceOnce attr_set;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!attr_set[dev]) {
+    if (!attr_set.is_set(dev)) {
         cudaError_t e = cudaFuncSetAttribute(grad11_kernel<T, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sizeof(Grad11Smem));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(grad11_kernel<T, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sizeof(Grad11Smem));
         if (e != cudaSuccess) return e;
-        attr_set[dev] = true;
+        attr_set.set(dev);
     }
     // the three coefficient planes of every image as one 3-D tensor
     // (columns, rows, image * 3 + map); 80 x 26 and 80 x 16 float tiles
@@ -405,14 +405,14 @@ cudaError_t launch_grad_tg(const GradLaunch &L, cudaStream_t st) {
     if (L.k == K11) return launch_grad11<T, G>(L, st);
     const int hk = L.k - 1;
     const size_t smem = sizeof(float) * (3 * (TH + hk) * (TW + hk) + 3 * (TH + hk) * TW);
-    static bool attr_set[64] = {};
+    static DeviceOnce attr_set;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!attr_set[dev]) {
+    if (!attr_set.is_set(dev)) {
         cudaError_t e = cudaFuncSetAttribute(grad_kernel<T, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              200 * 1024);
         if (e != cudaSuccess) return e;
-        attr_set[dev] = true;
+        attr_set.set(dev);
     }
     dim3 grid((unsigned)((L.x.W + TW - 1) / TW), (unsigned)((L.x.H + TH - 1) / TH), L.count);
     grad_kernel<T, G><<<grid, NT, smem, st>>>(L);

@@ -1014,15 +1014,15 @@ bool encode_plane_map(CUtensorMap *m, const void *data, int64_t H, int64_t W, in
 
 template <typename T, bool COEF>
 cudaError_t launch_gauss11_t(const GaussLaunch &L, cudaStream_t st) {
-    static bool attr_set[64] = {};
+    static DeviceOnce attr_set;
     const size_t smem = sizeof(Smem);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!attr_set[dev]) {
+    if (!attr_set.is_set(dev)) {
         cudaError_t e = cudaFuncSetAttribute(gauss11_kernel<T, COEF>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set[dev] = true;
+        attr_set.set(dev);
     }
     int strips, segs;
     gauss11_items(L.x.H, L.x.W, L.seg_rows, &strips, &segs);
@@ -1078,10 +1078,10 @@ cudaError_t launch_persistent_t(const Src &src, void *ws, int64_t counter_off, i
                                 unsigned wait_limit, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st,
                                 const CUtensorMap *mx = nullptr, const CUtensorMap *my = nullptr) {
     constexpr bool can_bulk = std::is_same<Src, UniformSource>::value;
-    static bool attr_set[64] = {};
+    static DeviceOnce attr_set;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!attr_set[dev]) {
+    if (!attr_set.is_set(dev)) {
         cudaError_t e = cudaFuncSetAttribute(gauss11_persistent_kernel<T, Src, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemNoBulk);
         if constexpr (can_bulk)
@@ -1089,7 +1089,7 @@ cudaError_t launch_persistent_t(const Src &src, void *ws, int64_t counter_off, i
                 e = cudaFuncSetAttribute(gauss11_persistent_kernel<T, Src, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
         if (e != cudaSuccess) return e;
-        attr_set[dev] = true;
+        attr_set.set(dev);
     }
     Taps2<11> t2;
     for (int n = 0; n < 11; ++n) t2.g2[n] = make_float2(taps.g[n], taps.g[n]);

@@ -159,14 +159,14 @@ size_t series_pool_smem(int n) {
 cudaError_t launch_series_pool(const double *scores, int n, int count, int64_t stride, int kind, double a0,
                                double a1, double *out, cudaStream_t st) {
     const size_t smem = series_pool_smem(n);
-    static bool attr_set[64] = {};
+    static DeviceOnce attr_set;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!attr_set[dev]) {
+    if (!attr_set.is_set(dev)) {
         const cudaError_t e = cudaFuncSetAttribute(series_pool_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)series_pool_smem(kVideoMaxFrames));
         if (e != cudaSuccess) return e;
-        attr_set[dev] = true;
+        attr_set.set(dev);
     }
     series_pool_kernel<<<count, ST, smem, st>>>(scores, n, stride, kind, a0, a1, out);
     return cudaGetLastError();

@@ -548,20 +548,20 @@ template <typename A, typename In, bool BULK>
 cudaError_t launch_level_k(const Ssim3dLaunch &L, const CUtensorMap &mx, const CUtensorMap &my, cudaStream_t st) {
     int tx, ty;
     ssim3d_tiles(L.x.H, L.x.W, L.k, sizeof(A) == 8, &tx, &ty);
-    static bool attr_set[64] = {};
-    static int slots[64] = {};
+    static DeviceOnce attr_set;
+    static std::atomic<int> slots[64];  // SMs per device
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     const size_t smem = smem_bytes<A>(L.k, BULK);
-    if (!attr_set[dev]) {
+    if (!attr_set.is_set(dev)) {
         const cudaError_t e = cudaFuncSetAttribute(ssim3d_kernel<A, In, BULK>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)smem_bytes<A>(kSsim3dMaxK, BULK));
         if (e != cudaSuccess) return e;
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return cudaErrorUnknown;
-        slots[dev] = sms;
-        attr_set[dev] = true;
+        slots[dev].store(sms, std::memory_order_relaxed);
+        attr_set.set(dev);
     }
     int per_sm = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ssim3d_kernel<A, In, BULK>, NT, smem) != cudaSuccess)
@@ -572,7 +572,7 @@ cudaError_t launch_level_k(const Ssim3dLaunch &L, const CUtensorMap &mx, const C
     // computed by one CTA with exact integer sums: the result does not depend
     // on the split.
     const int tiles = tx * ty, frames = L.T - L.kt + 1;
-    const int wave = max(1, per_sm) * slots[dev];
+    const int wave = max(1, per_sm) * slots[dev].load(std::memory_order_relaxed);
     int chunks = 1;
     if (tiles < 2 * wave) {
         const int want = (2 * wave + tiles - 1) / tiles;

@@ -243,3 +243,37 @@ def test_border_modes_on_host(g):
     assert _ws(g, x, both, g.OP_SSIM)[0] == g.ERR_INVALID_ARG
     assert g.map_shape(7, 9, g.make_params(border="zero")) == (7, 9)
     assert g.map_shape(1080, 1920, g.make_params(border="reflect", window="box", k=8, stride=4)) == (270, 480)
+
+
+def _host_ws(g, x, p, chunks):
+    n = ctypes.c_size_t(0)
+    rc = g.lib.gbssim_msssim_host_workspace_size(ctypes.byref(x), ctypes.byref(p), chunks, ctypes.byref(n))
+    return rc, n.value
+
+
+def test_host_pipeline_plans_on_host(g):
+    """gbssim_msssim_host's layouts: chunked mode holds two stages of one
+    chunk, streamed mode (chunks = 0) every pair at once plus one arrival
+    flag per pair; streamed mode takes only the persistent path's windows."""
+    h, w, n = 1080, 1920, 64
+    x = _plane(g, h, w, n)
+    p = g.make_params()
+    pitch_bytes = h * ((w + 15) // 16 * 16)  # uint8 rows padded to 16 bytes
+    rc, chunked = _host_ws(g, x, p, 4)
+    assert rc == 0 and chunked >= 2 * 2 * 16 * pitch_bytes  # two stages of x and y, 16 pairs each
+    rc, streamed = _host_ws(g, x, p, 0)
+    assert rc == 0 and streamed >= 2 * n * pitch_bytes + 4 * n + 8 * n
+    assert streamed > chunked
+    assert _host_ws(g, x, p, -1)[0] == g.ERR_INVALID_ARG
+    # chunks above the count are clamped: one chunk per pair
+    assert _host_ws(g, _plane(g, h, w, 3), p, 8) == _host_ws(g, _plane(g, h, w, 3), p, 3)
+    for kw in (dict(k=7, sigma=1.0), dict(window="box", k=8), dict(stride=2)):
+        pk = g.make_params(**kw)
+        assert _host_ws(g, x, pk, 4)[0] == 0, kw
+        assert _host_ws(g, x, pk, 0)[0] == g.ERR_UNSUPPORTED, kw
+    p97 = g.make_params(flags=2)  # GBSSIM_FLAG_PYRAMID_97
+    assert _host_ws(g, x, p97, 0)[0] == g.ERR_UNSUPPORTED
+    # every level must hold the window, streamed or not
+    small = _plane(g, 160, 160, 4)  # level 4 is 10 x 10
+    assert _host_ws(g, small, p, 0)[0] == g.ERR_TOO_SMALL
+    assert _host_ws(g, small, p, 2)[0] == g.ERR_TOO_SMALL
