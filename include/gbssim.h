@@ -392,7 +392,8 @@ int gbssim_msssim(const gbssim_plane *x, const gbssim_plane *y, const gbssim_par
  *   stream2      : nullable third stream.  When given, odd chunks are scored
  *                  on it (each stage has its own MS-SSIM workspace), so one
  *                  chunk's kernel fills the GPU while the previous one drains;
- *                  it must differ from the other two.
+ *                  it must differ from the other two.  Streamed mode has one
+ *                  launch and leaves it unused.
  * Six CUDA events are created per call and released when the streams pass
  * them. */
 int gbssim_msssim_host_workspace_size(const gbssim_plane *x, const gbssim_params *p, int32_t chunks,
