@@ -255,6 +255,11 @@ def test_downsample_exact_on_uint8_pyramid():
         scaled = a * 4 ** j
         assert np.all(scaled == np.round(scaled))
         assert np.all(a.astype(np.float32).astype(np.float64) == a)
+        assert scaled.min() >= 0 and scaled.max() <= 255 * 4 ** j <= 65535  # levels 1..4 fit 16 bits
+    white = np.full((32, 32), 255.0)
+    for _ in range(4):
+        white = oracle.downsample2x2(white)
+    assert np.all(white * 4 ** 4 == 65280)
 
 
 def test_msssim_single_scale_is_ssim():
