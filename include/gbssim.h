@@ -43,7 +43,7 @@ typedef enum gbssim_status {
     GBSSIM_OK = 0,
     GBSSIM_ERR_INVALID_ARG = -1,  /* null pointer, bad enum, stride < 1, ... */
     GBSSIM_ERR_TOO_SMALL = -2,    /* an image (or pyramid level) is smaller than k */
-    GBSSIM_ERR_UNSUPPORTED = -3,  /* valid combination this build does not implement */
+    GBSSIM_ERR_UNSUPPORTED = -3,  /* valid combination the library does not implement */
     GBSSIM_ERR_CUDA = -4,         /* the CUDA runtime reported an error */
     GBSSIM_ERR_DOMAIN = -5,       /* MS-SSIM product with a non-positive pooled term */
     GBSSIM_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up */
