@@ -67,6 +67,22 @@ def test_streamed_matches_oracle(g, synth, n, h, w):
     assert torch.equal(g.msssim_host(x.pin_memory(), y.pin_memory(), chunks=0), got)
 
 
+def test_streamed_full_size_sampled(g, synth):
+    """The end-to-end benchmark step: 64 pinned 1920x1080 pairs streamed
+    through one launch (copy groups of 4 pairs, 128-row items at the two
+    largest levels); every score against the device call, sampled pairs
+    (first, middle and last copy group) against the oracle."""
+    n = 64
+    x, y = synth.luma_pairs_u8(n, 1080, 1920)
+    got = g.msssim_host(x.pin_memory(), y.pin_memory(), chunks=0)
+    dev = g.msssim(x.to(DEV), y.to(DEV)).cpu()
+    assert torch.isfinite(got).all()
+    assert torch.allclose(got, dev, rtol=0, atol=1e-6)
+    for i in (0, 33, 63):
+        s, _ = oracle.msssim(x[i].numpy(), y[i].numpy())
+        assert abs(got[i].item() - s) <= 1e-6
+
+
 _BLOCKING_SCRIPT = """
 import torch
 from paper_2101_06354_gb300 import gbssim, synth
