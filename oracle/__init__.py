@@ -55,6 +55,9 @@ def _load():
         lib.oracle_downsample2x2.argtypes = [_dp, L, L, _dp]
         lib.oracle_ssim_grad.argtypes = [_dp, _dp, L, L, _dp, I, I, D, D, I, _dp]
         lib.oracle_num_threads.restype = I
+        lib.oracle_set_num_threads.argtypes = [I]
+        lib.oracle_set_num_threads.restype = None
+        lib.oracle_window_stats_separable.argtypes = [_dp, _dp, L, L, _dp, I, I, _dp, _dp, _dp, _dp, _dp]
         _lib = lib
     return _lib
 
@@ -75,6 +78,12 @@ def _check(rc):
 def num_threads() -> int:
     """Threads the oracle's OpenMP split uses."""
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the OpenMP split from now on (the CPU baseline times one
+    core and all cores)."""
+    _load().oracle_set_num_threads(int(n))
 
 
 def out_shape(h: int, w: int, k: int, stride: int):
@@ -99,6 +108,19 @@ def box_window(k: int) -> np.ndarray:
     w = np.empty((k, k), np.float64)
     _check(_load().oracle_box_window(k, _ptr(w)))
     return w
+
+
+def taps_1d(kind: str, k: int, sigma: float = 1.5) -> np.ndarray:
+    """1-D factor g of a separable window w = g g^T: the Gaussian
+    exp(-(t-c)^2 / 2 sigma^2) normalised to sum 1, or the box 1/k."""
+    if kind == "gaussian":
+        c = 0.5 * (k - 1)
+        t = np.arange(k, dtype=np.float64)
+        v = np.exp(-((t - c) ** 2) / (2.0 * sigma * sigma))
+        return v / v.sum()
+    if kind == "box":
+        return np.full(k, 1.0 / k)
+    raise ValueError(kind)
 
 
 def window(kind: str, k: int, sigma: float = 1.5) -> np.ndarray:
@@ -143,6 +165,21 @@ def window_stats(x, y, w, stride: int = 1):
     maps = [np.empty((oh, ow), np.float64) for _ in range(5)]
     _check(_load().oracle_window_stats(_ptr(x), _ptr(y), H, W, _ptr(w), k, stride,
                                        *[_ptr(m) for m in maps]))
+    return dict(zip(("mu1", "mu2", "var1", "var2", "cov"), maps))
+
+
+def window_stats_separable(x, y, g, stride: int = 1):
+    """The statistics of window_stats for the separable window g g^T, by a
+    row pass then a column pass (the mode the CPU baseline times)."""
+    x, y, g = _f64(x), _f64(y), _f64(g)
+    H, W = x.shape
+    k = g.shape[0]
+    if y.shape != x.shape or g.ndim != 1 or H < k or W < k or stride < 1:
+        raise ValueError("bad shapes")
+    oh, ow = out_shape(H, W, k, stride)
+    maps = [np.empty((oh, ow), np.float64) for _ in range(5)]
+    _check(_load().oracle_window_stats_separable(_ptr(x), _ptr(y), H, W, _ptr(g), k, stride,
+                                                 *[_ptr(m) for m in maps]))
     return dict(zip(("mu1", "mu2", "var1", "var2", "cov"), maps))
 
 
@@ -326,7 +363,7 @@ def downsample2x2(img) -> np.ndarray:
 def msssim(x, y, scales: int = 5, exponents=MSSSIM_EXPONENTS, combine: str = "product",
            window_kind: str = "gaussian", k: int = 11, sigma: float = 1.5,
            K1: float = 0.01, K2: float = 0.03, L: float = 255.0, pyramid: str = "avg2",
-           border: str = "valid"):
+           border: str = "valid", mode: str = "direct"):
     """MS-SSIM (Introduction; Section "Salient Features ...").
 
     Scale 1 is the input; scale j+1 is the 2x2 average of scale j
@@ -338,17 +375,27 @@ def msssim(x, y, scales: int = 5, exponents=MSSSIM_EXPONENTS, combine: str = "pr
     sum_j (beta_j / sum beta) m_j, a convex combination.  With border "zero"
     or "reflect" each level is extended (extend_border) for its own SSIM
     map; the pyramid is formed from the unextended levels.
+    mode="direct" (the checker) sums every k x k window; mode="separable"
+    takes the row-then-column passes of window_stats_separable (equal to
+    rounding; the CPU baseline's mode).
     Returns (score, per_scale) with per_scale[j] = (mean cs_j, mean Q_j).
     """
     exps = np.asarray(exponents[:scales], np.float64)
     if len(exps) != scales:
         raise ValueError("need one exponent per scale")
     C1, C2 = constants(K1, K2, L)
-    w = window(window_kind, k, sigma)
+    if mode == "direct":
+        w = window(window_kind, k, sigma)
+        stats = window_stats
+    elif mode == "separable":
+        w = taps_1d(window_kind, k, sigma)
+        stats = window_stats_separable
+    else:
+        raise ValueError(mode)
     a, b = _f64(x), _f64(y)
     per = []
     for j in range(scales):
-        st = window_stats(extend_border(a, k, border), extend_border(b, k, border), w, 1)
+        st = stats(extend_border(a, k, border), extend_border(b, k, border), w, 1)
         _, cs, q = ssim_terms(st, C1, C2)
         per.append((mean(cs), mean(q)))
         if j + 1 < scales:

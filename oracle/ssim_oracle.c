@@ -363,3 +363,80 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/* Set the number of threads of the OpenMP split (no effect without OpenMP);
+ * the CPU baseline times the oracle on one core and on all of them. */
+void oracle_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* The same local statistics as oracle_window_stats for a SEPARABLE window
+ * w(m,n) = g(m) g(n) (the Gaussian of the Background section, the
+ * rectangular window with g = 1/k), computed in two passes the way a plain
+ * CPU implementation does: first the five weighted row sums
+ *   h_p(r, b) = sum_n g(n) p(r, b s + n)   for p = I1, I2, I1^2, I2^2, I1 I2
+ * at every input row r and strided output column b, then the weighted column
+ * sums of those at every strided output row, and finally mu and the centred
+ * moments exactly as in Eqs. local_means .. local_corr.  Mathematically equal
+ * to the direct k x k sums; in FP64 the two agree to rounding (~1e-12
+ * relative).  This is the oracle mode the CPU baseline times; the direct mode
+ * stays the checker.  g: k taps. */
+int oracle_window_stats_separable(const double *x, const double *y, long H, long W,
+                                  const double *g, int k, int s,
+                                  double *mu1, double *mu2, double *var1, double *var2,
+                                  double *cov)
+{
+    if (!x || !y || !g || k < 1 || s < 1 || H < k || W < k) return ORACLE_BAD_ARG;
+    long OH = out_dim(H, k, s), OW = out_dim(W, k, s);
+    double *h = (double *)malloc(sizeof(double) * 5 * (size_t)H * (size_t)OW);
+    if (!h) return ORACLE_BAD_ARG;
+    double *h1 = h, *h2 = h + (size_t)H * OW, *h11 = h + 2 * (size_t)H * OW;
+    double *h22 = h + 3 * (size_t)H * OW, *h12 = h + 4 * (size_t)H * OW;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (long r = 0; r < H; ++r)
+        for (long b = 0; b < OW; ++b) {
+            double s1 = 0, s2 = 0, s11 = 0, s22 = 0, s12 = 0;
+            const double *xr = x + r * W + b * s, *yr = y + r * W + b * s;
+            for (int n = 0; n < k; ++n) {
+                double p = xr[n], q = yr[n];
+                s1 += g[n] * p;
+                s2 += g[n] * q;
+                s11 += g[n] * p * p;
+                s22 += g[n] * q * q;
+                s12 += g[n] * p * q;
+            }
+            long o = r * OW + b;
+            h1[o] = s1;
+            h2[o] = s2;
+            h11[o] = s11;
+            h22[o] = s22;
+            h12[o] = s12;
+        }
+#pragma omp parallel for schedule(dynamic, 8)
+    for (long a = 0; a < OH; ++a)
+        for (long b = 0; b < OW; ++b) {
+            double s1 = 0, s2 = 0, s11 = 0, s22 = 0, s12 = 0;
+            for (int m = 0; m < k; ++m) {
+                long o = (a * s + m) * OW + b;
+                s1 += g[m] * h1[o];
+                s2 += g[m] * h2[o];
+                s11 += g[m] * h11[o];
+                s22 += g[m] * h22[o];
+                s12 += g[m] * h12[o];
+            }
+            long o = a * OW + b;
+            mu1[o] = s1;
+            mu2[o] = s2;
+            var1[o] = s11 - s1 * s1;
+            var2[o] = s22 - s2 * s2;
+            cov[o] = s12 - s1 * s2;
+        }
+    free(h);
+    return ORACLE_OK;
+}

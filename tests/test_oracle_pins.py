@@ -80,6 +80,42 @@ def test_window_stats_match_scipy_correlation(shape, k, s):
     np.testing.assert_allclose(st["cov"], cor(x * y) - mu1 * mu2, atol=1e-8)
 
 
+@pytest.mark.parametrize("shape,k,s", [((13, 17), 5, 1), ((20, 9), 4, 3), ((11, 30), 3, 5), ((40, 33), 11, 1)])
+def test_separable_stats_match_scipy_and_direct_mode(shape, k, s):
+    """The row-then-column mode (the one the CPU baseline times) against
+    scipy's 2-D correlation with the outer-product window and against the
+    direct k x k mode.  The 1-D factor is not symmetric, so a flipped factor
+    fails, and the image is not square, so swapped passes fail."""
+    r = _rng(3)
+    x = r.uniform(0, 255, shape)
+    y = r.uniform(0, 255, shape)
+    g = r.uniform(0.1, 1.0, k)
+    g /= g.sum()
+    w = np.outer(g, g)
+    sep = oracle.window_stats_separable(x, y, g, s)
+    direct = oracle.window_stats(x, y, w, s)
+    cor = lambda a: scipy.signal.correlate2d(a, w, mode="valid")[::s, ::s]
+    mu1, mu2 = cor(x), cor(y)
+    np.testing.assert_allclose(sep["mu1"], mu1, rtol=1e-13)
+    np.testing.assert_allclose(sep["mu2"], mu2, rtol=1e-13)
+    np.testing.assert_allclose(sep["cov"], cor(x * y) - mu1 * mu2, atol=1e-8)
+    for key in ("mu1", "mu2", "var1", "var2", "cov"):
+        np.testing.assert_allclose(sep[key], direct[key], rtol=0, atol=1e-12 * 255.0 ** 2)
+
+
+def test_separable_mode_msssim_equals_direct_mode():
+    """MS-SSIM through the separable mode equals the direct mode to 1e-12 on a
+    smooth-noise pair (Gaussian window) and on a box-window pair."""
+    r = _rng(4)
+    x = np.round(r.uniform(0, 255, (180, 200)))
+    y = np.clip(x + np.round(r.normal(0, 12, x.shape)), 0, 255)
+    for kw in ({}, dict(window_kind="box", k=8)):
+        a, pa = oracle.msssim(x, y, **kw)
+        b, pb = oracle.msssim(x, y, mode="separable", **kw)
+        assert abs(a - b) <= 1e-12
+        np.testing.assert_allclose(np.array(pa), np.array(pb), rtol=0, atol=1e-12)
+
+
 @pytest.mark.parametrize("k", [3, 8, 11])
 def test_ramp_variance_closed_form_box(k):
     # I1(i,j) = alpha*j: over a k x k box the values are uniform on alpha*{0..k-1}
