@@ -34,8 +34,10 @@ UNIT = "Mpx-pairs/s"
 WORKLOAD = "msssim_1080p_u8_x64"
 CONFIG = {"workload": WORKLOAD, "pairs_per_gpu": N_PAIRS, "height": H, "width": W, "dtype_in": "u8",
           "scales": 5, "window": "gaussian11_sigma1.5", "l2": "inputs (265 MB) larger than L2, no flush"}
-# FP32 non-tensor peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz max SM clock
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# FP32 non-tensor peak derived from the unit counts (152 SMs x 128 FP32 lanes
+# x 2 flop (FMA) x 2.070 GHz max SM clock); the roofline uses the rate the
+# FMA probe measures on the GPU at hand, this figure is reported beside it
+FP32_PEAK_DERIVED_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # algorithmic FLOP per SSIM output: 5 moments x 2 separable passes x 11 taps x 2 + 3 products + ~17 formula
 FLOP_PER_OUTPUT = 240
 # pyramid levels of the workload (floor halving)
@@ -77,10 +79,82 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-class ClockSampler:
-    """nvidia-smi clock / throttle sampling in the background during the timed region."""
+def measure_fp32_peak(gbssim, dev, iters: int = 4000):
+    """FP32 FMA rate of this GPU (TFLOP/s): gbssim_fp32_probe, scalar FFMA
+    and packed FFMA2 chains on 16 CTAs x 256 threads per SM, median of 5
+    launches each (CUDA events on the launching stream); the larger of the
+    two rates is the peak."""
+    import torch
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = 16 * sms
+    sink = torch.empty(blocks * 256, device=dev)
+    st = torch.cuda.current_stream(dev)
+    rates = {}
+    for packed in (0, 1):
+        for _ in range(2):
+            gbssim._check(gbssim.lib.gbssim_fp32_probe(packed, blocks, iters, sink.data_ptr(), st.cuda_stream),
+                          "gbssim_fp32_probe")
+        ts = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            gbssim.lib.gbssim_fp32_probe(packed, blocks, iters, sink.data_ptr(), st.cuda_stream)
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        rates["ffma2" if packed else "ffma"] = blocks * 256 * 512 * iters / (ms / 1e3) / 1e12
+    return max(rates.values()), rates
+
+
+def c1_latency(gbssim, synth, dev, samples: int = 5, back_to_back: int = 200):
+    """Single 256x256 uint8 pair, SSIM with the 11x11 Gaussian (the smallest
+    workload, latency-bound): per-call latency in microseconds, CUDA events
+    around one gbssim_ssim_map call (+ its pooling finaliser) with L2 flushed
+    (a 256 MB write) before each sample, median of 5; plus the L2-warm
+    back-to-back rate."""
+    import torch
+
+    x, y = synth.single_pair_u8(256, 256, device="cpu")
+    x, y = x.reshape(1, 256, 256).to(dev), y.reshape(1, 256, 256).to(dev)
+    p = gbssim.make_params()
+    wsc = gbssim.workspace(gbssim.plane(x), p, gbssim.OP_SSIM, dev)
+    fn = lambda: gbssim.ssim(x, y, ws=wsc)
+    for _ in range(5):
+        fn()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream(dev)
+    lat = []
+    for _ in range(samples):
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        lat.append(e0.elapsed_time(e1) * 1e3)
+    del flush
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(back_to_back):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    b2b = e0.elapsed_time(e1) * 1e3 / back_to_back
+    return {"latency_us": statistics.median(lat), "samples_us": lat, "back_to_back_us": b2b,
+            "mpx_pairs_per_s_back_to_back": 256 * 256 / b2b, "kernels_per_call": 2,
+            "config": "1 pair 256x256 u8, Gaussian 11 / 1.5, valid, K = 0.01 / 0.03, L = 255, FP64 pooled; "
+                      "L2 flushed (256 MB write) before each latency sample"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling in the background: every sample is
+    stamped on arrival, so the summary can cover the whole timed phase or
+    one window of it."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -92,7 +166,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -101,8 +175,15 @@ class ClockSampler:
         return self
 
     def _read(self):
+        import datetime
+
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            line = line.strip()
+            try:  # nvidia-smi's own stamp (local time, ms): immune to pipe buffering
+                ts = datetime.datetime.strptime(line.split(",")[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = time.time()
+            self.lines.append((ts, line))
 
     def __exit__(self, *a):
         if self.proc:
@@ -112,11 +193,16 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
+    def summary(self, t_begin: float = None, t_end: float = None):
+        """Median SM clock, maximum clock and active throttle reasons of the
+        samples stamped inside [t_begin, t_end] (time.time() seconds; all
+        samples by default)."""
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [t.strip() for t in ln.split(",")]
+        for ts, ln in self.lines:
+            if (t_begin is not None and ts < t_begin) or (t_end is not None and ts > t_end):
+                continue
+            f = [t.strip() for t in ln.split(",")][1:]
             if len(f) < 9:
                 continue
             try:
@@ -153,7 +239,7 @@ def run_reference(args):
     sample = 4
     x, y = synth.luma_pairs_u8(sample, H, W)
     xs, ys = x.numpy(), y.numpy()
-    step = lambda: [oracle.msssim(xs[i], ys[i]) for i in range(sample)]
+    step = lambda: [oracle.msssim(xs[i], ys[i], mode="separable") for i in range(sample)]
     for _ in range(args.warmup):
         step()
     t = time.perf_counter()
@@ -167,32 +253,48 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(CONFIG, sample_pairs_per_step=sample), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d of the 64 1080p pairs per step, FP64 direct-sum oracle" % sample},
+                             "sample": "%d of the 64 1080p pairs per step, FP64 oracle, separable mode "
+                                       "(row then column passes), OpenMP over rows" % sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
-def cpu_baseline(min_seconds: float = 10.0, max_passes: int = 16):
-    """Oracle throughput on a bounded sample, for the JSON line: passes over
-    16 of the 64 pairs until about min_seconds of CPU work (at most
-    max_passes passes)."""
-    import oracle
-    from paper_2101_06354_gb300 import synth
-
-    sample = 16
-    x, y = synth.luma_pairs_u8(sample, H, W)
-    xs, ys = x.numpy(), y.numpy()
+def _oracle_rate(oracle, xs, ys, min_seconds: float, max_passes: int = 16):
+    """Passes of the separable FP64 oracle over the sample pairs until about
+    min_seconds; returns (Mpx-pairs/s, passes, seconds)."""
     passes = 0
     t = time.perf_counter()
     while passes < max_passes and (passes == 0 or time.perf_counter() - t < min_seconds):
-        for i in range(sample):
-            oracle.msssim(xs[i], ys[i])
+        for i in range(len(xs)):
+            oracle.msssim(xs[i], ys[i], mode="separable")
         passes += 1
     dt = time.perf_counter() - t
-    return {"value": passes * sample * PX_PER_PAIR / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": "%d passes over 16 of the 64 1080p pairs, MS-SSIM, FP64 direct-sum oracle (%.1f s)"
-                      % (passes, dt)}
+    return passes * len(xs) * PX_PER_PAIR / dt / 1e6, passes, dt
+
+
+def cpu_baseline(min_seconds: float = 6.0):
+    """The FP64 oracle (its separable mode: a row pass then a column pass per
+    window statistic, the plain CPU implementation of the definition) timed on
+    all host cores and on one core, on bounded samples of the 64 pairs:
+    16 pairs on all cores, 2 pairs on one core, passes repeated until about
+    min_seconds each."""
+    import oracle
+    from paper_2101_06354_gb300 import synth
+
+    x, y = synth.luma_pairs_u8(16, H, W)
+    xs, ys = x.numpy(), y.numpy()
+    cores = oracle.num_threads()
+    v_all, p_all, t_all = _oracle_rate(oracle, xs, ys, min_seconds)
+    oracle.set_num_threads(1)
+    try:
+        v_one, p_one, t_one = _oracle_rate(oracle, xs[:2], ys[:2], min_seconds)
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": v_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d passes over 16 of the 64 1080p pairs, MS-SSIM, FP64 oracle in its separable mode "
+                      "(row then column passes), all %d host cores (OpenMP, %.1f s)" % (p_all, cores, t_all),
+            "single_core": {"value": v_one, "unit": UNIT, "cores": 1,
+                            "sample": "%d passes over 2 of the pairs on one core (%.1f s)" % (p_one, t_one)}}
 
 
 def run_extras(args, gbssim, synth, x, y, dev, timed, ws):
@@ -241,29 +343,50 @@ def run_extras(args, gbssim, synth, x, y, dev, timed, ws):
         pool_res[kind] = {"ms": tq, "map_passes": passes, "gbs": gbs, "hbm_frac": gbs / hbm_peak}
     out["pool_maps"] = dict(pool_res, config="64 SSIM maps 1070x1910 fp32 (523 MB), one double per map")
     del qmap
+    # SSIM / MS-SSIM loss forward + backward, 32x3x512x512 in [0, 1] (L = 1),
+    # fp32 and bf16 storage, both forms of the autograd Function:
+    # "recompute" (the default: the backward recomputes the window moments)
+    # and "stored" (the forward keeps the coefficient maps).  Algorithmic FLOP
+    # per pixel and level: forward 240 (as the headline), coefficient pass 260
+    # (forward + the three coefficient formulas), gradient pass 138 (three
+    # maps x 11 taps x 2 passes x 2 + the combination); recompute = 240 + 260
+    # + 138, stored = 260 + 138; MS-SSIM levels add a third.
     lx, ly = synth.loss_pairs_float(32, 3, 512, 512)
     px_step = 32 * 3 * 512 * 512
+    flop_px = {"recompute": 240 + 260 + 138, "stored": 260 + 138}
+    ms_px = sum((512 >> j) ** 2 for j in range(5)) / 512 ** 2  # pyramid pixels per input pixel
     loss_res = {}
     for name, dt in (("fp32", torch.float32), ("bf16", torch.bfloat16)):
         xd = lx.to(dev, dt)
         yd = ly.to(dev, dt).requires_grad_(True)
+        esz = 4 if dt == torch.float32 else 2
         for ms_flag in (False, True):
-            lf = gbssim.SSIMLoss(multiscale=ms_flag, L=1.0)
+            for form in ("recompute", "stored"):
+                lf = gbssim.SSIMLoss(multiscale=ms_flag, recompute=form == "recompute", L=1.0)
 
-            def fb():
-                yd.grad = None
-                loss = lf(xd, yd)
-                loss.backward()
-                return loss
+                def fb():
+                    yd.grad = None
+                    loss = lf(xd, yd)
+                    loss.backward()
+                    return loss
 
-            for _ in range(3):
-                fb()
-            kk = max(5, args.steps // 20)
-            t = timed(fb, kk) / kk
-            loss_res[("msssim_" if ms_flag else "ssim_") + name] = {
-                "value": ws * px_step / (t / 1e3) / 1e6, "unit": "Mpx/s", "ms_per_step": t}
+                for _ in range(3):
+                    fb()
+                kk = max(5, args.steps // 20)
+                t = timed(fb, kk) / kk
+                flop = flop_px[form] * px_step * (ms_px if ms_flag else 1.0)
+                key = ("msssim_" if ms_flag else "ssim_") + name + ("" if form == "recompute" else "_stored")
+                loss_res[key] = {"value": ws * px_step / (t / 1e3) / 1e6, "unit": "Mpx/s", "ms_per_step": t,
+                                 "form": form,
+                                 "roofline": {"bound": "alu", "achieved": flop / (t / 1e3) / 1e12,
+                                              "peak": args.fp32_peak, "unit": "TFLOP/s",
+                                              "frac": flop / (t / 1e3) / 1e12 / args.fp32_peak,
+                                              "flop_per_px": flop_px[form] * (ms_px if ms_flag else 1.0)},
+                                 "hbm_frac": 3 * esz * px_step / (t / 1e3) / 1e9 / hbm_peak}
         del xd, yd
-    out["loss_fwd_bwd"] = dict(loss_res, config="32x3x512x512, L=1, loss = 1 - mean score, grad w.r.t. y",
+    out["loss_fwd_bwd"] = dict(loss_res, config="32x3x512x512, L=1, loss = 1 - mean score, grad w.r.t. y; "
+                                                "default form recomputes the moments in the backward, *_stored "
+                                                "keeps the forward's coefficient maps",
                                headline=loss_res["ssim_fp32"]["value"])
 
     # ragged batch: 512 pairs drawn from six resolutions 640x360..3840x2160 plus
@@ -373,9 +496,16 @@ def run_gbssim(args):
             ms = t.item()
         return ms
 
-    with ClockSampler(local) as clk:
-        ms = timed(step, args.steps)
-    clocks = clk.summary()
+    # FP32 peak of this GPU, measured before the timed phase (the ALU roofline's denominator)
+    fp32_peak, fp32_rates = measure_fp32_peak(gbssim, dev)
+    # clocks are sampled over the whole timed phase (the main steps, the
+    # scale-0 kernel, the end-to-end leg, C1 and the secondary workloads); the
+    # main steps alone last only tens of milliseconds
+    clk = ClockSampler(local).__enter__()
+    time.sleep(0.1)  # the sampler's first line
+    t_main0 = time.time()
+    ms = timed(step, args.steps)
+    t_main1 = time.time()
     value = ws * N_PAIRS * PX_PER_PAIR * args.steps / (ms / 1e3) / 1e6
     ms_step = ms / args.steps
     score = step()
@@ -409,9 +539,15 @@ def run_gbssim(args):
     e2e = {"value": ws * N_PAIRS * PX_PER_PAIR / (ms_e2e / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms_e2e,
            "chunks": args.e2e_chunks, "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": 8 * N_PAIRS}
 
+    c1 = c1_latency(gbssim, synth, dev)
+    args.fp32_peak = fp32_peak
     extra = {}
     if not args.no_extras:
         extra = run_extras(args, gbssim, synth, x, y, dev, timed, ws)
+    clk.__exit__()
+    clocks = dict(clk.summary(), window="whole timed phase (main steps, scale-0 kernel, end to end, C1, "
+                                         "secondary workloads), nvidia-smi every 20 ms")
+    clocks_main = clk.summary(t_main0 - 0.05, t_main1 + 0.05)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -422,16 +558,22 @@ def run_gbssim(args):
                 "e2e": e2e,
                 "hbm_frac": hbm_frac,
                 "roofline": {"bound": "alu", "kernel": "gauss11_persistent_kernel<uint8_t, UniformSource> (5 levels)",
-                             "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": achieved / FP32_PEAK_TFLOPS, "traffic": _traffic(),
-                             "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+                             "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                             "frac": achieved / fp32_peak, "traffic": _traffic(),
+                             "peak_source": "measured on this GPU before the timed phase: gbssim_fp32_probe "
+                                            "(independent FFMA / FFMA2 chains, 16 CTAs x 256 threads per SM, "
+                                            "median of 5 launches), the larger rate",
+                             "peak_probe_tflops": fp32_rates,
+                             "peak_derived_tflops": FP32_PEAK_DERIVED_TFLOPS,
                              "units_per_launch": outputs, "flop_per_unit": FLOP_PER_OUTPUT,
                              "kernel_ms": ms_step, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
                              "scale0_grid_kernel": {"kernel": "gauss11_kernel<uint8_t>", "ms": ms_k,
                                                     "achieved": FLOP_PER_OUTPUT * outputs0 / (ms_k / 1e3) / 1e12,
                                                     "frac": FLOP_PER_OUTPUT * outputs0 / (ms_k / 1e3) / 1e12
-                                                    / FP32_PEAK_TFLOPS}},
+                                                    / fp32_peak}},
+                "c1_single_pair_256": c1,
                 "clocks": clocks,
+                "clocks_main_region": clocks_main,
                 "score_mean": float(score.double().mean().item())}
         line.update(extra)
         if not args.no_cpu_baseline and ws == 1:

@@ -338,6 +338,35 @@ int gbssim_cmssim(const gbssim_plane rgb_x[3], const gbssim_plane rgb_y[3], cons
                   double *score_out, float *map_out, int64_t map_ld, int64_t map_image_stride, void *workspace,
                   size_t workspace_bytes, void *stream);
 
+/* QSSIM of `count` pairs of colour pictures (Section "Quaternion SSIM"): each
+ * pixel of a tristimulus picture (RGB, YUV, ... : the three planes given) is
+ * the pure quaternion q = c0 i + c1 j + c2 k; per picture the mean ("DC")
+ * mu_q = (1/MN) sum q and the deviations ("AC") ac_q = q - mu_q give
+ *   sigma_q^2 = sum |ac_q|^2 / ((M-1)(N-1)),
+ *   sigma_{ref,dis} = sum ac_ref conj(ac_dis) / ((M-1)(N-1))  (a quaternion),
+ *   QSSIM = |2 mu_ref conj(mu_dis) + C1| / (|mu_ref|^2 + |mu_dis|^2 + C1)
+ *         * |2 sigma_{ref,dis} + C2| / (sigma_ref^2 + sigma_dis^2 + C2),
+ * |.| the quaternion modulus: one global score per picture, no windows.
+ * Readings of the printed (garbled) formula: the contrast uses the squared
+ * norm; mu^2, sigma^2 in the denominators are squared moduli; the second
+ * factor's denominator is sigma_ref^2 + sigma_dis^2 and its numerator carries
+ * the grayscale cs term's factor 2 (so QSSIM(x, x) = 1); the grayscale
+ * stabilising constants C1, C2 are added (K1 = K2 = 0 gives the printed
+ * constant-free form); the (M-1)(N-1) normalisation is as printed.
+ *   tri_x, tri_y : three planes each (the tristimulus components), all six of
+ *                  one shape, dtype, count and strides; H, W >= 2.
+ *   p            : K1, K2 and L only (window, k, stride, scales are unused).
+ *   score_out    : count doubles (device).
+ *   terms_out    : nullable; 2 * count doubles (device): the luminance factor
+ *                  and the contrast-structure factor of each pair.
+ *   workspace    : gbssim_qssim_workspace_size bytes (x's shape and dtype).
+ * uint8 pictures take exact integer sums (one pass); float pictures two
+ * passes (means, then the deviations' sums), fp64 per CTA, fixed order.
+ * Errors: GBSSIM_ERR_TOO_SMALL for H or W < 2. */
+int gbssim_qssim_workspace_size(const gbssim_plane *x, size_t *bytes);
+int gbssim_qssim(const gbssim_plane tri_x[3], const gbssim_plane tri_y[3], const gbssim_params *p,
+                 double *score_out, double *terms_out, void *workspace, size_t workspace_bytes, void *stream);
+
 /* MS-SSIM of each pair (Introduction; Section "Salient Features of SSIM and
  * MS-SSIM Implementations"): scale 1 is the input, scale j+1 the 2x2 average
  * of scale j (floor size); the contrast-structure term is mean-pooled at every
@@ -387,8 +416,9 @@ int gbssim_msssim(const gbssim_plane *x, const gbssim_plane *y, const gbssim_par
  *                  every earlier call on `stream` that used it is finished
  *                  before this call's copies overwrite it.
  *   stream, copy_stream : two different streams (GBSSIM_ERR_INVALID_ARG if
- *                  equal); all work of the call is ordered before the end of
- *                  `stream`.
+ *                  equal); all work of the call, copies included, is ordered
+ *                  before the end of `stream` (also when a bounded wait gave
+ *                  up before every copy landed).
  *   stream2      : nullable third stream.  When given, odd chunks are scored
  *                  on it (each stage has its own MS-SSIM workspace), so one
  *                  chunk's kernel fills the GPU while the previous one drains;
@@ -494,6 +524,12 @@ typedef struct gbssim_tuning {
  * exists, so their bounded wait runs out and the run reports
  * GBSSIM_ERR_TIMEOUT through gbssim_batch_status.  Never set in production. */
 #define GBSSIM_TUNING_TEST_STALL 1
+/* Test hook of gbssim_msssim_host_ex (streamed mode): the last copy group's
+ * arrival flag is never written, so the level-0 items of its images wait
+ * until their bounded wait runs out; the call then reports
+ * GBSSIM_ERR_TIMEOUT in *status_host and NaN scores for those images (the
+ * copies themselves still run).  Never set in production. */
+#define GBSSIM_TUNING_TEST_DROP_ARRIVAL 2
 
 /* Build a plan for n entries: entry e pairs xs[e] with ys[e] (identical
  * shape; each entry may itself hold count >= 1 equally sized images); all
@@ -529,6 +565,23 @@ int gbssim_batch_status(const gbssim_batch *plan, const void *workspace, int32_t
 /* Release the plan's device tables (NULL is ignored). */
 void gbssim_batch_free(gbssim_batch *plan);
 
+/* gbssim_msssim_host with two more arguments (no counterpart in the paper):
+ *   tuning      : nullable; wait_limit (0 = default) bounds the persistent
+ *                 launch's device-side waits (a level-j item's wait for its
+ *                 image's level j-1, `wait_limit` polls; a level-0 item's wait
+ *                 for its copy group's arrival flag, 16 x `wait_limit` polls);
+ *                 flags may hold GBSSIM_TUNING_TEST_DROP_ARRIVAL only (else
+ *                 GBSSIM_ERR_INVALID_ARG); seg_rows and ctas_per_sm are ignored.
+ *   status_host : nullable host int32 (pinned for an asynchronous return);
+ *                 receives the launch's status word, GBSSIM_OK or
+ *                 GBSSIM_ERR_TIMEOUT when a bounded wait gave up (its images
+ *                 then score NaN), valid once `stream` has completed.
+ * status_host and the test flag need streamed mode (chunks = 0), else
+ * GBSSIM_ERR_UNSUPPORTED.  Everything else as gbssim_msssim_host. */
+int gbssim_msssim_host_ex(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t chunks,
+                          const gbssim_tuning *tuning, double *score_host, int32_t *status_host, void *workspace,
+                          size_t workspace_bytes, void *stream, void *copy_stream, void *stream2);
+
 /* gbssim_ssim_map without a workspace argument, for callers that cannot
  * allocate device memory: a plugin inside a host application that owns the
  * GPU allocator and gives it only input and output buffers, or a real-time
@@ -543,13 +596,25 @@ void gbssim_batch_free(gbssim_batch *plan);
  *   enqueued (about 430 pairs of 1920x1080 fit in one call).
  *   The call allocates nothing.  Its first call on a device (with that
  *   device current) looks up the array's device address once; make that
- *   first call before any stream capture.  All calls share the array and it
+ *   first call before any stream capture (a lookup that fails returns
+ *   GBSSIM_ERR_CUDA and is retried by the next call).  All calls share the array and it
  *   keeps the last call's contents (nothing needs clearing: each call writes
  *   every slot it reads), so calls whose GPU work overlaps race: serialise
  *   them. */
 int gbssim_ssim_map_static(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
                            float *map_out, int64_t map_ld, int64_t map_image_stride,
                            double *mean_out, void *stream);
+
+/* FP32 fused multiply-add throughput probe (no counterpart in the paper: it
+ * measures the peak that the ALU-bound Gaussian kernels are compared with).
+ * Enqueues one launch of `blocks` CTAs x 256 threads; every thread performs
+ * 256 * iters FMAs = 512 * iters FLOP, as 16 independent scalar FFMA chains
+ * (packed = 0) or 8 independent packed f32x2 FFMA2 chains (packed != 0), and
+ * writes one float to sink[block * 256 + thread] (device, blocks * 256
+ * floats, caller-owned).  Time it with CUDA events on `stream`: FP32 rate =
+ * blocks * 256 * 512 * iters / time.  Errors: GBSSIM_ERR_INVALID_ARG for a
+ * null sink or blocks, iters < 1. */
+int gbssim_fp32_probe(int32_t packed, int32_t blocks, int32_t iters, float *sink, void *stream);
 
 /* Exact integer window sums of a uint8 pair, the quantities the paper's
  * integral images produce (Eqs. integral_image_start..integral_image_end):

@@ -337,7 +337,8 @@ cudaError_t run_level(const Level &L, const ImgDesc &dx, const ImgDesc &dy, int 
 // on another stream.
 int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
                           const MsPlan &P, char *ws, double *score_out, double *per_scale_out,
-                          cudaStream_t st, const unsigned *arrive = nullptr, int arrive_group = 1) {
+                          cudaStream_t st, const unsigned *arrive = nullptr, int arrive_group = 1,
+                          unsigned wait_limit = 0) {
     const int S = p->scales, n = x->count;
     // the persistent path fuses the 2x2 pyramid into valid-window levels
     bool persistent = (p->flags & GBSSIM_FLAG_PYRAMID_97) == 0 && !border_mode(p);
@@ -391,7 +392,7 @@ int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_pa
         U.counter_off = (int64_t)P.counter_off;
         U.done_off = (int64_t)P.done_off;
         U.status_off = (int64_t)P.status_off;
-        U.wait_limit = 1u << 22;
+        U.wait_limit = wait_limit ? wait_limit : 1u << 22;
         if (begin > 0x7fffffff) return GBSSIM_ERR_UNSUPPORTED;
         U.arrive = arrive;
         U.arrive_group = arrive_group > 0 ? arrive_group : 1;
@@ -1229,6 +1230,42 @@ int gbssim_cmssim(const gbssim_plane rgb_x[3], const gbssim_plane rgb_y[3], cons
                : GBSSIM_ERR_CUDA;
 }
 
+int gbssim_qssim_workspace_size(const gbssim_plane *x, size_t *bytes) {
+    int rc = check_plane(x);
+    if (rc) return rc;
+    if (!bytes) return GBSSIM_ERR_INVALID_ARG;
+    if (x->height < 2 || x->width < 2) return GBSSIM_ERR_TOO_SMALL;
+    *bytes = qssim_workspace(x->dtype, x->height, x->width, x->count);
+    return GBSSIM_OK;
+}
+
+int gbssim_qssim(const gbssim_plane tri_x[3], const gbssim_plane tri_y[3], const gbssim_params *p,
+                 double *score_out, double *terms_out, void *workspace, size_t workspace_bytes, void *stream) {
+    if (!tri_x || !tri_y || !score_out) return GBSSIM_ERR_INVALID_ARG;
+    for (int c = 0; c < 3; ++c) {
+        int rc = check_pair(&tri_x[0], &tri_x[c]);
+        if (!rc) rc = check_pair(&tri_x[0], &tri_y[c]);
+        if (rc) return rc;
+    }
+    if (!p) return GBSSIM_ERR_INVALID_ARG;
+    if (!(isfinite(p->K1) && isfinite(p->K2) && p->K1 >= 0.0 && p->K2 >= 0.0)) return GBSSIM_ERR_INVALID_ARG;
+    if (!(p->L > 0.0 && isfinite(p->L))) return GBSSIM_ERR_INVALID_ARG;
+    const gbssim_plane &x = tri_x[0];
+    if (x.height < 2 || x.width < 2) return GBSSIM_ERR_TOO_SMALL;
+    const size_t need = qssim_workspace(x.dtype, x.height, x.width, x.count);
+    if (!workspace || workspace_bytes < need) return GBSSIM_ERR_WORKSPACE;
+    ImgDesc dx[3], dy[3];
+    for (int c = 0; c < 3; ++c) {
+        dx[c] = desc_of(&tri_x[c]);
+        dy[c] = desc_of(&tri_y[c]);
+    }
+    const double c1 = (p->K1 * p->L) * (p->K1 * p->L), c2 = (p->K2 * p->L) * (p->K2 * p->L);
+    return launch_qssim(dx, dy, x.dtype, x.count, c1, c2, workspace, score_out, terms_out, (cudaStream_t)stream) ==
+                   cudaSuccess
+               ? GBSSIM_OK
+               : GBSSIM_ERR_CUDA;
+}
+
 int gbssim_downscale_factor(int64_t h, int64_t w, int32_t rule) {
     if (h < 1 || w < 1) return GBSSIM_ERR_INVALID_ARG;
     if (rule == GBSSIM_DOWNSCALE_ROUND_MIN) {
@@ -1283,14 +1320,22 @@ int gbssim_msssim_host_workspace_size(const gbssim_plane *x, const gbssim_params
     return GBSSIM_OK;
 }
 
-int gbssim_msssim_host(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t chunks,
-                       double *score_host, void *workspace, size_t workspace_bytes, void *stream,
-                       void *copy_stream, void *stream2) {
+}  // extern "C"
+
+namespace {
+
+// gbssim_msssim_host and gbssim_msssim_host_ex.  wait_limit: 0 = the default;
+// drop_flag: test hook, the last copy group's arrival flag is never set;
+// status_host (nullable, streamed mode only): the launch's status word.
+int msssim_host_impl(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t chunks,
+                     double *score_host, int32_t *status_host, unsigned wait_limit, bool drop_flag,
+                     void *workspace, size_t workspace_bytes, void *stream, void *copy_stream, void *stream2) {
     int rc = check_pair(x, y);
     if (rc) return rc;
     rc = check_params_valid(p);
     if (rc) return rc;
     if (!score_host) return GBSSIM_ERR_INVALID_ARG;
+    if ((status_host || drop_flag) && chunks != 0) return GBSSIM_ERR_UNSUPPORTED;
     HostPlan H;
     rc = plan_host(x, p, chunks, &H);
     if (rc) return rc;
@@ -1338,10 +1383,15 @@ int gbssim_msssim_host(const gbssim_plane *x, const gbssim_plane *y, const gbssi
             const int m = x->count - i0 < group ? x->count - i0 : group;
             e = copy_images_h2d(x, i0, m, H, xs + i0 * img_bytes, cs);
             if (e == cudaSuccess) e = copy_images_h2d(y, i0, m, H, ysg + i0 * img_bytes, cs);
-            if (e == cudaSuccess && write32(cs, (CUdeviceptr)(flags + f), 1u, CU_STREAM_WRITE_VALUE_DEFAULT) !=
-                                        CUDA_SUCCESS)
+            const bool last = i0 + group >= x->count;
+            if (e == cudaSuccess && !(drop_flag && last) &&
+                write32(cs, (CUdeviceptr)(flags + f), 1u, CU_STREAM_WRITE_VALUE_DEFAULT) != CUDA_SUCCESS)
                 e = cudaErrorUnknown;
         }
+        // the copy stream's end: `stream` waits for it before the score
+        // readback, so every copy of the call (also one whose items' bounded
+        // wait gave up before it landed) is ordered before the end of `stream`
+        if (e == cudaSuccess && rc == GBSSIM_OK) e = cudaEventRecord(copied[1], cs);
         if (e == cudaSuccess && rc == GBSSIM_OK) e = cudaStreamWaitEvent(st, copied[0], 0);  // flags cleared
         if (e == cudaSuccess && rc == GBSSIM_OK) {
             gbssim_plane dx = *x, dy = *y;
@@ -1349,10 +1399,15 @@ int gbssim_msssim_host(const gbssim_plane *x, const gbssim_plane *y, const gbssi
             dy.data = ysg;
             dx.row_stride = dy.row_stride = H.pitch_elems;
             dx.image_stride = dy.image_stride = H.pitch_elems * x->height;
-            rc = msssim_forward(&dx, &dy, p, H.ms, ws + H.ws_off[0], score_dev, nullptr, st, flags, group);
+            rc = msssim_forward(&dx, &dy, p, H.ms, ws + H.ws_off[0], score_dev, nullptr, st, flags, group,
+                                wait_limit);
         }
+        if (e == cudaSuccess && rc == GBSSIM_OK) e = cudaStreamWaitEvent(st, copied[1], 0);
         if (e == cudaSuccess && rc == GBSSIM_OK)
             e = cudaMemcpyAsync(score_host, score_dev, sizeof(double) * (size_t)x->count, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && rc == GBSSIM_OK && status_host)
+            e = cudaMemcpyAsync(status_host, ws + H.ws_off[0] + H.ms.status_off, sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, st);
         for (auto &f : ev) cudaEventDestroy(f);
         if (rc != GBSSIM_OK) return rc;
         if (e == cudaErrorNotSupported) return GBSSIM_ERR_UNSUPPORTED;
@@ -1390,6 +1445,27 @@ int gbssim_msssim_host(const gbssim_plane *x, const gbssim_plane *y, const gbssi
     for (auto &f : ev) cudaEventDestroy(f);  // released once the streams are past them
     if (rc != GBSSIM_OK) return rc;
     return e == cudaSuccess ? GBSSIM_OK : GBSSIM_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gbssim_msssim_host(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t chunks,
+                       double *score_host, void *workspace, size_t workspace_bytes, void *stream,
+                       void *copy_stream, void *stream2) {
+    return msssim_host_impl(x, y, p, chunks, score_host, nullptr, 0, false, workspace, workspace_bytes, stream,
+                            copy_stream, stream2);
+}
+
+int gbssim_msssim_host_ex(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p, int32_t chunks,
+                          const gbssim_tuning *tuning, double *score_host, int32_t *status_host, void *workspace,
+                          size_t workspace_bytes, void *stream, void *copy_stream, void *stream2) {
+    if (tuning && (tuning->flags & ~GBSSIM_TUNING_TEST_DROP_ARRIVAL)) return GBSSIM_ERR_INVALID_ARG;
+    const unsigned wl = tuning ? tuning->wait_limit : 0u;
+    const bool drop = tuning && (tuning->flags & GBSSIM_TUNING_TEST_DROP_ARRIVAL);
+    return msssim_host_impl(x, y, p, chunks, score_host, status_host, wl, drop, workspace, workspace_bytes, stream,
+                            copy_stream, stream2);
 }
 
 int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,

@@ -373,6 +373,13 @@ cudaError_t launch_cmssim_weight(float *map, int64_t oh, int64_t ow, int64_t map
                                  const float *lab_x, const float *lab_y, int64_t H, int64_t W, int64_t cs, int centre,
                                  int stride, cudaStream_t st);
 
+// QSSIM (k_qssim.cu): the CTA band height, the workspace bytes and the launch
+// (x, y: the three planes of each picture, one shape and dtype).
+int64_t qssim_rows_per(int64_t H, int64_t W, int count);
+size_t qssim_workspace(int dtype, int64_t H, int64_t W, int count);
+cudaError_t launch_qssim(const ImgDesc x[3], const ImgDesc y[3], int dtype, int count, double C1, double C2, void *ws,
+                         double *score, double *terms, cudaStream_t st);
+
 // Temporal pooling of frame-score series (k_series.cu).
 cudaError_t launch_series_pool(const double *scores, int n, int count, int64_t stride, int kind, double a0,
                                double a1, double *out, cudaStream_t st);

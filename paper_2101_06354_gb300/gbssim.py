@@ -58,6 +58,7 @@ class Tuning(ctypes.Structure):
 
 
 TUNING_TEST_STALL = 1
+TUNING_TEST_DROP_ARRIVAL = 2
 
 
 class Plane(ctypes.Structure):
@@ -118,6 +119,11 @@ _SIGS = {
     "gbssim_cmssim_workspace_size": ([_P(Plane), _P(Params), _P(_sz)], ctypes.c_int),
     "gbssim_cmssim": ([_P(Plane), _P(Plane), _P(Params), _vp, _vp, _i64, _i64, _vp, _sz, _vp], ctypes.c_int),
     "gbssim_msssim_host": ([_P(Plane), _P(Plane), _P(Params), _i32, _vp, _vp, _sz, _vp, _vp, _vp], ctypes.c_int),
+    "gbssim_fp32_probe": ([_i32, _i32, _i32, _vp, _vp], ctypes.c_int),
+    "gbssim_qssim_workspace_size": ([_P(Plane), _P(_sz)], ctypes.c_int),
+    "gbssim_qssim": ([_P(Plane), _P(Plane), _P(Params), _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "gbssim_msssim_host_ex": ([_P(Plane), _P(Plane), _P(Params), _i32, _P(Tuning), _vp, _vp, _vp, _sz, _vp, _vp,
+                               _vp], ctypes.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -301,7 +307,7 @@ def host_workspace(x: torch.Tensor, chunks: int, **kw) -> torch.Tensor:
 
 def msssim_host(x: torch.Tensor, y: torch.Tensor, chunks: int = 4, ws: torch.Tensor = None,
                 out: torch.Tensor = None, sync: bool = True, two_compute_streams: bool = False,
-                **kw) -> torch.Tensor:
+                tuning: "Tuning" = None, status: torch.Tensor = None, **kw) -> torch.Tensor:
     """MS-SSIM of pairs held in host memory (gbssim_msssim_host): chunks of
     the batch are copied on a side stream while the previous chunk is scored
     on the current stream; chunks=0 streams instead (one launch over all
@@ -309,7 +315,9 @@ def msssim_host(x: torch.Tensor, y: torch.Tensor, chunks: int = 4, ws: torch.Ten
     device call up to fp32 summation order).  Returns a pinned CPU
     float64 tensor of length N, valid at return when sync=True (else once the
     current stream completes).  x and y should be pinned for the copies to
-    overlap."""
+    overlap.  ``tuning`` (a Tuning: wait_limit, test flags) and ``status``
+    (a pinned int32 CPU tensor of one element that receives the launch's
+    status word) go through gbssim_msssim_host_ex; streamed mode only."""
     if x.device.type != "cpu" or y.device.type != "cpu":
         raise ValueError("msssim_host takes host tensors")
     if y.dtype != x.dtype or y.shape != x.shape:
@@ -327,9 +335,18 @@ def msssim_host(x: torch.Tensor, y: torch.Tensor, chunks: int = 4, ws: torch.Ten
     if out is None:
         out = torch.empty(n, dtype=torch.float64, pin_memory=True)
     cs, s2 = _copy_stream(dev, 0), _copy_stream(dev, 1)
-    _check(lib.gbssim_msssim_host(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p), int(chunks), out.data_ptr(),
-                                  ws.data_ptr(), ws.numel(), _stream(dev), cs.cuda_stream,
-                                  s2.cuda_stream if two_compute_streams else None), "gbssim_msssim_host")
+    if tuning is not None or status is not None:
+        if status is not None and (status.device.type != "cpu" or status.dtype != torch.int32 or status.numel() < 1):
+            raise ValueError("status must be a CPU int32 tensor")
+        _check(lib.gbssim_msssim_host_ex(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p), int(chunks),
+                                         ctypes.byref(tuning) if tuning is not None else None, out.data_ptr(),
+                                         status.data_ptr() if status is not None else None, ws.data_ptr(),
+                                         ws.numel(), _stream(dev), cs.cuda_stream,
+                                         s2.cuda_stream if two_compute_streams else None), "gbssim_msssim_host_ex")
+    else:
+        _check(lib.gbssim_msssim_host(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p), int(chunks),
+                                      out.data_ptr(), ws.data_ptr(), ws.numel(), _stream(dev), cs.cuda_stream,
+                                      s2.cuda_stream if two_compute_streams else None), "gbssim_msssim_host")
     if sync:
         torch.cuda.current_stream(dev).synchronize()
     return out
@@ -595,6 +612,33 @@ def cmssim(ref_rgb, dis_rgb, return_map: bool = False, ws: torch.Tensor = None, 
     return (score, mp) if return_map else score
 
 
+def qssim(ref, dis, return_terms: bool = False, ws: torch.Tensor = None, **kw):
+    """QSSIM (gbssim_qssim) of colour pairs: ref and dis are 3-tuples of CUDA
+    tensors (H, W) or (N, H, W), the tristimulus planes (RGB, YUV, ...) of
+    one dtype and shape.  Keyword arguments K1, K2, L as make_params.
+    Returns the score per pair (float64, N)[, and (N, 2) luminance and
+    contrast-structure factors]."""
+    xs = [_as_batch(t).contiguous() for t in ref]
+    ys = [_as_batch(t).contiguous() for t in dis]
+    if len(xs) != 3 or len(ys) != 3:
+        raise ValueError("expected three planes per picture")
+    dev = xs[0].device
+    p = make_params(**kw)
+    px = (Plane * 3)(*[plane(t) for t in xs])
+    py = (Plane * 3)(*[plane(t) for t in ys])
+    n = xs[0].shape[0]
+    if ws is None:
+        nb = ctypes.c_size_t()
+        _check(lib.gbssim_qssim_workspace_size(ctypes.byref(px[0]), ctypes.byref(nb)), "gbssim_qssim_workspace_size")
+        ws = torch.empty(max(int(nb.value), 1), dtype=torch.uint8, device=dev)
+    score = torch.empty(n, dtype=torch.float64, device=dev)
+    terms = torch.empty((n, 2), dtype=torch.float64, device=dev) if return_terms else None
+    _check(lib.gbssim_qssim(px, py, ctypes.byref(p), score.data_ptr(),
+                            terms.data_ptr() if terms is not None else None, ws.data_ptr(), ws.numel(),
+                            _stream(dev)), "gbssim_qssim")
+    return (score, terms) if return_terms else score
+
+
 _GDT = {torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}
 
 
@@ -645,13 +689,21 @@ def ssim_backward(x: torch.Tensor, y: torch.Tensor, multiscale: bool = False, gr
 
 class _SSIMLossFn(torch.autograd.Function):
     """loss = 1 - mean over pairs of SSIM (or MS-SSIM); gradient w.r.t. y only
-    (x is the reference).  The forward (gbssim_loss_forward) runs each level
-    once in coefficient mode and keeps the coefficient maps, the pyramid and
-    the pooled values in a device buffer; the backward (gbssim_loss_backward)
-    runs only the gradient kernels from it."""
+    (x is the reference).
+
+    recompute=True (the default): the forward is the plain score call
+    (gbssim_ssim_map, or gbssim_msssim with its per-scale means) and keeps
+    only x, y and the pooled values; the backward (gbssim_ssim_backward)
+    recomputes every level's window moments, forms the coefficient maps in a
+    transient workspace and runs the gradient kernels.
+    recompute=False: the forward (gbssim_loss_forward) runs each level once in
+    coefficient mode and keeps the coefficient maps, the pyramid and the
+    pooled values in a device buffer (12 bytes per output position per
+    level); the backward (gbssim_loss_backward) runs only the gradient
+    kernels from it."""
 
     @staticmethod
-    def forward(ctx, x, y, multiscale, kw):
+    def forward(ctx, x, y, multiscale, recompute, kw):
         xb, yb = _as_batch(x), _as_batch(y)
         if xb.stride() != yb.stride():
             xb, yb = xb.contiguous(), yb.contiguous()
@@ -661,50 +713,89 @@ class _SSIMLossFn(torch.autograd.Function):
         p = make_params(**kw)
         px, py = plane(xb), plane(yb)
         dev = xb.device
-        nb = ctypes.c_size_t()
-        _check(lib.gbssim_loss_saved_size(ctypes.byref(px), ctypes.byref(p), int(multiscale), ctypes.byref(nb)),
-               "gbssim_loss_saved_size")
-        saved = torch.empty(max(int(nb.value), 1), dtype=torch.uint8, device=dev)
-        score = torch.empty(xb.shape[0], dtype=torch.float64, device=dev)
-        _check(lib.gbssim_loss_forward(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p), int(multiscale),
-                                       score.data_ptr(), None, saved.data_ptr(), saved.numel(), _stream(dev)),
-               "gbssim_loss_forward")
-        ctx.save_for_backward(xb, yb, saved)
+        n = xb.shape[0]
+        score = torch.empty(n, dtype=torch.float64, device=dev)
+        if recompute:
+            per = None
+            if multiscale:
+                per = torch.empty((n, p.scales, 2), dtype=torch.float64, device=dev)
+                ws = workspace(px, p, OP_MSSSIM, dev)
+                _check(lib.gbssim_msssim(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p), score.data_ptr(),
+                                         per.data_ptr(), ws.data_ptr(), ws.numel(), _stream(dev)), "gbssim_msssim")
+                ctx.save_for_backward(xb, yb, score, per)
+            else:
+                ws = workspace(px, p, OP_SSIM, dev)
+                _check(lib.gbssim_ssim_map(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p), None, 0, 0,
+                                           score.data_ptr(), ws.data_ptr(), ws.numel(), _stream(dev)),
+                       "gbssim_ssim_map")
+                ctx.save_for_backward(xb, yb)
+        else:
+            nb = ctypes.c_size_t()
+            _check(lib.gbssim_loss_saved_size(ctypes.byref(px), ctypes.byref(p), int(multiscale),
+                                              ctypes.byref(nb)), "gbssim_loss_saved_size")
+            saved = torch.empty(max(int(nb.value), 1), dtype=torch.uint8, device=dev)
+            _check(lib.gbssim_loss_forward(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p), int(multiscale),
+                                           score.data_ptr(), None, saved.data_ptr(), saved.numel(), _stream(dev)),
+                   "gbssim_loss_forward")
+            ctx.save_for_backward(xb, yb, saved)
         ctx.multiscale = multiscale
+        ctx.recompute = recompute
         ctx.params = p
         ctx.y_shape = y.shape
-        ctx.n = score.numel()
+        ctx.n = n
         return 1.0 - score.mean()
 
     @staticmethod
     def backward(ctx, grad_loss):
         if not ctx.needs_input_grad[1]:
-            return None, None, None, None
-        xb, yb, saved = ctx.saved_tensors
+            return None, None, None, None, None
+        xb, yb = ctx.saved_tensors[:2]
         n, h, w = yb.shape
-        g = torch.empty((n, h, w), dtype=yb.dtype, device=yb.device)
+        dev = yb.device
+        g = torch.empty((n, h, w), dtype=yb.dtype, device=dev)
         go = grad_loss.to(torch.float64).contiguous()
         px, py = plane(xb), plane(yb)
-        _check(lib.gbssim_loss_backward(ctypes.byref(px), ctypes.byref(py), ctypes.byref(ctx.params),
-                                        int(ctx.multiscale), -1.0 / ctx.n, go.data_ptr(), 0, saved.data_ptr(),
-                                        saved.numel(), g.data_ptr(), _GDT[yb.dtype], w, h * w, _stream(yb.device)),
-               "gbssim_loss_backward")
-        return None, g.reshape(ctx.y_shape), None, None
+        p = ctx.params
+        if ctx.recompute:
+            fs = fp = None
+            if ctx.multiscale:
+                fs, fp = ctx.saved_tensors[2], ctx.saved_tensors[3]
+            ws = workspace(px, p, OP_BACKWARD_MS if ctx.multiscale else OP_BACKWARD, dev)
+            _check(lib.gbssim_ssim_backward(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p),
+                                            int(ctx.multiscale), -1.0 / ctx.n, go.data_ptr(), 0,
+                                            fs.data_ptr() if fs is not None else None,
+                                            fp.data_ptr() if fp is not None else None, g.data_ptr(),
+                                            _GDT[yb.dtype], w, h * w, None, ws.data_ptr(), ws.numel(),
+                                            _stream(dev)), "gbssim_ssim_backward")
+        else:
+            saved = ctx.saved_tensors[2]
+            _check(lib.gbssim_loss_backward(ctypes.byref(px), ctypes.byref(py), ctypes.byref(p),
+                                            int(ctx.multiscale), -1.0 / ctx.n, go.data_ptr(), 0, saved.data_ptr(),
+                                            saved.numel(), g.data_ptr(), _GDT[yb.dtype], w, h * w, _stream(dev)),
+                   "gbssim_loss_backward")
+        return None, g.reshape(ctx.y_shape), None, None, None
 
 
 class SSIMLoss(torch.nn.Module):
     """1 - SSIM (or MS-SSIM with multiscale=True) averaged over the batch,
     differentiable with respect to the second argument.  Inputs (H, W),
     (N, H, W) or (B, C, H, W) float tensors on a CUDA device; keyword
-    arguments as ``make_params`` (e.g. L=1.0 for inputs in [0, 1])."""
+    arguments as ``make_params`` (e.g. L=1.0 for inputs in [0, 1]).
 
-    def __init__(self, multiscale: bool = False, **kw):
+    recompute=True (default): the backward recomputes the window moments from
+    x and y (nothing but the pooled scores is kept between forward and
+    backward); recompute=False keeps every level's coefficient maps from the
+    forward instead (faster backward, 12 bytes per output position per level
+    held until the backward)."""
+
+    def __init__(self, multiscale: bool = False, recompute: bool = True, **kw):
         super().__init__()
         self.multiscale = multiscale
+        self.recompute = recompute
         self.kw = kw
 
     def forward(self, x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
-        return _SSIMLossFn.apply(x.detach(), y, self.multiscale, dict(self.kw))
+        return _SSIMLossFn.apply(x.detach(), y, self.multiscale, self.recompute, dict(self.kw))
 
 
 def video_ssim(xs, ys, weights=(6.0, 1.0, 1.0), percentile: float = 10.0, pp_r: float = 4.0, **kw):

@@ -130,11 +130,12 @@ def test_gradient_zero_at_identity_and_scale_factors(g, synth):
 
 
 @pytest.mark.parametrize("multiscale", [False, True])
-def test_loss_autograd(g, synth, multiscale):
+@pytest.mark.parametrize("recompute", [True, False])
+def test_loss_autograd(g, synth, multiscale, recompute):
     x, y = synth.loss_pairs_float(2, 3, 176, 180)
     xd = x.to(DEV)
     yd = y.to(DEV).requires_grad_(True)
-    loss_fn = g.SSIMLoss(multiscale=multiscale, L=1.0)
+    loss_fn = g.SSIMLoss(multiscale=multiscale, recompute=recompute, L=1.0)
     loss = loss_fn(xd, yd)
     (2.5 * loss).backward()
     xs, ys = _np64(x).reshape(6, 176, 180), _np64(y).reshape(6, 176, 180)
@@ -153,19 +154,43 @@ def test_loss_autograd(g, synth, multiscale):
     assert _rel_err(yd.grad.double().cpu().numpy(), ref) <= 1e-4
 
 
-def test_loss_fwd_bwd_full_size_sampled(g, synth):
-    """The loss workload at full size (32 x 3 x 512 x 512 fp32, L = 1): the
-    forward value and the gradient of sampled planes against the oracle."""
+@pytest.mark.parametrize("multiscale", [False, True])
+def test_loss_fwd_bwd_full_size(g, synth, multiscale):
+    """The loss workload at full size (32 x 3 x 512 x 512 fp32, L = 1) through
+    the default Function (the backward recomputes the moments): the loss
+    value and the gradient of every one of the 96 planes against the
+    oracle's analytic gradient."""
     x, y = synth.loss_pairs_float(32, 3, 512, 512, device=DEV)
     yd = y.clone().requires_grad_(True)
-    loss = g.SSIMLoss(L=1.0)(x, yd)
+    loss = g.SSIMLoss(multiscale=multiscale, L=1.0)(x, yd)
     loss.backward()
-    xs, ys = x.reshape(96, 512, 512), y.reshape(96, 512, 512)
-    gr = yd.grad.reshape(96, 512, 512)
+    xs, ys = _np64(x.reshape(96, 512, 512)), _np64(y.reshape(96, 512, 512))
+    gr = yd.grad.reshape(96, 512, 512).double().cpu().numpy()
+    scores = []
+    for i in range(96):
+        if multiscale:
+            sc, ref = oracle.msssim_grad(xs[i], ys[i], L=1.0)
+        else:
+            sc, _ = oracle.ssim(xs[i], ys[i], L=1.0)
+            ref = oracle.ssim_grad(xs[i], ys[i], L=1.0)
+        scores.append(sc)
+        assert _rel_err(gr[i], -1.0 / 96 * ref) <= 1e-4, i
+    assert abs(loss.item() - (1.0 - np.mean(scores))) <= 1e-6
+
+
+def test_loss_fwd_bwd_full_size_bf16_sampled(g, synth):
+    """The bf16-stored variant of the full-size loss workload: sampled planes
+    against the oracle's gradient on the same rounded inputs."""
+    x, y = synth.loss_pairs_float(32, 3, 512, 512, device=DEV)
+    xb, yb = x.to(torch.bfloat16), y.to(torch.bfloat16).requires_grad_(True)
+    loss = g.SSIMLoss(L=1.0)(xb, yb)
+    loss.backward()
+    assert yb.grad.dtype == torch.bfloat16
+    xs, ys = xb.detach().reshape(96, 512, 512), yb.detach().reshape(96, 512, 512)
+    gr = yb.grad.reshape(96, 512, 512)
     for i in (0, 47, 95):
         ref = -1.0 / 96 * oracle.ssim_grad(_np64(xs[i]), _np64(ys[i]), L=1.0)
-        assert _rel_err(gr[i].double().cpu().numpy(), ref) <= 1e-4
-    assert torch.isfinite(yd.grad).all()
+        assert _rel_err(gr[i].double().cpu().numpy(), ref) <= 1e-2
 
 
 def test_backward_rejects_unsupported(g):
@@ -180,18 +205,35 @@ def test_backward_rejects_unsupported(g):
 
 @pytest.mark.parametrize("multiscale,dtype", [(False, torch.float32), (True, torch.float32), (False, torch.bfloat16)])
 def test_saved_loss_path_equals_recompute_path(g, synth, multiscale, dtype):
-    """SSIMLoss keeps the forward's coefficient maps (gbssim_loss_forward /
-    gbssim_loss_backward); its gradient must match gbssim_ssim_backward, which
-    recomputes them."""
+    """SSIMLoss(recompute=False) keeps the forward's coefficient maps
+    (gbssim_loss_forward / gbssim_loss_backward); the default form recomputes
+    them in the backward (gbssim_ssim_backward).  For SSIM both run the same
+    coefficient kernel on the same inputs, so the gradients agree bit for bit.
+    For MS-SSIM the default form's forward pools through the persistent
+    kernel (another fp32 summation order), so its per-scale means, and with
+    them the factors each level's gradient is scaled by, differ in the last
+    bits (the pooled means differ by about 1e-9): equal to 1e-6 of the largest
+    gradient."""
     x, y = synth.loss_pairs_float(2, 2, 190, 200)
-    xd, yd = x.to(DEV, dtype), y.to(DEV, dtype).requires_grad_(True)
-    loss = g.SSIMLoss(multiscale=multiscale, L=1.0)(xd, yd)
-    loss.backward()
-    xs, ys = xd.detach().reshape(4, 190, 200), yd.detach().reshape(4, 190, 200)
+    xd = x.to(DEV, dtype)
+    ys = y.to(DEV, dtype)
+    grads, losses = [], []
+    for recompute in (True, False):
+        yd = ys.clone().requires_grad_(True)
+        loss = g.SSIMLoss(multiscale=multiscale, recompute=recompute, L=1.0)(xd, yd)
+        loss.backward()
+        grads.append(yd.grad.reshape(4, 190, 200).float())
+        losses.append(loss.item())
+    if multiscale:
+        assert (grads[0] - grads[1]).abs().max().item() <= 1e-6 * grads[1].abs().max().item()
+        assert abs(losses[0] - losses[1]) <= 1e-7  # fp32 partial sums in another order
+    else:
+        assert torch.equal(grads[0], grads[1])
+        assert losses[0] == losses[1]
+    xs, yr = xd.reshape(4, 190, 200), ys.reshape(4, 190, 200)
     kw = dict(exponents=g.MSSSIM_EXPONENTS) if multiscale else {}
-    ref = g.ssim_backward(xs, ys, multiscale=multiscale, grad_scale=-0.25, L=1.0, grad_dtype=torch.float32, **kw)
-    got = yd.grad.reshape(4, 190, 200).float()
+    ref = g.ssim_backward(xs, yr, multiscale=multiscale, grad_scale=-0.25, L=1.0, grad_dtype=torch.float32, **kw)
     tol = 1e-6 if dtype == torch.float32 else 1e-2
-    assert (got - ref).abs().max().item() <= tol * ref.abs().max().item()
-    score = (g.msssim if multiscale else g.ssim)(xs, ys, L=1.0)
-    assert abs(loss.item() - (1.0 - score.mean().item())) <= 1e-7
+    assert (grads[0] - ref).abs().max().item() <= tol * ref.abs().max().item()
+    score = (g.msssim if multiscale else g.ssim)(xs, yr, L=1.0)
+    assert abs(losses[0] - (1.0 - score.mean().item())) <= 1e-7

@@ -67,20 +67,49 @@ def test_streamed_matches_oracle(g, synth, n, h, w):
     assert torch.equal(g.msssim_host(x.pin_memory(), y.pin_memory(), chunks=0), got)
 
 
-def test_streamed_full_size_sampled(g, synth):
+def test_streamed_full_size_all_pairs(g, synth):
     """The end-to-end benchmark step: 64 pinned 1920x1080 pairs streamed
     through one launch (copy groups of 4 pairs, 128-row items at the two
-    largest levels); every score against the device call, sampled pairs
-    (first, middle and last copy group) against the oracle."""
+    largest levels); every score against the device call and against the
+    oracle."""
     n = 64
     x, y = synth.luma_pairs_u8(n, 1080, 1920)
     got = g.msssim_host(x.pin_memory(), y.pin_memory(), chunks=0)
     dev = g.msssim(x.to(DEV), y.to(DEV)).cpu()
     assert torch.isfinite(got).all()
     assert torch.allclose(got, dev, rtol=0, atol=1e-6)
-    for i in (0, 33, 63):
-        s, _ = oracle.msssim(x[i].numpy(), y[i].numpy())
-        assert abs(got[i].item() - s) <= 1e-6
+    xs, ys = x.numpy(), y.numpy()
+    for i in range(n):
+        s, _ = oracle.msssim(xs[i], ys[i])
+        assert abs(got[i].item() - s) <= 1e-6, (i, got[i].item(), s)
+
+
+def test_streamed_arrival_wait_reports_timeout(g, synth):
+    """The test hook leaves the last copy group's arrival flag unset: the
+    level-0 items of its image wait until their bounded wait (16 x wait_limit
+    polls) runs out, the launch records GBSSIM_ERR_TIMEOUT, that image scores
+    NaN, and the call still completes.  37 pairs make copy groups of 3 with a
+    last group of one image."""
+    n = 37
+    x, y = synth.luma_pairs_u8(n, 176, 176)
+    xp, yp = x.pin_memory(), y.pin_memory()
+    dev = g.msssim(x.to(DEV), y.to(DEV)).cpu()
+    status = torch.full((1,), 12345, dtype=torch.int32).pin_memory()
+    t = g.Tuning(0, 0, 4000, g.TUNING_TEST_DROP_ARRIVAL)
+    got = g.msssim_host(xp, yp, chunks=0, tuning=t, status=status)
+    assert status.item() == g.ERR_TIMEOUT
+    assert torch.isnan(got[n - 1])
+    fin = torch.isfinite(got)
+    assert torch.allclose(got[fin], dev[fin], rtol=0, atol=1e-6)
+    # the same buffers again without the hook: every flag set, status OK
+    status.fill_(12345)
+    got = g.msssim_host(xp, yp, chunks=0, tuning=g.Tuning(0, 0, 0, 0), status=status)
+    assert status.item() == 0
+    assert torch.allclose(got, dev, rtol=0, atol=1e-6)
+    # the status word and the hook belong to streamed mode
+    with pytest.raises(g.GbssimError) as e:
+        g.msssim_host(xp, yp, chunks=2, status=status)
+    assert e.value.status == g.ERR_UNSUPPORTED
 
 
 _BLOCKING_SCRIPT = """
