@@ -338,7 +338,7 @@ cudaError_t run_level(const Level &L, const ImgDesc &dx, const ImgDesc &dy, int 
 int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
                           const MsPlan &P, char *ws, double *score_out, double *per_scale_out,
                           cudaStream_t st, const unsigned *arrive = nullptr, int arrive_group = 1,
-                          unsigned wait_limit = 0) {
+                          unsigned wait_limit = 0, bool int_pyramid = true) {
     const int S = p->scales, n = x->count;
     // the persistent path fuses the 2x2 pyramid into valid-window levels
     bool persistent = (p->flags & GBSSIM_FLAG_PYRAMID_97) == 0 && !border_mode(p);
@@ -356,6 +356,10 @@ int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_pa
         U.dtype = x->dtype;
         U.count = n;
         U.scales = S;
+        // uint8 input: pyramid levels 1..4 as exact uint16 planes (4^j times
+        // the level's values, at most 255 x 4^4 = 65280), rows padded to 8
+        // elements; they fit the workspace planned for fp32 levels
+        U.ipyr = int_pyramid && x->dtype == GBSSIM_U8 && S <= 5;
         int64_t begin = 0;
         MsFinalize F;
         memset(&F, 0, sizeof F);
@@ -375,7 +379,8 @@ int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_pa
                 u.vec = ((uintptr_t)x->data % vb == 0) && ((uintptr_t)y->data % vb == 0) && (U.rs % 4 == 0) &&
                         (U.image_stride % 4 == 0);
             } else {
-                u.vec = L.W % 4 == 0;
+                u.pitch = U.ipyr ? (L.W + 7) / 8 * 8 : L.W;
+                u.vec = u.pitch % 4 == 0;
             }
             u.item_begin = begin;
             begin += (int64_t)u.items_per_image * n;
@@ -1512,7 +1517,8 @@ int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbs
             dtype = GBSSIM_F32;
         }
     } else if (multiscale) {
-        rc = msssim_forward(x, y, p, B.fwd, ws, score, per, st);
+        // the coefficient passes below read the fp32 pyramid planes
+        rc = msssim_forward(x, y, p, B.fwd, ws, score, per, st, nullptr, 1, 0, false);
         if (rc) return rc;
     }
     double esum = 0.0;

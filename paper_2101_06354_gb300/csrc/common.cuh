@@ -210,6 +210,7 @@ struct UniformLevel {
     int strips, segs, seg_rows, items_per_image, vec, pad;
     int64_t item_begin;   // first item of this level (level-major order)
     int64_t x_off;        // levels >= 1: x planes of all images, then y planes
+    int64_t pitch;        // levels >= 1: row pitch of those planes, in elements
     int64_t part_off;     // pooling slots: image-major, items_per_image each
 };
 constexpr int kUniformMaxGroups = 16;  // arrival flags (copy groups) of the streamed host mode
@@ -218,6 +219,10 @@ struct UniformBatch {
     const void *x, *y;
     int64_t rs, image_stride;  // level 0, in elements
     int dtype, count, scales;
+    // 1: uint8 input with at most 5 scales; levels >= 1 are uint16 planes
+    // holding 4^j times the level's values (exact), row pitch a multiple of
+    // 8, read by bulk tensor copies.  0: fp32 planes of the 2x2 means.
+    int ipyr;
     UniformLevel lv[GBSSIM_MAX_SCALES];
     int64_t total_items;
     void *ws;

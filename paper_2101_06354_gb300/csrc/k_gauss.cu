@@ -109,6 +109,8 @@ struct Geo {
     int64_t own_r1;    // owned input rows [o0, own_r1) (downsample)
     int64_t own_c1;    // owned input columns [j0, own_c1)
     bool vec;          // rows and strip start aligned for 4-element vector loads
+    bool ds16;         // next level as exact uint16 block sums (else fp32 2x2 means)
+    int64_t ds_ld;     // row pitch of the next level's planes, in elements
 };
 
 // byte k of w placed in the mantissa of 2^23, minus 2^23: exact for 0..255
@@ -164,6 +166,11 @@ template <>
 __device__ __forceinline__ float elem_f32<__nv_bfloat16>(unsigned b) { return __uint_as_float(b << 16); }
 template <>
 __device__ __forceinline__ float elem_f32<float>(unsigned b) { return __uint_as_float(b); }
+// uint16: the exact integer pyramid levels (4^j times the level's values)
+template <>
+__device__ __forceinline__ float elem_f32<uint16_t>(unsigned b) {
+    return __int_as_float(0x4B000000u | (b & 0xffffu)) - 8388608.0f;
+}
 
 template <typename T>
 __device__ __forceinline__ float4 convert_raw(uint4 r, bool packed) {
@@ -186,10 +193,28 @@ __device__ __forceinline__ float2 uw_of_magic(float xm, float ym) {
 __device__ __forceinline__ float u8m(unsigned w, int k) {
     return __int_as_float(__byte_perm(w, 0x4B000000u, 0x7540u + k));
 }
+// 16-bit half h of w as the float 2^23 + half (exact)
+__device__ __forceinline__ float u16m(unsigned w, int h) {
+    return __int_as_float(__byte_perm(w, 0x4B000000u, h ? 0x7532u : 0x7510u));
+}
 
 // Convert a raw unit of x and y (four columns each) into four (u, w) pairs.
 template <typename T>
 __device__ __forceinline__ void convert_uw(uint4 rx, uint4 ry, bool packed, float2 (&o)[4]) {
+    if (std::is_same<T, uint16_t>::value) {
+        if (packed) {
+            o[0] = uw_of_magic(u16m(rx.x, 0), u16m(ry.x, 0));
+            o[1] = uw_of_magic(u16m(rx.x, 1), u16m(ry.x, 1));
+            o[2] = uw_of_magic(u16m(rx.y, 0), u16m(ry.y, 0));
+            o[3] = uw_of_magic(u16m(rx.y, 1), u16m(ry.y, 1));
+        } else {
+            o[0] = uw_of_magic(__int_as_float(0x4B000000u | rx.x), __int_as_float(0x4B000000u | ry.x));
+            o[1] = uw_of_magic(__int_as_float(0x4B000000u | rx.y), __int_as_float(0x4B000000u | ry.y));
+            o[2] = uw_of_magic(__int_as_float(0x4B000000u | rx.z), __int_as_float(0x4B000000u | ry.z));
+            o[3] = uw_of_magic(__int_as_float(0x4B000000u | rx.w), __int_as_float(0x4B000000u | ry.w));
+        }
+        return;
+    }
     if (sizeof(T) == 1) {
         if (packed) {
 #pragma unroll
@@ -297,30 +322,70 @@ __device__ __forceinline__ void load_unit_smem(Raw &R, const Unit &U, const Smem
     }
 }
 
-// 2x2 averages of the owned blocks of a unit (absolute rows r0 + 2p, +1).
+// Sums of the two 2x2 blocks of a unit (columns 0-1 and 2-3 of rows a, b),
+// packed as [block 0 | block 1 << 16]: exact integers.  uint8 rows: each
+// block sum is at most 4 x 255; uint16 rows (a pyramid level j holding 4^j
+// times its values, at most 255 x 4^j): at most 255 x 4^(j+1), which stays
+// below 2^16 up to level 4.  Packed uint8 rows hold bytes 0-3 in one word
+// (even and odd bytes are added in two 16-bit lanes, no carry can cross);
+// packed uint16 rows hold halves 0-1 and 2-3 in two words; unpacked rows hold
+// one element per component.
 template <typename T>
-__device__ __forceinline__ void downsample_unit(const Raw &R, const Unit &U, const Geo &g, int64_t r0, float *dsx,
-                                                float *dsy) {
+__device__ __forceinline__ unsigned block_pair(uint4 a, uint4 b, bool packed) {
+    if (packed) {
+        if (sizeof(T) == 1)
+            return (a.x & 0x00ff00ffu) + ((a.x >> 8) & 0x00ff00ffu) + (b.x & 0x00ff00ffu) + ((b.x >> 8) & 0x00ff00ffu);
+        const unsigned s0 = (a.x & 0xffffu) + (a.x >> 16) + (b.x & 0xffffu) + (b.x >> 16);
+        const unsigned s1 = (a.y & 0xffffu) + (a.y >> 16) + (b.y & 0xffffu) + (b.y >> 16);
+        return s0 | (s1 << 16);
+    }
+    return (a.x + a.y + b.x + b.y) | ((a.z + a.w + b.z + b.w) << 16);
+}
+
+// The next pyramid level from the owned blocks of a unit (absolute rows
+// r0 + 2p, +1): fp32 2x2 means, or (g.ds16, uint8 / uint16 data) exact
+// uint16 block sums, i.e. 4 x the means in the units of this level.
+template <typename T>
+__device__ __forceinline__ void downsample_unit(const Raw &R, const Unit &U, const Geo &g, int64_t r0, void *dsx,
+                                                void *dsy) {
     const int64_t r = r0 + 2 * U.p;  // even: segment and chunk starts are even
     const int64_t Hh = g.H >> 1, Wh = g.W >> 1, Rr = r >> 1;
     if (r >= g.own_r1 || Rr >= Hh) return;
+    const int64_t c = g.j0 + 4 * U.q;
+    const bool b0 = c < g.own_c1 && (c >> 1) < Wh;
+    const bool b1 = c + 2 < g.own_c1 && ((c + 2) >> 1) < Wh;  // implies b0
+    const int64_t o = Rr * g.ds_ld + (c >> 1);
+    if constexpr (std::is_same<T, uint8_t>::value || std::is_same<T, uint16_t>::value) {
+        if (g.ds16) {
+            const unsigned sx = block_pair<T>(R.x0, R.x1, U.packed), sy = block_pair<T>(R.y0, R.y1, U.packed);
+            uint16_t *px = static_cast<uint16_t *>(dsx) + o, *py = static_cast<uint16_t *>(dsy) + o;
+            if (b1) {  // c >> 1 is even and the pitch a multiple of 8: a 4-byte aligned pair
+                *reinterpret_cast<unsigned *>(px) = sx;
+                *reinterpret_cast<unsigned *>(py) = sy;
+            } else if (b0) {
+                *px = (uint16_t)(sx & 0xffffu);
+                *py = (uint16_t)(sy & 0xffffu);
+            }
+            return;
+        }
+    }
     const float4 x0 = convert_raw<T>(R.x0, U.packed), x1 = convert_raw<T>(R.x1, U.packed);
     const float4 y0 = convert_raw<T>(R.y0, U.packed), y1 = convert_raw<T>(R.y1, U.packed);
-    const int64_t c = g.j0 + 4 * U.q;
-    if (c < g.own_c1 && (c >> 1) < Wh) {
-        dsx[Rr * Wh + (c >> 1)] = 0.25f * ((x0.x + x0.y) + (x1.x + x1.y));
-        dsy[Rr * Wh + (c >> 1)] = 0.25f * ((y0.x + y0.y) + (y1.x + y1.y));
+    float *fx = static_cast<float *>(dsx) + o, *fy = static_cast<float *>(dsy) + o;
+    if (b0) {
+        fx[0] = 0.25f * ((x0.x + x0.y) + (x1.x + x1.y));
+        fy[0] = 0.25f * ((y0.x + y0.y) + (y1.x + y1.y));
     }
-    if (c + 2 < g.own_c1 && ((c + 2) >> 1) < Wh) {
-        dsx[Rr * Wh + (c >> 1) + 1] = 0.25f * ((x0.z + x0.w) + (x1.z + x1.w));
-        dsy[Rr * Wh + (c >> 1) + 1] = 0.25f * ((y0.z + y0.w) + (y1.z + y1.w));
+    if (b1) {
+        fx[1] = 0.25f * ((x0.z + x0.w) + (x1.z + x1.w));
+        fy[1] = 0.25f * ((y0.z + y0.w) + (y1.z + y1.w));
     }
 }
 
 // Store a unit into staged rows row0 + 2p, row0 + 2p + 1 (and its pyramid blocks).
 template <typename T>
 __device__ __forceinline__ void store_unit(Smem &S, const Raw &R, const Unit &U, const Geo &g, int64_t r0, int row0,
-                                           float *dsx, float *dsy) {
+                                           void *dsx, void *dsy) {
     if (U.p < 0) return;
     if (dsx) downsample_unit<T>(R, U, g, r0, dsx, dsy);
     put_unit<T>(S, row0 + 2 * U.p, U.q, R.x0, R.y0, U.packed);
@@ -330,7 +395,7 @@ __device__ __forceinline__ void store_unit(Smem &S, const Raw &R, const Unit &U,
 // Stage `nr` (even) input rows starting at absolute row r0 into in rows
 // 0..nr-1 (once per segment, for the first FIRST rows).
 template <typename T, int LD = 0>
-__device__ __forceinline__ void stage_direct(Smem &S, const Geo &g, int64_t r0, int nr, float *dsx, float *dsy) {
+__device__ __forceinline__ void stage_direct(Smem &S, const Geo &g, int64_t r0, int nr, void *dsx, void *dsy) {
     for (int t = threadIdx.x; t < (nr >> 1) * QUADS; t += NT) {
         Unit U;
         make_unit(U, g, t, nr >> 1);
@@ -524,7 +589,10 @@ struct Item {
     bool vec;
     float *map;            // image map base (nullable)
     int64_t map_ld;
-    float *dsx, *dsy;      // next-level planes of this image (nullable)
+    void *dsx, *dsy;       // next-level planes of this image (nullable): fp32, or uint16 when ds16
+    bool ds16;             // uint8 / uint16 data: the next level as exact uint16 block sums
+    int64_t ds_ld;         // row pitch of the next-level planes, in elements
+    float cscale;          // C1, C2 scale (16^j for a uint16 level holding 4^j times its values; else 1)
     float *coef_img;       // COEF mode: A, B, C planes of this image
     double2 *partial;      // this item's (sum Q, sum cs) slot
     const CUtensorMap *tmx, *tmy;  // nullable: bulk-copy maps of the (level-0) x, y planes
@@ -538,7 +606,7 @@ struct Item {
 // reads NaN).
 template <typename T, bool COEF, int LD, bool BULK>
 __device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps<K> &taps, const Taps2<K> &taps2,
-                                             const SsimConst &cc, const CoefOut &co, unsigned &phase, bool &tma_ok) {
+                                             const SsimConst &cc0, const CoefOut &co, unsigned &phase, bool &tma_ok) {
     Geo g;
     g.H = it.H;
     g.W = it.W;
@@ -553,7 +621,19 @@ __device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps
     g.own_r1 = (it.seg == it.segs - 1) ? g.H : g.o0 + it.seg_rows;
     g.own_c1 = (it.strip == it.strips - 1) ? g.W : g.j0 + TW;
     g.vec = it.vec;
+    g.ds16 = it.ds16;
+    g.ds_ld = it.ds_ld;
     const int nchunks = (int)((g.oend - g.o0 + CH - 1) / CH);
+    // SSIM is unchanged when x, y scale by a and C1, C2 by a^2; with a a
+    // power of two every fp32 step scales exactly, so a uint16 level holding
+    // 4^j times its values gives the bits of the unscaled level
+    SsimConst cc = cc0;
+    if (it.cscale != 1.f) {
+        cc.C1 *= it.cscale;
+        cc.C2 *= it.cscale;
+        cc.C1x2 *= it.cscale;
+        cc.C2x2 *= it.cscale;
+    }
 
     KSum accQ, accCS;
     Raw raw;
@@ -656,6 +736,9 @@ __global__ void __launch_bounds__(NT, 3)
     const int64_t dsn = (it.H >> 1) * (it.W >> 1);
     it.dsx = L.ds_x ? L.ds_x + img * dsn : nullptr;
     it.dsy = L.ds_y ? L.ds_y + img * dsn : nullptr;
+    it.ds16 = false;
+    it.ds_ld = it.W >> 1;
+    it.cscale = 1.f;
     it.coef_img = COEF ? L.co.coef + (int64_t)img * 3 * (it.H - HALO) * coef_ld(it.W - HALO) : nullptr;
     it.partial = L.partials + ((int64_t)img * segs + seg) * strips + strip;
     it.tmx = use_tma ? &tmx : nullptr;
@@ -693,6 +776,7 @@ struct Resolved {
     Item it;          // all fields but xb / yb
     const void *xb, *yb;
     int img;          // image index (uniform batches; -1 in ragged ones)
+    int level;        // pyramid level j
     bool pyramid;     // level >= 1: float planes written earlier in this launch
     int done_index;   // completion counter this item bumps
     int dep_index;    // counter it waits on (-1: none)
@@ -705,6 +789,7 @@ struct Resolved {
 struct TableSource {
     BatchTable B;
     __device__ int total() const { return B.total_items; }
+    __device__ bool ipyr() const { return false; }
     __device__ void resolve(int item, char *ws, Resolved &R) const {
         const BatchItem bi = B.items[item];
         const BatchLevel &lv = B.levels[bi.level_index];
@@ -720,11 +805,16 @@ struct TableSource {
         it.vec = lv.vec != 0;
         it.map = nullptr;
         it.map_ld = 0;
-        it.dsx = lv.ds_off >= 0 ? reinterpret_cast<float *>(ws + lv.ds_off) : nullptr;
-        it.dsy = lv.ds_off >= 0 ? it.dsx + (lv.H >> 1) * (lv.W >> 1) : nullptr;
+        float *ds = lv.ds_off >= 0 ? reinterpret_cast<float *>(ws + lv.ds_off) : nullptr;
+        it.dsx = ds;
+        it.dsy = ds ? ds + (lv.H >> 1) * (lv.W >> 1) : nullptr;
+        it.ds16 = false;
+        it.ds_ld = lv.W >> 1;
+        it.cscale = 1.f;
         it.coef_img = nullptr;
         it.partial = reinterpret_cast<double2 *>(ws + lv.part_off) + (int64_t)bi.seg * lv.strips + bi.strip;
         R.pyramid = lv.level > 0;
+        R.level = lv.level;
         R.img = -1;
         if (lv.level == 0) {
             R.xb = lv.x;
@@ -747,6 +837,7 @@ struct TableSource {
 struct UniformSource {
     UniformBatch U;
     __device__ int total() const { return (int)U.total_items; }
+    __device__ bool ipyr() const { return U.ipyr != 0; }
     __device__ void resolve(int item, char *ws, Resolved &R) const {
         int j = 0, img, rem;
         if (U.waves > 0) {
@@ -777,7 +868,7 @@ struct UniformSource {
         Item &it = R.it;
         it.H = lv.H;
         it.W = lv.W;
-        it.rs = j == 0 ? U.rs : lv.W;
+        it.rs = j == 0 ? U.rs : lv.pitch;
         it.strip = strip;
         it.seg = seg;
         it.strips = lv.strips;
@@ -786,25 +877,34 @@ struct UniformSource {
         it.vec = lv.vec != 0;
         it.map = nullptr;
         it.map_ld = 0;
-        const int64_t plane = lv.H * lv.W;
+        // pyramid planes (levels >= 1): fp32, or uint16 holding 4^j times the
+        // level's values (U.ipyr); each x plane of the level, then each y plane
+        const int64_t esz_p = U.ipyr ? 2 : 4;
+        const int64_t plane = lv.H * lv.pitch;
+        it.ds16 = U.ipyr != 0;
+        it.cscale = (U.ipyr && j > 0) ? __int_as_float((127 + 4 * j) << 23) : 1.f;  // 16^j
         if (j + 1 < U.scales) {
-            const int64_t nplane = (lv.H >> 1) * (lv.W >> 1);
-            it.dsx = reinterpret_cast<float *>(ws + U.lv[j + 1].x_off) + img * nplane;
-            it.dsy = reinterpret_cast<float *>(ws + U.lv[j + 1].x_off) + (U.count + img) * nplane;
+            const UniformLevel &nv = U.lv[j + 1];
+            const int64_t nplane = nv.H * nv.pitch;
+            it.dsx = ws + nv.x_off + esz_p * img * nplane;
+            it.dsy = ws + nv.x_off + esz_p * (U.count + img) * nplane;
+            it.ds_ld = nv.pitch;
         } else {
             it.dsx = it.dsy = nullptr;
+            it.ds_ld = 0;
         }
         it.coef_img = nullptr;
         it.partial = reinterpret_cast<double2 *>(ws + lv.part_off) + (int64_t)img * lv.items_per_image + rem;
         R.pyramid = j > 0;
+        R.level = j;
         R.img = img;
         if (j == 0) {
             const size_t esz = U.dtype == GBSSIM_U8 ? 1 : U.dtype == GBSSIM_F32 ? 4 : 2;
             R.xb = static_cast<const char *>(U.x) + esz * img * U.image_stride;
             R.yb = static_cast<const char *>(U.y) + esz * img * U.image_stride;
         } else {
-            R.xb = reinterpret_cast<const float *>(ws + lv.x_off) + img * plane;
-            R.yb = reinterpret_cast<const float *>(ws + lv.x_off) + (U.count + img) * plane;
+            R.xb = ws + lv.x_off + esz_p * img * plane;
+            R.yb = ws + lv.x_off + esz_p * (U.count + img) * plane;
         }
         R.arrive = (j == 0 && U.arrive) ? U.arrive + img / U.arrive_group : nullptr;
         R.done_index = img * U.scales + j;
@@ -813,16 +913,29 @@ struct UniformSource {
     }
 };
 
+// Bulk-copy maps of the uint16 pyramid levels 1..4 (x and y planes of all
+// images of a level; the image index is the third coordinate).
+constexpr int kPyrMaps = 4;
+struct PyrMaps {
+    CUtensorMap x[kPyrMaps], y[kPyrMaps];
+};
+
 // BULK: level-0 items (uniform batches) take their chunks by bulk tensor
-// copies (tmx, tmy; the image index is the map's third coordinate); pyramid
-// levels keep register staging (their planes are written in this launch).
-// After a bulk-copy wait gives up, the CTA's remaining level-0 items write NaN
-// partials.  Without BULK the launch needs the shared memory up to `raw` only.
+// copies (tmx, tmy; the image index is the map's third coordinate).  Pyramid
+// levels: with uint8 input and the uint16 pyramid (src.ipyr()), their
+// uint16 planes too (pm, written earlier in this launch: the writers fence
+// their generic stores against the async proxy before releasing the level's
+// completion count, the reader fences after acquiring it); otherwise fp32
+// planes by register staging.  After a bulk-copy wait gives up, the CTA's
+// remaining bulk-copied items write NaN partials.  Without BULK the launch
+// needs the shared memory up to `raw` only.
 template <typename T, typename Src, bool BULK>
 __global__ void __launch_bounds__(NT, 3)
     gauss11_persistent_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy,
-                              const Src src, void *ws_ptr, int64_t counter_off, int64_t done_off,
-                              int64_t status_off, unsigned wait_limit, Taps<K> taps, Taps2<K> taps2, SsimConst cc) {
+                              const __grid_constant__ PyrMaps pm, const Src src, void *ws_ptr, int64_t counter_off,
+                              int64_t done_off, int64_t status_off, unsigned wait_limit, Taps<K> taps, Taps2<K> taps2,
+                              SsimConst cc) {
+    constexpr bool kIpyr = BULK && std::is_same<T, uint8_t>::value && std::is_same<Src, UniformSource>::value;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
     if (BULK && threadIdx.x == 0) {
@@ -864,6 +977,8 @@ __global__ void __launch_bounds__(NT, 3)
                         }
                         __nanosleep(256);
                     }
+                    // bulk copies below may read the level this wait acquired
+                    if (kIpyr) fence_proxy_async_global();
                 }
                 if (R.arrive) {  // the image's bytes are still being copied in (bounded: 16x the level limit)
                     unsigned long long spins = 0;
@@ -891,8 +1006,23 @@ __global__ void __launch_bounds__(NT, 3)
         R.it.tmx = BULK ? &tmx : nullptr;
         R.it.tmy = BULK ? &tmy : nullptr;
         R.it.tz = R.img;
-        if (R.pyramid) gauss11_item<float, false, 1, false>(S, R.it, taps, taps2, cc, co, phase, tma_ok);
-        else gauss11_item<T, false, BULK ? 1 : 0, BULK>(S, R.it, taps, taps2, cc, co, phase, tma_ok);
+        if (R.pyramid) {
+            if constexpr (kIpyr) {
+                if (src.ipyr()) {
+                    R.it.tmx = &pm.x[R.level - 1];
+                    R.it.tmy = &pm.y[R.level - 1];
+                    gauss11_item<uint16_t, false, 1, true>(S, R.it, taps, taps2, cc, co, phase, tma_ok);
+                } else {
+                    gauss11_item<float, false, 1, false>(S, R.it, taps, taps2, cc, co, phase, tma_ok);
+                }
+            } else {
+                gauss11_item<float, false, 1, false>(S, R.it, taps, taps2, cc, co, phase, tma_ok);
+            }
+        } else {
+            gauss11_item<T, false, BULK ? 1 : 0, BULK>(S, R.it, taps, taps2, cc, co, phase, tma_ok);
+        }
+        // the next level's planes are read by bulk copies of other CTAs
+        if (kIpyr && R.it.dsx) fence_proxy_async_global();
         __syncthreads();  // every thread's partial and pyramid stores issued
         if (threadIdx.x == 0) {
             if (s_late) *R.it.partial = make_double2(nan(""), nan(""));  // the score reads NaN
@@ -989,10 +1119,11 @@ __global__ void __launch_bounds__(GT *GT) generic_kernel(const GenericLaunch L, 
 
 template <typename T>
 constexpr CUtensorMapDataType tma_dtype() {
-    return sizeof(T) == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
-                          : sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                           : (std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                                                              : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    return sizeof(T) == 1                      ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+           : sizeof(T) == 4                    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+           : std::is_same<T, uint16_t>::value ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+           : std::is_same<T, __half>::value   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                               : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
 }
 
 // Bulk-copy map of a batch of planes (columns, rows, image) with
@@ -1076,7 +1207,8 @@ cudaError_t launch_gauss11(const GaussLaunch &L, cudaStream_t st) {
 template <typename T, typename Src>
 cudaError_t launch_persistent_t(const Src &src, void *ws, int64_t counter_off, int64_t done_off, int64_t status_off,
                                 unsigned wait_limit, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st,
-                                const CUtensorMap *mx = nullptr, const CUtensorMap *my = nullptr) {
+                                const CUtensorMap *mx = nullptr, const CUtensorMap *my = nullptr,
+                                const PyrMaps *pm = nullptr) {
     constexpr bool can_bulk = std::is_same<Src, UniformSource>::value;
     static DeviceOnce attr_set;
     int dev = 0;
@@ -1093,10 +1225,12 @@ cudaError_t launch_persistent_t(const Src &src, void *ws, int64_t counter_off, i
     }
     Taps2<11> t2;
     for (int n = 0; n < 11; ++n) t2.g2[n] = make_float2(taps.g[n], taps.g[n]);
+    PyrMaps none;
+    memset(&none, 0, sizeof none);
     if constexpr (can_bulk) {
         if (mx && my) {
             gauss11_persistent_kernel<T, Src, true><<<grid, NT, sizeof(Smem), st>>>(
-                *mx, *my, src, ws, counter_off, done_off, status_off, wait_limit, taps, t2, cc);
+                *mx, *my, pm ? *pm : none, src, ws, counter_off, done_off, status_off, wait_limit, taps, t2, cc);
             return cudaGetLastError();
         }
     }
@@ -1104,7 +1238,7 @@ cudaError_t launch_persistent_t(const Src &src, void *ws, int64_t counter_off, i
     memset(&zx, 0, sizeof zx);
     memset(&zy, 0, sizeof zy);
     gauss11_persistent_kernel<T, Src, false><<<grid, NT, kSmemNoBulk, st>>>(
-        zx, zy, src, ws, counter_off, done_off, status_off, wait_limit, taps, t2, cc);
+        zx, zy, none, src, ws, counter_off, done_off, status_off, wait_limit, taps, t2, cc);
     return cudaGetLastError();
 }
 
@@ -1147,8 +1281,8 @@ cudaError_t launch_batch(const BatchTable &B, const Taps<11> &taps, SsimConst cc
 }
 
 template <typename T>
-cudaError_t launch_uniform_t(const UniformBatch &U, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st) {
-    UniformSource src{U};
+cudaError_t launch_uniform_t(const UniformBatch &U0, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st) {
+    UniformBatch U = U0;
     CUtensorMap mx, my;
     const bool bulk = encode_plane_map<T>(&mx, U.x, U.lv[0].H, U.lv[0].W, U.rs, U.image_stride, U.count) &&
                       encode_plane_map<T>(&my, U.y, U.lv[0].H, U.lv[0].W, U.rs, U.image_stride, U.count);
@@ -1156,8 +1290,29 @@ cudaError_t launch_uniform_t(const UniformBatch &U, const Taps<11> &taps, SsimCo
     // go through the read-only data cache, which bytes copied in during the
     // launch must not.
     if (U.arrive && !bulk) return cudaErrorNotSupported;
+    // The uint16 pyramid is read by bulk copies only: it needs the bulk
+    // variant (aligned level-0 planes) and a map per level; else the levels
+    // fall back to fp32 planes (the workspace holds either layout).
+    PyrMaps pm;
+    memset(&pm, 0, sizeof pm);
+    bool ipyr = U.ipyr && std::is_same<T, uint8_t>::value && bulk && U.scales - 1 <= kPyrMaps;
+    for (int j = 1; ipyr && j < U.scales; ++j) {
+        const UniformLevel &l = U.lv[j];
+        char *xb = static_cast<char *>(U.ws) + l.x_off;
+        const int64_t plane = l.H * l.pitch;
+        ipyr = encode_plane_map<uint16_t>(&pm.x[j - 1], xb, l.H, l.W, l.pitch, plane, U.count) &&
+               encode_plane_map<uint16_t>(&pm.y[j - 1], xb + 2 * plane * U.count, l.H, l.W, l.pitch, plane, U.count);
+    }
+    if (!ipyr && U.ipyr) {
+        U.ipyr = 0;
+        for (int j = 1; j < U.scales; ++j) {
+            U.lv[j].pitch = U.lv[j].W;
+            U.lv[j].vec = U.lv[j].W % 4 == 0;
+        }
+    }
+    UniformSource src{U};
     return launch_persistent_t<T>(src, U.ws, U.counter_off, U.done_off, U.status_off, U.wait_limit, taps, cc, grid,
-                                  st, bulk ? &mx : nullptr, bulk ? &my : nullptr);
+                                  st, bulk ? &mx : nullptr, bulk ? &my : nullptr, ipyr ? &pm : nullptr);
 }
 
 cudaError_t launch_uniform(const UniformBatch &U, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st) {
