@@ -584,8 +584,10 @@ def run_gbssim(args):
 
 
 def run_case(args):
-    """One of the bench's secondary workloads alone, `warmup` + `steps` calls,
-    for profilers: scale0 = gbssim_ssim_map on the 64 1080p pairs (the
+    """One of the bench's workloads alone, `warmup` + `steps` calls, for
+    profilers: msssim = the benchmark step itself (gbssim_msssim on the 64
+    1080p pairs: one persistent launch + finaliser); scale0 = gbssim_ssim_map
+    on the 64 1080p pairs (the
     scale-0 Gaussian level); box8s4 = the 8x8 stride-4 box SSIM on them;
     loss = SSIMLoss forward + backward on 32x3x512x512 fp32; ssim3d = SSIM-3D
     (11 x 11 x 5) of 40 luma frames of 1920x1080; msssim3d = MS-SSIM-3D (5
@@ -602,7 +604,13 @@ def run_case(args):
     from paper_2101_06354_gb300 import gbssim, synth
 
     dev = torch.device("cuda", 0)
-    if args.case in ("scale0", "box8s4"):
+    if args.case == "msssim":
+        x, y = synth.luma_pairs_u8(N_PAIRS, H, W)
+        x, y = x.to(dev), y.to(dev)
+        wsm = gbssim.workspace(gbssim.plane(x), gbssim.make_params(exponents=gbssim.MSSSIM_EXPONENTS),
+                               gbssim.OP_MSSSIM, dev)
+        fn = lambda: gbssim.msssim(x, y, ws=wsm)
+    elif args.case in ("scale0", "box8s4"):
         x, y = synth.luma_pairs_u8(N_PAIRS, H, W)
         x, y = x.to(dev), y.to(dev)
         kw = {} if args.case == "scale0" else dict(window="box", k=8, stride=4)
@@ -661,7 +669,7 @@ def main():
                     help="host pipeline of the end-to-end leg: 0 streams, N >= 1 double-buffers N chunks (the "
                          "form to run under a profiler that serialises launches: a streamed launch waits for "
                          "copies on another stream)")
-    ap.add_argument("--case", choices=["scale0", "box8s4", "loss", "ssim3d", "msssim3d", "ragged", "pool"],
+    ap.add_argument("--case", choices=["msssim", "scale0", "box8s4", "loss", "ssim3d", "msssim3d", "ragged", "pool"],
                     default=None,
                     help="run one secondary workload alone (for profilers) instead of the benchmark")
     args = ap.parse_args()

@@ -193,28 +193,10 @@ __device__ __forceinline__ float2 uw_of_magic(float xm, float ym) {
 __device__ __forceinline__ float u8m(unsigned w, int k) {
     return __int_as_float(__byte_perm(w, 0x4B000000u, 0x7540u + k));
 }
-// 16-bit half h of w as the float 2^23 + half (exact)
-__device__ __forceinline__ float u16m(unsigned w, int h) {
-    return __int_as_float(__byte_perm(w, 0x4B000000u, h ? 0x7532u : 0x7510u));
-}
 
 // Convert a raw unit of x and y (four columns each) into four (u, w) pairs.
 template <typename T>
 __device__ __forceinline__ void convert_uw(uint4 rx, uint4 ry, bool packed, float2 (&o)[4]) {
-    if (std::is_same<T, uint16_t>::value) {
-        if (packed) {
-            o[0] = uw_of_magic(u16m(rx.x, 0), u16m(ry.x, 0));
-            o[1] = uw_of_magic(u16m(rx.x, 1), u16m(ry.x, 1));
-            o[2] = uw_of_magic(u16m(rx.y, 0), u16m(ry.y, 0));
-            o[3] = uw_of_magic(u16m(rx.y, 1), u16m(ry.y, 1));
-        } else {
-            o[0] = uw_of_magic(__int_as_float(0x4B000000u | rx.x), __int_as_float(0x4B000000u | ry.x));
-            o[1] = uw_of_magic(__int_as_float(0x4B000000u | rx.y), __int_as_float(0x4B000000u | ry.y));
-            o[2] = uw_of_magic(__int_as_float(0x4B000000u | rx.z), __int_as_float(0x4B000000u | ry.z));
-            o[3] = uw_of_magic(__int_as_float(0x4B000000u | rx.w), __int_as_float(0x4B000000u | ry.w));
-        }
-        return;
-    }
     if (sizeof(T) == 1) {
         if (packed) {
 #pragma unroll
@@ -234,12 +216,63 @@ __device__ __forceinline__ void convert_uw(uint4 rx, uint4 ry, bool packed, floa
     o[3] = uw_of(a.w, b.w);
 }
 
+// Integer data (uint8, or the uint16 pyramid levels) is staged as BIASED
+// magic floats formed in integer lanes, with no FP32 work: u' = 2^23 + u and
+// w' = 2^23 + B + w, B the largest |w| (255 or 65535).  Both lie in
+// [2^23, 2^24), where fp32 holds every integer, and the horizontal pass only
+// ever forms differences of staged values (exact) and adds the bias back
+// once per group of four outputs.
+template <typename T>
+constexpr bool kBiasedStaging = std::is_same<T, uint8_t>::value || std::is_same<T, uint16_t>::value;
+template <typename T>
+__device__ __forceinline__ float2 staging_bias() {
+    return make_float2(8388608.0f, sizeof(T) == 1 ? 8388863.0f : 8454143.0f);  // 2^23, 2^23 + 255 / 65535
+}
+__device__ __forceinline__ float magic(unsigned v) { return __int_as_float(0x4B000000u | v); }
+
 // Store one staged unit: columns 4q..4q+3 as (u, w) pairs.
 template <typename T>
 __device__ __forceinline__ void put_unit(Smem &S, int r, int q, uint4 rx, uint4 ry, bool packed) {
+    float4 *d = reinterpret_cast<float4 *>(&S.in[r][4 * q]);
+    if constexpr (kBiasedStaging<T>) {
+        unsigned u[4], w[4];
+        if (sizeof(T) == 1 && packed) {
+            // even and odd bytes in two 16-bit lanes each: u <= 510 and
+            // w + 255 in [0, 510], so no carry or borrow crosses a lane
+            const unsigned xe = rx.x & 0x00ff00ffu, xo = (rx.x >> 8) & 0x00ff00ffu;
+            const unsigned ye = ry.x & 0x00ff00ffu, yo = (ry.x >> 8) & 0x00ff00ffu;
+            const unsigned ue = xe + ye, uo = xo + yo;
+            const unsigned we = xe + 0x00ff00ffu - ye, wo = xo + 0x00ff00ffu - yo;
+            d[0] = make_float4(__int_as_float(__byte_perm(ue, 0x4B000000u, 0x7510u)),
+                               __int_as_float(__byte_perm(we, 0x4B000000u, 0x7510u)),
+                               __int_as_float(__byte_perm(uo, 0x4B000000u, 0x7510u)),
+                               __int_as_float(__byte_perm(wo, 0x4B000000u, 0x7510u)));
+            d[1] = make_float4(__int_as_float(__byte_perm(ue, 0x4B000000u, 0x7532u)),
+                               __int_as_float(__byte_perm(we, 0x4B000000u, 0x7532u)),
+                               __int_as_float(__byte_perm(uo, 0x4B000000u, 0x7532u)),
+                               __int_as_float(__byte_perm(wo, 0x4B000000u, 0x7532u)));
+            return;
+        }
+        unsigned xv[4], yv[4];
+        if (sizeof(T) == 2 && packed) {
+            xv[0] = rx.x & 0xffffu, xv[1] = rx.x >> 16, xv[2] = rx.y & 0xffffu, xv[3] = rx.y >> 16;
+            yv[0] = ry.x & 0xffffu, yv[1] = ry.x >> 16, yv[2] = ry.y & 0xffffu, yv[3] = ry.y >> 16;
+        } else {  // one element per component
+            xv[0] = rx.x, xv[1] = rx.y, xv[2] = rx.z, xv[3] = rx.w;
+            yv[0] = ry.x, yv[1] = ry.y, yv[2] = ry.z, yv[3] = ry.w;
+        }
+        const unsigned B = sizeof(T) == 1 ? 255u : 65535u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            u[k] = xv[k] + yv[k];
+            w[k] = xv[k] + B - yv[k];
+        }
+        d[0] = make_float4(magic(u[0]), magic(w[0]), magic(u[1]), magic(w[1]));
+        d[1] = make_float4(magic(u[2]), magic(w[2]), magic(u[3]), magic(w[3]));
+        return;
+    }
     float2 o[4];
     convert_uw<T>(rx, ry, packed, o);
-    float4 *d = reinterpret_cast<float4 *>(&S.in[r][4 * q]);
     d[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
     d[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
 }
@@ -411,7 +444,7 @@ __device__ __forceinline__ void stage_direct(Smem &S, const Geo &g, int64_t r0, 
 // quarter-warp (8 lanes) lanes 0-3 and 4-7 take 4 consecutive groups of 4
 // outputs of the first and the second row.
 template <int NR>
-__device__ __forceinline__ void horizontal(Smem &S, int rel0, const Taps2<K> &t2) {
+__device__ __forceinline__ void horizontal(Smem &S, int rel0, const Taps2<K> &t2, float2 bias) {
     static_assert(NR % 2 == 0, "rows come in pairs");
 #pragma unroll 1
     for (int pass = 0; pass < (NR * (TW / 4) + NT - 1) / NT; ++pass) {
@@ -447,7 +480,7 @@ __device__ __forceinline__ void horizontal(Smem &S, int rel0, const Taps2<K> &t2
             }
         }
         const int slot = (rel0 + r) & (RING - 1);
-        const float2 cc = make_float2(-nc.x, -nc.y);
+        const float2 cc = add2(p[7], make_float2(-bias.x, -bias.y));  // the shift, unbiased (exact)
         float2 om[4], ov[4];
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
@@ -650,7 +683,8 @@ __device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps
 
     stage_direct<T, LD>(S, g, g.o0, FIRST, it.dsx, it.dsy);
     __syncthreads();
-    horizontal<FIRST>(S, 0, taps2);
+    const float2 bias = kBiasedStaging<T> ? staging_bias<T>() : make_float2(0.f, 0.f);
+    horizontal<FIRST>(S, 0, taps2, bias);
     if constexpr (!BULK) {
         for (int c = 0; c < nchunks; ++c) {
             const bool more = c + 1 < nchunks;
@@ -663,7 +697,7 @@ __device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps
             accCS.add(ccs);
             if (more) store_unit<T>(S, raw, U, g, next_r0, 0, it.dsx, it.dsy);
             __syncthreads();  // staging complete; ring rows of chunk c consumed
-            if (more) horizontal<CH>(S, FIRST + CH * c, taps2);
+            if (more) horizontal<CH>(S, FIRST + CH * c, taps2, bias);
         }
     } else {
         for (int c = 0; c < nchunks; ++c) {
@@ -700,7 +734,7 @@ __device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps
                 __syncthreads();
                 return;
             }
-            if (more) horizontal<CH>(S, FIRST + CH * c, taps2);
+            if (more) horizontal<CH>(S, FIRST + CH * c, taps2, bias);
         }
     }
     double a, b;
