@@ -132,17 +132,32 @@ int level_items(Path path, int64_t H, int64_t W, int count, const gbssim_params 
     }
 }
 
-// Rows per work item of the persistent MS-SSIM path at pyramid level j.
-// Level 0 takes long items (the ragged-batch autotuner's choice on 1080p /
-// 4K batches); the small upper levels take short ones, which shortens the
-// chain of dependent items of the last images at the end of the launch.
+// Rows per work item of the persistent MS-SSIM path at pyramid level j
+// (OH output rows, strips x count items per segment row).  Level 0 takes
+// items as long as a frame (every item restages its first 26 rows and pays
+// its fetch, so fewer, longer items win); the upper levels take about two
+// segments each, which keeps the chain of dependent items of the last images
+// short at the end of the launch.  Segments are balanced (no short
+// remainder item), a multiple of 16 rows, and there are at least about two
+// waves of the 152 SMs x 3 CTAs at every level when the level has the rows.
 // Streamed launches (inputs still arriving) take short items at the two
-// large levels too: the chain after the last copy lands is the step's tail,
+// large levels: the chain after the last copy lands is the step's tail,
 // while the extra halo rows cost time the copies leave idle.
-int persistent_seg_rows(int j, bool streamed) {
-    static const int rows[5] = {512, 256, 128, 64, 32}, streamed_rows[5] = {128, 128, 64, 32, 32};
-    const int *r = streamed ? streamed_rows : rows;
-    return j < 5 ? r[j] : r[4];
+int persistent_seg_rows(int j, bool streamed, int64_t OH, int64_t strips, int count) {
+    static const int streamed_rows[5] = {128, 128, 64, 32, 32};
+    if (streamed) return j < 5 ? streamed_rows[j] : streamed_rows[4];
+    static const int target[5] = {1100, 384, 192, 96, 48};
+    const int64_t t = j < 5 ? target[j] : target[4];
+    int64_t n = (OH + t - 1) / t;
+    const int64_t want = 912, per = strips * (int64_t)count;
+    if (n * per < want) {
+        const int64_t m = (want + per - 1) / per, cap = (OH + 31) / 32;
+        n = m < cap ? m : cap;
+        if (n < 1) n = 1;
+    }
+    int64_t r = (OH + n - 1) / n;
+    r = (r + 15) / 16 * 16;
+    return (int)(r < 16 ? 16 : r);
 }
 
 struct Level {
@@ -192,7 +207,7 @@ int plan_levels(const gbssim_plane *x, const gbssim_params *p, int scales, MsPla
         L.pitems = 0;
         if (L.path == PATH_GAUSS11 && !border) {
             int strips, segs;
-            L.pseg_rows = persistent_seg_rows(j, streamed);
+            L.pseg_rows = persistent_seg_rows(j, streamed, H - 10, (W - 10 + 63) / 64, x->count);
             L.pitems = gauss11_items(H, W, L.pseg_rows, &strips, &segs);
         }
         L.part_off = off;  // pooling slots for whichever layout runs
