@@ -458,6 +458,210 @@ __global__ void __launch_bounds__(NT, sizeof(A) == 4 ? 4 : 2)
     if (threadIdx.x == 0 && pending >= 0) flush(pending);
 }
 
+// ----------------------------------------------------------------- uint8, 11 x 11 x kt, int32 sums
+//
+// The SSIM-3D hot case (uint8 video, k = 11, int32 sums, bulk copies) keeps
+// the tile's temporal sums in REGISTERS: thread (q, c) owns quantity q (u, w,
+// u^2 or w^2 of (u, w) = (x + y, x - y)) of input column c for all 26 rows,
+// adds frame f and subtracts frame f - kt straight from the bulk-copied
+// bytes, and forms the 16 k-row sums of its column in registers (running
+// sums down the column); only those column sums go to shared memory, double
+// buffered, so one barrier per frame separates a frame's column sums from
+// the row pass that reads them while the next frame's column pass writes the
+// other buffer.  The row pass (running sums over 11 column sums, 4 outputs
+// per thread, 256 threads) and the formula are those of ssim3d_kernel.
+constexpr int NTC = 320;                 // 4 quantities x 80 column slots (74 used)
+constexpr int KC = 11;                   // window width and height
+constexpr int OHC = 16;                  // output rows per tile (as Tile3<int>)
+constexpr int IHC = OHC + KC - 1;        // 26 input rows
+constexpr int IWC = OW3 + KC - 1;        // 74 input columns
+constexpr int PVC = 20;                  // pitch of the column sums: 4 PVC = 16 mod 32 (row pass), int4 stores
+constexpr int SEGC = 4;                  // outputs per row-pass thread
+constexpr int T3C = OHC * (OW3 / SEGC);  // 256 row-pass threads (warps 2..9)
+constexpr int RWC = raw3_width(KC);      // 80 bytes per bulk-copied row
+constexpr int TILEC = (IHC * RWC + 127) & ~127;
+struct __align__(128) S3C {
+    unsigned char raw[4][TILEC];   // x, y of frame f; x, y of frame f - kt
+    int vs[2][4][IWC][PVC];        // column sums [buffer][quantity][column][row]
+    double2 red[2][T3C / 32];      // row-pass warp sums [buffer][warp]
+    unsigned long long bar;
+};
+
+__global__ void __launch_bounds__(NTC, 3)
+    ssim3d_cols_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy,
+                       const Ssim3dLaunch L, int tiles_x, int tiles_y, int t_chunk) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    S3C &S = *reinterpret_cast<S3C *>(smem_raw);
+    const int tiles = tiles_x * tiles_y;
+    const int tile = blockIdx.x % tiles;
+    const int t_begin = (blockIdx.x / tiles) * t_chunk;
+    const int t_end = min(t_begin + t_chunk, L.T - L.kt + 1);
+    const int f_begin = t_begin, f_end = t_end + L.kt - 1;
+    const int tx = tile % tiles_x, ty = tile / tiles_x;
+    const int64_t OHt = L.x.H - KC + 1, OWt = L.x.W - KC + 1;
+    const int64_t x0 = (int64_t)tx * OW3, y0 = (int64_t)ty * OHC;
+    const int64_t N = (int64_t)KC * KC * L.kt;
+    constexpr unsigned tile_bytes = IHC * RWC;
+    auto issue = [&](int ff) {  // thread 0: the tiles of frame ff (and of ff - kt once it leaves a window)
+        const bool with_old = ff - L.kt >= f_begin;
+        mbar_expect_tx(&S.bar, (with_old ? 4u : 2u) * tile_bytes);
+        tma_load_3d(S.raw[0], &tmx, (int)x0, (int)y0, ff, &S.bar);
+        tma_load_3d(S.raw[1], &tmy, (int)x0, (int)y0, ff, &S.bar);
+        if (with_old) {
+            tma_load_3d(S.raw[2], &tmx, (int)x0, (int)y0, ff - L.kt, &S.bar);
+            tma_load_3d(S.raw[3], &tmy, (int)x0, (int)y0, ff - L.kt, &S.bar);
+        }
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&S.bar, 1);
+        fence_mbar_init();
+        issue(f_begin);
+    }
+    __syncthreads();
+    // column thread: quantity q (0 u, 1 w, 2 u^2, 3 w^2), input column c
+    const int q = threadIdx.x / 80, c = threadIdx.x - 80 * q;
+    const bool col = c < IWC;
+    const int sgn = (q & 1) ? -1 : 1;  // w = x - y
+    const bool sq = q >= 2;
+    int T[IHC];
+#pragma unroll
+    for (int r = 0; r < IHC; ++r) T[r] = 0;
+    unsigned phase = 0;
+    int pending = -1;  // output frame whose warp sums wait in red[pending_buf]
+    int pending_buf = 0;
+    for (int f = f_begin; f < f_end; ++f) {
+        const bool old = f - L.kt >= f_begin;
+        const bool ok = mbar_wait_bounded(&S.bar, phase);
+        phase ^= 1u;
+        const bool out_frame = f >= f_begin + L.kt - 1;
+        const int buf = f & 1;
+        if (ok && col) {
+            const unsigned char *rx = S.raw[0] + c, *ry = S.raw[1] + c;
+            if (old) {
+                const unsigned char *ox = S.raw[2] + c, *oy = S.raw[3] + c;
+#pragma unroll
+                for (int r = 0; r < IHC; ++r) {
+                    const int a = (int)rx[r * RWC] + sgn * (int)ry[r * RWC];
+                    const int ao = (int)ox[r * RWC] + sgn * (int)oy[r * RWC];
+                    const int d = a - ao;
+                    T[r] += sq ? d * (a + ao) : d;  // u^2 - uo^2 = (u - uo)(u + uo)
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < IHC; ++r) {
+                    const int a = (int)rx[r * RWC] + sgn * (int)ry[r * RWC];
+                    T[r] += sq ? a * a : a;
+                }
+            }
+            if (out_frame) {
+                int v[OHC];
+                int sum = 0;
+#pragma unroll
+                for (int m = 0; m < KC; ++m) sum += T[m];
+                v[0] = sum;
+#pragma unroll
+                for (int i = 1; i < OHC; ++i) {
+                    sum += T[i + KC - 1] - T[i - 1];
+                    v[i] = sum;
+                }
+                int4 *dst = reinterpret_cast<int4 *>(&S.vs[buf][q][c][0]);
+#pragma unroll
+                for (int i = 0; i < OHC / 4; ++i) dst[i] = make_int4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                mbar_wait_bounded(&S.bar, phase ^ 1u);  // drain the copy that did not complete (bounded)
+                for (int tt = max(t_begin, f - L.kt); tt < t_end; ++tt)
+                    L.partials[(int64_t)tt * tiles + tile] = make_double2(nan(""), nan(""));
+            }
+            return;
+        }
+        if (threadIdx.x == 0) {
+            if (pending >= 0) {
+                double sq_ = 0.0, sc_ = 0.0;
+#pragma unroll
+                for (int w = 0; w < T3C / 32; ++w) {
+                    sq_ += S.red[pending_buf][w].x;
+                    sc_ += S.red[pending_buf][w].y;
+                }
+                L.partials[(int64_t)pending * tiles + tile] = make_double2(sq_, sc_);
+                pending = -1;
+            }
+            // every column thread is done with this frame's tiles: refill them
+            if (f + 1 < f_end) {
+                fence_proxy_async_smem();
+                issue(f + 1);
+            }
+        }
+        if (!out_frame) continue;
+        const int t = f - L.kt + 1;
+        if (threadIdx.x >= NTC - T3C) {
+            const int s3 = threadIdx.x - (NTC - T3C);
+            const int i = s3 % OHC, j0 = (s3 / OHC) * SEGC;
+            const int64_t a = y0 + i;
+            float accQ = 0.f, accC = 0.f;
+            if (a < OHt && x0 + j0 < OWt) {
+                const int *v0 = &S.vs[buf][0][j0][i], *v1 = &S.vs[buf][1][j0][i];
+                const int *v2 = &S.vs[buf][2][j0][i], *v3 = &S.vs[buf][3][j0][i];
+                int su = 0, sw = 0, su2 = 0, sw2 = 0;
+#pragma unroll
+                for (int m = 0; m < KC; ++m) {
+                    su += v0[m * PVC];
+                    sw += v1[m * PVC];
+                    su2 += v2[m * PVC];
+                    sw2 += v3[m * PVC];
+                }
+                const int nout = (int)min((int64_t)SEGC, OWt - (x0 + j0));
+                float *mrow = L.map ? L.map + t * L.map_fs + a * L.map_ld + x0 + j0 : nullptr;
+#pragma unroll
+                for (int e = 0; e < SEGC; ++e) {
+                    if (e > 0) {
+                        const int in = (e + KC - 1) * PVC, out = (e - 1) * PVC;
+                        su += v0[in] - v0[out];
+                        sw += v1[in] - v1[out];
+                        su2 += v2[in] - v2[out];
+                        sw2 += v3[in] - v3[out];
+                    }
+                    if (e < nout) {
+                        // |Su|, |Sw| <= 510 N < 2^23: exact in fp32; Su^2 - Sw^2 = (Su - Sw)(Su + Sw) rounds once
+                        const float fu = (float)su, fw = (float)sw;
+                        const float A1 = fmaf(fu - fw, fu + fw, L.C1x2n2);
+                        const float B1 = fmaf(fu, fu, fmaf(fw, fw, L.C1x2n2));
+                        const int n32 = (int)N;
+                        const int64_t Vu = (int64_t)n32 * su2 - (int64_t)su * su;
+                        const int64_t Vw = (int64_t)n32 * sw2 - (int64_t)sw * sw;
+                        const float A2 = __ll2float_rn(Vu - Vw) + L.C2x2n2, B2 = __ll2float_rn(Vu + Vw) + L.C2x2n2;
+                        const float cs = __fdividef(A2, B2);
+                        const float qv = __fdividef(A1, B1) * cs;
+                        accQ += qv;
+                        accC += cs;
+                        if (mrow) mrow[e] = qv;
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                accQ += __shfl_down_sync(0xffffffffu, accQ, o);
+                accC += __shfl_down_sync(0xffffffffu, accC, o);
+            }
+            if ((threadIdx.x & 31) == 0) S.red[buf][s3 >> 5] = make_double2((double)accQ, (double)accC);
+        }
+        pending = t;
+        pending_buf = buf;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && pending >= 0) {
+        double sq_ = 0.0, sc_ = 0.0;
+#pragma unroll
+        for (int w = 0; w < T3C / 32; ++w) {
+            sq_ += S.red[pending_buf][w].x;
+            sc_ += S.red[pending_buf][w].y;
+        }
+        L.partials[(int64_t)pending * tiles + tile] = make_double2(sq_, sc_);
+    }
+}
+
 // One CTA per output frame: per level, the fixed-order sum of the frame's
 // tile partials times 1 / positions -> (mean Q_j, mean cs_j); then the frame
 // score (m_j = mean cs_j for j < S, m_S = mean Q_S, combined as in MS-SSIM).
@@ -584,6 +788,40 @@ cudaError_t launch_level_k(const Ssim3dLaunch &L, const CUtensorMap &mx, const C
     return cudaGetLastError();
 }
 
+// The register-column kernel (uint8, k = 11, int32 sums, bulk copies): same
+// tiles and partial layout as ssim3d_kernel<int>, the same frame chunking.
+cudaError_t launch_cols(const Ssim3dLaunch &L, const CUtensorMap &mx, const CUtensorMap &my, cudaStream_t st) {
+    int tx, ty;
+    ssim3d_tiles(L.x.H, L.x.W, L.k, false, &tx, &ty);
+    static DeviceOnce attr_set;
+    static std::atomic<int> slots[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set.is_set(dev)) {
+        const cudaError_t e = cudaFuncSetAttribute(ssim3d_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)sizeof(S3C));
+        if (e != cudaSuccess) return e;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return cudaErrorUnknown;
+        slots[dev].store(sms, std::memory_order_relaxed);
+        attr_set.set(dev);
+    }
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ssim3d_cols_kernel, NTC, sizeof(S3C)) != cudaSuccess)
+        return cudaErrorUnknown;
+    const int tiles = tx * ty, frames = L.T - L.kt + 1;
+    const int wave = max(1, per_sm) * slots[dev].load(std::memory_order_relaxed);
+    int chunks = 1;
+    if (tiles < 2 * wave) {
+        const int want = (2 * wave + tiles - 1) / tiles;
+        chunks = max(1, min(want, frames / max(2, L.kt)));
+    }
+    const int t_chunk = (frames + chunks - 1) / chunks;
+    chunks = (frames + t_chunk - 1) / t_chunk;
+    ssim3d_cols_kernel<<<tiles * chunks, NTC, sizeof(S3C), st>>>(mx, my, L, tx, ty, t_chunk);
+    return cudaGetLastError();
+}
+
 // uint8 video with 16-byte aligned rows and frames: bulk-copied tiles.
 template <typename A, typename In>
 cudaError_t launch_level(const Ssim3dLaunch &L, cudaStream_t st) {
@@ -593,8 +831,11 @@ cudaError_t launch_level(const Ssim3dLaunch &L, cudaStream_t st) {
     if constexpr (std::is_same<In, uint8_t>::value) {
         const int ih = Tile3<A>::OH + L.k - 1;
         const int rw = raw3_width(L.k);
-        if (encode_video_map(&mx, L.x, L.T, ih, rw) && encode_video_map(&my, L.y, L.T, ih, rw))
+        if (encode_video_map(&mx, L.x, L.T, ih, rw) && encode_video_map(&my, L.y, L.T, ih, rw)) {
+            if constexpr (std::is_same<A, int>::value)
+                if (L.k == KC) return launch_cols(L, mx, my, st);
             return launch_level_k<A, In, true>(L, mx, my, st);
+        }
     }
     return launch_level_k<A, In, false>(L, mx, my, st);
 }

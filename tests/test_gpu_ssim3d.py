@@ -35,7 +35,11 @@ def _video(T, H, W, seed=0):
                                         (12, 20, 21, 3, 12), (7, 80, 129, 8, 4),
                                         (10, 40, 100, 31, 9),   # N = 8649: int64 window sums
                                         (20, 24, 40, 3, 2), (16, 30, 50, 5, 3),  # few tiles: frames split over CTAs
-                                        (6, 64, 128, 31, 2), (5, 50, 160, 19, 3)])  # 16-byte rows: bulk-copied tiles
+                                        (6, 64, 128, 31, 2), (5, 50, 160, 19, 3),  # 16-byte rows: bulk-copied tiles
+                                        # k = 11 on 16-byte rows: the register-column kernel (ragged tiles,
+                                        # kt = 1, few tiles with the frames split over CTAs)
+                                        (9, 40, 80, 11, 5), (7, 70, 144, 11, 3), (5, 27, 64, 11, 1),
+                                        (30, 26, 64, 11, 2), (11, 37, 208, 11, 11)])
 def test_ssim3d_matches_oracle(g, T, H, W, k, kt):
     x, y = _video(T, H, W, seed=T + k)
     score, frames, q = g.ssim3d(x.to(DEV), y.to(DEV), kt=kt, k=k, return_map=True)
