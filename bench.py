@@ -593,8 +593,8 @@ def run_case(args):
     (11 x 11 x 5) of 40 luma frames of 1920x1080; msssim3d = MS-SSIM-3D (5
     scales) of the same frames; ragged = one MS-SSIM run of a batch plan
     over 72 ragged pairs (64 drawn from the six resolutions, 8 odd sizes;
-    default tuning); pool = mean pooling of the 64 stored SSIM maps
-    (1070 x 1910 fp32).  Prints one JSON
+    default tuning); pool = pooling (--pool-kind, mean by default) of the 64
+    stored SSIM maps (1070 x 1910 fp32).  Prints one JSON
     line with the mean time per call (CUDA events)."""
     import torch
 
@@ -629,7 +629,8 @@ def run_case(args):
         nq, hq, wq = qmap.shape
         pq = gbssim.Plane(qmap.data_ptr(), gbssim.F32, nq, hq, wq, qmap.stride(1), qmap.stride(0))
         wsq = gbssim.workspace(pq, gbssim.Params(), gbssim.OP_POOL, dev)
-        fn = lambda: gbssim.ssim_pool(qmap, "mean", ws=wsq)
+        pargs = {"mean": (), "cov": (), "minkowski": (4.0,), "fns": (), "pp": (6.0, 4000.0)}[args.pool_kind]
+        fn = lambda: gbssim.ssim_pool(qmap, args.pool_kind, *pargs, ws=wsq)
     elif args.case == "ragged":
         sizes = synth.ragged_sizes(64, 8)
         xs, ys = synth.ragged_pairs_u8(sizes, device=dev)
@@ -672,6 +673,8 @@ def main():
     ap.add_argument("--case", choices=["msssim", "scale0", "box8s4", "loss", "ssim3d", "msssim3d", "ragged", "pool"],
                     default=None,
                     help="run one secondary workload alone (for profilers) instead of the benchmark")
+    ap.add_argument("--pool-kind", default="mean", choices=["mean", "cov", "minkowski", "fns", "pp"],
+                    help="pooling kind of --case pool")
     args = ap.parse_args()
     if args.case:
         run_case(args)

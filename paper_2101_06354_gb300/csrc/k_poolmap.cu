@@ -34,11 +34,11 @@ constexpr int UNR4 = 4;         // float4 loads in flight per thread (dense maps
 // 16-byte aligned images) the flat chunk [item CHK, (item + 1) CHK) read as
 // float4 groups, UNR4 of them in flight per thread; else PR rows, UNR scalar
 // loads in flight per thread and row.  `ax` (nullable) is read alongside.
-template <bool DENSE, typename F>
+template <bool DENSE, int64_t CHUNK = CHK, typename F>
 __device__ __forceinline__ void for_item(const float *m, const float *ax, int64_t h, int64_t w, int64_t ld,
                                          int item, F &&f) {
     if constexpr (DENSE) {
-        const int64_t n = h * w, e0 = (int64_t)item * CHK, e1 = min(e0 + CHK, n);
+        const int64_t n = h * w, e0 = (int64_t)item * CHUNK, e1 = min(e0 + CHUNK, n);
         for (int64_t g0 = e0 + 4 * threadIdx.x; g0 < e1; g0 += 4 * NT * UNR4) {
             float4 v[UNR4], u[UNR4];
 #pragma unroll
@@ -69,8 +69,9 @@ __device__ __forceinline__ void for_item(const float *m, const float *ax, int64_
             }
         }
     } else {
-        const int64_t r0 = (int64_t)item * PR;
-        for (int64_t row = r0; row < min(r0 + PR, h); ++row) {
+        constexpr int64_t ROWS = PR * (CHUNK / CHK);  // rows per item scale with the chunk
+        const int64_t r0 = (int64_t)item * ROWS;
+        for (int64_t row = r0; row < min(r0 + ROWS, h); ++row) {
             const float *rp = m + row * ld;
             const float *ap = ax ? ax + row * ld : nullptr;
             for (int64_t c0 = 0; c0 < w; c0 += UNR * NT) {
@@ -263,17 +264,41 @@ __device__ void unique_prefixes(SelState &s) {
 // into slot 0).  Each thread keeps a run-length count of its last (slot, bin)
 // and only adds to shared memory when the bin changes: neighbouring SSIM
 // values mostly share a bin, so few shared atomics contend.
+// The histogram passes take SEL_SCALE times the moment passes' chunks: every
+// CTA adds its nonzero bins (up to kPoolMaxRanks x 256) to the image's global
+// histogram with atomics, so fewer, longer CTAs contend less.
+constexpr int SEL_SCALE = 1;
 template <bool DENSE>
 __global__ void __launch_bounds__(NT) select_hist_kernel(const float *map, int64_t h, int64_t w, int64_t ld,
                                                          int64_t is, int pass, const SelState *st,
                                                          unsigned *hist) {
     __shared__ unsigned sh[kPoolMaxRanks][NBIN];
     __shared__ unsigned up[kPoolMaxRanks];
+    __shared__ unsigned lowmask[NBIN / 32], prange[2];  // quick rejection of values in no wanted bucket
     const int img = blockIdx.y;
     const int nu = pass == 0 ? 1 : st[img].nu;
     for (int i = threadIdx.x; i < nu * NBIN; i += NT) (&sh[0][0])[i] = 0u;
     if (threadIdx.x < nu) up[threadIdx.x] = pass == 0 ? 0u : st[img].uprefix[threadIdx.x];
+    if (threadIdx.x == 0) {
+        // the prefixes' range and the set of their last bytes: a value whose
+        // high bits fall outside the range, or whose last prefix byte no
+        // prefix has, matches no prefix (most values after pass 1)
+        unsigned lo = 0xffffffffu, hi = 0u, mk[NBIN / 32] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        for (int u = 0; u < nu; ++u) {
+            const unsigned v = pass == 0 ? 0u : st[img].uprefix[u];
+            lo = min(lo, v);
+            hi = max(hi, v);
+            mk[(v & 255u) >> 5] |= 1u << (v & 31u);
+        }
+        for (int k = 0; k < NBIN / 32; ++k) lowmask[k] = mk[k];
+        prange[0] = lo;
+        prange[1] = hi;
+    }
     __syncthreads();
+    const unsigned plo = prange[0], phi = prange[1];
+    unsigned upr[kPoolMaxRanks];  // the prefixes in registers: a branch-free slot search
+#pragma unroll
+    for (int u = 0; u < kPoolMaxRanks; ++u) upr[u] = u < nu ? up[u] : 0xffffffffu;
     const float *m = map + img * is;
     const int fixed = 32 - 8 * pass;  // bits above `fixed` are already known
     unsigned run_key = 0xffffffffu, run_n = 0u;  // (slot << 8 | bin) of the current run
@@ -286,18 +311,22 @@ __global__ void __launch_bounds__(NT) select_hist_kernel(const float *map, int64
             run_n = 1u;
         }
     };
-    for_item<DENSE>(m, nullptr, h, w, ld, blockIdx.x, [&](float q, float) {
+    for_item<DENSE, CHK * SEL_SCALE>(m, nullptr, h, w, ld, blockIdx.x, [&](float q, float) {
         const unsigned key = f2key(q);
         const unsigned bin = (key >> (fixed - 8)) & (NBIN - 1);
         if (pass == 0) {
             count(bin);
         } else {
             const unsigned hb = key >> fixed;
-            for (int u = 0; u < nu; ++u)
-                if (hb == up[u]) {
-                    count(((unsigned)u << 8) | bin);
-                    break;
-                }
+            if (hb < plo || hb > phi) return;
+            int slot = -1;  // distinct prefixes: at most one matches
+            if (nu <= 2) {  // a percentile, a median, percentile pooling
+                slot = hb == upr[0] ? 0 : (hb == upr[1] ? 1 : -1);
+            } else {
+#pragma unroll
+                for (int u = 0; u < kPoolMaxRanks; ++u) slot = hb == upr[u] ? u : slot;
+            }
+            if (slot >= 0) count(((unsigned)slot << 8) | bin);
         }
     });
     if (run_n) atomicAdd(&(&sh[0][0])[run_key], run_n);
@@ -309,25 +338,50 @@ __global__ void __launch_bounds__(NT) select_hist_kernel(const float *map, int64
     }
 }
 
-// One warp per image: walk each wanted rank's histogram to the bin that
-// holds it; extend the prefix by that bin and keep the rank within it.
-__global__ void select_step_kernel(SelState *st, const unsigned *hist, int pass) {
+// One CTA per image, one warp per wanted rank: find the bin of the rank's
+// histogram that holds it with a warp scan (each lane sums 8 consecutive
+// bins, an inclusive scan over the lanes finds the lane, a walk over its 8
+// bins the bin), then extend the prefix by that bin and keep the rank within
+// it.  The warp reads its histogram in parallel, once.
+constexpr int STEP_T = 32 * kPoolMaxRanks;
+__global__ void __launch_bounds__(STEP_T) select_step_kernel(SelState *st, const unsigned *hist, int pass) {
     const int img = blockIdx.x;
     SelState &s = st[img];
     const unsigned *hi = hist + (int64_t)img * kPoolMaxRanks * NBIN;
-    for (int t = threadIdx.x; t < s.nt; t += blockDim.x) {
+    const int t = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (t < s.nt) {
         const unsigned *hb = hi + (pass == 0 ? 0 : s.slot[t] * NBIN);
         const unsigned want = s.rank[t];
-        unsigned acc = 0u;
-        int b = 0;
-        for (; b < NBIN - 1; ++b) {
-            if (acc + hb[b] > want) break;
-            acc += hb[b];
+        constexpr int PER = NBIN / 32;  // 8 bins per lane
+        unsigned c[PER], tot = 0u;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            c[k] = hb[lane * PER + k];
+            tot += c[k];
         }
-        s.prefix[t] = pass == 0 ? (unsigned)b : (s.prefix[t] << 8) | (unsigned)b;
-        s.rank[t] = want - acc;
+        unsigned inc = tot;  // inclusive scan of the lane totals
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        const unsigned exc = inc - tot;
+        // the lane whose bins hold the rank (the last lane if the counts fall short)
+        const unsigned ballot = __ballot_sync(0xffffffffu, inc > want);
+        const int L = ballot ? __ffs(ballot) - 1 : 31;
+        if (lane == L) {
+            unsigned acc = exc;
+            int b = 0;
+            for (; b < PER - 1; ++b) {
+                if (acc + c[b] > want) break;
+                acc += c[b];
+            }
+            const unsigned bin = (unsigned)(L * PER + b);
+            s.prefix[t] = pass == 0 ? bin : (s.prefix[t] << 8) | bin;
+            s.rank[t] = want - acc;
+        }
     }
-    __syncwarp();
+    __syncthreads();
     if (threadIdx.x == 0) unique_prefixes(s);
 }
 
@@ -457,6 +511,8 @@ cudaError_t launch_pool_map(const float *map, int64_t h, int64_t w, int64_t ld, 
                        (!aux || (uintptr_t)aux % 16 == 0);
     const int items = dense ? (int)((h * w + CHK - 1) / CHK) : (int)((h + PR - 1) / PR);
     const dim3 grid(items, count);
+    const int64_t sel_chk = CHK * SEL_SCALE, sel_rows = (int64_t)PR * SEL_SCALE;
+    const dim3 sel_grid(dense ? (int)((h * w + sel_chk - 1) / sel_chk) : (int)((h + sel_rows - 1) / sel_rows), count);
     const int fb = (count + 127) / 128;
     cudaError_t e = cudaSuccess;
     auto moment = [&](int op, const double *c, double p, double r, int kindv, int stage) {
@@ -490,10 +546,10 @@ cudaError_t launch_pool_map(const float *map, int64_t h, int64_t w, int64_t ld, 
             cudaError_t r = cudaMemsetAsync(hist, 0, sizeof(unsigned) * (size_t)kPoolMaxRanks * NBIN * count, st);
             if (r != cudaSuccess) return r;
             if (dense)
-                select_hist_kernel<true><<<grid, NT, 0, st>>>(map, h, w, ld, is, pass, sel, hist);
+                select_hist_kernel<true><<<sel_grid, NT, 0, st>>>(map, h, w, ld, is, pass, sel, hist);
             else
-                select_hist_kernel<false><<<grid, NT, 0, st>>>(map, h, w, ld, is, pass, sel, hist);
-            select_step_kernel<<<count, 32, 0, st>>>(sel, hist, pass);
+                select_hist_kernel<false><<<sel_grid, NT, 0, st>>>(map, h, w, ld, is, pass, sel, hist);
+            select_step_kernel<<<count, STEP_T, 0, st>>>(sel, hist, pass);
         }
         select_finalize_kernel<<<fb, 128, 0, st>>>(sel, count, n, kind, parg, center, out);
         return cudaGetLastError();
