@@ -150,7 +150,7 @@ int gbssim_batch_plan(const gbssim_plane *xs, const gbssim_plane *ys, int32_t n,
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return GBSSIM_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GBSSIM_ERR_CUDA;
-    const int max_ctas = gauss11_batch_max_ctas_per_sm();
+    const int max_ctas = gauss11_batch_max_ctas_per_sm(dtype, true);
     if (max_ctas < 1) return GBSSIM_ERR_CUDA;
     if (ctas == 0 || ctas > max_ctas) ctas = max_ctas;
 

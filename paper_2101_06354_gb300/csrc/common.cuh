@@ -237,7 +237,7 @@ struct UniformBatch {
     int wave_begin[kUniformMaxWaves + 1];
 };
 cudaError_t launch_uniform(const UniformBatch &U, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st);
-int gauss11_batch_max_ctas_per_sm();
+int gauss11_batch_max_ctas_per_sm(int dtype, bool table);
 struct BatchFinalize {
     const BatchLevel *levels;
     const void *ws;

@@ -70,32 +70,52 @@ constexpr int QUADS = (IW + 3) / 4;                 // 4-column staging units pe
 constexpr int IWP = 4 * QUADS + 2;                  // staged row pitch in (u, w) pairs (78)
 constexpr int RWP = TW + 2;                         // ring row pitch in pairs (66)
 constexpr int NT = 256;
-// The vertical pass of a thread reads ring rows base..base+13 with base a
-// multiple of 4 below RING; rows 0..DUP-1 are also stored at RING..RING+DUP-1
-// so those reads never wrap.
-constexpr int DUP = 10;
-constexpr int RROWS = RING + DUP;
+// The vertical pass of a thread reads ring rows b0..b0+13 (mod RING) with
+// b0 a multiple of 4, the same for the 64 threads of a row group: where that
+// window wraps is one of four cases, each compiled with constant offsets.
 
 // u = x + y and w = x - y travel together as float2 pairs so that every
 // moment of the pair is one packed f32x2 instruction (FFMA2 / FADD2 / FMUL2
 // on sm_100+).
-// Level-0 chunks of 16 input rows may arrive by bulk tensor copies instead
-// of per-thread register prefetch: one 2-D tile of TMA_COLS elements x CH
-// rows per image (x, y) into `raw`, rows RAWP bytes apart at most, and the
-// staging threads then read their units from there.
-constexpr int TMA_COLS = 80;              // >= 4 * QUADS columns, 16-byte multiple for every dtype
-constexpr int RAWP = TMA_COLS * 4;        // bytes per staged raw row, widest dtype
+// Chunks of 16 input rows may arrive by bulk tensor copies instead of
+// per-thread register prefetch: one 2-D tile of TMA_COLS elements x CH rows
+// per image, x then y, into the staging area that follows Smem (dense rows
+// of TMA_COLS * sizeof(element) bytes), and the staging threads then read
+// their units from there.
+constexpr int TMA_COLS = 80;  // >= 4 * QUADS columns, 16-byte multiple for every dtype
 struct __align__(128) Smem {
-    float2 in[FIRST][IWP];   // staged input rows, (u, w) per column
-    float2 mu[RROWS][RWP];   // row-window means (mu_u, mu_w)
-    float2 v[RROWS][RWP];    // row-window variances (v_u, v_w)
+    float2 in[FIRST][IWP];  // staged input rows, (u, w) per column
+    float2 mu[RING][RWP];   // row-window means (mu_u, mu_w)
+    float2 v[RING][RWP];    // row-window variances (v_u, v_w)
     float red[2 * NT / 32];
-    alignas(128) unsigned char raw[2][CH][RAWP];  // [x|y] bulk-copied rows of the next chunk
-    unsigned long long bar;                         // their completion
+    unsigned long long bar;  // completion of the bulk copies
 };
-// Kernels that never take the bulk-copy path (the persistent ones) are
-// launched with the shared memory up to `raw` only.
-constexpr size_t kSmemNoBulk = offsetof(Smem, raw);
+// Shared memory of a launch: Smem, then (bulk-copy variants) the staging
+// area of two tiles of element size ESZ.  Without it 50 KB, with 1- or
+// 2-byte tiles 55 KB: four CTAs per SM.
+static_assert(offsetof(Smem, v) == offsetof(Smem, mu) + sizeof(float2) * RING * RWP,
+              "the vertical pass reads S.v at a fixed offset from S.mu");
+constexpr size_t kRawOff = (sizeof(Smem) + 127) / 128 * 128;
+constexpr size_t kSmemNoBulk = kRawOff;
+constexpr size_t smem_bulk(size_t esz) { return kRawOff + 2 * CH * TMA_COLS * esz; }
+__device__ __forceinline__ unsigned char *raw_tile(Smem &S, int img, int esz) {
+    return reinterpret_cast<unsigned char *>(&S) + kRawOff + img * (CH * TMA_COLS * esz);
+}
+// Resident CTAs per SM the kernels are compiled for (the register budget,
+// 64 registers a thread for four): four for 1- and 2-byte data, whose
+// shared memory allows it; three for fp32 data, for the coefficient-writing
+// (backward) variants and for the persistent variant that prefetches every
+// chunk through registers (LEAN false), which would spill at 64.
+template <typename T, bool COEF, bool LEAN = true>
+constexpr int min_ctas() {
+    return (sizeof(T) <= 2 && !COEF && LEAN) ? 4 : 3;
+}
+// The persistent bulk-copy variant of uint8 data also copies uint16 pyramid
+// tiles: its staging area is sized for 2-byte elements.
+template <typename T>
+constexpr size_t persistent_smem() {
+    return smem_bulk(sizeof(T) < 2 ? 2 : sizeof(T));
+}
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -329,12 +349,12 @@ __device__ __forceinline__ void load_unit(Raw &R, const Unit &U, const Geo &g, i
 // A unit read from the bulk-copied rows in shared memory (packed layout as
 // load_raw's vector form; rows past H and columns past W hold zeros).
 template <typename T>
-__device__ __forceinline__ void load_unit_smem(Raw &R, const Unit &U, const Smem &S) {
+__device__ __forceinline__ void load_unit_smem(Raw &R, const Unit &U, Smem &S) {
     R.x0 = R.y0 = R.x1 = R.y1 = make_uint4(0u, 0u, 0u, 0u);
     if (U.p < 0) return;
     constexpr int pitch = TMA_COLS * (int)sizeof(T);
     const int off = 2 * U.p * pitch + 4 * U.q * (int)sizeof(T);
-    const unsigned char *bx = &S.raw[0][0][0] + off, *by = &S.raw[1][0][0] + off;
+    const unsigned char *bx = raw_tile(S, 0, sizeof(T)) + off, *by = raw_tile(S, 1, sizeof(T)) + off;
     if (sizeof(T) == 1) {
         R.x0.x = *reinterpret_cast<const unsigned *>(bx);
         R.y0.x = *reinterpret_cast<const unsigned *>(by);
@@ -491,16 +511,41 @@ __device__ __forceinline__ void horizontal(Smem &S, int rel0, const Taps2<K> &t2
         const float4 m23 = make_float4(om[2].x, om[2].y, om[3].x, om[3].y);
         const float4 v01 = make_float4(ov[0].x, ov[0].y, ov[1].x, ov[1].y);
         const float4 v23 = make_float4(ov[2].x, ov[2].y, ov[3].x, ov[3].y);
+        float4 *dm = reinterpret_cast<float4 *>(&S.mu[slot][g4]);
+        float4 *dv = reinterpret_cast<float4 *>(&S.v[slot][g4]);
+        dm[0] = m01;
+        dm[1] = m23;
+        dv[0] = v01;
+        dv[1] = v23;
+    }
+}
+
+// Vertical window sums of 4 output rows of one column over ring rows
+// b0..b0+13 (mod RING), b0 a multiple of 4: the window is read as four
+// blocks of 4 rows, each contiguous in the ring, so only the block starts
+// wrap; b: the shift (the window-centre row's mean, ring row b0 + 7).
+__device__ __forceinline__ void column_sums(const Smem &S, int b0, int col, const Taps2<K> &t2, float2 &b,
+                                            float2 (&m)[4], float2 (&sq)[4]) {
+    const float2 *blk[4];
 #pragma unroll
-        for (int rep = 0; rep < 2; ++rep) {
-            const int sl = rep ? slot + RING : slot;
-            if (rep && slot >= DUP) break;
-            float4 *dm = reinterpret_cast<float4 *>(&S.mu[sl][g4]);
-            float4 *dv = reinterpret_cast<float4 *>(&S.v[sl][g4]);
-            dm[0] = m01;
-            dm[1] = m23;
-            dv[0] = v01;
-            dv[1] = v23;
+    for (int q = 0; q < 4; ++q) blk[q] = &S.mu[(b0 + 4 * q) & (RING - 1)][col];
+    constexpr int VOFF = RING * RWP;  // S.v follows S.mu (asserted at Smem)
+    b = blk[1][3 * RWP];
+    const float2 nb = make_float2(-b.x, -b.y);
+#pragma unroll
+    for (int o = 0; o < 4; ++o) m[o] = sq[o] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 14; ++i) {
+        const float2 *p = blk[i >> 2] + (i & 3) * RWP;
+        const float2 e = add2(p[0], nb);     // (eu, ew)
+        const float2 q = fma2(e, e, p[VOFF]);  // (eu^2 + v_u, ew^2 + v_w)
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            const int n = i - o;
+            if (n >= 0 && n < K) {
+                m[o] = fma2(t2.g2[n], e, m[o]);
+                sq[o] = fma2(t2.g2[n], q, sq[o]);
+            }
         }
     }
 }
@@ -513,26 +558,9 @@ __device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, 
                                          const CoefOut &co, float *coef_img, float &sumQ, float &sumCS) {
     const int col = threadIdx.x & (TW - 1);
     const int base = rel0 + 4 * (threadIdx.x >> 6);
-    const int b0 = base & (RING - 1);  // multiple of 4; b0 + 13 < RROWS
-    const float2 b = S.mu[b0 + 7][col];
-    const float2 nb = make_float2(-b.x, -b.y);
-    float2 m[4], sq[4];
-#pragma unroll
-    for (int o = 0; o < 4; ++o) m[o] = sq[o] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int i = 0; i < 14; ++i) {
-        const int s = b0 + i;
-        const float2 e = add2(S.mu[s][col], nb);   // (eu, ew)
-        const float2 q = fma2(e, e, S.v[s][col]);  // (eu^2 + v_u, ew^2 + v_w)
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-            const int n = i - o;
-            if (n >= 0 && n < K) {
-                m[o] = fma2(t2.g2[n], e, m[o]);
-                sq[o] = fma2(t2.g2[n], q, sq[o]);
-            }
-        }
-    }
+    const int b0 = base & (RING - 1);  // multiple of 4, uniform over the warp
+    float2 b, m[4], sq[4];
+    column_sums(S, b0, col, t2, b, m, sq);
     const int rows_left = col_ok ? (int)(g.oend - g.o0) - base : 0;
     float *mrow = map ? map + (g.o0 + base) * map_ld + g.j0 + col : nullptr;
     sumQ = 0.f;
@@ -707,8 +735,8 @@ __device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps
             if (more && threadIdx.x == 0) {
                 fence_proxy_async_smem();
                 mbar_expect_tx(&S.bar, 2u * CH * TMA_COLS * (unsigned)sizeof(T));
-                tma_load_3d(&S.raw[0][0][0], it.tmx, (int)g.j0, (int)next_r0, it.tz, &S.bar);
-                tma_load_3d(&S.raw[1][0][0], it.tmy, (int)g.j0, (int)next_r0, it.tz, &S.bar);
+                tma_load_3d(raw_tile(S, 0, sizeof(T)), it.tmx, (int)g.j0, (int)next_r0, it.tz, &S.bar);
+                tma_load_3d(raw_tile(S, 1, sizeof(T)), it.tmy, (int)g.j0, (int)next_r0, it.tz, &S.bar);
             }
             __syncthreads();  // ring rows of chunk c complete; staging free
             float cq, ccs;
@@ -743,7 +771,7 @@ __device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps
 }
 
 template <typename T, bool COEF>
-__global__ void __launch_bounds__(NT, 3)
+__global__ void __launch_bounds__(NT, (min_ctas<T, COEF>()))
     gauss11_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy, bool use_tma,
                    const GaussLaunch L, int strips, int segs) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -964,7 +992,7 @@ struct PyrMaps {
 // remaining bulk-copied items write NaN partials.  Without BULK the launch
 // needs the shared memory up to `raw` only.
 template <typename T, typename Src, bool BULK>
-__global__ void __launch_bounds__(NT, 3)
+__global__ void __launch_bounds__(NT, (min_ctas<T, false, BULK>()))
     gauss11_persistent_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy,
                               const __grid_constant__ PyrMaps pm, const Src src, void *ws_ptr, int64_t counter_off,
                               int64_t done_off, int64_t status_off, unsigned wait_limit, Taps<K> taps, Taps2<K> taps2,
@@ -1180,7 +1208,7 @@ bool encode_plane_map(CUtensorMap *m, const void *data, int64_t H, int64_t W, in
 template <typename T, bool COEF>
 cudaError_t launch_gauss11_t(const GaussLaunch &L, cudaStream_t st) {
     static DeviceOnce attr_set;
-    const size_t smem = sizeof(Smem);
+    const size_t smem = smem_bulk(sizeof(T));
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_set.is_set(dev)) {
@@ -1244,6 +1272,7 @@ cudaError_t launch_persistent_t(const Src &src, void *ws, int64_t counter_off, i
                                 const CUtensorMap *mx = nullptr, const CUtensorMap *my = nullptr,
                                 const PyrMaps *pm = nullptr) {
     constexpr bool can_bulk = std::is_same<Src, UniformSource>::value;
+    constexpr size_t smem = persistent_smem<T>();
     static DeviceOnce attr_set;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
@@ -1253,7 +1282,7 @@ cudaError_t launch_persistent_t(const Src &src, void *ws, int64_t counter_off, i
         if constexpr (can_bulk)
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(gauss11_persistent_kernel<T, Src, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set.set(dev);
     }
@@ -1263,7 +1292,7 @@ cudaError_t launch_persistent_t(const Src &src, void *ws, int64_t counter_off, i
     memset(&none, 0, sizeof none);
     if constexpr (can_bulk) {
         if (mx && my) {
-            gauss11_persistent_kernel<T, Src, true><<<grid, NT, sizeof(Smem), st>>>(
+            gauss11_persistent_kernel<T, Src, true><<<grid, NT, smem, st>>>(
                 *mx, *my, pm ? *pm : none, src, ws, counter_off, done_off, status_off, wait_limit, taps, t2, cc);
             return cudaGetLastError();
         }
@@ -1294,18 +1323,39 @@ cudaError_t launch_persistent(int dtype, const Src &src, void *ws, int64_t count
     return cudaErrorInvalidValue;
 }
 
-// Resident CTAs per SM of the persistent kernels (all instantiations share
-// the launch shape); the >48 KB dynamic shared memory attribute must be set
-// before the occupancy query sees it.
-int gauss11_batch_max_ctas_per_sm() {
-    // both variants fit the same CTAs per SM: the bulk one's extra shared
-    // memory (the staging area) stays within three CTAs' share
-    auto kern = gauss11_persistent_kernel<uint8_t, UniformSource, true>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem)) != cudaSuccess)
-        return 0;
+// Resident CTAs per SM of the persistent kernel of one dtype: the bulk-copy
+// variant of uniform batches, or the table (ragged batch) variant; the
+// >48 KB dynamic shared memory attribute must be set before the occupancy
+// query sees it.  A uniform batch whose planes admit no bulk-copy map runs
+// the register variant on a grid sized for the bulk one: the CTAs beyond
+// the resident ones start as others finish and find the queue drained or
+// not, either way correct.
+template <typename T>
+int max_ctas_t(bool table) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, sizeof(Smem)) != cudaSuccess) return 0;
+    if (table) {
+        auto kern = gauss11_persistent_kernel<T, TableSource, false>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemNoBulk) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, kSmemNoBulk) != cudaSuccess)
+            return 0;
+    } else {
+        auto kern = gauss11_persistent_kernel<T, UniformSource, true>;
+        constexpr size_t smem = persistent_smem<T>();
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, smem) != cudaSuccess)
+            return 0;
+    }
     return n;
+}
+
+int gauss11_batch_max_ctas_per_sm(int dtype, bool table) {
+    switch (dtype) {
+    case GBSSIM_U8: return max_ctas_t<uint8_t>(table);
+    case GBSSIM_F16: return max_ctas_t<__half>(table);
+    case GBSSIM_BF16: return max_ctas_t<__nv_bfloat16>(table);
+    case GBSSIM_F32: return max_ctas_t<float>(table);
+    }
+    return 0;
 }
 
 cudaError_t launch_batch(const BatchTable &B, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st) {
