@@ -298,6 +298,72 @@ def cpu_baseline(min_seconds: float = 6.0):
                             "sample": "%d passes over 2 of the pairs on one core (%.1f s)" % (p_one, t_one)}}
 
 
+def _rate(fn, units: float, min_seconds: float, max_passes: int = 10000):
+    """Calls of fn until about min_seconds; returns (units per second / 1e6, passes, seconds)."""
+    passes = 0
+    t = time.perf_counter()
+    while passes < max_passes and (passes == 0 or time.perf_counter() - t < min_seconds):
+        fn()
+        passes += 1
+    dt = time.perf_counter() - t
+    return passes * units / dt / 1e6, passes, dt
+
+
+def oracle_workloads(min_seconds: float = 1.5):
+    """The FP64 oracle on bounded samples of the secondary workloads, on all
+    host cores and on one core: a 256x256 pair (SSIM, the latency case); two
+    frames of the 3840x2160 YUV 4:2:0 video (SSIM per plane); four pairs of
+    the ragged batch (MS-SSIM); one 512x512 plane of the loss batch (SSIM and
+    its gradient w.r.t. y, L = 1).  Gaussian windows use the oracle's
+    separable window statistics; the gradient is its direct form."""
+    import oracle
+    from paper_2101_06354_gb300 import synth
+
+    taps = oracle.taps_1d("gaussian", 11)
+
+    def ssim_sep(a, b, L=255.0):
+        st = oracle.window_stats_separable(a, b, taps)
+        C1, C2 = oracle.constants(L=L)
+        return oracle.mean(oracle.ssim_terms(st, C1, C2)[2])
+
+    c1x, c1y = synth.luma_pairs_u8(1, 256, 256)
+    c1x, c1y = c1x[0].numpy(), c1y[0].numpy()
+    v = synth.video_yuv420_u8(2, 2160, 3840)
+    planes = [(v[p][0][i].numpy(), v[p][1][i].numpy()) for i in range(2) for p in "yuv"]
+    vpx = sum(a.size for a, _ in planes)
+    sizes = synth.ragged_sizes(512, 64)[:4]
+    rx, ry = synth.ragged_pairs_u8(sizes)
+    rx, ry = [t.numpy() for t in rx], [t.numpy() for t in ry]
+    lx, ly = synth.loss_pairs_float(1, 1, 512, 512)
+    lx, ly = lx[0, 0].double().numpy(), ly[0, 0].double().numpy()
+
+    def loss_step():
+        ssim_sep(lx, ly, L=1.0)
+        oracle.ssim_grad(lx, ly, L=1.0)
+
+    work = {
+        "c1_256": (lambda: ssim_sep(c1x, c1y), 256 * 256, UNIT, "1 pair 256x256 u8, SSIM"),
+        "video_yuv420_4k": (lambda: [ssim_sep(a, b) for a, b in planes], vpx, UNIT,
+                            "2 of the 120 frames 3840x2160 YUV 4:2:0, SSIM per plane"),
+        "ragged_msssim": (lambda: [oracle.msssim(a, b, mode="separable") for a, b in zip(rx, ry)],
+                          sum(h * w for h, w in sizes), UNIT,
+                          "4 of the 576 ragged pairs (%s), MS-SSIM" % ", ".join("%dx%d" % (w, h) for h, w in sizes)),
+        "loss_fwd_bwd": (loss_step, 512 * 512, "Mpx/s", "1 plane 512x512 of the 32x3 loss batch, SSIM + gradient"),
+    }
+    cores = oracle.num_threads()
+    out = {}
+    for key, (fn, units, unit, sample) in work.items():
+        va, pa, ta = _rate(fn, units, min_seconds)
+        oracle.set_num_threads(1)
+        try:
+            v1, p1, t1 = _rate(fn, units, min_seconds)
+        finally:
+            oracle.set_num_threads(cores)
+        out[key] = {"unit": unit, "all_cores": va, "cores": cores, "single_core": v1,
+                    "sample": "%s; %d passes on all cores (%.1f s), %d on one (%.1f s)" % (sample, pa, ta, p1, t1)}
+    return out
+
+
 def run_extras(args, gbssim, synth, x, y, dev, timed, ws):
     """Secondary figures on the same GPU: the 8x8 stride-4 integer box SSIM on
     the same 64 pairs (the HBM-bound path), and the SSIM-loss forward+backward
@@ -400,13 +466,14 @@ def run_extras(args, gbssim, synth, x, y, dev, timed, ws):
     px_total = sum(h * w for h, w in sizes)
     rb = {"pairs": len(sizes), "mpx_pairs": px_total / 1e6}
     for name, msf in (("ssim", False), ("msssim", True)):
-        rows, ctas, _ = tune.tune(xs, ys, multiscale=msf, reps=2)
-        plan = gbssim.BatchPlan(xs, ys, multiscale=msf, seg_rows=rows, ctas_per_sm=ctas)
+        rows, ctas, tw, _ = tune.tune(xs, ys, multiscale=msf, reps=2)
+        plan = gbssim.BatchPlan(xs, ys, multiscale=msf, seg_rows=rows, ctas_per_sm=ctas, tile_w=tw)
         plan.capture()
         kk = max(3, args.steps // 50)
         t = timed(plan.replay, kk) / kk
         rb[name] = {"value": ws * px_total / (t / 1e3) / 1e6, "unit": UNIT, "ms_per_run": t,
-                    "seg_rows": rows, "ctas_per_sm": ctas, "grid": plan.grid, "items": plan.total_items,
+                    "seg_rows": rows, "ctas_per_sm": ctas, "tile_w": tw, "grid": plan.grid,
+                    "items": plan.total_items,
                     "status": plan.status()}
         del plan
     out["ragged_batch"] = rb
@@ -580,6 +647,8 @@ def run_gbssim(args):
         line.update(extra)
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline()
+            if not args.no_extras:
+                line["cpu_baseline"]["workloads"] = oracle_workloads()
         print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()

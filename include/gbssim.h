@@ -518,6 +518,8 @@ typedef struct gbssim_tuning {
     int32_t ctas_per_sm;   /* resident CTAs per SM of the persistent grid (default: maximum) */
     uint32_t wait_limit;   /* spin iterations before a level dependency wait gives up (default 4M) */
     int32_t flags;         /* GBSSIM_TUNING_* */
+    int32_t tile_w;        /* output columns per work item (the strip width): 32, 64 (default) or 128;
+                              a CTA runs 4 x tile_w threads, each 4 output rows of one column */
 } gbssim_tuning;
 
 /* Test hook: image 0's level-1 items wait for one more level-0 item than
@@ -571,7 +573,7 @@ void gbssim_batch_free(gbssim_batch *plan);
  *                 image's level j-1, `wait_limit` polls; a level-0 item's wait
  *                 for its copy group's arrival flag, 16 x `wait_limit` polls);
  *                 flags may hold GBSSIM_TUNING_TEST_DROP_ARRIVAL only (else
- *                 GBSSIM_ERR_INVALID_ARG); seg_rows and ctas_per_sm are ignored.
+ *                 GBSSIM_ERR_INVALID_ARG); seg_rows, ctas_per_sm and tile_w are ignored.
  *   status_host : nullable host int32 (pinned for an asynchronous return);
  *                 receives the launch's status word, GBSSIM_OK or
  *                 GBSSIM_ERR_TIMEOUT when a bounded wait gave up (its images

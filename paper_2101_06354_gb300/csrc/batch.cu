@@ -31,7 +31,7 @@ struct gbssim_batch {
     int n_images, scales, dtype, combine;
     double exps[GBSSIM_MAX_SCALES];
     gbssim_params params;
-    int seg_rows, ctas_per_sm, grid;
+    int seg_rows, ctas_per_sm, grid, tile_w;
     unsigned wait_limit;
     int total_items;
     size_t ws_bytes;
@@ -58,7 +58,7 @@ int gbssim_batch_plan(const gbssim_plane *xs, const gbssim_plane *ys, int32_t n,
     if (multiscale && (p->combine != GBSSIM_COMBINE_PRODUCT && p->combine != GBSSIM_COMBINE_SUM))
         return GBSSIM_ERR_INVALID_ARG;
 
-    int seg_rows = 256, ctas = 0;
+    int seg_rows = 256, ctas = 0, tile_w = 64;
     unsigned wait_limit = 1u << 22;
     int flags = 0;
     if (tuning) {
@@ -66,8 +66,10 @@ int gbssim_batch_plan(const gbssim_plane *xs, const gbssim_plane *ys, int32_t n,
         ctas = tuning->ctas_per_sm;
         if (tuning->wait_limit) wait_limit = tuning->wait_limit;
         flags = tuning->flags;
+        if (tuning->tile_w) tile_w = tuning->tile_w;
     }
     if (seg_rows < 16 || seg_rows > 4096 || seg_rows % 16 != 0 || ctas < 0) return GBSSIM_ERR_INVALID_ARG;
+    if (tile_w != 32 && tile_w != 64 && tile_w != 128) return GBSSIM_ERR_INVALID_ARG;
 
     // expand entries into images
     const int dtype = xs[0].dtype;
@@ -119,7 +121,7 @@ int gbssim_batch_plan(const gbssim_plane *xs, const gbssim_plane *ys, int32_t n,
                 off = align_up(off + 2 * sizeof(float) * (size_t)H * W);
             }
             L.seg_rows = seg_rows;
-            L.strips = (int)((W - 10 + 63) / 64);
+            L.strips = (int)((W - 10 + tile_w - 1) / tile_w);
             L.segs = (int)((H - 10 + seg_rows - 1) / seg_rows);
             L.items = L.strips * L.segs;
             L.wait_target = L.items;
@@ -150,7 +152,7 @@ int gbssim_batch_plan(const gbssim_plane *xs, const gbssim_plane *ys, int32_t n,
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return GBSSIM_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GBSSIM_ERR_CUDA;
-    const int max_ctas = gauss11_batch_max_ctas_per_sm(dtype, true);
+    const int max_ctas = gauss11_batch_max_ctas_per_sm(dtype, true, tile_w);
     if (max_ctas < 1) return GBSSIM_ERR_CUDA;
     if (ctas == 0 || ctas > max_ctas) ctas = max_ctas;
 
@@ -165,6 +167,7 @@ int gbssim_batch_plan(const gbssim_plane *xs, const gbssim_plane *ys, int32_t n,
     for (int j = 0; j < S; ++j) B->exps[j] = multiscale ? p->exponents[j] : 1.0;
     B->params = *p;
     B->seg_rows = seg_rows;
+    B->tile_w = tile_w;
     B->ctas_per_sm = ctas;
     B->grid = sms * ctas;
     B->wait_limit = wait_limit;
@@ -227,6 +230,7 @@ int gbssim_batch_run(const gbssim_batch *plan, double *scores_out, double *per_s
     T.n_images = plan->n_images;
     T.scales = plan->scales;
     T.dtype = plan->dtype;
+    T.tile_w = plan->tile_w;
     T.wait_limit = plan->wait_limit;
     const gbssim_params *p = &plan->params;
     Taps<11> taps;

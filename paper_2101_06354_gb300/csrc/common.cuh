@@ -199,6 +199,7 @@ struct BatchTable {
     void *ws;
     int64_t counter_off, done_off, status_off;
     int total_items, n_images, scales, dtype;
+    int tile_w;  // strip width of the kernel: 32, 64 or 128 output columns (4 x that many threads a CTA)
     unsigned wait_limit;
 };
 cudaError_t launch_batch(const BatchTable &B, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st);
@@ -237,7 +238,7 @@ struct UniformBatch {
     int wave_begin[kUniformMaxWaves + 1];
 };
 cudaError_t launch_uniform(const UniformBatch &U, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st);
-int gauss11_batch_max_ctas_per_sm(int dtype, bool table);
+int gauss11_batch_max_ctas_per_sm(int dtype, bool table, int tile_w = 64);
 struct BatchFinalize {
     const BatchLevel *levels;
     const void *ws;

@@ -55,66 +55,85 @@ namespace {
 
 constexpr int K = 11;
 constexpr int HALO = K - 1;       // 10
-constexpr int TW = 64;            // output columns per strip
 constexpr int CH = 16;            // output rows per chunk
 constexpr int RING = 32;          // ring rows (>= CH + HALO, power of two)
 constexpr int FIRST = CH + HALO;  // input rows staged for the first chunk
-constexpr int IW = TW + HALO;     // input columns per strip (74)
-constexpr int QUADS = (IW + 3) / 4;                 // 4-column staging units per row (19)
-// Row pitches of the staged rows (78 pairs = 39 16-byte slots) and of the
-// moment ring (66 pairs = 33 slots) are odd in 16-byte slots: the horizontal
+
+// Strip geometry: TW output columns per strip (work item), NT = 4 TW threads
+// (in the vertical pass each thread takes 4 output rows of one column).  The
+// single-image, MS-SSIM and backward kernels use TW = 64; the ragged-batch
+// kernel is also built for 32 and 128, a tuning choice.
+// Row pitches of the staged rows (IWP pairs) and of the moment ring (RWP
+// pairs) are odd in 16-byte slots (39 and 33 at TW = 64): the horizontal
 // pass gives each quarter-warp 4 output groups of 2 adjacent rows, whose
 // 16-byte accesses then fall on the even and the odd bank groups
 // respectively, so no access of the pass conflicts and every tap offset is a
 // compile-time constant.
-constexpr int IWP = 4 * QUADS + 2;                  // staged row pitch in (u, w) pairs (78)
-constexpr int RWP = TW + 2;                         // ring row pitch in pairs (66)
-constexpr int NT = 256;
-// The vertical pass of a thread reads ring rows b0..b0+13 (mod RING) with
-// b0 a multiple of 4, the same for the 64 threads of a row group: where that
-// window wraps is one of four cases, each compiled with constant offsets.
+// Chunks of 16 input rows may arrive by bulk tensor copies instead of
+// per-thread register prefetch: one 2-D tile of TMA_COLS elements x CH rows
+// per image, x then y, into the staging area that follows the shared-memory
+// struct (dense rows of TMA_COLS * sizeof(element) bytes), and the staging
+// threads then read their units from there.
+template <int TW_>
+struct Geom {
+    static constexpr int TW = TW_;
+    static constexpr int NT = 4 * TW;
+    static constexpr int IW = TW + HALO;                  // input columns per strip (74)
+    static constexpr int QUADS = (IW + 3) / 4;            // 4-column staging units per row (19)
+    static constexpr int IWP = 4 * QUADS + 2;             // staged row pitch in (u, w) pairs (78)
+    static constexpr int RWP = TW + 2;                    // ring row pitch in pairs (66)
+    static constexpr int TMA_COLS = (4 * QUADS + 15) / 16 * 16;  // 16-byte multiple for every dtype (80)
+    static_assert(TW % 16 == 0 && (IWP / 2) % 2 == 1 && (RWP / 2) % 2 == 1, "odd row pitches in 16-byte slots");
+    static_assert(CH / 2 * QUADS <= NT, "one staging unit per thread per chunk");
+    static_assert(4 * QUADS <= TMA_COLS && TMA_COLS <= 256, "bulk-copy box");
+};
 
 // u = x + y and w = x - y travel together as float2 pairs so that every
 // moment of the pair is one packed f32x2 instruction (FFMA2 / FADD2 / FMUL2
 // on sm_100+).
-// Chunks of 16 input rows may arrive by bulk tensor copies instead of
-// per-thread register prefetch: one 2-D tile of TMA_COLS elements x CH rows
-// per image, x then y, into the staging area that follows Smem (dense rows
-// of TMA_COLS * sizeof(element) bytes), and the staging threads then read
-// their units from there.
-constexpr int TMA_COLS = 80;  // >= 4 * QUADS columns, 16-byte multiple for every dtype
+template <int TW>
 struct __align__(128) Smem {
-    float2 in[FIRST][IWP];  // staged input rows, (u, w) per column
-    float2 mu[RING][RWP];   // row-window means (mu_u, mu_w)
-    float2 v[RING][RWP];    // row-window variances (v_u, v_w)
-    float red[2 * NT / 32];
+    float2 in[FIRST][Geom<TW>::IWP];  // staged input rows, (u, w) per column
+    float2 mu[RING][Geom<TW>::RWP];   // row-window means (mu_u, mu_w)
+    float2 v[RING][Geom<TW>::RWP];    // row-window variances (v_u, v_w)
+    float red[2 * Geom<TW>::NT / 32];
     unsigned long long bar;  // completion of the bulk copies
 };
+// The vertical pass reads S.v at a fixed offset from S.mu.
+static_assert(offsetof(Smem<32>, v) == offsetof(Smem<32>, mu) + sizeof(float2) * RING * Geom<32>::RWP, "mu, v");
+static_assert(offsetof(Smem<64>, v) == offsetof(Smem<64>, mu) + sizeof(float2) * RING * Geom<64>::RWP, "mu, v");
+static_assert(offsetof(Smem<128>, v) == offsetof(Smem<128>, mu) + sizeof(float2) * RING * Geom<128>::RWP, "mu, v");
 // Shared memory of a launch: Smem, then (bulk-copy variants) the staging
-// area of two tiles of element size ESZ.  Without it 50 KB, with 1- or
-// 2-byte tiles 55 KB: four CTAs per SM.
-static_assert(offsetof(Smem, v) == offsetof(Smem, mu) + sizeof(float2) * RING * RWP,
-              "the vertical pass reads S.v at a fixed offset from S.mu");
-constexpr size_t kRawOff = (sizeof(Smem) + 127) / 128 * 128;
-constexpr size_t kSmemNoBulk = kRawOff;
-constexpr size_t smem_bulk(size_t esz) { return kRawOff + 2 * CH * TMA_COLS * esz; }
-__device__ __forceinline__ unsigned char *raw_tile(Smem &S, int img, int esz) {
-    return reinterpret_cast<unsigned char *>(&S) + kRawOff + img * (CH * TMA_COLS * esz);
+// area of two tiles of element size esz.  At TW = 64: 50 KB without it,
+// 55 KB with 1- or 2-byte tiles -- four CTAs per SM.
+template <int TW>
+constexpr size_t raw_off() {
+    return (sizeof(Smem<TW>) + 127) / 128 * 128;
 }
-// Resident CTAs per SM the kernels are compiled for (the register budget,
-// 64 registers a thread for four): four for 1- and 2-byte data, whose
-// shared memory allows it; three for fp32 data, for the coefficient-writing
-// (backward) variants and for the persistent variant that prefetches every
-// chunk through registers (LEAN false), which would spill at 64.
-template <typename T, bool COEF, bool LEAN = true>
+template <int TW>
+constexpr size_t smem_bulk(size_t esz) {
+    return raw_off<TW>() + 2 * CH * Geom<TW>::TMA_COLS * esz;
+}
+template <int TW>
+__device__ __forceinline__ unsigned char *raw_tile(Smem<TW> &S, int img, int esz) {
+    return reinterpret_cast<unsigned char *>(&S) + raw_off<TW>() + img * (CH * Geom<TW>::TMA_COLS * esz);
+}
+// Resident CTAs per SM the kernels are compiled for (the register budget;
+// 1024 threads an SM at 64 registers a thread): 1024 / NT for 1- and 2-byte
+// data, whose shared memory allows it; 768 / NT for fp32 data, for the
+// coefficient-writing (backward) variants and for the persistent variant
+// that prefetches every chunk through registers (LEAN false), which would
+// spill at 64.
+template <typename T, bool COEF, bool LEAN = true, int TW = 64>
 constexpr int min_ctas() {
-    return (sizeof(T) <= 2 && !COEF && LEAN) ? 4 : 3;
+    return (sizeof(T) <= 2 && !COEF && LEAN) ? 1024 / Geom<TW>::NT
+                                             : (768 / Geom<TW>::NT > 0 ? 768 / Geom<TW>::NT : 1);
 }
 // The persistent bulk-copy variant of uint8 data also copies uint16 pyramid
 // tiles: its staging area is sized for 2-byte elements.
 template <typename T>
 constexpr size_t persistent_smem() {
-    return smem_bulk(sizeof(T) < 2 ? 2 : sizeof(T));
+    return smem_bulk<64>(sizeof(T) < 2 ? 2 : sizeof(T));
 }
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -251,8 +270,8 @@ __device__ __forceinline__ float2 staging_bias() {
 __device__ __forceinline__ float magic(unsigned v) { return __int_as_float(0x4B000000u | v); }
 
 // Store one staged unit: columns 4q..4q+3 as (u, w) pairs.
-template <typename T>
-__device__ __forceinline__ void put_unit(Smem &S, int r, int q, uint4 rx, uint4 ry, bool packed) {
+template <typename T, int TW>
+__device__ __forceinline__ void put_unit(Smem<TW> &S, int r, int q, uint4 rx, uint4 ry, bool packed) {
     float4 *d = reinterpret_cast<float4 *>(&S.in[r][4 * q]);
     if constexpr (kBiasedStaging<T>) {
         unsigned u[4], w[4];
@@ -307,7 +326,9 @@ struct Unit {
     bool packed;
 };
 
+template <int TW>
 __device__ __forceinline__ void make_unit(Unit &U, const Geo &g, int t, int npairs) {
+    constexpr int QUADS = Geom<TW>::QUADS;
     U.p = -1;
     U.q = 0;
     U.ncols = 0;
@@ -348,11 +369,11 @@ __device__ __forceinline__ void load_unit(Raw &R, const Unit &U, const Geo &g, i
 
 // A unit read from the bulk-copied rows in shared memory (packed layout as
 // load_raw's vector form; rows past H and columns past W hold zeros).
-template <typename T>
-__device__ __forceinline__ void load_unit_smem(Raw &R, const Unit &U, Smem &S) {
+template <typename T, int TW>
+__device__ __forceinline__ void load_unit_smem(Raw &R, const Unit &U, Smem<TW> &S) {
     R.x0 = R.y0 = R.x1 = R.y1 = make_uint4(0u, 0u, 0u, 0u);
     if (U.p < 0) return;
-    constexpr int pitch = TMA_COLS * (int)sizeof(T);
+    constexpr int pitch = Geom<TW>::TMA_COLS * (int)sizeof(T);
     const int off = 2 * U.p * pitch + 4 * U.q * (int)sizeof(T);
     const unsigned char *bx = raw_tile(S, 0, sizeof(T)) + off, *by = raw_tile(S, 1, sizeof(T)) + off;
     if (sizeof(T) == 1) {
@@ -436,8 +457,8 @@ __device__ __forceinline__ void downsample_unit(const Raw &R, const Unit &U, con
 }
 
 // Store a unit into staged rows row0 + 2p, row0 + 2p + 1 (and its pyramid blocks).
-template <typename T>
-__device__ __forceinline__ void store_unit(Smem &S, const Raw &R, const Unit &U, const Geo &g, int64_t r0, int row0,
+template <typename T, int TW>
+__device__ __forceinline__ void store_unit(Smem<TW> &S, const Raw &R, const Unit &U, const Geo &g, int64_t r0, int row0,
                                            void *dsx, void *dsy) {
     if (U.p < 0) return;
     if (dsx) downsample_unit<T>(R, U, g, r0, dsx, dsy);
@@ -447,11 +468,11 @@ __device__ __forceinline__ void store_unit(Smem &S, const Raw &R, const Unit &U,
 
 // Stage `nr` (even) input rows starting at absolute row r0 into in rows
 // 0..nr-1 (once per segment, for the first FIRST rows).
-template <typename T, int LD = 0>
-__device__ __forceinline__ void stage_direct(Smem &S, const Geo &g, int64_t r0, int nr, void *dsx, void *dsy) {
-    for (int t = threadIdx.x; t < (nr >> 1) * QUADS; t += NT) {
+template <typename T, int LD, int TW>
+__device__ __forceinline__ void stage_direct(Smem<TW> &S, const Geo &g, int64_t r0, int nr, void *dsx, void *dsy) {
+    for (int t = threadIdx.x; t < (nr >> 1) * Geom<TW>::QUADS; t += Geom<TW>::NT) {
         Unit U;
-        make_unit(U, g, t, nr >> 1);
+        make_unit<TW>(U, g, t, nr >> 1);
         Raw R;
         load_unit<T, LD>(R, U, g, r0);
         store_unit<T>(S, R, U, g, r0, 0, dsx, dsy);
@@ -460,19 +481,21 @@ __device__ __forceinline__ void stage_direct(Smem &S, const Geo &g, int64_t r0, 
 
 // Horizontal pass over staged rows 0..NR-1 (NR even); results go to ring
 // rows (rel0 + r) & (RING-1), where rel0 is the row index relative to the
-// segment.  Task t: warp w = t / 32 takes rows 2w, 2w + 1; within a
-// quarter-warp (8 lanes) lanes 0-3 and 4-7 take 4 consecutive groups of 4
-// outputs of the first and the second row.
-template <int NR>
-__device__ __forceinline__ void horizontal(Smem &S, int rel0, const Taps2<K> &t2, float2 bias) {
+// segment.  Tasks come in quarter-warps of 8: quarter-warp Q takes row pair
+// Q / (TW / 16) and, within it, 4 consecutive groups of 4 outputs (group
+// quad Q % (TW / 16)): lanes 0-3 of the first row, lanes 4-7 of the second.
+// At TW = 64 warp w takes rows 2w and 2w + 1.
+template <int NR, int TW>
+__device__ __forceinline__ void horizontal(Smem<TW> &S, int rel0, const Taps2<K> &t2, float2 bias) {
     static_assert(NR % 2 == 0, "rows come in pairs");
+    constexpr int NT = Geom<TW>::NT, TASKS = NR * (TW / 4), QPR = TW / 16;
 #pragma unroll 1
-    for (int pass = 0; pass < (NR * (TW / 4) + NT - 1) / NT; ++pass) {
+    for (int pass = 0; pass < (TASKS + NT - 1) / NT; ++pass) {
         const int task = threadIdx.x + pass * NT;
-        if (NR * (TW / 4) % NT != 0 && task >= NR * (TW / 4)) break;
-        const int lane = task & 31;
-        const int r = 2 * (task >> 5) + ((lane >> 2) & 1);
-        const int g4 = 4 * (4 * (lane >> 3) + (lane & 3));
+        if (TASKS % NT != 0 && task >= TASKS) break;
+        const int Q = task >> 3, l = task & 7;
+        const int r = 2 * (Q / QPR) + ((l >> 2) & 1);
+        const int g4 = 4 * (4 * (Q % QPR) + (l & 3));
         float2 p[14];
         const float4 *src = reinterpret_cast<const float4 *>(&S.in[r][g4]);
 #pragma unroll
@@ -524,12 +547,13 @@ __device__ __forceinline__ void horizontal(Smem &S, int rel0, const Taps2<K> &t2
 // b0..b0+13 (mod RING), b0 a multiple of 4: the window is read as four
 // blocks of 4 rows, each contiguous in the ring, so only the block starts
 // wrap; b: the shift (the window-centre row's mean, ring row b0 + 7).
-__device__ __forceinline__ void column_sums(const Smem &S, int b0, int col, const Taps2<K> &t2, float2 &b,
+template <int TW>
+__device__ __forceinline__ void column_sums(const Smem<TW> &S, int b0, int col, const Taps2<K> &t2, float2 &b,
                                             float2 (&m)[4], float2 (&sq)[4]) {
     const float2 *blk[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) blk[q] = &S.mu[(b0 + 4 * q) & (RING - 1)][col];
-    constexpr int VOFF = RING * RWP;  // S.v follows S.mu (asserted at Smem)
+    constexpr int RWP = Geom<TW>::RWP, VOFF = RING * RWP;  // S.v follows S.mu (asserted at Smem)
     b = blk[1][3 * RWP];
     const float2 nb = make_float2(-b.x, -b.y);
 #pragma unroll
@@ -552,12 +576,12 @@ __device__ __forceinline__ void column_sums(const Smem &S, int b0, int col, cons
 
 // Vertical pass + SSIM formula for the 16 output rows starting at rel0
 // (relative to the segment); each thread does 4 rows of one column.
-template <bool COEF>
-__device__ __forceinline__ void vertical(const Smem &S, const Geo &g, int rel0, const Taps<K> &t,
+template <bool COEF, int TW>
+__device__ __forceinline__ void vertical(const Smem<TW> &S, const Geo &g, int rel0, const Taps<K> &t,
                                          const Taps2<K> &t2, const SsimConst &cc, float *map, int64_t map_ld, bool col_ok,
                                          const CoefOut &co, float *coef_img, float &sumQ, float &sumCS) {
     const int col = threadIdx.x & (TW - 1);
-    const int base = rel0 + 4 * (threadIdx.x >> 6);
+    const int base = rel0 + 4 * (threadIdx.x / TW);
     const int b0 = base & (RING - 1);  // multiple of 4, uniform over the warp
     float2 b, m[4], sq[4];
     column_sums(S, b0, col, t2, b, m, sq);
@@ -619,6 +643,7 @@ struct KSum {
 
 // Sum (a, b) over the CTA: fp32 pairwise tree inside each warp, fp64 across
 // warps; the result is valid in thread 0.
+template <int NT>
 __device__ __forceinline__ void block_sum2f(float a, float b, float *red, double &ra, double &rb) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -665,8 +690,8 @@ struct Item {
 // running count of bulk-copied chunks); `tma_ok`: cleared for the rest of
 // the CTA's items when a bulk-copy wait gives up (that item's partial then
 // reads NaN).
-template <typename T, bool COEF, int LD, bool BULK>
-__device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps<K> &taps, const Taps2<K> &taps2,
+template <typename T, bool COEF, int LD, bool BULK, int TW>
+__device__ __forceinline__ void gauss11_item(Smem<TW> &S, const Item &it, const Taps<K> &taps, const Taps2<K> &taps2,
                                              const SsimConst &cc0, const CoefOut &co, unsigned &phase, bool &tma_ok) {
     Geo g;
     g.H = it.H;
@@ -699,7 +724,7 @@ __device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps
     KSum accQ, accCS;
     Raw raw;
     Unit U;
-    make_unit(U, g, threadIdx.x, CH / 2);
+    make_unit<TW>(U, g, threadIdx.x, CH / 2);
     const bool col_ok = g.j0 + (threadIdx.x & (TW - 1)) < g.OW;
 
     if (BULK && !tma_ok) {  // an earlier bulk-copy wait of this CTA gave up
@@ -734,7 +759,7 @@ __device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps
             // raw[] was last read before the previous barrier
             if (more && threadIdx.x == 0) {
                 fence_proxy_async_smem();
-                mbar_expect_tx(&S.bar, 2u * CH * TMA_COLS * (unsigned)sizeof(T));
+                mbar_expect_tx(&S.bar, 2u * CH * Geom<TW>::TMA_COLS * (unsigned)sizeof(T));
                 tma_load_3d(raw_tile(S, 0, sizeof(T)), it.tmx, (int)g.j0, (int)next_r0, it.tz, &S.bar);
                 tma_load_3d(raw_tile(S, 1, sizeof(T)), it.tmy, (int)g.j0, (int)next_r0, it.tz, &S.bar);
             }
@@ -766,16 +791,16 @@ __device__ __forceinline__ void gauss11_item(Smem &S, const Item &it, const Taps
         }
     }
     double a, b;
-    block_sum2f(accQ.s - accQ.c, accCS.s - accCS.c, S.red, a, b);
+    block_sum2f<Geom<TW>::NT>(accQ.s - accQ.c, accCS.s - accCS.c, S.red, a, b);
     if (threadIdx.x == 0) *it.partial = make_double2(a, b);
 }
 
 template <typename T, bool COEF>
-__global__ void __launch_bounds__(NT, (min_ctas<T, COEF>()))
+__global__ void __launch_bounds__(Geom<64>::NT, (min_ctas<T, COEF>()))
     gauss11_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy, bool use_tma,
                    const GaussLaunch L, int strips, int segs) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    Smem<64> &S = *reinterpret_cast<Smem<64> *>(smem_raw);
     if (use_tma && threadIdx.x == 0) {
         mbar_init(&S.bar, 1);
         fence_mbar_init();
@@ -990,16 +1015,17 @@ struct PyrMaps {
 // completion count, the reader fences after acquiring it); otherwise fp32
 // planes by register staging.  After a bulk-copy wait gives up, the CTA's
 // remaining bulk-copied items write NaN partials.  Without BULK the launch
-// needs the shared memory up to `raw` only.
-template <typename T, typename Src, bool BULK>
-__global__ void __launch_bounds__(NT, (min_ctas<T, false, BULK>()))
+// needs no staging area after the shared-memory struct.  TW: the strip width (64 for
+// uniform batches; the ragged-batch table also runs at 32 and 128).
+template <typename T, typename Src, bool BULK, int TW = 64>
+__global__ void __launch_bounds__(Geom<TW>::NT, (min_ctas<T, false, BULK, TW>()))
     gauss11_persistent_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy,
                               const __grid_constant__ PyrMaps pm, const Src src, void *ws_ptr, int64_t counter_off,
                               int64_t done_off, int64_t status_off, unsigned wait_limit, Taps<K> taps, Taps2<K> taps2,
                               SsimConst cc) {
     constexpr bool kIpyr = BULK && std::is_same<T, uint8_t>::value && std::is_same<Src, UniformSource>::value;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    Smem<TW> &S = *reinterpret_cast<Smem<TW> *>(smem_raw);
     if (BULK && threadIdx.x == 0) {
         mbar_init(&S.bar, 1);
         fence_mbar_init();
@@ -1189,7 +1215,7 @@ constexpr CUtensorMapDataType tma_dtype() {
 }
 
 // Bulk-copy map of a batch of planes (columns, rows, image) with
-// TMA_COLS x CH tiles; false when the planes are not 16-byte aligned (base
+// TMA_COLS x CH tiles of the 64-column strips; false when the planes are not 16-byte aligned (base
 // and strides) or no encoder is available -- the register path runs then.
 template <typename T>
 bool encode_plane_map(CUtensorMap *m, const void *data, int64_t H, int64_t W, int64_t rs, int64_t is, int count) {
@@ -1199,7 +1225,7 @@ bool encode_plane_map(CUtensorMap *m, const void *data, int64_t H, int64_t W, in
     if ((uintptr_t)data % 16 != 0 || (rs * esz) % 16 != 0 || (istr * esz) % 16 != 0) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)count};
     const cuuint64_t strides[2] = {(cuuint64_t)(rs * esz), (cuuint64_t)(istr * esz)};
-    const cuuint32_t box[3] = {TMA_COLS, CH, 1}, estr[3] = {1, 1, 1};
+    const cuuint32_t box[3] = {Geom<64>::TMA_COLS, CH, 1}, estr[3] = {1, 1, 1};
     return fn(m, tma_dtype<T>(), 3, const_cast<void *>(data), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -1208,7 +1234,7 @@ bool encode_plane_map(CUtensorMap *m, const void *data, int64_t H, int64_t W, in
 template <typename T, bool COEF>
 cudaError_t launch_gauss11_t(const GaussLaunch &L, cudaStream_t st) {
     static DeviceOnce attr_set;
-    const size_t smem = smem_bulk(sizeof(T));
+    const size_t smem = smem_bulk<64>(sizeof(T));
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_set.is_set(dev)) {
@@ -1231,7 +1257,7 @@ cudaError_t launch_gauss11_t(const GaussLaunch &L, cudaStream_t st) {
     const bool tma =
         encode_plane_map<T>(&mx, L.x.data, L.x.H, L.x.W, L.x.row_stride, L.x.image_stride, L.count) &&
         encode_plane_map<T>(&my, L.y.data, L.y.H, L.y.W, L.y.row_stride, L.y.image_stride, L.count);
-    gauss11_kernel<T, COEF><<<grid, NT, smem, st>>>(mx, my, tma, A, strips, segs);
+    gauss11_kernel<T, COEF><<<grid, Geom<64>::NT, smem, st>>>(mx, my, tma, A, strips, segs);
     return cudaGetLastError();
 }
 
@@ -1248,7 +1274,7 @@ cudaError_t launch_generic_t(const GenericLaunch &L, cudaStream_t st) {
 
 int gauss11_items(int64_t H, int64_t W, int seg_rows, int *strips, int *segs) {
     const int64_t OH = H - HALO, OW = W - HALO;
-    *strips = (int)((OW + TW - 1) / TW);
+    *strips = (int)((OW + 63) / 64);
     *segs = (int)((OH + seg_rows - 1) / seg_rows);
     return *strips * *segs;
 }
@@ -1265,20 +1291,21 @@ cudaError_t launch_gauss11(const GaussLaunch &L, cudaStream_t st) {
     return cudaErrorInvalidValue;
 }
 
-// mx, my: nullable level-0 bulk-copy maps (uniform batches only).
-template <typename T, typename Src>
+// mx, my: nullable level-0 bulk-copy maps (uniform batches only, TW = 64).
+template <typename T, typename Src, int TW = 64>
 cudaError_t launch_persistent_t(const Src &src, void *ws, int64_t counter_off, int64_t done_off, int64_t status_off,
                                 unsigned wait_limit, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st,
                                 const CUtensorMap *mx = nullptr, const CUtensorMap *my = nullptr,
                                 const PyrMaps *pm = nullptr) {
-    constexpr bool can_bulk = std::is_same<Src, UniformSource>::value;
-    constexpr size_t smem = persistent_smem<T>();
+    constexpr bool can_bulk = std::is_same<Src, UniformSource>::value && TW == 64;
+    constexpr size_t smem = persistent_smem<T>(), smem_reg = raw_off<TW>();
+    constexpr int NT = Geom<TW>::NT;
     static DeviceOnce attr_set;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_set.is_set(dev)) {
-        cudaError_t e = cudaFuncSetAttribute(gauss11_persistent_kernel<T, Src, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemNoBulk);
+        cudaError_t e = cudaFuncSetAttribute(gauss11_persistent_kernel<T, Src, false, TW>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_reg);
         if constexpr (can_bulk)
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(gauss11_persistent_kernel<T, Src, true>,
@@ -1300,68 +1327,93 @@ cudaError_t launch_persistent_t(const Src &src, void *ws, int64_t counter_off, i
     CUtensorMap zx, zy;
     memset(&zx, 0, sizeof zx);
     memset(&zy, 0, sizeof zy);
-    gauss11_persistent_kernel<T, Src, false><<<grid, NT, kSmemNoBulk, st>>>(
+    gauss11_persistent_kernel<T, Src, false, TW><<<grid, NT, smem_reg, st>>>(
         zx, zy, none, src, ws, counter_off, done_off, status_off, wait_limit, taps, t2, cc);
     return cudaGetLastError();
 }
 
-template <typename Src>
+template <typename Src, int TW = 64>
 cudaError_t launch_persistent(int dtype, const Src &src, void *ws, int64_t counter_off, int64_t done_off,
                               int64_t status_off, unsigned wait_limit, const Taps<11> &taps, SsimConst cc, int grid,
                               cudaStream_t st) {
     switch (dtype) {
     case GBSSIM_U8:
-        return launch_persistent_t<uint8_t>(src, ws, counter_off, done_off, status_off, wait_limit, taps, cc, grid, st);
+        return launch_persistent_t<uint8_t, Src, TW>(src, ws, counter_off, done_off, status_off, wait_limit, taps, cc,
+                                                     grid, st);
     case GBSSIM_F16:
-        return launch_persistent_t<__half>(src, ws, counter_off, done_off, status_off, wait_limit, taps, cc, grid, st);
+        return launch_persistent_t<__half, Src, TW>(src, ws, counter_off, done_off, status_off, wait_limit, taps, cc,
+                                                    grid, st);
     case GBSSIM_BF16:
-        return launch_persistent_t<__nv_bfloat16>(src, ws, counter_off, done_off, status_off, wait_limit, taps, cc,
-                                                  grid, st);
+        return launch_persistent_t<__nv_bfloat16, Src, TW>(src, ws, counter_off, done_off, status_off, wait_limit,
+                                                           taps, cc, grid, st);
     case GBSSIM_F32:
-        return launch_persistent_t<float>(src, ws, counter_off, done_off, status_off, wait_limit, taps, cc, grid, st);
+        return launch_persistent_t<float, Src, TW>(src, ws, counter_off, done_off, status_off, wait_limit, taps, cc,
+                                                   grid, st);
     }
     return cudaErrorInvalidValue;
 }
 
 // Resident CTAs per SM of the persistent kernel of one dtype: the bulk-copy
-// variant of uniform batches, or the table (ragged batch) variant; the
-// >48 KB dynamic shared memory attribute must be set before the occupancy
-// query sees it.  A uniform batch whose planes admit no bulk-copy map runs
-// the register variant on a grid sized for the bulk one: the CTAs beyond
-// the resident ones start as others finish and find the queue drained or
-// not, either way correct.
-template <typename T>
+// variant of uniform batches, or the table (ragged batch) variant of strip
+// width TW; the >48 KB dynamic shared memory attribute must be set before
+// the occupancy query sees it.  A uniform batch whose planes admit no
+// bulk-copy map runs the register variant on a grid sized for the bulk one:
+// the CTAs beyond the resident ones start as others finish and find the
+// queue drained or not, either way correct.
+template <typename T, int TW>
 int max_ctas_t(bool table) {
     int n = 0;
     if (table) {
-        auto kern = gauss11_persistent_kernel<T, TableSource, false>;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemNoBulk) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, kSmemNoBulk) != cudaSuccess)
+        auto kern = gauss11_persistent_kernel<T, TableSource, false, TW>;
+        constexpr size_t smem = raw_off<TW>();
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, Geom<TW>::NT, smem) != cudaSuccess)
             return 0;
     } else {
         auto kern = gauss11_persistent_kernel<T, UniformSource, true>;
         constexpr size_t smem = persistent_smem<T>();
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, smem) != cudaSuccess)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, Geom<64>::NT, smem) != cudaSuccess)
             return 0;
     }
     return n;
 }
 
-int gauss11_batch_max_ctas_per_sm(int dtype, bool table) {
+template <int TW>
+int max_ctas_dtype(int dtype, bool table) {
     switch (dtype) {
-    case GBSSIM_U8: return max_ctas_t<uint8_t>(table);
-    case GBSSIM_F16: return max_ctas_t<__half>(table);
-    case GBSSIM_BF16: return max_ctas_t<__nv_bfloat16>(table);
-    case GBSSIM_F32: return max_ctas_t<float>(table);
+    case GBSSIM_U8: return max_ctas_t<uint8_t, TW>(table);
+    case GBSSIM_F16: return max_ctas_t<__half, TW>(table);
+    case GBSSIM_BF16: return max_ctas_t<__nv_bfloat16, TW>(table);
+    case GBSSIM_F32: return max_ctas_t<float, TW>(table);
+    }
+    return 0;
+}
+
+int gauss11_batch_max_ctas_per_sm(int dtype, bool table, int tile_w) {
+    if (!table) return max_ctas_dtype<64>(dtype, false);
+    switch (tile_w) {
+    case 32: return max_ctas_dtype<32>(dtype, true);
+    case 64: return max_ctas_dtype<64>(dtype, true);
+    case 128: return max_ctas_dtype<128>(dtype, true);
     }
     return 0;
 }
 
 cudaError_t launch_batch(const BatchTable &B, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st) {
     TableSource src{B};
-    return launch_persistent(B.dtype, src, B.ws, B.counter_off, B.done_off, B.status_off, B.wait_limit, taps, cc,
-                             grid, st);
+    switch (B.tile_w) {
+    case 32:
+        return launch_persistent<TableSource, 32>(B.dtype, src, B.ws, B.counter_off, B.done_off, B.status_off,
+                                                  B.wait_limit, taps, cc, grid, st);
+    case 64:
+        return launch_persistent<TableSource, 64>(B.dtype, src, B.ws, B.counter_off, B.done_off, B.status_off,
+                                                  B.wait_limit, taps, cc, grid, st);
+    case 128:
+        return launch_persistent<TableSource, 128>(B.dtype, src, B.ws, B.counter_off, B.done_off, B.status_off,
+                                                   B.wait_limit, taps, cc, grid, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>

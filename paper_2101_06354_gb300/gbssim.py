@@ -54,7 +54,7 @@ FLAG_BOX_TMA = 1
 
 class Tuning(ctypes.Structure):
     _fields_ = [("seg_rows", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("wait_limit", ctypes.c_uint32),
-                ("flags", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("tile_w", ctypes.c_int32)]
 
 
 TUNING_TEST_STALL = 1
@@ -837,10 +837,13 @@ class BatchPlan:
 
     ``run()`` enqueues one run and returns the float64 scores (one per image,
     entries expanded in order).  ``capture()`` records one run into a CUDA
-    graph; ``replay()`` launches it again."""
+    graph; ``replay()`` launches it again.  Tuning knobs (0 = default):
+    ``seg_rows`` output rows per work item, ``ctas_per_sm`` resident CTAs
+    per SM, ``tile_w`` output columns per work item (32, 64 or 128; the CTA
+    runs 4 x tile_w threads)."""
 
     def __init__(self, xs, ys, multiscale: bool = False, seg_rows: int = 0, ctas_per_sm: int = 0,
-                 wait_limit: int = 0, flags: int = 0, **kw):
+                 wait_limit: int = 0, flags: int = 0, tile_w: int = 0, **kw):
         if len(xs) != len(ys) or not xs:
             raise ValueError("xs and ys must be non-empty lists of equal length")
         self.xs = [_as_batch(t) for t in xs]
@@ -852,7 +855,8 @@ class BatchPlan:
         self.multiscale = bool(multiscale)
         px = (Plane * len(xs))(*[plane(t) for t in self.xs])
         py = (Plane * len(ys))(*[plane(t) for t in self.ys])
-        tun = Tuning(int(seg_rows), int(ctas_per_sm), int(wait_limit), int(flags))
+        tun = Tuning(int(seg_rows), int(ctas_per_sm), int(wait_limit), int(flags), int(tile_w))
+        self.tile_w = int(tile_w) or 64
         self._plan = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(lib.gbssim_batch_plan(px, py, len(xs), ctypes.byref(self.params), int(self.multiscale),

@@ -1,7 +1,9 @@
 """Autotuner for the ragged persistent batch (gbssim_batch_*).
 
-Times candidate tunings of one batch (rows per work item, resident CTAs per
-SM) with CUDA events on the current stream and keeps the fastest.  Results
+Times candidate tunings of one batch -- the work-item shape (output rows per
+item and the strip width, i.e. output columns per item, which sets the
+threads per CTA at 4 x the width) and the resident CTAs per SM -- with CUDA
+events on the current stream and keeps the fastest.  Results
 are cached in a JSON file keyed by GPU name, dtype, MS-SSIM flag and a size
 class of the batch (the image sizes rounded to powers of two and their
 counts), so later plans of a similar batch skip the search.  The cache lives
@@ -19,7 +21,11 @@ import torch
 
 from . import gbssim
 
-CANDIDATES = [(rows, ctas) for rows in (64, 128, 256, 512) for ctas in (0, 2)]
+# (seg_rows, ctas_per_sm, tile_w): 0 CTAs = as many as fit; the narrow strips
+# (128 threads a CTA) also try half residency, the wide ones (512 threads)
+# fit one CTA an SM
+CANDIDATES = [(rows, ctas, tw) for tw, ctas_list in ((32, (0, 4)), (64, (0, 2)), (128, (0,)))
+              for rows in (64, 128, 256, 512, 1024, 2048) for ctas in ctas_list]
 
 
 def cache_path() -> str:
@@ -76,29 +82,33 @@ def time_plan(plan: "gbssim.BatchPlan", reps: int = 5) -> float:
 
 
 def tune(xs, ys, multiscale: bool = False, candidates=None, reps: int = 5, use_cache: bool = True, **kw):
-    """Return (seg_rows, ctas_per_sm, results) for this batch; results maps
-    each tried candidate to its median milliseconds."""
+    """Return (seg_rows, ctas_per_sm, tile_w, results) for this batch;
+    candidates are (seg_rows, ctas_per_sm[, tile_w]) tuples (tile_w 64 when
+    left out); results maps each tried candidate "rows/ctas/tile_w" to its
+    median milliseconds."""
     key = signature(xs, multiscale)
     cache = _load() if use_cache else {}
     if use_cache and key in cache:
         c = cache[key]
-        return c["seg_rows"], c["ctas_per_sm"], c.get("results", {})
+        return c["seg_rows"], c["ctas_per_sm"], c.get("tile_w", 64), c.get("results", {})
     results = {}
     best = None
-    for rows, ctas in (candidates or CANDIDATES):
-        plan = gbssim.BatchPlan(xs, ys, multiscale=multiscale, seg_rows=rows, ctas_per_sm=ctas, **kw)
+    for cand in (candidates or CANDIDATES):
+        rows, ctas, tw = (tuple(cand) + (64,))[:3]
+        plan = gbssim.BatchPlan(xs, ys, multiscale=multiscale, seg_rows=rows, ctas_per_sm=ctas, tile_w=tw, **kw)
         ms = time_plan(plan, reps)
-        results["%d/%d" % (rows, ctas)] = ms
+        results["%d/%d/%d" % (rows, ctas, tw)] = ms
         if best is None or ms < best[0]:
-            best = (ms, rows, ctas)
+            best = (ms, rows, ctas, tw)
         del plan
-    cache[key] = {"seg_rows": best[1], "ctas_per_sm": best[2], "ms": best[0], "results": results}
+    cache[key] = {"seg_rows": best[1], "ctas_per_sm": best[2], "tile_w": best[3], "ms": best[0],
+                  "results": results}
     if use_cache:
         _store(cache)
-    return best[1], best[2], results
+    return best[1], best[2], best[3], results
 
 
 def autotuned_plan(xs, ys, multiscale: bool = False, **kw) -> "gbssim.BatchPlan":
     """A BatchPlan with the tuned (or cached) knobs for this batch."""
-    rows, ctas, _ = tune(xs, ys, multiscale, **kw)
-    return gbssim.BatchPlan(xs, ys, multiscale=multiscale, seg_rows=rows, ctas_per_sm=ctas, **kw)
+    rows, ctas, tw, _ = tune(xs, ys, multiscale, **kw)
+    return gbssim.BatchPlan(xs, ys, multiscale=multiscale, seg_rows=rows, ctas_per_sm=ctas, tile_w=tw, **kw)

@@ -172,6 +172,10 @@ def test_batch_plan_validation_on_host(g):
     bad = g.Tuning(24, 0, 0, 0)   # rows per item must be a multiple of 16
     assert g.lib.gbssim_batch_plan(x, x, 2, ctypes.byref(p), 0, ctypes.byref(bad), ctypes.byref(out)) \
         == g.ERR_INVALID_ARG
+    for tw in (16, 48, 96, 256):  # strips of 32, 64 or 128 columns only
+        bad = g.Tuning(0, 0, 0, 0, tw)
+        assert g.lib.gbssim_batch_plan(x, x, 2, ctypes.byref(p), 0, ctypes.byref(bad), ctypes.byref(out)) \
+            == g.ERR_INVALID_ARG
     assert out.value is None
 
 

@@ -100,6 +100,31 @@ def test_batch_tuning_knobs_agree(g, synth):
         assert torch.allclose(plan.run(), ref, rtol=0, atol=1e-7)
 
 
+@pytest.mark.parametrize("tile_w", [32, 128])
+@pytest.mark.parametrize("multiscale", [False, True])
+def test_batch_strip_widths_agree(g, synth, tile_w, multiscale):
+    """Strips of 32 and 128 output columns (128- and 512-thread CTAs) score as
+    the 64-column default, and as the oracle; the odd sizes leave ragged last
+    strips at every width."""
+    xs, ys = _pairs(synth, SIZES)
+    ref = g.BatchPlan(xs, ys, multiscale=multiscale).run().clone()
+    plan = g.BatchPlan(xs, ys, multiscale=multiscale, tile_w=tile_w, seg_rows=128)
+    got = plan.run().clone()
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    assert torch.allclose(got, ref, rtol=0, atol=1e-7)
+    for i in (3, 5):
+        if multiscale:
+            want, _ = oracle.msssim(xs[i].cpu().numpy(), ys[i].cpu().numpy())
+        else:
+            want, _ = oracle.ssim(xs[i].cpu().numpy(), ys[i].cpu().numpy())
+        assert abs(got[i].item() - want) <= 1e-6
+    fx, fy = _pairs(synth, SIZES[:3], dtype=torch.float32)
+    fref = g.BatchPlan(fx, fy, multiscale=multiscale, L=1.0).run().clone()
+    fgot = g.BatchPlan(fx, fy, multiscale=multiscale, L=1.0, tile_w=tile_w).run()
+    assert torch.allclose(fgot, fref, rtol=0, atol=1e-7)
+
+
 def test_bounded_wait_reports_timeout(g, synth):
     """The test hook makes image 0's level-1 items wait for a level-0 item that
     does not exist: the wait gives up after `wait_limit` spins, the kernel
@@ -119,12 +144,13 @@ def test_autotuner_picks_and_caches(g, synth, tmp_path, monkeypatch):
 
     monkeypatch.setenv("GBSSIM_TUNE_CACHE", str(tmp_path / "tune.json"))
     xs, ys = _pairs(synth, SIZES[:4])
-    rows, ctas, res = tune.tune(xs, ys, multiscale=True, candidates=[(64, 0), (256, 0), (128, 2)], reps=2)
-    assert "%d/%d" % (rows, ctas) in res and len(res) == 3
+    rows, ctas, tw, res = tune.tune(xs, ys, multiscale=True,
+                                    candidates=[(64, 0, 32), (256, 0), (128, 2, 64), (256, 0, 128)], reps=2)
+    assert "%d/%d/%d" % (rows, ctas, tw) in res and len(res) == 4
     assert os.path.exists(tmp_path / "tune.json")
-    rows2, ctas2, _ = tune.tune(xs, ys, multiscale=True, candidates=[(16, 1)], reps=1)
-    assert (rows2, ctas2) == (rows, ctas)   # served from the cache
+    rows2, ctas2, tw2, _ = tune.tune(xs, ys, multiscale=True, candidates=[(16, 1)], reps=1)
+    assert (rows2, ctas2, tw2) == (rows, ctas, tw)   # served from the cache
     plan = tune.autotuned_plan(xs, ys, multiscale=True)
-    assert plan.seg_rows == rows
+    assert plan.seg_rows == rows and plan.tile_w == tw
     ref = g.BatchPlan(xs, ys, multiscale=True).run()
     assert torch.allclose(plan.run(), ref, rtol=0, atol=1e-7)
