@@ -208,9 +208,8 @@ int plan_levels(const gbssim_plane *x, const gbssim_params *p, int scales, MsPla
         L.pseg_rows = 0;
         L.pitems = 0;
         if (L.path == PATH_GAUSS11 && !border) {
-            int strips, segs;
-            L.pseg_rows = persistent_seg_rows(j, streamed, H - 10, (W - 10 + 63) / 64, x->count);
-            L.pitems = gauss11_items(H, W, L.pseg_rows, &strips, &segs);
+            L.pseg_rows = persistent_seg_rows(j, streamed, H - 10, uniform_strips(W), x->count);
+            L.pitems = uniform_strips(W) * (int)((H - 10 + L.pseg_rows - 1) / L.pseg_rows);
         }
         L.part_off = off;  // pooling slots for whichever layout runs
         off = align_up(off + sizeof(double2) * (size_t)(L.items > L.pitems ? L.items : L.pitems) * x->count);
@@ -386,7 +385,7 @@ int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_pa
             u.H = L.H;
             u.W = L.W;
             u.seg_rows = L.pseg_rows;
-            u.strips = (int)((L.W - 10 + 63) / 64);
+            u.strips = uniform_strips(L.W);
             u.segs = (int)((L.H - 10 + L.pseg_rows - 1) / L.pseg_rows);
             u.items_per_image = u.strips * u.segs;
             if (u.items_per_image != L.pitems) return GBSSIM_ERR_INVALID_ARG;  // plan and launch disagree

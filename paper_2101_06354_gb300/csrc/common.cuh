@@ -175,6 +175,10 @@ struct GaussLaunch {
     CoefOut co;         // backward: coefficient maps instead of (besides) pooling
 };
 int gauss11_items(int64_t H, int64_t W, int seg_rows, int *strips, int *segs);
+// Strip width (output columns per work item) of the persistent MS-SSIM
+// kernel of equally sized images, and its strips per image of width W.
+constexpr int kUniformTW = 64;
+inline int uniform_strips(int64_t W) { return (int)((W - 10 + kUniformTW - 1) / kUniformTW); }
 cudaError_t launch_gauss11(const GaussLaunch &L, cudaStream_t st);
 
 // Ragged persistent batch (k_gauss.cu).  Device tables built by the host

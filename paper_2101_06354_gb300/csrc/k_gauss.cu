@@ -131,9 +131,15 @@ constexpr int min_ctas() {
 }
 // The persistent bulk-copy variant of uint8 data also copies uint16 pyramid
 // tiles: its staging area is sized for 2-byte elements.
-template <typename T>
+template <typename T, int TW = kUniformTW>
 constexpr size_t persistent_smem() {
-    return smem_bulk<64>(sizeof(T) < 2 ? 2 : sizeof(T));
+    return smem_bulk<TW>(sizeof(T) < 2 ? 2 : sizeof(T));
+}
+
+__device__ __forceinline__ unsigned dynamic_smem_bytes() {
+    unsigned n;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(n));
+    return n;
 }
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -1026,6 +1032,13 @@ __global__ void __launch_bounds__(Geom<TW>::NT, (min_ctas<T, false, BULK, TW>())
     constexpr bool kIpyr = BULK && std::is_same<T, uint8_t>::value && std::is_same<Src, UniformSource>::value;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem<TW> &S = *reinterpret_cast<Smem<TW> *>(smem_raw);
+    // a launch shaped for another strip width would index past its shared
+    // memory: refuse it (status word, no score) before any access
+    if (blockDim.x != (unsigned)Geom<TW>::NT || dynamic_smem_bytes() < (BULK ? persistent_smem<T, TW>() : raw_off<TW>())) {
+        if (threadIdx.x == 0) atomicExch(reinterpret_cast<int *>(static_cast<char *>(ws_ptr) + status_off),
+                                         (int)GBSSIM_ERR_INVALID_ARG);
+        return;
+    }
     if (BULK && threadIdx.x == 0) {
         mbar_init(&S.bar, 1);
         fence_mbar_init();
@@ -1215,9 +1228,10 @@ constexpr CUtensorMapDataType tma_dtype() {
 }
 
 // Bulk-copy map of a batch of planes (columns, rows, image) with
-// TMA_COLS x CH tiles of the 64-column strips; false when the planes are not 16-byte aligned (base
-// and strides) or no encoder is available -- the register path runs then.
-template <typename T>
+// TMA_COLS x CH tiles of the TW-column strips; false when the planes are not
+// 16-byte aligned (base and strides) or no encoder is available -- the
+// register path runs then.
+template <typename T, int TW>
 bool encode_plane_map(CUtensorMap *m, const void *data, int64_t H, int64_t W, int64_t rs, int64_t is, int count) {
     auto fn = tensor_map_encoder();
     if (!fn) return false;
@@ -1225,7 +1239,7 @@ bool encode_plane_map(CUtensorMap *m, const void *data, int64_t H, int64_t W, in
     if ((uintptr_t)data % 16 != 0 || (rs * esz) % 16 != 0 || (istr * esz) % 16 != 0) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)count};
     const cuuint64_t strides[2] = {(cuuint64_t)(rs * esz), (cuuint64_t)(istr * esz)};
-    const cuuint32_t box[3] = {Geom<64>::TMA_COLS, CH, 1}, estr[3] = {1, 1, 1};
+    const cuuint32_t box[3] = {Geom<TW>::TMA_COLS, CH, 1}, estr[3] = {1, 1, 1};
     return fn(m, tma_dtype<T>(), 3, const_cast<void *>(data), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -1255,8 +1269,8 @@ cudaError_t launch_gauss11_t(const GaussLaunch &L, cudaStream_t st) {
     memset(&mx, 0, sizeof mx);
     memset(&my, 0, sizeof my);
     const bool tma =
-        encode_plane_map<T>(&mx, L.x.data, L.x.H, L.x.W, L.x.row_stride, L.x.image_stride, L.count) &&
-        encode_plane_map<T>(&my, L.y.data, L.y.H, L.y.W, L.y.row_stride, L.y.image_stride, L.count);
+        encode_plane_map<T, 64>(&mx, L.x.data, L.x.H, L.x.W, L.x.row_stride, L.x.image_stride, L.count) &&
+        encode_plane_map<T, 64>(&my, L.y.data, L.y.H, L.y.W, L.y.row_stride, L.y.image_stride, L.count);
     gauss11_kernel<T, COEF><<<grid, Geom<64>::NT, smem, st>>>(mx, my, tma, A, strips, segs);
     return cudaGetLastError();
 }
@@ -1291,14 +1305,14 @@ cudaError_t launch_gauss11(const GaussLaunch &L, cudaStream_t st) {
     return cudaErrorInvalidValue;
 }
 
-// mx, my: nullable level-0 bulk-copy maps (uniform batches only, TW = 64).
+// mx, my: nullable level-0 bulk-copy maps (uniform batches only).
 template <typename T, typename Src, int TW = 64>
 cudaError_t launch_persistent_t(const Src &src, void *ws, int64_t counter_off, int64_t done_off, int64_t status_off,
                                 unsigned wait_limit, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st,
                                 const CUtensorMap *mx = nullptr, const CUtensorMap *my = nullptr,
                                 const PyrMaps *pm = nullptr) {
-    constexpr bool can_bulk = std::is_same<Src, UniformSource>::value && TW == 64;
-    constexpr size_t smem = persistent_smem<T>(), smem_reg = raw_off<TW>();
+    constexpr bool can_bulk = std::is_same<Src, UniformSource>::value && TW == kUniformTW;
+    constexpr size_t smem = persistent_smem<T, TW>(), smem_reg = raw_off<TW>();
     constexpr int NT = Geom<TW>::NT;
     static DeviceOnce attr_set;
     int dev = 0;
@@ -1308,7 +1322,7 @@ cudaError_t launch_persistent_t(const Src &src, void *ws, int64_t counter_off, i
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_reg);
         if constexpr (can_bulk)
             if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(gauss11_persistent_kernel<T, Src, true>,
+                e = cudaFuncSetAttribute(gauss11_persistent_kernel<T, Src, true, TW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set.set(dev);
@@ -1319,7 +1333,7 @@ cudaError_t launch_persistent_t(const Src &src, void *ws, int64_t counter_off, i
     memset(&none, 0, sizeof none);
     if constexpr (can_bulk) {
         if (mx && my) {
-            gauss11_persistent_kernel<T, Src, true><<<grid, NT, smem, st>>>(
+            gauss11_persistent_kernel<T, Src, true, TW><<<grid, NT, smem, st>>>(
                 *mx, *my, pm ? *pm : none, src, ws, counter_off, done_off, status_off, wait_limit, taps, t2, cc);
             return cudaGetLastError();
         }
@@ -1370,10 +1384,10 @@ int max_ctas_t(bool table) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, Geom<TW>::NT, smem) != cudaSuccess)
             return 0;
     } else {
-        auto kern = gauss11_persistent_kernel<T, UniformSource, true>;
+        auto kern = gauss11_persistent_kernel<T, UniformSource, true, kUniformTW>;
         constexpr size_t smem = persistent_smem<T>();
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, Geom<64>::NT, smem) != cudaSuccess)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, Geom<kUniformTW>::NT, smem) != cudaSuccess)
             return 0;
     }
     return n;
@@ -1391,7 +1405,7 @@ int max_ctas_dtype(int dtype, bool table) {
 }
 
 int gauss11_batch_max_ctas_per_sm(int dtype, bool table, int tile_w) {
-    if (!table) return max_ctas_dtype<64>(dtype, false);
+    if (!table) return max_ctas_dtype<kUniformTW>(dtype, false);
     switch (tile_w) {
     case 32: return max_ctas_dtype<32>(dtype, true);
     case 64: return max_ctas_dtype<64>(dtype, true);
@@ -1420,8 +1434,9 @@ template <typename T>
 cudaError_t launch_uniform_t(const UniformBatch &U0, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st) {
     UniformBatch U = U0;
     CUtensorMap mx, my;
-    const bool bulk = encode_plane_map<T>(&mx, U.x, U.lv[0].H, U.lv[0].W, U.rs, U.image_stride, U.count) &&
-                      encode_plane_map<T>(&my, U.y, U.lv[0].H, U.lv[0].W, U.rs, U.image_stride, U.count);
+    constexpr int TW = kUniformTW;
+    const bool bulk = encode_plane_map<T, TW>(&mx, U.x, U.lv[0].H, U.lv[0].W, U.rs, U.image_stride, U.count) &&
+                      encode_plane_map<T, TW>(&my, U.y, U.lv[0].H, U.lv[0].W, U.rs, U.image_stride, U.count);
     // Arrival flags need the bulk-copy path: the register path's first rows
     // go through the read-only data cache, which bytes copied in during the
     // launch must not.
@@ -1436,8 +1451,9 @@ cudaError_t launch_uniform_t(const UniformBatch &U0, const Taps<11> &taps, SsimC
         const UniformLevel &l = U.lv[j];
         char *xb = static_cast<char *>(U.ws) + l.x_off;
         const int64_t plane = l.H * l.pitch;
-        ipyr = encode_plane_map<uint16_t>(&pm.x[j - 1], xb, l.H, l.W, l.pitch, plane, U.count) &&
-               encode_plane_map<uint16_t>(&pm.y[j - 1], xb + 2 * plane * U.count, l.H, l.W, l.pitch, plane, U.count);
+        ipyr = encode_plane_map<uint16_t, TW>(&pm.x[j - 1], xb, l.H, l.W, l.pitch, plane, U.count) &&
+               encode_plane_map<uint16_t, TW>(&pm.y[j - 1], xb + 2 * plane * U.count, l.H, l.W, l.pitch, plane,
+                                              U.count);
     }
     if (!ipyr && U.ipyr) {
         U.ipyr = 0;
@@ -1447,8 +1463,9 @@ cudaError_t launch_uniform_t(const UniformBatch &U0, const Taps<11> &taps, SsimC
         }
     }
     UniformSource src{U};
-    return launch_persistent_t<T>(src, U.ws, U.counter_off, U.done_off, U.status_off, U.wait_limit, taps, cc, grid,
-                                  st, bulk ? &mx : nullptr, bulk ? &my : nullptr, ipyr ? &pm : nullptr);
+    return launch_persistent_t<T, UniformSource, TW>(src, U.ws, U.counter_off, U.done_off, U.status_off,
+                                                     U.wait_limit, taps, cc, grid, st, bulk ? &mx : nullptr,
+                                                     bulk ? &my : nullptr, ipyr ? &pm : nullptr);
 }
 
 cudaError_t launch_uniform(const UniformBatch &U, const Taps<11> &taps, SsimConst cc, int grid, cudaStream_t st) {
