@@ -40,6 +40,10 @@ CONFIG = {"workload": WORKLOAD, "pairs_per_gpu": N_PAIRS, "height": H, "width": 
 FP32_PEAK_DERIVED_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # algorithmic FLOP per SSIM output: 5 moments x 2 separable passes x 11 taps x 2 + 3 products + ~17 formula
 FLOP_PER_OUTPUT = 240
+# MS-SSIM pools only mean cs below the last level: those outputs need no
+# luminance term (2 mu_x mu_y + C1, mu_x^2 + mu_y^2 + C1, the divide and the
+# product l * cs: 6 FLOP)
+FLOP_PER_CS_OUTPUT = 234
 # pyramid levels of the workload (floor halving)
 LEVELS = [(H >> j, W >> j) for j in range(5)]
 # kernels of libgbssim per MS-SSIM step: the persistent level kernel and the finaliser
@@ -584,7 +588,9 @@ def run_gbssim(args):
     # around the timed steps (the step also holds a counter memset and the
     # finaliser, under 1% of it), so the fraction is a lower bound.
     outputs = N_PAIRS * sum((h - 10) * (w - 10) for h, w in LEVELS)
-    achieved = FLOP_PER_OUTPUT * outputs / (ms_step / 1e3) / 1e12
+    flop_step = N_PAIRS * sum((FLOP_PER_CS_OUTPUT if j < len(LEVELS) - 1 else FLOP_PER_OUTPUT) * (h - 10) * (w - 10)
+                              for j, (h, w) in enumerate(LEVELS))
+    achieved = flop_step / (ms_step / 1e3) / 1e12
     # secondary: the scale-0 grid kernel alone (gbssim_ssim_map on the same pairs)
     wss = gbssim.workspace(px, p, gbssim.OP_SSIM, dev)
     ms_k = timed(lambda: gbssim.ssim(x, y, ws=wss), args.steps) / args.steps
@@ -634,7 +640,7 @@ def run_gbssim(args):
                                             "median of 5 launches), the larger rate",
                              "peak_probe_tflops": fp32_rates,
                              "peak_derived_tflops": FP32_PEAK_DERIVED_TFLOPS,
-                             "units_per_launch": outputs, "flop_per_unit": FLOP_PER_OUTPUT,
+                             "units_per_launch": outputs, "flop_per_unit": flop_step / outputs,
                              "kernel_ms": ms_step, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
                              "scale0_grid_kernel": {"kernel": "gauss11_kernel<uint8_t>", "ms": ms_k,
                                                     "achieved": FLOP_PER_OUTPUT * outputs0 / (ms_k / 1e3) / 1e12,

@@ -376,6 +376,9 @@ int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_pa
         // the level's values, at most 255 x 4^4 = 65280), rows padded to 8
         // elements; they fit the workspace planned for fp32 levels
         U.ipyr = int_pyramid && x->dtype == GBSSIM_U8 && S <= 5;
+        // the score pools mean cs below the last level and mean Q at it:
+        // without per-scale output the lower levels form cs alone
+        U.cs_only_levels = per_scale_out ? 0 : S - 1;
         int64_t begin = 0;
         MsFinalize F;
         memset(&F, 0, sizeof F);

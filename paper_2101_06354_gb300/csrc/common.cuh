@@ -228,6 +228,9 @@ struct UniformBatch {
     // holding 4^j times the level's values (exact), row pitch a multiple of
     // 8, read by bulk tensor copies.  0: fp32 planes of the 2x2 means.
     int ipyr;
+    // levels j < cs_only_levels pool only mean cs (their mean Q is not
+    // asked for: MS-SSIM without per-scale output), the rest both
+    int cs_only_levels;
     UniformLevel lv[GBSSIM_MAX_SCALES];
     int64_t total_items;
     void *ws;

@@ -582,19 +582,39 @@ __device__ __forceinline__ void column_sums(const Smem<TW> &S, int b0, int col, 
 
 // Vertical pass + SSIM formula for the 16 output rows starting at rel0
 // (relative to the segment); each thread does 4 rows of one column.
+// cs_only (no map, no coefficients): the level's Q is not pooled (MS-SSIM
+// levels below the last), so only the contrast-structure term is formed and
+// sumQ is 0.
 template <bool COEF, int TW>
 __device__ __forceinline__ void vertical(const Smem<TW> &S, const Geo &g, int rel0, const Taps<K> &t,
                                          const Taps2<K> &t2, const SsimConst &cc, float *map, int64_t map_ld, bool col_ok,
-                                         const CoefOut &co, float *coef_img, float &sumQ, float &sumCS) {
+                                         const CoefOut &co, float *coef_img, bool cs_only, float &sumQ, float &sumCS) {
     const int col = threadIdx.x & (TW - 1);
     const int base = rel0 + 4 * (threadIdx.x / TW);
     const int b0 = base & (RING - 1);  // multiple of 4, uniform over the warp
     float2 b, m[4], sq[4];
     column_sums(S, b0, col, t2, b, m, sq);
     const int rows_left = col_ok ? (int)(g.oend - g.o0) - base : 0;
-    float *mrow = map ? map + (g.o0 + base) * map_ld + g.j0 + col : nullptr;
     sumQ = 0.f;
     sumCS = 0.f;
+    if (!COEF && cs_only) {
+        float css[4];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            const float2 var = fma2(make_float2(-m[o].x, -m[o].y), m[o], sq[o]);  // (Var u, Var w)
+            const float t2c = var.x + cc.C2x2;
+            css[o] = __fdividef(t2c - var.y, t2c + var.y);
+        }
+        if (rows_left >= 4) {
+            sumCS = (css[0] + css[1]) + (css[2] + css[3]);
+        } else {
+#pragma unroll
+            for (int o = 0; o < 4; ++o)
+                if (o < rows_left) sumCS += css[o];
+        }
+        return;
+    }
+    float *mrow = map ? map + (g.o0 + base) * map_ld + g.j0 + col : nullptr;
     float qs[4], css[4];
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
@@ -685,6 +705,7 @@ struct Item {
     bool ds16;             // uint8 / uint16 data: the next level as exact uint16 block sums
     int64_t ds_ld;         // row pitch of the next-level planes, in elements
     float cscale;          // C1, C2 scale (16^j for a uint16 level holding 4^j times its values; else 1)
+    bool cs_only;          // only the mean cs of the item is pooled (its sum Q slot reads 0)
     float *coef_img;       // COEF mode: A, B, C planes of this image
     double2 *partial;      // this item's (sum Q, sum cs) slot
     const CUtensorMap *tmx, *tmy;  // nullable: bulk-copy maps of the (level-0) x, y planes
@@ -751,7 +772,8 @@ __device__ __forceinline__ void gauss11_item(Smem<TW> &S, const Item &it, const 
             if (more) load_unit<T, LD>(raw, U, g, next_r0);
             __syncthreads();  // ring rows of chunk c complete; staging free
             float cq, ccs;
-            vertical<COEF>(S, g, CH * c, taps, taps2, cc, it.map, it.map_ld, col_ok, co, it.coef_img, cq, ccs);
+            vertical<COEF>(S, g, CH * c, taps, taps2, cc, it.map, it.map_ld, col_ok, co, it.coef_img, it.cs_only, cq,
+                           ccs);
             accQ.add(cq);
             accCS.add(ccs);
             if (more) store_unit<T>(S, raw, U, g, next_r0, 0, it.dsx, it.dsy);
@@ -771,7 +793,8 @@ __device__ __forceinline__ void gauss11_item(Smem<TW> &S, const Item &it, const 
             }
             __syncthreads();  // ring rows of chunk c complete; staging free
             float cq, ccs;
-            vertical<COEF>(S, g, CH * c, taps, taps2, cc, it.map, it.map_ld, col_ok, co, it.coef_img, cq, ccs);
+            vertical<COEF>(S, g, CH * c, taps, taps2, cc, it.map, it.map_ld, col_ok, co, it.coef_img, it.cs_only, cq,
+                           ccs);
             accQ.add(cq);
             accCS.add(ccs);
             bool failed = false;
@@ -832,6 +855,7 @@ __global__ void __launch_bounds__(Geom<64>::NT, (min_ctas<T, COEF>()))
     it.ds16 = false;
     it.ds_ld = it.W >> 1;
     it.cscale = 1.f;
+    it.cs_only = false;
     it.coef_img = COEF ? L.co.coef + (int64_t)img * 3 * (it.H - HALO) * coef_ld(it.W - HALO) : nullptr;
     it.partial = L.partials + ((int64_t)img * segs + seg) * strips + strip;
     it.tmx = use_tma ? &tmx : nullptr;
@@ -904,6 +928,7 @@ struct TableSource {
         it.ds16 = false;
         it.ds_ld = lv.W >> 1;
         it.cscale = 1.f;
+        it.cs_only = false;
         it.coef_img = nullptr;
         it.partial = reinterpret_cast<double2 *>(ws + lv.part_off) + (int64_t)bi.seg * lv.strips + bi.strip;
         R.pyramid = lv.level > 0;
@@ -976,6 +1001,7 @@ struct UniformSource {
         const int64_t plane = lv.H * lv.pitch;
         it.ds16 = U.ipyr != 0;
         it.cscale = (U.ipyr && j > 0) ? __int_as_float((127 + 4 * j) << 23) : 1.f;  // 16^j
+        it.cs_only = j < U.cs_only_levels;
         if (j + 1 < U.scales) {
             const UniformLevel &nv = U.lv[j + 1];
             const int64_t nplane = nv.H * nv.pitch;

@@ -261,6 +261,24 @@ def test_msssim_u8(g, synth, h, w):
         np.testing.assert_allclose(per[i].cpu().numpy(), np.array(ref_per), rtol=0, atol=POOL_TOL)
 
 
+@pytest.mark.parametrize("dtype", [torch.uint8, torch.float32])
+def test_msssim_score_same_with_and_without_per_scale(g, synth, dtype):
+    """Without per-scale output the levels below the last form only the
+    contrast-structure term (their mean Q is not pooled): the score is
+    bit-identical to the run that forms and returns both, and the returned
+    per-scale pairs match the oracle."""
+    x, y = synth.luma_pairs_u8(3, 300, 420)
+    if dtype != torch.uint8:
+        x, y = x.to(dtype) / 255, y.to(dtype) / 255
+    kw = {} if dtype == torch.uint8 else dict(L=1.0)
+    alone = g.msssim(x.to(DEV), y.to(DEV), **kw)
+    score, per = g.msssim(x.to(DEV), y.to(DEV), per_scale=True, **kw)
+    assert torch.equal(alone, score)
+    for i in (0, 2):
+        _, ref_per = oracle.msssim(x[i].double().numpy(), y[i].double().numpy(), **kw)
+        np.testing.assert_allclose(per[i].cpu().numpy(), np.array(ref_per), rtol=0, atol=POOL_TOL)
+
+
 @pytest.mark.parametrize("kw", [dict(combine="sum"), dict(scales=3, exponents=(0.3, 0.3, 0.4)),
                                 dict(window="box", k=8), dict(k=7, sigma=1.0), dict(stride=2),
                                 dict(scales=1, exponents=(1.0,))])
