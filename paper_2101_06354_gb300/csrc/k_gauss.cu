@@ -142,6 +142,11 @@ __device__ __forceinline__ unsigned dynamic_smem_bytes() {
     return n;
 }
 
+// The 11-tap windows (Gaussian, box) are symmetric, g[n] = g[10 - n] (the
+// launchers check it): the passes name taps 0..5 only, which keeps six tap
+// pairs live in registers instead of eleven.
+__host__ __device__ constexpr int sym(int n) { return n <= HALO / 2 ? n : HALO - n; }
+
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -523,8 +528,8 @@ __device__ __forceinline__ void horizontal(Smem<TW> &S, int rel0, const Taps2<K>
             for (int o = 0; o < 4; ++o) {
                 const int n = i - o;
                 if (n >= 0 && n < K) {
-                    m[o] = fma2(t2.g2[n], d, m[o]);
-                    sq[o] = fma2(t2.g2[n], dd, sq[o]);
+                    m[o] = fma2(t2.g2[sym(n)], d, m[o]);
+                    sq[o] = fma2(t2.g2[sym(n)], dd, sq[o]);
                 }
             }
         }
@@ -573,8 +578,8 @@ __device__ __forceinline__ void column_sums(const Smem<TW> &S, int b0, int col, 
         for (int o = 0; o < 4; ++o) {
             const int n = i - o;
             if (n >= 0 && n < K) {
-                m[o] = fma2(t2.g2[n], e, m[o]);
-                sq[o] = fma2(t2.g2[n], q, sq[o]);
+                m[o] = fma2(t2.g2[sym(n)], e, m[o]);
+                sq[o] = fma2(t2.g2[sym(n)], q, sq[o]);
             }
         }
     }
@@ -1286,7 +1291,10 @@ cudaError_t launch_gauss11_t(const GaussLaunch &L, cudaStream_t st) {
     int strips, segs;
     gauss11_items(L.x.H, L.x.W, L.seg_rows, &strips, &segs);
     GaussLaunch A = L;
-    for (int n = 0; n < 11; ++n) A.taps2.g2[n] = make_float2(L.taps.g[n], L.taps.g[n]);
+    for (int n = 0; n < 11; ++n) {
+        if (L.taps.g[n] != L.taps.g[sym(n)]) return cudaErrorInvalidValue;  // the passes assume symmetric taps
+        A.taps2.g2[n] = make_float2(L.taps.g[n], L.taps.g[n]);
+    }
     const uintptr_t vbytes = 4 * sizeof(T);  // one 4-element vector
     A.vec = ((uintptr_t)L.x.data % vbytes == 0) && ((uintptr_t)L.y.data % vbytes == 0) &&
             (L.x.row_stride % 4 == 0) && (L.x.image_stride % 4 == 0) && (L.y.image_stride % 4 == 0);
@@ -1354,7 +1362,10 @@ cudaError_t launch_persistent_t(const Src &src, void *ws, int64_t counter_off, i
         attr_set.set(dev);
     }
     Taps2<11> t2;
-    for (int n = 0; n < 11; ++n) t2.g2[n] = make_float2(taps.g[n], taps.g[n]);
+    for (int n = 0; n < 11; ++n) {
+        if (taps.g[n] != taps.g[sym(n)]) return cudaErrorInvalidValue;  // the passes assume symmetric taps
+        t2.g2[n] = make_float2(taps.g[n], taps.g[n]);
+    }
     PyrMaps none;
     memset(&none, 0, sizeof none);
     if constexpr (can_bulk) {
