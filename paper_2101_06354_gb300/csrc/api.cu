@@ -348,13 +348,14 @@ cudaError_t run_level(const Level &L, const ImgDesc &dx, const ImgDesc &dy, int 
 // where the path allows), then the finaliser.  Shared by gbssim_msssim and
 // the MS-SSIM backward.
 
-// arrive (nullable, persistent path only): level-0 items of image i wait
-// (bounded) until arrive[i / arrive_group] != 0, their bytes being copied in
-// on another stream.
+// arrive (nullable, persistent path only): the images come in `groups` copy
+// groups, group g holding images group_begin[g] .. group_begin[g + 1] - 1;
+// their level-0 items wait (bounded) until arrive[g] != 0, their bytes being
+// copied in on another stream.
 int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_params *p,
                           const MsPlan &P, char *ws, double *score_out, double *per_scale_out,
-                          cudaStream_t st, const unsigned *arrive = nullptr, int arrive_group = 1,
-                          unsigned wait_limit = 0, bool int_pyramid = true) {
+                          cudaStream_t st, const unsigned *arrive = nullptr, const int *group_begin = nullptr,
+                          int groups = 0, unsigned wait_limit = 0, bool int_pyramid = true) {
     const int S = p->scales, n = x->count;
     // the persistent path fuses the 2x2 pyramid into valid-window levels
     bool persistent = (p->flags & GBSSIM_FLAG_PYRAMID_97) == 0 && !border_mode(p);
@@ -419,19 +420,23 @@ int msssim_forward(const gbssim_plane *x, const gbssim_plane *y, const gbssim_pa
         U.wait_limit = wait_limit ? wait_limit : 1u << 22;
         if (begin > 0x7fffffff) return GBSSIM_ERR_UNSUPPORTED;
         U.arrive = arrive;
-        U.arrive_group = arrive_group > 0 ? arrive_group : 1;
         if (arrive) {
             // wavefront over copy groups: wave w runs level 0 of group w while
             // the upper levels of earlier groups fill the wait for copies
-            const int gs = U.arrive_group, G = (n + gs - 1) / gs;
-            if (G > kUniformMaxGroups) return GBSSIM_ERR_INVALID_ARG;
+            const int G = groups;
+            if (!group_begin || G < 1 || G > kUniformMaxGroups || group_begin[0] != 0 || group_begin[G] != n)
+                return GBSSIM_ERR_INVALID_ARG;
+            for (int g = 0; g <= G; ++g) {
+                if (g < G && group_begin[g + 1] <= group_begin[g]) return GBSSIM_ERR_INVALID_ARG;
+                U.group_begin[g] = group_begin[g];
+            }
             U.groups = G;
             U.waves = G + S - 1;
             U.wave_begin[0] = 0;
             int64_t at = 0;
             for (int w = 0; w < U.waves; ++w) {
                 for (int j = w - G + 1 > 0 ? w - G + 1 : 0; j <= w && j < S; ++j) {
-                    const int g = w - j, m = n - g * gs < gs ? n - g * gs : gs;
+                    const int g = w - j, m = group_begin[g + 1] - group_begin[g];
                     at += (int64_t)m * U.lv[j].items_per_image;
                 }
                 U.wave_begin[w + 1] = (int)at;
@@ -635,6 +640,27 @@ PFN_cuStreamWriteValue32_v11070 stream_write_value32() {
         return (PFN_cuStreamWriteValue32_v11070) nullptr;
     }();
     return fn;
+}
+
+// Copy groups of the streamed host mode (at most kUniformMaxGroups, each with
+// its arrival flag): with 32 images or more the last eight groups hold 4, 4,
+// 2, 2, 1, 1, 1, 1 images, so the work left after the last copy lands (that
+// group's level-0 items and the chain of its upper levels) is short, and the
+// first eight split the rest evenly; with fewer, equal groups of
+// ceil(n / 16).  begin[0..G] receives the groups' first images; returns G.
+int stream_groups(int n, int *begin) {
+    static const int tail[8] = {4, 4, 2, 2, 1, 1, 1, 1};
+    int G = 0;
+    begin[0] = 0;
+    if (n >= 32) {
+        const int head = n - 16;
+        for (int g = 0; g < 8; ++g, ++G) begin[G + 1] = begin[G] + head / 8 + (g < head % 8 ? 1 : 0);
+        for (int g = 0; g < 8; ++g, ++G) begin[G + 1] = begin[G] + tail[g];
+    } else {
+        const int gs = (n + kUniformMaxGroups - 1) / kUniformMaxGroups;
+        for (int i0 = 0; i0 < n; i0 += gs, ++G) begin[G + 1] = i0 + gs < n ? i0 + gs : n;
+    }
+    return G;
 }
 
 int plan_host(const gbssim_plane *x, const gbssim_params *p, int32_t chunks, HostPlan *H) {
@@ -1391,7 +1417,8 @@ int msssim_host_impl(const gbssim_plane *x, const gbssim_plane *y, const gbssim_
         // launch still finds its inputs arriving).
         auto write32 = stream_write_value32();
         unsigned *flags = (unsigned *)(ws + H.flags_off);
-        const int group = (x->count + kUniformMaxGroups - 1) / kUniformMaxGroups;  // images per copy group and flag
+        int gbegin[kUniformMaxGroups + 1];
+        const int G = stream_groups(x->count, gbegin);
         char *xs = ws + H.stage_off[0], *ysg = xs + H.plane_bytes;
         if (!write32) e = cudaErrorNotSupported;
         // the copy stream must not wait for the launch (an implicitly
@@ -1401,13 +1428,13 @@ int msssim_host_impl(const gbssim_plane *x, const gbssim_plane *y, const gbssim_
             rc = GBSSIM_ERR_INVALID_ARG;
         if (e == cudaSuccess && rc == GBSSIM_OK) e = cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)x->count, cs);
         if (e == cudaSuccess && rc == GBSSIM_OK) e = cudaEventRecord(copied[0], cs);
-        // groups of images per copy and flag: at most 16 groups (fewer, larger copies)
+        // one copy of x and one of y per group, then the group's flag
         const size_t img_bytes = (size_t)H.pitch_elems * H.esz * x->height;
-        for (int i0 = 0, f = 0; i0 < x->count && e == cudaSuccess && rc == GBSSIM_OK; i0 += group, ++f) {
-            const int m = x->count - i0 < group ? x->count - i0 : group;
+        for (int f = 0; f < G && e == cudaSuccess && rc == GBSSIM_OK; ++f) {
+            const int i0 = gbegin[f], m = gbegin[f + 1] - gbegin[f];
             e = copy_images_h2d(x, i0, m, H, xs + i0 * img_bytes, cs);
             if (e == cudaSuccess) e = copy_images_h2d(y, i0, m, H, ysg + i0 * img_bytes, cs);
-            const bool last = i0 + group >= x->count;
+            const bool last = f + 1 == G;
             if (e == cudaSuccess && !(drop_flag && last) &&
                 write32(cs, (CUdeviceptr)(flags + f), 1u, CU_STREAM_WRITE_VALUE_DEFAULT) != CUDA_SUCCESS)
                 e = cudaErrorUnknown;
@@ -1423,7 +1450,7 @@ int msssim_host_impl(const gbssim_plane *x, const gbssim_plane *y, const gbssim_
             dy.data = ysg;
             dx.row_stride = dy.row_stride = H.pitch_elems;
             dx.image_stride = dy.image_stride = H.pitch_elems * x->height;
-            rc = msssim_forward(&dx, &dy, p, H.ms, ws + H.ws_off[0], score_dev, nullptr, st, flags, group,
+            rc = msssim_forward(&dx, &dy, p, H.ms, ws + H.ws_off[0], score_dev, nullptr, st, flags, gbegin, G,
                                 wait_limit);
         }
         if (e == cudaSuccess && rc == GBSSIM_OK) e = cudaStreamWaitEvent(st, copied[1], 0);
@@ -1537,7 +1564,7 @@ int gbssim_ssim_backward(const gbssim_plane *x, const gbssim_plane *y, const gbs
         }
     } else if (multiscale) {
         // the coefficient passes below read the fp32 pyramid planes
-        rc = msssim_forward(x, y, p, B.fwd, ws, score, per, st, nullptr, 1, 0, false);
+        rc = msssim_forward(x, y, p, B.fwd, ws, score, per, st, nullptr, nullptr, 0, 0, false);
         if (rc) return rc;
     }
     double esum = 0.0;

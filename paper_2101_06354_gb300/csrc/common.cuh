@@ -236,10 +236,13 @@ struct UniformBatch {
     void *ws;
     int64_t counter_off, done_off, status_off;
     unsigned wait_limit;
-    const unsigned *arrive;  // nullable: level-0 items of image i wait (bounded) until arrive[i / arrive_group] != 0
-    int arrive_group;        // images per arrival flag (>= 1)
+    // nullable: level-0 items of the images of copy group g (images
+    // group_begin[g] .. group_begin[g + 1] - 1) wait (bounded) until
+    // arrive[g] != 0
+    const unsigned *arrive;
+    int group_begin[kUniformMaxGroups + 1];
     // waves > 0 (with arrive): items in copy-group wavefront order, wave w
-    // holding level j of group w - j for every level (groups of arrive_group
+    // holding level j of group w - j for every level (groups of group_begin
     // images); wave_begin[w] is its first item.  waves == 0: level-major.
     int waves, groups;
     int wave_begin[kUniformMaxWaves + 1];

@@ -962,7 +962,7 @@ struct UniformSource {
     __device__ int total() const { return (int)U.total_items; }
     __device__ bool ipyr() const { return U.ipyr != 0; }
     __device__ void resolve(int item, char *ws, Resolved &R) const {
-        int j = 0, img, rem;
+        int j = 0, img, rem, grp = -1;
         if (U.waves > 0) {
             // wave w: level j of copy group w - j, levels in order; a level's
             // dependency (the level below, same group) is one wave earlier
@@ -972,13 +972,14 @@ struct UniformSource {
             j = w - U.groups + 1 > 0 ? w - U.groups + 1 : 0;
             int g = w - j, m;
             for (;; ++j, --g) {
-                m = min(U.arrive_group, U.count - g * U.arrive_group);
+                m = U.group_begin[g + 1] - U.group_begin[g];
                 const int c = m * U.lv[j].items_per_image;
                 if (r < c || j + 1 >= U.scales || g == 0) break;
                 r -= c;
             }
             const int k = r / U.lv[j].items_per_image;
-            img = g * U.arrive_group + k;
+            img = U.group_begin[g] + k;
+            grp = g;
             rem = r - k * U.lv[j].items_per_image;
         } else {
             while (j + 1 < U.scales && item >= U.lv[j + 1].item_begin) ++j;
@@ -1030,7 +1031,7 @@ struct UniformSource {
             R.xb = ws + lv.x_off + esz_p * img * plane;
             R.yb = ws + lv.x_off + esz_p * (U.count + img) * plane;
         }
-        R.arrive = (j == 0 && U.arrive) ? U.arrive + img / U.arrive_group : nullptr;
+        R.arrive = (j == 0 && U.arrive && grp >= 0) ? U.arrive + grp : nullptr;
         R.done_index = img * U.scales + j;
         R.dep_index = j > 0 ? img * U.scales + j - 1 : -1;
         R.dep_target = j > 0 ? (unsigned)U.lv[j - 1].items_per_image : 0u;

@@ -52,7 +52,7 @@ def test_host_pipeline_equals_device_call(g, synth, n, h, w, chunks):
 
 
 # (n, h, w): several 128-row level-0 items with a ragged last one (600 rows),
-# one image, a group per image (n <= 16) and groups of several images (n = 37)
+# one image, a group per image (n <= 16) and uneven groups of several images (n = 37)
 @pytest.mark.parametrize("n,h,w", [(7, 200, 232), (5, 181, 203), (1, 200, 240), (3, 600, 300), (37, 176, 176)])
 def test_streamed_matches_oracle(g, synth, n, h, w):
     x, y = synth.luma_pairs_u8(n, h, w)
@@ -69,9 +69,9 @@ def test_streamed_matches_oracle(g, synth, n, h, w):
 
 def test_streamed_full_size_all_pairs(g, synth):
     """The end-to-end benchmark step: 64 pinned 1920x1080 pairs streamed
-    through one launch (copy groups of 4 pairs, 128-row items at the two
-    largest levels); every score against the device call and against the
-    oracle."""
+    through one launch (eight copy groups of 6 pairs, then groups of 4, 4, 2,
+    2, 1, 1, 1, 1; 128-row items at the two largest levels); every score
+    against the device call and against the oracle."""
     n = 64
     x, y = synth.luma_pairs_u8(n, 1080, 1920)
     got = g.msssim_host(x.pin_memory(), y.pin_memory(), chunks=0)
@@ -88,8 +88,9 @@ def test_streamed_arrival_wait_reports_timeout(g, synth):
     """The test hook leaves the last copy group's arrival flag unset: the
     level-0 items of its image wait until their bounded wait (16 x wait_limit
     polls) runs out, the launch records GBSSIM_ERR_TIMEOUT, that image scores
-    NaN, and the call still completes.  37 pairs make copy groups of 3 with a
-    last group of one image."""
+    NaN, and the call still completes.  37 pairs make eight copy groups of 2
+    or 3 images and then groups of 4, 4, 2, 2, 1, 1, 1, 1: the last holds one
+    image."""
     n = 37
     x, y = synth.luma_pairs_u8(n, 176, 176)
     xp, yp = x.pin_memory(), y.pin_memory()
