@@ -122,6 +122,15 @@ __device__ __forceinline__ int unpack(const Raw<float> &r, int e, float scale) {
 }
 
 // 4 consecutive accumulators += d (16-byte accesses: int4, or two longlong2).
+__device__ __forceinline__ void add4(unsigned *t, const unsigned (&d)[4]) {
+    uint4 *t4 = reinterpret_cast<uint4 *>(t);
+    uint4 v = *t4;
+    v.x += d[0];
+    v.y += d[1];
+    v.z += d[2];
+    v.w += d[3];
+    *t4 = v;
+}
 __device__ __forceinline__ void add4(int *t, const int (&d)[4]) {
     int4 *t4 = reinterpret_cast<int4 *>(t);
     int4 v = *t4;
@@ -150,6 +159,11 @@ __device__ __forceinline__ void store_col(int *vc, const int (&v)[OH]) {
     for (int i = 0; i < OH; i += 2) *reinterpret_cast<int2 *>(vc + i) = make_int2(v[i], v[i + 1]);
 }
 template <int OH>
+__device__ __forceinline__ void store_col(unsigned *vc, const unsigned (&v)[OH]) {
+#pragma unroll
+    for (int i = 0; i < OH; i += 2) *reinterpret_cast<uint2 *>(vc + i) = make_uint2(v[i], v[i + 1]);
+}
+template <int OH>
 __device__ __forceinline__ void store_col(long long *vc, const long long (&v)[OH]) {
 #pragma unroll
     for (int i = 0; i < OH; ++i) vc[i] = v[i];
@@ -160,11 +174,22 @@ __device__ __forceinline__ void store_col(long long *vc, const long long (&v)[OH
 // the previous frame's step 1, instead of per-thread loads.  A bulk-copy wait
 // that gives up writes NaN partials for the CTA's remaining output frames,
 // waits (bounded) for its copies in flight and returns.
+// 64 registers a thread (4 CTAs per SM) with 32-bit sums of byte input;
+// float input keeps four float4 prefetches per 4-column group in flight and
+// gets 80 (3 CTAs); int64 sums 128 (2 CTAs).
+template <typename A, typename In>
+constexpr int ssim3d_min_ctas() {
+    return sizeof(A) == 8 ? 2 : (std::is_same<In, float>::value ? 3 : 4);
+}
+
 template <typename A, typename In, bool BULK>
-__global__ void __launch_bounds__(NT, sizeof(A) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(NT, (ssim3d_min_ctas<A, In>()))
     ssim3d_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy,
                   const Ssim3dLaunch L, int tiles_x, int tiles_y, int t_chunk) {
     constexpr int OH = Tile3<A>::OH, PV = Tile3<A>::PV;
+    // 4-column groups whose loads are in flight together: float input holds
+    // a float4 per row and frame, so one group (the byte input's word, two)
+    constexpr int RBK = std::is_same<In, float>::value ? 1 : RB;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     A *sm = reinterpret_cast<A *>(smem_raw);
     S3Geo g;
@@ -226,13 +251,13 @@ __global__ void __launch_bounds__(NT, sizeof(A) == 4 ? 4 : 2)
         }
         L.partials[(int64_t)tp * (tiles_x * tiles_y) + tile] = make_double2(sq, sc);
     };
-    // the first RB groups of this thread: offsets and widths hoisted out of
+    // the first RBK groups of this thread: offsets and widths hoisted out of
     // the frame loop; their bytes of frame f+1 and of frame f+1-kt (the one
     // leaving the window) are loaded while frame f is in steps 2 and 3
-    int64_t o0[RB];
-    int n40[RB], at0[RB];
+    int64_t o0[RBK];
+    int n40[RBK], at0[RBK];
 #pragma unroll
-    for (int u = 0; u < RB; ++u) {
+    for (int u = 0; u < RBK; ++u) {
         const int unit = threadIdx.x + u * NT;
         const int r = unit / g.groups, c = 4 * (unit - r * g.groups);
         const int64_t row = y0 + r;
@@ -242,9 +267,9 @@ __global__ void __launch_bounds__(NT, sizeof(A) == 4 ? 4 : 2)
         at0[u] = r * g.pw + c;
         o0[u] = row * rs + x0 + c;
     }
-    Raw<In> px[RB], py[RB], pxo[RB], pyo[RB];  // frame f and frame f - kt of those groups
+    Raw<In> px[RBK], py[RBK], pxo[RBK], pyo[RBK];  // frame f and frame f - kt of those groups
 #pragma unroll
-    for (int u = 0; u < RB; ++u) {
+    for (int u = 0; u < RBK; ++u) {
         load_raw(xb + f_begin * fs + o0[u], BULK ? 0 : n40[u], words, px[u]);
         load_raw(yb + f_begin * fs + o0[u], BULK ? 0 : n40[u], words, py[u]);
         load_raw(xb, 0, words, pxo[u]);  // no frame leaves the window yet
@@ -253,7 +278,7 @@ __global__ void __launch_bounds__(NT, sizeof(A) == 4 ? 4 : 2)
     for (int f = f_begin; f < f_end; ++f) {
         // 1. temporal sums: + frame f, - frame f - kt.  Thread t owns the
         //    4-column groups t, t + NT, ... (row-major over the input tile),
-        //    RB of them with their loads in flight together; 16-byte shared
+        //    RBK of them with their loads in flight together; 16-byte shared
         //    accesses, consecutive across a warp.
         const bool old = f - L.kt >= f_begin;
         bool failed = false;
@@ -288,12 +313,12 @@ __global__ void __launch_bounds__(NT, sizeof(A) == 4 ? 4 : 2)
         } else {
         const In *xf = xb + f * fs, *yf = yb + f * fs;
         const In *xo = xb + (f - L.kt) * fs, *yo = yb + (f - L.kt) * fs;
-        for (int u0 = threadIdx.x; u0 < units; u0 += RB * NT) {
+        for (int u0 = threadIdx.x; u0 < units; u0 += RBK * NT) {
             const bool first = u0 == threadIdx.x;
-            Raw<In> rx[RB], ry[RB], qx[RB], qy[RB];
-            int n4[RB], at[RB];
+            Raw<In> rx[RBK], ry[RBK], qx[RBK], qy[RBK];
+            int n4[RBK], at[RBK];
 #pragma unroll
-            for (int u = 0; u < RB; ++u) {
+            for (int u = 0; u < RBK; ++u) {
                 if (first) {
                     n4[u] = n40[u];
                     at[u] = at0[u];
@@ -319,7 +344,7 @@ __global__ void __launch_bounds__(NT, sizeof(A) == 4 ? 4 : 2)
             if (first && f + 1 < f_end) {
                 const bool old1 = f + 1 - L.kt >= f_begin;
 #pragma unroll
-                for (int u = 0; u < RB; ++u) {
+                for (int u = 0; u < RBK; ++u) {
                     load_raw(xf + fs + o0[u], n40[u], words, px[u]);
                     load_raw(yf + fs + o0[u], n40[u], words, py[u]);
                     load_raw(xo + fs + o0[u], old1 ? n40[u] : 0, words, pxo[u]);
@@ -327,7 +352,7 @@ __global__ void __launch_bounds__(NT, sizeof(A) == 4 ? 4 : 2)
                 }
             }
 #pragma unroll
-            for (int u = 0; u < RB; ++u) {
+            for (int u = 0; u < RBK; ++u) {
                 if (n4[u] <= 0) continue;  // values past n4 are zero: they add nothing
                 A d[4][4];
 #pragma unroll
@@ -416,14 +441,18 @@ __global__ void __launch_bounds__(NT, sizeof(A) == 4 ? 4 : 2)
                         float A1, B1;
                         int64_t Vu, Vw;
                         if constexpr (sizeof(A) == 4) {
-                            // |Su|, |Sw| <= 510 N < 2^23 (N < 8256 here): exact in fp32, and
-                            // Su^2 - Sw^2 = (Su - Sw)(Su + Sw) rounds once
-                            const float fu = (float)su, fw = (float)sw;
+                            // |Su|, |Sw| < 2^23 (uint8 video: 510 N with N < 8256; the
+                            // unsigned level: checked by the launcher): exact in fp32, and
+                            // Su^2 - Sw^2 = (Su - Sw)(Su + Sw) rounds once.  Unsigned sums
+                            // are modulo 2^32: Sw (may be negative) reads as int32, the
+                            // square sums (>= 0, < 2^32) as uint32.
+                            const int64_t su_ = (int64_t)(int)su, sw_ = (int64_t)(int)sw;
+                            const int64_t su2_ = (int64_t)(unsigned)su2, sw2_ = (int64_t)(unsigned)sw2;
+                            const float fu = (float)su_, fw = (float)sw_;
                             A1 = fmaf(fu - fw, fu + fw, L.C1x2n2);
                             B1 = fmaf(fu, fu, fmaf(fw, fw, L.C1x2n2));
-                            const int n32 = (int)N;
-                            Vu = (int64_t)n32 * su2 - (int64_t)su * su;
-                            Vw = (int64_t)n32 * sw2 - (int64_t)sw * sw;
+                            Vu = N * su2_ - su_ * su_;
+                            Vw = N * sw2_ - sw_ * sw_;
                         } else {
                             const int64_t U2 = (int64_t)su * su, W2 = (int64_t)sw * sw;
                             Vu = N * (int64_t)su2 - U2;
@@ -848,8 +877,20 @@ void ssim3d_tiles(int64_t H, int64_t W, int k, bool wide, int *tx, int *ty) {
     *ty = (int)((H - k + 1 + oh - 1) / oh);
 }
 
+// Pyramid levels of uint8 video hold multiples of 1 / scale up to 255; as
+// integers (times scale) the window sums of u = x + y and its square over
+// N = k^2 kt pixels stay below 2 x 255 scale N and N (2 x 255 scale)^2.
+// When those fit 2^23 (exact in fp32) and 2^32, the level runs with 32-bit
+// sums kept modulo 2^32 (level 1 of an 11 x 11 x 5 window: 1.2 M and
+// 2.5e9), else with int64 sums.
+bool ssim3d_level_fits_u32(const Ssim3dLaunch &L) {
+    const double n = (double)L.k * L.k * L.kt, umax = 2.0 * 255.0 * L.scale;
+    return n * umax < 8388608.0 && n * umax * umax < 4294967296.0;
+}
+
 cudaError_t launch_ssim3d_level(const Ssim3dLaunch &L, bool u8_input, bool wide, cudaStream_t st) {
-    if (!u8_input) return launch_level<long long, float>(L, st);
+    if (!u8_input) return ssim3d_level_fits_u32(L) ? launch_level<unsigned, float>(L, st)
+                                                   : launch_level<long long, float>(L, st);
     return wide ? launch_level<long long, uint8_t>(L, st) : launch_level<int, uint8_t>(L, st);
 }
 
