@@ -405,8 +405,12 @@ def run_extras(args, gbssim, synth, x, y, dev, timed, ws):
     wsq = gbssim.workspace(pq, gbssim.Params(), gbssim.OP_POOL, dev)
     map_bytes = qmap.numel() * 4
     pool_res = {}
-    for kind, pargs, passes in (("mean", (), 1), ("cov", (), 2), ("minkowski", (4.0,), 1), ("fns", (), 4),
-                                ("pp", (6.0, 4000.0), 5)):
+    # map passes: order statistics read the map three times on their value-bin
+    # path (min / max, bin counts, the wanted bins' values; the radix passes
+    # that would follow for a crowded map are not taken on these maps); PP
+    # adds its moment pass
+    for kind, pargs, passes in (("mean", (), 1), ("cov", (), 2), ("minkowski", (4.0,), 1), ("fns", (), 3),
+                                ("pp", (6.0, 4000.0), 4)):
         fpool = lambda: gbssim.ssim_pool(qmap, kind, *pargs, ws=wsq)
         for _ in range(3):
             fpool()

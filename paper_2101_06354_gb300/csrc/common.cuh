@@ -337,7 +337,9 @@ constexpr int kVideoMaxFrames = 4096;  // 32 KB of shared memory for the sort
 constexpr int kPoolMaxRanks = 10;  // order statistics one call selects (five-number summary: 5 x 2)
 struct PoolLayout {
     int items;                          // row blocks per map
-    size_t partials, center, state, hist, bytes;
+    size_t partials, center, state, hist;
+    size_t fast, vhist, cand;           // value-bin selection: state, bin counts, candidates
+    size_t bytes;
 };
 PoolLayout pool_layout(int64_t h, int64_t w, int count);
 // SSIM-3D and MS-SSIM-3D (k_ssim3d.cu): k x k x kt rectangular windows over

@@ -246,7 +246,27 @@ struct SelState {
     unsigned uprefix[kPoolMaxRanks]; // the distinct prefixes; each value matches at most one
     int slot[kPoolMaxRanks];         // wanted rank -> its prefix's histogram slot
     int nt, nu;
+    int skip;                        // 1: the value-bin path found every key (prefix = the full key)
 };
+
+// Value-bin selection (the first path tried): the map's min and max, a
+// histogram of VB equal-width value bins over [min, max], the bins that hold
+// the wanted ranks, a gather of those bins' values (at most `cap` per image
+// together), and an exact select among them.  mode 1: non-finite values,
+// or more candidates than `cap` -- the radix passes select that image.
+constexpr int VB = 4096;
+struct FastSel {
+    unsigned kmin, kmax;               // keys of the image's min and max
+    int mode, nslot;                   // 0 value-bin path, 1 radix passes; distinct wanted bins
+    int bin[kPoolMaxRanks];            // wanted rank -> its bin
+    int slot[kPoolMaxRanks];           // wanted rank -> its bin's slot
+    unsigned below[kPoolMaxRanks];     // values in the bins before it
+    int sbin[kPoolMaxRanks];           // slot -> bin
+    unsigned soff[kPoolMaxRanks + 1];  // slot -> first candidate in the image's buffer
+    unsigned scnt[kPoolMaxRanks];      // slot -> candidates gathered so far
+};
+// Candidates kept per image: all wanted bins of an image together.
+__host__ __device__ inline int64_t vcap(int64_t n) { return n < 65536 ? n : 65536; }
 
 // Rebuild the distinct-prefix table after the prefixes changed.
 __device__ void unique_prefixes(SelState &s) {
@@ -276,6 +296,7 @@ __global__ void __launch_bounds__(NT) select_hist_kernel(const float *map, int64
     __shared__ unsigned up[kPoolMaxRanks];
     __shared__ unsigned lowmask[NBIN / 32], prange[2];  // quick rejection of values in no wanted bucket
     const int img = blockIdx.y;
+    if (st[img].skip) return;  // the value-bin path has the keys (uniform over the CTA)
     const int nu = pass == 0 ? 1 : st[img].nu;
     for (int i = threadIdx.x; i < nu * NBIN; i += NT) (&sh[0][0])[i] = 0u;
     if (threadIdx.x < nu) up[threadIdx.x] = pass == 0 ? 0u : st[img].uprefix[threadIdx.x];
@@ -347,6 +368,7 @@ constexpr int STEP_T = 32 * kPoolMaxRanks;
 __global__ void __launch_bounds__(STEP_T) select_step_kernel(SelState *st, const unsigned *hist, int pass) {
     const int img = blockIdx.x;
     SelState &s = st[img];
+    if (s.skip) return;  // uniform over the CTA
     const unsigned *hi = hist + (int64_t)img * kPoolMaxRanks * NBIN;
     const int t = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (t < s.nt) {
@@ -385,6 +407,292 @@ __global__ void __launch_bounds__(STEP_T) select_step_kernel(SelState *st, const
     if (threadIdx.x == 0) unique_prefixes(s);
 }
 
+// bin(v) = min(VB - 1, int((v - lo) * inv)) over [lo, hi] = [min, max]: the
+// same fp32 steps in every kernel (explicit roundings, no contraction), so a
+// value falls in the same bin each time, and bins are monotone in v.
+// False when min or max is not finite or the width is not usable.
+__device__ __forceinline__ bool vrange(const FastSel &f, float &lo, float &inv) {
+    lo = key2f(f.kmin);
+    const float hi = key2f(f.kmax);
+    if (!isfinite(lo) || !isfinite(hi)) return false;
+    inv = hi > lo ? __fdiv_rn((float)VB, __fsub_rn(hi, lo)) : 0.f;
+    return isfinite(inv);
+}
+__device__ __forceinline__ int vbin(float v, float lo, float inv) {
+    const float t = __fmul_rn(__fsub_rn(v, lo), inv);
+    return t >= (float)(VB - 1) ? VB - 1 : (int)t;  // t >= 0: lo is the minimum
+}
+
+// Pass M: the keys of each image's minimum and maximum (order-preserving
+// keys: NaN sorts outside +-inf and turns the image over to the radix path).
+template <bool DENSE>
+__global__ void __launch_bounds__(NT) vminmax_kernel(const float *map, int64_t h, int64_t w, int64_t ld, int64_t is,
+                                                     FastSel *fs) {
+    __shared__ unsigned smn[NT / 32], smx[NT / 32];
+    const int img = blockIdx.y;
+    unsigned mn = 0xffffffffu, mx = 0u;
+    for_item<DENSE, CHK * SEL_SCALE>(map + img * is, nullptr, h, w, ld, blockIdx.x, [&](float q, float) {
+        const unsigned k = f2key(q);
+        mn = min(mn, k);
+        mx = max(mx, k);
+    });
+    mn = __reduce_min_sync(0xffffffffu, mn);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        smn[warp] = mn;
+        smx[warp] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < NT / 32; ++k) {
+            mn = min(mn, smn[k]);
+            mx = max(mx, smx[k]);
+        }
+        atomicMin(&fs[img].kmin, mn);
+        atomicMax(&fs[img].kmax, mx);
+    }
+}
+
+// Pass H: per-CTA counts of the VB value bins (run-length aggregated, as in
+// the radix passes), added to the image's histogram.
+template <bool DENSE>
+__global__ void __launch_bounds__(NT) vhist_kernel(const float *map, int64_t h, int64_t w, int64_t ld, int64_t is,
+                                                   const FastSel *fs, unsigned *vh) {
+    __shared__ unsigned sh[VB];
+    const int img = blockIdx.y;
+    float lo, inv;
+    if (!vrange(fs[img], lo, inv)) return;  // uniform over the CTA
+    for (int i = threadIdx.x; i < VB; i += NT) sh[i] = 0u;
+    __syncthreads();
+    int run_bin = -1;
+    unsigned run_n = 0u;
+    for_item<DENSE, CHK * SEL_SCALE>(map + img * is, nullptr, h, w, ld, blockIdx.x, [&](float q, float) {
+        const int b = vbin(q, lo, inv);
+        if (b == run_bin) {
+            ++run_n;
+        } else {
+            if (run_n) atomicAdd(&sh[run_bin], run_n);
+            run_bin = b;
+            run_n = 1u;
+        }
+    });
+    if (run_n) atomicAdd(&sh[run_bin], run_n);
+    __syncthreads();
+    unsigned *hi = vh + (int64_t)img * VB;
+    for (int i = threadIdx.x; i < VB; i += NT) {
+        const unsigned v = sh[i];
+        if (v) atomicAdd(&hi[i], v);
+    }
+}
+
+// Step: one CTA of VSTEP_T threads per image.  Prefix sums over the bins
+// find each wanted rank's bin and the count below it; the distinct bins get
+// slots and buffer ranges; mode 1 when the bins hold more than `cap` values
+// together (or the range is unusable).  With mode 0 the radix passes skip
+// the image.
+constexpr int VSTEP_T = 1024, VPER = VB / VSTEP_T;
+__global__ void __launch_bounds__(VSTEP_T) vstep_kernel(SelState *st, FastSel *fs, const unsigned *vh, int64_t cap) {
+    __shared__ unsigned part[VSTEP_T];  // exclusive prefix of each thread's VPER bins
+    __shared__ unsigned wsum[VSTEP_T / 32];
+    const int img = blockIdx.x;
+    FastSel &f = fs[img];
+    float lo, inv;
+    const bool ok = vrange(f, lo, inv);
+    if (!ok) {  // uniform over the CTA
+        if (threadIdx.x == 0) f.mode = 1;
+        return;
+    }
+    const unsigned *hb = vh + (int64_t)img * VB;
+    unsigned c[VPER], tot = 0u;
+#pragma unroll
+    for (int k = 0; k < VPER; ++k) {
+        c[k] = hb[threadIdx.x * VPER + k];
+        tot += c[k];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned v = wsum[lane], x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
+        }
+        wsum[lane] = x - v;  // exclusive over the warps
+    }
+    __syncthreads();
+    part[threadIdx.x] = wsum[warp] + inc - tot;
+    __syncthreads();
+    const SelState &s = st[img];
+    if (threadIdx.x < s.nt) {
+        const int t = threadIdx.x;
+        const unsigned want = s.rank[t];
+        // the last thread whose exclusive prefix is <= want holds the rank
+        int a = 0, b = VSTEP_T - 1;
+        while (a < b) {
+            const int m = (a + b + 1) >> 1;
+            if (part[m] <= want) a = m;
+            else b = m - 1;
+        }
+        unsigned acc = part[a];
+        int bin = a * VPER;
+        for (int k = 0; k < VPER - 1; ++k, ++bin) {
+            const unsigned v = hb[bin];
+            if (acc + v > want) break;
+            acc += v;
+        }
+        f.bin[t] = bin;
+        f.below[t] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ns = 0;
+        unsigned off = 0u;
+        for (int t = 0; t < s.nt; ++t) {
+            int u = 0;
+            while (u < ns && f.sbin[u] != f.bin[t]) ++u;
+            if (u == ns) {
+                f.sbin[ns] = f.bin[t];
+                f.soff[ns] = off;
+                off += hb[f.bin[t]];
+                f.scnt[ns] = 0u;
+                ++ns;
+            }
+            f.slot[t] = u;
+        }
+        f.soff[ns] = off;
+        f.nslot = ns;
+        f.mode = (int64_t)off <= cap ? 0 : 1;
+        st[img].skip = f.mode == 0 ? 1 : 0;
+    }
+}
+
+// Pass G: the values of the wanted bins into the image's candidate buffer
+// (warp-aggregated slot counters; the order within a slot is arbitrary, the
+// select below does not depend on it).
+template <bool DENSE>
+__global__ void __launch_bounds__(NT) vgather_kernel(const float *map, int64_t h, int64_t w, int64_t ld, int64_t is,
+                                                     FastSel *fs, float *cand, int64_t cap) {
+    __shared__ signed char slot_of[VB];
+    __shared__ unsigned soff[kPoolMaxRanks + 1];
+    const int img = blockIdx.y;
+    FastSel &f = fs[img];
+    float lo, inv;
+    if (f.mode != 0 || !vrange(f, lo, inv)) return;  // uniform over the CTA
+    for (int i = threadIdx.x; i < VB; i += NT) slot_of[i] = -1;
+    __syncthreads();
+    const int ns = f.nslot;
+    if (threadIdx.x < ns) slot_of[f.sbin[threadIdx.x]] = (signed char)threadIdx.x;
+    if (threadIdx.x <= ns) soff[threadIdx.x] = f.soff[threadIdx.x];
+    __syncthreads();
+    float *cb = cand + (int64_t)img * cap;
+    const int lane = threadIdx.x & 31;
+    // append the hits of one value per lane: one counter update per
+    // distinct slot among the lanes of `am` that hit
+    auto append = [&](unsigned am, int sl, float q) {
+        unsigned pending = __ballot_sync(am, sl >= 0);
+        while (pending) {
+            const int leader = __ffs(pending) - 1;
+            const int s0 = __shfl_sync(am, sl, leader);
+            const unsigned peers = __ballot_sync(am, sl == s0);
+            unsigned base = 0u;
+            if (lane == leader) base = atomicAdd(&f.scnt[s0], (unsigned)__popc(peers));
+            base = __shfl_sync(am, base, leader);
+            if (sl == s0) {
+                const unsigned idx = soff[s0] + base + (unsigned)__popc(peers & ((1u << lane) - 1u));
+                if (idx < soff[s0 + 1]) cb[idx] = q;  // never more than the bin's count
+            }
+            pending &= ~peers;
+        }
+    };
+    for_item<DENSE, CHK * SEL_SCALE>(map + img * is, nullptr, h, w, ld, blockIdx.x, [&](float q, float) {
+        append(__activemask(), slot_of[vbin(q, lo, inv)], q);
+    });
+}
+
+// Exact select among one bin's candidates: one CTA per (image, wanted
+// rank); four 8-bit radix steps over the candidates' keys with run-length
+// aggregated shared counts.  The key goes to the rank's prefix, where the
+// radix path would leave it.
+constexpr int VSEL_T = 1024;
+__global__ void __launch_bounds__(VSEL_T) vselect_kernel(SelState *st, const FastSel *fs, const float *cand,
+                                                         int64_t cap) {
+    __shared__ unsigned hs[NBIN];
+    __shared__ unsigned s_prefix, s_want;
+    const int img = blockIdx.x, t = blockIdx.y;
+    const FastSel &f = fs[img];
+    if (f.mode != 0 || t >= st[img].nt) return;  // uniform over the CTA
+    const int sl = f.slot[t];
+    const float *cb = cand + (int64_t)img * cap + f.soff[sl];
+    const int c = (int)(f.soff[sl + 1] - f.soff[sl]);
+    if (threadIdx.x == 0) {
+        s_prefix = 0u;
+        s_want = st[img].rank[t] - f.below[t];
+    }
+    unsigned mask = 0u;
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 24 - 8 * pass;
+        for (int i = threadIdx.x; i < NBIN; i += VSEL_T) hs[i] = 0u;
+        __syncthreads();
+        const unsigned prefix = s_prefix;
+        int run_bin = -1;
+        unsigned run_n = 0u;
+        for (int i = threadIdx.x; i < c; i += VSEL_T) {
+            const unsigned k = f2key(cb[i]);
+            if ((k & mask) != prefix) continue;
+            const int b = (int)((k >> shift) & 255u);
+            if (b == run_bin) {
+                ++run_n;
+            } else {
+                if (run_n) atomicAdd(&hs[run_bin], run_n);
+                run_bin = b;
+                run_n = 1u;
+            }
+        }
+        if (run_n) atomicAdd(&hs[run_bin], run_n);
+        __syncthreads();
+        if (threadIdx.x < 32) {  // warp scan: 8 bins a lane
+            const int lane = threadIdx.x;
+            unsigned c[NBIN / 32], tot = 0u;
+#pragma unroll
+            for (int k = 0; k < NBIN / 32; ++k) {
+                c[k] = hs[lane * (NBIN / 32) + k];
+                tot += c[k];
+            }
+            unsigned inc = tot;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += v;
+            }
+            const unsigned want = s_want;
+            const unsigned ballot = __ballot_sync(0xffffffffu, inc > want);
+            const int L = ballot ? __ffs(ballot) - 1 : 31;
+            if (lane == L) {
+                unsigned acc = inc - tot;
+                int b = 0;
+                for (; b < NBIN / 32 - 1; ++b) {
+                    if (acc + c[b] > want) break;
+                    acc += c[b];
+                }
+                s_prefix = prefix | ((unsigned)(L * (NBIN / 32) + b) << shift);
+                s_want = want - acc;
+            }
+        }
+        mask |= 255u << shift;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) st[img].prefix[t] = s_prefix;
+}
+
 // Ranks of the order statistics a percentile needs: floor(h) and floor(h)+1
 // (clamped), h = p/100 (n-1).
 __host__ __device__ inline void pct_ranks(double p, double n, unsigned &lo, unsigned &hi, double &frac) {
@@ -395,7 +703,7 @@ __host__ __device__ inline void pct_ranks(double p, double n, unsigned &lo, unsi
     frac = hh - fl;
 }
 
-__global__ void select_init_kernel(SelState *st, int count, double n, int kind, double parg) {
+__global__ void select_init_kernel(SelState *st, FastSel *fs, int count, double n, int kind, double parg) {
     const int img = blockIdx.x * blockDim.x + threadIdx.x;
     if (img >= count) return;
     SelState s;
@@ -418,7 +726,12 @@ __global__ void select_init_kernel(SelState *st, int count, double n, int kind, 
         s.prefix[2 * i] = s.prefix[2 * i + 1] = 0u;
     }
     unique_prefixes(s);
+    s.skip = 0;
     st[img] = s;
+    FastSel z;
+    memset(&z, 0, sizeof z);
+    z.kmin = 0xffffffffu;
+    fs[img] = z;
 }
 
 // Values of the selected order statistics -> percentile interpolation.
@@ -494,6 +807,9 @@ PoolLayout pool_layout(int64_t h, int64_t w, int count) {
     L.center = take(sizeof(double) * (size_t)count);
     L.state = take(sizeof(SelState) * (size_t)count);
     L.hist = take(sizeof(unsigned) * (size_t)kPoolMaxRanks * NBIN * count);
+    L.fast = take(sizeof(FastSel) * (size_t)count);
+    L.vhist = take(sizeof(unsigned) * (size_t)VB * count);
+    L.cand = take(sizeof(float) * (size_t)vcap(h * w) * count);
     L.bytes = off;
     return L;
 }
@@ -505,6 +821,10 @@ cudaError_t launch_pool_map(const float *map, int64_t h, int64_t w, int64_t ld, 
     double *center = reinterpret_cast<double *>(ws + L.center);
     SelState *sel = reinterpret_cast<SelState *>(ws + L.state);
     unsigned *hist = reinterpret_cast<unsigned *>(ws + L.hist);
+    FastSel *fsel = reinterpret_cast<FastSel *>(ws + L.fast);
+    unsigned *vh = reinterpret_cast<unsigned *>(ws + L.vhist);
+    float *cand = reinterpret_cast<float *>(ws + L.cand);
+    const int64_t cap = vcap(h * w);
     const double n = (double)h * (double)w;
     // dense maps (and mu_1 maps) with 16-byte aligned images: flat chunks
     const bool dense = ld == w && (uintptr_t)map % 16 == 0 && (count == 1 || is % 4 == 0) &&
@@ -541,9 +861,28 @@ cudaError_t launch_pool_map(const float *map, int64_t h, int64_t w, int64_t ld, 
         return cudaGetLastError();
     };
     auto select = [&](double parg) {
-        select_init_kernel<<<fb, 128, 0, st>>>(sel, count, n, kind, parg);
+        select_init_kernel<<<fb, 128, 0, st>>>(sel, fsel, count, n, kind, parg);
+        // value bins first: min / max, bin counts, the wanted bins' values,
+        // an exact select among them; images it cannot take (non-finite
+        // values, crowded bins) go through the radix passes below, which
+        // skip the others
+        cudaError_t r = cudaMemsetAsync(vh, 0, sizeof(unsigned) * (size_t)VB * count, st);
+        if (r != cudaSuccess) return r;
+        if (dense) {
+            vminmax_kernel<true><<<sel_grid, NT, 0, st>>>(map, h, w, ld, is, fsel);
+            vhist_kernel<true><<<sel_grid, NT, 0, st>>>(map, h, w, ld, is, fsel, vh);
+        } else {
+            vminmax_kernel<false><<<sel_grid, NT, 0, st>>>(map, h, w, ld, is, fsel);
+            vhist_kernel<false><<<sel_grid, NT, 0, st>>>(map, h, w, ld, is, fsel, vh);
+        }
+        vstep_kernel<<<count, VSTEP_T, 0, st>>>(sel, fsel, vh, cap);
+        if (dense)
+            vgather_kernel<true><<<sel_grid, NT, 0, st>>>(map, h, w, ld, is, fsel, cand, cap);
+        else
+            vgather_kernel<false><<<sel_grid, NT, 0, st>>>(map, h, w, ld, is, fsel, cand, cap);
+        vselect_kernel<<<dim3(count, kPoolMaxRanks), VSEL_T, 0, st>>>(sel, fsel, cand, cap);
         for (int pass = 0; pass < 4; ++pass) {
-            cudaError_t r = cudaMemsetAsync(hist, 0, sizeof(unsigned) * (size_t)kPoolMaxRanks * NBIN * count, st);
+            r = cudaMemsetAsync(hist, 0, sizeof(unsigned) * (size_t)kPoolMaxRanks * NBIN * count, st);
             if (r != cudaSuccess) return r;
             if (dense)
                 select_hist_kernel<true><<<sel_grid, NT, 0, st>>>(map, h, w, ld, is, pass, sel, hist);

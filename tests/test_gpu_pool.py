@@ -81,6 +81,25 @@ def test_moment_kinds(g, maps, name, kind, args, f):
             assert abs(a - b) <= 1e-6 * max(1.0, abs(b)), (kind, args, a, b)
 
 
+@pytest.mark.parametrize("kind,args,f", ORDER + [("percentile", (80.0,), lambda v: P.percentile(v, 80.0))])
+def test_order_statistics_crowded_and_spread(g, kind, args, f):
+    """Selection first bins the values over [min, max] and selects among the
+    wanted bins' values when they hold at most 65536 of them together, else
+    it runs the radix passes.  Image 0: 80% of 102400 values equal one
+    number (its bin overflows the candidate buffer: the radix passes); image
+    1: the same values spread (the value-bin path); image 2: a narrow cluster
+    near 1 and a long tail, as SSIM maps have."""
+    r = np.random.default_rng(5)
+    n = 320 * 320
+    crowd = r.uniform(0.2, 1.0, n)
+    crowd[r.permutation(n)[: int(0.8 * n)]] = 0.875
+    spread = r.uniform(-0.3, 1.0, n)
+    tail = np.where(r.uniform(size=n) < 0.9, 1.0 - r.exponential(0.004, n), r.uniform(0.0, 1.0, n))
+    m = torch.tensor(np.stack([crowd, spread, tail]).reshape(3, 320, 320), dtype=torch.float32, device=DEV)
+    got = g.ssim_pool(m, kind, *args).cpu().tolist()
+    assert got == _refs(m, f)
+
+
 def test_degenerate_all_ones(g, maps):
     m = maps["ones"]
     assert g.ssim_pool(m, "gm_dssim").item() == 0.0
