@@ -23,6 +23,16 @@ struct DeviceOnce {
     void set(int dev) { done[dev].store(true, std::memory_order_release); }
 };
 
+// The correctly rounded fp32 value of an integer |v| < 2^48, the value
+// __ll2float_rn gives, without the 64-bit conversion (which runs on the slow
+// FP64 pipe): v = hi 2^24 + lo with 0 <= lo < 2^24, both parts exact in
+// fp32, and the FMA rounds the exact hi 2^24 + lo once.
+__device__ __forceinline__ float i48_to_f32(int64_t v) {
+    const int hi = (int)(v >> 24);
+    const int lo = (int)(v & 0xffffff);
+    return fmaf((float)hi, 16777216.0f, (float)lo);
+}
+
 // ---------------------------------------------------------------- element loads
 
 template <typename T>

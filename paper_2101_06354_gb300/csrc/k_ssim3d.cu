@@ -460,8 +460,17 @@ __global__ void __launch_bounds__(NT, (ssim3d_min_ctas<A, In>()))
                             A1 = __ll2float_rn(U2 - W2) + L.C1x2n2;
                             B1 = __ll2float_rn(U2 + W2) + L.C1x2n2;
                         }
-                        // variances need the exact int64 differences
-                        const float A2 = __ll2float_rn(Vu - Vw) + L.C2x2n2, B2 = __ll2float_rn(Vu + Vw) + L.C2x2n2;
+                        // variances need the exact int64 differences; with 32-bit sums
+                        // |Vu +- Vw| < 2 N^2 (2 x 255 scale)^2 < 2^48 (N < 8256 at scale 1;
+                        // the unsigned level's bounds), so the conversion avoids the FP64 pipe
+                        float A2, B2;
+                        if constexpr (sizeof(A) == 4) {
+                            A2 = i48_to_f32(Vu - Vw) + L.C2x2n2;
+                            B2 = i48_to_f32(Vu + Vw) + L.C2x2n2;
+                        } else {
+                            A2 = __ll2float_rn(Vu - Vw) + L.C2x2n2;
+                            B2 = __ll2float_rn(Vu + Vw) + L.C2x2n2;
+                        }
                         const float cs = __fdividef(A2, B2);
                         const float qv = __fdividef(A1, B1) * cs;
                         accQ += qv;
@@ -660,7 +669,8 @@ __global__ void __launch_bounds__(NTC, 3)
                         const int n32 = (int)N;
                         const int64_t Vu = (int64_t)n32 * su2 - (int64_t)su * su;
                         const int64_t Vw = (int64_t)n32 * sw2 - (int64_t)sw * sw;
-                        const float A2 = __ll2float_rn(Vu - Vw) + L.C2x2n2, B2 = __ll2float_rn(Vu + Vw) + L.C2x2n2;
+                        // |Vu +- Vw| < 2 N^2 510^2 < 2^48: no 64-bit conversion
+                        const float A2 = i48_to_f32(Vu - Vw) + L.C2x2n2, B2 = i48_to_f32(Vu + Vw) + L.C2x2n2;
                         const float cs = __fdividef(A2, B2);
                         const float qv = __fdividef(A1, B1) * cs;
                         accQ += qv;
