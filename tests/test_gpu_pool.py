@@ -88,14 +88,18 @@ def test_order_statistics_crowded_and_spread(g, kind, args, f):
     it runs the radix passes.  Image 0: 80% of 102400 values equal one
     number (its bin overflows the candidate buffer: the radix passes); image
     1: the same values spread (the value-bin path); image 2: a narrow cluster
-    near 1 and a long tail, as SSIM maps have."""
+    near 1 and a long tail, as SSIM maps have; images 3 and 4: values over
+    [-5, 5] and over [0, 255], maps that are not SSIM maps."""
     r = np.random.default_rng(5)
     n = 320 * 320
     crowd = r.uniform(0.2, 1.0, n)
     crowd[r.permutation(n)[: int(0.8 * n)]] = 0.875
     spread = r.uniform(-0.3, 1.0, n)
     tail = np.where(r.uniform(size=n) < 0.9, 1.0 - r.exponential(0.004, n), r.uniform(0.0, 1.0, n))
-    m = torch.tensor(np.stack([crowd, spread, tail]).reshape(3, 320, 320), dtype=torch.float32, device=DEV)
+    wide = r.uniform(-5.0, 5.0, n)
+    pixels = r.uniform(0.0, 255.0, n)
+    m = torch.tensor(np.stack([crowd, spread, tail, wide, pixels]).reshape(5, 320, 320), dtype=torch.float32,
+                     device=DEV)
     got = g.ssim_pool(m, kind, *args).cpu().tolist()
     assert got == _refs(m, f)
 
